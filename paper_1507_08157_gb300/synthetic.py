@@ -1,0 +1,365 @@
+"""Seeded synthetic localized-orbital systems.
+
+This module is the one place both sides of every parity check take their inputs from: the CUDA
+library and the CPU oracle each receive the arrays built here and nothing else. It holds none of
+the TDDFT method's arithmetic. It only does what the ground-state calculation does before a
+linear-response run starts (the paper's Sec. II C takes all of it as given):
+
+* draws atom positions (random sequential adsorption, minimum separation);
+* tabulates atom-centred Gaussian support functions {phi} (valence) and {chi} (conduction) on a
+  periodic real-space grid, inside one cubic box per atom, hard-cut at a localisation radius and
+  normalised on the grid (dV * sum f^2 = 1);
+* forms their overlap matrices S^phi, S^chi from those tables;
+* draws random sparse symmetric Hamiltonians H^phi, H^chi with exponentially decaying entries,
+  shifts H^chi so the Kohn-Sham gap is a set value, and builds the density kernels P^v, P^c as
+  spectral projectors of the generalised eigenproblems H c = eps S c;
+* tabulates the ground-state density n0 = 2 sum_ab phi_a P^v_ab phi_b.
+
+It also draws the random starting vectors the eigensolver needs, which each side then masks and
+projects itself.
+
+Units: Hartree atomic units (bohr, Ha) everywhere in the returned arrays. Grid arrays are C-order
+[ix][iy][iz] (z fastest); a box of extent (ex, ey, ez) with origin (ox, oy, oz) covers the grid
+points ((ox+i) mod n, (oy+j) mod n, (oz+l) mod n).
+"""
+from __future__ import annotations
+
+import dataclasses
+import hashlib
+import math
+
+import numpy as np
+import scipy.linalg
+
+BOHR_PER_ANG = 1.0 / 0.529177210903  # CODATA 2018
+HA_PER_EV = 1.0 / 27.211386246
+
+
+@dataclasses.dataclass(frozen=True)
+class Recipe:
+    """Parameters of one synthetic chromophore-like system (lengths in Angstrom, energies in eV/Ha)."""
+
+    natoms: int
+    cell_ang: float
+    ngrid: int
+    nphi: int = 4              # valence functions per atom: s, px, py, pz
+    nchi: int = 4              # conduction functions per atom: 4 (s, p) or 9 (s, p, d)
+    radius_ang: float = 7.0    # localisation radius of every support function
+    width_ang: tuple = (0.6, 1.2)
+    min_sep_ang: float = 1.4
+    gap_ev: float = 2.0
+    h_sigma: float = 0.1       # Ha, std of the random Hamiltonian entries
+    h_decay_ang: float = 2.0   # entries decay as exp(-d / h_decay)
+    kernel_cutoff_ang: float = 0.0   # <= 0: response kernels not truncated
+    seed: int = 0
+
+
+# The smallest workload: 8 atoms, 16 A cell, 48^3 grid, 4 phi + 4 chi (s, p) per atom, 7 A radius,
+# no truncation. Small enough for the dense oracle.
+CONFIG_SMALL = Recipe(natoms=8, cell_ang=16.0, ngrid=48, nphi=4, nchi=4, radius_ang=7.0, seed=1)
+
+# The chromophore-sized workload: 140 atoms in a 30 A cell, 0.25 A grid (120^3), 4 phi + 9 chi per
+# atom, 8 A radius, response kernels truncated at 12 A.
+CONFIG_CHROMOPHORE = Recipe(natoms=140, cell_ang=30.0, ngrid=120, nphi=4, nchi=9, radius_ang=8.0,
+                            kernel_cutoff_ang=12.0, seed=2)
+
+
+@dataclasses.dataclass
+class FunctionSet:
+    """Support functions tabulated in per-function periodic boxes (Hartree atomic units)."""
+
+    atom: np.ndarray   # int32 [nfun]   owning atom; functions are grouped by atom
+    box: np.ndarray    # int32 [nfun,6] origin (ox,oy,oz) in [0,n) and extent (ex,ey,ez)
+    off: np.ndarray    # int64 [nfun+1] offsets into val
+    val: np.ndarray    # float64 [off[-1]] box values, C order [i][j][l] (z fastest)
+
+    @property
+    def nfun(self) -> int:
+        return int(self.atom.shape[0])
+
+    def values(self, f: int) -> np.ndarray:
+        ex, ey, ez = (int(v) for v in self.box[f, 3:])
+        return self.val[self.off[f]:self.off[f + 1]].reshape(ex, ey, ez)
+
+
+@dataclasses.dataclass
+class System:
+    recipe: Recipe
+    cell: float            # bohr, cubic periodic cell side
+    n: int                 # grid points per side
+    pos: np.ndarray        # float64 [natoms,3] bohr
+    phi: FunctionSet
+    chi: FunctionSet
+    S_phi: np.ndarray
+    S_chi: np.ndarray
+    H_phi: np.ndarray
+    H_chi: np.ndarray
+    P_v: np.ndarray
+    P_c: np.ndarray
+    n0: np.ndarray         # float64 [n,n,n]
+    kernel_cutoff: float   # bohr; <= 0 means no truncation
+    n_occ: int
+    n_cond: int
+
+    @property
+    def natoms(self) -> int:
+        return int(self.pos.shape[0])
+
+    @property
+    def h(self) -> float:
+        return self.cell / self.n
+
+    @property
+    def dV(self) -> float:
+        return self.h ** 3
+
+
+# ----------------------------------------------------------------------------------------------
+# geometry and tables
+
+def _rsa_positions(rng, natoms, cell, min_sep):
+    pos = np.zeros((natoms, 3))
+    placed = 0
+    tries = 0
+    while placed < natoms:
+        tries += 1
+        if tries > 2000000:
+            raise RuntimeError("could not place atoms at the requested minimum separation")
+        x = rng.uniform(0.0, cell, size=3)
+        if placed:
+            d = pos[:placed] - x
+            d -= cell * np.round(d / cell)
+            if np.min(np.einsum("ij,ij->i", d, d)) < min_sep * min_sep:
+                continue
+        pos[placed] = x
+        placed += 1
+    return pos
+
+
+def _angular(kind, dx, dy, dz, w):
+    """Real solid-harmonic prefactors (up to normalisation): s, p_x, p_y, p_z, then 5 d."""
+    if kind == 0:
+        return np.ones_like(dx)
+    if kind == 1:
+        return dx / w
+    if kind == 2:
+        return dy / w
+    if kind == 3:
+        return dz / w
+    w2 = w * w
+    if kind == 4:
+        return dx * dy / w2
+    if kind == 5:
+        return dy * dz / w2
+    if kind == 6:
+        return dz * dx / w2
+    if kind == 7:
+        return 0.5 * (dx * dx - dy * dy) / w2
+    if kind == 8:
+        return (2.0 * dz * dz - dx * dx - dy * dy) / (2.0 * math.sqrt(3.0) * w2)
+    raise ValueError(kind)
+
+
+def box_half_width(radius, h):
+    """Half width m (grid points) of the cube that holds a sphere of the given radius."""
+    return int(math.ceil(radius / h)) + 1
+
+
+def _tabulate(rng_w, pos, nper, cell, n, radius, width):
+    h = cell / n
+    m = box_half_width(radius, h)
+    e = 2 * m + 1
+    if e > n:
+        raise ValueError("localisation box wider than the cell: the cell must exceed 2R + 2h")
+    natoms = pos.shape[0]
+    nfun = natoms * nper
+    atom = np.repeat(np.arange(natoms, dtype=np.int32), nper)
+    box = np.zeros((nfun, 6), dtype=np.int32)
+    off = np.arange(nfun + 1, dtype=np.int64) * (e ** 3)
+    val = np.empty(int(off[-1]), dtype=np.float64)
+    dV = h ** 3
+    t = np.arange(-m, m + 1, dtype=np.float64)
+    for ia in range(natoms):
+        c = np.rint(pos[ia] / h).astype(np.int64)
+        d = [(c[a] + t) * h - pos[ia, a] for a in range(3)]
+        dx, dy, dz = np.meshgrid(d[0], d[1], d[2], indexing="ij")
+        r2 = dx * dx + dy * dy + dz * dz
+        inside = r2 <= radius * radius
+        for kf in range(nper):
+            f = ia * nper + kf
+            w = rng_w.uniform(width[0], width[1])
+            g = np.exp(-r2 / (w * w)) * _angular(kf, dx, dy, dz, w)
+            g[~inside] = 0.0
+            g /= math.sqrt(dV * np.sum(g * g))
+            val[off[f]:off[f + 1]] = g.ravel()
+            box[f, :3] = np.mod(c - m, n)
+            box[f, 3:] = e
+    return FunctionSet(atom=atom, box=box, off=off, val=val)
+
+
+def _axis_overlaps(oa, ob, e, n):
+    """Common grid points of two wrapped ranges [oa, oa+e) and [ob, ob+e) (mod n).
+
+    Returns a list of (start_in_a, start_in_b, length) runs.
+    """
+    shift = (ob - oa) % n
+    runs = []
+    if shift < e:
+        runs.append((shift, 0, e - shift))
+    if shift + e > n:
+        ln = shift + e - n
+        runs.append((0, n - shift, min(ln, e)))
+    return runs
+
+
+def _atom_pairs_within(pos, cell, rmax):
+    natoms = pos.shape[0]
+    pairs = []
+    for i in range(natoms):
+        d = pos[i:] - pos[i]
+        d -= cell * np.round(d / cell)
+        dist = np.sqrt(np.einsum("ij,ij->i", d, d))
+        for jj in np.nonzero(dist <= rmax)[0]:
+            pairs.append((i, i + int(jj), float(dist[jj])))
+    return pairs
+
+
+def _atom_block(fs, ia, nper):
+    f0 = ia * nper
+    e = int(fs.box[f0, 3])
+    return fs.val[fs.off[f0]:fs.off[f0 + nper]].reshape(nper, e, e, e), fs.box[f0, :3], e
+
+
+def _pair_overlap(fa, fb, nper_a, nper_b, ia, ib, n):
+    """sum_r f_a(r) f_b(r) for all functions of atoms ia (set fa) and ib (set fb)."""
+    A, oa, e = _atom_block(fa, ia, nper_a)
+    B, ob, _ = _atom_block(fb, ib, nper_b)
+    out = np.zeros((nper_a, nper_b))
+    rx = _axis_overlaps(int(oa[0]), int(ob[0]), e, n)
+    ry = _axis_overlaps(int(oa[1]), int(ob[1]), e, n)
+    rz = _axis_overlaps(int(oa[2]), int(ob[2]), e, n)
+    for (ax, bx, lx) in rx:
+        for (ay, by, ly) in ry:
+            for (az, bz, lz) in rz:
+                a = A[:, ax:ax + lx, ay:ay + ly, az:az + lz].reshape(nper_a, -1)
+                b = B[:, bx:bx + lx, by:by + ly, bz:bz + lz].reshape(nper_b, -1)
+                out += a @ b.T
+    return out
+
+
+def _overlap_matrix(fs, nper, pos, cell, n, dV, rmax):
+    natoms = pos.shape[0]
+    N = natoms * nper
+    S = np.zeros((N, N))
+    for (i, j, _) in _atom_pairs_within(pos, cell, rmax):
+        blk = dV * _pair_overlap(fs, fs, nper, nper, i, j, n)
+        S[i * nper:(i + 1) * nper, j * nper:(j + 1) * nper] = blk
+        if i != j:
+            S[j * nper:(j + 1) * nper, i * nper:(i + 1) * nper] = blk.T
+    return 0.5 * (S + S.T)
+
+
+def _random_hamiltonian(rng, pos, cell, nper, rmax, sigma, decay):
+    natoms = pos.shape[0]
+    N = natoms * nper
+    H = np.zeros((N, N))
+    for (i, j, d) in _atom_pairs_within(pos, cell, rmax):
+        blk = rng.normal(0.0, sigma, size=(nper, nper)) * math.exp(-d / decay)
+        if i == j:
+            blk = 0.5 * (blk + blk.T)
+        H[i * nper:(i + 1) * nper, j * nper:(j + 1) * nper] = blk
+        if i != j:
+            H[j * nper:(j + 1) * nper, i * nper:(i + 1) * nper] = blk.T
+    return H
+
+
+def _density_on_grid(fs, nper, K, pos, cell, n, rmax):
+    """sum_ab f_a(r) K_ab f_b(r) on the full grid, over atom pairs within rmax."""
+    out = np.zeros((n, n, n))
+    for (i, j, _) in _atom_pairs_within(pos, cell, rmax):
+        for (ia, ib) in ((i, j), (j, i)) if i != j else ((i, i),):
+            A, oa, e = _atom_block(fs, ia, nper)
+            B, ob, _ = _atom_block(fs, ib, nper)
+            Kab = K[ia * nper:(ia + 1) * nper, ib * nper:(ib + 1) * nper]
+            rx = _axis_overlaps(int(oa[0]), int(ob[0]), e, n)
+            ry = _axis_overlaps(int(oa[1]), int(ob[1]), e, n)
+            rz = _axis_overlaps(int(oa[2]), int(ob[2]), e, n)
+            for (ax, bx, lx) in rx:
+                for (ay, by, ly) in ry:
+                    for (az, bz, lz) in rz:
+                        a = A[:, ax:ax + lx, ay:ay + ly, az:az + lz].reshape(nper, -1)
+                        b = B[:, bx:bx + lx, by:by + ly, bz:bz + lz].reshape(nper, -1)
+                        contrib = np.einsum("ar,ar->r", Kab @ b, a).reshape(lx, ly, lz)
+                        gx = (int(oa[0]) + ax + np.arange(lx)) % n
+                        gy = (int(oa[1]) + ay + np.arange(ly)) % n
+                        gz = (int(oa[2]) + az + np.arange(lz)) % n
+                        out[np.ix_(gx, gy, gz)] += contrib
+    return out
+
+
+def _spectral_projector(H, S, nkeep):
+    eps, C = scipy.linalg.eigh(H, S)
+    Ck = C[:, :nkeep]
+    return eps, Ck @ Ck.T
+
+
+def generate(recipe: Recipe) -> System:
+    """Build one seeded synthetic system from a recipe."""
+    ss = np.random.SeedSequence(recipe.seed)
+    r_pos, r_wphi, r_wchi, r_hphi, r_hchi = (np.random.default_rng(s) for s in ss.spawn(5))
+    cell = recipe.cell_ang * BOHR_PER_ANG
+    n = int(recipe.ngrid)
+    h = cell / n
+    R = recipe.radius_ang * BOHR_PER_ANG
+    pos = _rsa_positions(r_pos, recipe.natoms, cell, recipe.min_sep_ang * BOHR_PER_ANG)
+    width = (recipe.width_ang[0] * BOHR_PER_ANG, recipe.width_ang[1] * BOHR_PER_ANG)
+    phi = _tabulate(r_wphi, pos, recipe.nphi, cell, n, R, width)
+    chi = _tabulate(r_wchi, pos, recipe.nchi, cell, n, R, width)
+    dV = h ** 3
+    S_phi = _overlap_matrix(phi, recipe.nphi, pos, cell, n, dV, 2.0 * R)
+    S_chi = _overlap_matrix(chi, recipe.nchi, pos, cell, n, dV, 2.0 * R)
+    decay = recipe.h_decay_ang * BOHR_PER_ANG
+    H_phi = _random_hamiltonian(r_hphi, pos, cell, recipe.nphi, 2.0 * R, recipe.h_sigma, decay)
+    H_chi = _random_hamiltonian(r_hchi, pos, cell, recipe.nchi, 2.0 * R, recipe.h_sigma, decay)
+    n_phi = recipe.natoms * recipe.nphi
+    n_chi = recipe.natoms * recipe.nchi
+    n_occ = n_phi // 2
+    n_cond = n_chi // 2
+    eps_v, P_v = _spectral_projector(H_phi, S_phi, n_occ)
+    eps_c = scipy.linalg.eigh(H_chi, S_chi, eigvals_only=True)
+    shift = recipe.gap_ev * HA_PER_EV - (eps_c[0] - eps_v[n_occ - 1])
+    H_chi = H_chi + shift * S_chi
+    _, P_c = _spectral_projector(H_chi, S_chi, n_cond)
+    n0 = 2.0 * _density_on_grid(phi, recipe.nphi, P_v, pos, cell, n, 2.0 * R)
+    return System(recipe=recipe, cell=cell, n=n, pos=pos, phi=phi, chi=chi,
+                  S_phi=S_phi, S_chi=S_chi, H_phi=H_phi, H_chi=H_chi, P_v=P_v, P_c=P_c,
+                  n0=n0, kernel_cutoff=recipe.kernel_cutoff_ang * BOHR_PER_ANG,
+                  n_occ=n_occ, n_cond=n_cond)
+
+
+def initial_guess(sys: System, k: int, seed: int):
+    """Random starting vectors (paper Sec. II B: CG starts from a random vector).
+
+    Returns one float64 array [k, N_chi, N_phi] of N(0,1) draws. Masking to the kernel pattern,
+    projection and orthonormalisation are the solver's job, not the generator's.
+    """
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 7919]))
+    nc, nv = sys.chi.nfun, sys.phi.nfun
+    return rng.standard_normal((k, nc, nv))
+
+
+def random_kernels(sys: System, k: int, seed: int):
+    """Random (P^p, P^q) batches [k, N_chi, N_phi] for operator tests (not projected)."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 104729]))
+    nc, nv = sys.chi.nfun, sys.phi.nfun
+    return (rng.standard_normal((k, nc, nv)), rng.standard_normal((k, nc, nv)))
+
+
+def fingerprint(sys: System) -> str:
+    """Short hash of the generated arrays, for checking two machines built the same system."""
+    hsh = hashlib.sha256()
+    for a in (sys.pos, sys.S_phi, sys.S_chi, sys.H_phi, sys.H_chi, sys.P_v, sys.P_c, sys.n0):
+        hsh.update(np.ascontiguousarray(a).tobytes())
+    hsh.update(sys.phi.val[::97].tobytes())
+    hsh.update(sys.chi.val[::97].tobytes())
+    return hsh.hexdigest()[:16]
