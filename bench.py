@@ -1,0 +1,303 @@
+"""Benchmark: full-TDDFT PCG iterations on the chromophore-sized synthetic workload.
+
+One step = one preconditioned-CG iteration (tddft_pcg_step) on k = 10 state pairs: traces and
+Q (Sec. III C), multi-state gradient, inner-CG preconditioner (Eq. precond), conjugation, one
+batched operator application on the search directions (Eq. operator_RPA: L -> P map, Kohn-Sham
+difference products, response density, FFT Hartree + LDA kernel, potential integrals, coupling
+products), the sum-functional line step and sign flip + Gram-Schmidt (Eq. ortho).
+
+Metric: operator applies (state pairs) per second over whole iterations, counting the k applies
+of each iteration and the k of every periodic re-application. The end-to-end figure runs
+tddft_apply on pinned host buffers (host->device and device->host copies inside the timed
+region). `--impl reference` times the FP64 CPU oracle on a bounded sample of one application.
+
+Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under torch.distributed.run,
+one independent replica per GPU (the single-system path has no data-parallel split).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "TDDFT operator applies/s; time to k states at 1e-5 Ha, learned vs plain PCG"
+UNIT = "applies/s"
+WORKLOAD = ("chromophore-140: 140 pseudo-atoms in a 30 A cell, 120^3 grid (0.25 A), 4 phi + 9 chi "
+            "per atom, 8 A localisation radius, 12 A kernel cutoff, k=10 states, synthetic seeded")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--k", type=int, default=10)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--config", default="chromophore", choices=["chromophore", "small"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def recipe(name):
+    from paper_1507_08157_gb300 import synthetic as sy
+    return sy.CONFIG_CHROMOPHORE if name == "chromophore" else sy.CONFIG_SMALL
+
+
+def workload_name(args):
+    if args.config == "small":
+        return "small-8: 8 pseudo-atoms, 16 A cell, 48^3 grid, 4 phi + 4 chi per atom, 7 A radius, no truncation"
+    return WORKLOAD
+
+
+# ------------------------------------------------------------------------------------------------
+# GPU clocks during the timed region
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in getattr(self, "lines", []):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 10:
+                continue
+            try:
+                clk, mx, util = float(f[1]), float(f[2]), float(f[4])
+            except ValueError:
+                continue
+            smax = mx
+            if util > 0:
+                sm.append(clk)
+            for name, v in zip(names, f[6:10]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------------
+def cpu_oracle_sample(sys_, target_s=15.0):
+    """Time the FP64 oracle's operator application on a bounded sample and scale it to one
+    state-pair application: all matrix products and one FFT Poisson solve in full, the response
+    density and potential integrals on the chi functions of the first m atoms (their cost is
+    linear in the chi atoms covered), scaled by natoms / m."""
+    from oracle import grid as ogrid
+    from oracle import operator as oop
+    from paper_1507_08157_gb300 import synthetic as sy
+    op = oop.Operator(sys_)
+    Pp, Pq = sy.random_kernels(sys_, 1, 9)
+    t0 = time.perf_counter()
+    Pc, Hc, Hv, Pv = op.Pc, op.Hc, op.Hv, op.Pv
+    _ = Pc @ Hc @ Pp[0] - Pp[0] @ Hv @ Pv
+    fq = Pc @ Hc @ Pq[0] - Pq[0] @ Hv @ Pv
+    rho_full = np.zeros((1, sys_.n, sys_.n, sys_.n))
+    V = op.response_potential(rho_full)
+    _ = fq + 2.0 * Pc @ np.zeros_like(Pq[0]) @ Pv
+    t_fixed = time.perf_counter() - t0
+    chi_sub = ogrid.BoxedSet(sys_.chi, sys_.n)
+    groups = chi_sub.groups
+    m, spent = 0, 0.0
+    while m < len(groups) and spent < target_s:
+        chi_sub.groups = groups[m:m + 1]
+        t1 = time.perf_counter()
+        ogrid.response_density(chi_sub, op.phi, Pq)
+        ogrid.potential_integrals(chi_sub, op.phi, V, sys_.dV)
+        spent += time.perf_counter() - t1
+        m += 1
+    per_apply = t_fixed + spent * len(groups) / max(m, 1)
+    return {"value": 1.0 / per_apply, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": (f"one state-pair application: matrix products and FFT Poisson solve in full, "
+                       f"grid contractions on the chi functions of {m} of {len(groups)} atoms "
+                       f"({spent:.1f} s), scaled linearly; numpy/scipy float64, BLAS threads = all cores")}
+
+
+# ------------------------------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_1507_08157_gb300 import synthetic as sy
+    s = sy.generate(recipe(args.config))
+    vals = []
+    for i in range(args.warmup + args.steps):
+        r = cpu_oracle_sample(s, target_s=3.0)
+        if i >= args.warmup:
+            vals.append(r["value"])
+    v = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * args.k / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": workload_name(args), "states": args.k, "precision": "fp64"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1507_08157_gb300 import synthetic as sy
+    from paper_1507_08157_gb300 import tddft
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    tddft.load()
+    s = sy.generate(recipe(args.config))
+    stream = torch.cuda.current_stream()
+    ctx = tddft.Context(s, precision=args.precision, stream=stream.cuda_stream, tol=1e-5)
+    k = args.k
+    st = ctx.state(sy.initial_guess(s, k, 0))
+    for _ in range(args.warmup):
+        st.step()
+    reapply = ctx.options.reapply_every
+    it0 = args.warmup
+    extra = sum(1 for i in range(it0, it0 + args.steps) if reapply > 0 and (i + 1) % reapply == 0)
+    applies = k * (args.steps + extra)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    ctx.profile(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            om, res = st.step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    t = torch.tensor([ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = applies * world / (ms_max / 1000.0)
+
+    # end to end: tddft_apply from pinned host buffers, copies inside the timed region
+    Pp, Pq = sy.random_kernels(s, k, 3)
+    hPp = torch.from_numpy(Pp).pin_memory()
+    hPq = torch.from_numpy(Pq).pin_memory()
+    hfp = torch.empty_like(hPp).pin_memory()
+    hfq = torch.empty_like(hPq).pin_memory()
+    dPp, dPq = hPp.cuda(), hPq.cuda()
+    for _ in range(2):
+        ctx.apply(hPp, hPq, hfp, hfq)
+    barrier()
+    t0 = time.perf_counter()
+    n_e2e = max(3, args.steps // 2)
+    for _ in range(n_e2e):
+        ctx.apply(hPp, hPq, hfp, hfq)
+    e2e_s = time.perf_counter() - t0
+    # device-resident operator only (context figure)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(n_e2e):
+        ctx.apply(dPp, dPq)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    apply_only = k * n_e2e / (e0.elapsed_time(e1) / 1000.0)
+    e2e = {"value": k * n_e2e * world / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(hPp.numel() * 8 * 2), "d2h_bytes_per_step": int(hfp.numel() * 8 * 2)}
+
+    # roofline of the dominant stage
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    name, (launches, dms, dfl, dby) = dom
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    clock = clk.summary()
+    sm_mhz = clock["sm_max_mhz"] or 2070.0
+    if name in ("fft_poisson_fxc", "vector", "trace"):
+        achieved = dby / (dms / 1000.0) / 1e9
+        peak = peaks.get("hbm_gbs", 6800.0)
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "kernel": name,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s"}
+    else:
+        # CUDA-core float32 (mixed) or float64 contraction: ALU bound.
+        lanes = 128 if args.precision == "mixed" else 2
+        peak = 152 * lanes * 2 * sm_mhz * 1e6 / 1e12
+        achieved = dfl / (dms / 1000.0) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": name,
+                "peak_source": f"152 SMs x {lanes} lanes x 2 flop x {sm_mhz:.0f} MHz"}
+    gpu_launches = sum(v[0] for v in prof.values()) + 4 * prof.get("fft_poisson_fxc", (0,))[0]
+    stages = {n: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / max(ms, 1e-9), 4)}
+              for n, v in prof.items() if v[0]}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
+                "config": {"workload": workload_name(args), "states": k, "precision": args.precision,
+                           "parallelism": f"replicas{world}" if world > 1 else "single",
+                           "l2": "inputs larger than L2 (function tables > 1 GB per pass)",
+                           "applies_per_step": applies / args.steps},
+                "e2e": e2e, "apply_only": {"value": apply_only, "unit": UNIT},
+                "roofline": roof, "stages": stages, "gpu_launches": int(gpu_launches),
+                "clocks": {k_: clock[k_] for k_ in ("sm_mhz", "sm_max_mhz", "reasons")},
+                "omega_last": [float(x) for x in om], "resid_last": [float(x) for x in res]}
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_oracle_sample(s)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

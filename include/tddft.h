@@ -1,0 +1,203 @@
+/*
+ * tddft.h -- C ABI of the GB300 full-TDDFT (Tsiper p/q) operator and PCG eigensolver.
+ *
+ * Method: linear-response TDDFT beyond the Tamm-Dancoff approximation in a mixed representation
+ * of localised conduction functions {chi} and valence functions {phi} (Zuehlsdorff, Hine, Payne,
+ * Haynes, "Linear-scaling time-dependent density-functional theory beyond the Tamm-Dancoff
+ * approximation", 2015). Equation names below are the paper's labels.
+ *
+ * Conventions (all entry points):
+ *  - Hartree atomic units (bohr, Ha). All arrays are row-major (C order). Grid arrays are
+ *    [ix][iy][iz] with z fastest; n^3 points on a cubic periodic cell.
+ *  - Matrices are dense float64: N_chi x N_chi, N_phi x N_phi, and response kernels N_chi x N_phi
+ *    (rows = chi functions, columns = phi functions). A batch of k kernels is [k][N_chi][N_phi].
+ *  - Ownership: the caller owns every pointer it passes. tddft_create deep-copies the system into
+ *    device memory owned by the context; nothing keeps a caller pointer after a call returns.
+ *  - Host or device: array arguments of tddft_apply, tddft_state_create/get and the component
+ *    entry points may be host memory or device memory of the context's GPU; the library tells
+ *    them apart with cudaPointerGetAttributes. Device pointers must be 8-byte aligned.
+ *  - Ordering: all GPU work is issued on the stream given to tddft_create; calls return after
+ *    their results are in the caller's buffers (they synchronise that stream).
+ *  - Errors: a non-zero tddft_status; the message is kept on the context (tddft_last_error).
+ *    Nothing throws across the ABI. Outputs are undefined after an error, except where noted.
+ *  - Threads: a context (and its states) must not be used by two threads at once.
+ */
+#ifndef TDDFT_H
+#define TDDFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TDDFT_OK = 0,
+    TDDFT_E_INVALID = 1,        /* bad argument, size or layout */
+    TDDFT_E_NOMEM = 2,          /* device allocation failed */
+    TDDFT_E_CUDA = 3,           /* CUDA runtime error (message names the call) */
+    TDDFT_E_NOT_CONVERGED = 4,  /* tddft_solve hit max_iter; outputs hold the last iterate */
+    TDDFT_E_BREAKDOWN = 5,      /* NaN/Inf, or a non-positive norm in Gram-Schmidt */
+    TDDFT_E_TIMEOUT = 6,        /* reserved: a bounded device wait expired */
+    TDDFT_E_PAIRING = 7         /* converged pairs fail the +-omega pairing check */
+} tddft_status;
+
+enum { TDDFT_FP64 = 0, TDDFT_MIXED = 1 };                       /* tddft_options.precision */
+enum { TDDFT_MODE_FULL = 0, TDDFT_MODE_TDA = 1, TDDFT_MODE_D_ONLY = 2 };
+enum { TDDFT_PRECOND_NONE = 0, TDDFT_PRECOND_ITER = 1 };
+enum { TDDFT_FXC_NONE = 0, TDDFT_FXC_LDA_PW92 = 1 };
+
+/* Localised functions tabulated in periodic boxes (paper Sec. II C: NGWFs phi_alpha, chi_alpha).
+ * Function f covers the grid points ((ox+i) mod n, (oy+j) mod n, (oz+l) mod n) for
+ * 0 <= i < ex, 0 <= j < ey, 0 <= l < ez, with box[6f..6f+5] = (ox, oy, oz, ex, ey, ez),
+ * 0 <= o < n, 1 <= e <= n. Its values are val[off[f] .. off[f+1]), C order (l fastest), and
+ * off[f+1] - off[f] = ex*ey*ez. atom[f] is the owning atom (used for the kernel cutoff). */
+typedef struct {
+    int32_t nfun;
+    const int32_t *atom;
+    const int32_t *box;
+    const int64_t *off;
+    const double *val;
+} tddft_funcs;
+
+/* One system: the ground-state inputs the linear-response calculation takes as given
+ * (Sec. II C). All host pointers. */
+typedef struct {
+    double cell;              /* cubic cell side (bohr) */
+    int32_t n;                /* grid points per side: 2^a 3^b 5^c, 8 <= n <= 256 */
+    int32_t natoms;
+    const double *pos;        /* [natoms][3] (bohr) */
+    tddft_funcs phi;          /* valence functions, N_phi = phi.nfun */
+    tddft_funcs chi;          /* conduction functions, N_chi = chi.nfun */
+    const double *S_chi;      /* [N_chi][N_chi] overlap <chi_a|chi_b> */
+    const double *S_phi;      /* [N_phi][N_phi] */
+    const double *H_chi;      /* [N_chi][N_chi] Kohn-Sham Hamiltonian in chi */
+    const double *H_phi;      /* [N_phi][N_phi] */
+    const double *P_v;        /* [N_phi][N_phi] valence density kernel (contravariant) */
+    const double *P_c;        /* [N_chi][N_chi] conduction density kernel (contravariant) */
+    const double *n0;         /* [n^3] ground-state density (bohr^-3), for f_xc */
+    int32_t fxc_kind;         /* TDDFT_FXC_LDA_PW92 or TDDFT_FXC_NONE (Hartree only) */
+    double kernel_cutoff;     /* bohr; <= 0: response kernels not truncated. Otherwise the
+                                 auxiliary matrices L (Eq. auxiliary) keep entry (a,b) only when
+                                 the minimum-image distance of the atoms of chi_a and phi_b is
+                                 <= kernel_cutoff */
+} tddft_system;
+
+typedef struct {
+    int32_t precision;        /* TDDFT_FP64: all arithmetic in float64.
+                                 TDDFT_MIXED: matrices, grids and FFTs in float32; traces,
+                                 line search, Gram-Schmidt, eigenvalues in float64 */
+    int32_t mode;             /* TDDFT_MODE_FULL (Eq. operator_RPA); TDDFT_MODE_TDA (B = 0:
+                                 f_p = A p, f_q = A q); TDDFT_MODE_D_ONLY (coupling K = 0) */
+    int32_t precond;          /* TDDFT_PRECOND_ITER: CG solve of Eq. precond; NONE: identity */
+    int32_t precond_maxit;    /* inner CG iterations cap (default 50) */
+    double precond_tol;       /* inner CG relative residual (default 1e-4) */
+    double tol;               /* convergence: max residual (Ha) <= tol and max |d omega| <= tol/10 */
+    int32_t max_iter;         /* outer iteration cap of tddft_solve */
+    int32_t reapply_every;    /* recompute f = f(P) from scratch every this many steps (10) */
+    int32_t restart_every;    /* Polak-Ribiere restart period (10) */
+} tddft_options;
+
+typedef struct tddft_ctx tddft_ctx;
+typedef struct tddft_state tddft_state;
+
+/* Fill *opt with the defaults: FP64, FULL, ITER, 50, 1e-4, tol 1e-6, 500, 10, 10. */
+void tddft_default_options(tddft_options *opt);
+
+/* Build a context on the current CUDA device: copies the system to the device, builds the
+ * grid-tile tables of the functions, f_xc[n0] (Sec. II A, LDA) and the products
+ * M_c = P^c H^chi, M_v = H^phi P^v, R_c = P^c S^chi, R_v = S^phi P^v used by Eqs.
+ * operator_RPA and auxiliary. cuda_stream: a cudaStream_t, or NULL for the default stream.
+ * Errors: INVALID (sizes, grid not 2/3/5-smooth, a box wider than the cell), NOMEM, CUDA. */
+tddft_status tddft_create(const tddft_system *sys, const tddft_options *opt, void *cuda_stream,
+                          tddft_ctx **out);
+void tddft_destroy(tddft_ctx *ctx);
+const char *tddft_last_error(const tddft_ctx *ctx);
+tddft_status tddft_dims(const tddft_ctx *ctx, int32_t *n_chi, int32_t *n_phi, int32_t *n);
+
+/* The operator of Eq. operator_RPA on k state pairs:
+ *   f_p = P^c H^chi P^p - P^p H^phi P^v
+ *   f_q = P^c H^chi P^q - P^q H^phi P^v + 2 P^c V_SCF[P^q] P^v
+ * with V_SCF[P]_ab = <chi_a| v_H[rho] + f_xc rho |phi_b> and rho(r) = sum chi_a P_ab phi_b
+ * (Secs. II A, II C, III A). Pp, Pq: [k][N_chi][N_phi]; fp, fq: same shape, written.
+ * The mode option selects TDA (B = 0) or D_ONLY instead. */
+tddft_status tddft_apply(tddft_ctx *ctx, int32_t k, const double *Pp, const double *Pq,
+                         double *fp, double *fq);
+
+/* Components of V_SCF, for element-by-element checks:
+ *   tddft_response_density: rho_s(r) = sum_ab chi_a(r) P_s,ab phi_b(r); P [k][N_chi][N_phi],
+ *     rho [k][n^3].
+ *   tddft_response_potential: V_s = v_H[rho_s] + f_xc rho_s (periodic, G = 0 dropped);
+ *     rho, V [k][n^3].
+ *   tddft_potential_integrals: out_s,ab = dV sum_r chi_a(r) V_s(r) phi_b(r); V [k][n^3],
+ *     out [k][N_chi][N_phi].
+ *   tddft_fxc: the f_xc[n0] grid [n^3] the context uses. */
+tddft_status tddft_response_density(tddft_ctx *ctx, int32_t k, const double *P, double *rho);
+tddft_status tddft_response_potential(tddft_ctx *ctx, int32_t k, const double *rho, double *V);
+tddft_status tddft_potential_integrals(tddft_ctx *ctx, int32_t k, const double *V, double *out);
+tddft_status tddft_fxc(tddft_ctx *ctx, double *fxc);
+
+/* Solver state for k trial pairs (Sec. III C). Y0 [k][N_chi][N_phi] is the random start X
+ * (Y = 0, so p = q = X); it is masked to the kernel pattern, mapped through Eq. auxiliary,
+ * sign-flipped and Gram-Schmidt orthonormalised in the metric of Eq. ortho, then f is applied.
+ * Errors: INVALID, BREAKDOWN (dependent start vectors), NOMEM, CUDA. */
+tddft_status tddft_state_create(tddft_ctx *ctx, int32_t k, const double *Y0, tddft_state **out);
+void tddft_state_destroy(tddft_state *st);
+
+/* One preconditioned CG iteration (Sec. III C): Q_ij, multi-state gradient, preconditioner
+ * (Eq. precond), Polak-Ribiere conjugation, one line step minimising the sum functional of
+ * Eq. Tsiper_multiple, sign flip + Gram-Schmidt (Eq. ortho). omega [k] (ascending eigenvalues
+ * of Q) and resid [k] (per-pair gradient norms) describe the iterate the step started from.
+ * Either may be NULL. */
+tddft_status tddft_pcg_step(tddft_ctx *ctx, tddft_state *st, double *omega, double *resid);
+
+/* Iterate until max resid <= tol and max |d omega| <= tol/10, or max_iter. omega [k] = final
+ * eigenvalues of Q ascending (Sec. III C subspace diagonalisation), resid [k], iters (may be
+ * NULL). NOT_CONVERGED leaves the last iterate's values in the outputs. Then checks the pairing
+ * of the converged Ritz pairs: each half of the Tsiper numerator must equal omega within
+ * 10 * max(resid) * (1 + |omega|) (PAIRING otherwise). */
+tddft_status tddft_solve(tddft_ctx *ctx, tddft_state *st, double *omega, double *resid,
+                         int32_t *iters);
+
+/* Copy out the current trial pairs and operator images ([k][N_chi][N_phi] each; any may be
+ * NULL) and L (the masked search variables) if Lp/Lq are given. */
+tddft_status tddft_state_get(tddft_ctx *ctx, const tddft_state *st, double *Pp, double *Pq,
+                             double *fp, double *fq, double *Lp, double *Lq);
+
+/* Per Ritz pair of the current subspace: omega [k] ascending and pairing [2k] =
+ * |<p, f_p> - omega|, |<q, f_q> - omega| (an eigenpair has both zero; (-p, q) is then the
+ * -omega partner of Eq. (1)). */
+tddft_status tddft_subspace(tddft_ctx *ctx, tddft_state *st, double *omega, double *pairing);
+
+/* Atom-pair pattern of the response kernels: mask [natoms][natoms], 1 where a chi on atom I and
+ * a phi on atom J are coupled (distance <= kernel_cutoff, or everywhere with no cutoff). */
+tddft_status tddft_pattern(const tddft_ctx *ctx, uint8_t *mask);
+
+/* Per-stage launch timing. tddft_profile(ctx, 1) clears the counters and starts recording a CUDA
+ * event pair on the context's stream around every launch; tddft_profile(ctx, 0) stops. Stages:
+ * gemm, response_density, potential_integrals, fft_poisson_fxc, trace, vector, small_fp64.
+ * tddft_profile_read synchronises and fills up to cap entries (count = entries written). flops
+ * and bytes are algorithmic counts (for response_density and potential_integrals:
+ * 2 * pair_points per state and the nonzero table values plus the grids; for gemm 2MNK). */
+typedef struct {
+    char name[32];
+    int64_t launches;
+    double ms;        /* summed event-to-event time of the stage's launches */
+    double flops;
+    double bytes;
+} tddft_stage_stats;
+
+tddft_status tddft_profile(tddft_ctx *ctx, int32_t enable);
+tddft_status tddft_profile_read(tddft_ctx *ctx, tddft_stage_stats *out, int32_t cap, int32_t *count);
+
+/* Algorithmic work of the grid contractions: pair_points = sum over grid points of
+ * (number of chi nonzero there) * (number of phi nonzero there) = sum over (a, b) of
+ * |supp chi_a  intersect  supp phi_b|; table_values = nonzero tabulated values of both sets. */
+tddft_status tddft_work(const tddft_ctx *ctx, double *pair_points, double *table_values);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TDDFT_H */

@@ -1,0 +1,1038 @@
+// C ABI of libtddft: context construction, the batched full-TDDFT operator (Eq. operator_RPA)
+// and the preconditioned CG eigensolver of Sec. III C, orchestrated on one CUDA stream.
+#include "tddft.h"
+#include "solver_kernels.h"
+#include "tddft_internal.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+namespace tddft {
+
+void check(cudaError_t e, const char *where) {
+    if (e != cudaSuccess) throw CudaError{e, where};
+}
+void check_launch(const char *where) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) throw CudaError{e, where};
+}
+
+namespace {
+
+struct InvalidArg {
+    std::string msg;
+};
+struct Breakdown {
+    std::string msg;
+};
+
+// owning list of device allocations
+struct Mem {
+    std::vector<void *> ptrs;
+    template <typename T>
+    T *alloc(size_t n) {
+        void *p = nullptr;
+        if (n == 0) n = 1;
+        cudaError_t e = cudaMalloc(&p, n * sizeof(T));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            throw std::bad_alloc();
+        }
+        ptrs.push_back(p);
+        return static_cast<T *>(p);
+    }
+    void release() {
+        for (void *p : ptrs) cudaFree(p);
+        ptrs.clear();
+    }
+    ~Mem() { release(); }
+};
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+struct Impl {
+    Mem mem;
+    TileSet<T> chi, phi;
+    T *Sc = nullptr, *Sv = nullptr, *Pc = nullptr, *Pv = nullptr, *Mc = nullptr, *Mv = nullptr;
+    T *Rc = nullptr, *Rv = nullptr, *Ac = nullptr, *Av = nullptr, *mask = nullptr, *fxc = nullptr;
+    double *fxc64 = nullptr;
+    // operator workspace, sized for up to `cap` grid states
+    Mem wmem;
+    int cap = 0;
+    T *rho = nullptr, *V = nullptr, *Vmat = nullptr, *tmp = nullptr, *bufP = nullptr, *bufF = nullptr;
+    void *fft = nullptr;
+    double *stage = nullptr;
+    double *gscratch = nullptr;
+};
+
+}  // namespace
+}  // namespace tddft
+
+using namespace tddft;
+
+struct tddft_ctx {
+    cudaStream_t st = nullptr;
+    tddft_options opt{};
+    int prec = TDDFT_FP64;
+    int n = 0, nt = 0, natoms = 0, nc = 0, nv = 0;
+    double cell = 0.0, dV = 0.0;
+    bool trunc = false;
+    double pair_points = 0.0, table_values = 0.0;
+    Profiler *prof = nullptr;
+    bool prof_on = false;
+    std::vector<uint8_t> amask;
+    std::string err;
+    std::unique_ptr<Impl<double>> d64;
+    std::unique_ptr<Impl<float>> d32;
+    GridShape grid() const { return GridShape{n, nt, cell, dV, pair_points, table_values}; }
+    ~tddft_ctx();
+    long long len() const { return (long long)nc * nv; }
+    long long n3() const { return (long long)n * n * n; }
+};
+
+namespace tddft {
+Profiler *profiler_new();
+void profiler_delete(Profiler *p);
+void profiler_read(Profiler *p, long long *launches, double *ms, double *flops, double *bytes);
+void profiler_reset(Profiler *p);
+}  // namespace tddft
+
+tddft_ctx::~tddft_ctx() {
+    if (prof) profiler_delete(prof);
+}
+
+namespace {
+
+template <typename T> Impl<T> &impl(tddft_ctx *c);
+template <> Impl<double> &impl<double>(tddft_ctx *c) { return *c->d64; }
+template <> Impl<float> &impl<float>(tddft_ctx *c) { return *c->d32; }
+
+struct ProfilerBinding {
+    ProfilerBinding(tddft_ctx *c) { active_profiler() = (c->prof_on ? c->prof : nullptr); }
+    ~ProfilerBinding() { active_profiler() = nullptr; }
+};
+
+template <typename F>
+tddft_status guarded(tddft_ctx *c, F &&f) {
+    try {
+        ProfilerBinding pb(c);
+        return f();
+    } catch (const CudaError &e) {
+        c->err = std::string(e.where) + ": " + cudaGetErrorString(e.code);
+        cudaGetLastError();
+        return e.code == cudaErrorMemoryAllocation ? TDDFT_E_NOMEM : TDDFT_E_CUDA;
+    } catch (const InvalidArg &e) {
+        c->err = e.msg;
+        return TDDFT_E_INVALID;
+    } catch (const Breakdown &e) {
+        c->err = e.msg;
+        return TDDFT_E_BREAKDOWN;
+    } catch (const std::bad_alloc &) {
+        c->err = "out of memory";
+        return TDDFT_E_NOMEM;
+    }
+}
+
+// ---- grid tables -------------------------------------------------------------------------------
+template <typename T>
+void build_tiles(const tddft_funcs &fs, int n, int nt, Mem &mem, TileSet<T> &out,
+                 std::vector<int> &cnt) {
+    const int ntiles = nt * nt * nt;
+    const int nf = fs.nfun;
+    std::vector<std::vector<int>> ftiles(nf);
+#pragma omp parallel
+    {
+        std::vector<int> mark(ntiles, 0);
+        int stamp = 0;
+#pragma omp for schedule(dynamic, 4)
+        for (int f = 0; f < nf; ++f) {
+            ++stamp;
+            const int *b = fs.box + 6 * f;
+            const double *v = fs.val + fs.off[f];
+            for (int i = 0; i < b[3]; ++i) {
+                const int gx = (b[0] + i) % n;
+                for (int j = 0; j < b[4]; ++j) {
+                    const int gy = (b[1] + j) % n;
+                    const double *row = v + ((long long)i * b[4] + j) * b[5];
+                    for (int l = 0; l < b[5]; ++l) {
+                        if (row[l] == 0.0) continue;
+                        const int gz = (b[2] + l) % n;
+                        const int t = ((gx / TILE) * nt + gy / TILE) * nt + gz / TILE;
+                        if (mark[t] != stamp) {
+                            mark[t] = stamp;
+                            ftiles[f].push_back(t);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    std::vector<int> off(ntiles + 1, 0);
+    for (int f = 0; f < nf; ++f)
+        for (int t : ftiles[f]) off[t + 1]++;
+    int maxper = 0;
+    for (int t = 0; t < ntiles; ++t) {
+        maxper = std::max(maxper, off[t + 1]);
+        off[t + 1] += off[t];
+    }
+    const long long slots = off[ntiles];
+    std::vector<int> ids(slots);
+    std::vector<std::vector<int>> fslot(nf);
+    {
+        std::vector<int> pos(off.begin(), off.end() - 1);
+        for (int f = 0; f < nf; ++f) {
+            fslot[f].reserve(ftiles[f].size());
+            for (int t : ftiles[f]) {
+                fslot[f].push_back(pos[t]);
+                ids[pos[t]++] = f;
+            }
+        }
+    }
+    std::vector<T> val((size_t)slots * TILE_PTS, T(0));
+#pragma omp parallel
+    {
+        std::vector<int> slot_of(ntiles, -1);
+#pragma omp for schedule(dynamic, 4)
+        for (int f = 0; f < nf; ++f) {
+            for (size_t a = 0; a < ftiles[f].size(); ++a) slot_of[ftiles[f][a]] = fslot[f][a];
+            const int *b = fs.box + 6 * f;
+            const double *v = fs.val + fs.off[f];
+            for (int i = 0; i < b[3]; ++i) {
+                const int gx = (b[0] + i) % n;
+                for (int j = 0; j < b[4]; ++j) {
+                    const int gy = (b[1] + j) % n;
+                    const double *row = v + ((long long)i * b[4] + j) * b[5];
+                    for (int l = 0; l < b[5]; ++l) {
+                        if (row[l] == 0.0) continue;
+                        const int gz = (b[2] + l) % n;
+                        const int t = ((gx / TILE) * nt + gy / TILE) * nt + gz / TILE;
+                        const int lp = ((gx % TILE) * TILE + gy % TILE) * TILE + gz % TILE;
+                        val[(size_t)slot_of[t] * TILE_PTS + lp] = T(row[l]);
+                    }
+                }
+            }
+            for (int t : ftiles[f]) slot_of[t] = -1;
+        }
+    }
+    // nonzero values per (tile, point), for the algorithmic work counts
+    cnt.assign((size_t)ntiles * TILE_PTS, 0);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int t = 0; t < ntiles; ++t)
+        for (int sl = off[t]; sl < off[t + 1]; ++sl)
+            for (int lp = 0; lp < TILE_PTS; ++lp)
+                if (val[(size_t)sl * TILE_PTS + lp] != T(0)) cnt[(size_t)t * TILE_PTS + lp]++;
+    int *d_off = mem.template alloc<int>(off.size());
+    int *d_ids = mem.template alloc<int>(ids.size());
+    T *d_val = mem.template alloc<T>(val.size());
+    check(cudaMemcpy(d_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice), "upload tile off");
+    check(cudaMemcpy(d_ids, ids.data(), ids.size() * sizeof(int), cudaMemcpyHostToDevice), "upload tile ids");
+    check(cudaMemcpy(d_val, val.data(), val.size() * sizeof(T), cudaMemcpyHostToDevice), "upload tile values");
+    out.ntiles = ntiles;
+    out.max_per_tile = maxper;
+    out.off = d_off;
+    out.ids = d_ids;
+    out.val = d_val;
+}
+
+void validate_funcs(const tddft_funcs &fs, int n, int natoms, const char *name) {
+    if (fs.nfun <= 0 || !fs.atom || !fs.box || !fs.off || !fs.val)
+        throw InvalidArg{std::string(name) + ": empty or null function set"};
+    if (fs.off[0] != 0) throw InvalidArg{std::string(name) + ": off[0] must be 0"};
+    for (int f = 0; f < fs.nfun; ++f) {
+        const int *b = fs.box + 6 * f;
+        for (int a = 0; a < 3; ++a)
+            if (b[a] < 0 || b[a] >= n || b[3 + a] < 1 || b[3 + a] > n)
+                throw InvalidArg{std::string(name) + ": box out of range (origin in [0,n), extent in [1,n])"};
+        if (fs.off[f + 1] - fs.off[f] != (long long)b[3] * b[4] * b[5])
+            throw InvalidArg{std::string(name) + ": off does not match the box extents"};
+        if (fs.atom[f] < 0 || fs.atom[f] >= natoms) throw InvalidArg{std::string(name) + ": atom index out of range"};
+    }
+}
+
+// ---- transfers at the ABI ----------------------------------------------------------------------
+template <typename T>
+void upload(tddft_ctx *c, Impl<T> &I, const double *src, T *dst, long long count) {
+    if (is_device_ptr(src)) {
+        convert<double, T>(c->st, src, dst, count);
+    } else {
+        check(cudaMemcpyAsync(I.stage, src, count * sizeof(double), cudaMemcpyHostToDevice, c->st), "H2D");
+        convert<double, T>(c->st, I.stage, dst, count);
+    }
+}
+
+template <typename T>
+void download(tddft_ctx *c, Impl<T> &I, const T *src, double *dst, long long count) {
+    if (!dst) return;
+    if (is_device_ptr(dst)) {
+        convert<T, double>(c->st, src, dst, count);
+    } else {
+        convert<T, double>(c->st, src, I.stage, count);
+        check(cudaMemcpyAsync(dst, I.stage, count * sizeof(double), cudaMemcpyDeviceToHost, c->st), "D2H");
+        check(cudaStreamSynchronize(c->st), "sync D2H");
+    }
+}
+
+template <> void download<double>(tddft_ctx *c, Impl<double> &I, const double *src, double *dst, long long count) {
+    if (!dst) return;
+    check(cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyDefault, c->st), "copy out");
+    check(cudaStreamSynchronize(c->st), "sync copy out");
+}
+
+// workspace for the operator on up to `states` grid states (2k for a batch of k pairs)
+template <typename T>
+void ensure_workspace(tddft_ctx *c, Impl<T> &I, int states) {
+    if (states <= I.cap) return;
+    check(cudaStreamSynchronize(c->st), "sync before workspace");
+    I.wmem.release();
+    const long long len = c->len(), n3 = c->n3();
+    I.rho = I.wmem.template alloc<T>((size_t)states * n3);
+    I.V = I.wmem.template alloc<T>((size_t)states * n3);
+    I.fft = I.wmem.template alloc<T>((size_t)((states + 1) / 2) * n3 * 2);
+    I.Vmat = I.wmem.template alloc<T>((size_t)states * len);
+    I.tmp = I.wmem.template alloc<T>((size_t)states * len);
+    I.bufP = I.wmem.template alloc<T>((size_t)states * len);
+    I.bufF = I.wmem.template alloc<T>((size_t)states * len);
+    I.stage = I.wmem.template alloc<double>((size_t)std::max<long long>(states * len, states * n3));
+    I.gscratch = I.wmem.template alloc<double>((size_t)gram_scratch_doubles(64, 32));
+    I.cap = states;
+}
+
+// ---- the operator (Eq. operator_RPA) -------------------------------------------------------------
+// P, f: [2][k][N_chi][N_phi] (the k p-matrices, then the k q-matrices)
+template <typename T>
+void apply_impl(tddft_ctx *c, Impl<T> &I, int k, const T *P, T *f) {
+    ensure_workspace(c, I, 2 * k);
+    const int nc = c->nc, nv = c->nv;
+    const long long len = c->len();
+    cudaStream_t st = c->st;
+    // Kohn-Sham difference part: f = (P^c H^chi) P - P (H^phi P^v) on all 2k matrices
+    gemm<T>(st, false, false, nc, nv, nc, T(1), I.Mc, nc, 0, P, nv, len, T(0), f, nv, len, 2 * k);
+    gemm<T>(st, false, false, 2 * k * nc, nv, nv, T(-1), P, nv, 0, I.Mv, nv, 0, T(1), f, nv, 0, 1);
+    if (c->opt.mode == TDDFT_MODE_D_ONLY) return;
+    const bool tda = c->opt.mode == TDDFT_MODE_TDA;
+    const int ns = tda ? 2 * k : k;
+    const T *Ps = tda ? P : P + k * len;
+    T *fs = tda ? f : f + k * len;
+    const T alpha = tda ? T(1) : T(2);
+    const GridShape g = c->grid();
+    response_density<T>(st, g, I.chi, I.phi, nv, Ps, len, ns, I.rho);
+    hartree_fxc<T>(st, g, I.rho, I.fxc, ns, I.V, I.fft);
+    potential_integrals<T>(st, g, I.chi, I.phi, nc, nv, I.V, ns, I.Vmat);
+    // coupling: f_q += 2 P^c V_SCF P^v
+    gemm<T>(st, false, false, nc, nv, nc, T(1), I.Pc, nc, 0, I.Vmat, nv, len, T(0), I.tmp, nv, len, ns);
+    gemm<T>(st, false, false, ns * nc, nv, nv, alpha, I.tmp, nv, 0, I.Pv, nv, 0, T(1), fs, nv, 0, 1);
+}
+
+// ---- context construction ----------------------------------------------------------------------
+template <typename T>
+void build_impl(tddft_ctx *c, const tddft_system *s) {
+    auto I = std::make_unique<Impl<T>>();
+    const int nc = c->nc, nv = c->nv, n = c->n;
+    cudaStream_t st = c->st;
+    std::vector<int> cc_cnt, cv_cnt;
+    build_tiles<T>(s->chi, n, c->nt, I->mem, I->chi, cc_cnt);
+    build_tiles<T>(s->phi, n, c->nt, I->mem, I->phi, cv_cnt);
+    double pp = 0.0, tv = 0.0;
+    for (size_t i = 0; i < cc_cnt.size(); ++i) {
+        pp += (double)cc_cnt[i] * cv_cnt[i];
+        tv += cc_cnt[i] + cv_cnt[i];
+    }
+    c->pair_points = pp;
+    c->table_values = tv;
+    // float64 products on the device, then stored in T
+    Mem tmpm;
+    auto up64 = [&](const double *h, long long cnt) {
+        double *d = tmpm.alloc<double>(cnt);
+        check(cudaMemcpyAsync(d, h, cnt * sizeof(double), cudaMemcpyHostToDevice, st), "upload matrix");
+        return d;
+    };
+    const long long cc = (long long)nc * nc, vv = (long long)nv * nv;
+    double *Sc = up64(s->S_chi, cc), *Sv = up64(s->S_phi, vv), *Hc = up64(s->H_chi, cc);
+    double *Hv = up64(s->H_phi, vv), *Pc = up64(s->P_c, cc), *Pv = up64(s->P_v, vv);
+    double *Mc = tmpm.alloc<double>(cc), *Rc = tmpm.alloc<double>(cc), *Ac = tmpm.alloc<double>(cc);
+    double *Mv = tmpm.alloc<double>(vv), *Rv = tmpm.alloc<double>(vv), *Av = tmpm.alloc<double>(vv);
+    gemm<double>(st, false, false, nc, nc, nc, 1.0, Pc, nc, 0, Hc, nc, 0, 0.0, Mc, nc, 0, 1);   // P^c H^chi
+    gemm<double>(st, false, false, nv, nv, nv, 1.0, Hv, nv, 0, Pv, nv, 0, 0.0, Mv, nv, 0, 1);   // H^phi P^v
+    gemm<double>(st, false, false, nc, nc, nc, 1.0, Pc, nc, 0, Sc, nc, 0, 0.0, Rc, nc, 0, 1);   // P^c S^chi
+    gemm<double>(st, false, false, nv, nv, nv, 1.0, Sv, nv, 0, Pv, nv, 0, 0.0, Rv, nv, 0, 1);   // S^phi P^v
+    gemm<double>(st, false, false, nc, nc, nc, 1.0, Sc, nc, 0, Rc, nc, 0, 0.0, Ac, nc, 0, 1);   // S P^c S
+    gemm<double>(st, false, false, nv, nv, nv, 1.0, Rv, nv, 0, Sv, nv, 0, 0.0, Av, nv, 0, 1);   // S P^v S
+    auto keep = [&](const double *d, long long cnt) {
+        T *o = I->mem.template alloc<T>(cnt);
+        convert<double, T>(st, d, o, cnt);
+        return o;
+    };
+    I->Sc = keep(Sc, cc); I->Sv = keep(Sv, vv); I->Pc = keep(Pc, cc); I->Pv = keep(Pv, vv);
+    I->Mc = keep(Mc, cc); I->Mv = keep(Mv, vv); I->Rc = keep(Rc, cc); I->Rv = keep(Rv, vv);
+    I->Ac = keep(Ac, cc); I->Av = keep(Av, vv);
+    // kernel pattern mask over (chi, phi) function pairs
+    std::vector<double> m((size_t)nc * nv);
+    for (int a = 0; a < nc; ++a)
+        for (int b = 0; b < nv; ++b)
+            m[(size_t)a * nv + b] = c->amask[(size_t)s->chi.atom[a] * c->natoms + s->phi.atom[b]] ? 1.0 : 0.0;
+    double *dm = up64(m.data(), (long long)nc * nv);
+    I->mask = keep(dm, (long long)nc * nv);
+    // f_xc[n0], float64, once per system
+    const long long n3 = c->n3();
+    I->fxc64 = I->mem.template alloc<double>(n3);
+    if (s->fxc_kind == TDDFT_FXC_LDA_PW92) {
+        double *n0 = up64(s->n0, n3);
+        fxc_lda(st, n0, I->fxc64, n3);
+        I->fxc = keep(I->fxc64, n3);
+    } else {
+        check(cudaMemsetAsync(I->fxc64, 0, n3 * sizeof(double), st), "memset fxc");
+        I->fxc = nullptr;
+    }
+    check(cudaStreamSynchronize(st), "build sync");
+    if constexpr (sizeof(T) == 8) c->d64 = std::move(I);
+    else c->d32 = std::move(I);
+}
+
+}  // namespace
+
+// ================================================================================================
+// state of the PCG solver
+
+namespace {
+
+template <typename T>
+struct StateBufs {
+    Mem mem;
+    T *Y, *P, *f, *g, *G1, *h, *z, *Z, *dir, *D, *fD, *covP, *covD;
+    T *pdir, *pD, *pz, *pZ, *tmp;
+    T *cr, *cp, *cLp, *cLpp, *cpv, *cLv;   // inner CG
+    double *A, *BDf, *CDfD, *PP, *PD, *DP, *DD, *Q, *coef, *Cp, *Cq, *lam, *sc, *flip;
+    double *dvec, *dvec2, *dvec3, *evout;
+    double *cg_pLp, *cg_rr, *cg_rrn, *cg_r0, *cg_alpha, *cg_beta, *gscr;
+    int *status, *cg_active, *cg_nactive;
+};
+
+}  // namespace
+
+struct tddft_state {
+    tddft_ctx *ctx = nullptr;
+    int k = 0;
+    int it = 0;
+    bool evaluated = false;
+    bool have_prev_omega = false;
+    std::vector<double> omega, resid, omega_prev;
+    std::unique_ptr<StateBufs<double>> s64;
+    std::unique_ptr<StateBufs<float>> s32;
+    double *host = nullptr;   // pinned: [omega k][resid k][status][n_active][lam]
+    ~tddft_state() {
+        if (host) cudaFreeHost(host);
+    }
+};
+
+namespace {
+
+template <typename T> StateBufs<T> &bufs(tddft_state *s);
+template <> StateBufs<double> &bufs<double>(tddft_state *s) { return *s->s64; }
+template <> StateBufs<float> &bufs<float>(tddft_state *s) { return *s->s32; }
+
+template <typename T>
+void alloc_state(tddft_ctx *c, tddft_state *S) {
+    auto B = std::make_unique<StateBufs<T>>();
+    const size_t n2 = (size_t)2 * S->k * c->len();
+    T **mats[] = {&B->Y, &B->P, &B->f, &B->g, &B->G1, &B->h, &B->z, &B->Z, &B->dir, &B->D,
+                  &B->fD, &B->covP, &B->covD, &B->pdir, &B->pD, &B->pz, &B->pZ, &B->tmp,
+                  &B->cr, &B->cp, &B->cLp, &B->cLpp, &B->cpv, &B->cLv};
+    for (T **m : mats) *m = B->mem.template alloc<T>(n2);
+    const size_t k2 = 2 * S->k, kk4 = k2 * k2, kk = (size_t)S->k * S->k;
+    double **sm[] = {&B->A, &B->BDf, &B->CDfD, &B->PP, &B->PD, &B->DP, &B->DD, &B->coef};
+    for (double **m : sm) *m = B->mem.template alloc<double>(kk4);
+    B->Q = B->mem.template alloc<double>(kk);
+    B->Cp = B->mem.template alloc<double>(kk);
+    B->Cq = B->mem.template alloc<double>(kk);
+    B->lam = B->mem.template alloc<double>(1);
+    B->sc = B->mem.template alloc<double>(4);
+    B->flip = B->mem.template alloc<double>(1);
+    double **vv[] = {&B->dvec, &B->dvec2, &B->dvec3, &B->evout, &B->cg_pLp, &B->cg_rr, &B->cg_rrn,
+                     &B->cg_r0, &B->cg_alpha, &B->cg_beta};
+    for (double **m : vv) *m = B->mem.template alloc<double>(k2);
+    B->gscr = B->mem.template alloc<double>((size_t)gram_scratch_doubles(64, 32));
+    B->status = B->mem.template alloc<int>(1);
+    B->cg_active = B->mem.template alloc<int>(k2);
+    B->cg_nactive = B->mem.template alloc<int>(1);
+    check(cudaMemsetAsync(B->sc, 0, 4 * sizeof(double), c->st), "memset sc");
+    check(cudaMemsetAsync(B->flip, 0, sizeof(double), c->st), "memset flip");
+    check(cudaMemsetAsync(B->status, 0, sizeof(int), c->st), "memset status");
+    check(cudaMemsetAsync(B->pdir, 0, n2 * sizeof(T), c->st), "memset pdir");
+    check(cudaMemsetAsync(B->pD, 0, n2 * sizeof(T), c->st), "memset pD");
+    check(cudaMemsetAsync(B->pz, 0, n2 * sizeof(T), c->st), "memset pz");
+    check(cudaMemsetAsync(B->pZ, 0, n2 * sizeof(T), c->st), "memset pZ");
+    if constexpr (sizeof(T) == 8) S->s64 = std::move(B);
+    else S->s32 = std::move(B);
+}
+
+// cov(X) = S^chi X S^phi for 2k matrices
+template <typename T>
+void covariant(tddft_ctx *c, Impl<T> &I, int nb, const T *X, T *out, T *tmp) {
+    const int nc = c->nc, nv = c->nv;
+    const long long len = c->len();
+    gemm<T>(c->st, false, false, nc, nv, nc, T(1), I.Sc, nc, 0, X, nv, len, T(0), tmp, nv, len, nb);
+    gemm<T>(c->st, false, false, nb * nc, nv, nv, T(1), tmp, nv, 0, I.Sv, nv, 0, T(0), out, nv, 0, 1);
+}
+
+// out = L X R (left nc x nc, right nv x nv) for nb matrices
+template <typename T>
+void sandwich(tddft_ctx *c, int nb, const T *Lm, const T *X, const T *Rm, T *out, T *tmp) {
+    const int nc = c->nc, nv = c->nv;
+    const long long len = c->len();
+    gemm<T>(c->st, false, false, nc, nv, nc, T(1), Lm, nc, 0, X, nv, len, T(0), tmp, nv, len, nb);
+    gemm<T>(c->st, false, false, nb * nc, nv, nv, T(1), tmp, nv, 0, Rm, nv, 0, T(0), out, nv, 0, 1);
+}
+
+void sync_status(tddft_ctx *c, tddft_state *S, const int *dstatus) {
+    check(cudaMemcpyAsync(reinterpret_cast<int *>(S->host + 2 * S->k), dstatus, sizeof(int),
+                          cudaMemcpyDeviceToHost, c->st),
+          "D2H status");
+    check(cudaStreamSynchronize(c->st), "sync status");
+    const int stv = *reinterpret_cast<int *>(S->host + 2 * S->k);
+    if (stv == DEV_BREAKDOWN) throw Breakdown{"non-positive norm in Gram-Schmidt (dependent trial pairs)"};
+    if (stv == DEV_NAN) throw Breakdown{"NaN or Inf in the trial pairs"};
+}
+
+// recombine Y, P, f with the Gram-Schmidt coefficients (sign flips folded into Cq)
+template <typename T>
+void recombine(tddft_ctx *c, StateBufs<T> &B, int k) {
+    const long long len = c->len();
+    T *arrs[] = {B.Y, B.P, B.f};
+    for (T *X : arrs) {
+        check(cudaMemcpyAsync(B.tmp, X, 2 * k * len * sizeof(T), cudaMemcpyDeviceToDevice, c->st), "copy recombine");
+        combine<T>(c->st, B.Cp, k, k, k, B.tmp, len, X, len, len, false);
+        combine<T>(c->st, B.Cq, k, k, k, B.tmp + k * len, len, X + k * len, len, len, false);
+    }
+}
+
+template <typename T>
+void state_init(tddft_ctx *c, tddft_state *S, const double *Y0) {
+    Impl<T> &I = impl<T>(c);
+    StateBufs<T> &B = bufs<T>(S);
+    const int k = S->k;
+    const long long len = c->len();
+    ensure_workspace(c, I, 2 * k);
+    // Y = mask * Y0 for both p and q (X random, Y = 0 => p = q)
+    upload<T>(c, I, Y0, B.Y, k * len);
+    if (c->trunc) mask_mul<T>(c->st, B.Y, I.mask, len, k);
+    check(cudaMemcpyAsync(B.Y + k * len, B.Y, k * len * sizeof(T), cudaMemcpyDeviceToDevice, c->st), "copy Y");
+    // P = P^c S^chi L S^phi P^v (Eq. auxiliary)
+    sandwich<T>(c, 2 * k, I.Rc, B.Y, I.Rv, B.P, B.tmp);
+    covariant<T>(c, I, 2 * k, B.P, B.covP, B.tmp);
+    gram<T>(c->st, B.covP, len, 2 * k, B.P, len, 2 * k, len, B.PP, B.gscr);
+    init_gs(c->st, k, B.PP, B.Cp, B.Cq, B.status);
+    sync_status(c, S, B.status);
+    check(cudaMemsetAsync(B.f, 0, 2 * k * len * sizeof(T), c->st), "memset f");
+    recombine<T>(c, B, k);
+    apply_impl<T>(c, I, k, B.P, B.f);
+    check(cudaStreamSynchronize(c->st), "sync init");
+}
+
+// Q, omega, gradient and residuals of the current iterate
+template <typename T>
+void evaluate(tddft_ctx *c, tddft_state *S) {
+    Impl<T> &I = impl<T>(c);
+    StateBufs<T> &B = bufs<T>(S);
+    const int k = S->k;
+    const long long len = c->len();
+    cudaStream_t st = c->st;
+    covariant<T>(c, I, 2 * k, B.P, B.covP, B.tmp);
+    gram<T>(st, B.covP, len, 2 * k, B.f, len, 2 * k, len, B.A, B.gscr);   // A[x][y] = <P_x, f_y>
+    make_q(st, k, B.A, B.Q, B.coef);
+    // g = f - swap(P) Q^T
+    check(cudaMemcpyAsync(B.g, B.f, 2 * k * len * sizeof(T), cudaMemcpyDeviceToDevice, st), "copy g");
+    combine<T>(st, B.coef, 2 * k, 2 * k, 2 * k, B.P, len, B.g, len, len, true);
+    if (c->trunc) {
+        // G_L = mask * (S P^c S) g (S P^v S); residual = Frobenius norm
+        sandwich<T>(c, 2 * k, I.Ac, B.g, I.Av, B.G1, B.tmp);
+        mask_mul<T>(st, B.G1, I.mask, len, 2 * k);
+        dots<T>(st, B.G1, len, B.G1, len, 2 * k, len, B.dvec, B.gscr);
+    } else {
+        covariant<T>(c, I, 2 * k, B.g, B.G1, B.tmp);   // cov(g)
+        dots<T>(st, B.g, len, B.G1, len, 2 * k, len, B.dvec, B.gscr);
+    }
+    eval_finish(st, k, B.Q, B.dvec, B.evout, B.status);
+    check(cudaMemcpyAsync(S->host, B.evout, 2 * k * sizeof(double), cudaMemcpyDeviceToHost, st), "D2H eval");
+    sync_status(c, S, B.status);
+    S->omega.assign(S->host, S->host + k);
+    S->resid.assign(S->host + k, S->host + 2 * k);
+    S->evaluated = true;
+}
+
+// z = Pinv(h): CG on P^c H^chi G - G H^phi P^v = h (Eq. precond) in the trace metric, for the 2k
+// systems at once. Systems stop individually (relative residual precond_tol, non-positive
+// curvature); the loop ends when none is active or after precond_maxit iterations.
+template <typename T>
+void precondition(tddft_ctx *c, tddft_state *S, const T *h, T *z) {
+    Impl<T> &I = impl<T>(c);
+    StateBufs<T> &B = bufs<T>(S);
+    const int k2 = 2 * S->k, nc = c->nc, nv = c->nv;
+    const long long len = c->len(), tot = k2 * len;
+    cudaStream_t st = c->st;
+    if (c->opt.precond == TDDFT_PRECOND_NONE) {
+        check(cudaMemcpyAsync(z, h, tot * sizeof(T), cudaMemcpyDeviceToDevice, st), "copy z");
+        return;
+    }
+    T *r = B.cLpp, *cr = B.cr, *p = B.cp, *cp = B.cpv, *Lp = B.cLp, *cLp = B.cLv;
+    check(cudaMemsetAsync(z, 0, tot * sizeof(T), st), "memset z");
+    check(cudaMemcpyAsync(r, h, tot * sizeof(T), cudaMemcpyDeviceToDevice, st), "copy r");
+    covariant<T>(c, I, k2, r, cr, B.tmp);
+    check(cudaMemcpyAsync(p, r, tot * sizeof(T), cudaMemcpyDeviceToDevice, st), "copy p");
+    check(cudaMemcpyAsync(cp, cr, tot * sizeof(T), cudaMemcpyDeviceToDevice, st), "copy cp");
+    dots<T>(st, r, len, cr, len, k2, len, B.dvec2, B.gscr);
+    cg_init(st, k2, c->opt.precond_tol, B.dvec2, B.cg_rr, B.cg_r0, B.cg_active, B.cg_nactive);
+    int *hn = reinterpret_cast<int *>(S->host + 2 * S->k) + 1;
+    for (int it = 0; it < c->opt.precond_maxit; ++it) {
+        check(cudaMemcpyAsync(hn, B.cg_nactive, sizeof(int), cudaMemcpyDeviceToHost, st), "D2H n_active");
+        check(cudaStreamSynchronize(st), "sync cg");
+        if (*hn == 0) break;
+        gemm<T>(st, false, false, nc, nv, nc, T(1), I.Mc, nc, 0, p, nv, len, T(0), Lp, nv, len, k2);
+        gemm<T>(st, false, false, k2 * nc, nv, nv, T(-1), p, nv, 0, I.Mv, nv, 0, T(1), Lp, nv, 0, 1);
+        covariant<T>(c, I, k2, Lp, cLp, B.tmp);
+        dots<T>(st, cp, len, Lp, len, k2, len, B.cg_pLp, B.gscr);
+        cg_scalars(st, k2, 0, c->opt.precond_tol, B.cg_pLp, B.cg_rrn, B.cg_rr, B.cg_r0, B.cg_alpha,
+                   B.cg_beta, B.cg_active, B.cg_nactive);
+        axpy_dev<T>(st, B.cg_alpha, 1, 1.0, z, p, len, k2);
+        axpy_dev<T>(st, B.cg_alpha, 1, -1.0, r, Lp, len, k2);
+        axpy_dev<T>(st, B.cg_alpha, 1, -1.0, cr, cLp, len, k2);
+        dots<T>(st, r, len, cr, len, k2, len, B.cg_rrn, B.gscr);
+        cg_scalars(st, k2, 1, c->opt.precond_tol, B.cg_pLp, B.cg_rrn, B.cg_rr, B.cg_r0, B.cg_alpha,
+                   B.cg_beta, B.cg_active, B.cg_nactive);
+        cg_dir<T>(st, p, r, B.cg_beta, len, k2);
+        cg_dir<T>(st, cp, cr, B.cg_beta, len, k2);
+    }
+}
+
+// one PCG update from an evaluated iterate (Sec. III C)
+template <typename T>
+void update(tddft_ctx *c, tddft_state *S) {
+    Impl<T> &I = impl<T>(c);
+    StateBufs<T> &B = bufs<T>(S);
+    const int k = S->k, k2 = 2 * k;
+    const long long len = c->len(), tot = k2 * len;
+    cudaStream_t st = c->st;
+    // preconditioned gradient in the search variables
+    const T *h = B.g;
+    if (c->trunc) {
+        sandwich<T>(c, k2, I.Pc, B.G1, I.Pv, B.h, B.tmp);   // P^c G_L P^v
+        h = B.h;
+    }
+    precondition<T>(c, S, h, B.z);
+    if (c->trunc) mask_mul<T>(st, B.z, I.mask, len, k2);
+    sandwich<T>(c, k2, I.Rc, B.z, I.Rv, B.Z, B.tmp);         // Z = P^c S z S P^v (Eq. auxiliary)
+    // Polak-Ribiere over the set
+    if (c->trunc) {
+        dots<T>(st, B.G1, len, B.z, len, k2, len, B.dvec, B.gscr);
+        dots<T>(st, B.G1, len, B.pz, len, k2, len, B.dvec2, B.gscr);
+        dots<T>(st, B.G1, len, B.pdir, len, k2, len, B.dvec3, B.gscr);
+    } else {
+        dots<T>(st, B.G1, len, B.Z, len, k2, len, B.dvec, B.gscr);
+        dots<T>(st, B.G1, len, B.pZ, len, k2, len, B.dvec2, B.gscr);
+        dots<T>(st, B.G1, len, B.pD, len, k2, len, B.dvec3, B.gscr);
+    }
+    const int restart = (S->it == 0 || S->it % std::max(1, c->opt.restart_every) == 0) ? 1 : 0;
+    conj_coeff(st, k2, B.dvec, B.dvec2, B.dvec3, restart, B.flip, B.sc);
+    direction<T>(st, B.dir, B.z, B.pdir, B.sc + 2, tot);
+    direction<T>(st, B.D, B.Z, B.pD, B.sc + 2, tot);
+    // one operator application on the directions
+    apply_impl<T>(c, I, k, B.D, B.fD);
+    covariant<T>(c, I, k2, B.D, B.covD, B.tmp);
+    gram<T>(st, B.covD, len, k2, B.f, len, k2, len, B.BDf, B.gscr);
+    gram<T>(st, B.covD, len, k2, B.fD, len, k2, len, B.CDfD, B.gscr);
+    gram<T>(st, B.covP, len, k2, B.P, len, k2, len, B.PP, B.gscr);
+    gram<T>(st, B.covP, len, k2, B.D, len, k2, len, B.PD, B.gscr);
+    gram<T>(st, B.covD, len, k2, B.P, len, k2, len, B.DP, B.gscr);
+    gram<T>(st, B.covD, len, k2, B.D, len, k2, len, B.DD, B.gscr);
+    line_gs(st, k, B.A, B.BDf, B.CDfD, B.PP, B.PD, B.DP, B.DD, B.Q, B.lam, B.Cp, B.Cq, B.flip,
+            B.status);
+    axpy_dev<T>(st, B.lam, 0, 1.0, B.Y, B.dir, tot, 1);
+    axpy_dev<T>(st, B.lam, 0, 1.0, B.P, B.D, tot, 1);
+    axpy_dev<T>(st, B.lam, 0, 1.0, B.f, B.fD, tot, 1);
+    recombine<T>(c, B, k);
+    check(cudaMemcpyAsync(S->host + 2 * k + 1, B.lam, sizeof(double), cudaMemcpyDeviceToHost, st), "D2H lam");
+    sync_status(c, S, B.status);
+    S->it += 1;
+    if (c->opt.reapply_every > 0 && S->it % c->opt.reapply_every == 0) apply_impl<T>(c, I, k, B.P, B.f);
+    std::swap(B.pdir, B.dir);
+    std::swap(B.pD, B.D);
+    std::swap(B.pz, B.z);
+    std::swap(B.pZ, B.Z);
+    S->omega_prev = S->omega;
+    S->have_prev_omega = true;
+    S->evaluated = false;
+}
+
+template <typename T>
+bool converged(tddft_ctx *c, tddft_state *S) {
+    if (!S->have_prev_omega) return false;
+    double rmax = 0.0, dmax = 0.0;
+    for (int i = 0; i < S->k; ++i) {
+        rmax = std::max(rmax, S->resid[i]);
+        dmax = std::max(dmax, std::fabs(S->omega[i] - S->omega_prev[i]));
+    }
+    return rmax <= c->opt.tol && dmax <= 0.1 * c->opt.tol;
+}
+
+template <typename T>
+void subspace_pairs(tddft_ctx *c, tddft_state *S, double *omega, double *pairing) {
+    StateBufs<T> &B = bufs<T>(S);
+    const int k = S->k;
+    if (!S->evaluated) evaluate<T>(c, S);
+    subspace(c->st, k, B.A, B.evout, B.dvec3);
+    check(cudaMemcpyAsync(S->host, B.evout, k * sizeof(double), cudaMemcpyDeviceToHost, c->st), "D2H omega");
+    check(cudaMemcpyAsync(S->host + k, B.dvec3, 2 * k * sizeof(double), cudaMemcpyDeviceToHost, c->st), "D2H pairing");
+    check(cudaStreamSynchronize(c->st), "sync subspace");
+    if (omega) std::memcpy(omega, S->host, k * sizeof(double));
+    if (pairing) std::memcpy(pairing, S->host + k, 2 * k * sizeof(double));
+}
+
+template <typename T>
+tddft_status solve_impl(tddft_ctx *c, tddft_state *S, double *omega, double *resid, int32_t *iters) {
+    bool conv = false;
+    for (int it = 0; it < c->opt.max_iter; ++it) {
+        evaluate<T>(c, S);
+        if (converged<T>(c, S)) {
+            conv = true;
+            break;
+        }
+        update<T>(c, S);
+    }
+    if (!conv) {
+        evaluate<T>(c, S);
+        conv = converged<T>(c, S);
+    }
+    if (omega) std::memcpy(omega, S->omega.data(), S->k * sizeof(double));
+    if (resid) std::memcpy(resid, S->resid.data(), S->k * sizeof(double));
+    if (iters) *iters = S->it;
+    if (!conv) {
+        c->err = "not converged within max_iter";
+        return TDDFT_E_NOT_CONVERGED;
+    }
+    if (!c->trunc) {
+        std::vector<double> om(S->k), pr(2 * S->k);
+        subspace_pairs<T>(c, S, om.data(), pr.data());
+        double rmax = 0.0, omax = 0.0, pmax = 0.0;
+        for (int i = 0; i < S->k; ++i) {
+            rmax = std::max(rmax, S->resid[i]);
+            omax = std::max(omax, std::fabs(om[i]));
+        }
+        for (double v : pr) pmax = std::max(pmax, v);
+        if (pmax > 10.0 * rmax * (1.0 + omax) + 1e-10) {
+            c->err = "converged pairs fail the +-omega pairing check";
+            return TDDFT_E_PAIRING;
+        }
+    }
+    return TDDFT_OK;
+}
+
+}  // namespace
+
+// ================================================================================================
+// ABI
+
+#define DISPATCH(ctx, EXPR)                                   \
+    ((ctx)->prec == TDDFT_FP64 ? ([&]() { using T = double; return EXPR; })() \
+                               : ([&]() { using T = float; return EXPR; })())
+
+extern "C" {
+
+void tddft_default_options(tddft_options *o) {
+    if (!o) return;
+    o->precision = TDDFT_FP64;
+    o->mode = TDDFT_MODE_FULL;
+    o->precond = TDDFT_PRECOND_ITER;
+    o->precond_maxit = 50;
+    o->precond_tol = 1e-4;
+    o->tol = 1e-6;
+    o->max_iter = 500;
+    o->reapply_every = 10;
+    o->restart_every = 10;
+}
+
+tddft_status tddft_create(const tddft_system *s, const tddft_options *opt, void *stream,
+                          tddft_ctx **out) {
+    if (!out) return TDDFT_E_INVALID;
+    *out = nullptr;
+    auto c = std::make_unique<tddft_ctx>();
+    if (opt) c->opt = *opt;
+    else tddft_default_options(&c->opt);
+    c->st = static_cast<cudaStream_t>(stream);
+    c->prec = c->opt.precision;
+    tddft_status rc = guarded(c.get(), [&]() -> tddft_status {
+        if (!s) throw InvalidArg{"null system"};
+        if (c->prec != TDDFT_FP64 && c->prec != TDDFT_MIXED) throw InvalidArg{"unknown precision"};
+        if (c->opt.mode < 0 || c->opt.mode > 2) throw InvalidArg{"unknown mode"};
+        if (!(s->cell > 0.0)) throw InvalidArg{"cell must be positive"};
+        if (!fft_size_ok(s->n)) throw InvalidArg{"grid size must be 2^a 3^b 5^c with 8 <= n <= 256"};
+        if (s->natoms <= 0 || !s->pos) throw InvalidArg{"no atoms"};
+        if (!s->S_chi || !s->S_phi || !s->H_chi || !s->H_phi || !s->P_v || !s->P_c) throw InvalidArg{"null matrix"};
+        if (s->fxc_kind == TDDFT_FXC_LDA_PW92 && !s->n0) throw InvalidArg{"LDA kernel needs n0"};
+        validate_funcs(s->phi, s->n, s->natoms, "phi");
+        validate_funcs(s->chi, s->n, s->natoms, "chi");
+        c->n = s->n;
+        c->nt = (s->n + TILE - 1) / TILE;
+        c->natoms = s->natoms;
+        c->nc = s->chi.nfun;
+        c->nv = s->phi.nfun;
+        c->cell = s->cell;
+        const double h = s->cell / s->n;
+        c->dV = h * h * h;
+        c->trunc = s->kernel_cutoff > 0.0;
+        c->amask.assign((size_t)s->natoms * s->natoms, 1);
+        if (c->trunc) {
+            for (int a = 0; a < s->natoms; ++a)
+                for (int b = 0; b < s->natoms; ++b) {
+                    double d2 = 0.0;
+                    for (int x = 0; x < 3; ++x) {
+                        double d = s->pos[3 * a + x] - s->pos[3 * b + x];
+                        d -= s->cell * std::nearbyint(d / s->cell);
+                        d2 += d * d;
+                    }
+                    c->amask[(size_t)a * s->natoms + b] = std::sqrt(d2) <= s->kernel_cutoff ? 1 : 0;
+                }
+        }
+        if (c->prec == TDDFT_FP64) build_impl<double>(c.get(), s);
+        else build_impl<float>(c.get(), s);
+        return TDDFT_OK;
+    });
+    if (rc != TDDFT_OK) {
+        static thread_local std::string last;
+        last = c->err;
+        std::fprintf(stderr, "tddft_create: %s\n", last.c_str());
+        return rc;
+    }
+    *out = c.release();
+    return TDDFT_OK;
+}
+
+void tddft_destroy(tddft_ctx *c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->st);
+    delete c;
+}
+
+const char *tddft_last_error(const tddft_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+tddft_status tddft_dims(const tddft_ctx *c, int32_t *nc, int32_t *nv, int32_t *n) {
+    if (!c) return TDDFT_E_INVALID;
+    if (nc) *nc = c->nc;
+    if (nv) *nv = c->nv;
+    if (n) *n = c->n;
+    return TDDFT_OK;
+}
+
+tddft_status tddft_apply(tddft_ctx *c, int32_t k, const double *Pp, const double *Pq, double *fp,
+                         double *fq) {
+    if (!c) return TDDFT_E_INVALID;
+    return guarded(c, [&]() -> tddft_status {
+        if (k <= 0 || !Pp || !Pq || !fp || !fq) throw InvalidArg{"tddft_apply: bad arguments"};
+        const long long kl = (long long)k * c->len();
+        return DISPATCH(c, ([&]() {
+            Impl<T> &I = impl<T>(c);
+            ensure_workspace(c, I, 2 * k);
+            upload<T>(c, I, Pp, I.bufP, kl);
+            upload<T>(c, I, Pq, I.bufP + kl, kl);
+            apply_impl<T>(c, I, k, I.bufP, I.bufF);
+            download<T>(c, I, I.bufF, fp, kl);
+            download<T>(c, I, I.bufF + kl, fq, kl);
+            check(cudaStreamSynchronize(c->st), "sync apply");
+            return TDDFT_OK;
+        })());
+    });
+}
+
+tddft_status tddft_response_density(tddft_ctx *c, int32_t k, const double *P, double *rho) {
+    if (!c) return TDDFT_E_INVALID;
+    return guarded(c, [&]() -> tddft_status {
+        if (k <= 0 || !P || !rho) throw InvalidArg{"tddft_response_density: bad arguments"};
+        return DISPATCH(c, ([&]() {
+            Impl<T> &I = impl<T>(c);
+            ensure_workspace(c, I, k);
+            upload<T>(c, I, P, I.bufP, (long long)k * c->len());
+            response_density<T>(c->st, c->grid(), I.chi, I.phi, c->nv, I.bufP, c->len(), k, I.rho);
+            download<T>(c, I, I.rho, rho, (long long)k * c->n3());
+            check(cudaStreamSynchronize(c->st), "sync density");
+            return TDDFT_OK;
+        })());
+    });
+}
+
+tddft_status tddft_response_potential(tddft_ctx *c, int32_t k, const double *rho, double *V) {
+    if (!c) return TDDFT_E_INVALID;
+    return guarded(c, [&]() -> tddft_status {
+        if (k <= 0 || !rho || !V) throw InvalidArg{"tddft_response_potential: bad arguments"};
+        return DISPATCH(c, ([&]() {
+            Impl<T> &I = impl<T>(c);
+            ensure_workspace(c, I, k);
+            upload<T>(c, I, rho, I.rho, (long long)k * c->n3());
+            hartree_fxc<T>(c->st, c->grid(), I.rho, I.fxc, k, I.V, I.fft);
+            download<T>(c, I, I.V, V, (long long)k * c->n3());
+            check(cudaStreamSynchronize(c->st), "sync potential");
+            return TDDFT_OK;
+        })());
+    });
+}
+
+tddft_status tddft_potential_integrals(tddft_ctx *c, int32_t k, const double *V, double *out) {
+    if (!c) return TDDFT_E_INVALID;
+    return guarded(c, [&]() -> tddft_status {
+        if (k <= 0 || !V || !out) throw InvalidArg{"tddft_potential_integrals: bad arguments"};
+        return DISPATCH(c, ([&]() {
+            Impl<T> &I = impl<T>(c);
+            ensure_workspace(c, I, k);
+            upload<T>(c, I, V, I.V, (long long)k * c->n3());
+            potential_integrals<T>(c->st, c->grid(), I.chi, I.phi, c->nc, c->nv, I.V, k, I.Vmat);
+            download<T>(c, I, I.Vmat, out, (long long)k * c->len());
+            check(cudaStreamSynchronize(c->st), "sync integrals");
+            return TDDFT_OK;
+        })());
+    });
+}
+
+tddft_status tddft_fxc(tddft_ctx *c, double *fxc) {
+    if (!c || !fxc) return TDDFT_E_INVALID;
+    return guarded(c, [&]() -> tddft_status {
+        const double *src = c->prec == TDDFT_FP64 ? c->d64->fxc64 : c->d32->fxc64;
+        check(cudaMemcpyAsync(fxc, src, c->n3() * sizeof(double), cudaMemcpyDefault, c->st), "copy fxc");
+        check(cudaStreamSynchronize(c->st), "sync fxc");
+        return TDDFT_OK;
+    });
+}
+
+tddft_status tddft_state_create(tddft_ctx *c, int32_t k, const double *Y0, tddft_state **out) {
+    if (!c || !out) return TDDFT_E_INVALID;
+    *out = nullptr;
+    auto S = std::make_unique<tddft_state>();
+    tddft_status rc = guarded(c, [&]() -> tddft_status {
+        if (k <= 0 || k > KMAX || !Y0) throw InvalidArg{"tddft_state_create: need 1 <= k <= 16 and Y0"};
+        S->ctx = c;
+        S->k = k;
+        check(cudaMallocHost(reinterpret_cast<void **>(&S->host), (2 * k + 8) * sizeof(double)), "cudaMallocHost");
+        return DISPATCH(c, ([&]() {
+            alloc_state<T>(c, S.get());
+            state_init<T>(c, S.get(), Y0);
+            return TDDFT_OK;
+        })());
+    });
+    if (rc == TDDFT_OK) *out = S.release();
+    return rc;
+}
+
+void tddft_state_destroy(tddft_state *s) {
+    if (!s) return;
+    if (s->ctx) cudaStreamSynchronize(s->ctx->st);
+    delete s;
+}
+
+tddft_status tddft_pcg_step(tddft_ctx *c, tddft_state *S, double *omega, double *resid) {
+    if (!c || !S || S->ctx != c) return TDDFT_E_INVALID;
+    return guarded(c, [&]() -> tddft_status {
+        return DISPATCH(c, ([&]() {
+            if (!S->evaluated) evaluate<T>(c, S);
+            if (omega) std::memcpy(omega, S->omega.data(), S->k * sizeof(double));
+            if (resid) std::memcpy(resid, S->resid.data(), S->k * sizeof(double));
+            update<T>(c, S);
+            return TDDFT_OK;
+        })());
+    });
+}
+
+tddft_status tddft_solve(tddft_ctx *c, tddft_state *S, double *omega, double *resid, int32_t *iters) {
+    if (!c || !S || S->ctx != c) return TDDFT_E_INVALID;
+    return guarded(c, [&]() -> tddft_status {
+        return DISPATCH(c, (solve_impl<T>(c, S, omega, resid, iters)));
+    });
+}
+
+tddft_status tddft_state_get(tddft_ctx *c, const tddft_state *S, double *Pp, double *Pq, double *fp,
+                             double *fq, double *Lp, double *Lq) {
+    if (!c || !S || S->ctx != c) return TDDFT_E_INVALID;
+    return guarded(c, [&]() -> tddft_status {
+        return DISPATCH(c, ([&]() {
+            Impl<T> &I = impl<T>(c);
+            StateBufs<T> &B = bufs<T>(const_cast<tddft_state *>(S));
+            const long long kl = (long long)S->k * c->len();
+            ensure_workspace(c, I, 2 * S->k);
+            download<T>(c, I, B.P, Pp, kl);
+            download<T>(c, I, B.P + kl, Pq, kl);
+            download<T>(c, I, B.f, fp, kl);
+            download<T>(c, I, B.f + kl, fq, kl);
+            download<T>(c, I, B.Y, Lp, kl);
+            download<T>(c, I, B.Y + kl, Lq, kl);
+            check(cudaStreamSynchronize(c->st), "sync state_get");
+            return TDDFT_OK;
+        })());
+    });
+}
+
+tddft_status tddft_subspace(tddft_ctx *c, tddft_state *S, double *omega, double *pairing) {
+    if (!c || !S || S->ctx != c) return TDDFT_E_INVALID;
+    return guarded(c, [&]() -> tddft_status {
+        return DISPATCH(c, ([&]() {
+            subspace_pairs<T>(c, S, omega, pairing);
+            return TDDFT_OK;
+        })());
+    });
+}
+
+tddft_status tddft_profile(tddft_ctx *c, int32_t enable) {
+    if (!c) return TDDFT_E_INVALID;
+    return guarded(c, [&]() -> tddft_status {
+        check(cudaStreamSynchronize(c->st), "sync profile");
+        if (!c->prof) c->prof = profiler_new();
+        profiler_reset(c->prof);
+        c->prof_on = enable != 0;
+        return TDDFT_OK;
+    });
+}
+
+tddft_status tddft_profile_read(tddft_ctx *c, tddft_stage_stats *out, int32_t cap, int32_t *count) {
+    if (!c || !out || cap < 0) return TDDFT_E_INVALID;
+    return guarded(c, [&]() -> tddft_status {
+        long long l[ST_COUNT] = {};
+        double ms[ST_COUNT] = {}, fl[ST_COUNT] = {}, by[ST_COUNT] = {};
+        if (c->prof) profiler_read(c->prof, l, ms, fl, by);
+        const int nst = std::min<int>(cap, ST_COUNT);
+        for (int i = 0; i < nst; ++i) {
+            std::memset(&out[i], 0, sizeof(out[i]));
+            std::strncpy(out[i].name, stage_name(i), sizeof(out[i].name) - 1);
+            out[i].launches = l[i];
+            out[i].ms = ms[i];
+            out[i].flops = fl[i];
+            out[i].bytes = by[i];
+        }
+        if (count) *count = nst;
+        return TDDFT_OK;
+    });
+}
+
+tddft_status tddft_work(const tddft_ctx *c, double *pair_points, double *table_values) {
+    if (!c) return TDDFT_E_INVALID;
+    if (pair_points) *pair_points = c->pair_points;
+    if (table_values) *table_values = c->table_values;
+    return TDDFT_OK;
+}
+
+tddft_status tddft_pattern(const tddft_ctx *c, uint8_t *mask) {
+    if (!c || !mask) return TDDFT_E_INVALID;
+    std::memcpy(mask, c->amask.data(), c->amask.size());
+    return TDDFT_OK;
+}
+
+}  // extern "C"

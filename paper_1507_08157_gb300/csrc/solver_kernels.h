@@ -1,0 +1,36 @@
+// Declarations of the solver primitives defined in solver_kernels.cu.
+#pragma once
+
+#include "tddft_internal.h"
+
+namespace tddft {
+
+// d_i = sum_e X_i[e] Y_i[e] for i < n (float64, fixed order); scratch as for gram
+template <typename T>
+void dots(cudaStream_t st, const T *X, long long sx, const T *Y, long long sy, int n, long long len,
+          double *d, double *scratch);
+
+// out = -z + beta * prev, beta a device scalar
+template <typename T>
+void direction(cudaStream_t st, T *out, const T *z, const T *prev, const double *beta, long long n);
+
+// p_b <- r_b + beta[b] p_b
+template <typename T>
+void cg_dir(cudaStream_t st, T *p, const T *r, const double *beta, long long len, int nb);
+
+void make_q(cudaStream_t st, int k, const double *A, double *Q, double *coef);
+void eval_finish(cudaStream_t st, int k, const double *Q, const double *d, double *out, int *status);
+void conj_coeff(cudaStream_t st, int k2, const double *gz, const double *gzp, const double *gd,
+                int restart, const double *flip, double *sc);
+void line_gs(cudaStream_t st, int k, const double *A, const double *BDf, const double *CDfD,
+             const double *PP, const double *PD, const double *DP, const double *DD, const double *Q,
+             double *lam, double *Cp, double *Cq, double *flip, int *status);
+void init_gs(cudaStream_t st, int k, const double *PP, double *Cp, double *Cq, int *status);
+void cg_init(cudaStream_t st, int n, double tol, const double *rr0, double *rr, double *r0,
+             int *active, int *n_active);
+void cg_scalars(cudaStream_t st, int n, int phase, double tol, const double *pLp,
+                const double *rr_new, double *rr, const double *r0, double *alpha, double *beta,
+                int *active, int *n_active);
+void subspace(cudaStream_t st, int k, const double *A, double *omega, double *pairing);
+
+}  // namespace tddft

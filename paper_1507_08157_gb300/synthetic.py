@@ -24,9 +24,11 @@ points ((ox+i) mod n, (oy+j) mod n, (oz+l) mod n).
 """
 from __future__ import annotations
 
+import concurrent.futures
 import dataclasses
 import hashlib
 import math
+import os
 
 import numpy as np
 import scipy.linalg
@@ -117,6 +119,10 @@ class System:
 # ----------------------------------------------------------------------------------------------
 # geometry and tables
 
+def _workers():
+    return max(1, min(32, os.cpu_count() or 1))
+
+
 def _rsa_positions(rng, natoms, cell, min_sep):
     pos = np.zeros((natoms, 3))
     placed = 0
@@ -177,9 +183,11 @@ def _tabulate(rng_w, pos, nper, cell, n, radius, width):
     box = np.zeros((nfun, 6), dtype=np.int32)
     off = np.arange(nfun + 1, dtype=np.int64) * (e ** 3)
     val = np.empty(int(off[-1]), dtype=np.float64)
+    widths = rng_w.uniform(width[0], width[1], size=nfun)   # one draw per function, in order
     dV = h ** 3
     t = np.arange(-m, m + 1, dtype=np.float64)
-    for ia in range(natoms):
+
+    def one_atom(ia):
         c = np.rint(pos[ia] / h).astype(np.int64)
         d = [(c[a] + t) * h - pos[ia, a] for a in range(3)]
         dx, dy, dz = np.meshgrid(d[0], d[1], d[2], indexing="ij")
@@ -187,13 +195,16 @@ def _tabulate(rng_w, pos, nper, cell, n, radius, width):
         inside = r2 <= radius * radius
         for kf in range(nper):
             f = ia * nper + kf
-            w = rng_w.uniform(width[0], width[1])
+            w = widths[f]
             g = np.exp(-r2 / (w * w)) * _angular(kf, dx, dy, dz, w)
             g[~inside] = 0.0
             g /= math.sqrt(dV * np.sum(g * g))
             val[off[f]:off[f + 1]] = g.ravel()
             box[f, :3] = np.mod(c - m, n)
             box[f, 3:] = e
+
+    with concurrent.futures.ThreadPoolExecutor(_workers()) as ex:
+        list(ex.map(one_atom, range(natoms)))
     return FunctionSet(atom=atom, box=box, off=off, val=val)
 
 
@@ -251,8 +262,10 @@ def _overlap_matrix(fs, nper, pos, cell, n, dV, rmax):
     natoms = pos.shape[0]
     N = natoms * nper
     S = np.zeros((N, N))
-    for (i, j, _) in _atom_pairs_within(pos, cell, rmax):
-        blk = dV * _pair_overlap(fs, fs, nper, nper, i, j, n)
+    pairs = _atom_pairs_within(pos, cell, rmax)
+    with concurrent.futures.ThreadPoolExecutor(_workers()) as ex:
+        blocks = list(ex.map(lambda p: dV * _pair_overlap(fs, fs, nper, nper, p[0], p[1], n), pairs))
+    for (i, j, _), blk in zip(pairs, blocks):
         S[i * nper:(i + 1) * nper, j * nper:(j + 1) * nper] = blk
         if i != j:
             S[j * nper:(j + 1) * nper, i * nper:(i + 1) * nper] = blk.T
@@ -273,27 +286,49 @@ def _random_hamiltonian(rng, pos, cell, nper, rmax, sigma, decay):
     return H
 
 
+def _density_contrib(fs, nper, K, n, ia, ib):
+    """(index arrays, values) of sum_ab f_a K_ab f_b over the common points of atoms ia, ib."""
+    A, oa, e = _atom_block(fs, ia, nper)
+    B, ob, _ = _atom_block(fs, ib, nper)
+    Kab = K[ia * nper:(ia + 1) * nper, ib * nper:(ib + 1) * nper]
+    out = []
+    rx = _axis_overlaps(int(oa[0]), int(ob[0]), e, n)
+    ry = _axis_overlaps(int(oa[1]), int(ob[1]), e, n)
+    rz = _axis_overlaps(int(oa[2]), int(ob[2]), e, n)
+    for (ax, bx, lx) in rx:
+        for (ay, by, ly) in ry:
+            for (az, bz, lz) in rz:
+                a = A[:, ax:ax + lx, ay:ay + ly, az:az + lz].reshape(nper, -1)
+                b = B[:, bx:bx + lx, by:by + ly, bz:bz + lz].reshape(nper, -1)
+                contrib = np.einsum("ar,ar->r", Kab @ b, a).reshape(lx, ly, lz)
+                out.append(((int(oa[0]) + ax) % n, (int(oa[1]) + ay) % n, (int(oa[2]) + az) % n,
+                            contrib))
+    return out
+
+
+def _split(start, length, n):
+    """Split the wrapped range [start, start+length) (mod n) into (dst, src, len) slices."""
+    if start + length <= n:
+        return [(start, 0, length)]
+    first = n - start
+    return [(start, 0, first), (0, first, length - first)]
+
+
 def _density_on_grid(fs, nper, K, pos, cell, n, rmax):
     """sum_ab f_a(r) K_ab f_b(r) on the full grid, over atom pairs within rmax."""
     out = np.zeros((n, n, n))
+    jobs = []
     for (i, j, _) in _atom_pairs_within(pos, cell, rmax):
-        for (ia, ib) in ((i, j), (j, i)) if i != j else ((i, i),):
-            A, oa, e = _atom_block(fs, ia, nper)
-            B, ob, _ = _atom_block(fs, ib, nper)
-            Kab = K[ia * nper:(ia + 1) * nper, ib * nper:(ib + 1) * nper]
-            rx = _axis_overlaps(int(oa[0]), int(ob[0]), e, n)
-            ry = _axis_overlaps(int(oa[1]), int(ob[1]), e, n)
-            rz = _axis_overlaps(int(oa[2]), int(ob[2]), e, n)
-            for (ax, bx, lx) in rx:
-                for (ay, by, ly) in ry:
-                    for (az, bz, lz) in rz:
-                        a = A[:, ax:ax + lx, ay:ay + ly, az:az + lz].reshape(nper, -1)
-                        b = B[:, bx:bx + lx, by:by + ly, bz:bz + lz].reshape(nper, -1)
-                        contrib = np.einsum("ar,ar->r", Kab @ b, a).reshape(lx, ly, lz)
-                        gx = (int(oa[0]) + ax + np.arange(lx)) % n
-                        gy = (int(oa[1]) + ay + np.arange(ly)) % n
-                        gz = (int(oa[2]) + az + np.arange(lz)) % n
-                        out[np.ix_(gx, gy, gz)] += contrib
+        jobs += [(i, j), (j, i)] if i != j else [(i, i)]
+    with concurrent.futures.ThreadPoolExecutor(_workers()) as ex:
+        for parts in ex.map(lambda p: _density_contrib(fs, nper, K, n, p[0], p[1]), jobs):
+            for x0, y0, z0, contrib in parts:
+                lx, ly, lz = contrib.shape
+                for (dx, sx, nx) in _split(x0, lx, n):
+                    for (dy, sy, ny) in _split(y0, ly, n):
+                        for (dz, sz, nz) in _split(z0, lz, n):
+                            out[dx:dx + nx, dy:dy + ny, dz:dz + nz] += \
+                                contrib[sx:sx + nx, sy:sy + ny, sz:sz + nz]
     return out
 
 

@@ -1,0 +1,317 @@
+"""ctypes binding of libtddft (include/tddft.h): argument marshalling only.
+
+Every computation runs in the CUDA library. Arrays may be numpy (host) or torch CUDA float64
+tensors (device); the library tells them apart. If the library has not been built this module
+raises at load time: there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .synthetic import System
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libtddft.so")
+
+OK, E_INVALID, E_NOMEM, E_CUDA, E_NOT_CONVERGED, E_BREAKDOWN, E_TIMEOUT, E_PAIRING = range(8)
+FP64, MIXED = 0, 1
+MODE = {"full": 0, "tda": 1, "d_only": 2}
+PRECOND = {"none": 0, "iter": 1}
+FXC = {"none": 0, "lda": 1}
+
+c_double_p = ctypes.POINTER(ctypes.c_double)
+c_int32_p = ctypes.POINTER(ctypes.c_int32)
+c_int64_p = ctypes.POINTER(ctypes.c_int64)
+
+
+class _Funcs(ctypes.Structure):
+    _fields_ = [("nfun", ctypes.c_int32), ("atom", c_int32_p), ("box", c_int32_p),
+                ("off", c_int64_p), ("val", c_double_p)]
+
+
+class _System(ctypes.Structure):
+    _fields_ = [("cell", ctypes.c_double), ("n", ctypes.c_int32), ("natoms", ctypes.c_int32),
+                ("pos", c_double_p), ("phi", _Funcs), ("chi", _Funcs),
+                ("S_chi", c_double_p), ("S_phi", c_double_p), ("H_chi", c_double_p),
+                ("H_phi", c_double_p), ("P_v", c_double_p), ("P_c", c_double_p),
+                ("n0", c_double_p), ("fxc_kind", ctypes.c_int32),
+                ("kernel_cutoff", ctypes.c_double)]
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("mode", ctypes.c_int32),
+                ("precond", ctypes.c_int32), ("precond_maxit", ctypes.c_int32),
+                ("precond_tol", ctypes.c_double), ("tol", ctypes.c_double),
+                ("max_iter", ctypes.c_int32), ("reapply_every", ctypes.c_int32),
+                ("restart_every", ctypes.c_int32)]
+
+
+class StageStats(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("ms", ctypes.c_double),
+                ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
+SYMBOLS = sorted(["tddft_default_options", "tddft_create", "tddft_destroy", "tddft_last_error",
+                  "tddft_dims", "tddft_apply", "tddft_response_density", "tddft_response_potential",
+                  "tddft_potential_integrals", "tddft_fxc", "tddft_state_create",
+                  "tddft_state_destroy", "tddft_pcg_step", "tddft_solve", "tddft_state_get",
+                  "tddft_subspace", "tddft_pattern", "tddft_profile", "tddft_profile_read",
+                  "tddft_work"])
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libtddft.so and declare its signatures (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with `python -m paper_1507_08157_gb300.build`")
+    lib = ctypes.CDLL(path)
+    vp = ctypes.c_void_p
+    lib.tddft_default_options.argtypes = [ctypes.POINTER(_Options)]
+    lib.tddft_default_options.restype = None
+    lib.tddft_create.argtypes = [ctypes.POINTER(_System), ctypes.POINTER(_Options), vp, ctypes.POINTER(vp)]
+    lib.tddft_destroy.argtypes = [vp]
+    lib.tddft_destroy.restype = None
+    lib.tddft_last_error.argtypes = [vp]
+    lib.tddft_last_error.restype = ctypes.c_char_p
+    lib.tddft_dims.argtypes = [vp, c_int32_p, c_int32_p, c_int32_p]
+    lib.tddft_apply.argtypes = [vp, ctypes.c_int32, vp, vp, vp, vp]
+    for name in ("tddft_response_density", "tddft_response_potential", "tddft_potential_integrals"):
+        getattr(lib, name).argtypes = [vp, ctypes.c_int32, vp, vp]
+    lib.tddft_fxc.argtypes = [vp, vp]
+    lib.tddft_state_create.argtypes = [vp, ctypes.c_int32, vp, ctypes.POINTER(vp)]
+    lib.tddft_state_destroy.argtypes = [vp]
+    lib.tddft_state_destroy.restype = None
+    lib.tddft_pcg_step.argtypes = [vp, vp, vp, vp]
+    lib.tddft_solve.argtypes = [vp, vp, vp, vp, c_int32_p]
+    lib.tddft_state_get.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.tddft_subspace.argtypes = [vp, vp, vp, vp]
+    lib.tddft_pattern.argtypes = [vp, ctypes.POINTER(ctypes.c_uint8)]
+    lib.tddft_profile.argtypes = [vp, ctypes.c_int32]
+    lib.tddft_profile_read.argtypes = [vp, ctypes.POINTER(StageStats), ctypes.c_int32, c_int32_p]
+    lib.tddft_work.argtypes = [vp, c_double_p, c_double_p]
+    for name in ("tddft_create", "tddft_dims", "tddft_apply", "tddft_response_density",
+                 "tddft_response_potential", "tddft_potential_integrals", "tddft_fxc",
+                 "tddft_state_create", "tddft_pcg_step", "tddft_solve", "tddft_state_get",
+                 "tddft_subspace", "tddft_pattern", "tddft_profile", "tddft_profile_read",
+                 "tddft_work"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+class TddftError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"tddft status {status}: {msg}")
+        self.status = status
+
+
+def _ptr(a):
+    """Address of a numpy array or a torch tensor (must be float64 and contiguous)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous float64")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        import torch
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise ValueError("tensors must be contiguous float64")
+        return a.data_ptr()
+    raise TypeError(type(a))
+
+
+def _options(precision="fp64", mode="full", precond="iter", precond_tol=1e-4, precond_maxit=50,
+             tol=1e-6, max_iter=500, reapply_every=10, restart_every=10):
+    o = _Options()
+    load().tddft_default_options(ctypes.byref(o))
+    o.precision = FP64 if precision == "fp64" else MIXED
+    o.mode = MODE[mode]
+    o.precond = PRECOND[precond]
+    o.precond_tol = precond_tol
+    o.precond_maxit = precond_maxit
+    o.tol = tol
+    o.max_iter = max_iter
+    o.reapply_every = reapply_every
+    o.restart_every = restart_every
+    return o
+
+
+class Context:
+    """One system on the GPU (tddft_create). Keyword options follow tddft_options."""
+
+    def __init__(self, sys: System, fxc="lda", stream=None, **opts):
+        lib = load()
+        self._lib = lib
+        self.sys = sys
+        keep = []
+
+        def arr(a, dt):
+            a = np.ascontiguousarray(a, dtype=dt)
+            keep.append(a)
+            return a.ctypes.data_as(ctypes.POINTER(np.ctypeslib.as_ctypes_type(dt)))
+
+        def funcs(fs):
+            f = _Funcs()
+            f.nfun = fs.nfun
+            f.atom = arr(fs.atom, np.int32)
+            f.box = arr(fs.box, np.int32)
+            f.off = arr(fs.off, np.int64)
+            f.val = arr(fs.val, np.float64)
+            return f
+
+        s = _System()
+        s.cell = sys.cell
+        s.n = sys.n
+        s.natoms = sys.natoms
+        s.pos = arr(sys.pos, np.float64)
+        s.phi = funcs(sys.phi)
+        s.chi = funcs(sys.chi)
+        s.S_chi = arr(sys.S_chi, np.float64)
+        s.S_phi = arr(sys.S_phi, np.float64)
+        s.H_chi = arr(sys.H_chi, np.float64)
+        s.H_phi = arr(sys.H_phi, np.float64)
+        s.P_v = arr(sys.P_v, np.float64)
+        s.P_c = arr(sys.P_c, np.float64)
+        s.n0 = arr(sys.n0, np.float64)
+        s.fxc_kind = FXC[fxc]
+        s.kernel_cutoff = sys.kernel_cutoff
+        self.options = _options(**opts)
+        ctx = ctypes.c_void_p()
+        st = ctypes.c_void_p(stream) if stream is not None else None
+        rc = lib.tddft_create(ctypes.byref(s), ctypes.byref(self.options), st, ctypes.byref(ctx))
+        if rc != OK:
+            raise TddftError(rc, "tddft_create failed (see stderr)")
+        self._ctx = ctx
+        self.nc, self.nv, self.n = sys.chi.nfun, sys.phi.nfun, sys.n
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self._lib.tddft_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != OK:
+            raise TddftError(rc, self._lib.tddft_last_error(self._ctx).decode())
+
+    def _out(self, like, shape):
+        if like is not None and hasattr(like, "data_ptr"):
+            import torch
+            return torch.empty(shape, dtype=torch.float64, device=like.device)
+        return np.empty(shape)
+
+    # -- Eq. operator_RPA --------------------------------------------------------------------------
+    def apply(self, Pp, Pq, fp=None, fq=None):
+        k = Pp.shape[0]
+        shape = (k, self.nc, self.nv)
+        fp = self._out(Pp, shape) if fp is None else fp
+        fq = self._out(Pp, shape) if fq is None else fq
+        self._check(self._lib.tddft_apply(self._ctx, k, _ptr(Pp), _ptr(Pq), _ptr(fp), _ptr(fq)))
+        return fp, fq
+
+    def response_density(self, P):
+        out = self._out(P, (P.shape[0], self.n, self.n, self.n))
+        self._check(self._lib.tddft_response_density(self._ctx, P.shape[0], _ptr(P), _ptr(out)))
+        return out
+
+    def response_potential(self, rho):
+        out = self._out(rho, rho.shape)
+        self._check(self._lib.tddft_response_potential(self._ctx, rho.shape[0], _ptr(rho), _ptr(out)))
+        return out
+
+    def potential_integrals(self, V):
+        out = self._out(V, (V.shape[0], self.nc, self.nv))
+        self._check(self._lib.tddft_potential_integrals(self._ctx, V.shape[0], _ptr(V), _ptr(out)))
+        return out
+
+    def fxc(self):
+        out = np.empty((self.n, self.n, self.n))
+        self._check(self._lib.tddft_fxc(self._ctx, _ptr(out)))
+        return out
+
+    def pattern(self):
+        m = np.empty((self.sys.natoms, self.sys.natoms), dtype=np.uint8)
+        self._check(self._lib.tddft_pattern(self._ctx, m.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))))
+        return m
+
+    def state(self, Y0):
+        return State(self, Y0)
+
+    def profile(self, enable=True):
+        self._check(self._lib.tddft_profile(self._ctx, 1 if enable else 0))
+
+    def profile_read(self):
+        """Per-stage {name: (launches, ms, flops, bytes)} since profiling was enabled."""
+        buf = (StageStats * 16)()
+        n = ctypes.c_int32(0)
+        self._check(self._lib.tddft_profile_read(self._ctx, buf, 16, ctypes.byref(n)))
+        return {buf[i].name.decode(): (int(buf[i].launches), buf[i].ms, buf[i].flops, buf[i].bytes)
+                for i in range(n.value)}
+
+    def work(self):
+        """(pair_points, table_values): algorithmic work of the grid contractions."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        self._check(self._lib.tddft_work(self._ctx, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+
+class State:
+    """Trial pairs of the PCG solver (tddft_state_create)."""
+
+    def __init__(self, ctx: Context, Y0):
+        self.ctx = ctx
+        self.k = Y0.shape[0]
+        Y0 = np.ascontiguousarray(Y0, dtype=np.float64) if isinstance(Y0, np.ndarray) else Y0
+        st = ctypes.c_void_p()
+        ctx._check(ctx._lib.tddft_state_create(ctx._ctx, self.k, _ptr(Y0), ctypes.byref(st)))
+        self._st = st
+
+    def close(self):
+        if getattr(self, "_st", None):
+            self.ctx._lib.tddft_state_destroy(self._st)
+            self._st = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self):
+        om, res = np.empty(self.k), np.empty(self.k)
+        self.ctx._check(self.ctx._lib.tddft_pcg_step(self.ctx._ctx, self._st, _ptr(om), _ptr(res)))
+        return om, res
+
+    def solve(self):
+        """Returns (omega, resid, iters, status); status is OK, NOT_CONVERGED or PAIRING."""
+        om, res = np.empty(self.k), np.empty(self.k)
+        it = ctypes.c_int32(0)
+        rc = self.ctx._lib.tddft_solve(self.ctx._ctx, self._st, _ptr(om), _ptr(res), ctypes.byref(it))
+        if rc not in (OK, E_NOT_CONVERGED, E_PAIRING):
+            self.ctx._check(rc)
+        return om, res, int(it.value), rc
+
+    def get(self):
+        shape = (self.k, self.ctx.nc, self.ctx.nv)
+        out = {name: np.empty(shape) for name in ("Pp", "Pq", "fp", "fq", "Lp", "Lq")}
+        self.ctx._check(self.ctx._lib.tddft_state_get(
+            self.ctx._ctx, self._st, *(_ptr(out[n]) for n in ("Pp", "Pq", "fp", "fq", "Lp", "Lq"))))
+        return out
+
+    def subspace(self):
+        om, pr = np.empty(self.k), np.empty(2 * self.k)
+        self.ctx._check(self.ctx._lib.tddft_subspace(self.ctx._ctx, self._st, _ptr(om), _ptr(pr)))
+        return om, pr.reshape(self.k, 2)

@@ -1,0 +1,115 @@
+"""Parity of the CUDA PCG solver with the FP64 oracle and the dense reference, through the C ABI.
+
+* step parity: from the same random start, the GPU state after creation and after each PCG step
+  equals the oracle's (FP64: trial pairs to 1e-8 of their scale, omega to 1e-10 Ha);
+* converged energies: |omega_GPU - omega_dense| <= 1e-6 Ha in FP64 mode and <= 1e-5 Ha in mixed
+  mode (the target accuracies of the method), checked on the 3-atom system and the 8-atom / 48^3
+  workload, plus the TDA and D-only fixed points;
+* truncated kernels (Eq. auxiliary): step parity with the oracle.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from oracle import casida, operator as oop, solver as osolver
+from paper_1507_08157_gb300 import synthetic as sy
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tddft():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1507_08157_gb300 import build, tddft as td
+    build.build()
+    td.load()
+    return td
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    return sy.generate(sy.Recipe(natoms=3, cell_ang=10.0, ngrid=30, radius_ang=4.0, seed=11))
+
+
+@pytest.fixture(scope="module")
+def tiny_dense(tiny):
+    return casida.Casida(tiny)
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+@pytest.mark.parametrize("trunc", [False, True])
+def test_step_parity_fp64(tddft, tiny, trunc):
+    s = dataclasses.replace(tiny, kernel_cutoff=3.0 / 0.529177210903) if trunc else tiny
+    k = 2
+    Y0 = sy.initial_guess(s, k, 3)
+    ref = osolver.PCG(oop.Operator(s), Y0)
+    ctx = tddft.Context(s, precision="fp64")
+    st = ctx.state(Y0)
+    got = st.get()
+    assert _rel(got["Pp"], ref.Pp) < 1e-9 and _rel(got["Pq"], ref.Pq) < 1e-9
+    assert _rel(got["fq"], ref.fq) < 1e-9
+    for _ in range(4):
+        om_r, res_r = ref.step()
+        om_g, res_g = st.step()
+        assert np.max(np.abs(om_g - om_r)) < 1e-10
+        assert np.max(np.abs(res_g - res_r) / res_r) < 1e-6
+        got = st.get()
+        assert _rel(got["Pp"], ref.Pp) < 1e-7 and _rel(got["Pq"], ref.Pq) < 1e-7
+        assert _rel(got["Lq"], ref.Yq) < 1e-7
+
+
+@pytest.mark.parametrize("prec,tol,acc", [("fp64", 1e-8, 1e-6), ("mixed", 1e-6, 1e-5)])
+def test_converged_energies_match_dense(tddft, tiny, tiny_dense, prec, tol, acc):
+    k = 3
+    ctx = tddft.Context(tiny, precision=prec, tol=tol, max_iter=400)
+    st = ctx.state(sy.initial_guess(tiny, k, 1))
+    om, res, it, rc = st.solve()
+    assert rc == tddft.OK, (rc, it, res)
+    ref = tiny_dense.omega_symmetric()[:k]
+    assert np.max(np.abs(om - ref)) <= acc
+    om2, pairing = st.subspace()
+    assert np.max(pairing) < 1e-4
+
+
+@pytest.mark.parametrize("mode", ["tda", "d_only"])
+def test_fixed_points(tddft, tiny, tiny_dense, mode):
+    k = 2
+    ctx = tddft.Context(tiny, precision="fp64", mode=mode, tol=1e-8, max_iter=400)
+    st = ctx.state(sy.initial_guess(tiny, k, 2))
+    om, res, it, rc = st.solve()
+    assert rc == tddft.OK
+    ref = tiny_dense.omega_tda()[:k] if mode == "tda" else np.sort(tiny_dense.ks_differences())[:k]
+    assert np.max(np.abs(om - ref)) <= 1e-9
+
+
+def test_small_workload_lowest_state(tddft):
+    s = sy.generate(sy.CONFIG_SMALL)
+    ref = casida.Casida(s).omega_symmetric()[0]
+    for prec, acc in (("fp64", 1e-6), ("mixed", 1e-5)):
+        ctx = tddft.Context(s, precision=prec, tol=1e-6, max_iter=400)
+        st = ctx.state(sy.initial_guess(s, 1, 0))
+        om, res, it, rc = st.solve()
+        assert rc == tddft.OK, (prec, rc, it, res)
+        assert abs(om[0] - ref) <= acc, (prec, om[0], ref)
+
+
+def test_breakdown_on_nan_start(tddft, tiny):
+    ctx = tddft.Context(tiny, precision="fp64")
+    Y0 = sy.initial_guess(tiny, 2, 4)
+    Y0[1, 0, 0] = np.nan
+    with pytest.raises(tddft.TddftError) as e:
+        ctx.state(Y0)
+    assert e.value.status == tddft.E_BREAKDOWN
+
+
+def test_not_converged_reports_last_iterate(tddft, tiny):
+    ctx = tddft.Context(tiny, precision="fp64", tol=1e-12, max_iter=3)
+    st = ctx.state(sy.initial_guess(tiny, 1, 5))
+    om, res, it, rc = st.solve()
+    assert rc == tddft.E_NOT_CONVERGED and it == 3 and np.all(np.isfinite(om))
