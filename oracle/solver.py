@@ -22,8 +22,9 @@ Readings where the paper is silent (Algorithms 1 and 2 of its supplement are not
   * line step: along x_i(lambda) = x_i + lambda Delta_i the sum of the Tsiper energies of the
     re-orthonormalised set is Omega(lambda) = Tr[M(lambda)^-1 N(lambda)] / 2 with the k x k
     matrices N_ij = <x_i, f(x_j)>_E and M_ij = (<p_i,q_j> + <p_j,q_i>)/2, each quadratic in
-    lambda. Its first minimum on the descent side is found exactly: bracket by doubling, then 100
-    bisections on the sign of dOmega/dlambda (a non-positive-definite M counts as past the minimum);
+    lambda. A minimum on the descent side is found to machine precision: a sign change of
+    dOmega/dlambda is bracketed by doubling a Newton estimate (a non-positive-definite M counts as
+    past the minimum), then located by Illinois regula falsi;
   * conjugation: Polak-Ribiere on the whole set, beta = max(0, sum_i <g_i, z_i - z_prev,i> /
     sum_i <g_prev,i, z_prev,i>), z the projected preconditioned gradient; reset every 10
     iterations, after a sign flip, and whenever the conjugate direction is not a descent direction;
@@ -75,26 +76,51 @@ def sum_functional(lam, N0, N1, N2, M0, M1, M2):
 
 
 def line_step(N0, N1, N2, M0, M1, M2):
-    """First minimiser lambda > 0 of the sum functional along the line (0 if not a descent line)."""
+    """A minimiser lambda > 0 of the sum functional along the line (0 if not a descent line):
+    bracket a sign change of dOmega/dlambda from below by doubling a Newton estimate, then
+    Illinois regula falsi inside the bracket to machine precision."""
     _, d0 = sum_functional(0.0, N0, N1, N2, M0, M1, M2)
     if not np.isfinite(d0) or d0 >= 0.0:
         return 0.0
     # Newton estimate of the step from the model with M0 = I
     h0 = np.trace(2.0 * N2 - 2.0 * M1 @ N1 + 2.0 * M1 @ M1 @ N0 - 2.0 * M2 @ N0) * 0.5
     hi = -d0 / h0 if h0 > 0.0 and np.isfinite(h0) else 1.0
-    lo = 0.0
+    lo, dlo, d = 0.0, d0, d0
     for _ in range(60):
         _, d = sum_functional(hi, N0, N1, N2, M0, M1, M2)
         if d >= 0.0:
             break
-        lo, hi = hi, 2.0 * hi
-    for _ in range(100):
+        lo, dlo, hi = hi, d, 2.0 * hi
+    dhi = d
+    for _ in range(200):          # past the positive-definite region: bisect to a finite end
+        if np.isfinite(dhi):
+            break
         mid = 0.5 * (lo + hi)
         _, d = sum_functional(mid, N0, N1, N2, M0, M1, M2)
         if d < 0.0:
-            lo = mid
+            lo, dlo = mid, d
         else:
-            hi = mid
+            hi, dhi = mid, d
+    side = 0
+    for _ in range(100):
+        if not hi - lo > 4e-16 * hi:
+            break
+        x = hi - dhi * (hi - lo) / (dhi - dlo) if (np.isfinite(dhi) and dhi != dlo) else 0.5 * (lo + hi)
+        if not lo < x < hi:
+            x = 0.5 * (lo + hi)
+        _, d = sum_functional(x, N0, N1, N2, M0, M1, M2)
+        if d == 0.0:
+            return x
+        if d < 0.0:
+            lo, dlo = x, d
+            if side == -1:
+                dhi *= 0.5
+            side = -1
+        else:
+            hi, dhi = x, d
+            if side == 1:
+                dlo *= 0.5
+            side = 1
     return 0.5 * (lo + hi)
 
 

@@ -252,18 +252,43 @@ __device__ double line_step(int k, const LineBlocks &lb, Scratch &s) {
         h0 += 0.5 * t;
     }
     double hi = (h0 > 0.0 && isfinite(h0)) ? -d0 / h0 : 1.0;
-    double lo = 0.0, f, d;
-    for (int it = 0; it < 60; ++it) {
+    double lo = 0.0, dlo = d0, dhi = 0.0, f, d;
+    // bracket: dOmega < 0 at lo, >= 0 (or M not positive definite) at hi
+    int it = 0;
+    for (; it < 60; ++it) {
         if (!sum_functional(k, lb, hi, &f, &d, s)) d = INFINITY;
         if (d >= 0.0) break;
         lo = hi;
+        dlo = d;
         hi = 2.0 * hi;
     }
-    for (int it = 0; it < 100; ++it) {
+    dhi = d;
+    // past the positive-definite region: bisect until dOmega is finite at hi
+    for (int b = 0; b < 200 && !isfinite(dhi); ++b) {
         const double mid = 0.5 * (lo + hi);
         if (!sum_functional(k, lb, mid, &f, &d, s)) d = INFINITY;
-        if (d < 0.0) lo = mid;
-        else hi = mid;
+        if (d < 0.0) { lo = mid; dlo = d; }
+        else { hi = mid; dhi = d; }
+    }
+    // Illinois regula falsi on dOmega(lambda) inside [lo, hi], to machine precision
+    int side = 0;
+    for (int r = 0; r < 100; ++r) {
+        if (!(hi - lo > 4e-16 * hi)) break;
+        double x = (isfinite(dhi) && dhi != dlo) ? hi - dhi * (hi - lo) / (dhi - dlo) : 0.5 * (lo + hi);
+        if (!(x > lo && x < hi)) x = 0.5 * (lo + hi);
+        if (!sum_functional(k, lb, x, &f, &d, s)) d = INFINITY;
+        if (d == 0.0) return x;
+        if (d < 0.0) {
+            lo = x;
+            dlo = d;
+            if (side == -1) dhi *= 0.5;
+            side = -1;
+        } else {
+            hi = x;
+            dhi = d;
+            if (side == +1) dlo *= 0.5;
+            side = +1;
+        }
     }
     return 0.5 * (lo + hi);
 }
