@@ -6,7 +6,23 @@
 // broadcasts (A) or conflict-free (B) and the C stores are coalesced along tx.
 #include "tddft_internal.h"
 
+#include <cstdlib>
+
 namespace tddft {
+
+void tc_gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, float alpha, const float *A, int lda,
+             long long sA, const float *B, int ldb, long long sB, float beta, float *C, int ldc, long long sC,
+             int batch, bool split);
+bool tc_gemm_available();
+
+bool tc_enabled() {
+    static int on = -1;
+    if (on < 0) {
+        const char *e = std::getenv("TDDFT_NO_TC");
+        on = (e && e[0] == '1') ? 0 : (tc_gemm_available() ? 1 : 0);
+    }
+    return on == 1;
+}
 
 namespace {
 
@@ -104,6 +120,13 @@ void gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, T alpha, const
     const double bytes = sizeof(T) * ((double)M * K * (sA ? batch : 1) + (double)K * N * (sB ? batch : 1) +
                                       (double)M * N * batch * (beta == T(0) ? 1 : 2));
     ProfScope ps(st, ST_GEMM, 2.0 * M * N * K * batch, bytes);
+    // float32 products of useful size go to the tensor cores (three-term TF32 split: float32
+    // accuracy); float64 and tiny products stay on the CUDA cores
+    if (sizeof(T) == 4 && tc_enabled() && (double)M * N * K * batch >= 2.0e6) {
+        tc_gemm(st, ta, tb, M, N, K, (float)alpha, (const float *)A, lda, sA, (const float *)B, ldb, sB,
+                (float)beta, (float *)C, ldc, sC, batch, true);
+        return;
+    }
     if (!ta && !tb) launch<T, false, false>(st, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch);
     else if (!ta && tb) launch<T, false, true>(st, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch);
     else if (ta && !tb) launch<T, true, false>(st, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch);

@@ -1,0 +1,450 @@
+// Tensor-core GEMM for sm_103a: tcgen05.mma (kind::tf32) with TMA-staged operands and a TMEM
+// accumulator, float32 in and out, float32 accuracy by the three-term TF32 split.
+//
+//   C[b] = alpha * A[b] * B[b]^T + beta * C[b]      A: M x K, B: N x K, both K contiguous.
+//
+// The split: x = x_hi + x_lo with x_hi = x rounded to tf32 (cvt.rna.tf32.f32, low 13 mantissa
+// bits zero) and x_lo = x - x_hi (exact in float32, |x_lo| <= 2^-11 |x|). Then
+// x*y ~= x_hi y_hi + x_hi y_lo + x_lo y_hi; the dropped x_lo y_lo term and the tf32 reading of the
+// lo parts leave a relative error of about 2^-21 per product (plain TF32: 2^-11).
+//
+// Block: 192 threads. Warps 0-3 read the accumulator out of TMEM (warp w owns lanes 32w..32w+31,
+// i.e. tile rows) and write C; warp 4 lane 0 issues the TMA loads; warp 5 allocates TMEM and its
+// lane 0 issues the MMAs. 128 x 128 output tile, K in slices of 32 floats (one 128-byte swizzle
+// row), 4-stage mbarrier pipeline. Every wait is bounded: on expiry the block records an error
+// and skips to the teardown, which always frees TMEM.
+#include "tddft_internal.h"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+namespace tddft {
+
+namespace {
+
+constexpr int TBM = 128, TBN = 128, TBK = 32;
+template <int NSPLIT> __host__ __device__ constexpr int stages() { return NSPLIT == 1 ? 4 : 3; }
+constexpr int TSTAGES = 4;   // control-block capacity (>= stages<NSPLIT>())
+constexpr int TILE_BYTES = TBM * TBK * 4;                  // 16 KB per operand tile
+constexpr long long WAIT_LIMIT = 4000000000LL;             // clock64 ticks (~2 s)
+
+struct __align__(8) TcShared {
+    unsigned long long full[TSTAGES];
+    unsigned long long empty[TSTAGES];
+    unsigned long long accum;
+    unsigned int tmem_base;
+    int abort;
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *b, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *b, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *b, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait; returns false on expiry or when another role already gave up
+__device__ __forceinline__ bool mbar_wait(unsigned long long *b, unsigned parity, volatile int *abort) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(b, parity)) {
+        if (*abort) return false;
+        if (clock64() - t0 > WAIT_LIMIT) {
+            *abort = 1;
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, unsigned long long *bar,
+                                            int c0, int c1, int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<unsigned long long>(map)), "r"(smem_u32(bar)),
+          "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
+}
+
+// UMMA shared-memory descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ unsigned long long smem_desc(unsigned saddr) {
+    unsigned long long d = 0;
+    d |= (unsigned long long)((saddr & 0x3FFFF) >> 4);       // start address, bits 0-13
+    d |= (unsigned long long)(16 >> 4) << 16;                // leading byte offset (unused here)
+    d |= (unsigned long long)(1024 >> 4) << 32;              // stride byte offset: 8 rows x 128 B
+    d |= (unsigned long long)1 << 46;                        // descriptor version (sm_100 family)
+    d |= (unsigned long long)2 << 61;                        // swizzle: 128 B
+    return d;
+}
+
+// instruction descriptor, kind::tf32: D f32, A/B tf32, both K-major, M = 128, N = 128
+__host__ __device__ constexpr unsigned idesc_tf32(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(N >> 3) << 17) | ((unsigned)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(unsigned tmem_d, unsigned long long da, unsigned long long db,
+                                         unsigned idesc, unsigned accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(tmem_d), "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(unsigned long long *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(unsigned taddr, float *v) {
+    unsigned r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// NSPLIT = 1: plain TF32; 3: three-term split (needs A_lo and B_lo maps)
+template <int NSPLIT>
+__global__ void __launch_bounds__(192, 1) tc_gemm_kernel(
+    const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
+    const __grid_constant__ CUtensorMap mAlo, const __grid_constant__ CUtensorMap mBlo, int M, int N,
+    int K, int batchA, int batchB, float alpha, float beta, float *__restrict__ C, int ldc, long long sC,
+    int *err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // 1024-byte aligned tile area, then the control block
+    unsigned char *base = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<unsigned long long>(smem_raw) + 1023ull) & ~1023ull);
+    constexpr int NT = NSPLIT == 1 ? 2 : 4;   // operand tiles per stage
+    constexpr int S = stages<NSPLIT>();
+    unsigned char *tiles = base;
+    TcShared *ctl = reinterpret_cast<TcShared *>(base + (size_t)S * NT * TILE_BYTES);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * TBM, n0 = blockIdx.x * TBN, b = blockIdx.z;
+    const int nk = (K + TBK - 1) / TBK;
+    volatile int *abort = &ctl->abort;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&ctl->full[s], 1);
+            mbar_init(&ctl->empty[s], 1);
+        }
+        mbar_init(&ctl->accum, 1);
+        ctl->abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 5) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&ctl->tmem_base)),
+                     "r"(TBN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = ctl->tmem_base;
+
+    if (warp == 4 && lane == 0) {
+        // TMA producer
+        const int ba = batchA > 1 ? b : 0, bb = batchB > 1 ? b : 0;
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % S;
+            const unsigned par = ((kb / S) & 1) ^ 1;
+            if (!mbar_wait(&ctl->empty[s], par, abort)) break;
+            unsigned char *st = tiles + (size_t)s * NT * TILE_BYTES;
+            mbar_expect_tx(&ctl->full[s], NT * TILE_BYTES);
+            tma_load_3d(st, &mA, &ctl->full[s], kb * TBK, m0, ba);
+            tma_load_3d(st + TILE_BYTES, &mB, &ctl->full[s], kb * TBK, n0, bb);
+            if (NSPLIT == 3) {
+                tma_load_3d(st + 2 * TILE_BYTES, &mAlo, &ctl->full[s], kb * TBK, m0, ba);
+                tma_load_3d(st + 3 * TILE_BYTES, &mBlo, &ctl->full[s], kb * TBK, n0, bb);
+            }
+        }
+    } else if (warp == 5 && lane == 0) {
+        // MMA issuer
+        constexpr unsigned idesc = idesc_tf32(TBM, TBN);
+        bool ok = true;
+        for (int kb = 0; kb < nk && ok; ++kb) {
+            const int s = kb % S;
+            const unsigned par = (kb / S) & 1;
+            if (!mbar_wait(&ctl->full[s], par, abort)) {
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            unsigned char *st = tiles + (size_t)s * NT * TILE_BYTES;
+            const unsigned a = smem_u32(st), bt = smem_u32(st + TILE_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < TBK / 8; ++kk) {
+                const unsigned off = kk * 32;   // 8 tf32 = 32 bytes along K inside the swizzle row
+                const unsigned acc = (kb > 0 || kk > 0) ? 1u : 0u;
+                mma_tf32(tmem, smem_desc(a + off), smem_desc(bt + off), idesc, acc);
+                if (NSPLIT == 3) {
+                    const unsigned alo = smem_u32(st + 2 * TILE_BYTES), blo = smem_u32(st + 3 * TILE_BYTES);
+                    mma_tf32(tmem, smem_desc(a + off), smem_desc(blo + off), idesc, 1u);
+                    mma_tf32(tmem, smem_desc(alo + off), smem_desc(bt + off), idesc, 1u);
+                }
+            }
+            mma_commit(&ctl->empty[s]);
+        }
+        mma_commit(&ctl->accum);
+    } else if (warp < 4) {
+        // epilogue: TMEM -> registers -> C
+        const bool ok = mbar_wait(&ctl->accum, 0, abort) && !*abort;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int row = m0 + warp * 32 + lane;
+        float *crow = C + (long long)b * sC + (long long)row * ldc;
+        for (int c0 = 0; c0 < TBN; c0 += 32) {
+            float v[32];
+            tmem_ld32(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0, v);
+            if (!ok || row >= M) continue;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int col = n0 + c0 + j;
+                if (col < N) crow[col] = (beta == 0.0f) ? alpha * v[j] : fmaf(alpha, v[j], beta * crow[col]);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 5) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TBN));
+    }
+    if (threadIdx.x == 0 && ctl->abort) atomicExch(err, 1);
+}
+
+// ---- host side ---------------------------------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, []() {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// 3-D map over [batch][rows][K] float32 with row stride ld and batch stride sb (elements);
+// box 32 (K) x 128 rows x 1, 128-byte swizzle, zero fill outside.
+bool make_map(CUtensorMap *map, const float *ptr, int K, int rows, int ld, long long sb, int batch) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)(batch > 0 ? batch : 1)};
+    const long long bs = (batch > 1) ? sb * 4 : (long long)ld * rows * 4;
+    cuuint64_t strides[2] = {(cuuint64_t)ld * 4, (cuuint64_t)(bs > 0 ? ((bs + 15) / 16) * 16 : 16)};
+    cuuint32_t box[3] = {TBK, TBM, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(ptr), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+size_t tc_smem(int nsplit) {
+    return (nsplit == 1 ? (size_t)stages<1>() * 2 : (size_t)stages<3>() * 4) * TILE_BYTES + sizeof(TcShared) + 1024;
+}
+
+int *error_word() {
+    static int *w = nullptr;
+    if (!w) {
+        check(cudaMalloc(&w, sizeof(int)), "cudaMalloc tc error word");
+        check(cudaMemset(w, 0, sizeof(int)), "memset tc error word");
+    }
+    return w;
+}
+
+}  // namespace
+
+bool tc_gemm_available() { return encode_fn() != nullptr; }
+
+// C[b] = alpha * A[b] B[b]^T + beta C[b] with A (M x K, ld lda, batch stride sA; 0 = shared) and
+// B (N x K, ldb, sB). Alo/Blo: the lo parts for the split (both null: plain TF32). K-contiguous
+// rows must start on 16-byte boundaries: lda, ldb, sA, sB multiples of 4, pointers 16-aligned.
+void tc_gemm_nt(cudaStream_t st, int M, int N, int K, float alpha, const float *A, int lda, long long sA,
+                const float *Alo, const float *B, int ldb, long long sB, const float *Blo, float beta, float *C,
+                int ldc, long long sC, int batch) {
+    const int nsplit = (Alo && Blo) ? 3 : 1;
+    CUtensorMap ma, mb, malo, mblo;
+    const int bA = sA ? batch : 1, bB = sB ? batch : 1;
+    if (!make_map(&ma, A, K, M, lda, sA, bA) || !make_map(&mb, B, K, N, ldb, sB, bB))
+        throw CudaError{cudaErrorInvalidValue, "cuTensorMapEncodeTiled"};
+    if (nsplit == 3) {
+        if (!make_map(&malo, Alo, K, M, lda, sA, bA) || !make_map(&mblo, Blo, K, N, ldb, sB, bB))
+            throw CudaError{cudaErrorInvalidValue, "cuTensorMapEncodeTiled (lo)"};
+    } else {
+        malo = ma;
+        mblo = mb;
+    }
+    const size_t sm = tc_smem(nsplit);
+    static bool attr1 = false, attr3 = false;
+    if (nsplit == 1 && !attr1) {
+        check(cudaFuncSetAttribute(tc_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm), "attr tc1");
+        attr1 = true;
+    }
+    if (nsplit == 3 && !attr3) {
+        check(cudaFuncSetAttribute(tc_gemm_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm), "attr tc3");
+        attr3 = true;
+    }
+    dim3 grid((N + TBN - 1) / TBN, (M + TBM - 1) / TBM, batch);
+    int *err = error_word();
+    if (nsplit == 3)
+        tc_gemm_kernel<3><<<grid, 192, sm, st>>>(ma, mb, malo, mblo, M, N, K, bA, bB, alpha, beta, C, ldc, sC, err);
+    else
+        tc_gemm_kernel<1><<<grid, 192, sm, st>>>(ma, mb, malo, mblo, M, N, K, bA, bB, alpha, beta, C, ldc, sC, err);
+    check_launch("tc_gemm_kernel");
+}
+
+namespace {
+
+__device__ __forceinline__ float tf32_rna(float x) {
+    unsigned r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// hi/lo split of nb matrices (rows x cols, ld / s_in) into row-major outputs of row length ldo
+// (>= cols, the pad written as zeros)
+__global__ void split_kernel(const float *__restrict__ in, int rows, int cols, int ld, long long s_in,
+                             float *__restrict__ hi, float *__restrict__ lo, int ldo, long long s_out, int nb) {
+    const long long per = (long long)rows * ldo, tot = per * nb;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(i / per);
+        const long long r = (i - b * per) / ldo, c = (i - b * per) - r * ldo;
+        const float x = c < cols ? in[b * s_in + r * ld + c] : 0.0f;
+        if (lo) {
+            const float h = tf32_rna(x);
+            hi[b * s_out + r * ldo + c] = h;
+            lo[b * s_out + r * ldo + c] = x - h;
+        } else {
+            hi[b * s_out + r * ldo + c] = x;
+        }
+    }
+}
+
+// out[b][c][r] = in[b][r][c] (32 x 32 tiles through shared memory), rows of the output padded to
+// ldo (>= rows) with zeros, with the hi/lo split when lo is given
+__global__ void transpose_split_kernel(const float *__restrict__ in, int rows, int cols, int ld,
+                                       long long s_in, float *__restrict__ hi, float *__restrict__ lo,
+                                       int ldo, long long s_out) {
+    __shared__ float t[32][33];
+    const int b = blockIdx.z;
+    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    const float *src = in + (long long)b * s_in;
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int r = r0 + i, c = c0 + threadIdx.x;
+        t[i][threadIdx.x] = (r < rows && c < cols) ? src[(long long)r * ld + c] : 0.0f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int c = c0 + i, r = r0 + threadIdx.x;
+        if (c < cols && r < ldo) {
+            const float x = t[threadIdx.x][i];
+            const long long o = (long long)b * s_out + (long long)c * ldo + r;
+            if (lo) {
+                const float h = tf32_rna(x);
+                hi[o] = h;
+                lo[o] = x - h;
+            } else {
+                hi[o] = x;
+            }
+        }
+    }
+}
+
+// process-wide scratch for the split operands (grown on demand, never shrunk)
+struct Scratch {
+    float *p = nullptr;
+    size_t cap = 0;
+    float *get(size_t n) {
+        if (n > cap) {
+            if (p) cudaFree(p);
+            p = nullptr;
+            check(cudaMalloc(&p, n * sizeof(float)), "cudaMalloc tc scratch");
+            cap = n;
+        }
+        return p;
+    }
+};
+Scratch &scratch() {
+    static Scratch s;
+    return s;
+}
+
+int grid1(long long n) {
+    long long b = (n + 255) / 256;
+    return (int)(b < 8 * 152 ? (b > 0 ? b : 1) : 8 * 152);
+}
+
+}  // namespace
+
+// Dispatch of a row-major C[b] = alpha op(A[b]) op(B[b]) + beta C[b] onto the tensor cores:
+// operands are brought to K-major (transposed where needed) and split into hi/lo parts in scratch.
+void tc_gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, float alpha, const float *A, int lda,
+             long long sA, const float *B, int ldb, long long sB, float beta, float *C, int ldc, long long sC,
+             int batch, bool split) {
+    const int bA = sA ? batch : 1, bB = sB ? batch : 1;
+    const int Kp = (K + 3) / 4 * 4;                     // 16-byte rows for the tensor maps
+    auto up64 = [](size_t n) { return (n + 63) / 64 * 64; };
+    const size_t na = up64((size_t)M * Kp * bA), nbt = up64((size_t)N * Kp * bB);
+    const size_t need = (split ? 2 : 1) * (na + nbt);
+    float *base = scratch().get(need);
+    float *Ahi = base, *Alo = split ? base + na : nullptr;
+    float *Bhi = base + (split ? 2 * na : na), *Blo = split ? Bhi + nbt : nullptr;
+    const long long sa = (long long)M * Kp, sb = (long long)N * Kp;
+    // A as M x Kp, K contiguous
+    if (!ta) {
+        split_kernel<<<grid1((long long)M * Kp * bA), 256, 0, st>>>(A, M, K, lda, sA, Ahi, Alo, Kp, sa, bA);
+    } else {
+        dim3 g((M + 31) / 32, (Kp + 31) / 32, bA);
+        transpose_split_kernel<<<g, dim3(32, 8), 0, st>>>(A, K, M, lda, sA, Ahi, Alo, Kp, sa);
+    }
+    check_launch("tc split A");
+    // B as N x Kp, K contiguous
+    if (tb) {
+        split_kernel<<<grid1((long long)N * Kp * bB), 256, 0, st>>>(B, N, K, ldb, sB, Bhi, Blo, Kp, sb, bB);
+    } else {
+        dim3 g((N + 31) / 32, (Kp + 31) / 32, bB);
+        transpose_split_kernel<<<g, dim3(32, 8), 0, st>>>(B, K, N, ldb, sB, Bhi, Blo, Kp, sb);
+    }
+    check_launch("tc split B");
+    tc_gemm_nt(st, M, N, Kp, alpha, Ahi, Kp, bA > 1 ? sa : 0, Alo, Bhi, Kp, bB > 1 ? sb : 0, Blo, beta, C, ldc,
+               sC, batch);
+}
+
+int tc_error_read_and_clear(cudaStream_t st) {
+    int h = 0;
+    int *w = error_word();
+    check(cudaMemcpyAsync(&h, w, sizeof(int), cudaMemcpyDeviceToHost, st), "D2H tc error");
+    check(cudaStreamSynchronize(st), "sync tc error");
+    if (h) check(cudaMemsetAsync(w, 0, sizeof(int), st), "clear tc error");
+    return h;
+}
+
+}  // namespace tddft
