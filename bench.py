@@ -259,6 +259,15 @@ def run_ours(args):
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": None, "kernel": name,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s"}
+    elif name == "gemm" and args.precision == "mixed" and os.environ.get("TDDFT_NO_TC") != "1":
+        # tcgen05 kind::tf32 (three-term split); peak = measured sustained bf16 x nominal tf32/bf16
+        bf16 = peaks.get("bf16_tflops_sustained", 1700.0)
+        peak = bf16 * (1.1 / 2.25)
+        achieved = dfl / (dms / 1000.0) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": name,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained x 1.1/2.25 (tf32/bf16 nominal)",
+                "note": "achieved counts 2MNK per product; the three-term split issues 3 MMAs per product"}
     else:
         # CUDA-core float32 (mixed) or float64 contraction: ALU bound.
         lanes = 128 if args.precision == "mixed" else 2

@@ -40,7 +40,8 @@ Readings where the paper is silent (Algorithms 1 and 2 of its supplement are not
     coefficient vectors of the M Gram matrix (which the line search already holds); a
     non-positive norm after projection is a breakdown;
   * f is carried along by the same linear combinations and recomputed from scratch every
-    ``reapply_every`` iterations.
+    ``reapply_every`` iterations, after P is recomputed from L by Eq. auxiliary (the two agree
+    in exact arithmetic; in float32 this keeps P on the invariant subspace).
 """
 import numpy as np
 
@@ -315,6 +316,9 @@ class PCG:
         self.flipped = self.orthonormalize(T, order)
         self.it += 1
         if self.reapply_every > 0 and self.it % self.reapply_every == 0:
+            # P afresh from the search variables (equal in exact arithmetic), then f = f(P)
+            self.Pp = np.array([op.project(Y) for Y in self.Yp])
+            self.Pq = np.array([op.project(Y) for Y in self.Yq])
             self.reapply()
         self.prev = (dir_p, dir_q, Dp, Dq, Zp, Zq, gz)
         self.omega_prev = omega

@@ -434,7 +434,8 @@ struct tddft_state {
     std::vector<double> omega, resid, omega_prev;
     std::unique_ptr<StateBufs<double>> s64;
     std::unique_ptr<StateBufs<float>> s32;
-    double *host = nullptr;   // pinned: [omega k][resid k][status][n_active][lam]
+    double *host = nullptr;   // pinned, 4k + 16 doubles: [omega k][resid k][status, n_active][lam]
+                              // (tddft_subspace uses [omega k][pairing 2k])
     ~tddft_state() {
         if (host) cudaFreeHost(host);
     }
@@ -668,7 +669,13 @@ void update(tddft_ctx *c, tddft_state *S) {
     check(cudaMemcpyAsync(S->host + 2 * k + 1, B.lam, sizeof(double), cudaMemcpyDeviceToHost, st), "D2H lam");
     sync_status(c, S, B.status);
     S->it += 1;
-    if (c->opt.reapply_every > 0 && S->it % c->opt.reapply_every == 0) apply_impl<T>(c, I, k, B.P, B.f);
+    if (c->opt.reapply_every > 0 && S->it % c->opt.reapply_every == 0) {
+        // P = P^c S L S P^v afresh from the search variables (Eq. auxiliary), then f = f(P)
+        check(cudaMemcpyAsync(B.tmp, B.Y, tot * sizeof(T), cudaMemcpyDeviceToDevice, st), "copy Y");
+        if (c->trunc) mask_mul<T>(st, B.tmp, I.mask, len, k2);
+        sandwich<T>(c, k2, I.Rc, B.tmp, I.Rv, B.P, B.cLpp);
+        apply_impl<T>(c, I, k, B.P, B.f);
+    }
     std::swap(B.pdir, B.dir);
     std::swap(B.pD, B.D);
     std::swap(B.pz, B.z);
@@ -923,7 +930,7 @@ tddft_status tddft_state_create(tddft_ctx *c, int32_t k, const double *Y0, tddft
         if (k <= 0 || k > KMAX || !Y0) throw InvalidArg{"tddft_state_create: need 1 <= k <= 16 and Y0"};
         S->ctx = c;
         S->k = k;
-        check(cudaMallocHost(reinterpret_cast<void **>(&S->host), (2 * k + 8) * sizeof(double)), "cudaMallocHost");
+        check(cudaMallocHost(reinterpret_cast<void **>(&S->host), (4 * k + 16) * sizeof(double)), "cudaMallocHost");
         return DISPATCH(c, ([&]() {
             alloc_state<T>(c, S.get());
             state_init<T>(c, S.get(), Y0);
@@ -936,7 +943,7 @@ tddft_status tddft_state_create(tddft_ctx *c, int32_t k, const double *Y0, tddft
 
 void tddft_state_destroy(tddft_state *s) {
     if (!s) return;
-    if (s->ctx) cudaStreamSynchronize(s->ctx->st);
+    cudaDeviceSynchronize();   // the state's buffers may still be in use by queued work
     delete s;
 }
 

@@ -6,8 +6,10 @@ raises at load time: there is no CPU path.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes
 import os
+import weakref
 
 import numpy as np
 
@@ -62,6 +64,18 @@ SYMBOLS = sorted(["tddft_default_options", "tddft_create", "tddft_destroy", "tdd
                   "tddft_work"])
 
 _lib = None
+_live = weakref.WeakSet()      # open contexts and states, closed before interpreter shutdown
+_closed_all = False
+
+
+@atexit.register
+def _close_all():
+    global _closed_all
+    for obj in [o for o in list(_live) if isinstance(o, State)]:
+        obj.close()
+    for obj in list(_live):
+        obj.close()
+    _closed_all = True
 
 
 def load(path: str = LIB_PATH):
@@ -191,9 +205,13 @@ class Context:
             raise TddftError(rc, "tddft_create failed (see stderr)")
         self._ctx = ctx
         self.nc, self.nv, self.n = sys.chi.nfun, sys.phi.nfun, sys.n
+        self._states = weakref.WeakSet()
+        _live.add(self)
 
     def close(self):
         if getattr(self, "_ctx", None):
+            for st in list(getattr(self, "_states", ())):
+                st.close()
             self._lib.tddft_destroy(self._ctx)
             self._ctx = None
 
@@ -278,10 +296,13 @@ class State:
         st = ctypes.c_void_p()
         ctx._check(ctx._lib.tddft_state_create(ctx._ctx, self.k, _ptr(Y0), ctypes.byref(st)))
         self._st = st
+        ctx._states.add(self)
+        _live.add(self)
 
     def close(self):
         if getattr(self, "_st", None):
-            self.ctx._lib.tddft_state_destroy(self._st)
+            if getattr(self.ctx, "_ctx", None):
+                self.ctx._lib.tddft_state_destroy(self._st)
             self._st = None
 
     def __del__(self):
