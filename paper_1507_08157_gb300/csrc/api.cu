@@ -33,6 +33,9 @@ struct InvalidArg {
 struct Breakdown {
     std::string msg;
 };
+struct TimeoutErr {
+    std::string msg;
+};
 
 // owning list of device allocations
 struct Mem {
@@ -72,6 +75,12 @@ struct Impl {
     T *Sc = nullptr, *Sv = nullptr, *Pc = nullptr, *Pv = nullptr, *Mc = nullptr, *Mv = nullptr;
     T *Rc = nullptr, *Rv = nullptr, *Ac = nullptr, *Av = nullptr, *mask = nullptr, *fxc = nullptr;
     double *fxc64 = nullptr;
+    // tensor-core grid path (float32 contexts): point-major f16 chi tables [tile][512][CK]
+    unsigned short *chi_pm = nullptr;
+    int CK = 0, NPmax = 0;
+    bool grid_tc = false;
+    unsigned *tc_bits = nullptr;
+    float *tc_scale = nullptr;
     // operator workspace, sized for up to `cap` grid states
     Mem wmem;
     int cap = 0;
@@ -107,6 +116,16 @@ struct tddft_ctx {
 };
 
 namespace tddft {
+bool tc_enabled();
+int *tc_error_word();
+int tc_error_read_and_clear(cudaStream_t st);
+void build_point_major_f16(const int *off_h, const float *val_h_or_null, const double *vald_h_or_null,
+                           int ntiles, int CK, unsigned short *out_h);
+int density_tc_group(int KBmax, int NP, int k);
+void response_density_tc(cudaStream_t st, const GridShape &g, const TileSet<float> &chi,
+                         const TileSet<float> &phi, const unsigned short *chi_pm, int CK, int NPmax, int nphi,
+                         const float *P, long long sP, int k, float *rho, unsigned *scratch_bits,
+                         float *scale, int *err);
 Profiler *profiler_new();
 void profiler_delete(Profiler *p);
 void profiler_read(Profiler *p, long long *launches, double *ms, double *flops, double *bytes);
@@ -143,6 +162,9 @@ tddft_status guarded(tddft_ctx *c, F &&f) {
     } catch (const Breakdown &e) {
         c->err = e.msg;
         return TDDFT_E_BREAKDOWN;
+    } catch (const TimeoutErr &e) {
+        c->err = e.msg;
+        return TDDFT_E_TIMEOUT;
     } catch (const std::bad_alloc &) {
         c->err = "out of memory";
         return TDDFT_E_NOMEM;
@@ -310,7 +332,27 @@ void ensure_workspace(tddft_ctx *c, Impl<T> &I, int states) {
     I.bufF = I.wmem.template alloc<T>((size_t)states * len);
     I.stage = I.wmem.template alloc<double>((size_t)std::max<long long>(states * len, states * n3));
     I.gscratch = I.wmem.template alloc<double>((size_t)gram_scratch_doubles(64, 32));
+    I.tc_bits = I.wmem.template alloc<unsigned>((size_t)states);
+    I.tc_scale = I.wmem.template alloc<float>((size_t)states);
     I.cap = states;
+}
+
+// response density of ns states into I.rho: tensor cores (f16 operands) for float32 contexts
+// whose tiles fit, CUDA cores otherwise
+template <typename T>
+void density(tddft_ctx *c, Impl<T> &I, const T *P, int ns) {
+    if constexpr (sizeof(T) == 4) {
+        if (I.grid_tc) {
+            response_density_tc(c->st, c->grid(), I.chi, I.phi, I.chi_pm, I.CK, I.NPmax, c->nv, P, c->len(), ns,
+                                I.rho, I.tc_bits, I.tc_scale, tc_error_word());
+            return;
+        }
+    }
+    response_density<T>(c->st, c->grid(), I.chi, I.phi, c->nv, P, c->len(), ns, I.rho);
+}
+
+void check_tc_error(tddft_ctx *c) {
+    if (tc_error_read_and_clear(c->st)) throw TimeoutErr{"a bounded wait in a tensor-core kernel expired"};
 }
 
 // ---- the operator (Eq. operator_RPA) -------------------------------------------------------------
@@ -331,7 +373,7 @@ void apply_impl(tddft_ctx *c, Impl<T> &I, int k, const T *P, T *f) {
     T *fs = tda ? f : f + k * len;
     const T alpha = tda ? T(1) : T(2);
     const GridShape g = c->grid();
-    response_density<T>(st, g, I.chi, I.phi, nv, Ps, len, ns, I.rho);
+    density(c, I, Ps, ns);
     hartree_fxc<T>(st, g, I.rho, I.fxc, ns, I.V, I.fft);
     potential_integrals<T>(st, g, I.chi, I.phi, nc, nv, I.V, ns, I.Vmat);
     // coupling: f_q += 2 P^c V_SCF P^v
@@ -348,6 +390,35 @@ void build_impl(tddft_ctx *c, const tddft_system *s) {
     std::vector<int> cc_cnt, cv_cnt;
     build_tiles<T>(s->chi, n, c->nt, I->mem, I->chi, cc_cnt);
     build_tiles<T>(s->phi, n, c->nt, I->mem, I->phi, cv_cnt);
+    if constexpr (sizeof(T) == 4) {
+        // tensor-core grid path: point-major f16 chi copy, state-group shape
+        if (tc_enabled()) {
+            const int ntl = I->chi.ntiles;
+            std::vector<int> coff(ntl + 1), poff(ntl + 1);
+            check(cudaMemcpy(coff.data(), I->chi.off, coff.size() * sizeof(int), cudaMemcpyDeviceToHost), "D2H off");
+            check(cudaMemcpy(poff.data(), I->phi.off, poff.size() * sizeof(int), cudaMemcpyDeviceToHost), "D2H off");
+            int maxc = 0, maxp = 0;
+            for (int t = 0; t < ntl; ++t) {
+                maxc = std::max(maxc, coff[t + 1] - coff[t]);
+                maxp = std::max(maxp, poff[t + 1] - poff[t]);
+            }
+            const int CK = std::max(64, (maxc + 63) / 64 * 64);
+            const int NP = std::max(16, (maxp + 15) / 16 * 16);
+            if (NP <= 256 && density_tc_group(CK / 64, NP, 1) >= 1) {
+                std::vector<float> cval((size_t)coff[ntl] * TILE_PTS);
+                check(cudaMemcpy(cval.data(), I->chi.val, cval.size() * sizeof(float), cudaMemcpyDeviceToHost),
+                      "D2H chi tables");
+                std::vector<unsigned short> pm((size_t)ntl * TILE_PTS * CK, 0);
+                build_point_major_f16(coff.data(), cval.data(), nullptr, ntl, CK, pm.data());
+                I->chi_pm = I->mem.template alloc<unsigned short>(pm.size());
+                check(cudaMemcpy(I->chi_pm, pm.data(), pm.size() * sizeof(unsigned short), cudaMemcpyHostToDevice),
+                      "upload point-major chi");
+                I->CK = CK;
+                I->NPmax = NP;
+                I->grid_tc = true;
+            }
+        }
+    }
     double pp = 0.0, tv = 0.0;
     for (size_t i = 0; i < cc_cnt.size(); ++i) {
         pp += (double)cc_cnt[i] * cv_cnt[i];
@@ -505,6 +576,7 @@ void sync_status(tddft_ctx *c, tddft_state *S, const int *dstatus) {
                           cudaMemcpyDeviceToHost, c->st),
           "D2H status");
     check(cudaStreamSynchronize(c->st), "sync status");
+    check_tc_error(c);
     const int stv = *reinterpret_cast<int *>(S->host + 2 * S->k);
     if (stv == DEV_BREAKDOWN) throw Breakdown{"non-positive norm in Gram-Schmidt (dependent trial pairs)"};
     if (stv == DEV_NAN) throw Breakdown{"NaN or Inf in the trial pairs"};
@@ -859,6 +931,7 @@ tddft_status tddft_apply(tddft_ctx *c, int32_t k, const double *Pp, const double
             download<T>(c, I, I.bufF, fp, kl);
             download<T>(c, I, I.bufF + kl, fq, kl);
             check(cudaStreamSynchronize(c->st), "sync apply");
+            check_tc_error(c);
             return TDDFT_OK;
         })());
     });
@@ -872,9 +945,10 @@ tddft_status tddft_response_density(tddft_ctx *c, int32_t k, const double *P, do
             Impl<T> &I = impl<T>(c);
             ensure_workspace(c, I, k);
             upload<T>(c, I, P, I.bufP, (long long)k * c->len());
-            response_density<T>(c->st, c->grid(), I.chi, I.phi, c->nv, I.bufP, c->len(), k, I.rho);
+            density(c, I, I.bufP, k);
             download<T>(c, I, I.rho, rho, (long long)k * c->n3());
             check(cudaStreamSynchronize(c->st), "sync density");
+            check_tc_error(c);
             return TDDFT_OK;
         })());
     });

@@ -13,6 +13,7 @@
 // lane 0 issues the MMAs. 128 x 128 output tile, K in slices of 32 floats (one 128-byte swizzle
 // row), 4-stage mbarrier pipeline. Every wait is bounded: on expiry the block records an error
 // and skips to the teardown, which always frees TMEM.
+#include "tc_common.cuh"
 #include "tddft_internal.h"
 
 #include <cuda.h>
@@ -28,7 +29,6 @@ constexpr int TBM = 128, TBN = 128, TBK = 32;
 template <int NSPLIT> __host__ __device__ constexpr int stages() { return NSPLIT == 1 ? 4 : 3; }
 constexpr int TSTAGES = 4;   // control-block capacity (>= stages<NSPLIT>())
 constexpr int TILE_BYTES = TBM * TBK * 4;                  // 16 KB per operand tile
-constexpr long long WAIT_LIMIT = 4000000000LL;             // clock64 ticks (~2 s)
 
 struct __align__(8) TcShared {
     unsigned long long full[TSTAGES];
@@ -38,93 +38,7 @@ struct __align__(8) TcShared {
     int abort;
 };
 
-__device__ __forceinline__ unsigned smem_u32(const void *p) {
-    return static_cast<unsigned>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(unsigned long long *b, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long *b, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long *b, unsigned parity) {
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(b)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// bounded wait; returns false on expiry or when another role already gave up
-__device__ __forceinline__ bool mbar_wait(unsigned long long *b, unsigned parity, volatile int *abort) {
-    const long long t0 = clock64();
-    while (!mbar_try_wait(b, parity)) {
-        if (*abort) return false;
-        if (clock64() - t0 > WAIT_LIMIT) {
-            *abort = 1;
-            return false;
-        }
-    }
-    return true;
-}
-
-__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, unsigned long long *bar,
-                                            int c0, int c1, int c2) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
-        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<unsigned long long>(map)), "r"(smem_u32(bar)),
-          "r"(c0), "r"(c1), "r"(c2)
-        : "memory");
-}
-
-// UMMA shared-memory descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 B apart
-__device__ __forceinline__ unsigned long long smem_desc(unsigned saddr) {
-    unsigned long long d = 0;
-    d |= (unsigned long long)((saddr & 0x3FFFF) >> 4);       // start address, bits 0-13
-    d |= (unsigned long long)(16 >> 4) << 16;                // leading byte offset (unused here)
-    d |= (unsigned long long)(1024 >> 4) << 32;              // stride byte offset: 8 rows x 128 B
-    d |= (unsigned long long)1 << 46;                        // descriptor version (sm_100 family)
-    d |= (unsigned long long)2 << 61;                        // swizzle: 128 B
-    return d;
-}
-
-// instruction descriptor, kind::tf32: D f32, A/B tf32, both K-major, M = 128, N = 128
-__host__ __device__ constexpr unsigned idesc_tf32(int M, int N) {
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(N >> 3) << 17) | ((unsigned)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_tf32(unsigned tmem_d, unsigned long long da, unsigned long long db,
-                                         unsigned idesc, unsigned accumulate) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
-        ::"r"(tmem_d), "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
-}
-
-__device__ __forceinline__ void mma_commit(unsigned long long *bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(unsigned taddr, float *v) {
-    unsigned r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
+using namespace tc;
 
 // NSPLIT = 1: plain TF32; 3: three-term split (needs A_lo and B_lo maps)
 template <int NSPLIT>
@@ -283,6 +197,21 @@ int *error_word() {
 
 bool tc_gemm_available() { return encode_fn() != nullptr; }
 
+// 2-D tiled map, 128-byte swizzle, zero fill outside: `inner` elements per row (contiguous),
+// `rows` rows `row_bytes` apart; box box_inner x box_rows
+bool encode_map_2d(CUtensorMap *map, CUtensorMapDataType dt, const void *ptr, unsigned long long inner,
+                   unsigned long long rows, unsigned long long row_bytes, unsigned box_inner, unsigned box_rows) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {inner, rows};
+    cuuint64_t strides[1] = {row_bytes};
+    cuuint32_t box[2] = {box_inner, box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    return fn(map, dt, 2, const_cast<void *>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // C[b] = alpha * A[b] B[b]^T + beta C[b] with A (M x K, ld lda, batch stride sA; 0 = shared) and
 // B (N x K, ldb, sB). Alo/Blo: the lo parts for the split (both null: plain TF32). K-contiguous
 // rows must start on 16-byte boundaries: lda, ldb, sA, sB multiples of 4, pointers 16-aligned.
@@ -437,6 +366,8 @@ void tc_gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, float alpha
     tc_gemm_nt(st, M, N, Kp, alpha, Ahi, Kp, bA > 1 ? sa : 0, Alo, Bhi, Kp, bB > 1 ? sb : 0, Blo, beta, C, ldc,
                sC, batch);
 }
+
+int *tc_error_word() { return error_word(); }
 
 int tc_error_read_and_clear(cudaStream_t st) {
     int h = 0;

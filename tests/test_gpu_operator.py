@@ -2,9 +2,16 @@
 
 Cases: a 3-atom system on a 30^3 grid (tiles of 8 leave a ragged tail of 6), a 2-atom system whose
 boxes wrap the periodic cell on every axis (20^3), a 9-chi (s, p, d) system, and the 8-atom /
-48^3 workload. Tolerances: FP64 mode 1e-10 of the largest reference entry; mixed (float32)
-mode 3e-5 of it (float32 unit roundoff 6e-8 times the ~500-term tile sums and ~1000-term matrix
-products, with margin).
+48^3 workload. Tolerances, relative to the largest reference entry:
+  * FP64 mode: 1e-10;
+  * mixed mode, float32 stages (FFT Poisson + f_xc, potential integrals, matrix products on
+    three-term-split TF32 tensor cores): 3e-5 (float32 roundoff 6e-8 times ~500-term tile sums and
+    ~1000-term products, with margin);
+  * mixed mode, response density on the tensor cores: float16 operands (unit roundoff 2^-11 =
+    4.9e-4) with float32 accumulation; the rounding errors of the ~10^4 products per point are
+    independent, so the error is ~4.9e-4 times the rms term times sqrt(#terms), i.e. ~4.9e-4 of
+    the density's own scale: 2e-3 of the largest entry. The same bound covers f in the full and
+    TDA modes, whose coupling term is built from that density.
 """
 import numpy as np
 import pytest
@@ -18,6 +25,7 @@ from paper_1507_08157_gb300 import synthetic as sy
 pytestmark = pytest.mark.gpu
 
 TOL = {"fp64": 1e-10, "mixed": 3e-5}
+TOL_DENSITY = {"fp64": 1e-10, "mixed": 2e-3}
 
 
 @pytest.fixture(scope="module")
@@ -70,7 +78,7 @@ def test_response_density(tddft, name, prec):
     P = sy.random_kernels(s, 3, 1)[0]
     got = ctx.response_density(P)
     ref = ogrid.response_density(ogrid.BoxedSet(s.chi, s.n), ogrid.BoxedSet(s.phi, s.n), P)
-    assert _err(got, ref) < TOL[prec]
+    assert _err(got, ref) < TOL_DENSITY[prec]
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
@@ -106,8 +114,9 @@ def test_apply_matches_oracle(tddft, name, mode, prec):
     Pp, Pq = sy.random_kernels(s, 3, 4)
     fp, fq = ctx.apply(Pp, Pq)
     rp, rq = oop.Operator(s).apply(Pp, Pq, mode=mode)
-    assert _err(fp, rp) < TOL[prec]
-    assert _err(fq, rq) < TOL[prec]
+    tol = TOL[prec] if mode == "d_only" else TOL_DENSITY[prec]
+    assert _err(fp, rp) < (TOL[prec] if mode != "tda" else tol)
+    assert _err(fq, rq) < tol
 
 
 def test_apply_device_pointers(tddft):
