@@ -4,11 +4,13 @@
 #include "solver_kernels.h"
 #include "tddft_internal.h"
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <new>
@@ -77,8 +79,9 @@ struct Impl {
     double *fxc64 = nullptr;
     // tensor-core grid path (float32 contexts): point-major f16 chi tables [tile][512][CK]
     unsigned short *chi_pm = nullptr;
-    int CK = 0, NPmax = 0;
-    bool grid_tc = false;
+    unsigned short *chi_fm16 = nullptr;   // function-major f16 chi tables [slot][512]
+    int CK = 0, NPmax = 0, nslots_chi = 0;
+    bool grid_tc = false, integrals_tc = false;
     unsigned *tc_bits = nullptr;
     float *tc_scale = nullptr;
     // operator workspace, sized for up to `cap` grid states
@@ -122,6 +125,11 @@ int tc_error_read_and_clear(cudaStream_t st);
 void build_point_major_f16(const int *off_h, const float *val_h_or_null, const double *vald_h_or_null,
                            int ntiles, int CK, unsigned short *out_h);
 int density_tc_group(int KBmax, int NP, int k);
+int integrals_tc_group(int NP, int k);
+void potential_integrals_tc(cudaStream_t st, const GridShape &g, const TileSet<float> &chi,
+                            const TileSet<float> &phi, const unsigned short *chi_fm16, int nslots, int NPmax,
+                            int nchi, int nphi, const float *V, int k, float *out, unsigned *scratch_bits,
+                            float *scale, int *err);
 void response_density_tc(cudaStream_t st, const GridShape &g, const TileSet<float> &chi,
                          const TileSet<float> &phi, const unsigned short *chi_pm, int CK, int NPmax, int nphi,
                          const float *P, long long sP, int k, float *rho, unsigned *scratch_bits,
@@ -351,6 +359,18 @@ void density(tddft_ctx *c, Impl<T> &I, const T *P, int ns) {
     response_density<T>(c->st, c->grid(), I.chi, I.phi, c->nv, P, c->len(), ns, I.rho);
 }
 
+template <typename T>
+void integrals(tddft_ctx *c, Impl<T> &I, int ns) {
+    if constexpr (sizeof(T) == 4) {
+        if (I.integrals_tc) {
+            potential_integrals_tc(c->st, c->grid(), I.chi, I.phi, I.chi_fm16, I.nslots_chi, I.NPmax, c->nc, c->nv,
+                                   I.V, ns, I.Vmat, I.tc_bits, I.tc_scale, tc_error_word());
+            return;
+        }
+    }
+    potential_integrals<T>(c->st, c->grid(), I.chi, I.phi, c->nc, c->nv, I.V, ns, I.Vmat);
+}
+
 void check_tc_error(tddft_ctx *c) {
     if (tc_error_read_and_clear(c->st)) throw TimeoutErr{"a bounded wait in a tensor-core kernel expired"};
 }
@@ -375,7 +395,7 @@ void apply_impl(tddft_ctx *c, Impl<T> &I, int k, const T *P, T *f) {
     const GridShape g = c->grid();
     density(c, I, Ps, ns);
     hartree_fxc<T>(st, g, I.rho, I.fxc, ns, I.V, I.fft);
-    potential_integrals<T>(st, g, I.chi, I.phi, nc, nv, I.V, ns, I.Vmat);
+    integrals(c, I, ns);
     // coupling: f_q += 2 P^c V_SCF P^v
     gemm<T>(st, false, false, nc, nv, nc, T(1), I.Pc, nc, 0, I.Vmat, nv, len, T(0), I.tmp, nv, len, ns);
     gemm<T>(st, false, false, ns * nc, nv, nv, alpha, I.tmp, nv, 0, I.Pv, nv, 0, T(1), fs, nv, 0, 1);
@@ -392,7 +412,8 @@ void build_impl(tddft_ctx *c, const tddft_system *s) {
     build_tiles<T>(s->phi, n, c->nt, I->mem, I->phi, cv_cnt);
     if constexpr (sizeof(T) == 4) {
         // tensor-core grid path: point-major f16 chi copy, state-group shape
-        if (tc_enabled()) {
+        const char *ng = std::getenv("TDDFT_NO_GRID_TC");
+        if (tc_enabled() && !(ng && ng[0] == '1')) {
             const int ntl = I->chi.ntiles;
             std::vector<int> coff(ntl + 1), poff(ntl + 1);
             check(cudaMemcpy(coff.data(), I->chi.off, coff.size() * sizeof(int), cudaMemcpyDeviceToHost), "D2H off");
@@ -416,6 +437,18 @@ void build_impl(tddft_ctx *c, const tddft_system *s) {
                 I->CK = CK;
                 I->NPmax = NP;
                 I->grid_tc = true;
+                if (maxc <= 256 && integrals_tc_group(NP, 1) >= 1) {
+                    std::vector<unsigned short> fm(cval.size());
+#pragma omp parallel for schedule(static)
+                    for (long long i = 0; i < (long long)cval.size(); ++i)
+                        fm[i] = __half_as_ushort(__float2half_rn(cval[i]));
+                    I->chi_fm16 = I->mem.template alloc<unsigned short>(fm.size());
+                    check(cudaMemcpy(I->chi_fm16, fm.data(), fm.size() * sizeof(unsigned short),
+                                     cudaMemcpyHostToDevice),
+                          "upload f16 chi");
+                    I->nslots_chi = coff[ntl];
+                    I->integrals_tc = true;
+                }
             }
         }
     }
@@ -580,6 +613,9 @@ void sync_status(tddft_ctx *c, tddft_state *S, const int *dstatus) {
     const int stv = *reinterpret_cast<int *>(S->host + 2 * S->k);
     if (stv == DEV_BREAKDOWN) throw Breakdown{"non-positive norm in Gram-Schmidt (dependent trial pairs)"};
     if (stv == DEV_NAN) throw Breakdown{"NaN or Inf in the trial pairs"};
+    if (stv == DEV_NAN_EVAL) throw Breakdown{"NaN or Inf in Q or the residuals of the trial pairs"};
+    if (stv == DEV_NAN_LINE) throw Breakdown{"NaN or Inf in the line-search traces (directions or f of them)"};
+    if (stv == DEV_NAN_INIT) throw Breakdown{"NaN or Inf in the starting trial pairs"};
 }
 
 // recombine Y, P, f with the Gram-Schmidt coefficients (sign flips folded into Cq)
@@ -978,9 +1014,10 @@ tddft_status tddft_potential_integrals(tddft_ctx *c, int32_t k, const double *V,
             Impl<T> &I = impl<T>(c);
             ensure_workspace(c, I, k);
             upload<T>(c, I, V, I.V, (long long)k * c->n3());
-            potential_integrals<T>(c->st, c->grid(), I.chi, I.phi, c->nc, c->nv, I.V, k, I.Vmat);
+            integrals(c, I, k);
             download<T>(c, I, I.Vmat, out, (long long)k * c->len());
             check(cudaStreamSynchronize(c->st), "sync integrals");
+            check_tc_error(c);
             return TDDFT_OK;
         })());
     });

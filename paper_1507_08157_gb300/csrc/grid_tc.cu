@@ -251,3 +251,247 @@ void response_density_tc(cudaStream_t st, const GridShape &g, const TileSet<floa
 }
 
 }  // namespace tddft
+
+// ================================================================================================
+// Potential integrals on the tensor cores (mixed precision): V_s,ab = dV sum_r chi_a(r) V_s(r) phi_b(r)
+// (the <chi|V_SCF|phi> matrix of Eqs. operator_TDA / operator_RPA) as one tcgen05 kind::f16
+// product per tile and state group,
+//
+//   D[a][(s,b)] = sum_r X[a][r] W[(s,b)][r],   W[(s,b)][r] = V_s(r) phi_b(r)
+//
+// M = chi functions of the tile (<= 2 blocks of 128), N = states x phi functions, K = the 512
+// tile points in 8 slices of 64. The chi block comes by TMA from the function-major f16 table;
+// four worker warps build W slice by slice (V scaled per state by a power of two) into a
+// double-buffered swizzled stage; one thread issues the MMAs. The epilogue adds dV * D into the
+// output matrices with vector reductions where four phi of one atom are contiguous.
+namespace tddft {
+namespace {
+
+struct __align__(8) IntShared {
+    unsigned long long x_full[2];
+    unsigned long long w_ready[2];
+    unsigned long long mma_done[2];
+    unsigned long long acc_done;
+    unsigned int tmem_base;
+    int abort;
+};
+
+__device__ __forceinline__ void red_add_v4(float *addr, float a, float b, float c, float d) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c), "f"(d)
+                 : "memory");
+}
+
+__global__ void __launch_bounds__(192, 1) integrals_tc_kernel(
+    const __grid_constant__ CUtensorMap mX,   // function-major chi: [slot][512] f16
+    int n, int nt, int NP, int G, int k, const int *__restrict__ coff, const int *__restrict__ cids,
+    const int *__restrict__ poff, const int *__restrict__ pids, const float *__restrict__ pval, int nchi,
+    int nphi, const float *__restrict__ V, const float *__restrict__ vscale, float dV, float *__restrict__ out,
+    bool vec_ok, int *err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *base = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<unsigned long long>(smem_raw) + 1023ull) & ~1023ull);
+    const int t = blockIdx.y, grp = blockIdx.x;
+    const int s0 = grp * G;
+    const int gs = min(G, k - s0);
+    const int c0 = coff[t], nc = coff[t + 1] - c0;
+    const int p0 = poff[t], np = poff[t + 1] - p0;
+    if (nc == 0 || np == 0) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int MB = (nc + 127) / 128;                 // 1 or 2 (host guarantees nc <= 256)
+    const int NB = G * NP;                           // <= 256, multiple of 16
+    // layout: X stages [2][2 x 16 KB], W stages [2][NB x 128 B], V tile [G][512] f32, control
+    unsigned char *Xs = base;
+    unsigned char *Ws = base + 2 * 32768;
+    float *Vt = reinterpret_cast<float *>(Ws + (size_t)2 * NB * 128);
+    IntShared *ctl = reinterpret_cast<IntShared *>(Vt + (size_t)G * TILE_PTS);
+    volatile int *abort = &ctl->abort;
+    const long long n3 = (long long)n * n * n;
+    const int tx = t / (nt * nt), ty = (t / nt) % nt, tz = t % nt;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&ctl->x_full[i], 1);
+            mbar_init(&ctl->w_ready[i], 128);
+            mbar_init(&ctl->mma_done[i], 1);
+        }
+        mbar_init(&ctl->acc_done, 1);
+        ctl->abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 5) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&ctl->tmem_base)),
+                     "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    // V of the group's states on the tile points, scaled
+    for (int i = threadIdx.x; i < gs * TILE_PTS; i += blockDim.x) {
+        const int sl = i / TILE_PTS, lp = i - sl * TILE_PTS;
+        const int gx = tx * TILE + (lp >> 6), gy = ty * TILE + ((lp >> 3) & 7), gz = tz * TILE + (lp & 7);
+        float v = 0.0f;
+        if (gx < n && gy < n && gz < n) v = V[(long long)(s0 + sl) * n3 + ((long long)gx * n + gy) * n + gz];
+        Vt[i] = v * vscale[s0 + sl];
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = ctl->tmem_base;
+    const unsigned idesc = idesc_f16(128, NB);
+    constexpr int KS = TILE_PTS / 64;                // 8 K slices
+
+    if (warp == 4) {
+        if (lane == 0) {
+            for (int kb = 0; kb < KS; ++kb) {
+                const int st = kb & 1, use = kb >> 1;
+                if (use > 0 && !mbar_wait(&ctl->mma_done[st], (use - 1) & 1, abort)) break;
+                mbar_expect_tx(&ctl->x_full[st], MB * 16384);
+                for (int mb = 0; mb < MB; ++mb)
+                    tma_load_2d(Xs + st * 32768 + mb * 16384, &mX, &ctl->x_full[st], kb * 64, c0 + mb * 128);
+            }
+        }
+    } else if (warp == 5) {
+        if (lane == 0) {
+            for (int kb = 0; kb < KS; ++kb) {
+                const int st = kb & 1, use = kb >> 1;
+                if (!mbar_wait(&ctl->x_full[st], use & 1, abort)) break;
+                if (!mbar_wait(&ctl->w_ready[st], use & 1, abort)) break;
+                tc_fence_after();
+                const unsigned wb = smem_u32(Ws + (size_t)st * NB * 128);
+                for (int mb = 0; mb < MB; ++mb) {
+                    const unsigned xa = smem_u32(Xs + st * 32768 + mb * 16384);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        mma_f16(tmem + mb * 256, smem_desc(xa + kk * 32), smem_desc(wb + kk * 32), idesc,
+                                (kb > 0 || kk > 0) ? 1u : 0u);
+                }
+                mma_commit(&ctl->mma_done[st]);
+            }
+            mma_commit(&ctl->acc_done);
+        }
+    } else {
+        // workers: build W slices, then the epilogue
+        for (int kb = 0; kb < KS; ++kb) {
+            const int st = kb & 1, use = kb >> 1;
+            if (use > 0 && !mbar_wait(&ctl->mma_done[st], (use - 1) & 1, abort)) break;
+            unsigned char *W = Ws + (size_t)st * NB * 128;
+            for (int idx = threadIdx.x; idx < NB * 8; idx += 128) {
+                const int row = idx % NB, c8 = idx / NB;
+                const int sl = row / NP, b = row - sl * NP;
+                unsigned short h[8];
+                if (sl < gs && b < np) {
+                    const float *ph = pval + (long long)(p0 + b) * TILE_PTS + kb * 64 + c8 * 8;
+                    const float *vv = Vt + sl * TILE_PTS + kb * 64 + c8 * 8;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) h[j] = __half_as_ushort(__float2half_rn(ph[j] * vv[j]));
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) h[j] = 0;
+                }
+                uint4 q;
+                q.x = h[0] | ((unsigned)h[1] << 16);
+                q.y = h[2] | ((unsigned)h[3] << 16);
+                q.z = h[4] | ((unsigned)h[5] << 16);
+                q.w = h[6] | ((unsigned)h[7] << 16);
+                *reinterpret_cast<uint4 *>(W + sw128_offset(row, c8)) = q;
+            }
+            fence_async_smem();
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ctl->w_ready[st])) : "memory");
+        }
+        const bool ok = mbar_wait(&ctl->acc_done, 0, abort) && !*abort;
+        tc_fence_after();
+        for (int mb = 0; mb < MB; ++mb) {
+            const int a = mb * 128 + warp * 32 + lane;
+            const bool arow = ok && a < nc;
+            const long long rowoff = arow ? (long long)cids[c0 + a] * nphi : 0;
+            for (int c = 0; c < NB; c += 32) {
+                float v[32];
+                tmem_ld32(tmem + mb * 256 + ((unsigned)(warp * 32) << 16) + (unsigned)c, v);
+                if (!arow) continue;
+#pragma unroll
+                for (int j = 0; j < 32; j += 4) {
+                    const int col = c + j;
+                    const int sl = col / NP, b = col - sl * NP;
+                    if (sl >= gs) continue;
+                    const float f = dV / vscale[s0 + sl];
+                    float *o = out + (long long)(s0 + sl) * nchi * nphi + rowoff;
+                    const int B0 = b < np ? pids[p0 + b] : -1;
+                    // four consecutive phi of one atom land on one aligned float4
+                    const bool vec = vec_ok && (b + 3 < np) && (B0 % 4 == 0) && pids[p0 + b + 3] == B0 + 3;
+                    if (vec) {
+                        red_add_v4(o + B0, f * v[j], f * v[j + 1], f * v[j + 2], f * v[j + 3]);
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int bu = b + u;
+                            if (bu < np && (col + u) / NP == sl) atomicAdd(o + pids[p0 + bu], f * v[j + u]);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 5) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+    }
+    if (threadIdx.x == 0 && ctl->abort) atomicExch(err, 1);
+}
+
+__global__ void vmaxabs_kernel(const float *__restrict__ V, long long n3, unsigned *__restrict__ bits) {
+    const int s = blockIdx.y;
+    float m = 0.0f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n3; i += (long long)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(V[(long long)s * n3 + i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(&bits[s], __float_as_uint(m));
+}
+
+}  // namespace
+
+size_t integrals_tc_smem(int NB, int G) {
+    return 1024 + 2 * 32768 + (size_t)2 * NB * 128 + (size_t)G * TILE_PTS * 4 + sizeof(IntShared);
+}
+
+int integrals_tc_group(int NP, int k) {
+    for (int G = std::min(16, std::min(k, 256 / NP)); G >= 1; --G)
+        if (integrals_tc_smem(G * NP, G) <= 227 * 1024) return G;
+    return 0;
+}
+
+void potential_integrals_tc(cudaStream_t st, const GridShape &g, const TileSet<float> &chi,
+                            const TileSet<float> &phi, const unsigned short *chi_fm16, int nslots, int NPmax,
+                            int nchi, int nphi, const float *V, int k, float *out, unsigned *scratch_bits,
+                            float *scale, int *err) {
+    if (k <= 0) return;
+    ProfScope ps(st, ST_INTEGRALS, 2.0 * k * g.pair_points,
+                 2.0 * g.table_values + 4.0 * k * g.n * g.n * g.n + 4.0 * k * nchi * nphi);
+    check(cudaMemsetAsync(out, 0, sizeof(float) * (size_t)k * nchi * nphi, st), "memset(integrals)");
+    check(cudaMemsetAsync(scratch_bits, 0, sizeof(unsigned) * k, st), "memset vmaxabs");
+    const long long n3 = (long long)g.n * g.n * g.n;
+    vmaxabs_kernel<<<dim3(64, k), 256, 0, st>>>(V, n3, scratch_bits);
+    check_launch("vmaxabs_kernel");
+    scale_kernel<<<1, 32, 0, st>>>(scratch_bits, k, scale);
+    check_launch("scale_kernel");
+    CUtensorMap mx;
+    if (!encode_map_2d(&mx, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, chi_fm16, (unsigned long long)TILE_PTS,
+                       (unsigned long long)nslots, (unsigned long long)TILE_PTS * 2, 64, 128))
+        throw CudaError{cudaErrorInvalidValue, "cuTensorMapEncodeTiled (integrals)"};
+    const int G = integrals_tc_group(NPmax, k);
+    if (G < 1) throw CudaError{cudaErrorInvalidValue, "integrals_tc: tile too large for shared memory"};
+    const int ngroups = (k + G - 1) / G;
+    const size_t sm = integrals_tc_smem(G * NPmax, G);
+    static bool attr = false;
+    if (!attr) {
+        check(cudaFuncSetAttribute(integrals_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),
+              "attr integrals_tc");
+        attr = true;
+    }
+    dim3 grid(ngroups, chi.ntiles);
+    const bool vec_ok = (nphi % 4 == 0) && ((reinterpret_cast<unsigned long long>(out) & 15ull) == 0);
+    integrals_tc_kernel<<<grid, 192, sm, st>>>(mx, g.n, g.nt, NPmax, G, k, chi.off, chi.ids, phi.off, phi.ids,
+                                               phi.val, nchi, nphi, V, scale, (float)g.dV, out, vec_ok, err);
+    check_launch("integrals_tc_kernel");
+}
+
+}  // namespace tddft

@@ -5,6 +5,7 @@
 #include "solver_kernels.h"
 
 #include <cmath>
+#include <cstdlib>
 
 namespace tddft {
 
@@ -547,7 +548,7 @@ __global__ void eval_finish_kernel(int k, const double *Q, const double *d, doub
         if (!isfinite(r2)) bad = true;
     }
     if (bad) {
-        *status = DEV_NAN;
+        *status = DEV_NAN_EVAL;
         for (int i = 0; i < k; ++i) out[i] = NAN;
         return;
     }
@@ -584,10 +585,10 @@ __global__ void conj_kernel(int k2, const double *gz_d, const double *gzp_d, con
 //  PP = gram(cov P, P), PD = gram(cov P, D), DP = gram(cov D, P), DD = gram(cov D, D)
 // Outputs: lam[0]; Cp, Cq [k][k] combination coefficients (sign flips folded into Cq);
 // flip_any -> sc_flip[0]; status.
-__global__ void line_gs_kernel(int k, const double *A, const double *BDf, const double *CDfD,
-                               const double *PP, const double *PD, const double *DP,
-                               const double *DD, const double *Q, double *lam, double *Cp,
-                               double *Cq, double *sc_flip, int *status) {
+__global__ void line_gs_warp_kernel(int k, const double *A, const double *BDf, const double *CDfD,
+                                    const double *PP, const double *PD, const double *DP,
+                                    const double *DD, const double *Q, double *lam, double *Cp,
+                                    double *Cq, double *sc_flip, int *status) {
     __shared__ WarpLine s;
     __shared__ double T0[KMAX * KMAX], T1[KMAX * KMAX], T2[KMAX * KMAX], Mg[KMAX * KMAX];
     __shared__ double lam_s;
@@ -623,7 +624,7 @@ __global__ void line_gs_kernel(int k, const double *A, const double *BDf, const 
     }
     __syncwarp();
     if (bad_s) {
-        if (lane == 0) *status = DEV_NAN;
+        if (lane == 0) *status = DEV_NAN_LINE;
         return;
     }
     const double l = warp_line_step(k, s, lane);
@@ -664,6 +665,77 @@ __global__ void line_gs_kernel(int k, const double *A, const double *BDf, const 
     }
 }
 
+
+// single-thread version of the line step and re-orthonormalisation
+__global__ void line_gs_kernel(int k, const double *A, const double *BDf, const double *CDfD,
+                               const double *PP, const double *PD, const double *DP,
+                               const double *DD, const double *Q, double *lam, double *Cp,
+                               double *Cq, double *sc_flip, int *status) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int k2 = 2 * k;
+    LineBlocks lb;
+    Scratch s;
+    double T0[KMAX * KMAX], T1[KMAX * KMAX], T2[KMAX * KMAX];
+    for (int i = 0; i < k; ++i)
+        for (int j = 0; j < k; ++j) {
+            const int e = i * k + j;
+            const double n0ij = A[i * k2 + j] + A[(k + i) * k2 + k + j];
+            const double n0ji = A[j * k2 + i] + A[(k + j) * k2 + k + i];
+            lb.N0[e] = 0.5 * (n0ij + n0ji);
+            const double efij = BDf[i * k2 + j] + BDf[(k + i) * k2 + k + j];
+            const double efji = BDf[j * k2 + i] + BDf[(k + j) * k2 + k + i];
+            lb.N1[e] = efij + efji;
+            const double n2ij = CDfD[i * k2 + j] + CDfD[(k + i) * k2 + k + j];
+            const double n2ji = CDfD[j * k2 + i] + CDfD[(k + j) * k2 + k + i];
+            lb.N2[e] = 0.5 * (n2ij + n2ji);
+            T0[e] = PP[i * k2 + k + j];
+            T1[e] = PD[i * k2 + k + j] + DP[i * k2 + k + j];
+            T2[e] = DD[i * k2 + k + j];
+        }
+    for (int i = 0; i < k; ++i)
+        for (int j = 0; j < k; ++j) {
+            const int e = i * k + j;
+            lb.M0[e] = 0.5 * (T0[e] + T0[j * k + i]);
+            lb.M1[e] = 0.5 * (T1[e] + T1[j * k + i]);
+            lb.M2[e] = 0.5 * (T2[e] + T2[j * k + i]);
+        }
+    for (int e = 0; e < k * k; ++e)
+        if (!isfinite(lb.N0[e]) || !isfinite(lb.N1[e]) || !isfinite(lb.N2[e]) || !isfinite(lb.M1[e]) ||
+            !isfinite(lb.M2[e])) {
+            *status = DEV_NAN_LINE;
+            return;
+        }
+    const double l = line_step(k, lb, s);
+    *lam = l;
+    double Tm[KMAX * KMAX], Mg[KMAX * KMAX], sg[KMAX];
+    for (int i = 0; i < k * k; ++i) Tm[i] = T0[i] + l * T1[i] + l * l * T2[i];
+    int any = 0;
+    for (int i = 0; i < k; ++i) {
+        sg[i] = Tm[i * k + i] < 0.0 ? -1.0 : 1.0;
+        if (sg[i] < 0.0) any = 1;
+    }
+    for (int i = 0; i < k; ++i)
+        for (int j = 0; j < k; ++j) Mg[i * k + j] = 0.5 * (Tm[i * k + j] * sg[j] + Tm[j * k + i] * sg[i]);
+    int order[KMAX];
+    for (int i = 0; i < k; ++i) order[i] = i;
+    for (int i = 1; i < k; ++i) {
+        const int x = order[i];
+        int j = i - 1;
+        while (j >= 0 && Q[order[j] * k + order[j]] > Q[x * k + x]) {
+            order[j + 1] = order[j];
+            --j;
+        }
+        order[j + 1] = x;
+    }
+    if (!gram_schmidt(k, Mg, order, Cp)) {
+        *status = DEV_BREAKDOWN;
+        return;
+    }
+    for (int i = 0; i < k; ++i)
+        for (int j = 0; j < k; ++j) Cq[i * k + j] = Cp[i * k + j] * sg[j];
+    *sc_flip = any ? 1.0 : 0.0;
+}
+
 // initial orthonormalisation: T0 from PP only, identity order
 __global__ void init_gs_kernel(int k, const double *PP, double *Cp, double *Cq, int *status) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -675,7 +747,7 @@ __global__ void init_gs_kernel(int k, const double *PP, double *Cp, double *Cq, 
             const double tij = PP[i * k2 + k + j] * sg[j], tji = PP[j * k2 + k + i] * sg[i];
             Mg[i * k + j] = 0.5 * (tij + tji);
             if (!isfinite(Mg[i * k + j])) {
-                *status = DEV_NAN;
+                *status = DEV_NAN_INIT;
                 return;
             }
         }
@@ -895,7 +967,12 @@ void line_gs(cudaStream_t st, int k, const double *A, const double *BDf, const d
              const double *PP, const double *PD, const double *DP, const double *DD, const double *Q,
              double *lam, double *Cp, double *Cq, double *flip, int *status) {
     ProfScope ps(st, ST_SMALL, 0.0, 0.0);
-    line_gs_kernel<<<1, 32, 0, st>>>(k, A, BDf, CDfD, PP, PD, DP, DD, Q, lam, Cp, Cq, flip, status);
+    static const bool warp = [] {
+        const char *e = std::getenv("TDDFT_WARP_LINE");
+        return e && e[0] == '1';
+    }();
+    if (warp) line_gs_warp_kernel<<<1, 32, 0, st>>>(k, A, BDf, CDfD, PP, PD, DP, DD, Q, lam, Cp, Cq, flip, status);
+    else line_gs_kernel<<<1, 1, 0, st>>>(k, A, BDf, CDfD, PP, PD, DP, DD, Q, lam, Cp, Cq, flip, status);
     check_launch("line_gs_kernel");
 }
 void init_gs(cudaStream_t st, int k, const double *PP, double *Cp, double *Cq, int *status) {

@@ -117,6 +117,6 @@ void axpy_dev(cudaStream_t st, const double *a, int a_stride, double sgn, T *y, 
 constexpr int KMAX = 16;
 
 // Status word bits written by the small kernels
-enum { DEV_OK = 0, DEV_BREAKDOWN = 1, DEV_NAN = 2 };
+enum { DEV_OK = 0, DEV_BREAKDOWN = 1, DEV_NAN = 2, DEV_NAN_EVAL = 3, DEV_NAN_LINE = 4, DEV_NAN_INIT = 5 };
 
 }  // namespace tddft

@@ -7,11 +7,11 @@ boxes wrap the periodic cell on every axis (20^3), a 9-chi (s, p, d) system, and
   * mixed mode, float32 stages (FFT Poisson + f_xc, potential integrals, matrix products on
     three-term-split TF32 tensor cores): 3e-5 (float32 roundoff 6e-8 times ~500-term tile sums and
     ~1000-term products, with margin);
-  * mixed mode, response density on the tensor cores: float16 operands (unit roundoff 2^-11 =
-    4.9e-4) with float32 accumulation; the rounding errors of the ~10^4 products per point are
-    independent, so the error is ~4.9e-4 times the rms term times sqrt(#terms), i.e. ~4.9e-4 of
-    the density's own scale: 2e-3 of the largest entry. The same bound covers f in the full and
-    TDA modes, whose coupling term is built from that density.
+  * mixed mode, response density and potential integrals on the tensor cores: float16 operands
+    (unit roundoff 2^-11 = 4.9e-4) with float32 accumulation; the rounding errors of the
+    products are independent, so the error is ~4.9e-4 times the rms term times sqrt(#terms),
+    i.e. ~4.9e-4 of the result's own scale: 2e-3 of the largest entry. The same bound covers f in
+    the full and TDA modes, whose coupling term is built from them.
 """
 import numpy as np
 import pytest
@@ -102,7 +102,7 @@ def test_potential_integrals(tddft, name, prec):
     V = np.random.default_rng(3).standard_normal((2, s.n, s.n, s.n))
     got = ctx.potential_integrals(V)
     ref = ogrid.potential_integrals(ogrid.BoxedSet(s.chi, s.n), ogrid.BoxedSet(s.phi, s.n), V, s.dV)
-    assert _err(got, ref) < TOL[prec]
+    assert _err(got, ref) < TOL_DENSITY[prec]
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
