@@ -80,7 +80,7 @@ struct Impl {
     // tensor-core grid path (float32 contexts): point-major f16 chi tables [tile][512][CK]
     unsigned short *chi_pm = nullptr;
     unsigned short *chi_fm16 = nullptr;   // function-major f16 chi tables [slot][512]
-    int CK = 0, NPmax = 0, nslots_chi = 0;
+    int CK = 0, NPmax = 0, nslots_chi = 0, maxc = 0;
     bool grid_tc = false, integrals_tc = false;
     unsigned *tc_bits = nullptr;
     float *tc_scale = nullptr;
@@ -125,10 +125,10 @@ int tc_error_read_and_clear(cudaStream_t st);
 void build_point_major_f16(const int *off_h, const float *val_h_or_null, const double *vald_h_or_null,
                            int ntiles, int CK, unsigned short *out_h);
 int density_tc_group(int KBmax, int NP, int k);
-int integrals_tc_group(int NP, int k);
+int integrals_tc_group(int NP, int k, int maxc);
 void potential_integrals_tc(cudaStream_t st, const GridShape &g, const TileSet<float> &chi,
                             const TileSet<float> &phi, const unsigned short *chi_fm16, int nslots, int NPmax,
-                            int nchi, int nphi, const float *V, int k, float *out, unsigned *scratch_bits,
+                            int maxc, int nchi, int nphi, const float *V, int k, float *out, unsigned *scratch_bits,
                             float *scale, int *err);
 void response_density_tc(cudaStream_t st, const GridShape &g, const TileSet<float> &chi,
                          const TileSet<float> &phi, const unsigned short *chi_pm, int CK, int NPmax, int nphi,
@@ -363,8 +363,8 @@ template <typename T>
 void integrals(tddft_ctx *c, Impl<T> &I, int ns) {
     if constexpr (sizeof(T) == 4) {
         if (I.integrals_tc) {
-            potential_integrals_tc(c->st, c->grid(), I.chi, I.phi, I.chi_fm16, I.nslots_chi, I.NPmax, c->nc, c->nv,
-                                   I.V, ns, I.Vmat, I.tc_bits, I.tc_scale, tc_error_word());
+            potential_integrals_tc(c->st, c->grid(), I.chi, I.phi, I.chi_fm16, I.nslots_chi, I.NPmax, I.maxc, c->nc,
+                                   c->nv, I.V, ns, I.Vmat, I.tc_bits, I.tc_scale, tc_error_word());
             return;
         }
     }
@@ -437,7 +437,8 @@ void build_impl(tddft_ctx *c, const tddft_system *s) {
                 I->CK = CK;
                 I->NPmax = NP;
                 I->grid_tc = true;
-                if (maxc <= 256 && integrals_tc_group(NP, 1) >= 1) {
+                I->maxc = maxc;
+                if (integrals_tc_group(NP, 1, maxc) >= 1) {
                     std::vector<unsigned short> fm(cval.size());
 #pragma omp parallel for schedule(static)
                     for (long long i = 0; i < (long long)cval.size(); ++i)

@@ -25,15 +25,22 @@ using namespace tc;
 namespace {
 
 struct __align__(8) DensShared {
-    unsigned long long a_full;
-    unsigned long long mma_done;
+    unsigned long long a_full[4];
+    unsigned long long a_empty[4];
+    unsigned long long acc_full[2];
+    unsigned long long acc_empty[2];
+    unsigned long long b_ready;
     unsigned int tmem_base;
     int abort;
 };
 
-constexpr int DENS_TMEM_COLS = 256;
+constexpr int DENS_THREADS = 256;      // warps 0-3 gather + epilogue, 4 TMA, 5 MMA, 6-7 gather
+constexpr int DENS_GATHER = 192;       // gathering threads: warps 0-3 and 6-7
+constexpr int DENS_STAGES = 4;         // chi-block ring (16 KB each)
 
-__global__ void __launch_bounds__(192, 1) density_tc_kernel(
+__device__ __forceinline__ int gather_rank(int warp, int lane) { return (warp < 4 ? warp : warp - 2) * 32 + lane; }
+
+__global__ void __launch_bounds__(DENS_THREADS, 1) density_tc_kernel(
     const __grid_constant__ CUtensorMap mX,   // point-major chi: [tile*512 + point][CK] f16
     int n, int nt, int KBmax, int NP, int G, int k, const int *__restrict__ coff, const int *__restrict__ cids,
     const int *__restrict__ poff, const int *__restrict__ pids, const float *__restrict__ pval, int nphi,
@@ -60,110 +67,160 @@ __global__ void __launch_bounds__(192, 1) density_tc_kernel(
     }
     const int KB = (nc + 63) / 64;                       // 64-wide K blocks (128 bytes of f16)
     const int NB = G * NP;                               // B rows (multiple of 16, <= 256)
-    unsigned char *A = base;                             // KBmax x [128 rows x 128 B]
-    unsigned char *B = base + (size_t)KBmax * 16384;     // KBmax x [NB rows x 128 B]
+    unsigned char *A = base;                             // ring of DENS_STAGES x [128 rows x 128 B]
+    unsigned char *B = base + DENS_STAGES * 16384;       // KBmax x [NB rows x 128 B]
     DensShared *ctl = reinterpret_cast<DensShared *>(B + (size_t)KBmax * NB * 128);
     volatile int *abort = &ctl->abort;
 
     if (threadIdx.x == 0) {
-        mbar_init(&ctl->a_full, 1);
-        mbar_init(&ctl->mma_done, 1);
+        for (int i = 0; i < DENS_STAGES; ++i) {
+            mbar_init(&ctl->a_full[i], 1);
+            mbar_init(&ctl->a_empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&ctl->acc_full[i], 1);
+            mbar_init(&ctl->acc_empty[i], 128);
+        }
+        mbar_init(&ctl->b_ready, DENS_GATHER);
         ctl->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 5) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&ctl->tmem_base)),
-                     "r"(DENS_TMEM_COLS));
+                     "r"(512));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    // gather the P block: row (s, b), K = a, 8 consecutive a per 16-byte chunk
-    {
-        const int chunks = KB * 8;                       // 16-byte chunks per row
-        for (int idx = threadIdx.x; idx < NB * chunks; idx += blockDim.x) {
-            const int row = idx % NB, ch = idx / NB;     // consecutive threads -> consecutive rows (b)
-            const int sl = row / NP, b = row - sl * NP;
-            const int kb = ch >> 3, c8 = ch & 7;
-            unsigned short h[8];
-            const bool live = sl < gs && b < np;
-            const float sc = live ? pscale[s0 + sl] : 0.0f;
-            const float *Ps = P + (long long)(s0 + (live ? sl : 0)) * sP;
-            const int col = live ? pids[p0 + b] : 0;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int a = kb * 64 + c8 * 8 + j;
-                float v = 0.0f;
-                if (live && a < nc) v = Ps[(long long)cids[c0 + a] * nphi + col] * sc;
-                h[j] = __half_as_ushort(__float2half_rn(v));
-            }
-            uint4 q;
-            q.x = h[0] | ((unsigned)h[1] << 16);
-            q.y = h[2] | ((unsigned)h[3] << 16);
-            q.z = h[4] | ((unsigned)h[5] << 16);
-            q.w = h[6] | ((unsigned)h[7] << 16);
-            *reinterpret_cast<uint4 *>(B + (size_t)kb * NB * 128 + sw128_offset(row, c8)) = q;
-        }
-    }
-    fence_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const unsigned tmem = ctl->tmem_base;
-    const unsigned idesc = idesc_f16(128, NB);
 
-    for (int pb = 0; pb < TILE_PTS / 128; ++pb) {
-        const unsigned par = pb & 1;
-        if (warp == 4 && lane == 0 && !*abort) {
-            mbar_expect_tx(&ctl->a_full, KB * 16384);
-            for (int kb = 0; kb < KB; ++kb)
-                tma_load_2d(A + kb * 16384, &mX, &ctl->a_full, kb * 64, t * TILE_PTS + pb * 128);
-        } else if (warp == 5 && lane == 0) {
-            if (mbar_wait(&ctl->a_full, par, abort)) {
+    if (warp == 4) {
+        // TMA producer: chi blocks (pb, kb) through the ring
+        if (lane == 0) {
+            int i = 0;
+            for (int pb = 0; pb < TILE_PTS / 128 && !*abort; ++pb)
+                for (int kb = 0; kb < KB; ++kb, ++i) {
+                    const int st = i % DENS_STAGES, use = i / DENS_STAGES;
+                    if (use > 0 && !mbar_wait(&ctl->a_empty[st], (use - 1) & 1, abort)) break;
+                    mbar_expect_tx(&ctl->a_full[st], 16384);
+                    tma_load_2d(A + st * 16384, &mX, &ctl->a_full[st], kb * 64, t * TILE_PTS + pb * 128);
+                }
+        }
+    } else if (warp == 5) {
+        // MMA issuer: accumulator pb % 2, one commit per chi block (frees the ring slot)
+        if (lane == 0) {
+            const unsigned idesc = idesc_f16(128, NB);
+            bool ok = mbar_wait(&ctl->b_ready, 0, abort);
+            int i = 0;
+            for (int pb = 0; pb < TILE_PTS / 128 && ok; ++pb) {
+                const int acc = pb & 1, use = pb >> 1;
+                if (use > 0 && !mbar_wait(&ctl->acc_empty[acc], (use - 1) & 1, abort)) break;
                 tc_fence_after();
-                for (int kb = 0; kb < KB; ++kb) {
-                    const unsigned a = smem_u32(A + kb * 16384), bb = smem_u32(B + (size_t)kb * NB * 128);
+                for (int kb = 0; kb < KB; ++kb, ++i) {
+                    const int st = i % DENS_STAGES, u = i / DENS_STAGES;
+                    if (!mbar_wait(&ctl->a_full[st], u & 1, abort)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const unsigned a = smem_u32(A + st * 16384), bb = smem_u32(B + (size_t)kb * NB * 128);
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk)
-                        mma_f16(tmem, smem_desc(a + kk * 32), smem_desc(bb + kk * 32), idesc,
+                        mma_f16(tmem + acc * 256, smem_desc(a + kk * 32), smem_desc(bb + kk * 32), idesc,
                                 (kb > 0 || kk > 0) ? 1u : 0u);
+                    mma_commit(&ctl->a_empty[st]);
+                }
+                mma_commit(&ctl->acc_full[acc]);
+            }
+        }
+    }
+    if (warp < 4 || warp >= 6) {
+        // gather the P block: row (s, b), K = a, 8 consecutive a per 16-byte chunk; four items in
+        // flight per thread (32 independent loads)
+        const int rank = gather_rank(warp, lane);
+        const int chunks = KB * 8;
+        const int total = NB * chunks;
+        for (int i0 = rank; i0 < total; i0 += 4 * DENS_GATHER) {
+            float v[4][8];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int idx = i0 + u * DENS_GATHER;
+                const int row = idx % NB, ch = idx / NB;
+                const int sl = row / NP, b = row - sl * NP;
+                const bool live = idx < total && sl < gs && b < np;
+                const float *Ps = P + (long long)(s0 + (live ? sl : 0)) * sP + (live ? pids[p0 + b] : 0);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int a = (ch >> 3) * 64 + (ch & 7) * 8 + j;
+                    v[u][j] = (live && a < nc) ? Ps[(long long)cids[c0 + a] * nphi] : 0.0f;
                 }
             }
-            mma_commit(&ctl->mma_done);
-        } else if (warp < 4) {
-            const bool ok = mbar_wait(&ctl->mma_done, par, abort) && !*abort;
-            tc_fence_after();
-            const int lp = pb * 128 + warp * 32 + lane;      // tile point of this TMEM lane
-            float acc[16];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) acc[i] = 0.0f;
+            for (int u = 0; u < 4; ++u) {
+                const int idx = i0 + u * DENS_GATHER;
+                if (idx >= total) continue;
+                const int row = idx % NB, ch = idx / NB;
+                const int sl = row / NP;
+                const float sc = sl < gs ? pscale[s0 + sl] : 0.0f;
+                unsigned short h[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) h[j] = __half_as_ushort(__float2half_rn(v[u][j] * sc));
+                uint4 q;
+                q.x = h[0] | ((unsigned)h[1] << 16);
+                q.y = h[2] | ((unsigned)h[3] << 16);
+                q.z = h[4] | ((unsigned)h[5] << 16);
+                q.w = h[6] | ((unsigned)h[7] << 16);
+                *reinterpret_cast<uint4 *>(B + (size_t)(ch >> 3) * NB * 128 + sw128_offset(row, ch & 7)) = q;
+            }
+        }
+        fence_async_smem();
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ctl->b_ready)) : "memory");
+    }
+    if (warp < 4) {
+        // epilogue: rho_s(r) = sum_b T[r][(s,b)] phi_b(r) for the 128 points of block pb
+        for (int pb = 0; pb < TILE_PTS / 128; ++pb) {
+            const int acc = pb & 1;
+            const bool ok = mbar_wait(&ctl->acc_full[acc], (pb >> 1) & 1, abort) && !*abort;
+            tc_fence_after();
+            const int lp = pb * 128 + warp * 32 + lane;
+            float r[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) r[q] = 0.0f;
             for (int c = 0; c < NB; c += 32) {
                 float v[32];
-                tmem_ld32(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c, v);
+                tmem_ld32(tmem + acc * 256 + ((unsigned)(warp * 32) << 16) + (unsigned)c, v);
+                float ph[32];
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
-                    const int col = c + j;
-                    const int sl = col / NP, b = col - sl * NP;
-                    if (sl < gs && b < np) {
-                        const float w = v[j] * pval[(long long)(p0 + b) * TILE_PTS + lp];
+                    const int col = c + j, sl = col / NP, b = col - sl * NP;
+                    ph[j] = (sl < gs && b < np) ? pval[(long long)(p0 + b) * TILE_PTS + lp] : 0.0f;
+                }
 #pragma unroll
-                        for (int q = 0; q < 16; ++q)
-                            if (q == sl) acc[q] += w;
-                    }
+                for (int j = 0; j < 32; ++j) {
+                    const int sl = (c + j) / NP;
+                    const float w = v[j] * ph[j];
+#pragma unroll
+                    for (int q = 0; q < 16; ++q)
+                        if (q == sl) r[q] += w;
                 }
             }
+            tc_fence_before();
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ctl->acc_empty[acc])) : "memory");
             const int gx = tx * TILE + (lp >> 6), gy = ty * TILE + ((lp >> 3) & 7), gz = tz * TILE + (lp & 7);
             if (ok && gx < n && gy < n && gz < n) {
                 const long long gi = ((long long)gx * n + gy) * n + gz;
 #pragma unroll
                 for (int q = 0; q < 16; ++q)
-                    if (q < gs) rho[(long long)(s0 + q) * n3 + gi] = acc[q] / pscale[s0 + q];
+                    if (q < gs) rho[(long long)(s0 + q) * n3 + gi] = r[q] / pscale[s0 + q];
             }
         }
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
     }
+    tc_fence_before();
+    __syncthreads();
     if (warp == 5) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(DENS_TMEM_COLS));
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
     }
     if (threadIdx.x == 0 && ctl->abort) atomicExch(err, 1);
 }
@@ -208,7 +265,7 @@ bool encode_map_2d(CUtensorMap *map, CUtensorMapDataType dt, const void *ptr, un
                    unsigned long long rows, unsigned long long row_bytes, unsigned box_inner, unsigned box_rows);
 
 size_t density_tc_smem(int KBmax, int NB) {
-    return 1024 + (size_t)KBmax * 16384 + (size_t)KBmax * NB * 128 + sizeof(DensShared);
+    return 1024 + (size_t)DENS_STAGES * 16384 + (size_t)KBmax * NB * 128 + sizeof(DensShared);
 }
 
 // largest state group G (<= 16, G * NP <= 256) whose shared memory fits; 0 if none does
@@ -245,8 +302,8 @@ void response_density_tc(cudaStream_t st, const GridShape &g, const TileSet<floa
         attr = true;
     }
     dim3 grid(ngroups, chi.ntiles);
-    density_tc_kernel<<<grid, 192, sm, st>>>(mx, g.n, g.nt, KBmax, NP, G, k, chi.off, chi.ids, phi.off, phi.ids,
-                                             phi.val, nphi, P, sP, scale, rho, err);
+    density_tc_kernel<<<grid, DENS_THREADS, sm, st>>>(mx, g.n, g.nt, KBmax, NP, G, k, chi.off, chi.ids, phi.off,
+                                                      phi.ids, phi.val, nphi, P, sP, scale, rho, err);
     check_launch("density_tc_kernel");
 }
 
@@ -286,7 +343,7 @@ __global__ void __launch_bounds__(192, 1) integrals_tc_kernel(
     int n, int nt, int NP, int G, int k, const int *__restrict__ coff, const int *__restrict__ cids,
     const int *__restrict__ poff, const int *__restrict__ pids, const float *__restrict__ pval, int nchi,
     int nphi, const float *__restrict__ V, const float *__restrict__ vscale, float dV, float *__restrict__ out,
-    bool vec_ok, int *err) {
+    bool vec_ok, int acc_stride, int *err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<unsigned long long>(smem_raw) + 1023ull) & ~1023ull);
@@ -297,11 +354,11 @@ __global__ void __launch_bounds__(192, 1) integrals_tc_kernel(
     const int p0 = poff[t], np = poff[t + 1] - p0;
     if (nc == 0 || np == 0) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int MB = (nc + 127) / 128;                 // 1 or 2 (host guarantees nc <= 256)
-    const int NB = G * NP;                           // <= 256, multiple of 16
-    // layout: X stages [2][2 x 16 KB], W stages [2][NB x 128 B], V tile [G][512] f32, control
+    const int MB = (nc + 127) / 128;                 // <= 3 (host guarantees nc <= 384)
+    const int NB = G * NP;                           // <= acc_stride, multiple of 16
+    // layout: X stages [2][3 x 16 KB], W stages [2][NB x 128 B], V tile [G][512] f32, control
     unsigned char *Xs = base;
-    unsigned char *Ws = base + 2 * 32768;
+    unsigned char *Ws = base + 2 * 49152;
     float *Vt = reinterpret_cast<float *>(Ws + (size_t)2 * NB * 128);
     IntShared *ctl = reinterpret_cast<IntShared *>(Vt + (size_t)G * TILE_PTS);
     volatile int *abort = &ctl->abort;
@@ -345,7 +402,7 @@ __global__ void __launch_bounds__(192, 1) integrals_tc_kernel(
                 if (use > 0 && !mbar_wait(&ctl->mma_done[st], (use - 1) & 1, abort)) break;
                 mbar_expect_tx(&ctl->x_full[st], MB * 16384);
                 for (int mb = 0; mb < MB; ++mb)
-                    tma_load_2d(Xs + st * 32768 + mb * 16384, &mX, &ctl->x_full[st], kb * 64, c0 + mb * 128);
+                    tma_load_2d(Xs + st * 49152 + mb * 16384, &mX, &ctl->x_full[st], kb * 64, c0 + mb * 128);
             }
         }
     } else if (warp == 5) {
@@ -357,10 +414,10 @@ __global__ void __launch_bounds__(192, 1) integrals_tc_kernel(
                 tc_fence_after();
                 const unsigned wb = smem_u32(Ws + (size_t)st * NB * 128);
                 for (int mb = 0; mb < MB; ++mb) {
-                    const unsigned xa = smem_u32(Xs + st * 32768 + mb * 16384);
+                    const unsigned xa = smem_u32(Xs + st * 49152 + mb * 16384);
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk)
-                        mma_f16(tmem + mb * 256, smem_desc(xa + kk * 32), smem_desc(wb + kk * 32), idesc,
+                        mma_f16(tmem + mb * acc_stride, smem_desc(xa + kk * 32), smem_desc(wb + kk * 32), idesc,
                                 (kb > 0 || kk > 0) ? 1u : 0u);
                 }
                 mma_commit(&ctl->mma_done[st]);
@@ -404,7 +461,7 @@ __global__ void __launch_bounds__(192, 1) integrals_tc_kernel(
             const long long rowoff = arow ? (long long)cids[c0 + a] * nphi : 0;
             for (int c = 0; c < NB; c += 32) {
                 float v[32];
-                tmem_ld32(tmem + mb * 256 + ((unsigned)(warp * 32) << 16) + (unsigned)c, v);
+                tmem_ld32(tmem + mb * acc_stride + ((unsigned)(warp * 32) << 16) + (unsigned)c, v);
                 if (!arow) continue;
 #pragma unroll
                 for (int j = 0; j < 32; j += 4) {
@@ -450,18 +507,23 @@ __global__ void vmaxabs_kernel(const float *__restrict__ V, long long n3, unsign
 }  // namespace
 
 size_t integrals_tc_smem(int NB, int G) {
-    return 1024 + 2 * 32768 + (size_t)2 * NB * 128 + (size_t)G * TILE_PTS * 4 + sizeof(IntShared);
+    return 1024 + 2 * 49152 + (size_t)2 * NB * 128 + (size_t)G * TILE_PTS * 4 + sizeof(IntShared);
 }
 
-int integrals_tc_group(int NP, int k) {
-    for (int G = std::min(16, std::min(k, 256 / NP)); G >= 1; --G)
+// accumulator stride in TMEM columns: 256 when every tile has <= 256 chi (2 M blocks), else 128
+int integrals_tc_stride(int maxc) { return maxc <= 256 ? 256 : 128; }
+
+int integrals_tc_group(int NP, int k, int maxc) {
+    if (maxc > 384) return 0;
+    const int stride = integrals_tc_stride(maxc);
+    for (int G = std::min(16, std::min(k, stride / NP)); G >= 1; --G)
         if (integrals_tc_smem(G * NP, G) <= 227 * 1024) return G;
     return 0;
 }
 
 void potential_integrals_tc(cudaStream_t st, const GridShape &g, const TileSet<float> &chi,
                             const TileSet<float> &phi, const unsigned short *chi_fm16, int nslots, int NPmax,
-                            int nchi, int nphi, const float *V, int k, float *out, unsigned *scratch_bits,
+                            int maxc, int nchi, int nphi, const float *V, int k, float *out, unsigned *scratch_bits,
                             float *scale, int *err) {
     if (k <= 0) return;
     ProfScope ps(st, ST_INTEGRALS, 2.0 * k * g.pair_points,
@@ -477,8 +539,9 @@ void potential_integrals_tc(cudaStream_t st, const GridShape &g, const TileSet<f
     if (!encode_map_2d(&mx, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, chi_fm16, (unsigned long long)TILE_PTS,
                        (unsigned long long)nslots, (unsigned long long)TILE_PTS * 2, 64, 128))
         throw CudaError{cudaErrorInvalidValue, "cuTensorMapEncodeTiled (integrals)"};
-    const int G = integrals_tc_group(NPmax, k);
+    const int G = integrals_tc_group(NPmax, k, maxc);
     if (G < 1) throw CudaError{cudaErrorInvalidValue, "integrals_tc: tile too large for shared memory"};
+    const int stride = integrals_tc_stride(maxc);
     const int ngroups = (k + G - 1) / G;
     const size_t sm = integrals_tc_smem(G * NPmax, G);
     static bool attr = false;
@@ -490,7 +553,7 @@ void potential_integrals_tc(cudaStream_t st, const GridShape &g, const TileSet<f
     dim3 grid(ngroups, chi.ntiles);
     const bool vec_ok = (nphi % 4 == 0) && ((reinterpret_cast<unsigned long long>(out) & 15ull) == 0);
     integrals_tc_kernel<<<grid, 192, sm, st>>>(mx, g.n, g.nt, NPmax, G, k, chi.off, chi.ids, phi.off, phi.ids,
-                                               phi.val, nchi, nphi, V, scale, (float)g.dV, out, vec_ok, err);
+                                               phi.val, nchi, nphi, V, scale, (float)g.dV, out, vec_ok, stride, err);
     check_launch("integrals_tc_kernel");
 }
 
