@@ -280,6 +280,23 @@ def run_ours(args):
     stages = {n: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / max(ms, 1e-9), 4)}
               for n, v in prof.items() if v[0]}
 
+    # time to k states with plain PCG on the small-8 workload (lowest state, FP64, 1e-6 Ha)
+    time_to_k = None
+    if rank == 0:
+        s8 = sy.generate(sy.CONFIG_SMALL)
+        c8 = tddft.Context(s8, precision="fp64", tol=1e-6, max_iter=500, stream=stream.cuda_stream)
+        st8 = c8.state(sy.initial_guess(s8, 1, 0))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        om8, res8, it8, rc8 = st8.solve()
+        torch.cuda.synchronize()
+        time_to_k = {"workload": "small-8: 8 atoms, 16 A cell, 48^3 grid, 4 phi + 4 chi per atom, no truncation",
+                     "k": 1, "precision": "fp64", "tol_Ha": 1e-6, "plain_pcg_s": time.perf_counter() - t0,
+                     "iterations": it8, "omega_Ha": float(om8[0]), "status": int(rc8),
+                     "learned_pcg_s": None}
+        st8.close()
+        c8.close()
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -292,6 +309,7 @@ def run_ours(args):
                 "e2e": e2e, "apply_only": {"value": apply_only, "unit": UNIT},
                 "roofline": roof, "stages": stages, "gpu_launches": int(gpu_launches),
                 "clocks": {k_: clock[k_] for k_ in ("sm_mhz", "sm_max_mhz", "reasons")},
+                "time_to_k": time_to_k,
                 "omega_last": [float(x) for x in om], "resid_last": [float(x) for x in res]}
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_oracle_sample(s)

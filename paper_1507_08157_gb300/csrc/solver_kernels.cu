@@ -4,6 +4,7 @@
 // of Eq. ortho, subspace eigenvalues.
 #include "solver_kernels.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 
@@ -95,6 +96,98 @@ void gram_impl(cudaStream_t st, const T *X, long long sx, int nx, const T *Y, lo
     check_launch("gram_partial");
     gram_final<<<(pairs + 255) / 256, 256, 0, st>>>(scratch, nb, pairs, G);
     check_launch("gram_final");
+}
+
+// ------------------------------------------------------------------------------------------------
+// Register-tiled trace products. Block (x, y): element slice x, pair tile y of 8 x 8 (i, j);
+// each thread accumulates its 64 products over a strided run of elements (float32 products
+// summed in T per run of at most RUN elements, then in float64), the block reduces in float64
+// in a fixed order and writes one partial per pair; gram_final sums the partials over slices.
+constexpr int RUN = 32;
+
+template <typename T>
+__global__ void __launch_bounds__(256) gram_tiled(const T *__restrict__ X, long long sx, int nx,
+                                                  const T *__restrict__ Y, long long sy, int ny,
+                                                  long long len, int tiles_j, double *__restrict__ partial,
+                                                  int pairs) {
+    __shared__ double red[8][8][33];
+    const int ti = blockIdx.y / tiles_j, tj = blockIdx.y - ti * tiles_j;
+    const int i0 = ti * 8, j0 = tj * 8;
+    double acc[8][8];
+    T run[8][8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) acc[a][b] = 0.0, run[a][b] = T(0);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    int cnt = 0;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len; e += stride) {
+        T xv[8], yv[8];
+#pragma unroll
+        for (int a = 0; a < 8; ++a) xv[a] = (i0 + a < nx) ? X[(i0 + a) * sx + e] : T(0);
+#pragma unroll
+        for (int b = 0; b < 8; ++b) yv[b] = (j0 + b < ny) ? Y[(j0 + b) * sy + e] : T(0);
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+            for (int b = 0; b < 8; ++b) run[a][b] = fma(xv[a], yv[b], run[a][b]);
+        if (++cnt == RUN) {
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+                for (int b = 0; b < 8; ++b) acc[a][b] += (double)run[a][b], run[a][b] = T(0);
+            cnt = 0;
+        }
+    }
+    // warp reduction (fixed butterfly order), then across the 8 warps through shared memory
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            double v = acc[a][b] + (double)run[a][b];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) red[a][b][warp] = v;
+        }
+    __syncthreads();
+    if (threadIdx.x < 64) {
+        const int a = threadIdx.x >> 3, b = threadIdx.x & 7;
+        double v = 0.0;
+        for (int w = 0; w < 8; ++w) v += red[a][b][w];
+        const int i = i0 + a, j = j0 + b;
+        if (i < nx && j < ny) partial[(long long)blockIdx.x * pairs + i * ny + j] = v;
+    }
+}
+
+// d_i = sum_e X_i[e] Y_i[e]: one row per blockIdx.y, float32 runs of RUN then float64
+template <typename T>
+__global__ void __launch_bounds__(256) dots_kernel(const T *__restrict__ X, long long sx, const T *__restrict__ Y,
+                                                   long long sy, long long len, int n, double *__restrict__ partial) {
+    __shared__ double red[8];
+    const int i = blockIdx.y;
+    const T *x = X + i * sx;
+    const T *y = Y + i * sy;
+    double acc = 0.0;
+    T run = T(0);
+    int cnt = 0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len; e += stride) {
+        run = fma(x[e], y[e], run);
+        if (++cnt == RUN) {
+            acc += (double)run;
+            run = T(0);
+            cnt = 0;
+        }
+    }
+    acc += (double)run;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double v = 0.0;
+        for (int w = 0; w < 8; ++w) v += red[w];
+        partial[(long long)blockIdx.x * n + i] = v;
+    }
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -294,150 +387,6 @@ __device__ double line_step(int k, const LineBlocks &lb, Scratch &s) {
     return 0.5 * (lo + hi);
 }
 
-// ---- warp-cooperative versions (32 lanes, k <= KMAX, matrices in shared memory) ----------------
-struct WarpLine {
-    double N0[KMAX * KMAX], N1[KMAX * KMAX], N2[KMAX * KMAX];
-    double M0[KMAX * KMAX], M1[KMAX * KMAX], M2[KMAX * KMAX];
-    double M[KMAX * KMAX], N[KMAX * KMAX], dM[KMAX * KMAX], dN[KMAX * KMAX];
-    double W[KMAX * KMAX], X[KMAX * KMAX], Z[KMAX * KMAX], T[KMAX * KMAX], L[KMAX * KMAX];
-    int bad;
-};
-
-// X = M^-1 B via Cholesky (L in s.L); false if M is not positive definite. All lanes return
-// the same value.
-__device__ bool warp_chol_factor(int k, const double *M, double *L, int *bad, int lane) {
-    if (lane == 0) *bad = 0;
-    __syncwarp();
-    for (int j = 0; j < k; ++j) {
-        if (lane == 0) {
-            double s = M[j * k + j];
-            for (int p = 0; p < j; ++p) s -= L[j * k + p] * L[j * k + p];
-            if (!(s > 0.0)) *bad = 1;
-            L[j * k + j] = s > 0.0 ? sqrt(s) : 1.0;
-        }
-        __syncwarp();
-        const double d = L[j * k + j];
-        for (int i = j + 1 + lane; i < k; i += 32) {
-            double s = M[i * k + j];
-            for (int p = 0; p < j; ++p) s -= L[i * k + p] * L[j * k + p];
-            L[i * k + j] = s / d;
-        }
-        __syncwarp();
-    }
-    return *bad == 0;
-}
-
-__device__ void warp_chol_solve(int k, const double *L, const double *B, double *X, int lane) {
-    for (int c = lane; c < k; c += 32) {   // one right-hand-side column per lane
-        for (int i = 0; i < k; ++i) {
-            double s = B[i * k + c];
-            for (int p = 0; p < i; ++p) s -= L[i * k + p] * X[p * k + c];
-            X[i * k + c] = s / L[i * k + i];
-        }
-        for (int i = k - 1; i >= 0; --i) {
-            double s = X[i * k + c];
-            for (int p = i + 1; p < k; ++p) s -= L[p * k + i] * X[p * k + c];
-            X[i * k + c] = s / L[i * k + i];
-        }
-    }
-    __syncwarp();
-}
-
-__device__ double warp_sum(double v) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Omega(lam) = Tr[M^-1 N]/2 and its derivative (same arithmetic as sum_functional)
-__device__ bool warp_sum_functional(int k, WarpLine &s, double lam, double *f, double *d, int lane) {
-    const int kk = k * k;
-    for (int i = lane; i < kk; i += 32) {
-        s.M[i] = s.M0[i] + lam * s.M1[i] + lam * lam * s.M2[i];
-        s.N[i] = s.N0[i] + lam * s.N1[i] + lam * lam * s.N2[i];
-        s.dM[i] = s.M1[i] + 2.0 * lam * s.M2[i];
-        s.dN[i] = s.N1[i] + 2.0 * lam * s.N2[i];
-    }
-    __syncwarp();
-    if (!warp_chol_factor(k, s.M, s.L, &s.bad, lane)) return false;
-    warp_chol_solve(k, s.L, s.N, s.W, lane);
-    warp_chol_solve(k, s.L, s.dN, s.X, lane);
-    for (int e = lane; e < kk; e += 32) {
-        const int i = e / k, j = e - i * k;
-        double acc = 0.0;
-        for (int p = 0; p < k; ++p) acc += s.dM[i * k + p] * s.W[p * k + j];
-        s.T[e] = acc;
-    }
-    __syncwarp();
-    warp_chol_solve(k, s.L, s.T, s.Z, lane);
-    double tw = 0.0, tx = 0.0, tz = 0.0;
-    for (int i = lane; i < k; i += 32) {
-        tw += s.W[i * k + i];
-        tx += s.X[i * k + i];
-        tz += s.Z[i * k + i];
-    }
-    tw = warp_sum(tw);
-    tx = warp_sum(tx);
-    tz = warp_sum(tz);
-    *f = 0.5 * tw;
-    *d = 0.5 * (tx - tz);
-    return true;
-}
-
-// same procedure as line_step: bracket by doubling a Newton estimate, Illinois regula falsi
-__device__ double warp_line_step(int k, WarpLine &s, int lane) {
-    double f0, d0;
-    if (!warp_sum_functional(k, s, 0.0, &f0, &d0, lane) || !isfinite(d0) || d0 >= 0.0) return 0.0;
-    double h0 = 0.0;
-    for (int i = lane; i < k; i += 32) {
-        double t = 2.0 * s.N2[i * k + i];
-        for (int p = 0; p < k; ++p) {
-            t -= 2.0 * s.M1[i * k + p] * s.N1[p * k + i];
-            t -= 2.0 * s.M2[i * k + p] * s.N0[p * k + i];
-            double m1m1 = 0.0;
-            for (int q = 0; q < k; ++q) m1m1 += s.M1[i * k + q] * s.M1[q * k + p];
-            t += 2.0 * m1m1 * s.N0[p * k + i];
-        }
-        h0 += 0.5 * t;
-    }
-    h0 = warp_sum(h0);
-    double hi = (h0 > 0.0 && isfinite(h0)) ? -d0 / h0 : 1.0;
-    double lo = 0.0, dlo = d0, f, d = d0;
-    for (int it = 0; it < 60; ++it) {
-        if (!warp_sum_functional(k, s, hi, &f, &d, lane)) d = INFINITY;
-        if (d >= 0.0) break;
-        lo = hi;
-        dlo = d;
-        hi = 2.0 * hi;
-    }
-    double dhi = d;
-    for (int b = 0; b < 200 && !isfinite(dhi); ++b) {
-        const double mid = 0.5 * (lo + hi);
-        if (!warp_sum_functional(k, s, mid, &f, &d, lane)) d = INFINITY;
-        if (d < 0.0) { lo = mid; dlo = d; }
-        else { hi = mid; dhi = d; }
-    }
-    int side = 0;
-    for (int r = 0; r < 100; ++r) {
-        if (!(hi - lo > 4e-16 * hi)) break;
-        double x = (isfinite(dhi) && dhi != dlo) ? hi - dhi * (hi - lo) / (dhi - dlo) : 0.5 * (lo + hi);
-        if (!(x > lo && x < hi)) x = 0.5 * (lo + hi);
-        if (!warp_sum_functional(k, s, x, &f, &d, lane)) d = INFINITY;
-        if (d == 0.0) return x;
-        if (d < 0.0) {
-            lo = x;
-            dlo = d;
-            if (side == -1) dhi *= 0.5;
-            side = -1;
-        } else {
-            hi = x;
-            dhi = d;
-            if (side == +1) dlo *= 0.5;
-            side = +1;
-        }
-    }
-    return 0.5 * (lo + hi);
-}
-
 // classical Gram-Schmidt twice on coefficient vectors; rows of C are the new vectors
 __device__ bool gram_schmidt(int k, const double *Mg, const int *order, double *C) {
     for (int i = 0; i < k * k; ++i) C[i] = 0.0;
@@ -585,86 +534,6 @@ __global__ void conj_kernel(int k2, const double *gz_d, const double *gzp_d, con
 //  PP = gram(cov P, P), PD = gram(cov P, D), DP = gram(cov D, P), DD = gram(cov D, D)
 // Outputs: lam[0]; Cp, Cq [k][k] combination coefficients (sign flips folded into Cq);
 // flip_any -> sc_flip[0]; status.
-__global__ void line_gs_warp_kernel(int k, const double *A, const double *BDf, const double *CDfD,
-                                    const double *PP, const double *PD, const double *DP,
-                                    const double *DD, const double *Q, double *lam, double *Cp,
-                                    double *Cq, double *sc_flip, int *status) {
-    __shared__ WarpLine s;
-    __shared__ double T0[KMAX * KMAX], T1[KMAX * KMAX], T2[KMAX * KMAX], Mg[KMAX * KMAX];
-    __shared__ double lam_s;
-    __shared__ int bad_s;
-    const int lane = threadIdx.x;
-    const int k2 = 2 * k;
-    if (lane == 0) bad_s = 0;
-    __syncwarp();
-    for (int e = lane; e < k * k; e += 32) {
-        const int i = e / k, j = e - i * k;
-        const double n0ij = A[i * k2 + j] + A[(k + i) * k2 + k + j];
-        const double n0ji = A[j * k2 + i] + A[(k + j) * k2 + k + i];
-        s.N0[e] = 0.5 * (n0ij + n0ji);
-        const double efij = BDf[i * k2 + j] + BDf[(k + i) * k2 + k + j];
-        const double efji = BDf[j * k2 + i] + BDf[(k + j) * k2 + k + i];
-        s.N1[e] = efij + efji;
-        const double n2ij = CDfD[i * k2 + j] + CDfD[(k + i) * k2 + k + j];
-        const double n2ji = CDfD[j * k2 + i] + CDfD[(k + j) * k2 + k + i];
-        s.N2[e] = 0.5 * (n2ij + n2ji);
-        T0[e] = PP[i * k2 + k + j];                          // <p_i, q_j>
-        T1[e] = PD[i * k2 + k + j] + DP[i * k2 + k + j];     // <p_i, Dq_j> + <Dp_i, q_j>
-        T2[e] = DD[i * k2 + k + j];                          // <Dp_i, Dq_j>
-    }
-    __syncwarp();
-    for (int e = lane; e < k * k; e += 32) {
-        const int i = e / k, j = e - i * k;
-        s.M0[e] = 0.5 * (T0[e] + T0[j * k + i]);
-        s.M1[e] = 0.5 * (T1[e] + T1[j * k + i]);
-        s.M2[e] = 0.5 * (T2[e] + T2[j * k + i]);
-        if (!isfinite(s.N0[e]) || !isfinite(s.N1[e]) || !isfinite(s.N2[e]) || !isfinite(s.M1[e]) ||
-            !isfinite(s.M2[e]))
-            bad_s = 1;
-    }
-    __syncwarp();
-    if (bad_s) {
-        if (lane == 0) *status = DEV_NAN_LINE;
-        return;
-    }
-    const double l = warp_line_step(k, s, lane);
-    if (lane == 0) {
-        lam_s = l;
-        *lam = l;
-        double Tm[KMAX * KMAX];
-        for (int i = 0; i < k * k; ++i) Tm[i] = T0[i] + l * T1[i] + l * l * T2[i];
-        double sg[KMAX];
-        int any = 0;
-        for (int i = 0; i < k; ++i) {
-            sg[i] = Tm[i * k + i] < 0.0 ? -1.0 : 1.0;
-            if (sg[i] < 0.0) any = 1;
-        }
-        for (int i = 0; i < k; ++i)
-            for (int j = 0; j < k; ++j) {
-                const double tij = Tm[i * k + j] * sg[j], tji = Tm[j * k + i] * sg[i];
-                Mg[i * k + j] = 0.5 * (tij + tji);
-            }
-        int order[KMAX];
-        for (int i = 0; i < k; ++i) order[i] = i;
-        for (int i = 1; i < k; ++i) {
-            const int x = order[i];
-            int j = i - 1;
-            while (j >= 0 && Q[order[j] * k + order[j]] > Q[x * k + x]) {
-                order[j + 1] = order[j];
-                --j;
-            }
-            order[j + 1] = x;
-        }
-        if (!gram_schmidt(k, Mg, order, Cp)) {
-            *status = DEV_BREAKDOWN;
-        } else {
-            for (int i = 0; i < k; ++i)
-                for (int j = 0; j < k; ++j) Cq[i * k + j] = Cp[i * k + j] * sg[j];
-            *sc_flip = any ? 1.0 : 0.0;
-        }
-    }
-}
-
 
 // single-thread version of the line step and re-orthonormalisation
 __global__ void line_gs_kernel(int k, const double *A, const double *BDf, const double *CDfD,
@@ -886,18 +755,38 @@ __global__ void subspace_kernel(int k, const double *A, double *omega, double *p
 }  // namespace
 
 // ---- host wrappers ------------------------------------------------------------------------------
-long long gram_scratch_doubles(int nx, int ny) { return (long long)GBLOCKS * nx * ny + 64; }
+
+constexpr int TRACE_SLICES = 152;
+
+long long gram_scratch_doubles(int nx, int ny) { return (long long)2 * TRACE_SLICES * nx * ny + 64; }
 
 template <typename T>
 void gram(cudaStream_t st, const T *X, long long sx, int nx, const T *Y, long long sy, int ny,
           long long len, double *G, double *scratch) {
-    gram_impl<T>(st, X, sx, nx, Y, sy, ny, len, false, G, scratch);
+    const int pairs = nx * ny;
+    if (pairs <= 0) return;
+    if (nx > 64 || ny > 64) throw CudaError{cudaErrorInvalidValue, "gram: too many matrices"};
+    ProfScope ps(st, ST_TRACE, 2.0 * pairs * (double)len, sizeof(T) * (double)(nx + ny) * len);
+    const int ti = (nx + 7) / 8, tj = (ny + 7) / 8;
+    const long long per = (len + 255) / 256;
+    const int slices = (int)std::min<long long>(TRACE_SLICES, std::max<long long>(1, per));
+    gram_tiled<T><<<dim3(slices, ti * tj), 256, 0, st>>>(X, sx, nx, Y, sy, ny, len, tj, scratch, pairs);
+    check_launch("gram_tiled");
+    gram_final<<<(pairs + 255) / 256, 256, 0, st>>>(scratch, slices, pairs, G);
+    check_launch("gram_final");
 }
 
 template <typename T>
 void dots(cudaStream_t st, const T *X, long long sx, const T *Y, long long sy, int n, long long len,
           double *d, double *scratch) {
-    gram_impl<T>(st, X, sx, n, Y, sy, n, len, true, d, scratch);
+    if (n <= 0) return;
+    ProfScope ps(st, ST_TRACE, 2.0 * n * (double)len, sizeof(T) * 2.0 * n * len);
+    const long long per = (len + 255) / 256;
+    const int slices = (int)std::min<long long>(2 * TRACE_SLICES, std::max<long long>(1, per));
+    dots_kernel<T><<<dim3(slices, n), 256, 0, st>>>(X, sx, Y, sy, len, n, scratch);
+    check_launch("dots_kernel");
+    gram_final<<<(n + 255) / 256, 256, 0, st>>>(scratch, slices, n, d);
+    check_launch("gram_final");
 }
 
 template <typename T>
@@ -967,12 +856,7 @@ void line_gs(cudaStream_t st, int k, const double *A, const double *BDf, const d
              const double *PP, const double *PD, const double *DP, const double *DD, const double *Q,
              double *lam, double *Cp, double *Cq, double *flip, int *status) {
     ProfScope ps(st, ST_SMALL, 0.0, 0.0);
-    static const bool warp = [] {
-        const char *e = std::getenv("TDDFT_WARP_LINE");
-        return e && e[0] == '1';
-    }();
-    if (warp) line_gs_warp_kernel<<<1, 32, 0, st>>>(k, A, BDf, CDfD, PP, PD, DP, DD, Q, lam, Cp, Cq, flip, status);
-    else line_gs_kernel<<<1, 1, 0, st>>>(k, A, BDf, CDfD, PP, PD, DP, DD, Q, lam, Cp, Cq, flip, status);
+    line_gs_kernel<<<1, 1, 0, st>>>(k, A, BDf, CDfD, PP, PD, DP, DD, Q, lam, Cp, Cq, flip, status);
     check_launch("line_gs_kernel");
 }
 void init_gs(cudaStream_t st, int k, const double *PP, double *Cp, double *Cq, int *status) {
