@@ -700,9 +700,6 @@ void precondition(tddft_ctx *c, tddft_state *S, const T *h, T *z) {
         return;
     }
     T *r = B.cLpp, *cr = B.cr, *p = B.cp, *cp = B.cpv, *Lp = B.cLp, *cLp = B.cLv;
-    // the preconditioner is an approximate solve: its products may run in plain TF32
-    const char *pf = std::getenv("TDDFT_PRECOND_SPLIT");
-    FastGemmScope fast(!(pf && pf[0] == '1'));
     check(cudaMemsetAsync(z, 0, tot * sizeof(T), st), "memset z");
     check(cudaMemcpyAsync(r, h, tot * sizeof(T), cudaMemcpyDeviceToDevice, st), "copy r");
     covariant<T>(c, I, k2, r, cr, B.tmp);

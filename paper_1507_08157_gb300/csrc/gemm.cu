@@ -15,11 +15,6 @@ void tc_gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, float alpha
              int batch, bool split);
 bool tc_gemm_available();
 
-bool &gemm_fast_mode() {
-    static thread_local bool fast = false;
-    return fast;
-}
-
 bool tc_enabled() {
     static int on = -1;
     if (on < 0) {
@@ -129,7 +124,7 @@ void gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, T alpha, const
     // accuracy); float64 and tiny products stay on the CUDA cores
     if (sizeof(T) == 4 && tc_enabled() && (double)M * N * K * batch >= 2.0e6) {
         tc_gemm(st, ta, tb, M, N, K, (float)alpha, (const float *)A, lda, sA, (const float *)B, ldb, sB,
-                (float)beta, (float *)C, ldc, sC, batch, !gemm_fast_mode());
+                (float)beta, (float *)C, ldc, sC, batch, true);
         return;
     }
     if (!ta && !tb) launch<T, false, false>(st, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch);

@@ -236,7 +236,7 @@ __global__ void maxabs_kernel(const float *__restrict__ P, long long len, int k,
 }
 
 __global__ void scale_kernel(const unsigned *__restrict__ bits, int k, float *__restrict__ scale) {
-    const int s = threadIdx.x;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= k) return;
     const float m = __uint_as_float(bits[s]);
     int e = 0;
@@ -284,7 +284,7 @@ void response_density_tc(cudaStream_t st, const GridShape &g, const TileSet<floa
     check(cudaMemsetAsync(scratch_bits, 0, sizeof(unsigned) * k, st), "memset maxabs");
     maxabs_kernel<<<dim3(64, k), 256, 0, st>>>(P, sP, k, scratch_bits);
     check_launch("maxabs_kernel");
-    scale_kernel<<<1, 32, 0, st>>>(scratch_bits, k, scale);
+    scale_kernel<<<(k + 127) / 128, 128, 0, st>>>(scratch_bits, k, scale);
     check_launch("scale_kernel");
     CUtensorMap mx;
     if (!encode_map_2d(&mx, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, chi_pm, (unsigned long long)CK,
@@ -533,7 +533,7 @@ void potential_integrals_tc(cudaStream_t st, const GridShape &g, const TileSet<f
     const long long n3 = (long long)g.n * g.n * g.n;
     vmaxabs_kernel<<<dim3(64, k), 256, 0, st>>>(V, n3, scratch_bits);
     check_launch("vmaxabs_kernel");
-    scale_kernel<<<1, 32, 0, st>>>(scratch_bits, k, scale);
+    scale_kernel<<<(k + 127) / 128, 128, 0, st>>>(scratch_bits, k, scale);
     check_launch("scale_kernel");
     CUtensorMap mx;
     if (!encode_map_2d(&mx, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, chi_fm16, (unsigned long long)TILE_PTS,

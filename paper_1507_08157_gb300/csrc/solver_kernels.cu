@@ -197,9 +197,11 @@ __global__ void __launch_bounds__(256) combine_kernel(const double *__restrict__
                                                       long long sin, T *__restrict__ out,
                                                       long long sout, long long len, bool accumulate) {
     __shared__ T Cs[32 * 32];
-    for (int i = threadIdx.x; i < nout * nin; i += blockDim.x) {
-        const int r = i / nin, c = i - r * nin;
-        Cs[r * 32 + c] = T(C[r * ldc + c]);
+    // every slot the product loop reads is written (zero past nin): stale shared memory from an
+    // earlier kernel may hold NaN patterns, and NaN * 0 is NaN
+    for (int i = threadIdx.x; i < nout * 32; i += blockDim.x) {
+        const int r = i >> 5, c = i & 31;
+        Cs[i] = c < nin ? T(C[r * ldc + c]) : T(0);
     }
     __syncthreads();
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len;

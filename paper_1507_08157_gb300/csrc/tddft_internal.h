@@ -61,15 +61,6 @@ struct GridShape {
 };
 
 // ---------------------------------------------------------------------------------------------
-// float32 products inside this scope may use plain TF32 on the tensor cores (one MMA per
-// product, relative error ~2^-11) instead of the three-term split; for approximate solves only
-bool &gemm_fast_mode();
-struct FastGemmScope {
-    bool prev;
-    explicit FastGemmScope(bool on) : prev(gemm_fast_mode()) { gemm_fast_mode() = on; }
-    ~FastGemmScope() { gemm_fast_mode() = prev; }
-};
-
 // dense GEMM, row-major: C[b] = alpha * op(A[b]) op(B[b]) + beta * C[b]
 template <typename T>
 void gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, T alpha, const T *A, int lda,
