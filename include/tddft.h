@@ -138,6 +138,30 @@ tddft_status tddft_response_potential(tddft_ctx *ctx, int32_t k, const double *r
 tddft_status tddft_potential_integrals(tddft_ctx *ctx, int32_t k, const double *V, double *out);
 tddft_status tddft_fxc(tddft_ctx *ctx, double *fxc);
 
+/* Allocation-free response density. The paper has no counterpart: this is a library-level
+ * variant of tddft_response_density for callers that cannot allocate device memory when they
+ * need a density (a process whose own pool allocator already holds the device memory, or a
+ * latency-bound loop in which cudaMalloc / cudaFree, which synchronise the device, are not
+ * allowed). It computes the same rho_s(r) = sum_ab chi_a(r) P_s,ab phi_b(r) (Sec. II C) with the
+ * same tensor-core kernel, but takes float32 device buffers and uses no context workspace.
+ *   ctx: a TDDFT_MIXED context whose grid products run on the tensor cores; anything else
+ *        returns TDDFT_E_INVALID. Call with the context's device current.
+ *   k:   number of states, 1 <= k <= TDDFT_NOALLOC_MAX_STATES (TDDFT_E_INVALID otherwise).
+ *   P:   device pointer, float32 [k][N_chi][N_phi], read only, owned by the caller.
+ *   rho: device pointer, float32 [k][n^3] (x slowest), every element written, owned by the
+ *        caller.
+ * Scratch: one fixed array of about 520 bytes per device in the library's static device memory
+ * (64 max-reduction words, 64 scales, a wait-expiry flag). The first call on a device looks up
+ * its address (cudaGetSymbolAddress) and loads the kernels; make that first call before the
+ * phase that must not allocate. Each call clears the array on the stream before use, so the
+ * caller zeroes nothing. All calls on one device share the array: overlapping calls (two host
+ * threads, or two contexts on different streams) race and must be serialised by the caller.
+ * The call makes no cudaMalloc / cudaFree and no allocating library call; it waits for the
+ * context's stream at the end to read the flag, and returns TDDFT_E_TIMEOUT if a bounded wait
+ * in the kernel expired. */
+#define TDDFT_NOALLOC_MAX_STATES 64
+tddft_status tddft_response_density_noalloc(tddft_ctx *ctx, int32_t k, const float *P, float *rho);
+
 /* Solver state for k trial pairs (Sec. III C). Y0 [k][N_chi][N_phi] is the random start X
  * (Y = 0, so p = q = X); it is masked to the kernel pattern, mapped through Eq. auxiliary,
  * sign-flipped and Gram-Schmidt orthonormalised in the metric of Eq. ortho, then f is applied.

@@ -134,6 +134,11 @@ void response_density_tc(cudaStream_t st, const GridShape &g, const TileSet<floa
                          const TileSet<float> &phi, const unsigned short *chi_pm, int CK, int NPmax, int nphi,
                          const float *P, long long sP, int k, float *rho, unsigned *scratch_bits,
                          float *scale, int *err);
+int noalloc_max_states();
+void response_density_tc_noalloc(cudaStream_t st, const GridShape &g, const TileSet<float> &chi,
+                                 const TileSet<float> &phi, const unsigned short *chi_pm, int CK, int NPmax,
+                                 int nphi, const float *P, long long sP, int k, float *rho);
+int response_density_tc_noalloc_error(cudaStream_t st);
 Profiler *profiler_new();
 void profiler_delete(Profiler *p);
 void profiler_read(Profiler *p, long long *launches, double *ms, double *flops, double *bytes);
@@ -1146,6 +1151,25 @@ tddft_status tddft_work(const tddft_ctx *c, double *pair_points, double *table_v
     if (pair_points) *pair_points = c->pair_points;
     if (table_values) *table_values = c->table_values;
     return TDDFT_OK;
+}
+
+tddft_status tddft_response_density_noalloc(tddft_ctx *c, int32_t k, const float *P, float *rho) {
+    if (!c) return TDDFT_E_INVALID;
+    return guarded(c, [&]() -> tddft_status {
+        if (c->prec != TDDFT_MIXED || !c->d32 || !c->d32->grid_tc)
+            throw InvalidArg{"tddft_response_density_noalloc: needs a mixed-precision context on the tensor-core path"};
+        if (k < 1 || k > noalloc_max_states())
+            throw InvalidArg{"tddft_response_density_noalloc: k must be between 1 and " +
+                             std::to_string(noalloc_max_states())};
+        if (!P || !rho || !is_device_ptr(P) || !is_device_ptr(rho))
+            throw InvalidArg{"tddft_response_density_noalloc: P and rho must be device pointers"};
+        Impl<float> &I = *c->d32;
+        response_density_tc_noalloc(c->st, c->grid(), I.chi, I.phi, I.chi_pm, I.CK, I.NPmax, c->nv, P, c->len(), k,
+                                    rho);
+        if (response_density_tc_noalloc_error(c->st))
+            throw TimeoutErr{"a bounded wait in the density kernel expired"};
+        return TDDFT_OK;
+    });
 }
 
 tddft_status tddft_pattern(const tddft_ctx *c, uint8_t *mask) {

@@ -17,6 +17,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <mutex>
 
 namespace tddft {
 
@@ -555,6 +556,89 @@ void potential_integrals_tc(cudaStream_t st, const GridShape &g, const TileSet<f
     integrals_tc_kernel<<<grid, 192, sm, st>>>(mx, g.n, g.nt, NPmax, G, k, chi.off, chi.ids, phi.off, phi.ids,
                                                phi.val, nchi, nphi, V, scale, (float)g.dV, out, vec_ok, stride, err);
     check_launch("integrals_tc_kernel");
+}
+
+}  // namespace tddft
+
+// ================================================================================================
+// Allocation-free variant of the tensor-core response density. Some callers cannot allocate
+// device memory at the point where they need a density: a process whose own pool allocator has
+// already reserved the device memory, or a latency-bound loop in which cudaMalloc / cudaFree
+// (which synchronise the whole device) are not allowed. For them the per-state scale words and
+// the wait-expiry flag live in one fixed file-scope device array instead of context workspace,
+// and the caller passes float32 device buffers for P and rho. The array is shared by every call
+// on a device, so overlapping calls race and must be serialised by the caller.
+namespace tddft {
+
+constexpr int NOALLOC_MAX_STATES = 64;
+
+struct NoallocScratch {
+    unsigned bits[NOALLOC_MAX_STATES];
+    float scale[NOALLOC_MAX_STATES];
+    int err;
+};
+
+// one copy per device that loads the library (64 + 64 words + a flag, about 520 bytes); each call
+// clears it before use, so nothing in it needs to start at zero
+static __device__ __align__(256) NoallocScratch g_density_noalloc_scratch;
+
+namespace {
+std::mutex g_noalloc_mu;
+NoallocScratch *g_noalloc_addr[64] = {};   // device address of the array, per device ordinal
+}  // namespace
+
+// device address of the scratch array on the current device, looked up once per device with that
+// device current (the first call on a device does this set-up)
+NoallocScratch *noalloc_scratch_address() {
+    int dev = 0;
+    check(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev < 0 || dev >= 64) throw CudaError{cudaErrorInvalidDevice, "device ordinal beyond 63"};
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        check(cudaGetSymbolAddress(&p, g_density_noalloc_scratch), "cudaGetSymbolAddress(density scratch)");
+        g_noalloc_addr[dev] = static_cast<NoallocScratch *>(p);
+    }
+    return g_noalloc_addr[dev];
+}
+
+int noalloc_max_states() { return NOALLOC_MAX_STATES; }
+
+// rho[k][n^3] from P[k][N_chi][N_phi] (float32, device); no allocation, no context workspace.
+void response_density_tc_noalloc(cudaStream_t st, const GridShape &g, const TileSet<float> &chi,
+                                 const TileSet<float> &phi, const unsigned short *chi_pm, int CK, int NPmax,
+                                 int nphi, const float *P, long long sP, int k, float *rho) {
+    if (k < 1 || k > NOALLOC_MAX_STATES) throw CudaError{cudaErrorInvalidValue, "k beyond the scratch maximum"};
+    NoallocScratch *s = noalloc_scratch_address();
+    // the scale words must start at zero for the max reduction; the flag is cleared per call
+    check(cudaMemsetAsync(s, 0, sizeof(NoallocScratch), st), "clear density scratch");
+    maxabs_kernel<<<dim3(64, k), 256, 0, st>>>(P, sP, k, s->bits);
+    check_launch("maxabs_kernel");
+    scale_kernel<<<(k + 127) / 128, 128, 0, st>>>(s->bits, k, s->scale);
+    check_launch("scale_kernel");
+    CUtensorMap mx;
+    if (!encode_map_2d(&mx, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, chi_pm, (unsigned long long)CK,
+                       (unsigned long long)chi.ntiles * TILE_PTS, (unsigned long long)CK * 2, 64, 128))
+        throw CudaError{cudaErrorInvalidValue, "cuTensorMapEncodeTiled (density)"};
+    const int NP = NPmax, KBmax = CK / 64;
+    const int G = density_tc_group(KBmax, NP, k);
+    if (G < 1) throw CudaError{cudaErrorInvalidValue, "density_tc: tile too large for shared memory"};
+    const size_t sm = density_tc_smem(KBmax, G * NP);
+    check(cudaFuncSetAttribute(density_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),
+          "attr density_tc");
+    dim3 grid((k + G - 1) / G, chi.ntiles);
+    density_tc_kernel<<<grid, DENS_THREADS, sm, st>>>(mx, g.n, g.nt, KBmax, NP, G, k, chi.off, chi.ids, phi.off,
+                                                      phi.ids, phi.val, nphi, P, sP, s->scale, rho, &s->err);
+    check_launch("density_tc_kernel (allocation-free)");
+}
+
+// wait-expiry flag of the last call on this device (synchronises the stream)
+int response_density_tc_noalloc_error(cudaStream_t st) {
+    NoallocScratch *s = noalloc_scratch_address();
+    int h = 0;
+    check(cudaMemcpyAsync(&h, &s->err, sizeof(int), cudaMemcpyDeviceToHost, st), "D2H density flag");
+    check(cudaStreamSynchronize(st), "sync density flag");
+    return h;
 }
 
 }  // namespace tddft

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libtddft.so")
 
 OK, E_INVALID, E_NOMEM, E_CUDA, E_NOT_CONVERGED, E_BREAKDOWN, E_TIMEOUT, E_PAIRING = range(8)
 FP64, MIXED = 0, 1
+NOALLOC_MAX_STATES = 64        # TDDFT_NOALLOC_MAX_STATES of the header
 MODE = {"full": 0, "tda": 1, "d_only": 2}
 PRECOND = {"none": 0, "iter": 1}
 FXC = {"none": 0, "lda": 1}
@@ -57,7 +58,8 @@ class StageStats(ctypes.Structure):
 
 
 SYMBOLS = sorted(["tddft_default_options", "tddft_create", "tddft_destroy", "tddft_last_error",
-                  "tddft_dims", "tddft_apply", "tddft_response_density", "tddft_response_potential",
+                  "tddft_dims", "tddft_apply", "tddft_response_density", "tddft_response_density_noalloc",
+                  "tddft_response_potential",
                   "tddft_potential_integrals", "tddft_fxc", "tddft_state_create",
                   "tddft_state_destroy", "tddft_pcg_step", "tddft_solve", "tddft_state_get",
                   "tddft_subspace", "tddft_pattern", "tddft_profile", "tddft_profile_read",
@@ -99,6 +101,8 @@ def load(path: str = LIB_PATH):
     for name in ("tddft_response_density", "tddft_response_potential", "tddft_potential_integrals"):
         getattr(lib, name).argtypes = [vp, ctypes.c_int32, vp, vp]
     lib.tddft_fxc.argtypes = [vp, vp]
+    lib.tddft_response_density_noalloc.argtypes = [vp, ctypes.c_int32, vp, vp]
+    lib.tddft_response_density_noalloc.restype = ctypes.c_int
     lib.tddft_state_create.argtypes = [vp, ctypes.c_int32, vp, ctypes.POINTER(vp)]
     lib.tddft_state_destroy.argtypes = [vp]
     lib.tddft_state_destroy.restype = None
@@ -244,6 +248,19 @@ class Context:
         out = self._out(P, (P.shape[0], self.n, self.n, self.n))
         self._check(self._lib.tddft_response_density(self._ctx, P.shape[0], _ptr(P), _ptr(out)))
         return out
+
+    def response_density_noalloc(self, P, rho):
+        """rho = density of P through the allocation-free entry point; P [k][N_chi][N_phi] and
+        rho [k][n][n][n] are contiguous float32 CUDA tensors owned by the caller."""
+        import torch
+        for a in (P, rho):
+            if not (a.is_cuda and a.dtype == torch.float32 and a.is_contiguous()):
+                raise ValueError("P and rho must be contiguous float32 CUDA tensors")
+        k = P.shape[0]
+        if tuple(P.shape[1:]) != (self.nc, self.nv) or tuple(rho.shape) != (k, self.n, self.n, self.n):
+            raise ValueError("P must be [k][N_chi][N_phi] and rho [k][n][n][n]")
+        self._check(self._lib.tddft_response_density_noalloc(self._ctx, k, P.data_ptr(), rho.data_ptr()))
+        return rho
 
     def response_potential(self, rho):
         out = self._out(rho, rho.shape)
