@@ -12,154 +12,85 @@ namespace tddft {
 
 namespace {
 
-constexpr int GCH = 64;        // elements per staged chunk in the trace kernels
-constexpr int GMAXQ = 8;       // pair slots per thread (pairs <= 2048)
-constexpr int GBLOCKS = 304;   // 2 blocks per SM on 152 SMs
 
 // ------------------------------------------------------------------------------------------------
-// G[i][j] = sum_e X_i[e] Y_j[e] (or only i == j when diag). float32 inputs: 64-term float32
-// partial sums per chunk (products of float32 values are exact in the float64 accumulator's
-// range but not in float32; the chunk sums carry ~64 ulp), accumulated in float64 across chunks.
-template <typename T>
-__global__ void __launch_bounds__(256) gram_partial(const T *__restrict__ X, long long sx, int nx,
-                                                    const T *__restrict__ Y, long long sy, int ny,
-                                                    long long len, bool diag,
-                                                    double *__restrict__ partial) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *xs = reinterpret_cast<T *>(smem_raw);   // [nx][GCH+1]
-    T *ys = xs + nx * (GCH + 1);               // [ny][GCH+1]
-    const int pairs = diag ? nx : nx * ny;
-    double acc[GMAXQ];
-#pragma unroll
-    for (int q = 0; q < GMAXQ; ++q) acc[q] = 0.0;
-    const long long nchunks = (len + GCH - 1) / GCH;
-    for (long long c = blockIdx.x; c < nchunks; c += gridDim.x) {
-        const long long e0 = c * GCH;
-        for (int i = threadIdx.x; i < nx * GCH; i += blockDim.x) {
-            const int r = i / GCH, e = i - r * GCH;
-            xs[r * (GCH + 1) + e] = (e0 + e < len) ? X[r * sx + e0 + e] : T(0);
-        }
-        for (int i = threadIdx.x; i < ny * GCH; i += blockDim.x) {
-            const int r = i / GCH, e = i - r * GCH;
-            ys[r * (GCH + 1) + e] = (e0 + e < len) ? Y[r * sy + e0 + e] : T(0);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < GMAXQ; ++q) {
-            const int p = threadIdx.x + 256 * q;
-            if (p >= pairs) break;
-            const int i = diag ? p : p / ny, j = diag ? p : p - (p / ny) * ny;
-            const T *xr = xs + i * (GCH + 1);
-            const T *yr = ys + j * (GCH + 1);
-            T part = T(0);
-#pragma unroll 16
-            for (int e = 0; e < GCH; ++e) part = fma(xr[e], yr[e], part);
-            acc[q] += (double)part;
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int q = 0; q < GMAXQ; ++q) {
-        const int p = threadIdx.x + 256 * q;
-        if (p < pairs) partial[(long long)blockIdx.x * pairs + p] = acc[q];
-    }
-}
-
+// G[p] = sum over the slices of partial[slice][p]: one warp per output, lanes stride the slices,
+// then a fixed butterfly (deterministic)
 __global__ void gram_final(const double *__restrict__ partial, int nblocks, int pairs,
                            double *__restrict__ G) {
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < pairs; p += gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int b = 0; b < nblocks; ++b) s += partial[(long long)b * pairs + p];
-        G[p] = s;
-    }
-}
-
-template <typename T>
-void gram_impl(cudaStream_t st, const T *X, long long sx, int nx, const T *Y, long long sy, int ny,
-               long long len, bool diag, double *G, double *scratch) {
-    const int pairs = diag ? nx : nx * ny;
-    if (pairs <= 0) return;
-    if (pairs > 256 * GMAXQ || nx > 64 || ny > 64)
-        throw CudaError{cudaErrorInvalidValue, "gram: too many pairs"};
-    const long long nchunks = (len + GCH - 1) / GCH;
-    const int nb = (int)(nchunks < GBLOCKS ? (nchunks > 0 ? nchunks : 1) : GBLOCKS);
-    const size_t sm = sizeof(T) * (size_t)(nx + ny) * (GCH + 1);
-    ProfScope ps(st, ST_TRACE, 2.0 * pairs * (double)len, sizeof(T) * (double)(nx + ny) * len);
-    static bool attr = false;
-    if (!attr) {
-        check(cudaFuncSetAttribute(gram_partial<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)(sizeof(T) * 128 * (GCH + 1))),
-              "attr gram");
-        attr = true;
-    }
-    gram_partial<T><<<nb, 256, sm, st>>>(X, sx, nx, Y, sy, ny, len, diag, scratch);
-    check_launch("gram_partial");
-    gram_final<<<(pairs + 255) / 256, 256, 0, st>>>(scratch, nb, pairs, G);
-    check_launch("gram_final");
+    const int lane = threadIdx.x & 31;
+    const int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (p >= pairs) return;
+    double s = 0.0;
+    for (int b = lane; b < nblocks; b += 32) s += partial[(long long)b * pairs + p];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) G[p] = s;
 }
 
 // ------------------------------------------------------------------------------------------------
-// Register-tiled trace products. Block (x, y): element slice x, pair tile y of 8 x 8 (i, j);
-// each thread accumulates its 64 products over a strided run of elements (float32 products
-// summed in T per run of at most RUN elements, then in float64), the block reduces in float64
-// in a fixed order and writes one partial per pair; gram_final sums the partials over slices.
+// Register-tiled trace products. Block (x, y): pair tile x of TI x TJ (i, j), element slice y
+// (consecutive blocks share a slice, so the rows a tile re-reads come from L2). Each thread sums
+// its products in T over runs of RUN elements and the runs in T again (at most RUN * RUN
+// elements per thread by the choice of the slice count), the warp reduces in T by a fixed
+// butterfly, the block sums its 8 warps in float64 and writes one partial per pair; gram_final
+// sums the partials over slices in float64. float64 arithmetic is scarce on this part, so it is
+// kept off the per-element path.
 constexpr int RUN = 32;
+constexpr int TI = 4, TJ = 8;
 
 template <typename T>
-__global__ void __launch_bounds__(256) gram_tiled(const T *__restrict__ X, long long sx, int nx,
-                                                  const T *__restrict__ Y, long long sy, int ny,
-                                                  long long len, int tiles_j, double *__restrict__ partial,
-                                                  int pairs) {
-    __shared__ double red[8][8][33];
-    const int ti = blockIdx.y / tiles_j, tj = blockIdx.y - ti * tiles_j;
-    const int i0 = ti * 8, j0 = tj * 8;
-    double acc[8][8];
-    T run[8][8];
+__global__ void __launch_bounds__(256, 2) gram_tiled(const T *__restrict__ X, long long sx, int nx,
+                                                     const T *__restrict__ Y, long long sy, int ny,
+                                                     long long len, int tiles_j, double *__restrict__ partial,
+                                                     int pairs) {
+    __shared__ double red[TI][TJ][8];
+    const int ti = blockIdx.x / tiles_j, tj = blockIdx.x - ti * tiles_j;
+    const int i0 = ti * TI, j0 = tj * TJ;
+    T tot[TI][TJ], run[TI][TJ];
 #pragma unroll
-    for (int a = 0; a < 8; ++a)
+    for (int a = 0; a < TI; ++a)
 #pragma unroll
-        for (int b = 0; b < 8; ++b) acc[a][b] = 0.0, run[a][b] = T(0);
-    const long long stride = (long long)gridDim.x * blockDim.x;
+        for (int b = 0; b < TJ; ++b) tot[a][b] = T(0), run[a][b] = T(0);
+    const long long stride = (long long)gridDim.y * blockDim.x;
     int cnt = 0;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len; e += stride) {
-        T xv[8], yv[8];
+    for (long long e = blockIdx.y * (long long)blockDim.x + threadIdx.x; e < len; e += stride) {
+        T xv[TI], yv[TJ];
 #pragma unroll
-        for (int a = 0; a < 8; ++a) xv[a] = (i0 + a < nx) ? X[(i0 + a) * sx + e] : T(0);
+        for (int a = 0; a < TI; ++a) xv[a] = (i0 + a < nx) ? X[(i0 + a) * sx + e] : T(0);
 #pragma unroll
-        for (int b = 0; b < 8; ++b) yv[b] = (j0 + b < ny) ? Y[(j0 + b) * sy + e] : T(0);
+        for (int b = 0; b < TJ; ++b) yv[b] = (j0 + b < ny) ? Y[(j0 + b) * sy + e] : T(0);
 #pragma unroll
-        for (int a = 0; a < 8; ++a)
+        for (int a = 0; a < TI; ++a)
 #pragma unroll
-            for (int b = 0; b < 8; ++b) run[a][b] = fma(xv[a], yv[b], run[a][b]);
+            for (int b = 0; b < TJ; ++b) run[a][b] = fma(xv[a], yv[b], run[a][b]);
         if (++cnt == RUN) {
 #pragma unroll
-            for (int a = 0; a < 8; ++a)
+            for (int a = 0; a < TI; ++a)
 #pragma unroll
-                for (int b = 0; b < 8; ++b) acc[a][b] += (double)run[a][b], run[a][b] = T(0);
+                for (int b = 0; b < TJ; ++b) tot[a][b] += run[a][b], run[a][b] = T(0);
             cnt = 0;
         }
     }
-    // warp reduction (fixed butterfly order), then across the 8 warps through shared memory
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int a = 0; a < 8; ++a)
+    for (int a = 0; a < TI; ++a)
 #pragma unroll
-        for (int b = 0; b < 8; ++b) {
-            double v = acc[a][b] + (double)run[a][b];
+        for (int b = 0; b < TJ; ++b) {
+            T v = tot[a][b] + run[a][b];
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) red[a][b][warp] = v;
+            if (lane == 0) red[a][b][warp] = (double)v;
         }
     __syncthreads();
-    if (threadIdx.x < 64) {
-        const int a = threadIdx.x >> 3, b = threadIdx.x & 7;
+    if (threadIdx.x < TI * TJ) {
+        const int a = threadIdx.x / TJ, b = threadIdx.x - a * TJ;
         double v = 0.0;
         for (int w = 0; w < 8; ++w) v += red[a][b][w];
         const int i = i0 + a, j = j0 + b;
-        if (i < nx && j < ny) partial[(long long)blockIdx.x * pairs + i * ny + j] = v;
+        if (i < nx && j < ny) partial[(long long)blockIdx.y * pairs + i * ny + j] = v;
     }
 }
 
-// d_i = sum_e X_i[e] Y_i[e]: one row per blockIdx.y, float32 runs of RUN then float64
+// d_i = sum_e X_i[e] Y_i[e]: one row per blockIdx.y, the same two-level runs and reductions
 template <typename T>
 __global__ void __launch_bounds__(256) dots_kernel(const T *__restrict__ X, long long sx, const T *__restrict__ Y,
                                                    long long sy, long long len, int n, double *__restrict__ partial) {
@@ -167,26 +98,25 @@ __global__ void __launch_bounds__(256) dots_kernel(const T *__restrict__ X, long
     const int i = blockIdx.y;
     const T *x = X + i * sx;
     const T *y = Y + i * sy;
-    double acc = 0.0;
-    T run = T(0);
+    T tot = T(0), run = T(0);
     int cnt = 0;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len; e += stride) {
         run = fma(x[e], y[e], run);
         if (++cnt == RUN) {
-            acc += (double)run;
+            tot += run;
             run = T(0);
             cnt = 0;
         }
     }
-    acc += (double)run;
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    T v = tot + run;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)v;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double v = 0.0;
-        for (int w = 0; w < 8; ++w) v += red[w];
-        partial[(long long)blockIdx.x * n + i] = v;
+        double s = 0.0;
+        for (int w = 0; w < 8; ++w) s += red[w];
+        partial[(long long)blockIdx.x * n + i] = s;
     }
 }
 
@@ -261,118 +191,165 @@ int grid_for(long long n) {
 }
 
 // ------------------------------------------------------------------------------------------------
-// small float64 algebra (single thread)
-__device__ bool chol_solve(int k, const double *M, const double *B, double *X, double *L) {
-    // L L^T = M; X = M^-1 B (B, X: k x k)
-    for (int i = 0; i < k; ++i) {
-        for (int j = 0; j <= i; ++j) {
-            double s = M[i * k + j];
-            for (int p = 0; p < j; ++p) s -= L[i * k + p] * L[j * k + p];
-            if (i == j) {
-                if (!(s > 0.0)) return false;
-                L[i * k + i] = sqrt(s);
-            } else {
-                L[i * k + j] = s / L[j * k + j];
-            }
+// Small float64 algebra for one thread block (k <= KMAX, so k * k <= 256 threads hold one matrix
+// element each). Matrices live in shared memory; every routine is entered and left by all
+// threads of the block. The updates run in the same order as the textbook row-by-row loops
+// (right-looking, one pivot or row at a time), so the results equal theirs up to the order of
+// the backward-substitution sums.
+constexpr int SB_THREADS = 256;
+
+// L L^T = M (lower L, full k x k, upper part zero); false (in every thread) if M is not
+// positive definite. W is a k x k work array.
+__device__ bool sb_cholesky(int k, const double *M, double *L, double *W, int *bad) {
+    const int t = threadIdx.x, kk = k * k;
+    if (t == 0) *bad = 0;
+    if (t < kk) { W[t] = M[t]; L[t] = 0.0; }
+    __syncthreads();
+    for (int j = 0; j < k; ++j) {
+        if (t == 0) {
+            const double d = W[j * k + j];
+            if (!(d > 0.0)) *bad = 1;
+            L[j * k + j] = d > 0.0 ? sqrt(d) : 1.0;
         }
+        __syncthreads();
+        if (t > j && t < k) L[t * k + j] = W[t * k + j] / L[j * k + j];
+        __syncthreads();
+        if (t < kk) {
+            const int i = t / k, l = t - i * k;
+            if (i > j && l > j && l <= i) W[i * k + l] -= L[i * k + j] * L[l * k + j];
+        }
+        __syncthreads();
     }
-    for (int c = 0; c < k; ++c) {
-        for (int i = 0; i < k; ++i) {   // forward
-            double s = B[i * k + c];
-            for (int p = 0; p < i; ++p) s -= L[i * k + p] * X[p * k + c];
-            X[i * k + c] = s / L[i * k + i];
-        }
-        for (int i = k - 1; i >= 0; --i) {   // backward with L^T
-            double s = X[i * k + c];
-            for (int p = i + 1; p < k; ++p) s -= L[p * k + i] * X[p * k + c];
-            X[i * k + c] = s / L[i * k + i];
-        }
-    }
-    return true;
+    return *bad == 0;
 }
 
-struct LineBlocks {
+// X = (L L^T)^-1 B for nrhs <= 2 KMAX right-hand sides (B, X: k x nrhs); X may alias B
+__device__ void sb_solve(int k, int nrhs, const double *L, const double *B, double *X) {
+    const int t = threadIdx.x, tot = k * nrhs;
+    if (X != B)
+        for (int e = t; e < tot; e += blockDim.x) X[e] = B[e];
+    __syncthreads();
+    for (int i = 0; i < k; ++i) {          // forward: L y = b
+        if (t < nrhs) X[i * nrhs + t] /= L[i * k + i];
+        __syncthreads();
+        for (int e = (i + 1) * nrhs + t; e < tot; e += blockDim.x) {
+            const int r = e / nrhs, c = e - r * nrhs;
+            X[e] -= L[r * k + i] * X[i * nrhs + c];
+        }
+        __syncthreads();
+    }
+    for (int i = k - 1; i >= 0; --i) {     // backward: L^T x = y
+        if (t < nrhs) X[i * nrhs + t] /= L[i * k + i];
+        __syncthreads();
+        for (int e = t; e < i * nrhs; e += blockDim.x) {
+            const int r = e / nrhs, c = e - r * nrhs;
+            X[e] -= L[i * k + r] * X[i * nrhs + c];
+        }
+        __syncthreads();
+    }
+}
+
+struct SbLine {
     double N0[KMAX * KMAX], N1[KMAX * KMAX], N2[KMAX * KMAX];
     double M0[KMAX * KMAX], M1[KMAX * KMAX], M2[KMAX * KMAX];
+    double M[KMAX * KMAX], dM[KMAX * KMAX], L[KMAX * KMAX], Wk[KMAX * KMAX];
+    double R[KMAX * 2 * KMAX];     // [k][2k]: N | dN, then M^-1 N | M^-1 dN
+    double T[KMAX * KMAX], Z[KMAX * KMAX];
+    double out[4];
+    int bad;
 };
 
-struct Scratch {
-    double M[KMAX * KMAX], N[KMAX * KMAX], dM[KMAX * KMAX], dN[KMAX * KMAX];
-    double W[KMAX * KMAX], X[KMAX * KMAX], Z[KMAX * KMAX], T[KMAX * KMAX], L[KMAX * KMAX];
-};
-
-// Omega(lam) = Tr[M^-1 N]/2 and its derivative; returns false when M is not positive definite
-__device__ bool sum_functional(int k, const LineBlocks &lb, double lam, double *f, double *d,
-                               Scratch &s) {
-    const int kk = k * k;
-    for (int i = 0; i < kk; ++i) {
-        s.M[i] = lb.M0[i] + lam * lb.M1[i] + lam * lam * lb.M2[i];
-        s.N[i] = lb.N0[i] + lam * lb.N1[i] + lam * lam * lb.N2[i];
-        s.dM[i] = lb.M1[i] + 2.0 * lam * lb.M2[i];
-        s.dN[i] = lb.N1[i] + 2.0 * lam * lb.N2[i];
+// Omega(lam) = Tr[M^-1 N]/2 and dOmega/dlam = Tr[M^-1 dN - M^-1 dM M^-1 N]/2 with
+// M = M0 + lam M1 + lam^2 M2, N likewise; false (in every thread) if M is not positive definite
+__device__ bool sb_sum_functional(int k, SbLine &s, double lam, double *f, double *d) {
+    const int t = threadIdx.x, kk = k * k, k2 = 2 * k;
+    if (t < kk) {
+        const int i = t / k, j = t - i * k;
+        s.M[t] = s.M0[t] + lam * s.M1[t] + lam * lam * s.M2[t];
+        s.dM[t] = s.M1[t] + 2.0 * lam * s.M2[t];
+        s.R[i * k2 + j] = s.N0[t] + lam * s.N1[t] + lam * lam * s.N2[t];
+        s.R[i * k2 + k + j] = s.N1[t] + 2.0 * lam * s.N2[t];
     }
-    if (!chol_solve(k, s.M, s.N, s.W, s.L)) return false;
-    chol_solve(k, s.M, s.dN, s.X, s.L);
-    for (int i = 0; i < k; ++i)          // T = dM W
-        for (int j = 0; j < k; ++j) {
-            double acc = 0.0;
-            for (int p = 0; p < k; ++p) acc += s.dM[i * k + p] * s.W[p * k + j];
-            s.T[i * k + j] = acc;
+    __syncthreads();
+    if (!sb_cholesky(k, s.M, s.L, s.Wk, &s.bad)) return false;
+    sb_solve(k, k2, s.L, s.R, s.R);         // W = M^-1 N, X = M^-1 dN
+    if (t < kk) {                           // T = dM W
+        const int i = t / k, j = t - i * k;
+        double acc = 0.0;
+        for (int p = 0; p < k; ++p) acc += s.dM[i * k + p] * s.R[p * k2 + j];
+        s.T[t] = acc;
+    }
+    __syncthreads();
+    sb_solve(k, k, s.L, s.T, s.Z);          // Z = M^-1 dM M^-1 N
+    if (t == 0) {
+        double tw = 0.0, tx = 0.0, tz = 0.0;
+        for (int i = 0; i < k; ++i) {
+            tw += s.R[i * k2 + i];
+            tx += s.R[i * k2 + k + i];
+            tz += s.Z[i * k + i];
         }
-    chol_solve(k, s.M, s.T, s.Z, s.L);
-    double tw = 0.0, tx = 0.0, tz = 0.0;
-    for (int i = 0; i < k; ++i) {
-        tw += s.W[i * k + i];
-        tx += s.X[i * k + i];
-        tz += s.Z[i * k + i];
+        s.out[0] = 0.5 * tw;
+        s.out[1] = 0.5 * (tx - tz);
     }
-    *f = 0.5 * tw;
-    *d = 0.5 * (tx - tz);
+    __syncthreads();
+    *f = s.out[0];
+    *d = s.out[1];
+    __syncthreads();
     return true;
 }
 
-__device__ double line_step(int k, const LineBlocks &lb, Scratch &s) {
+// Minimiser of Omega along the common step (every thread returns the same value): a Newton
+// estimate from the second derivative at 0 (with M0 = I), doubled until dOmega >= 0 brackets the
+// root, bisection while M is indefinite at the upper end, then Illinois regula falsi on dOmega
+// to machine precision
+__device__ double sb_line_step(int k, SbLine &s) {
     double f0, d0;
-    if (!sum_functional(k, lb, 0.0, &f0, &d0, s) || !isfinite(d0) || d0 >= 0.0) return 0.0;
-    // Newton estimate with M0 = I: h0 = Tr[2 N2 - 2 M1 N1 + 2 M1 M1 N0 - 2 M2 N0] / 2
-    double h0 = 0.0;
-    for (int i = 0; i < k; ++i) {
-        double t = 2.0 * lb.N2[i * k + i];
+    if (!sb_sum_functional(k, s, 0.0, &f0, &d0) || !isfinite(d0) || d0 >= 0.0) return 0.0;
+    const int t = threadIdx.x;
+    // h0 = Tr[2 N2 - 2 M1 N1 + 2 M1 M1 N0 - 2 M2 N0] / 2, one row per thread, summed in order
+    if (t < k) {
+        const int i = t;
+        double h = 2.0 * s.N2[i * k + i];
         for (int p = 0; p < k; ++p) {
-            t -= 2.0 * lb.M1[i * k + p] * lb.N1[p * k + i];
-            t -= 2.0 * lb.M2[i * k + p] * lb.N0[p * k + i];
+            h -= 2.0 * s.M1[i * k + p] * s.N1[p * k + i];
+            h -= 2.0 * s.M2[i * k + p] * s.N0[p * k + i];
             double m1m1 = 0.0;
-            for (int q = 0; q < k; ++q) m1m1 += lb.M1[i * k + q] * lb.M1[q * k + p];
-            t += 2.0 * m1m1 * lb.N0[p * k + i];
+            for (int q = 0; q < k; ++q) m1m1 += s.M1[i * k + q] * s.M1[q * k + p];
+            h += 2.0 * m1m1 * s.N0[p * k + i];
         }
-        h0 += 0.5 * t;
+        s.T[i] = 0.5 * h;
     }
+    __syncthreads();
+    if (t == 0) {
+        double h0 = 0.0;
+        for (int i = 0; i < k; ++i) h0 += s.T[i];
+        s.out[2] = h0;
+    }
+    __syncthreads();
+    const double h0 = s.out[2];
+    __syncthreads();
     double hi = (h0 > 0.0 && isfinite(h0)) ? -d0 / h0 : 1.0;
-    double lo = 0.0, dlo = d0, dhi = 0.0, f, d;
-    // bracket: dOmega < 0 at lo, >= 0 (or M not positive definite) at hi
-    int it = 0;
-    for (; it < 60; ++it) {
-        if (!sum_functional(k, lb, hi, &f, &d, s)) d = INFINITY;
+    double lo = 0.0, dlo = d0, dhi = 0.0, f, d = d0;
+    for (int it = 0; it < 60; ++it) {
+        if (!sb_sum_functional(k, s, hi, &f, &d)) d = INFINITY;
         if (d >= 0.0) break;
         lo = hi;
         dlo = d;
         hi = 2.0 * hi;
     }
     dhi = d;
-    // past the positive-definite region: bisect until dOmega is finite at hi
     for (int b = 0; b < 200 && !isfinite(dhi); ++b) {
         const double mid = 0.5 * (lo + hi);
-        if (!sum_functional(k, lb, mid, &f, &d, s)) d = INFINITY;
+        if (!sb_sum_functional(k, s, mid, &f, &d)) d = INFINITY;
         if (d < 0.0) { lo = mid; dlo = d; }
         else { hi = mid; dhi = d; }
     }
-    // Illinois regula falsi on dOmega(lambda) inside [lo, hi], to machine precision
     int side = 0;
     for (int r = 0; r < 100; ++r) {
         if (!(hi - lo > 4e-16 * hi)) break;
         double x = (isfinite(dhi) && dhi != dlo) ? hi - dhi * (hi - lo) / (dhi - dlo) : 0.5 * (lo + hi);
         if (!(x > lo && x < hi)) x = 0.5 * (lo + hi);
-        if (!sum_functional(k, lb, x, &f, &d, s)) d = INFINITY;
+        if (!sb_sum_functional(k, s, x, &f, &d)) d = INFINITY;
         if (d == 0.0) return x;
         if (d < 0.0) {
             lo = x;
@@ -387,6 +364,124 @@ __device__ double line_step(int k, const LineBlocks &lb, Scratch &s) {
         }
     }
     return 0.5 * (lo + hi);
+}
+
+// Classical Gram-Schmidt run twice on coefficient vectors in the metric Mg, vectors taken in
+// the given order; rows of C are the new vectors. u and coef are k-vectors of work space.
+// False (in every thread) if a norm is not positive.
+__device__ bool sb_gram_schmidt(int k, const double *Mg, const int *order, double *C, double *v,
+                                double *u, double *coef, int *bad) {
+    const int t = threadIdx.x;
+    if (t < k * k) C[t] = 0.0;
+    if (t == 0) *bad = 0;
+    __syncthreads();
+    for (int a = 0; a < k; ++a) {
+        const int i = order[a];
+        if (t < k) v[t] = (t == i) ? 1.0 : 0.0;
+        __syncthreads();
+        for (int pass = 0; pass < 2; ++pass) {
+            if (t < k) {                    // u = Mg v
+                double acc = 0.0;
+                for (int q = 0; q < k; ++q) acc += Mg[t * k + q] * v[q];
+                u[t] = acc;
+            }
+            __syncthreads();
+            if (t < a) {                    // coef_b = <v, C_order[b]>_Mg
+                const int j = order[t];
+                double acc = 0.0;
+                for (int p = 0; p < k; ++p) acc += C[j * k + p] * u[p];
+                coef[t] = acc;
+            }
+            __syncthreads();
+            if (t < k) {
+                double x = v[t];
+                for (int b = 0; b < a; ++b) x -= coef[b] * C[order[b] * k + t];
+                v[t] = x;
+            }
+            __syncthreads();
+        }
+        if (t < k) {
+            double acc = 0.0;
+            for (int q = 0; q < k; ++q) acc += Mg[t * k + q] * v[q];
+            u[t] = acc;
+        }
+        __syncthreads();
+        if (t == 0) {
+            double nrm = 0.0;
+            for (int p = 0; p < k; ++p) nrm += v[p] * u[p];
+            const double ref = fabs(Mg[i * k + i]) > 1.0 ? fabs(Mg[i * k + i]) : 1.0;
+            if (!isfinite(nrm) || nrm <= 1e-12 * ref) *bad = 1;
+            coef[KMAX] = *bad ? 0.0 : 1.0 / sqrt(nrm);
+        }
+        __syncthreads();
+        if (*bad) return false;
+        if (t < k) C[i * k + t] = v[t] * coef[KMAX];
+        __syncthreads();
+    }
+    return true;
+}
+
+// Eigenvalues of a symmetric k x k matrix (cyclic Jacobi, one rotation at a time), ascending,
+// into w (written by thread 0). a is overwritten.
+__device__ void sb_jacobi_eigenvalues(int k, double *a, double *w, double *cs) {
+    const int t = threadIdx.x;
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        if (t == 0) {
+            double off = 0.0, tot = 0.0;
+            for (int i = 0; i < k; ++i)
+                for (int j = 0; j < k; ++j) {
+                    tot += a[i * k + j] * a[i * k + j];
+                    if (i != j) off += a[i * k + j] * a[i * k + j];
+                }
+            cs[2] = (off <= 1e-30 * tot || off == 0.0) ? 1.0 : 0.0;
+        }
+        __syncthreads();
+        const bool done = cs[2] != 0.0;
+        __syncthreads();
+        if (done) break;
+        for (int p = 0; p < k; ++p)
+            for (int q = p + 1; q < k; ++q) {
+                if (t == 0) {
+                    const double apq = a[p * k + q];
+                    if (apq == 0.0) {
+                        cs[0] = 1.0;
+                        cs[1] = 0.0;
+                    } else {
+                        const double theta = (a[q * k + q] - a[p * k + p]) / (2.0 * apq);
+                        const double tt = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                        cs[0] = 1.0 / sqrt(tt * tt + 1.0);
+                        cs[1] = tt * cs[0];
+                    }
+                }
+                __syncthreads();
+                const double c = cs[0], sn = cs[1];
+                if (sn != 0.0 && t < k) {   // columns p, q
+                    const double arp = a[t * k + p], arq = a[t * k + q];
+                    a[t * k + p] = c * arp - sn * arq;
+                    a[t * k + q] = sn * arp + c * arq;
+                }
+                __syncthreads();
+                if (sn != 0.0 && t < k) {   // rows p, q
+                    const double apr = a[p * k + t], aqr = a[q * k + t];
+                    a[p * k + t] = c * apr - sn * aqr;
+                    a[q * k + t] = sn * apr + c * aqr;
+                }
+                __syncthreads();
+            }
+    }
+    if (t == 0) {
+        for (int i = 0; i < k; ++i) w[i] = a[i * k + i];
+        for (int i = 1; i < k; ++i) {
+            const double x = w[i];
+            int j = i - 1;
+            while (j >= 0 && w[j] > x) {
+                w[j + 1] = w[j];
+                --j;
+            }
+            w[j + 1] = x;
+        }
+    }
+    __syncthreads();
 }
 
 // classical Gram-Schmidt twice on coefficient vectors; rows of C are the new vectors
@@ -421,49 +516,6 @@ __device__ bool gram_schmidt(int k, const double *Mg, const int *order, double *
     return true;
 }
 
-// cyclic Jacobi eigenvalues of a symmetric k x k matrix, ascending
-__device__ void jacobi_eigenvalues(int k, const double *A, double *w) {
-    double a[KMAX * KMAX];
-    for (int i = 0; i < k * k; ++i) a[i] = A[i];
-    for (int sweep = 0; sweep < 60; ++sweep) {
-        double off = 0.0, tot = 0.0;
-        for (int i = 0; i < k; ++i)
-            for (int j = 0; j < k; ++j) {
-                tot += a[i * k + j] * a[i * k + j];
-                if (i != j) off += a[i * k + j] * a[i * k + j];
-            }
-        if (off <= 1e-30 * tot || off == 0.0) break;
-        for (int p = 0; p < k; ++p)
-            for (int q = p + 1; q < k; ++q) {
-                const double apq = a[p * k + q];
-                if (apq == 0.0) continue;
-                const double theta = (a[q * k + q] - a[p * k + p]) / (2.0 * apq);
-                const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-                const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
-                for (int r = 0; r < k; ++r) {   // columns p, q
-                    const double arp = a[r * k + p], arq = a[r * k + q];
-                    a[r * k + p] = c * arp - s * arq;
-                    a[r * k + q] = s * arp + c * arq;
-                }
-                for (int r = 0; r < k; ++r) {   // rows p, q
-                    const double apr = a[p * k + r], aqr = a[q * k + r];
-                    a[p * k + r] = c * apr - s * aqr;
-                    a[q * k + r] = s * apr + c * aqr;
-                }
-            }
-    }
-    for (int i = 0; i < k; ++i) w[i] = a[i * k + i];
-    for (int i = 1; i < k; ++i) {   // insertion sort
-        const double x = w[i];
-        int j = i - 1;
-        while (j >= 0 && w[j] > x) {
-            w[j + 1] = w[j];
-            --j;
-        }
-        w[j + 1] = x;
-    }
-}
-
 // ---- kernels ----------------------------------------------------------------------------------
 
 // From A[x][y] = <cov(P_x), f_y> (x, y over p_0..p_k-1, q_0..q_k-1): Q_ij = (A[j][i] +
@@ -483,27 +535,30 @@ __global__ void make_q_kernel(int k, const double *A, double *Q, double *coef) {
 }
 
 // residuals and Ritz values: r_i = sqrt(d_p,i + d_q,i); omega = eig(sym Q); out = [omega, r]
-__global__ void eval_finish_kernel(int k, const double *Q, const double *d, double *out,
-                                   int *status) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double S[KMAX * KMAX];
-    bool bad = false;
-    for (int i = 0; i < k; ++i)
-        for (int j = 0; j < k; ++j) {
-            S[i * k + j] = 0.5 * (Q[i * k + j] + Q[j * k + i]);
-            if (!isfinite(S[i * k + j])) bad = true;
-        }
-    for (int i = 0; i < k; ++i) {
-        const double r2 = d[i] + d[k + i];
-        out[k + i] = sqrt(r2 > 0.0 ? r2 : 0.0);
-        if (!isfinite(r2)) bad = true;
+__global__ void __launch_bounds__(SB_THREADS) eval_finish_kernel(int k, const double *Q, const double *d,
+                                                                 double *out, int *status) {
+    __shared__ double S[KMAX * KMAX], cs[4];
+    __shared__ int bad;
+    const int t = threadIdx.x, kk = k * k;
+    if (t == 0) bad = 0;
+    __syncthreads();
+    if (t < kk) {
+        const int i = t / k, j = t - i * k;
+        S[t] = 0.5 * (Q[i * k + j] + Q[j * k + i]);
+        if (!isfinite(S[t])) bad = 1;
     }
+    if (t < k) {
+        const double r2 = d[t] + d[k + t];
+        out[k + t] = sqrt(r2 > 0.0 ? r2 : 0.0);
+        if (!isfinite(r2)) bad = 1;
+    }
+    __syncthreads();
     if (bad) {
-        *status = DEV_NAN_EVAL;
-        for (int i = 0; i < k; ++i) out[i] = NAN;
+        if (t == 0) *status = DEV_NAN_EVAL;
+        if (t < k) out[t] = NAN;
         return;
     }
-    jacobi_eigenvalues(k, S, out);
+    sb_jacobi_eigenvalues(k, S, out, cs);
 }
 
 // Polak-Ribiere coefficient over the whole set (sums of the 2k dot products)
@@ -537,74 +592,87 @@ __global__ void conj_kernel(int k2, const double *gz_d, const double *gzp_d, con
 // Outputs: lam[0]; Cp, Cq [k][k] combination coefficients (sign flips folded into Cq);
 // flip_any -> sc_flip[0]; status.
 
-// single-thread version of the line step and re-orthonormalisation
-__global__ void line_gs_kernel(int k, const double *A, const double *BDf, const double *CDfD,
-                               const double *PP, const double *PD, const double *DP,
-                               const double *DD, const double *Q, double *lam, double *Cp,
-                               double *Cq, double *sc_flip, int *status) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    const int k2 = 2 * k;
-    LineBlocks lb;
-    Scratch s;
-    double T0[KMAX * KMAX], T1[KMAX * KMAX], T2[KMAX * KMAX];
-    for (int i = 0; i < k; ++i)
-        for (int j = 0; j < k; ++j) {
-            const int e = i * k + j;
-            const double n0ij = A[i * k2 + j] + A[(k + i) * k2 + k + j];
-            const double n0ji = A[j * k2 + i] + A[(k + j) * k2 + k + i];
-            lb.N0[e] = 0.5 * (n0ij + n0ji);
-            const double efij = BDf[i * k2 + j] + BDf[(k + i) * k2 + k + j];
-            const double efji = BDf[j * k2 + i] + BDf[(k + j) * k2 + k + i];
-            lb.N1[e] = efij + efji;
-            const double n2ij = CDfD[i * k2 + j] + CDfD[(k + i) * k2 + k + j];
-            const double n2ji = CDfD[j * k2 + i] + CDfD[(k + j) * k2 + k + i];
-            lb.N2[e] = 0.5 * (n2ij + n2ji);
-            T0[e] = PP[i * k2 + k + j];
-            T1[e] = PD[i * k2 + k + j] + DP[i * k2 + k + j];
-            T2[e] = DD[i * k2 + k + j];
-        }
-    for (int i = 0; i < k; ++i)
-        for (int j = 0; j < k; ++j) {
-            const int e = i * k + j;
-            lb.M0[e] = 0.5 * (T0[e] + T0[j * k + i]);
-            lb.M1[e] = 0.5 * (T1[e] + T1[j * k + i]);
-            lb.M2[e] = 0.5 * (T2[e] + T2[j * k + i]);
-        }
-    for (int e = 0; e < k * k; ++e)
-        if (!isfinite(lb.N0[e]) || !isfinite(lb.N1[e]) || !isfinite(lb.N2[e]) || !isfinite(lb.M1[e]) ||
-            !isfinite(lb.M2[e])) {
-            *status = DEV_NAN_LINE;
-            return;
-        }
-    const double l = line_step(k, lb, s);
-    *lam = l;
-    double Tm[KMAX * KMAX], Mg[KMAX * KMAX], sg[KMAX];
-    for (int i = 0; i < k * k; ++i) Tm[i] = T0[i] + l * T1[i] + l * l * T2[i];
-    int any = 0;
-    for (int i = 0; i < k; ++i) {
-        sg[i] = Tm[i * k + i] < 0.0 ? -1.0 : 1.0;
-        if (sg[i] < 0.0) any = 1;
+// Line step and re-orthonormalisation for one thread block of SB_THREADS threads
+__global__ void __launch_bounds__(SB_THREADS) line_gs_kernel(int k, const double *A, const double *BDf,
+                                                             const double *CDfD, const double *PP,
+                                                             const double *PD, const double *DP,
+                                                             const double *DD, const double *Q, double *lam,
+                                                             double *Cp, double *Cq, double *sc_flip,
+                                                             int *status) {
+    __shared__ SbLine s;
+    __shared__ double T0[KMAX * KMAX], T1[KMAX * KMAX], T2[KMAX * KMAX], Mg[KMAX * KMAX], C[KMAX * KMAX];
+    __shared__ double sg[KMAX], v[KMAX], u[KMAX], coef[KMAX + 1];
+    __shared__ int order[KMAX], flags[2];
+    const int t = threadIdx.x, k2 = 2 * k, kk = k * k;
+    if (t == 0) flags[0] = 0;
+    __syncthreads();
+    if (t < kk) {
+        const int i = t / k, j = t - i * k;
+        const double n0ij = A[i * k2 + j] + A[(k + i) * k2 + k + j];
+        const double n0ji = A[j * k2 + i] + A[(k + j) * k2 + k + i];
+        s.N0[t] = 0.5 * (n0ij + n0ji);
+        const double efij = BDf[i * k2 + j] + BDf[(k + i) * k2 + k + j];
+        const double efji = BDf[j * k2 + i] + BDf[(k + j) * k2 + k + i];
+        s.N1[t] = efij + efji;
+        const double n2ij = CDfD[i * k2 + j] + CDfD[(k + i) * k2 + k + j];
+        const double n2ji = CDfD[j * k2 + i] + CDfD[(k + j) * k2 + k + i];
+        s.N2[t] = 0.5 * (n2ij + n2ji);
+        T0[t] = PP[i * k2 + k + j];                          // <p_i, q_j>
+        T1[t] = PD[i * k2 + k + j] + DP[i * k2 + k + j];     // <p_i, Dq_j> + <Dp_i, q_j>
+        T2[t] = DD[i * k2 + k + j];                          // <Dp_i, Dq_j>
     }
-    for (int i = 0; i < k; ++i)
-        for (int j = 0; j < k; ++j) Mg[i * k + j] = 0.5 * (Tm[i * k + j] * sg[j] + Tm[j * k + i] * sg[i]);
-    int order[KMAX];
-    for (int i = 0; i < k; ++i) order[i] = i;
-    for (int i = 1; i < k; ++i) {
-        const int x = order[i];
-        int j = i - 1;
-        while (j >= 0 && Q[order[j] * k + order[j]] > Q[x * k + x]) {
-            order[j + 1] = order[j];
-            --j;
-        }
-        order[j + 1] = x;
+    __syncthreads();
+    if (t < kk) {
+        const int i = t / k, j = t - i * k;
+        s.M0[t] = 0.5 * (T0[t] + T0[j * k + i]);
+        s.M1[t] = 0.5 * (T1[t] + T1[j * k + i]);
+        s.M2[t] = 0.5 * (T2[t] + T2[j * k + i]);
+        if (!isfinite(s.N0[t]) || !isfinite(s.N1[t]) || !isfinite(s.N2[t]) || !isfinite(s.M1[t]) ||
+            !isfinite(s.M2[t]))
+            flags[0] = 1;
     }
-    if (!gram_schmidt(k, Mg, order, Cp)) {
-        *status = DEV_BREAKDOWN;
+    __syncthreads();
+    if (flags[0]) {
+        if (t == 0) *status = DEV_NAN_LINE;
         return;
     }
-    for (int i = 0; i < k; ++i)
-        for (int j = 0; j < k; ++j) Cq[i * k + j] = Cp[i * k + j] * sg[j];
-    *sc_flip = any ? 1.0 : 0.0;
+    const double l = sb_line_step(k, s);
+    if (t < kk) T0[t] = T0[t] + l * T1[t] + l * l * T2[t];   // <p_i, q_j> at the new point
+    __syncthreads();
+    if (t < k) sg[t] = T0[t * k + t] < 0.0 ? -1.0 : 1.0;
+    __syncthreads();
+    if (t < kk) {
+        const int i = t / k, j = t - i * k;
+        Mg[t] = 0.5 * (T0[t] * sg[j] + T0[j * k + i] * sg[i]);
+    }
+    if (t == 0) {
+        *lam = l;
+        int any = 0;
+        for (int i = 0; i < k; ++i) any |= sg[i] < 0.0;
+        flags[1] = any;
+        // Gram-Schmidt order: ascending Ritz diagonal Q_ii (insertion sort, stable)
+        for (int i = 0; i < k; ++i) order[i] = i;
+        for (int i = 1; i < k; ++i) {
+            const int x = order[i];
+            int j = i - 1;
+            while (j >= 0 && Q[order[j] * k + order[j]] > Q[x * k + x]) {
+                order[j + 1] = order[j];
+                --j;
+            }
+            order[j + 1] = x;
+        }
+    }
+    __syncthreads();
+    if (!sb_gram_schmidt(k, Mg, order, C, v, u, coef, &s.bad)) {
+        if (t == 0) *status = DEV_BREAKDOWN;
+        return;
+    }
+    if (t < kk) {
+        const int j = t % k;
+        Cp[t] = C[t];
+        Cq[t] = C[t] * sg[j];
+    }
+    if (t == 0) *sc_flip = flags[1] ? 1.0 : 0.0;
 }
 
 // initial orthonormalisation: T0 from PP only, identity order
@@ -637,9 +705,10 @@ __global__ void init_gs_kernel(int k, const double *PP, double *Cp, double *Cq, 
 __global__ void cg_scalars_kernel(int n, int phase, double tol, const double *pLp,
                                   const double *rr_new, double *rr, const double *r0, double *alpha,
                                   double *beta, int *active, int *n_active) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    int cnt = 0;
-    for (int i = 0; i < n; ++i) {
+    // one thread per system (n <= blockDim.x)
+    const int i = threadIdx.x;
+    int act = 0;
+    if (i < n) {
         if (phase == 0) {
             const bool go = active[i] && pLp[i] > 0.0 && isfinite(pLp[i]);
             if (!go) active[i] = 0;
@@ -651,10 +720,11 @@ __global__ void cg_scalars_kernel(int n, int phase, double tol, const double *pL
                 rr[i] = rr_new[i];
                 if (!(sqrt(rr_new[i] > 0.0 ? rr_new[i] : 0.0) > tol * r0[i])) active[i] = 0;
             }
-            cnt += active[i];
+            act = active[i];
         }
     }
-    if (phase == 1) *n_active = cnt;
+    const int cnt = __syncthreads_count(act);
+    if (phase == 1 && i == 0) *n_active = cnt;
 }
 
 __global__ void cg_init_kernel(int n, double tol, const double *rr0, double *rr, double *r0,
@@ -762,6 +832,17 @@ constexpr int TRACE_SLICES = 152;
 
 long long gram_scratch_doubles(int nx, int ny) { return (long long)2 * TRACE_SLICES * nx * ny + 64; }
 
+// slices of a trace launch: `want`, fewer for short vectors (one 256-thread block per slice
+// holds at least one element per thread), more (up to `cap`) when a thread would otherwise
+// sum more than RUN * RUN elements
+int trace_slices(long long len, int want, int cap) {
+    const long long per = (len + 255) / 256;
+    long long s = std::min<long long>(want, std::max<long long>(1, per));
+    const long long need = (len + 256LL * RUN * RUN - 1) / (256LL * RUN * RUN);
+    s = std::max(s, std::min<long long>(need, cap));
+    return (int)s;
+}
+
 template <typename T>
 void gram(cudaStream_t st, const T *X, long long sx, int nx, const T *Y, long long sy, int ny,
           long long len, double *G, double *scratch) {
@@ -769,12 +850,11 @@ void gram(cudaStream_t st, const T *X, long long sx, int nx, const T *Y, long lo
     if (pairs <= 0) return;
     if (nx > 64 || ny > 64) throw CudaError{cudaErrorInvalidValue, "gram: too many matrices"};
     ProfScope ps(st, ST_TRACE, 2.0 * pairs * (double)len, sizeof(T) * (double)(nx + ny) * len);
-    const int ti = (nx + 7) / 8, tj = (ny + 7) / 8;
-    const long long per = (len + 255) / 256;
-    const int slices = (int)std::min<long long>(TRACE_SLICES, std::max<long long>(1, per));
-    gram_tiled<T><<<dim3(slices, ti * tj), 256, 0, st>>>(X, sx, nx, Y, sy, ny, len, tj, scratch, pairs);
+    const int ti = (nx + TI - 1) / TI, tj = (ny + TJ - 1) / TJ;
+    const int slices = trace_slices(len, TRACE_SLICES, 2 * TRACE_SLICES);
+    gram_tiled<T><<<dim3(ti * tj, slices), 256, 0, st>>>(X, sx, nx, Y, sy, ny, len, tj, scratch, pairs);
     check_launch("gram_tiled");
-    gram_final<<<(pairs + 255) / 256, 256, 0, st>>>(scratch, slices, pairs, G);
+    gram_final<<<(pairs + 7) / 8, 256, 0, st>>>(scratch, slices, pairs, G);
     check_launch("gram_final");
 }
 
@@ -783,11 +863,10 @@ void dots(cudaStream_t st, const T *X, long long sx, const T *Y, long long sy, i
           double *d, double *scratch) {
     if (n <= 0) return;
     ProfScope ps(st, ST_TRACE, 2.0 * n * (double)len, sizeof(T) * 2.0 * n * len);
-    const long long per = (len + 255) / 256;
-    const int slices = (int)std::min<long long>(2 * TRACE_SLICES, std::max<long long>(1, per));
+    const int slices = trace_slices(len, 2 * TRACE_SLICES, 2 * TRACE_SLICES);
     dots_kernel<T><<<dim3(slices, n), 256, 0, st>>>(X, sx, Y, sy, len, n, scratch);
     check_launch("dots_kernel");
-    gram_final<<<(n + 255) / 256, 256, 0, st>>>(scratch, slices, n, d);
+    gram_final<<<(n + 7) / 8, 256, 0, st>>>(scratch, slices, n, d);
     check_launch("gram_final");
 }
 
@@ -845,7 +924,7 @@ void make_q(cudaStream_t st, int k, const double *A, double *Q, double *coef) {
 }
 void eval_finish(cudaStream_t st, int k, const double *Q, const double *d, double *out, int *status) {
     ProfScope ps(st, ST_SMALL, 0.0, 0.0);
-    eval_finish_kernel<<<1, 1, 0, st>>>(k, Q, d, out, status);
+    eval_finish_kernel<<<1, SB_THREADS, 0, st>>>(k, Q, d, out, status);
     check_launch("eval_finish_kernel");
 }
 void conj_coeff(cudaStream_t st, int k2, const double *gz, const double *gzp, const double *gd,
@@ -858,7 +937,7 @@ void line_gs(cudaStream_t st, int k, const double *A, const double *BDf, const d
              const double *PP, const double *PD, const double *DP, const double *DD, const double *Q,
              double *lam, double *Cp, double *Cq, double *flip, int *status) {
     ProfScope ps(st, ST_SMALL, 0.0, 0.0);
-    line_gs_kernel<<<1, 1, 0, st>>>(k, A, BDf, CDfD, PP, PD, DP, DD, Q, lam, Cp, Cq, flip, status);
+    line_gs_kernel<<<1, SB_THREADS, 0, st>>>(k, A, BDf, CDfD, PP, PD, DP, DD, Q, lam, Cp, Cq, flip, status);
     check_launch("line_gs_kernel");
 }
 void init_gs(cudaStream_t st, int k, const double *PP, double *Cp, double *Cq, int *status) {
@@ -875,7 +954,8 @@ void cg_init(cudaStream_t st, int n, double tol, const double *rr0, double *rr, 
 void cg_scalars(cudaStream_t st, int n, int phase, double tol, const double *pLp, const double *rr_new,
                 double *rr, const double *r0, double *alpha, double *beta, int *active, int *n_active) {
     ProfScope ps(st, ST_SMALL, 0.0, 0.0);
-    cg_scalars_kernel<<<1, 1, 0, st>>>(n, phase, tol, pLp, rr_new, rr, r0, alpha, beta, active, n_active);
+    cg_scalars_kernel<<<1, 32 * ((n + 31) / 32), 0, st>>>(n, phase, tol, pLp, rr_new, rr, r0, alpha, beta, active,
+                                                          n_active);
     check_launch("cg_scalars_kernel");
 }
 void subspace(cudaStream_t st, int k, const double *A, double *omega, double *pairing) {
