@@ -148,10 +148,16 @@ def gram_schmidt_coefficients(Mg, order):
 
 class PCG:
     def __init__(self, op, Y0, mode=FULL, precond="iter", precond_tol=1e-4,
-                 precond_maxit=50, reapply_every=10, restart_every=10):
+                 precond_maxit=50, reapply_every=10, restart_every=10, mlp=None):
+        """precond: "iter" (inner CG on Eq. precond), "none", or "learned" with mlp =
+        (parameter vector, hidden width) of the atom-block network of ``learned``."""
         self.op = op
         self.mode = mode
         self.precond = precond
+        self.learned = None
+        if precond == "learned":
+            from .learned import LearnedPreconditioner
+            self.learned = LearnedPreconditioner(op.sys, mlp[0], mlp[1], op.mask)
         self.precond_tol = precond_tol
         self.precond_maxit = precond_maxit
         self.reapply_every = reapply_every
@@ -175,6 +181,7 @@ class PCG:
         self.prev = None
         self.flipped = False
         self.inner_iters = 0
+        self.fallbacks = 0
         self.last_lambda = 0.0
 
     # ---------------------------------------------------------------------------------------------
@@ -256,21 +263,50 @@ class PCG:
             self.inner_iters += 1
         return G
 
+    def search_gradient(self, gp, gq):
+        """The gradient the preconditioner acts on: g itself, or P^c G_L P^v with truncation."""
+        op = self.op
+        if self.trunc:
+            # precondition the L-gradient: z = mask * Pinv(P^c G_L P^v), positive in Frobenius
+            return (np.array([op.Pc @ G @ op.Pv for G in self.GLp]),
+                    np.array([op.Pc @ G @ op.Pv for G in self.GLq]))
+        return gp, gq
+
+    def iterative_z(self, hp, hq):
+        m = self.op.mask
+        return (np.array([m * self.apply_preconditioner(x) for x in hp]),
+                np.array([m * self.apply_preconditioner(x) for x in hq]))
+
+    def samples(self):
+        """Training rows of the learned preconditioner at the current iterate: inputs from the
+        search gradient h, targets from the iterative preconditioner's z = mask * Pinv(h)."""
+        from .learned import Features
+        Q, omega, gp, gq, res = self.evaluate()
+        hp, hq = self.search_gradient(gp, gq)
+        zp, zq = self.iterative_z(hp, hq)
+        feat = Features(self.op.sys)
+        X, s = feat.rows(hp, hq)
+        return X, feat.targets(zp, zq, s)
+
     def update(self, Q, omega, gp, gq):
         k = self.k
         op = self.op
-        m = op.mask
-        if self.trunc:
-            # precondition the L-gradient: z = mask * Pinv(P^c G_L P^v), positive in Frobenius
-            hp = np.array([op.Pc @ G @ op.Pv for G in self.GLp])
-            hq = np.array([op.Pc @ G @ op.Pv for G in self.GLq])
-        else:
-            hp, hq = gp, gq
-        zp = np.array([m * self.apply_preconditioner(hp[i]) for i in range(k)])
-        zq = np.array([m * self.apply_preconditioner(hq[i]) for i in range(k)])
-        Zp = np.array([op.project(X) for X in zp])
-        Zq = np.array([op.project(X) for X in zq])
-        gz = sum(self.inner(gp[i], Zp[i]) + self.inner(gq[i], Zq[i]) for i in range(k))
+        hp, hq = self.search_gradient(gp, gq)
+        gz = 0.0
+        if self.learned is not None:
+            # learned map; the iterative preconditioner stands in when -z is not a descent
+            # direction of the sum functional (<g, Z> <= 0)
+            zp, zq = self.learned.apply(hp, hq)
+            Zp = np.array([op.project(X) for X in zp])
+            Zq = np.array([op.project(X) for X in zq])
+            gz = sum(self.inner(gp[i], Zp[i]) + self.inner(gq[i], Zq[i]) for i in range(k))
+            if not gz > 0.0:
+                self.fallbacks += 1
+        if self.learned is None or not gz > 0.0:
+            zp, zq = self.iterative_z(hp, hq)
+            Zp = np.array([op.project(X) for X in zp])
+            Zq = np.array([op.project(X) for X in zq])
+            gz = sum(self.inner(gp[i], Zp[i]) + self.inner(gq[i], Zq[i]) for i in range(k))
         restart = self.prev is None or self.it % self.restart_every == 0 or self.flipped
         beta = 0.0
         if not restart:

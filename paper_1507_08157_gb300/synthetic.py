@@ -390,6 +390,33 @@ def random_kernels(sys: System, k: int, seed: int):
     return (rng.standard_normal((k, nc, nv)), rng.standard_normal((k, nc, nv)))
 
 
+def mlp_init(n_in: int, width: int, n_out: int, seed: int):
+    """Initial parameters of the atom-block network (in -> width -> width -> out), float32, in
+    the order W1 [n_in][width], b1, W2 [width][width], b2, W3 [width][n_out], b3. Weights are
+    uniform in +-sqrt(6 / fan_in) (He et al. 2015), the output layer scaled by 0.1; biases 0."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 15485863]))
+    parts = []
+    for fi, fo, scale in ((n_in, width, 1.0), (width, width, 1.0), (width, n_out, 0.1)):
+        lim = np.sqrt(6.0 / fi)
+        parts.append(scale * rng.uniform(-lim, lim, size=fi * fo))
+        parts.append(np.zeros(fo))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def minibatch_order(n: int, steps: int, batch: int, seed: int):
+    """Sample indices of `steps` minibatches of `batch` rows drawn from n rows: a fresh random
+    permutation per epoch, concatenated; int64 [steps * batch]."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 32452843]))
+    need = steps * batch
+    out = []
+    have = 0
+    while have < need:
+        p = rng.permutation(n)
+        out.append(p)
+        have += n
+    return np.concatenate(out)[:need].astype(np.int64)
+
+
 def fingerprint(sys: System) -> str:
     """Short hash of the generated arrays, for checking two machines built the same system."""
     hsh = hashlib.sha256()
