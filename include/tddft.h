@@ -45,7 +45,7 @@ typedef enum {
 
 enum { TDDFT_FP64 = 0, TDDFT_MIXED = 1 };                       /* tddft_options.precision */
 enum { TDDFT_MODE_FULL = 0, TDDFT_MODE_TDA = 1, TDDFT_MODE_D_ONLY = 2 };
-enum { TDDFT_PRECOND_NONE = 0, TDDFT_PRECOND_ITER = 1 };
+enum { TDDFT_PRECOND_NONE = 0, TDDFT_PRECOND_ITER = 1, TDDFT_PRECOND_LEARNED = 2 };
 enum { TDDFT_FXC_NONE = 0, TDDFT_FXC_LDA_PW92 = 1 };
 
 /* Localised functions tabulated in periodic boxes (paper Sec. II C: NGWFs phi_alpha, chi_alpha).
@@ -90,7 +90,9 @@ typedef struct {
                                  line search, Gram-Schmidt, eigenvalues in float64 */
     int32_t mode;             /* TDDFT_MODE_FULL (Eq. operator_RPA); TDDFT_MODE_TDA (B = 0:
                                  f_p = A p, f_q = A q); TDDFT_MODE_D_ONLY (coupling K = 0) */
-    int32_t precond;          /* TDDFT_PRECOND_ITER: CG solve of Eq. precond; NONE: identity */
+    int32_t precond;          /* TDDFT_PRECOND_ITER: CG solve of Eq. precond; NONE: identity;
+                                 LEARNED: the atom-block network bound by tddft_set_mlp, with the
+                                 CG solve as fallback */
     int32_t precond_maxit;    /* inner CG iterations cap (default 50) */
     double precond_tol;       /* inner CG relative residual (default 1e-4) */
     double tol;               /* convergence: max residual (Ha) <= tol and max |d omega| <= tol/10 */
@@ -197,6 +199,75 @@ tddft_status tddft_subspace(tddft_ctx *ctx, tddft_state *st, double *omega, doub
 /* Atom-pair pattern of the response kernels: mask [natoms][natoms], 1 where a chi on atom I and
  * a phi on atom J are coupled (distance <= kernel_cutoff, or everywhere with no cutoff). */
 tddft_status tddft_pattern(const tddft_ctx *ctx, uint8_t *mask);
+
+/* ---- Learned atom-block preconditioner ---------------------------------------------------------
+ * A stand-in for the inner-CG solve of Eq. precond (Sec. III B) inside the PCG of Sec. III C: each
+ * atom block (chi-atom I, phi-atom J) of the search gradient h goes to z_IJ = h_IJ + A_IJ h_IJ,
+ * blocks read as vectors (p block then q block, row-major), with the n_b x n_b matrix A_IJ
+ * predicted by a 3-layer perceptron from the block's fixed features. The map is linear in h, as
+ * the CG solve is. Needs equal function counts n_c (chi) and n_v (phi) on every atom, functions
+ * grouped by atom. Training rows (state i, I, J; J fastest):
+ *   input  x = [b, f], b = [h^p_IJ / s, h^q_IJ / s]                 (n_b = 2 n_c n_v)
+ *                      f = [M^c_II, S^chi_II, M^v_JJ, S^phi_JJ, d_IJ / 10]
+ *                                                                   (n_f = 2 n_c^2 + 2 n_v^2 + 1)
+ *   target y = [(z^p_IJ - h^p_IJ) / s, (z^q_IJ - h^q_IJ) / s]       (n_b)
+ *   weight w = s^2 / (sum of s^2 over the rows of the same state)
+ * with s the Frobenius norm of the pair (h^p_IJ, h^q_IJ), M^c = P^c H^chi, M^v = H^phi P^v, d_IJ
+ * the minimum-image atom distance in bohr. The model's output for a row is A(f) b. With
+ * truncation the kernel mask follows the map. When the learned direction is not a descent
+ * direction of the sum functional, the step takes the CG solve instead (counted in
+ * tddft_state_stats). The paper has no network: this is the learned stand-in its
+ * preconditioner admits. */
+typedef struct tddft_mlp tddft_mlp;
+
+/* Model for n_b-entry blocks and n_f features with hidden width `width`, on the current device,
+ * parameters zero. The perceptron is n_f -> width -> width -> n_b^2 with ReLU after the two hidden
+ * layers: H1 = relu(F W1 + b1), H2 = relu(H1 W2 + b2), vec(A) = H2 W3 + b3 (A row-major).
+ * Parameter vector (float32, tddft_mlp_size entries): W1 [n_f][width], b1 [width],
+ * W2 [width][width], b2, W3 [width][n_b^2], b3 [n_b^2], each row-major, concatenated.
+ * 1 <= n_b <= 128, 1 <= n_f, width <= 4096 (INVALID otherwise). One model serves one stream at a
+ * time. */
+tddft_status tddft_mlp_create(int32_t n_block, int32_t n_feat, int32_t width, tddft_mlp **out);
+void tddft_mlp_destroy(tddft_mlp *m);
+const char *tddft_mlp_last_error(const tddft_mlp *m);
+int64_t tddft_mlp_size(const tddft_mlp *m);
+/* Copy the parameter vector in (resets the Adam moments and step count) or out; host or device
+ * pointers. The inference copy is the parameters rounded to bfloat16 (nearest, ties to even). */
+tddft_status tddft_mlp_set(tddft_mlp *m, const float *theta);
+tddft_status tddft_mlp_get(const tddft_mlp *m, float *theta);
+/* Y [n][n_b] = A(f_r) b_r for rows X [n][n_b + n_f] = [b, f], with the bfloat16-rounded
+ * parameters; device pointers, float32, row-major. Products on the tensor cores, float32
+ * accumulation. */
+tddft_status tddft_mlp_forward(tddft_mlp *m, int64_t n, const float *X, float *Y);
+/* Weighted mean-squared loss L = sum_r w_r sum_j (y_rj - T_rj)^2 / (n n_b) of the model over n
+ * rows with the float32 parameters, and its gradient (backpropagation; relu'(0) = 0). X, T and
+ * the row weights w [n] are device pointers (w NULL: all 1); loss, grad host (either may be NULL;
+ * grad has tddft_mlp_size entries). */
+tddft_status tddft_mlp_loss_grad(tddft_mlp *m, int64_t n, const float *X, const float *T, const float *w,
+                                 double *loss, float *grad);
+/* steps Adam updates (Kingma & Ba: beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) of the
+ * weighted loss on minibatches of `batch` rows: step s uses rows order[s*batch .. (s+1)*batch)
+ * (host int64 indices into the n rows of X, T, w, which are device pointers; w may be NULL).
+ * loss_first / loss_last (may be NULL): the loss of the first and last minibatch before their
+ * updates. */
+tddft_status tddft_mlp_train(tddft_mlp *m, int64_t n, const float *X, const float *T, const float *w,
+                             int32_t steps, int32_t batch, float lr, const int64_t *order,
+                             double *loss_first, double *loss_last);
+/* n_b and n_f of the rows for this context's system (INVALID without equal per-atom counts). */
+tddft_status tddft_learned_dims(const tddft_ctx *ctx, int32_t *n_block, int32_t *n_feat);
+/* Bind the model used by TDDFT_PRECOND_LEARNED (NULL unbinds); the context does not own it and
+ * recomputes its block maps A_IJ whenever the model's parameters change. */
+tddft_status tddft_set_mlp(tddft_ctx *ctx, tddft_mlp *m);
+/* Training rows at the state's current iterate: inputs from its search gradient h, targets from
+ * the CG solve z = mask * Pinv(h) of Eq. precond, and row weights. X [count][n_b + n_f],
+ * T [count][n_b], w [count], device pointers, count = k natoms^2 (returned); cap smaller than
+ * count returns INVALID. */
+tddft_status tddft_samples(tddft_ctx *ctx, tddft_state *st, int64_t cap, float *X, float *T, float *w,
+                           int64_t *count);
+/* Counters of a state: PCG steps taken, steps where the learned direction fell back to the CG
+ * solve, and inner CG iterations summed over steps (any pointer may be NULL). */
+tddft_status tddft_state_stats(const tddft_state *st, int32_t *iters, int32_t *fallbacks,
+                               int64_t *inner_iters);
 
 /* Per-stage launch timing. tddft_profile(ctx, 1) clears the counters and starts recording a CUDA
  * event pair on the context's stream around every launch; tddft_profile(ctx, 0) stops. Stages:

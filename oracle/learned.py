@@ -6,26 +6,34 @@ CPU-baseline leg of the benchmark may import this module.
 
 The paper's preconditioner (Sec. III B, Eq. precond) is the approximate solution z of
 P^c H^chi z - z H^phi P^v = h for a gradient h, obtained by an inner CG. Its learned stand-in
-maps each atom block of h to the same block of z with a small network, one block at a time:
+maps each atom block of h to the same block of z with a linear map that a small network predicts
+from the block's fixed features, so the preconditioner stays linear in h (as the CG solve is):
 
 * Samples. For state i, chi-atom I and phi-atom J (functions grouped by atom, n_c chi and n_v phi
   per atom) the block h^p_IJ = h^p_i[I n_c : (I+1) n_c, J n_v : (J+1) n_v] and h^q_IJ likewise.
   With s = sqrt(|h^p_IJ|^2 + |h^q_IJ|^2) (Frobenius) the input row is
       x = [h^p_IJ / s, h^q_IJ / s, M^c_II, S^chi_II, M^v_JJ, S^phi_JJ, d_IJ / 10]
   (blocks flattened row-major; M^c = P^c H^chi, M^v = H^phi P^v, the two matrices of Eq.
-  precond; d_IJ the minimum-image distance of the two atoms in bohr), of length
-  n_in = 2 n_c n_v + 2 n_c^2 + 2 n_v^2 + 1, and the target row is y = [z^p_IJ / s, z^q_IJ / s]
-  (n_out = 2 n_c n_v). A block with s = 0 has a zero h part, and its z block is zero. Rows are
-  ordered (i, I, J) with J fastest.
-* Network. y = W3^T relu(W2^T relu(W1^T x + b1) + b2) + b3, i.e. in row form
-  H1 = relu(X W1 + b1), H2 = relu(H1 W2 + b2), Y = H2 W3 + b3, with W1 [n_in][w], W2 [w][w],
-  W3 [w][n_out]. The parameter vector is W1, b1, W2, b2, W3, b3, each row-major, concatenated.
-* Loss. L = sum (Y - T)^2 / (n n_out) over the n rows.
+  precond; d_IJ the minimum-image distance of the two atoms in bohr): the block part b of
+  n_b = 2 n_c n_v entries, then the feature part f of n_f = 2 n_c^2 + 2 n_v^2 + 1. The model
+  learns the correction to the identity map: the target row is
+  y = [(z^p_IJ - h^p_IJ) / s, (z^q_IJ - h^q_IJ) / s] (n_b entries)
+  and the row weight is w = s^2 / (sum of s^2 over the rows of the same state), the share of the
+  state's gradient norm that the block carries. A block with s = 0 has a zero h part, zero
+  weight, and its z block is zero. Rows are ordered (i, I, J) with J fastest.
+* Model. A 3-layer perceptron maps the features to an n_b x n_b matrix,
+  vec(A) = W3^T relu(W2^T relu(W1^T f + b1) + b2) + b3 (row form H1 = relu(F W1 + b1),
+  H2 = relu(H1 W2 + b2), vec(A) = H2 W3 + b3, W1 [n_f][w], W2 [w][w], W3 [w][n_b^2], A row-major),
+  and the output row is y = A b. The parameter vector is W1, b1, W2, b2, W3, b3, each row-major,
+  concatenated.
+* Loss. L = sum_r w_r sum_j (y_rj - T_rj)^2 / (n n_b) over the n rows (w = 1 without
+  weights), i.e. the weighted squared error of the z blocks themselves.
 * Adam (Kingma & Ba 2015): m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
   theta -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps), b1 = 0.9, b2 = 0.999, eps = 1e-8.
 * Inference uses the parameters rounded to bfloat16 (round to nearest, ties to even).
-* The map: z blocks = s * (network output of the block's x), then the kernel mask as for the
-  iterative preconditioner. Output scales with s, so the map is homogeneous of degree one in h.
+* The map: z_IJ = h_IJ + A_IJ h_IJ (blocks as vectors; s cancels), then the kernel mask as for
+  the iterative preconditioner. It is linear in h; an untrained network with small output is
+  close to the identity (no preconditioner).
 """
 import numpy as np
 
@@ -46,8 +54,9 @@ def block_dims(sys):
 
 
 def io_sizes(sys):
+    """(n_b, n_f): lengths of the block part and the feature part of a row."""
     nc, nv, _ = block_dims(sys)
-    return 2 * nc * nv + 2 * nc * nc + 2 * nv * nv + 1, 2 * nc * nv
+    return 2 * nc * nv, 2 * nc * nc + 2 * nv * nv + 1
 
 
 def atom_distances(sys):
@@ -89,8 +98,8 @@ class Features:
                     s.append(sc)
         return np.array(X), np.array(s)
 
-    def targets(self, zp, zq, s):
-        """Target rows T [k na na][n_out]: the z blocks divided by the scales of the h blocks."""
+    def targets(self, zp, zq, s, hp, hq):
+        """Target rows T [k na na][n_out]: (z - h) blocks divided by the scales of the h blocks."""
         nc, nv, na = self.nc, self.nv, self.na
         k = zp.shape[0]
         T = []
@@ -99,23 +108,32 @@ class Features:
             for I in range(na):
                 for J in range(na):
                     inv = 1.0 / s[q] if s[q] > 0.0 else 0.0
-                    T.append(np.concatenate([zp[i, I * nc:(I + 1) * nc, J * nv:(J + 1) * nv].ravel() * inv,
-                                             zq[i, I * nc:(I + 1) * nc, J * nv:(J + 1) * nv].ravel() * inv]))
+                    rows, cols = slice(I * nc, (I + 1) * nc), slice(J * nv, (J + 1) * nv)
+                    T.append(np.concatenate([(zp[i, rows, cols] - hp[i, rows, cols]).ravel() * inv,
+                                             (zq[i, rows, cols] - hq[i, rows, cols]).ravel() * inv]))
                     q += 1
         return np.array(T)
 
-    def scatter(self, Y, s, k):
-        """z^p, z^q [k][N_chi][N_phi] from output rows Y and block scales s."""
+    def weights(self, s, k):
+        """Row weights s^2 / (sum of s^2 over the rows of the same state)."""
+        s2 = np.asarray(s, dtype=np.float64).reshape(k, -1) ** 2
+        tot = s2.sum(axis=1, keepdims=True)
+        return np.where(tot > 0.0, s2 / np.where(tot > 0.0, tot, 1.0), 0.0).ravel()
+
+    def scatter(self, Y, s, hp, hq):
+        """z^p, z^q [k][N_chi][N_phi] = h + s * Y block by block."""
         nc, nv, na = self.nc, self.nv, self.na
-        zp = np.zeros((k, na * nc, na * nv))
-        zq = np.zeros_like(zp)
+        k = hp.shape[0]
+        zp = np.zeros_like(hp)
+        zq = np.zeros_like(hq)
         q = 0
         for i in range(k):
             for I in range(na):
                 for J in range(na):
                     y = Y[q] * s[q]
-                    zp[i, I * nc:(I + 1) * nc, J * nv:(J + 1) * nv] = y[:nc * nv].reshape(nc, nv)
-                    zq[i, I * nc:(I + 1) * nc, J * nv:(J + 1) * nv] = y[nc * nv:].reshape(nc, nv)
+                    rows, cols = slice(I * nc, (I + 1) * nc), slice(J * nv, (J + 1) * nv)
+                    zp[i, rows, cols] = hp[i, rows, cols] + y[:nc * nv].reshape(nc, nv)
+                    zq[i, rows, cols] = hq[i, rows, cols] + y[nc * nv:].reshape(nc, nv)
                     q += 1
         return zp, zq
 
@@ -135,30 +153,48 @@ def unpack(theta, n_in, w, n_out):
     return out
 
 
-def forward(theta, dims, X):
-    """Network output rows Y for input rows X; also the hidden activations (H1, H2)."""
+def mlp_dims(n_b, n_f, width):
+    """(inputs, width, outputs) of the perceptron inside the model."""
+    return n_f, width, n_b * n_b
+
+
+def mlp(theta, dims, F):
+    """vec(A) rows of the perceptron for feature rows F, and its hidden activations."""
     W1, b1, W2, b2, W3, b3 = unpack(theta, *dims)
-    H1 = np.maximum(X @ W1 + b1, 0.0)
+    H1 = np.maximum(F @ W1 + b1, 0.0)
     H2 = np.maximum(H1 @ W2 + b2, 0.0)
     return H2 @ W3 + b3, H1, H2
 
 
-def loss_grad(theta, dims, X, T):
-    """Mean-squared loss and its gradient with respect to the parameter vector (backpropagation
-    through the three layers; relu'(0) = 0)."""
+def forward(theta, n_b, width, X):
+    """Model output rows y = A(f) b for rows X = [b, f]; also A and the hidden activations."""
+    n_f = X.shape[1] - n_b
+    A, H1, H2 = mlp(theta, mlp_dims(n_b, n_f, width), X[:, n_b:])
+    Am = A.reshape(-1, n_b, n_b)
+    return np.einsum("rij,rj->ri", Am, X[:, :n_b]), Am, H1, H2
+
+
+def loss_grad(theta, n_b, width, X, T, w=None):
+    """Weighted mean-squared loss and its gradient with respect to the parameter vector
+    (through y = A b, then backpropagation through the three layers; relu'(0) = 0).
+    w: row weights (None = 1)."""
+    n_f = X.shape[1] - n_b
+    dims = mlp_dims(n_b, n_f, width)
     W1, b1, W2, b2, W3, b3 = unpack(theta, *dims)
-    Y, H1, H2 = forward(theta, dims, X)
-    n, n_out = Y.shape
-    R = Y - T
-    L = float(np.sum(R * R) / (n * n_out))
-    dY = 2.0 * R / (n * n_out)
+    Yb, Am, H1, H2 = forward(theta, n_b, width, X)
+    n = Yb.shape[0]
+    R = Yb - T
+    wr = np.ones(n) if w is None else np.asarray(w, dtype=np.float64)
+    L = float(np.sum(wr[:, None] * R * R) / (n * n_b))
+    dYb = 2.0 * wr[:, None] * R / (n * n_b)
+    dY = (dYb[:, :, None] * X[:, None, :n_b]).reshape(n, n_b * n_b)     # d vec(A)
     gW3 = H2.T @ dY
     gb3 = dY.sum(axis=0)
     dH2 = (dY @ W3.T) * (H2 > 0.0)
     gW2 = H1.T @ dH2
     gb2 = dH2.sum(axis=0)
     dH1 = (dH2 @ W2.T) * (H1 > 0.0)
-    gW1 = X.T @ dH1
+    gW1 = X[:, n_b:].T @ dH1
     gb1 = dH1.sum(axis=0)
     g = np.concatenate([a.ravel() for a in (gW1, gb1, gW2, gb2, gW3, gb3)])
     return L, g
@@ -182,19 +218,19 @@ def round_bf16(x):
 
 
 class LearnedPreconditioner:
-    """z = mask * s * net(x) block by block (inference with bfloat16-rounded parameters)."""
+    """z = mask * (h + A h) block by block (inference with bfloat16-rounded parameters)."""
 
     def __init__(self, sys, theta, width, mask):
         self.feat = Features(sys)
-        n_in, n_out = io_sizes(sys)
-        self.dims = (n_in, width, n_out)
-        if len(theta) != n_params(*self.dims):
+        self.n_b, n_f = io_sizes(sys)
+        self.width = width
+        if len(theta) != n_params(*mlp_dims(self.n_b, n_f, width)):
             raise ValueError("parameter vector has the wrong length")
         self.theta = round_bf16(theta)
         self.mask = mask
 
     def apply(self, hp, hq):
         X, s = self.feat.rows(hp, hq)
-        Y, _, _ = forward(self.theta, self.dims, X)
-        zp, zq = self.feat.scatter(Y, s, hp.shape[0])
+        Y, _, _, _ = forward(self.theta, self.n_b, self.width, X)
+        zp, zq = self.feat.scatter(Y, s, hp, hq)
         return zp * self.mask, zq * self.mask

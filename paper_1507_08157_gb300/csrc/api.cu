@@ -1,6 +1,7 @@
 // C ABI of libtddft: context construction, the batched full-TDDFT operator (Eq. operator_RPA)
 // and the preconditioned CG eigensolver of Sec. III C, orchestrated on one CUDA stream.
 #include "tddft.h"
+#include "learned.h"
 #include "solver_kernels.h"
 #include "tddft_internal.h"
 
@@ -39,28 +40,6 @@ struct TimeoutErr {
     std::string msg;
 };
 
-// owning list of device allocations
-struct Mem {
-    std::vector<void *> ptrs;
-    template <typename T>
-    T *alloc(size_t n) {
-        void *p = nullptr;
-        if (n == 0) n = 1;
-        cudaError_t e = cudaMalloc(&p, n * sizeof(T));
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            throw std::bad_alloc();
-        }
-        ptrs.push_back(p);
-        return static_cast<T *>(p);
-    }
-    void release() {
-        for (void *p : ptrs) cudaFree(p);
-        ptrs.clear();
-    }
-    ~Mem() { release(); }
-};
-
 bool is_device_ptr(const void *p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -90,7 +69,13 @@ struct Impl {
     T *rho = nullptr, *V = nullptr, *Vmat = nullptr, *tmp = nullptr, *bufP = nullptr, *bufF = nullptr;
     void *fft = nullptr;
     double *stage = nullptr;
-    double *gscratch = nullptr;
+    // learned preconditioner: per-atom features, feature rows of the na^2 blocks and their maps A
+    // (lmemf); block scales for `lrows` sample rows (lmemr)
+    Mem lmemf, lmemr;
+    long long lrows = 0;
+    float *lfc = nullptr, *lfv = nullptr, *ldist = nullptr, *lF = nullptr, *lA = nullptr, *ls = nullptr;
+    const tddft_mlp *lA_model = nullptr;
+    long long lA_version = -1;
 };
 
 }  // namespace
@@ -109,6 +94,11 @@ struct tddft_ctx {
     Profiler *prof = nullptr;
     bool prof_on = false;
     std::vector<uint8_t> amask;
+    // equal per-atom function counts (atom-major order) for the learned preconditioner
+    bool uniform = false;
+    int nca = 0, nva = 0;
+    std::vector<float> adist;     // [natoms][natoms] minimum-image distance / 10 bohr
+    tddft_mlp *mlp = nullptr;
     std::string err;
     std::unique_ptr<Impl<double>> d64;
     std::unique_ptr<Impl<float>> d32;
@@ -344,7 +334,6 @@ void ensure_workspace(tddft_ctx *c, Impl<T> &I, int states) {
     I.bufP = I.wmem.template alloc<T>((size_t)states * len);
     I.bufF = I.wmem.template alloc<T>((size_t)states * len);
     I.stage = I.wmem.template alloc<double>((size_t)std::max<long long>(states * len, states * n3));
-    I.gscratch = I.wmem.template alloc<double>((size_t)gram_scratch_doubles(64, 32));
     I.tc_bits = I.wmem.template alloc<unsigned>((size_t)states);
     I.tc_scale = I.wmem.template alloc<float>((size_t)states);
     I.cap = states;
@@ -539,6 +528,8 @@ struct tddft_state {
     tddft_ctx *ctx = nullptr;
     int k = 0;
     int it = 0;
+    int fallbacks = 0;             // learned steps that took the CG solve instead
+    long long inner_iters = 0;     // inner CG iterations over all steps
     bool evaluated = false;
     bool have_prev_omega = false;
     std::vector<double> omega, resid, omega_prev;
@@ -717,6 +708,7 @@ void precondition(tddft_ctx *c, tddft_state *S, const T *h, T *z) {
         check(cudaMemcpyAsync(hn, B.cg_nactive, sizeof(int), cudaMemcpyDeviceToHost, st), "D2H n_active");
         check(cudaStreamSynchronize(st), "sync cg");
         if (*hn == 0) break;
+        S->inner_iters += 1;
         gemm<T>(st, false, false, nc, nv, nc, T(1), I.Mc, nc, 0, p, nv, len, T(0), Lp, nv, len, k2);
         gemm<T>(st, false, false, k2 * nc, nv, nv, T(-1), p, nv, 0, I.Mv, nv, 0, T(1), Lp, nv, 0, 1);
         covariant<T>(c, I, k2, Lp, cLp, B.tmp);
@@ -734,6 +726,64 @@ void precondition(tddft_ctx *c, tddft_state *S, const T *h, T *z) {
     }
 }
 
+// learned preconditioner: fixed features and feature rows on first use; scales for k states
+template <typename T>
+void ensure_learned(tddft_ctx *c, Impl<T> &I, int k) {
+    if (!c->uniform) throw InvalidArg{"the learned preconditioner needs equal function counts on every atom"};
+    const int na = c->natoms;
+    if (!I.lfc) {
+        const int nb = 2 * c->nca * c->nva, nf = 2 * c->nca * c->nca + 2 * c->nva * c->nva + 1;
+        I.lfc = I.lmemf.template alloc<float>((size_t)na * 2 * c->nca * c->nca);
+        I.lfv = I.lmemf.template alloc<float>((size_t)na * 2 * c->nva * c->nva);
+        I.ldist = I.lmemf.template alloc<float>((size_t)na * na);
+        I.lF = I.lmemf.template alloc<float>((size_t)na * na * nf);
+        I.lA = I.lmemf.template alloc<float>((size_t)na * na * nb * nb);
+        check(cudaMemcpyAsync(I.ldist, c->adist.data(), (size_t)na * na * sizeof(float), cudaMemcpyHostToDevice,
+                              c->st),
+              "upload atom distances");
+        learned_fixed_features<T>(c->st, I.Mc, I.Sc, c->nc, c->nca, na, I.lfc);
+        learned_fixed_features<T>(c->st, I.Mv, I.Sv, c->nv, c->nva, na, I.lfv);
+        learned_feature_rows(c->st, I.lfc, I.lfv, I.ldist, na, c->nca, c->nva, I.lF);
+        check(cudaStreamSynchronize(c->st), "sync learned features");
+    }
+    const long long rows = (long long)k * na * na;
+    if (rows <= I.lrows) return;
+    check(cudaStreamSynchronize(c->st), "sync before learned buffers");
+    I.lmemr.release();
+    I.ls = I.lmemr.template alloc<float>((size_t)rows);
+    I.lrows = rows;
+}
+
+// z_IJ = h_IJ + A_IJ h_IJ with the block maps of the bound model (recomputed when it changes)
+template <typename T>
+void learned_precondition(tddft_ctx *c, tddft_state *S, const T *h, T *z) {
+    Impl<T> &I = impl<T>(c);
+    const int k = S->k, na = c->natoms;
+    if (!c->mlp) throw InvalidArg{"TDDFT_PRECOND_LEARNED without a model (tddft_set_mlp)"};
+    if (mlp_n_block(c->mlp) != 2 * c->nca * c->nva ||
+        mlp_n_feat(c->mlp) != 2 * c->nca * c->nca + 2 * c->nva * c->nva + 1)
+        throw InvalidArg{"model sizes do not match the system's rows (tddft_learned_dims)"};
+    ensure_learned<T>(c, I, k);
+    if (I.lA_model != c->mlp || I.lA_version != mlp_version(c->mlp)) {
+        mlp_block_maps(c->st, c->mlp, (long long)na * na, I.lF, I.lA);
+        I.lA_model = c->mlp;
+        I.lA_version = mlp_version(c->mlp);
+    }
+    learned_apply<T>(c->st, I.lA, h, k, na, c->nca, c->nva, c->nc, c->nv, z);
+}
+
+// the gradient the preconditioner acts on: g, or P^c G_L P^v with truncation
+template <typename T>
+const T *search_gradient(tddft_ctx *c, tddft_state *S) {
+    Impl<T> &I = impl<T>(c);
+    StateBufs<T> &B = bufs<T>(S);
+    if (c->trunc) {
+        sandwich<T>(c, 2 * S->k, I.Pc, B.G1, I.Pv, B.h, B.tmp);   // P^c G_L P^v
+        return B.h;
+    }
+    return B.g;
+}
+
 // one PCG update from an evaluated iterate (Sec. III C)
 template <typename T>
 void update(tddft_ctx *c, tddft_state *S) {
@@ -743,23 +793,35 @@ void update(tddft_ctx *c, tddft_state *S) {
     const long long len = c->len(), tot = k2 * len;
     cudaStream_t st = c->st;
     // preconditioned gradient in the search variables
-    const T *h = B.g;
-    if (c->trunc) {
-        sandwich<T>(c, k2, I.Pc, B.G1, I.Pv, B.h, B.tmp);   // P^c G_L P^v
-        h = B.h;
-    }
-    precondition<T>(c, S, h, B.z);
-    if (c->trunc) mask_mul<T>(st, B.z, I.mask, len, k2);
-    sandwich<T>(c, k2, I.Rc, B.z, I.Rv, B.Z, B.tmp);         // Z = P^c S z S P^v (Eq. auxiliary)
-    // Polak-Ribiere over the set
-    if (c->trunc) {
-        dots<T>(st, B.G1, len, B.z, len, k2, len, B.dvec, B.gscr);
-        dots<T>(st, B.G1, len, B.pz, len, k2, len, B.dvec2, B.gscr);
-        dots<T>(st, B.G1, len, B.pdir, len, k2, len, B.dvec3, B.gscr);
-    } else {
-        dots<T>(st, B.G1, len, B.Z, len, k2, len, B.dvec, B.gscr);
-        dots<T>(st, B.G1, len, B.pZ, len, k2, len, B.dvec2, B.gscr);
-        dots<T>(st, B.G1, len, B.pD, len, k2, len, B.dvec3, B.gscr);
+    const T *h = search_gradient<T>(c, S);
+    auto precondition_and_dots = [&](bool learned) {
+        if (learned) learned_precondition<T>(c, S, h, B.z);
+        else precondition<T>(c, S, h, B.z);
+        if (c->trunc) mask_mul<T>(st, B.z, I.mask, len, k2);
+        sandwich<T>(c, k2, I.Rc, B.z, I.Rv, B.Z, B.tmp);     // Z = P^c S z S P^v (Eq. auxiliary)
+        // Polak-Ribiere over the set
+        if (c->trunc) {
+            dots<T>(st, B.G1, len, B.z, len, k2, len, B.dvec, B.gscr);
+            dots<T>(st, B.G1, len, B.pz, len, k2, len, B.dvec2, B.gscr);
+            dots<T>(st, B.G1, len, B.pdir, len, k2, len, B.dvec3, B.gscr);
+        } else {
+            dots<T>(st, B.G1, len, B.Z, len, k2, len, B.dvec, B.gscr);
+            dots<T>(st, B.G1, len, B.pZ, len, k2, len, B.dvec2, B.gscr);
+            dots<T>(st, B.G1, len, B.pD, len, k2, len, B.dvec3, B.gscr);
+        }
+    };
+    const bool learned = c->opt.precond == TDDFT_PRECOND_LEARNED;
+    precondition_and_dots(learned);
+    if (learned) {
+        // the CG solve stands in when -z is not a descent direction (<g, Z> summed <= 0)
+        check(cudaMemcpyAsync(S->host, B.dvec, k2 * sizeof(double), cudaMemcpyDeviceToHost, st), "D2H gz");
+        check(cudaStreamSynchronize(st), "sync gz");
+        double gz = 0.0;
+        for (int i = 0; i < k2; ++i) gz += S->host[i];
+        if (!(gz > 0.0)) {
+            S->fallbacks += 1;
+            precondition_and_dots(false);
+        }
     }
     const int restart = (S->it == 0 || S->it % std::max(1, c->opt.restart_every) == 0) ? 1 : 0;
     conj_coeff(st, k2, B.dvec, B.dvec2, B.dvec3, restart, B.flip, B.sc);
@@ -899,6 +961,7 @@ tddft_status tddft_create(const tddft_system *s, const tddft_options *opt, void 
         if (!s) throw InvalidArg{"null system"};
         if (c->prec != TDDFT_FP64 && c->prec != TDDFT_MIXED) throw InvalidArg{"unknown precision"};
         if (c->opt.mode < 0 || c->opt.mode > 2) throw InvalidArg{"unknown mode"};
+        if (c->opt.precond < 0 || c->opt.precond > 2) throw InvalidArg{"unknown preconditioner"};
         if (!(s->cell > 0.0)) throw InvalidArg{"cell must be positive"};
         if (!fft_size_ok(s->n)) throw InvalidArg{"grid size must be 2^a 3^b 5^c with 8 <= n <= 256"};
         if (s->natoms <= 0 || !s->pos) throw InvalidArg{"no atoms"};
@@ -915,6 +978,25 @@ tddft_status tddft_create(const tddft_system *s, const tddft_options *opt, void 
         const double h = s->cell / s->n;
         c->dV = h * h * h;
         c->trunc = s->kernel_cutoff > 0.0;
+        // per-atom function counts and atom distances (learned preconditioner)
+        c->uniform = s->chi.nfun % s->natoms == 0 && s->phi.nfun % s->natoms == 0;
+        if (c->uniform) {
+            c->nca = s->chi.nfun / s->natoms;
+            c->nva = s->phi.nfun / s->natoms;
+            for (int f = 0; f < s->chi.nfun && c->uniform; ++f) c->uniform = s->chi.atom[f] == f / c->nca;
+            for (int f = 0; f < s->phi.nfun && c->uniform; ++f) c->uniform = s->phi.atom[f] == f / c->nva;
+        }
+        c->adist.assign((size_t)s->natoms * s->natoms, 0.0f);
+        for (int a = 0; a < s->natoms; ++a)
+            for (int b = 0; b < s->natoms; ++b) {
+                double d2 = 0.0;
+                for (int x = 0; x < 3; ++x) {
+                    double d = s->pos[3 * a + x] - s->pos[3 * b + x];
+                    d -= s->cell * std::nearbyint(d / s->cell);
+                    d2 += d * d;
+                }
+                c->adist[(size_t)a * s->natoms + b] = (float)(std::sqrt(d2) / 10.0);
+            }
         c->amask.assign((size_t)s->natoms * s->natoms, 1);
         if (c->trunc) {
             for (int a = 0; a < s->natoms; ++a)
@@ -1170,6 +1252,58 @@ tddft_status tddft_response_density_noalloc(tddft_ctx *c, int32_t k, const float
             throw TimeoutErr{"a bounded wait in the density kernel expired"};
         return TDDFT_OK;
     });
+}
+
+tddft_status tddft_learned_dims(const tddft_ctx *c, int32_t *n_block, int32_t *n_feat) {
+    if (!c) return TDDFT_E_INVALID;
+    if (!c->uniform) {
+        const_cast<tddft_ctx *>(c)->err = "the learned preconditioner needs equal function counts on every atom";
+        return TDDFT_E_INVALID;
+    }
+    if (n_block) *n_block = 2 * c->nca * c->nva;
+    if (n_feat) *n_feat = 2 * c->nca * c->nca + 2 * c->nva * c->nva + 1;
+    return TDDFT_OK;
+}
+
+tddft_status tddft_set_mlp(tddft_ctx *c, tddft_mlp *m) {
+    if (!c) return TDDFT_E_INVALID;
+    c->mlp = m;
+    return TDDFT_OK;
+}
+
+tddft_status tddft_samples(tddft_ctx *c, tddft_state *S, int64_t cap, float *X, float *Tg, float *Wt,
+                           int64_t *count) {
+    if (!c || !S || S->ctx != c || !X || !Tg || !Wt) return TDDFT_E_INVALID;
+    return guarded(c, [&]() -> tddft_status {
+        if (!c->uniform) throw InvalidArg{"the learned preconditioner needs equal function counts on every atom"};
+        const long long rows = (long long)S->k * c->natoms * c->natoms;
+        if (count) *count = rows;
+        if (cap < rows) throw InvalidArg{"tddft_samples: cap smaller than k * natoms^2"};
+        if (!is_device_ptr(X) || !is_device_ptr(Tg) || !is_device_ptr(Wt))
+            throw InvalidArg{"tddft_samples: X, T and w must be device pointers"};
+        return DISPATCH(c, ([&]() {
+            Impl<T> &I = impl<T>(c);
+            StateBufs<T> &B = bufs<T>(S);
+            const int k = S->k, k2 = 2 * k, na = c->natoms;
+            if (!S->evaluated) evaluate<T>(c, S);
+            ensure_learned<T>(c, I, k);
+            const T *h = search_gradient<T>(c, S);
+            precondition<T>(c, S, h, B.z);
+            if (c->trunc) mask_mul<T>(c->st, B.z, I.mask, c->len(), k2);
+            learned_features<T>(c->st, h, k, na, c->nca, c->nva, c->nc, c->nv, I.lfc, I.lfv, I.ldist, X, I.ls);
+            learned_targets<T>(c->st, B.z, h, I.ls, k, na, c->nca, c->nva, c->nc, c->nv, Tg, Wt);
+            check(cudaStreamSynchronize(c->st), "sync samples");
+            return TDDFT_OK;
+        })());
+    });
+}
+
+tddft_status tddft_state_stats(const tddft_state *S, int32_t *iters, int32_t *fallbacks, int64_t *inner_iters) {
+    if (!S) return TDDFT_E_INVALID;
+    if (iters) *iters = S->it;
+    if (fallbacks) *fallbacks = S->fallbacks;
+    if (inner_iters) *inner_iters = S->inner_iters;
+    return TDDFT_OK;
 }
 
 tddft_status tddft_pattern(const tddft_ctx *c, uint8_t *mask) {

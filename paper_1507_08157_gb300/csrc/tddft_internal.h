@@ -4,7 +4,9 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <new>
 #include <string>
+#include <vector>
 
 namespace tddft {
 
@@ -14,6 +16,28 @@ constexpr int TILE_PTS = TILE * TILE * TILE;
 struct CudaError {
     cudaError_t code;
     std::string where;
+};
+
+// owning list of device allocations (freed on release or destruction)
+struct Mem {
+    std::vector<void *> ptrs;
+    template <typename T>
+    T *alloc(size_t n) {
+        void *p = nullptr;
+        if (n == 0) n = 1;
+        cudaError_t e = cudaMalloc(&p, n * sizeof(T));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            throw std::bad_alloc();
+        }
+        ptrs.push_back(p);
+        return static_cast<T *>(p);
+    }
+    void release() {
+        for (void *p : ptrs) cudaFree(p);
+        ptrs.clear();
+    }
+    ~Mem() { release(); }
 };
 
 void check(cudaError_t e, const char *where);   // throws CudaError on failure

@@ -22,7 +22,7 @@ OK, E_INVALID, E_NOMEM, E_CUDA, E_NOT_CONVERGED, E_BREAKDOWN, E_TIMEOUT, E_PAIRI
 FP64, MIXED = 0, 1
 NOALLOC_MAX_STATES = 64        # TDDFT_NOALLOC_MAX_STATES of the header
 MODE = {"full": 0, "tda": 1, "d_only": 2}
-PRECOND = {"none": 0, "iter": 1}
+PRECOND = {"none": 0, "iter": 1, "learned": 2}
 FXC = {"none": 0, "lda": 1}
 
 c_double_p = ctypes.POINTER(ctypes.c_double)
@@ -63,7 +63,10 @@ SYMBOLS = sorted(["tddft_default_options", "tddft_create", "tddft_destroy", "tdd
                   "tddft_potential_integrals", "tddft_fxc", "tddft_state_create",
                   "tddft_state_destroy", "tddft_pcg_step", "tddft_solve", "tddft_state_get",
                   "tddft_subspace", "tddft_pattern", "tddft_profile", "tddft_profile_read",
-                  "tddft_work"])
+                  "tddft_work", "tddft_mlp_create", "tddft_mlp_destroy", "tddft_mlp_last_error",
+                  "tddft_mlp_size", "tddft_mlp_set", "tddft_mlp_get", "tddft_mlp_forward",
+                  "tddft_mlp_loss_grad", "tddft_mlp_train", "tddft_learned_dims", "tddft_set_mlp",
+                  "tddft_samples", "tddft_state_stats"])
 
 _lib = None
 _live = weakref.WeakSet()      # open contexts and states, closed before interpreter shutdown
@@ -114,11 +117,31 @@ def load(path: str = LIB_PATH):
     lib.tddft_profile.argtypes = [vp, ctypes.c_int32]
     lib.tddft_profile_read.argtypes = [vp, ctypes.POINTER(StageStats), ctypes.c_int32, c_int32_p]
     lib.tddft_work.argtypes = [vp, c_double_p, c_double_p]
+    i64 = ctypes.c_int64
+    lib.tddft_mlp_create.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(vp)]
+    lib.tddft_mlp_destroy.argtypes = [vp]
+    lib.tddft_mlp_destroy.restype = None
+    lib.tddft_mlp_last_error.argtypes = [vp]
+    lib.tddft_mlp_last_error.restype = ctypes.c_char_p
+    lib.tddft_mlp_size.argtypes = [vp]
+    lib.tddft_mlp_size.restype = i64
+    lib.tddft_mlp_set.argtypes = [vp, vp]
+    lib.tddft_mlp_get.argtypes = [vp, vp]
+    lib.tddft_mlp_forward.argtypes = [vp, i64, vp, vp]
+    lib.tddft_mlp_loss_grad.argtypes = [vp, i64, vp, vp, vp, c_double_p, vp]
+    lib.tddft_mlp_train.argtypes = [vp, i64, vp, vp, vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, vp,
+                                    c_double_p, c_double_p]
+    lib.tddft_learned_dims.argtypes = [vp, c_int32_p, c_int32_p]
+    lib.tddft_set_mlp.argtypes = [vp, vp]
+    lib.tddft_samples.argtypes = [vp, vp, i64, vp, vp, vp, ctypes.POINTER(i64)]
+    lib.tddft_state_stats.argtypes = [vp, c_int32_p, c_int32_p, ctypes.POINTER(i64)]
     for name in ("tddft_create", "tddft_dims", "tddft_apply", "tddft_response_density",
                  "tddft_response_potential", "tddft_potential_integrals", "tddft_fxc",
                  "tddft_state_create", "tddft_pcg_step", "tddft_solve", "tddft_state_get",
                  "tddft_subspace", "tddft_pattern", "tddft_profile", "tddft_profile_read",
-                 "tddft_work"):
+                 "tddft_work", "tddft_mlp_create", "tddft_mlp_set", "tddft_mlp_get", "tddft_mlp_forward",
+                 "tddft_mlp_loss_grad", "tddft_mlp_train", "tddft_learned_dims", "tddft_set_mlp",
+                 "tddft_samples", "tddft_state_stats"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -296,6 +319,31 @@ class Context:
         return {buf[i].name.decode(): (int(buf[i].launches), buf[i].ms, buf[i].flops, buf[i].bytes)
                 for i in range(n.value)}
 
+    # -- learned atom-block preconditioner ---------------------------------------------------------
+    def learned_dims(self):
+        """(n_b, n_f): block and feature lengths of the learned preconditioner's rows."""
+        a, b = ctypes.c_int32(), ctypes.c_int32()
+        self._check(self._lib.tddft_learned_dims(self._ctx, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def set_mlp(self, mlp):
+        """Bind the model used by precond="learned" (None unbinds)."""
+        self._mlp = mlp
+        self._check(self._lib.tddft_set_mlp(self._ctx, mlp._m if mlp is not None else None))
+
+    def samples(self, state):
+        """Training rows (X, T, w) at the state's iterate, as float32 CUDA tensors."""
+        import torch
+        n_b, n_f = self.learned_dims()
+        rows = state.k * self.sys.natoms ** 2
+        X = torch.empty((rows, n_b + n_f), dtype=torch.float32, device="cuda")
+        T = torch.empty((rows, n_b), dtype=torch.float32, device="cuda")
+        w = torch.empty((rows,), dtype=torch.float32, device="cuda")
+        cnt = ctypes.c_int64(0)
+        self._check(self._lib.tddft_samples(self._ctx, state._st, rows, X.data_ptr(), T.data_ptr(),
+                                            w.data_ptr(), ctypes.byref(cnt)))
+        return X, T, w
+
     def work(self):
         """(pair_points, table_values): algorithmic work of the grid contractions."""
         a, b = ctypes.c_double(), ctypes.c_double()
@@ -349,7 +397,99 @@ class State:
             self.ctx._ctx, self._st, *(_ptr(out[n]) for n in ("Pp", "Pq", "fp", "fq", "Lp", "Lq"))))
         return out
 
+    def stats(self):
+        """(PCG steps, learned-to-CG fallbacks, inner CG iterations)."""
+        a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        self.ctx._check(self.ctx._lib.tddft_state_stats(self._st, ctypes.byref(a), ctypes.byref(b),
+                                                        ctypes.byref(c)))
+        return a.value, b.value, c.value
+
     def subspace(self):
         om, pr = np.empty(self.k), np.empty(2 * self.k)
         self.ctx._check(self.ctx._lib.tddft_subspace(self.ctx._ctx, self._st, _ptr(om), _ptr(pr)))
         return om, pr.reshape(self.k, 2)
+
+
+class Mlp:
+    """The model of the learned preconditioner (tddft_mlp_*): features (n_f) -> width -> width ->
+    an n_b x n_b map A, applied to the block part of each row. Rows and targets are float32 CUDA
+    tensors; parameters move as float32 numpy vectors."""
+
+    def __init__(self, n_block, n_feat, width):
+        lib = load()
+        self._lib = lib
+        m = ctypes.c_void_p()
+        rc = lib.tddft_mlp_create(n_block, n_feat, width, ctypes.byref(m))
+        if rc != OK:
+            raise TddftError(rc, "tddft_mlp_create failed")
+        self._m = m
+        self.n_block, self.n_feat, self.width = n_block, n_feat, width
+        self.n_in = n_block + n_feat
+        self.size = int(lib.tddft_mlp_size(m))
+        _live.add(self)
+
+    def close(self):
+        if getattr(self, "_m", None):
+            self._lib.tddft_mlp_destroy(self._m)
+            self._m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != OK:
+            raise TddftError(rc, self._lib.tddft_mlp_last_error(self._m).decode())
+
+    @staticmethod
+    def _dev(a, cols):
+        import torch
+        if not (a.is_cuda and a.dtype == torch.float32 and a.is_contiguous() and a.shape[1] == cols):
+            raise ValueError(f"expected a contiguous float32 CUDA tensor with {cols} columns")
+        return a.data_ptr()
+
+    def set(self, theta):
+        theta = np.ascontiguousarray(theta, dtype=np.float32)
+        if theta.size != self.size:
+            raise ValueError("parameter vector has the wrong length")
+        self._check(self._lib.tddft_mlp_set(self._m, theta.ctypes.data))
+
+    def get(self):
+        out = np.empty(self.size, dtype=np.float32)
+        self._check(self._lib.tddft_mlp_get(self._m, out.ctypes.data))
+        return out
+
+    def forward(self, X):
+        import torch
+        Y = torch.empty((X.shape[0], self.n_block), dtype=torch.float32, device=X.device)
+        self._check(self._lib.tddft_mlp_forward(self._m, X.shape[0], self._dev(X, self.n_in), Y.data_ptr()))
+        return Y
+
+    @staticmethod
+    def _weights(w, n):
+        import torch
+        if w is None:
+            return None
+        if not (w.is_cuda and w.dtype == torch.float32 and w.is_contiguous() and w.numel() == n):
+            raise ValueError("row weights must be a contiguous float32 CUDA tensor of n entries")
+        return w.data_ptr()
+
+    def loss_grad(self, X, T, w=None):
+        loss = ctypes.c_double()
+        g = np.empty(self.size, dtype=np.float32)
+        self._check(self._lib.tddft_mlp_loss_grad(self._m, X.shape[0], self._dev(X, self.n_in),
+                                                  self._dev(T, self.n_block), self._weights(w, X.shape[0]),
+                                                  ctypes.byref(loss), g.ctypes.data))
+        return loss.value, g
+
+    def train(self, X, T, steps, batch, lr, order, w=None):
+        order = np.ascontiguousarray(order, dtype=np.int64)
+        if order.size < steps * batch:
+            raise ValueError("order holds fewer than steps * batch indices")
+        a, b = ctypes.c_double(), ctypes.c_double()
+        self._check(self._lib.tddft_mlp_train(self._m, X.shape[0], self._dev(X, self.n_in),
+                                              self._dev(T, self.n_block), self._weights(w, X.shape[0]), steps,
+                                              batch, lr, order.ctypes.data, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
