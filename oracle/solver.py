@@ -279,14 +279,15 @@ class PCG:
 
     def samples(self):
         """Training rows of the learned preconditioner at the current iterate: inputs from the
-        search gradient h, targets from the iterative preconditioner's z = mask * Pinv(h)."""
+        search gradient h, targets from the iterative preconditioner's z = mask * Pinv(h), and
+        the row weights."""
         from .learned import Features
         Q, omega, gp, gq, res = self.evaluate()
         hp, hq = self.search_gradient(gp, gq)
         zp, zq = self.iterative_z(hp, hq)
         feat = Features(self.op.sys)
         X, s = feat.rows(hp, hq)
-        return X, feat.targets(zp, zq, s)
+        return X, feat.targets(zp, zq, s, hp, hq), feat.weights(s, self.k)
 
     def update(self, Q, omega, gp, gq):
         k = self.k
