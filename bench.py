@@ -172,6 +172,80 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def c1_density_recipe(natoms, seed):
+    """Config-1 recipe (4 phi + 4 chi per atom, 7 A radius, 1/3 A grid) at its atom density,
+    the cubic cell grown with the atom count; the grid is the next 2/3/5-smooth size."""
+    cell = 16.0 * (natoms / 8.0) ** (1.0 / 3.0)
+    n = int(np.ceil(cell * 3.0))
+    while not _smooth(n):
+        n += 1
+    from paper_1507_08157_gb300 import synthetic as sy
+    return sy.Recipe(natoms=natoms, cell_ang=cell, ngrid=n, nphi=4, nchi=4, radius_ang=7.0, seed=seed)
+
+
+def _smooth(n):
+    for p in (2, 3, 5):
+        while n % p == 0:
+            n //= p
+    return n == 1
+
+
+def learned_vs_plain(tddft, sy, torch, stream, k=10, train_atoms=16, eval_atoms=24, tol=1e-5):
+    rows = ([], [], [])
+    for seed in (31, 32):
+        s = sy.generate(c1_density_recipe(train_atoms, seed))
+        c = tddft.Context(s, precision="fp64", stream=stream.cuda_stream)
+        st = c.state(sy.initial_guess(s, k, seed))
+        for it in range(30):
+            st.step()
+            if it % 3 == 2:
+                for acc, t in zip(rows, c.samples(st)):
+                    acc.append(t)
+        st.close()
+        c.close()
+    X, T, W = (torch.cat(a).contiguous() for a in rows)
+    n_b = T.shape[1]
+    n_f = X.shape[1] - n_b
+    net = tddft.Mlp(n_b, n_f, 256)
+    net.set(sy.mlp_init(n_f, 256, n_b * n_b, 33))
+    steps, batch = 2000, 512
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    l0, l1 = net.train(X, T, steps, batch, 1e-3, sy.minibatch_order(X.shape[0], steps, batch, 34), W)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    s = sy.generate(c1_density_recipe(eval_atoms, 35))
+    Y0 = sy.initial_guess(s, k, 35)
+    out = {}
+    for pre in ("iter", "learned", "none"):
+        c = tddft.Context(s, precision="fp64", precond=pre, tol=tol, max_iter=1000, stream=stream.cuda_stream)
+        if pre == "learned":
+            c.set_mlp(net)
+        st = c.state(Y0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        om, res, it, rc = st.solve()
+        torch.cuda.synchronize()
+        out[pre] = {"s": time.perf_counter() - t0, "iterations": it, "status": int(rc),
+                    "omega_Ha": [float(x) for x in om], "stats": st.stats()}
+        st.close()
+        c.close()
+    net.close()
+    dw = max(abs(a - b) for a, b in zip(out["learned"]["omega_Ha"], out["iter"]["omega_Ha"]))
+    r = s.recipe
+    return {"workload": f"c1-density systems: train 2 x {train_atoms} atoms ({X.shape[0]} rows, {steps} Adam "
+                        f"steps of {batch}), evaluate an unseen {eval_atoms}-atom system, "
+                        f"{r.cell_ang:.1f} A cell, {r.ngrid}^3 grid, 4 phi + 4 chi per atom",
+            "k": k, "precision": "fp64", "tol_Ha": tol,
+            "plain_pcg_s": out["iter"]["s"], "plain_iterations": out["iter"]["iterations"],
+            "plain_inner_cg_iterations": out["iter"]["stats"][2],
+            "learned_pcg_s": out["learned"]["s"], "learned_iterations": out["learned"]["iterations"],
+            "learned_fallbacks": out["learned"]["stats"][1],
+            "unpreconditioned_s": out["none"]["s"], "unpreconditioned_iterations": out["none"]["iterations"],
+            "status": [out[p]["status"] for p in ("iter", "learned", "none")],
+            "max_domega_learned_vs_plain_Ha": dw, "train_s": train_s, "train_loss": [l0, l1]}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -282,22 +356,12 @@ def run_ours(args):
     stages = {n: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / max(ms, 1e-9), 4)}
               for n, v in prof.items() if v[0]}
 
-    # time to k states with plain PCG on the small-8 workload (lowest state, FP64, 1e-6 Ha)
+    # time to k states at 1e-5 Ha, learned vs plain PCG (FP64): the model is trained on rows from
+    # plain-PCG runs on two systems of the small workload's recipe and density, then both solvers
+    # start from the same vectors on an unseen, larger system
     time_to_k = None
     if rank == 0 and not args.no_time_to_k:
-        s8 = sy.generate(sy.CONFIG_SMALL)
-        c8 = tddft.Context(s8, precision="fp64", tol=1e-6, max_iter=500, stream=stream.cuda_stream)
-        st8 = c8.state(sy.initial_guess(s8, 1, 0))
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        om8, res8, it8, rc8 = st8.solve()
-        torch.cuda.synchronize()
-        time_to_k = {"workload": "small-8: 8 atoms, 16 A cell, 48^3 grid, 4 phi + 4 chi per atom, no truncation",
-                     "k": 1, "precision": "fp64", "tol_Ha": 1e-6, "plain_pcg_s": time.perf_counter() - t0,
-                     "iterations": it8, "omega_Ha": float(om8[0]), "status": int(rc8),
-                     "learned_pcg_s": None}
-        st8.close()
-        c8.close()
+        time_to_k = learned_vs_plain(tddft, sy, torch, stream)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
