@@ -61,6 +61,7 @@ struct Impl {
     unsigned short *chi_fm16 = nullptr;   // function-major f16 chi tables [slot][512]
     int CK = 0, NPmax = 0, nslots_chi = 0, maxc = 0;
     bool grid_tc = false, integrals_tc = false;
+    bool phi_quads = false;   // every tile's phi list is whole aligned groups of 4 (vector gather)
     unsigned *tc_bits = nullptr;
     float *tc_scale = nullptr;
     // operator workspace, sized for up to `cap` grid states
@@ -123,7 +124,7 @@ void potential_integrals_tc(cudaStream_t st, const GridShape &g, const TileSet<f
 void response_density_tc(cudaStream_t st, const GridShape &g, const TileSet<float> &chi,
                          const TileSet<float> &phi, const unsigned short *chi_pm, int CK, int NPmax, int nphi,
                          const float *P, long long sP, int k, float *rho, unsigned *scratch_bits,
-                         float *scale, int *err);
+                         float *scale, int *err, bool phi_quads);
 int noalloc_max_states();
 void response_density_tc_noalloc(cudaStream_t st, const GridShape &g, const TileSet<float> &chi,
                                  const TileSet<float> &phi, const unsigned short *chi_pm, int CK, int NPmax,
@@ -346,7 +347,7 @@ void density(tddft_ctx *c, Impl<T> &I, const T *P, int ns) {
     if constexpr (sizeof(T) == 4) {
         if (I.grid_tc) {
             response_density_tc(c->st, c->grid(), I.chi, I.phi, I.chi_pm, I.CK, I.NPmax, c->nv, P, c->len(), ns,
-                                I.rho, I.tc_bits, I.tc_scale, tc_error_word());
+                                I.rho, I.tc_bits, I.tc_scale, tc_error_word(), I.phi_quads);
             return;
         }
     }
@@ -431,6 +432,22 @@ void build_impl(tddft_ctx *c, const tddft_system *s) {
                 I->CK = CK;
                 I->NPmax = NP;
                 I->grid_tc = true;
+                {
+                    // whole aligned phi quads in every tile (4 functions per atom, grouped by atom)
+                    std::vector<int> pids(poff[ntl]);
+                    check(cudaMemcpy(pids.data(), I->phi.ids, pids.size() * sizeof(int), cudaMemcpyDeviceToHost),
+                          "D2H phi ids");
+                    bool ok = c->nv % 4 == 0 && NP % 4 == 0;
+                    for (int t = 0; t < ntl && ok; ++t) {
+                        const int p0 = poff[t], np = poff[t + 1] - p0;
+                        if (np % 4) ok = false;
+                        for (int q = 0; q + 3 < np && ok; q += 4)
+                            ok = pids[p0 + q] % 4 == 0 && pids[p0 + q + 1] == pids[p0 + q] + 1 &&
+                                 pids[p0 + q + 2] == pids[p0 + q] + 2 && pids[p0 + q + 3] == pids[p0 + q] + 3;
+                    }
+                    const char *nq = std::getenv("TDDFT_NO_QUAD_GATHER");
+                    I->phi_quads = ok && !(nq && nq[0] == '1');
+                }
                 I->maxc = maxc;
                 if (integrals_tc_group(NP, 1, maxc) >= 1) {
                     std::vector<unsigned short> fm(cval.size());

@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(DENS_THREADS, 1) density_tc_kernel(
     int n, int nt, int KBmax, int NP, int G, int k, const int *__restrict__ coff, const int *__restrict__ cids,
     const int *__restrict__ poff, const int *__restrict__ pids, const float *__restrict__ pval, int nphi,
     const float *__restrict__ P, long long sP, const float *__restrict__ pscale, float *__restrict__ rho,
-    int *err) {
+    int *err, int quad) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<unsigned long long>(smem_raw) + 1023ull) & ~1023ull);
@@ -136,7 +136,55 @@ __global__ void __launch_bounds__(DENS_THREADS, 1) density_tc_kernel(
             }
         }
     }
-    if (warp < 4 || warp >= 6) {
+    if ((warp < 4 || warp >= 6) && quad) {
+        // gather the P block by phi quads: the tile's phi list holds whole atoms of 4 consecutive
+        // functions, so P[a][b0 .. b0+3] is one aligned 16-byte load; item = (row quad, 8-wide K
+        // chunk), quads fastest so a warp reads 512 contiguous bytes of one P row per load
+        const int rank = gather_rank(warp, lane);
+        const int nq = NB / 4, chunks = KB * 8, total = nq * chunks;
+        for (int i0 = rank; i0 < total; i0 += 2 * DENS_GATHER) {
+            float4 v[2][8];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int idx = i0 + u * DENS_GATHER;
+                const int qd = idx % nq, ch = idx / nq;
+                const int sl = (qd * 4) / NP, b0 = qd * 4 - sl * NP;
+                const bool live = idx < total && sl < gs && b0 < np;
+                const float *Ps = P + (long long)(s0 + (live ? sl : 0)) * sP + (live ? pids[p0 + b0] : 0);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int a = (ch >> 3) * 64 + (ch & 7) * 8 + j;
+                    v[u][j] = (live && a < nc) ? __ldg(reinterpret_cast<const float4 *>(Ps + (long long)cids[c0 + a] * nphi))
+                                               : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int idx = i0 + u * DENS_GATHER;
+                if (idx >= total) continue;
+                const int qd = idx % nq, ch = idx / nq;
+                const int sl = (qd * 4) / NP;
+                const float sc = sl < gs ? pscale[s0 + sl] : 0.0f;
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    unsigned short h[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const float x = r == 0 ? v[u][j].x : r == 1 ? v[u][j].y : r == 2 ? v[u][j].z : v[u][j].w;
+                        h[j] = __half_as_ushort(__float2half_rn(x * sc));
+                    }
+                    uint4 q;
+                    q.x = h[0] | ((unsigned)h[1] << 16);
+                    q.y = h[2] | ((unsigned)h[3] << 16);
+                    q.z = h[4] | ((unsigned)h[5] << 16);
+                    q.w = h[6] | ((unsigned)h[7] << 16);
+                    *reinterpret_cast<uint4 *>(B + (size_t)(ch >> 3) * NB * 128 + sw128_offset(qd * 4 + r, ch & 7)) = q;
+                }
+            }
+        }
+        fence_async_smem();
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ctl->b_ready)) : "memory");
+    } else if (warp < 4 || warp >= 6) {
         // gather the P block: row (s, b), K = a, 8 consecutive a per 16-byte chunk; four items in
         // flight per thread (32 independent loads)
         const int rank = gather_rank(warp, lane);
@@ -279,7 +327,7 @@ int density_tc_group(int KBmax, int NP, int k) {
 void response_density_tc(cudaStream_t st, const GridShape &g, const TileSet<float> &chi,
                          const TileSet<float> &phi, const unsigned short *chi_pm, int CK, int NPmax, int nphi,
                          const float *P, long long sP, int k, float *rho, unsigned *scratch_bits,
-                         float *scale, int *err) {
+                         float *scale, int *err, bool phi_quads) {
     if (k <= 0) return;
     ProfScope ps(st, ST_DENSITY, 2.0 * k * g.pair_points, 2.0 * g.table_values + 4.0 * k * g.n * g.n * g.n);
     check(cudaMemsetAsync(scratch_bits, 0, sizeof(unsigned) * k, st), "memset maxabs");
@@ -304,7 +352,8 @@ void response_density_tc(cudaStream_t st, const GridShape &g, const TileSet<floa
     }
     dim3 grid(ngroups, chi.ntiles);
     density_tc_kernel<<<grid, DENS_THREADS, sm, st>>>(mx, g.n, g.nt, KBmax, NP, G, k, chi.off, chi.ids, phi.off,
-                                                      phi.ids, phi.val, nphi, P, sP, scale, rho, err);
+                                                      phi.ids, phi.val, nphi, P, sP, scale, rho, err,
+                                                      phi_quads ? 1 : 0);
     check_launch("density_tc_kernel");
 }
 
@@ -628,7 +677,7 @@ void response_density_tc_noalloc(cudaStream_t st, const GridShape &g, const Tile
           "attr density_tc");
     dim3 grid((k + G - 1) / G, chi.ntiles);
     density_tc_kernel<<<grid, DENS_THREADS, sm, st>>>(mx, g.n, g.nt, KBmax, NP, G, k, chi.off, chi.ids, phi.off,
-                                                      phi.ids, phi.val, nphi, P, sP, s->scale, rho, &s->err);
+                                                      phi.ids, phi.val, nphi, P, sP, s->scale, rho, &s->err, 0);
     check_launch("density_tc_kernel (allocation-free)");
 }
 
