@@ -236,22 +236,62 @@ __global__ void __launch_bounds__(DENS_THREADS, 1) density_tc_kernel(
             float r[16];
 #pragma unroll
             for (int q = 0; q < 16; ++q) r[q] = 0.0f;
-            for (int c = 0; c < NB; c += 32) {
-                float v[32];
-                tmem_ld32(tmem + acc * 256 + ((unsigned)(warp * 32) << 16) + (unsigned)c, v);
+            if (NP % 32 == 0) {
+                // every 32-column chunk belongs to one state: skip the chunks that are all padding
+                // (warp-uniform), prefetch the next chunk's phi while this chunk's columns come
+                // out of TMEM, and add one dot product per chunk
+                auto live = [&](int cc) {
+                    const int sl = cc / NP;
+                    return sl < gs && cc - sl * NP < np;
+                };
+                auto load_phi = [&](int cc, float *dst) {
+                    const int b0 = cc - (cc / NP) * NP;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        dst[j] = (b0 + j < np) ? pval[(long long)(p0 + b0 + j) * TILE_PTS + lp] : 0.0f;
+                };
+                int c = 0;
+                while (c < NB && !live(c)) c += 32;
                 float ph[32];
+                if (c < NB) load_phi(c, ph);
+                while (c < NB) {
+                    int cn = c + 32;
+                    while (cn < NB && !live(cn)) cn += 32;
+                    float phn[32];
+                    if (cn < NB) load_phi(cn, phn);
+                    float v[32];
+                    tmem_ld32(tmem + acc * 256 + ((unsigned)(warp * 32) << 16) + (unsigned)c, v);
+                    float d = 0.0f;
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int col = c + j, sl = col / NP, b = col - sl * NP;
-                    ph[j] = (sl < gs && b < np) ? pval[(long long)(p0 + b) * TILE_PTS + lp] : 0.0f;
-                }
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int sl = (c + j) / NP;
-                    const float w = v[j] * ph[j];
+                    for (int j = 0; j < 32; ++j) d = fmaf(v[j], ph[j], d);
+                    const int sl = c / NP;
 #pragma unroll
                     for (int q = 0; q < 16; ++q)
-                        if (q == sl) r[q] += w;
+                        if (q == sl) r[q] += d;
+                    if (cn < NB) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) ph[j] = phn[j];
+                    }
+                    c = cn;
+                }
+            } else {
+                for (int c = 0; c < NB; c += 32) {
+                    float v[32];
+                    tmem_ld32(tmem + acc * 256 + ((unsigned)(warp * 32) << 16) + (unsigned)c, v);
+                    float ph[32];
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int col = c + j, sl = col / NP, b = col - sl * NP;
+                        ph[j] = (sl < gs && b < np) ? pval[(long long)(p0 + b) * TILE_PTS + lp] : 0.0f;
+                    }
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int sl = (c + j) / NP;
+                        const float w = v[j] * ph[j];
+#pragma unroll
+                        for (int q = 0; q < 16; ++q)
+                            if (q == sl) r[q] += w;
+                    }
                 }
             }
             tc_fence_before();
@@ -485,10 +525,18 @@ __global__ void __launch_bounds__(192, 1) integrals_tc_kernel(
                 const int sl = row / NP, b = row - sl * NP;
                 unsigned short h[8];
                 if (sl < gs && b < np) {
-                    const float *ph = pval + (long long)(p0 + b) * TILE_PTS + kb * 64 + c8 * 8;
-                    const float *vv = Vt + sl * TILE_PTS + kb * 64 + c8 * 8;
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) h[j] = __half_as_ushort(__float2half_rn(ph[j] * vv[j]));
+                    // 8 consecutive points: two 16-byte loads each of phi (global) and V (shared)
+                    const float4 *ph = reinterpret_cast<const float4 *>(pval + (long long)(p0 + b) * TILE_PTS + kb * 64 + c8 * 8);
+                    const float4 *vv = reinterpret_cast<const float4 *>(Vt + sl * TILE_PTS + kb * 64 + c8 * 8);
+                    const float4 p0v = __ldg(ph), p1v = __ldg(ph + 1), v0 = vv[0], v1 = vv[1];
+                    h[0] = __half_as_ushort(__float2half_rn(p0v.x * v0.x));
+                    h[1] = __half_as_ushort(__float2half_rn(p0v.y * v0.y));
+                    h[2] = __half_as_ushort(__float2half_rn(p0v.z * v0.z));
+                    h[3] = __half_as_ushort(__float2half_rn(p0v.w * v0.w));
+                    h[4] = __half_as_ushort(__float2half_rn(p1v.x * v1.x));
+                    h[5] = __half_as_ushort(__float2half_rn(p1v.y * v1.y));
+                    h[6] = __half_as_ushort(__float2half_rn(p1v.z * v1.z));
+                    h[7] = __half_as_ushort(__float2half_rn(p1v.w * v1.w));
                 } else {
 #pragma unroll
                     for (int j = 0; j < 8; ++j) h[j] = 0;

@@ -5,6 +5,7 @@
 #include "solver_kernels.h"
 
 #include <algorithm>
+#include <initializer_list>
 #include <cmath>
 #include <cstdlib>
 
@@ -148,14 +149,6 @@ __global__ void __launch_bounds__(256) combine_kernel(const double *__restrict__
     }
 }
 
-template <typename T>
-__global__ void mask_kernel(T *__restrict__ X, const T *__restrict__ mask, long long len, int nb) {
-    const long long tot = len * nb;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
-         i += (long long)gridDim.x * blockDim.x)
-        X[i] *= mask[i % len];
-}
-
 template <typename Tin, typename Tout>
 __global__ void convert_kernel(const Tin *__restrict__ in, Tout *__restrict__ out, long long n) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -163,14 +156,43 @@ __global__ void convert_kernel(const Tin *__restrict__ in, Tout *__restrict__ ou
         out[i] = Tout(in[i]);
 }
 
-template <typename T>
-__global__ void axpy_dev_kernel(const double *__restrict__ a, int a_stride, double sgn,
-                                T *__restrict__ y, const T *__restrict__ x, long long len, int nb) {
-    const long long tot = len * nb;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int b = (int)(i / len);
-        y[i] = fma(T(sgn * a[b * a_stride]), x[i], y[i]);
+// 16-byte vectors of T (4 float or 2 double) for the batched element-wise kernels
+template <typename T> struct Vec16;
+template <> struct Vec16<float> {
+    using type = float4;
+    static constexpr int n = 4;
+    __device__ static float4 fma1(float a, float4 x, float4 y) {
+        return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+    }
+    __device__ static float4 mul(float4 x, float4 m) { return make_float4(x.x * m.x, x.y * m.y, x.z * m.z, x.w * m.w); }
+};
+template <> struct Vec16<double> {
+    using type = double2;
+    static constexpr int n = 2;
+    __device__ static double2 fma1(double a, double2 x, double2 y) { return make_double2(fma(a, x.x, y.x), fma(a, x.y, y.y)); }
+    __device__ static double2 mul(double2 x, double2 m) { return make_double2(x.x * m.x, x.y * m.y); }
+};
+
+// Batched element-wise kernels: blockIdx.y = matrix b of nb, blockIdx.x strides over the len
+// entries of one matrix (in 16-byte vectors when len allows), so the per-matrix coefficient is
+// read once per thread and no index division runs per element.
+// y_b += sgn * a[b * a_stride] * x_b
+template <typename T, bool VEC>
+__global__ void axpy_dev_kernel(const double *__restrict__ a, int a_stride, double sgn, T *__restrict__ y,
+                                const T *__restrict__ x, long long len) {
+    const int b = blockIdx.y;
+    const T c = T(sgn * a[(long long)b * a_stride]);
+    const long long base = (long long)b * len;
+    if (VEC) {
+        using V = typename Vec16<T>::type;
+        V *yv = reinterpret_cast<V *>(y + base);
+        const V *xv = reinterpret_cast<const V *>(x + base);
+        const long long nv = len / Vec16<T>::n;
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nv; i += (long long)gridDim.x * blockDim.x)
+            yv[i] = Vec16<T>::fma1(c, xv[i], yv[i]);
+    } else {
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x)
+            y[base + i] = fma(c, x[base + i], y[base + i]);
     }
 }
 
@@ -183,6 +205,24 @@ __global__ void direction_kernel(T *__restrict__ out, const T *__restrict__ z,
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
         out[i] = b != T(0) ? fma(b, prev[i], -z[i]) : -z[i];
+}
+
+// grid of a batched element-wise launch: x blocks over one matrix of len entries (vectors of
+// 16 bytes when len and the pointers allow), y = the nb matrices; about 8 blocks per SM in all
+dim3 batched_grid(long long len, int nb, bool vec, int per) {
+    const long long units = vec ? len / per : len;
+    long long bx = (units + 255) / 256;
+    const long long cap = std::max<long long>(1, 8 * 152 / std::max(1, nb));
+    bx = std::max<long long>(1, std::min(bx, cap));
+    return dim3((unsigned)bx, (unsigned)nb);
+}
+
+template <typename T>
+bool vec_ok(long long len, std::initializer_list<const void *> ptrs) {
+    if (len % (16 / (long long)sizeof(T))) return false;
+    for (const void *p : ptrs)
+        if (reinterpret_cast<unsigned long long>(p) % 16) return false;
+    return true;
 }
 
 int grid_for(long long n) {
@@ -740,15 +780,40 @@ __global__ void cg_init_kernel(int n, double tol, const double *rr0, double *rr,
     *n_active = cnt;
 }
 
-// p <- r + beta p for each system (beta on the device)
-template <typename T>
-__global__ void cg_dir_kernel(T *__restrict__ p, const T *__restrict__ r,
-                              const double *__restrict__ beta, long long len, int nb) {
-    const long long tot = len * nb;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int b = (int)(i / len);
-        p[i] = fma(T(beta[b]), p[i], r[i]);
+// X_b *= mask (blockIdx.y = b)
+template <typename T, bool VEC>
+__global__ void mask_kernel(T *__restrict__ X, const T *__restrict__ mask, long long len) {
+    const long long base = (long long)blockIdx.y * len;
+    if (VEC) {
+        using V = typename Vec16<T>::type;
+        V *xv = reinterpret_cast<V *>(X + base);
+        const V *mv = reinterpret_cast<const V *>(mask);
+        const long long nv = len / Vec16<T>::n;
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nv; i += (long long)gridDim.x * blockDim.x)
+            xv[i] = Vec16<T>::mul(xv[i], mv[i]);
+    } else {
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x)
+            X[base + i] *= mask[i];
+    }
+}
+
+// p_b <- r_b + beta_b p_b (beta on the device; blockIdx.y = b)
+template <typename T, bool VEC>
+__global__ void cg_dir_kernel(T *__restrict__ p, const T *__restrict__ r, const double *__restrict__ beta,
+                              long long len) {
+    const int b = blockIdx.y;
+    const T c = T(beta[b]);
+    const long long base = (long long)b * len;
+    if (VEC) {
+        using V = typename Vec16<T>::type;
+        V *pv = reinterpret_cast<V *>(p + base);
+        const V *rv = reinterpret_cast<const V *>(r + base);
+        const long long nv = len / Vec16<T>::n;
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nv; i += (long long)gridDim.x * blockDim.x)
+            pv[i] = Vec16<T>::fma1(c, pv[i], rv[i]);
+    } else {
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x)
+            p[base + i] = fma(c, p[base + i], r[base + i]);
     }
 }
 
@@ -884,7 +949,11 @@ void combine(cudaStream_t st, const double *C, int ldc, int nout, int nin, const
 template <typename T>
 void mask_mul(cudaStream_t st, T *X, const T *mask, long long len, int nb) {
     ProfScope ps(st, ST_VECTOR, (double)len * nb, sizeof(T) * (2.0 * nb + 1.0) * len);
-    mask_kernel<T><<<grid_for(len * nb), 256, 0, st>>>(X, mask, len, nb);
+    if (nb <= 0) return;
+    const bool v = vec_ok<T>(len, {X, mask});
+    const dim3 g = batched_grid(len, nb, v, Vec16<T>::n);
+    if (v) mask_kernel<T, true><<<g, 256, 0, st>>>(X, mask, len);
+    else mask_kernel<T, false><<<g, 256, 0, st>>>(X, mask, len);
     check_launch("mask_kernel");
 }
 
@@ -899,7 +968,11 @@ template <typename T>
 void axpy_dev(cudaStream_t st, const double *a, int a_stride, double sgn, T *y, const T *x,
               long long len, int nb) {
     ProfScope ps(st, ST_VECTOR, 2.0 * len * nb, 3.0 * sizeof(T) * len * nb);
-    axpy_dev_kernel<T><<<grid_for(len * nb), 256, 0, st>>>(a, a_stride, sgn, y, x, len, nb);
+    if (nb <= 0) return;
+    const bool v = vec_ok<T>(len, {y, x});
+    const dim3 g = batched_grid(len, nb, v, Vec16<T>::n);
+    if (v) axpy_dev_kernel<T, true><<<g, 256, 0, st>>>(a, a_stride, sgn, y, x, len);
+    else axpy_dev_kernel<T, false><<<g, 256, 0, st>>>(a, a_stride, sgn, y, x, len);
     check_launch("axpy_dev_kernel");
 }
 
@@ -913,7 +986,11 @@ void direction(cudaStream_t st, T *out, const T *z, const T *prev, const double 
 template <typename T>
 void cg_dir(cudaStream_t st, T *p, const T *r, const double *beta, long long len, int nb) {
     ProfScope ps(st, ST_VECTOR, 2.0 * len * nb, 3.0 * sizeof(T) * len * nb);
-    cg_dir_kernel<T><<<grid_for(len * nb), 256, 0, st>>>(p, r, beta, len, nb);
+    if (nb <= 0) return;
+    const bool v = vec_ok<T>(len, {p, r});
+    const dim3 g = batched_grid(len, nb, v, Vec16<T>::n);
+    if (v) cg_dir_kernel<T, true><<<g, 256, 0, st>>>(p, r, beta, len);
+    else cg_dir_kernel<T, false><<<g, 256, 0, st>>>(p, r, beta, len);
     check_launch("cg_dir_kernel");
 }
 
