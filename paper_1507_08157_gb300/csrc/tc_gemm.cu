@@ -8,10 +8,15 @@
 // x*y ~= x_hi y_hi + x_hi y_lo + x_lo y_hi; the dropped x_lo y_lo term and the tf32 reading of the
 // lo parts leave a relative error of about 2^-21 per product (plain TF32: 2^-11).
 //
-// Block: 192 threads. Warps 0-3 read the accumulator out of TMEM (warp w owns lanes 32w..32w+31,
-// i.e. tile rows) and write C; warp 4 lane 0 issues the TMA loads; warp 5 allocates TMEM and its
-// lane 0 issues the MMAs. 128 x 128 output tile, K in slices of 32 floats (one 128-byte swizzle
-// row), 4-stage mbarrier pipeline. Every wait is bounded: on expiry the block records an error
+// The split is made inside the kernel: TMA brings the raw float32 tiles of A and B, warps 0-3
+// round each element to tf32 in place (hi) and write x - hi into a second tile of the same
+// swizzled layout (lo), so the operands cross L2 once, as float32.
+//
+// Block: 192 threads. Warps 0-3 split the staged tiles during the K loop, then read the
+// accumulator out of TMEM (warp w owns lanes 32w..32w+31, i.e. tile rows) and write C; warp 4
+// lane 0 issues the TMA loads; warp 5 allocates TMEM and its lane 0 issues the MMAs. 128 x 128
+// output tile, K in slices of 32 floats (one 128-byte swizzle row), mbarrier pipeline of 3
+// stages (split) or 4 (plain TF32). Every wait is bounded: on expiry the block records an error
 // and skips to the teardown, which always frees TMEM.
 #include "tc_common.cuh"
 #include "tddft_internal.h"
@@ -32,6 +37,7 @@ constexpr int TILE_BYTES = TBM * TBK * 4;                  // 16 KB per operand 
 
 struct __align__(8) TcShared {
     unsigned long long full[TSTAGES];
+    unsigned long long split[TSTAGES];
     unsigned long long empty[TSTAGES];
     unsigned long long accum;
     unsigned int tmem_base;
@@ -40,18 +46,22 @@ struct __align__(8) TcShared {
 
 using namespace tc;
 
-// NSPLIT = 1: plain TF32; 3: three-term split (needs A_lo and B_lo maps)
+__device__ __forceinline__ float tf32_rna_dev(float x) {
+    unsigned r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// NSPLIT = 1: plain TF32 on the raw tiles; 3: three-term split, hi/lo made in shared memory
 template <int NSPLIT>
 __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(
-    const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
-    const __grid_constant__ CUtensorMap mAlo, const __grid_constant__ CUtensorMap mBlo, int M, int N,
-    int K, int batchA, int batchB, float alpha, float beta, float *__restrict__ C, int ldc, long long sC,
-    int *err) {
+    const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB, int M, int N, int K,
+    int batchA, int batchB, float alpha, float beta, float *__restrict__ C, int ldc, long long sC, int *err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte aligned tile area, then the control block
     unsigned char *base = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<unsigned long long>(smem_raw) + 1023ull) & ~1023ull);
-    constexpr int NT = NSPLIT == 1 ? 2 : 4;   // operand tiles per stage
+    constexpr int NT = NSPLIT == 1 ? 2 : 4;   // operand tiles per stage: A, B (hi in place), A lo, B lo
     constexpr int S = stages<NSPLIT>();
     unsigned char *tiles = base;
     TcShared *ctl = reinterpret_cast<TcShared *>(base + (size_t)S * NT * TILE_BYTES);
@@ -63,6 +73,7 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(&ctl->full[s], 1);
+            mbar_init(&ctl->split[s], 128);
             mbar_init(&ctl->empty[s], 1);
         }
         mbar_init(&ctl->accum, 1);
@@ -80,20 +91,16 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(
     const unsigned tmem = ctl->tmem_base;
 
     if (warp == 4 && lane == 0) {
-        // TMA producer
+        // TMA producer: raw float32 tiles of A and B
         const int ba = batchA > 1 ? b : 0, bb = batchB > 1 ? b : 0;
         for (int kb = 0; kb < nk; ++kb) {
             const int s = kb % S;
             const unsigned par = ((kb / S) & 1) ^ 1;
             if (!mbar_wait(&ctl->empty[s], par, abort)) break;
             unsigned char *st = tiles + (size_t)s * NT * TILE_BYTES;
-            mbar_expect_tx(&ctl->full[s], NT * TILE_BYTES);
+            mbar_expect_tx(&ctl->full[s], 2 * TILE_BYTES);
             tma_load_3d(st, &mA, &ctl->full[s], kb * TBK, m0, ba);
             tma_load_3d(st + TILE_BYTES, &mB, &ctl->full[s], kb * TBK, n0, bb);
-            if (NSPLIT == 3) {
-                tma_load_3d(st + 2 * TILE_BYTES, &mAlo, &ctl->full[s], kb * TBK, m0, ba);
-                tma_load_3d(st + 3 * TILE_BYTES, &mBlo, &ctl->full[s], kb * TBK, n0, bb);
-            }
         }
     } else if (warp == 5 && lane == 0) {
         // MMA issuer
@@ -102,7 +109,7 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(
         for (int kb = 0; kb < nk && ok; ++kb) {
             const int s = kb % S;
             const unsigned par = (kb / S) & 1;
-            if (!mbar_wait(&ctl->full[s], par, abort)) {
+            if (!mbar_wait(NSPLIT == 3 ? &ctl->split[s] : &ctl->full[s], par, abort)) {
                 ok = false;
                 break;
             }
@@ -124,6 +131,38 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(
         }
         mma_commit(&ctl->accum);
     } else if (warp < 4) {
+        if (NSPLIT == 3) {
+            // split each staged pair of tiles: hi = rna_tf32(x) in place, lo = x - hi alongside
+            // (an element-wise map, so the swizzled layout carries over unchanged)
+            for (int kb = 0; kb < nk; ++kb) {
+                const int s = kb % S;
+                const unsigned par = (kb / S) & 1;
+                if (!mbar_wait(&ctl->full[s], par, abort)) break;
+                unsigned char *st = tiles + (size_t)s * NT * TILE_BYTES;
+#pragma unroll
+                for (int op = 0; op < 2; ++op) {
+                    float4 *hi = reinterpret_cast<float4 *>(st + op * TILE_BYTES);
+                    float4 *lo = reinterpret_cast<float4 *>(st + (2 + op) * TILE_BYTES);
+#pragma unroll 4
+                    for (int i = threadIdx.x; i < TILE_BYTES / 16; i += 128) {
+                        const float4 x = hi[i];
+                        float4 h, l;
+                        h.x = tf32_rna_dev(x.x);
+                        h.y = tf32_rna_dev(x.y);
+                        h.z = tf32_rna_dev(x.z);
+                        h.w = tf32_rna_dev(x.w);
+                        l.x = x.x - h.x;
+                        l.y = x.y - h.y;
+                        l.z = x.z - h.z;
+                        l.w = x.w - h.w;
+                        hi[i] = h;
+                        lo[i] = l;
+                    }
+                }
+                fence_async_smem();
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ctl->split[s])) : "memory");
+            }
+        }
         // epilogue: TMEM -> registers -> C
         const bool ok = mbar_wait(&ctl->accum, 0, abort) && !*abort;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -213,23 +252,17 @@ bool encode_map_2d(CUtensorMap *map, CUtensorMapDataType dt, const void *ptr, un
 }
 
 // C[b] = alpha * A[b] B[b]^T + beta C[b] with A (M x K, ld lda, batch stride sA; 0 = shared) and
-// B (N x K, ldb, sB). Alo/Blo: the lo parts for the split (both null: plain TF32). K-contiguous
-// rows must start on 16-byte boundaries: lda, ldb, sA, sB multiples of 4, pointers 16-aligned.
+// B (N x K, ldb, sB), both K-contiguous; split: three-term TF32 split made in the kernel, else
+// plain TF32. Rows must start on 16-byte boundaries: lda, ldb, sA, sB multiples of 4 and the
+// pointers 16-byte aligned.
 void tc_gemm_nt(cudaStream_t st, int M, int N, int K, float alpha, const float *A, int lda, long long sA,
-                const float *Alo, const float *B, int ldb, long long sB, const float *Blo, float beta, float *C,
-                int ldc, long long sC, int batch) {
-    const int nsplit = (Alo && Blo) ? 3 : 1;
-    CUtensorMap ma, mb, malo, mblo;
+                const float *B, int ldb, long long sB, float beta, float *C, int ldc, long long sC, int batch,
+                bool split) {
+    const int nsplit = split ? 3 : 1;
+    CUtensorMap ma, mb;
     const int bA = sA ? batch : 1, bB = sB ? batch : 1;
     if (!make_map(&ma, A, K, M, lda, sA, bA) || !make_map(&mb, B, K, N, ldb, sB, bB))
         throw CudaError{cudaErrorInvalidValue, "cuTensorMapEncodeTiled"};
-    if (nsplit == 3) {
-        if (!make_map(&malo, Alo, K, M, lda, sA, bA) || !make_map(&mblo, Blo, K, N, ldb, sB, bB))
-            throw CudaError{cudaErrorInvalidValue, "cuTensorMapEncodeTiled (lo)"};
-    } else {
-        malo = ma;
-        mblo = mb;
-    }
     const size_t sm = tc_smem(nsplit);
     static bool attr1 = false, attr3 = false;
     if (nsplit == 1 && !attr1) {
@@ -243,9 +276,9 @@ void tc_gemm_nt(cudaStream_t st, int M, int N, int K, float alpha, const float *
     dim3 grid((N + TBN - 1) / TBN, (M + TBM - 1) / TBM, batch);
     int *err = error_word();
     if (nsplit == 3)
-        tc_gemm_kernel<3><<<grid, 192, sm, st>>>(ma, mb, malo, mblo, M, N, K, bA, bB, alpha, beta, C, ldc, sC, err);
+        tc_gemm_kernel<3><<<grid, 192, sm, st>>>(ma, mb, M, N, K, bA, bB, alpha, beta, C, ldc, sC, err);
     else
-        tc_gemm_kernel<1><<<grid, 192, sm, st>>>(ma, mb, malo, mblo, M, N, K, bA, bB, alpha, beta, C, ldc, sC, err);
+        tc_gemm_kernel<1><<<grid, 192, sm, st>>>(ma, mb, M, N, K, bA, bB, alpha, beta, C, ldc, sC, err);
     check_launch("tc_gemm_kernel");
 }
 
@@ -333,38 +366,55 @@ int grid1(long long n) {
 
 }  // namespace
 
-// Dispatch of a row-major C[b] = alpha op(A[b]) op(B[b]) + beta C[b] onto the tensor cores:
-// operands are brought to K-major (transposed where needed) and split into hi/lo parts in scratch.
+// Dispatch of a row-major C[b] = alpha op(A[b]) op(B[b]) + beta C[b] onto the tensor cores. The
+// kernel wants both operands K-contiguous with 16-byte row starts: an operand that already is
+// (A not transposed, B transposed) goes in as it lies; otherwise a transposed (or re-strided)
+// float32 copy is made in scratch. The split into hi/lo parts happens inside the kernel.
 void tc_gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, float alpha, const float *A, int lda,
              long long sA, const float *B, int ldb, long long sB, float beta, float *C, int ldc, long long sC,
              int batch, bool split) {
     const int bA = sA ? batch : 1, bB = sB ? batch : 1;
+    auto direct = [](const float *p, int ld, long long s) {
+        return reinterpret_cast<unsigned long long>(p) % 16 == 0 && ld % 4 == 0 && s % 4 == 0;
+    };
+    const bool a_direct = !ta && direct(A, lda, sA), b_direct = tb && direct(B, ldb, sB);
     const int Kp = (K + 3) / 4 * 4;                     // 16-byte rows for the tensor maps
     auto up64 = [](size_t n) { return (n + 63) / 64 * 64; };
-    const size_t na = up64((size_t)M * Kp * bA), nbt = up64((size_t)N * Kp * bB);
-    const size_t need = (split ? 2 : 1) * (na + nbt);
-    float *base = scratch().get(need);
-    float *Ahi = base, *Alo = split ? base + na : nullptr;
-    float *Bhi = base + (split ? 2 * na : na), *Blo = split ? Bhi + nbt : nullptr;
-    const long long sa = (long long)M * Kp, sb = (long long)N * Kp;
-    // A as M x Kp, K contiguous
-    if (!ta) {
-        split_kernel<<<grid1((long long)M * Kp * bA), 256, 0, st>>>(A, M, K, lda, sA, Ahi, Alo, Kp, sa, bA);
-    } else {
-        dim3 g((M + 31) / 32, (Kp + 31) / 32, bA);
-        transpose_split_kernel<<<g, dim3(32, 8), 0, st>>>(A, K, M, lda, sA, Ahi, Alo, Kp, sa);
+    const size_t na = a_direct ? 0 : up64((size_t)M * Kp * bA), nbt = b_direct ? 0 : up64((size_t)N * Kp * bB);
+    float *base = (na + nbt) ? scratch().get(na + nbt) : nullptr;
+    const float *Ak = A, *Bk = B;
+    int lak = lda, lbk = ldb;
+    long long sak = sA, sbk = sB;
+    if (!a_direct) {
+        float *Ac = base;
+        const long long sa = (long long)M * Kp;
+        if (!ta) {
+            split_kernel<<<grid1((long long)M * Kp * bA), 256, 0, st>>>(A, M, K, lda, sA, Ac, nullptr, Kp, sa, bA);
+        } else {
+            dim3 g((M + 31) / 32, (Kp + 31) / 32, bA);
+            transpose_split_kernel<<<g, dim3(32, 8), 0, st>>>(A, K, M, lda, sA, Ac, nullptr, Kp, sa);
+        }
+        check_launch("tc copy A");
+        Ak = Ac;
+        lak = Kp;
+        sak = bA > 1 ? sa : 0;
     }
-    check_launch("tc split A");
-    // B as N x Kp, K contiguous
-    if (tb) {
-        split_kernel<<<grid1((long long)N * Kp * bB), 256, 0, st>>>(B, N, K, ldb, sB, Bhi, Blo, Kp, sb, bB);
-    } else {
-        dim3 g((N + 31) / 32, (Kp + 31) / 32, bB);
-        transpose_split_kernel<<<g, dim3(32, 8), 0, st>>>(B, K, N, ldb, sB, Bhi, Blo, Kp, sb);
+    if (!b_direct) {
+        float *Bc = base + na;
+        const long long sb = (long long)N * Kp;
+        if (tb) {
+            split_kernel<<<grid1((long long)N * Kp * bB), 256, 0, st>>>(B, N, K, ldb, sB, Bc, nullptr, Kp, sb, bB);
+        } else {
+            dim3 g((N + 31) / 32, (Kp + 31) / 32, bB);
+            transpose_split_kernel<<<g, dim3(32, 8), 0, st>>>(B, K, N, ldb, sB, Bc, nullptr, Kp, sb);
+        }
+        check_launch("tc copy B");
+        Bk = Bc;
+        lbk = Kp;
+        sbk = bB > 1 ? sb : 0;
     }
-    check_launch("tc split B");
-    tc_gemm_nt(st, M, N, Kp, alpha, Ahi, Kp, bA > 1 ? sa : 0, Alo, Bhi, Kp, bB > 1 ? sb : 0, Blo, beta, C, ldc,
-               sC, batch);
+    // both maps span the K real columns (copies are zero-padded to Kp; reads past K fill zeros)
+    tc_gemm_nt(st, M, N, K, alpha, Ak, lak, sak, Bk, lbk, sbk, beta, C, ldc, sC, batch, split);
 }
 
 int *tc_error_word() { return error_word(); }
