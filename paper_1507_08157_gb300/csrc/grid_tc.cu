@@ -421,6 +421,8 @@ struct __align__(8) IntShared {
     unsigned long long acc_done;
     unsigned int tmem_base;
     int abort;
+    int pid[256];      // the tile's phi indices (np <= NP <= 256)
+    float vsc[16];     // scales of the group's states
 };
 
 __device__ __forceinline__ void red_add_v4(float *addr, float a, float b, float c, float d) {
@@ -470,6 +472,8 @@ __global__ void __launch_bounds__(192, 1) integrals_tc_kernel(
                      "r"(512));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
+    for (int i = threadIdx.x; i < np; i += blockDim.x) ctl->pid[i] = pids[p0 + i];
+    if (threadIdx.x < gs) ctl->vsc[threadIdx.x] = vscale[s0 + threadIdx.x];
     // V of the group's states on the tile points, scaled
     for (int i = threadIdx.x; i < gs * TILE_PTS; i += blockDim.x) {
         const int sl = i / TILE_PTS, lp = i - sl * TILE_PTS;
@@ -558,6 +562,11 @@ __global__ void __launch_bounds__(192, 1) integrals_tc_kernel(
             const bool arow = ok && a < nc;
             const long long rowoff = arow ? (long long)cids[c0 + a] * nphi : 0;
             for (int c = 0; c < NB; c += 32) {
+                if (NP % 32 == 0) {
+                    // state-aligned chunk: skip it when it is all padding (warp-uniform)
+                    const int sl = c / NP;
+                    if (sl >= gs || c - sl * NP >= np) continue;
+                }
                 float v[32];
                 tmem_ld32(tmem + mb * acc_stride + ((unsigned)(warp * 32) << 16) + (unsigned)c, v);
                 if (!arow) continue;
@@ -565,19 +574,19 @@ __global__ void __launch_bounds__(192, 1) integrals_tc_kernel(
                 for (int j = 0; j < 32; j += 4) {
                     const int col = c + j;
                     const int sl = col / NP, b = col - sl * NP;
-                    if (sl >= gs) continue;
-                    const float f = dV / vscale[s0 + sl];
+                    if (sl >= gs || b >= np) continue;
+                    const float f = dV / ctl->vsc[sl];
                     float *o = out + (long long)(s0 + sl) * nchi * nphi + rowoff;
-                    const int B0 = b < np ? pids[p0 + b] : -1;
+                    const int B0 = ctl->pid[b];
                     // four consecutive phi of one atom land on one aligned float4
-                    const bool vec = vec_ok && (b + 3 < np) && (B0 % 4 == 0) && pids[p0 + b + 3] == B0 + 3;
+                    const bool vec = vec_ok && (b + 3 < np) && (B0 % 4 == 0) && ctl->pid[b + 3] == B0 + 3;
                     if (vec) {
                         red_add_v4(o + B0, f * v[j], f * v[j + 1], f * v[j + 2], f * v[j + 3]);
                     } else {
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
                             const int bu = b + u;
-                            if (bu < np && (col + u) / NP == sl) atomicAdd(o + pids[p0 + bu], f * v[j + u]);
+                            if (bu < np && (col + u) / NP == sl) atomicAdd(o + ctl->pid[bu], f * v[j + u]);
                         }
                     }
                 }
