@@ -12,18 +12,22 @@
 // round each element to tf32 in place (hi) and write x - hi into a second tile of the same
 // swizzled layout (lo), so the operands cross L2 once, as float32.
 //
-// Block: 192 threads. Warps 0-3 split the staged tiles during the K loop, then read the
-// accumulator out of TMEM (warp w owns lanes 32w..32w+31, i.e. tile rows) and write C; warp 4
-// lane 0 issues the TMA loads; warp 5 allocates TMEM and its lane 0 issues the MMAs. 128 x 128
-// output tile, K in slices of 32 floats (one 128-byte swizzle row), mbarrier pipeline of 3
-// stages (split) or 4 (plain TF32). Every wait is bounded: on expiry the block records an error
-// and skips to the teardown, which always frees TMEM.
+// Persistent kernel, one CTA of 320 threads per SM looping over 128 x 128 output tiles (n
+// fastest, then m, then the batch): warps 0-3 read the accumulator out of TMEM (warp w owns
+// lanes 32w..32w+31, i.e. tile rows) and write C through a shared-memory block so that each
+// store covers 128 contiguous bytes of a row; warps 4-7 split the staged tiles; warp 8 lane 0
+// issues the TMA loads; warp 9 allocates TMEM and its lane 0 issues the MMAs. Two TMEM
+// accumulators let the epilogue of one tile overlap the MMAs of the next. K in slices of 32
+// floats (one 128-byte swizzle row), mbarrier ring of 3 stages (split) or 4 (plain TF32). Every
+// wait is bounded: on expiry the block records an error and skips to the teardown, which always
+// frees TMEM.
 #include "tc_common.cuh"
 #include "tddft_internal.h"
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <mutex>
 
 namespace tddft {
@@ -39,10 +43,14 @@ struct __align__(8) TcShared {
     unsigned long long full[TSTAGES];
     unsigned long long split[TSTAGES];
     unsigned long long empty[TSTAGES];
-    unsigned long long accum;
+    unsigned long long acc_full[2];
+    unsigned long long acc_empty[2];
     unsigned int tmem_base;
     int abort;
 };
+
+constexpr int GEMM_THREADS = 320;
+constexpr int STAGE_FLOATS = 4 * 32 * 33;      // epilogue staging: one 32 x 33 block per warp
 
 using namespace tc;
 
@@ -54,19 +62,21 @@ __device__ __forceinline__ float tf32_rna_dev(float x) {
 
 // NSPLIT = 1: plain TF32 on the raw tiles; 3: three-term split, hi/lo made in shared memory
 template <int NSPLIT>
-__global__ void __launch_bounds__(192, 1) tc_gemm_kernel(
+__global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(
     const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB, int M, int N, int K,
-    int batchA, int batchB, float alpha, float beta, float *__restrict__ C, int ldc, long long sC, int *err) {
+    int batchA, int batchB, int batch, float alpha, float beta, float *__restrict__ C, int ldc, long long sC,
+    int *err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    // 1024-byte aligned tile area, then the control block
     unsigned char *base = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<unsigned long long>(smem_raw) + 1023ull) & ~1023ull);
     constexpr int NT = NSPLIT == 1 ? 2 : 4;   // operand tiles per stage: A, B (hi in place), A lo, B lo
     constexpr int S = stages<NSPLIT>();
     unsigned char *tiles = base;
-    TcShared *ctl = reinterpret_cast<TcShared *>(base + (size_t)S * NT * TILE_BYTES);
+    float *staging = reinterpret_cast<float *>(base + (size_t)S * NT * TILE_BYTES);
+    TcShared *ctl = reinterpret_cast<TcShared *>(staging + STAGE_FLOATS);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * TBM, n0 = blockIdx.x * TBN, b = blockIdx.z;
+    const int tn = (N + TBN - 1) / TBN, tm = (M + TBM - 1) / TBM;
+    const int ntiles = tn * tm * batch;
     const int nk = (K + TBK - 1) / TBK;
     volatile int *abort = &ctl->abort;
 
@@ -76,13 +86,16 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(
             mbar_init(&ctl->split[s], 128);
             mbar_init(&ctl->empty[s], 1);
         }
-        mbar_init(&ctl->accum, 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&ctl->acc_full[i], 1);
+            mbar_init(&ctl->acc_empty[i], 128);
+        }
         ctl->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 5) {
+    if (warp == 9) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&ctl->tmem_base)),
-                     "r"(TBN));
+                     "r"(2 * TBN));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -90,100 +103,145 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = ctl->tmem_base;
 
-    if (warp == 4 && lane == 0) {
-        // TMA producer: raw float32 tiles of A and B
-        const int ba = batchA > 1 ? b : 0, bb = batchB > 1 ? b : 0;
-        for (int kb = 0; kb < nk; ++kb) {
-            const int s = kb % S;
-            const unsigned par = ((kb / S) & 1) ^ 1;
-            if (!mbar_wait(&ctl->empty[s], par, abort)) break;
-            unsigned char *st = tiles + (size_t)s * NT * TILE_BYTES;
-            mbar_expect_tx(&ctl->full[s], 2 * TILE_BYTES);
-            tma_load_3d(st, &mA, &ctl->full[s], kb * TBK, m0, ba);
-            tma_load_3d(st + TILE_BYTES, &mB, &ctl->full[s], kb * TBK, n0, bb);
-        }
-    } else if (warp == 5 && lane == 0) {
-        // MMA issuer
-        constexpr unsigned idesc = idesc_tf32(TBM, TBN);
-        bool ok = true;
-        for (int kb = 0; kb < nk && ok; ++kb) {
-            const int s = kb % S;
-            const unsigned par = (kb / S) & 1;
-            if (!mbar_wait(NSPLIT == 3 ? &ctl->split[s] : &ctl->full[s], par, abort)) {
-                ok = false;
-                break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            unsigned char *st = tiles + (size_t)s * NT * TILE_BYTES;
-            const unsigned a = smem_u32(st), bt = smem_u32(st + TILE_BYTES);
-#pragma unroll
-            for (int kk = 0; kk < TBK / 8; ++kk) {
-                const unsigned off = kk * 32;   // 8 tf32 = 32 bytes along K inside the swizzle row
-                const unsigned acc = (kb > 0 || kk > 0) ? 1u : 0u;
-                mma_tf32(tmem, smem_desc(a + off), smem_desc(bt + off), idesc, acc);
-                if (NSPLIT == 3) {
-                    const unsigned alo = smem_u32(st + 2 * TILE_BYTES), blo = smem_u32(st + 3 * TILE_BYTES);
-                    mma_tf32(tmem, smem_desc(a + off), smem_desc(blo + off), idesc, 1u);
-                    mma_tf32(tmem, smem_desc(alo + off), smem_desc(bt + off), idesc, 1u);
+    if (warp == 8) {
+        if (lane == 0) {
+            // TMA producer: raw float32 tiles of A and B, for every K slice of every tile
+            long long it = 0;
+            bool go = true;
+            for (int t = blockIdx.x; t < ntiles && go; t += gridDim.x) {
+                const int n0 = (t % tn) * TBN, m0 = ((t / tn) % tm) * TBM, b = t / (tn * tm);
+                const int ba = batchA > 1 ? b : 0, bb = batchB > 1 ? b : 0;
+                for (int kb = 0; kb < nk; ++kb, ++it) {
+                    const int s = (int)(it % S);
+                    const unsigned par = (unsigned)(((it / S) & 1) ^ 1);
+                    if (!mbar_wait(&ctl->empty[s], par, abort)) {
+                        go = false;
+                        break;
+                    }
+                    unsigned char *st = tiles + (size_t)s * NT * TILE_BYTES;
+                    mbar_expect_tx(&ctl->full[s], 2 * TILE_BYTES);
+                    tma_load_3d(st, &mA, &ctl->full[s], kb * TBK, m0, ba);
+                    tma_load_3d(st + TILE_BYTES, &mB, &ctl->full[s], kb * TBK, n0, bb);
                 }
             }
-            mma_commit(&ctl->empty[s]);
         }
-        mma_commit(&ctl->accum);
-    } else if (warp < 4) {
+    } else if (warp == 9) {
+        if (lane == 0) {
+            // MMA issuer: accumulator tcount % 2 per tile
+            constexpr unsigned idesc = idesc_tf32(TBM, TBN);
+            long long it = 0;
+            int tcount = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tcount) {
+                const int buf = tcount & 1, use = tcount >> 1;
+                if (!mbar_wait(&ctl->acc_empty[buf], (unsigned)((use & 1) ^ 1), abort)) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const unsigned acc_t = tmem + (unsigned)(buf * TBN);
+                for (int kb = 0; kb < nk; ++kb, ++it) {
+                    const int s = (int)(it % S);
+                    const unsigned par = (unsigned)((it / S) & 1);
+                    if (!mbar_wait(NSPLIT == 3 ? &ctl->split[s] : &ctl->full[s], par, abort)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    unsigned char *st = tiles + (size_t)s * NT * TILE_BYTES;
+                    const unsigned a = smem_u32(st), bt = smem_u32(st + TILE_BYTES);
+#pragma unroll
+                    for (int kk = 0; kk < TBK / 8; ++kk) {
+                        const unsigned off = kk * 32;   // 8 tf32 = 32 bytes along K inside the swizzle row
+                        const unsigned acc = (kb > 0 || kk > 0) ? 1u : 0u;
+                        mma_tf32(acc_t, smem_desc(a + off), smem_desc(bt + off), idesc, acc);
+                        if (NSPLIT == 3) {
+                            const unsigned alo = smem_u32(st + 2 * TILE_BYTES), blo = smem_u32(st + 3 * TILE_BYTES);
+                            mma_tf32(acc_t, smem_desc(a + off), smem_desc(blo + off), idesc, 1u);
+                            mma_tf32(acc_t, smem_desc(alo + off), smem_desc(bt + off), idesc, 1u);
+                        }
+                    }
+                    mma_commit(&ctl->empty[s]);
+                }
+                if (!ok) break;
+                mma_commit(&ctl->acc_full[buf]);
+            }
+        }
+    } else if (warp >= 4) {
         if (NSPLIT == 3) {
             // split each staged pair of tiles: hi = rna_tf32(x) in place, lo = x - hi alongside
             // (an element-wise map, so the swizzled layout carries over unchanged)
-            for (int kb = 0; kb < nk; ++kb) {
-                const int s = kb % S;
-                const unsigned par = (kb / S) & 1;
-                if (!mbar_wait(&ctl->full[s], par, abort)) break;
-                unsigned char *st = tiles + (size_t)s * NT * TILE_BYTES;
-#pragma unroll
-                for (int op = 0; op < 2; ++op) {
-                    float4 *hi = reinterpret_cast<float4 *>(st + op * TILE_BYTES);
-                    float4 *lo = reinterpret_cast<float4 *>(st + (2 + op) * TILE_BYTES);
-#pragma unroll 4
-                    for (int i = threadIdx.x; i < TILE_BYTES / 16; i += 128) {
-                        const float4 x = hi[i];
-                        float4 h, l;
-                        h.x = tf32_rna_dev(x.x);
-                        h.y = tf32_rna_dev(x.y);
-                        h.z = tf32_rna_dev(x.z);
-                        h.w = tf32_rna_dev(x.w);
-                        l.x = x.x - h.x;
-                        l.y = x.y - h.y;
-                        l.z = x.z - h.z;
-                        l.w = x.w - h.w;
-                        hi[i] = h;
-                        lo[i] = l;
+            const int ts = threadIdx.x - 128;
+            long long it = 0;
+            bool go = true;
+            for (int t = blockIdx.x; t < ntiles && go; t += gridDim.x) {
+                for (int kb = 0; kb < nk; ++kb, ++it) {
+                    const int s = (int)(it % S);
+                    const unsigned par = (unsigned)((it / S) & 1);
+                    if (!mbar_wait(&ctl->full[s], par, abort)) {
+                        go = false;
+                        break;
                     }
+                    unsigned char *st = tiles + (size_t)s * NT * TILE_BYTES;
+#pragma unroll
+                    for (int op = 0; op < 2; ++op) {
+                        float4 *hi = reinterpret_cast<float4 *>(st + op * TILE_BYTES);
+                        float4 *lo = reinterpret_cast<float4 *>(st + (2 + op) * TILE_BYTES);
+#pragma unroll 4
+                        for (int i = ts; i < TILE_BYTES / 16; i += 128) {
+                            const float4 x = hi[i];
+                            float4 h, l;
+                            h.x = tf32_rna_dev(x.x);
+                            h.y = tf32_rna_dev(x.y);
+                            h.z = tf32_rna_dev(x.z);
+                            h.w = tf32_rna_dev(x.w);
+                            l.x = x.x - h.x;
+                            l.y = x.y - h.y;
+                            l.z = x.z - h.z;
+                            l.w = x.w - h.w;
+                            hi[i] = h;
+                            lo[i] = l;
+                        }
+                    }
+                    fence_async_smem();
+                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ctl->split[s])) : "memory");
                 }
-                fence_async_smem();
-                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ctl->split[s])) : "memory");
             }
         }
-        // epilogue: TMEM -> registers -> C
-        const bool ok = mbar_wait(&ctl->accum, 0, abort) && !*abort;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int row = m0 + warp * 32 + lane;
-        float *crow = C + (long long)b * sC + (long long)row * ldc;
-        for (int c0 = 0; c0 < TBN; c0 += 32) {
-            float v[32];
-            tmem_ld32(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0, v);
-            if (!ok || row >= M) continue;
+    } else {
+        // epilogue (warps 0-3): TMEM -> registers -> 32 x 32 staging block -> C rows
+        float *stg = staging + warp * 32 * 33;
+        int tcount = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tcount) {
+            const int buf = tcount & 1, use = tcount >> 1;
+            if (!mbar_wait(&ctl->acc_full[buf], (unsigned)(use & 1), abort)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int n0 = (t % tn) * TBN, m0 = ((t / tn) % tm) * TBM, b = t / (tn * tm);
+            float *Cb = C + (long long)b * sC;
+            for (int c0 = 0; c0 < TBN; c0 += 32) {
+                float v[32];
+                tmem_ld32(tmem + (unsigned)(buf * TBN) + ((unsigned)(warp * 32) << 16) + (unsigned)c0, v);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const int col = n0 + c0 + j;
-                if (col < N) crow[col] = (beta == 0.0f) ? alpha * v[j] : fmaf(alpha, v[j], beta * crow[col]);
+                for (int j = 0; j < 32; ++j) stg[lane * 33 + j] = v[j];
+                __syncwarp();
+                const int col = n0 + c0 + lane;
+#pragma unroll 8
+                for (int rr = 0; rr < 32; ++rr) {
+                    const int row = m0 + warp * 32 + rr;
+                    if (row < M && col < N) {
+                        float *cp = Cb + (long long)row * ldc + col;
+                        const float x = stg[rr * 33 + lane];
+                        *cp = (beta == 0.0f) ? alpha * x : fmaf(alpha, x, beta * *cp);
+                    }
+                }
+                __syncwarp();
             }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ctl->acc_empty[buf])) : "memory");
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 5) {
+    if (warp == 9) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TBN));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TBN));
     }
     if (threadIdx.x == 0 && ctl->abort) atomicExch(err, 1);
 }
@@ -220,7 +278,18 @@ bool make_map(CUtensorMap *map, const float *ptr, int K, int rows, int ld, long 
 }
 
 size_t tc_smem(int nsplit) {
-    return (nsplit == 1 ? (size_t)stages<1>() * 2 : (size_t)stages<3>() * 4) * TILE_BYTES + sizeof(TcShared) + 1024;
+    return (nsplit == 1 ? (size_t)stages<1>() * 2 : (size_t)stages<3>() * 4) * TILE_BYTES +
+           STAGE_FLOATS * sizeof(float) + sizeof(TcShared) + 1024;
+}
+
+int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        check(cudaGetDevice(&dev), "cudaGetDevice");
+        check(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    }
+    return n;
 }
 
 int *error_word() {
@@ -273,12 +342,15 @@ void tc_gemm_nt(cudaStream_t st, int M, int N, int K, float alpha, const float *
         check(cudaFuncSetAttribute(tc_gemm_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm), "attr tc3");
         attr3 = true;
     }
-    dim3 grid((N + TBN - 1) / TBN, (M + TBM - 1) / TBM, batch);
+    const long long ntiles = (long long)((N + TBN - 1) / TBN) * ((M + TBM - 1) / TBM) * batch;
+    const int grid = (int)std::min<long long>(ntiles, sm_count());
     int *err = error_word();
     if (nsplit == 3)
-        tc_gemm_kernel<3><<<grid, 192, sm, st>>>(ma, mb, M, N, K, bA, bB, alpha, beta, C, ldc, sC, err);
+        tc_gemm_kernel<3><<<grid, GEMM_THREADS, sm, st>>>(ma, mb, M, N, K, bA, bB, batch, alpha, beta, C, ldc, sC,
+                                                          err);
     else
-        tc_gemm_kernel<1><<<grid, 192, sm, st>>>(ma, mb, M, N, K, bA, bB, alpha, beta, C, ldc, sC, err);
+        tc_gemm_kernel<1><<<grid, GEMM_THREADS, sm, st>>>(ma, mb, M, N, K, bA, bB, batch, alpha, beta, C, ldc, sC,
+                                                          err);
     check_launch("tc_gemm_kernel");
 }
 
