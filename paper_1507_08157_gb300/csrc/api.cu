@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <initializer_list>
 #include <memory>
 #include <new>
 #include <string>
@@ -136,8 +137,23 @@ void profiler_read(Profiler *p, long long *launches, double *ms, double *flops, 
 void profiler_reset(Profiler *p);
 }  // namespace tddft
 
+namespace {
+// float32 constants of a context: the tensor-core GEMM caches their split copies
+void register_constants(Impl<float> &I) {
+    const float *ps[] = {I.Sc, I.Sv, I.Pc, I.Pv, I.Mc, I.Mv, I.Rc, I.Rv, I.Ac, I.Av};
+    for (const float *p : ps) tc_register_constant(p);
+}
+void register_constants(Impl<double> &) {}
+}  // namespace
+
 tddft_ctx::~tddft_ctx() {
     if (prof) profiler_delete(prof);
+    if (d32) {
+        Impl<float> &I = *d32;
+        const float *ps[] = {I.Sc, I.Sv, I.Pc, I.Pv, I.Mc, I.Mv, I.Rc, I.Rv, I.Ac, I.Av};
+        for (const float *p : ps)
+            if (p) tc_unregister_constant(p);
+    }
 }
 
 namespace {
@@ -497,6 +513,7 @@ void build_impl(tddft_ctx *c, const tddft_system *s) {
     I->Sc = keep(Sc, cc); I->Sv = keep(Sv, vv); I->Pc = keep(Pc, cc); I->Pv = keep(Pv, vv);
     I->Mc = keep(Mc, cc); I->Mv = keep(Mv, vv); I->Rc = keep(Rc, cc); I->Rv = keep(Rv, vv);
     I->Ac = keep(Ac, cc); I->Av = keep(Av, vv);
+    register_constants(*I);
     // kernel pattern mask over (chi, phi) function pairs
     std::vector<double> m((size_t)nc * nv);
     for (int a = 0; a < nc; ++a)

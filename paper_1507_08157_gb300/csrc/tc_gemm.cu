@@ -61,11 +61,14 @@ __device__ __forceinline__ float tf32_rna_dev(float x) {
 }
 
 // NSPLIT = 1: plain TF32 on the raw tiles; 3: three-term split, hi/lo made in shared memory
+// With the split, an operand is either raw (split here) or arrives split (hi and lo maps):
+// a_split / b_split select the latter.
 template <int NSPLIT>
 __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(
-    const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB, int M, int N, int K,
-    int batchA, int batchB, int batch, float alpha, float beta, float *__restrict__ C, int ldc, long long sC,
-    int *err) {
+    const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
+    const __grid_constant__ CUtensorMap mAlo, const __grid_constant__ CUtensorMap mBlo, int a_split, int b_split,
+    int M, int N, int K, int batchA, int batchB, int batch, float alpha, float beta, float *__restrict__ C, int ldc,
+    long long sC, int *err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<unsigned long long>(smem_raw) + 1023ull) & ~1023ull);
@@ -119,9 +122,12 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(
                         break;
                     }
                     unsigned char *st = tiles + (size_t)s * NT * TILE_BYTES;
-                    mbar_expect_tx(&ctl->full[s], 2 * TILE_BYTES);
+                    const int ntx = 2 + (NSPLIT == 3 ? a_split + b_split : 0);
+                    mbar_expect_tx(&ctl->full[s], ntx * TILE_BYTES);
                     tma_load_3d(st, &mA, &ctl->full[s], kb * TBK, m0, ba);
                     tma_load_3d(st + TILE_BYTES, &mB, &ctl->full[s], kb * TBK, n0, bb);
+                    if (NSPLIT == 3 && a_split) tma_load_3d(st + 2 * TILE_BYTES, &mAlo, &ctl->full[s], kb * TBK, m0, ba);
+                    if (NSPLIT == 3 && b_split) tma_load_3d(st + 3 * TILE_BYTES, &mBlo, &ctl->full[s], kb * TBK, n0, bb);
                 }
             }
         }
@@ -182,6 +188,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(
                     unsigned char *st = tiles + (size_t)s * NT * TILE_BYTES;
 #pragma unroll
                     for (int op = 0; op < 2; ++op) {
+                        if (op == 0 ? a_split : b_split) continue;   // arrived split
                         float4 *hi = reinterpret_cast<float4 *>(st + op * TILE_BYTES);
                         float4 *lo = reinterpret_cast<float4 *>(st + (2 + op) * TILE_BYTES);
 #pragma unroll 4
@@ -321,17 +328,23 @@ bool encode_map_2d(CUtensorMap *map, CUtensorMapDataType dt, const void *ptr, un
 }
 
 // C[b] = alpha * A[b] B[b]^T + beta C[b] with A (M x K, ld lda, batch stride sA; 0 = shared) and
-// B (N x K, ldb, sB), both K-contiguous; split: three-term TF32 split made in the kernel, else
-// plain TF32. Rows must start on 16-byte boundaries: lda, ldb, sA, sB multiples of 4 and the
-// pointers 16-byte aligned.
-void tc_gemm_nt(cudaStream_t st, int M, int N, int K, float alpha, const float *A, int lda, long long sA,
-                const float *B, int ldb, long long sB, float beta, float *C, int ldc, long long sC, int batch,
-                bool split) {
+// B (N x K, ldb, sB), both K-contiguous. split: three-term TF32 split; an operand with a lo part
+// (Alo / Blo non-null, same layout) arrives split, one without is split inside the kernel.
+// Rows must start on 16-byte boundaries: lda, ldb, sA, sB multiples of 4 and the pointers
+// 16-byte aligned.
+void tc_gemm_nt(cudaStream_t st, int M, int N, int K, float alpha, const float *A, const float *Alo, int lda,
+                long long sA, const float *B, const float *Blo, int ldb, long long sB, float beta, float *C, int ldc,
+                long long sC, int batch, bool split) {
     const int nsplit = split ? 3 : 1;
-    CUtensorMap ma, mb;
+    CUtensorMap ma, mb, malo, mblo;
     const int bA = sA ? batch : 1, bB = sB ? batch : 1;
     if (!make_map(&ma, A, K, M, lda, sA, bA) || !make_map(&mb, B, K, N, ldb, sB, bB))
         throw CudaError{cudaErrorInvalidValue, "cuTensorMapEncodeTiled"};
+    const bool asp = split && Alo, bsp = split && Blo;
+    if ((asp && !make_map(&malo, Alo, K, M, lda, sA, bA)) || (bsp && !make_map(&mblo, Blo, K, N, ldb, sB, bB)))
+        throw CudaError{cudaErrorInvalidValue, "cuTensorMapEncodeTiled (lo)"};
+    if (!asp) malo = ma;
+    if (!bsp) mblo = mb;
     const size_t sm = tc_smem(nsplit);
     static bool attr1 = false, attr3 = false;
     if (nsplit == 1 && !attr1) {
@@ -346,11 +359,11 @@ void tc_gemm_nt(cudaStream_t st, int M, int N, int K, float alpha, const float *
     const int grid = (int)std::min<long long>(ntiles, sm_count());
     int *err = error_word();
     if (nsplit == 3)
-        tc_gemm_kernel<3><<<grid, GEMM_THREADS, sm, st>>>(ma, mb, M, N, K, bA, bB, batch, alpha, beta, C, ldc, sC,
-                                                          err);
+        tc_gemm_kernel<3><<<grid, GEMM_THREADS, sm, st>>>(ma, mb, malo, mblo, asp ? 1 : 0, bsp ? 1 : 0, M, N, K, bA,
+                                                          bB, batch, alpha, beta, C, ldc, sC, err);
     else
-        tc_gemm_kernel<1><<<grid, GEMM_THREADS, sm, st>>>(ma, mb, M, N, K, bA, bB, batch, alpha, beta, C, ldc, sC,
-                                                          err);
+        tc_gemm_kernel<1><<<grid, GEMM_THREADS, sm, st>>>(ma, mb, malo, mblo, 0, 0, M, N, K, bA, bB, batch, alpha,
+                                                          beta, C, ldc, sC, err);
     check_launch("tc_gemm_kernel");
 }
 
@@ -438,10 +451,74 @@ int grid1(long long n) {
 
 }  // namespace
 
+// Operands registered as constant (matrices fixed for the life of a context) keep a K-major
+// hi/lo copy, made on first use and freed when they are unregistered.
+namespace {
+struct SplitCopy {
+    bool trans;
+    int rows, cols, ld;
+    float *hi, *lo;
+    int kp;
+};
+std::mutex g_const_mu;
+std::vector<std::pair<const float *, std::vector<SplitCopy>>> g_const;   // registered pointer -> copies
+
+std::vector<SplitCopy> *const_entry(const float *p) {
+    for (auto &e : g_const)
+        if (e.first == p) return &e.second;
+    return nullptr;
+}
+
+// hi/lo K-major copy of a constant operand: rows x K out of a (rows x K, !trans) or (K x rows,
+// trans) matrix with leading dimension ld
+bool const_split(cudaStream_t st, const float *p, bool trans, int rows, int K, int ld, SplitCopy *out) {
+    std::lock_guard<std::mutex> lock(g_const_mu);
+    std::vector<SplitCopy> *v = const_entry(p);
+    if (!v) return false;
+    for (const SplitCopy &c : *v)
+        if (c.trans == trans && c.rows == rows && c.cols == K && c.ld == ld) {
+            *out = c;
+            return true;
+        }
+    SplitCopy c{trans, rows, K, ld, nullptr, nullptr, (K + 3) / 4 * 4};
+    const size_t n = (size_t)rows * c.kp;
+    check(cudaMalloc(&c.hi, n * sizeof(float)), "cudaMalloc constant split");
+    check(cudaMalloc(&c.lo, n * sizeof(float)), "cudaMalloc constant split");
+    if (!trans) {
+        split_kernel<<<grid1((long long)n), 256, 0, st>>>(p, rows, K, ld, 0, c.hi, c.lo, c.kp, 0, 1);
+    } else {
+        dim3 g((rows + 31) / 32, (c.kp + 31) / 32, 1);
+        transpose_split_kernel<<<g, dim3(32, 8), 0, st>>>(p, K, rows, ld, 0, c.hi, c.lo, c.kp, 0);
+    }
+    check_launch("constant split");
+    v->push_back(c);
+    *out = c;
+    return true;
+}
+}  // namespace
+
+void tc_register_constant(const float *p) {
+    std::lock_guard<std::mutex> lock(g_const_mu);
+    if (!const_entry(p)) g_const.push_back({p, {}});
+}
+
+void tc_unregister_constant(const float *p) {
+    std::lock_guard<std::mutex> lock(g_const_mu);
+    for (size_t i = 0; i < g_const.size(); ++i)
+        if (g_const[i].first == p) {
+            for (SplitCopy &c : g_const[i].second) {
+                cudaFree(c.hi);
+                cudaFree(c.lo);
+            }
+            g_const.erase(g_const.begin() + (long)i);
+            return;
+        }
+}
+
 // Dispatch of a row-major C[b] = alpha op(A[b]) op(B[b]) + beta C[b] onto the tensor cores. The
-// kernel wants both operands K-contiguous with 16-byte row starts: an operand that already is
-// (A not transposed, B transposed) goes in as it lies; otherwise a transposed (or re-strided)
-// float32 copy is made in scratch. The split into hi/lo parts happens inside the kernel.
+// kernel wants both operands K-contiguous with 16-byte row starts. A registered constant operand
+// comes from its cached hi/lo copy; a K-contiguous variable operand goes in as it lies and is
+// split inside the kernel; any other operand gets a hi/lo K-major copy in scratch.
 void tc_gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, float alpha, const float *A, int lda,
              long long sA, const float *B, int ldb, long long sB, float beta, float *C, int ldc, long long sC,
              int batch, bool split) {
@@ -449,44 +526,61 @@ void tc_gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, float alpha
     auto direct = [](const float *p, int ld, long long s) {
         return reinterpret_cast<unsigned long long>(p) % 16 == 0 && ld % 4 == 0 && s % 4 == 0;
     };
-    const bool a_direct = !ta && direct(A, lda, sA), b_direct = tb && direct(B, ldb, sB);
+    SplitCopy cav{}, cbv{};
+    const SplitCopy *ca = (split && bA == 1 && const_split(st, A, ta, M, K, lda, &cav)) ? &cav : nullptr;
+    const SplitCopy *cb = (split && bB == 1 && const_split(st, B, !tb, N, K, ldb, &cbv)) ? &cbv : nullptr;
+    const bool a_direct = !ca && !ta && direct(A, lda, sA), b_direct = !cb && tb && direct(B, ldb, sB);
+    const bool a_copy = !ca && !a_direct, b_copy = !cb && !b_direct;
     const int Kp = (K + 3) / 4 * 4;                     // 16-byte rows for the tensor maps
+    const int nsp = split ? 2 : 1;                      // copies carry hi and lo when splitting
     auto up64 = [](size_t n) { return (n + 63) / 64 * 64; };
-    const size_t na = a_direct ? 0 : up64((size_t)M * Kp * bA), nbt = b_direct ? 0 : up64((size_t)N * Kp * bB);
-    float *base = (na + nbt) ? scratch().get(na + nbt) : nullptr;
-    const float *Ak = A, *Bk = B;
+    const size_t na = a_copy ? up64((size_t)M * Kp * bA) : 0, nbt = b_copy ? up64((size_t)N * Kp * bB) : 0;
+    float *base = (na + nbt) ? scratch().get(nsp * (na + nbt)) : nullptr;
+    const float *Ak = A, *Alo = nullptr, *Bk = B, *Blo = nullptr;
     int lak = lda, lbk = ldb;
     long long sak = sA, sbk = sB;
-    if (!a_direct) {
-        float *Ac = base;
+    if (ca) {
+        Ak = ca->hi;
+        Alo = ca->lo;
+        lak = ca->kp;
+        sak = 0;
+    } else if (a_copy) {
+        float *Ah = base, *Al = split ? base + na : nullptr;
         const long long sa = (long long)M * Kp;
         if (!ta) {
-            split_kernel<<<grid1((long long)M * Kp * bA), 256, 0, st>>>(A, M, K, lda, sA, Ac, nullptr, Kp, sa, bA);
+            split_kernel<<<grid1((long long)M * Kp * bA), 256, 0, st>>>(A, M, K, lda, sA, Ah, Al, Kp, sa, bA);
         } else {
             dim3 g((M + 31) / 32, (Kp + 31) / 32, bA);
-            transpose_split_kernel<<<g, dim3(32, 8), 0, st>>>(A, K, M, lda, sA, Ac, nullptr, Kp, sa);
+            transpose_split_kernel<<<g, dim3(32, 8), 0, st>>>(A, K, M, lda, sA, Ah, Al, Kp, sa);
         }
         check_launch("tc copy A");
-        Ak = Ac;
+        Ak = Ah;
+        Alo = Al;
         lak = Kp;
         sak = bA > 1 ? sa : 0;
     }
-    if (!b_direct) {
-        float *Bc = base + na;
+    if (cb) {
+        Bk = cb->hi;
+        Blo = cb->lo;
+        lbk = cb->kp;
+        sbk = 0;
+    } else if (b_copy) {
+        float *Bh = base + nsp * na, *Bl = split ? base + nsp * na + nbt : nullptr;
         const long long sb = (long long)N * Kp;
         if (tb) {
-            split_kernel<<<grid1((long long)N * Kp * bB), 256, 0, st>>>(B, N, K, ldb, sB, Bc, nullptr, Kp, sb, bB);
+            split_kernel<<<grid1((long long)N * Kp * bB), 256, 0, st>>>(B, N, K, ldb, sB, Bh, Bl, Kp, sb, bB);
         } else {
             dim3 g((N + 31) / 32, (Kp + 31) / 32, bB);
-            transpose_split_kernel<<<g, dim3(32, 8), 0, st>>>(B, K, N, ldb, sB, Bc, nullptr, Kp, sb);
+            transpose_split_kernel<<<g, dim3(32, 8), 0, st>>>(B, K, N, ldb, sB, Bh, Bl, Kp, sb);
         }
         check_launch("tc copy B");
-        Bk = Bc;
+        Bk = Bh;
+        Blo = Bl;
         lbk = Kp;
         sbk = bB > 1 ? sb : 0;
     }
     // both maps span the K real columns (copies are zero-padded to Kp; reads past K fill zeros)
-    tc_gemm_nt(st, M, N, K, alpha, Ak, lak, sak, Bk, lbk, sbk, beta, C, ldc, sC, batch, split);
+    tc_gemm_nt(st, M, N, K, alpha, Ak, Alo, lak, sak, Bk, Blo, lbk, sbk, beta, C, ldc, sC, batch, split);
 }
 
 int *tc_error_word() { return error_word(); }

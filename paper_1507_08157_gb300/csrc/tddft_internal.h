@@ -85,6 +85,11 @@ struct GridShape {
 };
 
 // ---------------------------------------------------------------------------------------------
+// float32 matrices that stay fixed while registered: the tensor-core GEMM keeps their split
+// (hi/lo, K-major) copies; unregister before freeing them
+void tc_register_constant(const float *p);
+void tc_unregister_constant(const float *p);
+
 // dense GEMM, row-major: C[b] = alpha * op(A[b]) op(B[b]) + beta * C[b]
 template <typename T>
 void gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, T alpha, const T *A, int lda,
