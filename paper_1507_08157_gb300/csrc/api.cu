@@ -29,6 +29,34 @@ void check_launch(const char *where) {
     if (e != cudaSuccess) throw CudaError{e, where};
 }
 
+namespace roots {
+// kernels of the coupled Newton-Schulz iteration for the overlap square roots (float64)
+__global__ void ns_init_kernel(const double *S, double inv_c, double *Y, double *Z, int n) {
+    const long long tot = (long long)n * n;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x) {
+        Y[i] = S[i] * inv_c;
+        Z[i] = (i / n == i % n) ? 1.0 : 0.0;
+    }
+}
+// T = (3 I - T) / 2 and dev = max |T_old - I| (bit pattern of a non-negative double)
+__global__ void ns_step_kernel(double *T, int n, unsigned long long *dev) {
+    const long long tot = (long long)n * n;
+    double m = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x) {
+        const double d = (i / n == i % n) ? 1.0 : 0.0;
+        m = fmax(m, fabs(T[i] - d));
+        T[i] = 0.5 * (3.0 * d - T[i]);
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(dev, (unsigned long long)__double_as_longlong(m));
+}
+__global__ void scale_kernel64(const double *X, double a, double *Y, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        Y[i] = a * X[i];
+}
+
+}  // namespace roots
+
 namespace {
 
 struct InvalidArg {
@@ -56,6 +84,9 @@ struct Impl {
     TileSet<T> chi, phi;
     T *Sc = nullptr, *Sv = nullptr, *Pc = nullptr, *Pv = nullptr, *Mc = nullptr, *Mv = nullptr;
     T *Rc = nullptr, *Rv = nullptr, *Ac = nullptr, *Av = nullptr, *mask = nullptr, *fxc = nullptr;
+    // preconditioner in Loewdin variables: S^{1/2}, S^{-1/2} of both overlaps and the transformed
+    // M~c = Sc^{1/2} Mc Sc^{-1/2}, M~v = Sv^{-1/2} Mv Sv^{1/2}
+    T *Sch = nullptr, *Scmh = nullptr, *Svh = nullptr, *Svmh = nullptr, *Mct = nullptr, *Mvt = nullptr;
     double *fxc64 = nullptr;
     // tensor-core grid path (float32 contexts): point-major f16 chi tables [tile][512][CK]
     unsigned short *chi_pm = nullptr;
@@ -140,7 +171,8 @@ void profiler_reset(Profiler *p);
 namespace {
 // float32 constants of a context: the tensor-core GEMM caches their split copies
 void register_constants(Impl<float> &I) {
-    const float *ps[] = {I.Sc, I.Sv, I.Pc, I.Pv, I.Mc, I.Mv, I.Rc, I.Rv, I.Ac, I.Av};
+    const float *ps[] = {I.Sc, I.Sv, I.Pc, I.Pv, I.Mc, I.Mv, I.Rc, I.Rv, I.Ac, I.Av, I.Sch, I.Scmh, I.Svh, I.Svmh,
+                         I.Mct, I.Mvt};
     for (const float *p : ps) tc_register_constant(p);
 }
 void register_constants(Impl<double> &) {}
@@ -150,7 +182,8 @@ tddft_ctx::~tddft_ctx() {
     if (prof) profiler_delete(prof);
     if (d32) {
         Impl<float> &I = *d32;
-        const float *ps[] = {I.Sc, I.Sv, I.Pc, I.Pv, I.Mc, I.Mv, I.Rc, I.Rv, I.Ac, I.Av};
+        const float *ps[] = {I.Sc, I.Sv, I.Pc, I.Pv, I.Mc, I.Mv, I.Rc, I.Rv, I.Ac, I.Av, I.Sch, I.Scmh, I.Svh, I.Svmh,
+                             I.Mct, I.Mvt};
         for (const float *p : ps)
             if (p) tc_unregister_constant(p);
     }
@@ -413,6 +446,50 @@ void apply_impl(tddft_ctx *c, Impl<T> &I, int k, const T *P, T *f) {
 }
 
 // ---- context construction ----------------------------------------------------------------------
+// S^{1/2} and S^{-1/2} of a symmetric positive definite n x n matrix (device, float64): Y -> A^{1/2},
+// Z -> A^{-1/2} for A = S / c, c >= the largest eigenvalue (max absolute row sum of the host copy)
+void overlap_roots(cudaStream_t st, Mem &tmp, const double *S_dev, const double *S_host, int n, double *Sh,
+                   double *Smh) {
+    double c = 0.0;
+    for (int i = 0; i < n; ++i) {
+        double r = 0.0;
+        for (int j = 0; j < n; ++j) r += std::fabs(S_host[(size_t)i * n + j]);
+        c = std::max(c, r);
+    }
+    if (!(c > 0.0)) throw InvalidArg{"overlap matrix is zero"};
+    const long long nn = (long long)n * n;
+    double *Y = tmp.alloc<double>(nn), *Z = tmp.alloc<double>(nn), *T = tmp.alloc<double>(nn);
+    double *Y2 = tmp.alloc<double>(nn), *Z2 = tmp.alloc<double>(nn);
+    unsigned long long *dev = tmp.alloc<unsigned long long>(1);
+    const int gb = (int)std::min<long long>((nn + 255) / 256, 1216);
+    roots::ns_init_kernel<<<gb, 256, 0, st>>>(S_dev, 1.0 / c, Y, Z, n);
+    check_launch("ns_init");
+    int settled = 0;
+    for (int it = 0; it < 100 && settled < 2; ++it) {
+        gemm<double>(st, false, false, n, n, n, 1.0, Z, n, 0, Y, n, 0, 0.0, T, n, 0, 1);   // T = Z Y
+        check(cudaMemsetAsync(dev, 0, sizeof(unsigned long long), st), "memset ns dev");
+        roots::ns_step_kernel<<<gb, 256, 0, st>>>(T, n, dev);
+        check_launch("ns_step");
+        gemm<double>(st, false, false, n, n, n, 1.0, Y, n, 0, T, n, 0, 0.0, Y2, n, 0, 1);  // Y T
+        gemm<double>(st, false, false, n, n, n, 1.0, T, n, 0, Z, n, 0, 0.0, Z2, n, 0, 1);  // T Z
+        std::swap(Y, Y2);
+        std::swap(Z, Z2);
+        unsigned long long hb = 0;
+        check(cudaMemcpyAsync(&hb, dev, sizeof(hb), cudaMemcpyDeviceToHost, st), "D2H ns dev");
+        check(cudaStreamSynchronize(st), "sync ns");
+        double d;
+        std::memcpy(&d, &hb, sizeof(d));
+        if (!std::isfinite(d)) throw InvalidArg{"overlap square root did not converge (matrix not positive definite?)"};
+        // quadratic convergence: once |ZY - I| is below 1e-10 one more step reaches the rounding floor
+        if (d < 1e-10) ++settled;
+    }
+    if (settled < 2) throw InvalidArg{"overlap square root did not converge (matrix not positive definite?)"};
+    roots::scale_kernel64<<<gb, 256, 0, st>>>(Y, std::sqrt(c), Sh, nn);
+    check_launch("scale root");
+    roots::scale_kernel64<<<gb, 256, 0, st>>>(Z, 1.0 / std::sqrt(c), Smh, nn);
+    check_launch("scale inverse root");
+}
+
 template <typename T>
 void build_impl(tddft_ctx *c, const tddft_system *s) {
     auto I = std::make_unique<Impl<T>>();
@@ -505,6 +582,17 @@ void build_impl(tddft_ctx *c, const tddft_system *s) {
     gemm<double>(st, false, false, nv, nv, nv, 1.0, Sv, nv, 0, Pv, nv, 0, 0.0, Rv, nv, 0, 1);   // S^phi P^v
     gemm<double>(st, false, false, nc, nc, nc, 1.0, Sc, nc, 0, Rc, nc, 0, 0.0, Ac, nc, 0, 1);   // S P^c S
     gemm<double>(st, false, false, nv, nv, nv, 1.0, Rv, nv, 0, Sv, nv, 0, 0.0, Av, nv, 0, 1);   // S P^v S
+    // Loewdin variables of the preconditioner's CG: G~ = Sc^{1/2} G Sv^{1/2} turns the trace metric
+    // into the Frobenius product and the operator into M~c G~ - G~ M~v
+    double *Sch = tmpm.alloc<double>(cc), *Scmh = tmpm.alloc<double>(cc), *Svh = tmpm.alloc<double>(vv),
+           *Svmh = tmpm.alloc<double>(vv), *Mct = tmpm.alloc<double>(cc), *Mvt = tmpm.alloc<double>(vv),
+           *W = tmpm.alloc<double>(std::max(cc, vv));
+    overlap_roots(st, tmpm, Sc, s->S_chi, nc, Sch, Scmh);
+    overlap_roots(st, tmpm, Sv, s->S_phi, nv, Svh, Svmh);
+    gemm<double>(st, false, false, nc, nc, nc, 1.0, Sch, nc, 0, Mc, nc, 0, 0.0, W, nc, 0, 1);
+    gemm<double>(st, false, false, nc, nc, nc, 1.0, W, nc, 0, Scmh, nc, 0, 0.0, Mct, nc, 0, 1);  // Sc^1/2 Mc Sc^-1/2
+    gemm<double>(st, false, false, nv, nv, nv, 1.0, Svmh, nv, 0, Mv, nv, 0, 0.0, W, nv, 0, 1);
+    gemm<double>(st, false, false, nv, nv, nv, 1.0, W, nv, 0, Svh, nv, 0, 0.0, Mvt, nv, 0, 1);   // Sv^-1/2 Mv Sv^1/2
     auto keep = [&](const double *d, long long cnt) {
         T *o = I->mem.template alloc<T>(cnt);
         convert<double, T>(st, d, o, cnt);
@@ -513,6 +601,8 @@ void build_impl(tddft_ctx *c, const tddft_system *s) {
     I->Sc = keep(Sc, cc); I->Sv = keep(Sv, vv); I->Pc = keep(Pc, cc); I->Pv = keep(Pv, vv);
     I->Mc = keep(Mc, cc); I->Mv = keep(Mv, vv); I->Rc = keep(Rc, cc); I->Rv = keep(Rv, vv);
     I->Ac = keep(Ac, cc); I->Av = keep(Av, vv);
+    I->Sch = keep(Sch, cc); I->Scmh = keep(Scmh, cc); I->Svh = keep(Svh, vv); I->Svmh = keep(Svmh, vv);
+    I->Mct = keep(Mct, cc); I->Mvt = keep(Mvt, vv);
     register_constants(*I);
     // kernel pattern mask over (chi, phi) function pairs
     std::vector<double> m((size_t)nc * nv);
@@ -729,13 +819,14 @@ void precondition(tddft_ctx *c, tddft_state *S, const T *h, T *z) {
         check(cudaMemcpyAsync(z, h, tot * sizeof(T), cudaMemcpyDeviceToDevice, st), "copy z");
         return;
     }
-    T *r = B.cLpp, *cr = B.cr, *p = B.cp, *cp = B.cpv, *Lp = B.cLp, *cLp = B.cLv;
-    check(cudaMemsetAsync(z, 0, tot * sizeof(T), st), "memset z");
-    check(cudaMemcpyAsync(r, h, tot * sizeof(T), cudaMemcpyDeviceToDevice, st), "copy r");
-    covariant<T>(c, I, k2, r, cr, B.tmp);
+    // CG in Loewdin variables X~ = Sc^{1/2} X Sv^{1/2}: the trace metric of Eq. precond's CG becomes
+    // the Frobenius product and L becomes M~c X~ - X~ M~v, so an iteration takes two products
+    // instead of four; the iterates are those of the CG in the original variables
+    T *r = B.cLpp, *zt = B.cr, *p = B.cp, *Lp = B.cLp;
+    check(cudaMemsetAsync(zt, 0, tot * sizeof(T), st), "memset z");
+    sandwich<T>(c, k2, I.Sch, h, I.Svh, r, B.tmp);           // r~ = h~
     check(cudaMemcpyAsync(p, r, tot * sizeof(T), cudaMemcpyDeviceToDevice, st), "copy p");
-    check(cudaMemcpyAsync(cp, cr, tot * sizeof(T), cudaMemcpyDeviceToDevice, st), "copy cp");
-    dots<T>(st, r, len, cr, len, k2, len, B.dvec2, B.gscr);
+    dots<T>(st, r, len, r, len, k2, len, B.dvec2, B.gscr);
     cg_init(st, k2, c->opt.precond_tol, B.dvec2, B.cg_rr, B.cg_r0, B.cg_active, B.cg_nactive);
     int *hn = reinterpret_cast<int *>(S->host + 2 * S->k) + 1;
     for (int it = 0; it < c->opt.precond_maxit; ++it) {
@@ -743,21 +834,19 @@ void precondition(tddft_ctx *c, tddft_state *S, const T *h, T *z) {
         check(cudaStreamSynchronize(st), "sync cg");
         if (*hn == 0) break;
         S->inner_iters += 1;
-        gemm<T>(st, false, false, nc, nv, nc, T(1), I.Mc, nc, 0, p, nv, len, T(0), Lp, nv, len, k2);
-        gemm<T>(st, false, false, k2 * nc, nv, nv, T(-1), p, nv, 0, I.Mv, nv, 0, T(1), Lp, nv, 0, 1);
-        covariant<T>(c, I, k2, Lp, cLp, B.tmp);
-        dots<T>(st, cp, len, Lp, len, k2, len, B.cg_pLp, B.gscr);
+        gemm<T>(st, false, false, nc, nv, nc, T(1), I.Mct, nc, 0, p, nv, len, T(0), Lp, nv, len, k2);
+        gemm<T>(st, false, false, k2 * nc, nv, nv, T(-1), p, nv, 0, I.Mvt, nv, 0, T(1), Lp, nv, 0, 1);
+        dots<T>(st, p, len, Lp, len, k2, len, B.cg_pLp, B.gscr);
         cg_scalars(st, k2, 0, c->opt.precond_tol, B.cg_pLp, B.cg_rrn, B.cg_rr, B.cg_r0, B.cg_alpha,
                    B.cg_beta, B.cg_active, B.cg_nactive);
-        axpy_dev<T>(st, B.cg_alpha, 1, 1.0, z, p, len, k2);
+        axpy_dev<T>(st, B.cg_alpha, 1, 1.0, zt, p, len, k2);
         axpy_dev<T>(st, B.cg_alpha, 1, -1.0, r, Lp, len, k2);
-        axpy_dev<T>(st, B.cg_alpha, 1, -1.0, cr, cLp, len, k2);
-        dots<T>(st, r, len, cr, len, k2, len, B.cg_rrn, B.gscr);
+        dots<T>(st, r, len, r, len, k2, len, B.cg_rrn, B.gscr);
         cg_scalars(st, k2, 1, c->opt.precond_tol, B.cg_pLp, B.cg_rrn, B.cg_rr, B.cg_r0, B.cg_alpha,
                    B.cg_beta, B.cg_active, B.cg_nactive);
         cg_dir<T>(st, p, r, B.cg_beta, len, k2);
-        cg_dir<T>(st, cp, cr, B.cg_beta, len, k2);
     }
+    sandwich<T>(c, k2, I.Scmh, zt, I.Svmh, z, B.tmp);        // z = Sc^{-1/2} z~ Sv^{-1/2}
 }
 
 // learned preconditioner: fixed features and feature rows on first use; scales for k states
