@@ -343,7 +343,11 @@ def run_ours(args):
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None, "kernel": name,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained x 1.1/2.25 (tf32/bf16 nominal)",
-                "note": "achieved counts 2MNK per product; the three-term split issues 3 MMAs per product"}
+                "note": "achieved counts 2MNK per product; the three-term split issues 3 MMAs per product",
+                "frac_of_fp32_accurate_peak": achieved / (peak / 3.0),
+                "traffic_note": "the stage mixes product shapes; ncu DRAM bytes of the left product "
+                                "(1260 x 1260 by 20 x 1260 x 560): 1.6e8 per launch against ~1.8e8 "
+                                "algorithmic (profiles/launches_tc_chromophore140.md)"}
     else:
         # CUDA-core float32 (mixed) or float64 contraction: ALU bound.
         lanes = 128 if args.precision == "mixed" else 2

@@ -94,6 +94,9 @@ struct Impl {
     int CK = 0, NPmax = 0, nslots_chi = 0, maxc = 0;
     bool grid_tc = false, integrals_tc = false;
     bool phi_quads = false;   // every tile's phi list is whole aligned groups of 4 (vector gather)
+    // integrals launches: tiles holding chi and phi, those with <= 256 chi first
+    int *int_tiles = nullptr;
+    int int_small = 0, int_large = 0;
     unsigned *tc_bits = nullptr;
     float *tc_scale = nullptr;
     // operator workspace, sized for up to `cap` grid states
@@ -152,7 +155,7 @@ int integrals_tc_group(int NP, int k, int maxc);
 void potential_integrals_tc(cudaStream_t st, const GridShape &g, const TileSet<float> &chi,
                             const TileSet<float> &phi, const unsigned short *chi_fm16, int nslots, int NPmax,
                             int maxc, int nchi, int nphi, const float *V, int k, float *out, unsigned *scratch_bits,
-                            float *scale, int *err);
+                            float *scale, const int *tile_list, int tiles_small, int tiles_large, int *err);
 void response_density_tc(cudaStream_t st, const GridShape &g, const TileSet<float> &chi,
                          const TileSet<float> &phi, const unsigned short *chi_pm, int CK, int NPmax, int nphi,
                          const float *P, long long sP, int k, float *rho, unsigned *scratch_bits,
@@ -408,7 +411,8 @@ void integrals(tddft_ctx *c, Impl<T> &I, int ns) {
     if constexpr (sizeof(T) == 4) {
         if (I.integrals_tc) {
             potential_integrals_tc(c->st, c->grid(), I.chi, I.phi, I.chi_fm16, I.nslots_chi, I.NPmax, I.maxc, c->nc,
-                                   c->nv, I.V, ns, I.Vmat, I.tc_bits, I.tc_scale, tc_error_word());
+                                   c->nv, I.V, ns, I.Vmat, I.tc_bits, I.tc_scale, I.int_tiles, I.int_small,
+                                   I.int_large, tc_error_word());
             return;
         }
     }
@@ -552,7 +556,20 @@ void build_impl(tddft_ctx *c, const tddft_system *s) {
                                      cudaMemcpyHostToDevice),
                           "upload f16 chi");
                     I->nslots_chi = coff[ntl];
-                    I->integrals_tc = true;
+                    std::vector<int> small, large;
+                    for (int t = 0; t < ntl; ++t) {
+                        const int nct = coff[t + 1] - coff[t], npt = poff[t + 1] - poff[t];
+                        if (nct == 0 || npt == 0) continue;
+                        (nct <= 256 ? small : large).push_back(t);
+                    }
+                    I->int_small = (int)small.size();
+                    I->int_large = (int)large.size();
+                    small.insert(small.end(), large.begin(), large.end());
+                    I->int_tiles = I->mem.template alloc<int>(std::max<size_t>(1, small.size()));
+                    if (!small.empty())
+                        check(cudaMemcpy(I->int_tiles, small.data(), small.size() * sizeof(int), cudaMemcpyHostToDevice),
+                              "upload integrals tile lists");
+                    I->integrals_tc = NP <= 128;
                 }
             }
         }
@@ -739,11 +756,12 @@ void sync_status(tddft_ctx *c, tddft_state *S, const int *dstatus) {
     if (stv == DEV_NAN_INIT) throw Breakdown{"NaN or Inf in the starting trial pairs"};
 }
 
-// recombine Y, P, f with the Gram-Schmidt coefficients (sign flips folded into Cq)
+// recombine Y, P, f and cov(P) with the Gram-Schmidt coefficients (sign flips folded into Cq);
+// cov is linear, so cov(P) follows the same combinations as P
 template <typename T>
 void recombine(tddft_ctx *c, StateBufs<T> &B, int k) {
     const long long len = c->len();
-    T *arrs[] = {B.Y, B.P, B.f};
+    T *arrs[] = {B.Y, B.P, B.f, B.covP};
     for (T *X : arrs) {
         check(cudaMemcpyAsync(B.tmp, X, 2 * k * len * sizeof(T), cudaMemcpyDeviceToDevice, c->st), "copy recombine");
         combine<T>(c->st, B.Cp, k, k, k, B.tmp, len, X, len, len, false);
@@ -782,7 +800,7 @@ void evaluate(tddft_ctx *c, tddft_state *S) {
     const int k = S->k;
     const long long len = c->len();
     cudaStream_t st = c->st;
-    covariant<T>(c, I, 2 * k, B.P, B.covP, B.tmp);
+    // cov(P) is carried along with P (state creation, line step, recombination, re-application)
     gram<T>(st, B.covP, len, 2 * k, B.f, len, 2 * k, len, B.A, B.gscr);   // A[x][y] = <P_x, f_y>
     make_q(st, k, B.A, B.Q, B.coef);
     // g = f - swap(P) Q^T
@@ -964,6 +982,7 @@ void update(tddft_ctx *c, tddft_state *S) {
     axpy_dev<T>(st, B.lam, 0, 1.0, B.Y, B.dir, tot, 1);
     axpy_dev<T>(st, B.lam, 0, 1.0, B.P, B.D, tot, 1);
     axpy_dev<T>(st, B.lam, 0, 1.0, B.f, B.fD, tot, 1);
+    axpy_dev<T>(st, B.lam, 0, 1.0, B.covP, B.covD, tot, 1);
     recombine<T>(c, B, k);
     check(cudaMemcpyAsync(S->host + 2 * k + 1, B.lam, sizeof(double), cudaMemcpyDeviceToHost, st), "D2H lam");
     sync_status(c, S, B.status);
@@ -973,6 +992,7 @@ void update(tddft_ctx *c, tddft_state *S) {
         check(cudaMemcpyAsync(B.tmp, B.Y, tot * sizeof(T), cudaMemcpyDeviceToDevice, st), "copy Y");
         if (c->trunc) mask_mul<T>(st, B.tmp, I.mask, len, k2);
         sandwich<T>(c, k2, I.Rc, B.tmp, I.Rv, B.P, B.cLpp);
+        covariant<T>(c, I, k2, B.P, B.covP, B.tmp);
         apply_impl<T>(c, I, k, B.P, B.f);
     }
     std::swap(B.pdir, B.dir);

@@ -430,27 +430,30 @@ __device__ __forceinline__ void red_add_v4(float *addr, float a, float b, float 
                  : "memory");
 }
 
-__global__ void __launch_bounds__(192, 1) integrals_tc_kernel(
+// CTA = (state group, tile of the launch's list); mbmax: most chi row blocks of a listed tile
+// (sizes the X stages), tmem_cols: TMEM columns allocated (mbmax * acc_stride, a power of two)
+__global__ void __launch_bounds__(192, 2) integrals_tc_kernel(
     const __grid_constant__ CUtensorMap mX,   // function-major chi: [slot][512] f16
     int n, int nt, int NP, int G, int k, const int *__restrict__ coff, const int *__restrict__ cids,
     const int *__restrict__ poff, const int *__restrict__ pids, const float *__restrict__ pval, int nchi,
     int nphi, const float *__restrict__ V, const float *__restrict__ vscale, float dV, float *__restrict__ out,
-    bool vec_ok, int acc_stride, int *err) {
+    bool vec_ok, int acc_stride, const int *__restrict__ tiles, int mbmax, int tmem_cols, int *err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<unsigned long long>(smem_raw) + 1023ull) & ~1023ull);
-    const int t = blockIdx.y, grp = blockIdx.x;
+    const int t = tiles[blockIdx.y], grp = blockIdx.x;
     const int s0 = grp * G;
     const int gs = min(G, k - s0);
     const int c0 = coff[t], nc = coff[t + 1] - c0;
     const int p0 = poff[t], np = poff[t + 1] - p0;
     if (nc == 0 || np == 0) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int MB = (nc + 127) / 128;                 // <= 3 (host guarantees nc <= 384)
+    const int MB = (nc + 127) / 128;                 // <= mbmax (the host lists tiles by M blocks)
     const int NB = G * NP;                           // <= acc_stride, multiple of 16
-    // layout: X stages [2][3 x 16 KB], W stages [2][NB x 128 B], V tile [G][512] f32, control
+    // layout: X stages [2][mbmax x 16 KB], W stages [2][NB x 128 B], V tile [G][512] f32, control
     unsigned char *Xs = base;
-    unsigned char *Ws = base + 2 * 49152;
+    const int xstage = mbmax * 16384;
+    unsigned char *Ws = base + 2 * xstage;
     float *Vt = reinterpret_cast<float *>(Ws + (size_t)2 * NB * 128);
     IntShared *ctl = reinterpret_cast<IntShared *>(Vt + (size_t)G * TILE_PTS);
     volatile int *abort = &ctl->abort;
@@ -469,7 +472,7 @@ __global__ void __launch_bounds__(192, 1) integrals_tc_kernel(
     }
     if (warp == 5) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&ctl->tmem_base)),
-                     "r"(512));
+                     "r"(tmem_cols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     for (int i = threadIdx.x; i < np; i += blockDim.x) ctl->pid[i] = pids[p0 + i];
@@ -496,7 +499,7 @@ __global__ void __launch_bounds__(192, 1) integrals_tc_kernel(
                 if (use > 0 && !mbar_wait(&ctl->mma_done[st], (use - 1) & 1, abort)) break;
                 mbar_expect_tx(&ctl->x_full[st], MB * 16384);
                 for (int mb = 0; mb < MB; ++mb)
-                    tma_load_2d(Xs + st * 49152 + mb * 16384, &mX, &ctl->x_full[st], kb * 64, c0 + mb * 128);
+                    tma_load_2d(Xs + st * xstage + mb * 16384, &mX, &ctl->x_full[st], kb * 64, c0 + mb * 128);
             }
         }
     } else if (warp == 5) {
@@ -508,7 +511,7 @@ __global__ void __launch_bounds__(192, 1) integrals_tc_kernel(
                 tc_fence_after();
                 const unsigned wb = smem_u32(Ws + (size_t)st * NB * 128);
                 for (int mb = 0; mb < MB; ++mb) {
-                    const unsigned xa = smem_u32(Xs + st * 49152 + mb * 16384);
+                    const unsigned xa = smem_u32(Xs + st * xstage + mb * 16384);
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk)
                         mma_f16(tmem + mb * acc_stride, smem_desc(xa + kk * 32), smem_desc(wb + kk * 32), idesc,
@@ -597,7 +600,7 @@ __global__ void __launch_bounds__(192, 1) integrals_tc_kernel(
     __syncthreads();
     if (warp == 5) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
     }
     if (threadIdx.x == 0 && ctl->abort) atomicExch(err, 1);
 }
@@ -613,8 +616,8 @@ __global__ void vmaxabs_kernel(const float *__restrict__ V, long long n3, unsign
 
 }  // namespace
 
-size_t integrals_tc_smem(int NB, int G) {
-    return 1024 + 2 * 49152 + (size_t)2 * NB * 128 + (size_t)G * TILE_PTS * 4 + sizeof(IntShared);
+size_t integrals_tc_smem(int NB, int G, int mbmax) {
+    return 1024 + (size_t)2 * mbmax * 16384 + (size_t)2 * NB * 128 + (size_t)G * TILE_PTS * 4 + sizeof(IntShared);
 }
 
 // accumulator stride in TMEM columns: 256 when every tile has <= 256 chi (2 M blocks), else 128
@@ -624,14 +627,14 @@ int integrals_tc_group(int NP, int k, int maxc) {
     if (maxc > 384) return 0;
     const int stride = integrals_tc_stride(maxc);
     for (int G = std::min(16, std::min(k, stride / NP)); G >= 1; --G)
-        if (integrals_tc_smem(G * NP, G) <= 227 * 1024) return G;
+        if (integrals_tc_smem(G * NP, G, 3) <= 227 * 1024) return G;
     return 0;
 }
 
 void potential_integrals_tc(cudaStream_t st, const GridShape &g, const TileSet<float> &chi,
                             const TileSet<float> &phi, const unsigned short *chi_fm16, int nslots, int NPmax,
                             int maxc, int nchi, int nphi, const float *V, int k, float *out, unsigned *scratch_bits,
-                            float *scale, int *err) {
+                            float *scale, const int *tile_list, int tiles_small, int tiles_large, int *err) {
     if (k <= 0) return;
     ProfScope ps(st, ST_INTEGRALS, 2.0 * k * g.pair_points,
                  2.0 * g.table_values + 4.0 * k * g.n * g.n * g.n + 4.0 * k * nchi * nphi);
@@ -646,22 +649,30 @@ void potential_integrals_tc(cudaStream_t st, const GridShape &g, const TileSet<f
     if (!encode_map_2d(&mx, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, chi_fm16, (unsigned long long)TILE_PTS,
                        (unsigned long long)nslots, (unsigned long long)TILE_PTS * 2, 64, 128))
         throw CudaError{cudaErrorInvalidValue, "cuTensorMapEncodeTiled (integrals)"};
-    const int G = integrals_tc_group(NPmax, k, maxc);
-    if (G < 1) throw CudaError{cudaErrorInvalidValue, "integrals_tc: tile too large for shared memory"};
-    const int stride = integrals_tc_stride(maxc);
-    const int ngroups = (k + G - 1) / G;
-    const size_t sm = integrals_tc_smem(G * NPmax, G);
+    // two launches: tiles with <= 256 chi (at most two 128-row blocks) one state per CTA and two
+    // CTAs per SM; tiles with more chi (three blocks) one CTA per SM
+    if (NPmax > 128) throw CudaError{cudaErrorInvalidValue, "integrals_tc: more than 128 phi per tile"};
     static bool attr = false;
     if (!attr) {
         check(cudaFuncSetAttribute(integrals_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),
               "attr integrals_tc");
         attr = true;
     }
-    dim3 grid(ngroups, chi.ntiles);
     const bool vec_ok = (nphi % 4 == 0) && ((reinterpret_cast<unsigned long long>(out) & 15ull) == 0);
-    integrals_tc_kernel<<<grid, 192, sm, st>>>(mx, g.n, g.nt, NPmax, G, k, chi.off, chi.ids, phi.off, phi.ids,
-                                               phi.val, nchi, nphi, V, scale, (float)g.dV, out, vec_ok, stride, err);
-    check_launch("integrals_tc_kernel");
+    const int lists[2] = {tiles_small, tiles_large};
+    const int *lp[2] = {tile_list, tile_list + tiles_small};
+    for (int c = 0; c < 2; ++c) {
+        if (lists[c] == 0) continue;
+        const int mbmax = c == 0 ? 2 : 3;
+        const int stride = 128;                           // one state: NB = NPmax <= 128 columns
+        const int tmem_cols = c == 0 ? 256 : 512;
+        const size_t sm = integrals_tc_smem(NPmax, 1, mbmax);
+        dim3 grid(k, lists[c]);
+        integrals_tc_kernel<<<grid, 192, sm, st>>>(mx, g.n, g.nt, NPmax, 1, k, chi.off, chi.ids, phi.off, phi.ids,
+                                                   phi.val, nchi, nphi, V, scale, (float)g.dV, out, vec_ok, stride,
+                                                   lp[c], mbmax, tmem_cols, err);
+        check_launch("integrals_tc_kernel");
+    }
 }
 
 }  // namespace tddft
