@@ -63,7 +63,8 @@ __device__ __forceinline__ float tf32_rna_dev(float x) {
 // NSPLIT = 1: plain TF32 on the raw tiles; 3: three-term split, hi/lo made in shared memory
 // With the split, an operand is either raw (split here) or arrives split (hi and lo maps):
 // a_split / b_split select the latter.
-template <int NSPLIT>
+// TN: output tile width (128, or 112 when N is a multiple of 112, so that N = 560 needs no padding)
+template <int NSPLIT, int TN>
 __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(
     const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
     const __grid_constant__ CUtensorMap mAlo, const __grid_constant__ CUtensorMap mBlo, int a_split, int b_split,
@@ -78,7 +79,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(
     float *staging = reinterpret_cast<float *>(base + (size_t)S * NT * TILE_BYTES);
     TcShared *ctl = reinterpret_cast<TcShared *>(staging + STAGE_FLOATS);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tn = (N + TBN - 1) / TBN, tm = (M + TBM - 1) / TBM;
+    const int tn = (N + TN - 1) / TN, tm = (M + TBM - 1) / TBM;
     const int ntiles = tn * tm * batch;
     const int nk = (K + TBK - 1) / TBK;
     volatile int *abort = &ctl->abort;
@@ -112,7 +113,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(
             long long it = 0;
             bool go = true;
             for (int t = blockIdx.x; t < ntiles && go; t += gridDim.x) {
-                const int n0 = (t % tn) * TBN, m0 = ((t / tn) % tm) * TBM, b = t / (tn * tm);
+                const int n0 = (t % tn) * TN, m0 = ((t / tn) % tm) * TBM, b = t / (tn * tm);
                 const int ba = batchA > 1 ? b : 0, bb = batchB > 1 ? b : 0;
                 for (int kb = 0; kb < nk; ++kb, ++it) {
                     const int s = (int)(it % S);
@@ -122,8 +123,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(
                         break;
                     }
                     unsigned char *st = tiles + (size_t)s * NT * TILE_BYTES;
-                    const int ntx = 2 + (NSPLIT == 3 ? a_split + b_split : 0);
-                    mbar_expect_tx(&ctl->full[s], ntx * TILE_BYTES);
+                    const int bytes = TILE_BYTES * (1 + (NSPLIT == 3 ? a_split : 0)) +
+                                      TN * TBK * 4 * (1 + (NSPLIT == 3 ? b_split : 0));
+                    mbar_expect_tx(&ctl->full[s], bytes);
                     tma_load_3d(st, &mA, &ctl->full[s], kb * TBK, m0, ba);
                     tma_load_3d(st + TILE_BYTES, &mB, &ctl->full[s], kb * TBK, n0, bb);
                     if (NSPLIT == 3 && a_split) tma_load_3d(st + 2 * TILE_BYTES, &mAlo, &ctl->full[s], kb * TBK, m0, ba);
@@ -134,7 +136,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(
     } else if (warp == 9) {
         if (lane == 0) {
             // MMA issuer: accumulator tcount % 2 per tile
-            constexpr unsigned idesc = idesc_tf32(TBM, TBN);
+            constexpr unsigned idesc = idesc_tf32(TBM, TN);
             long long it = 0;
             int tcount = 0;
             bool ok = true;
@@ -191,8 +193,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(
                         if (op == 0 ? a_split : b_split) continue;   // arrived split
                         float4 *hi = reinterpret_cast<float4 *>(st + op * TILE_BYTES);
                         float4 *lo = reinterpret_cast<float4 *>(st + (2 + op) * TILE_BYTES);
+                        const int nvec = (op == 0 ? TBM : TN) * TBK / 4;
 #pragma unroll 4
-                        for (int i = ts; i < TILE_BYTES / 16; i += 128) {
+                        for (int i = ts; i < nvec; i += 128) {
                             const float4 x = hi[i];
                             float4 h, l;
                             h.x = tf32_rna_dev(x.x);
@@ -220,19 +223,20 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(
             const int buf = tcount & 1, use = tcount >> 1;
             if (!mbar_wait(&ctl->acc_full[buf], (unsigned)(use & 1), abort)) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int n0 = (t % tn) * TBN, m0 = ((t / tn) % tm) * TBM, b = t / (tn * tm);
+            const int n0 = (t % tn) * TN, m0 = ((t / tn) % tm) * TBM, b = t / (tn * tm);
             float *Cb = C + (long long)b * sC;
-            for (int c0 = 0; c0 < TBN; c0 += 32) {
+            for (int c0 = 0; c0 < TN; c0 += 32) {
                 float v[32];
                 tmem_ld32(tmem + (unsigned)(buf * TBN) + ((unsigned)(warp * 32) << 16) + (unsigned)c0, v);
 #pragma unroll
                 for (int j = 0; j < 32; ++j) stg[lane * 33 + j] = v[j];
                 __syncwarp();
                 const int col = n0 + c0 + lane;
+                const bool colok = c0 + lane < TN && col < N;
 #pragma unroll 8
                 for (int rr = 0; rr < 32; ++rr) {
                     const int row = m0 + warp * 32 + rr;
-                    if (row < M && col < N) {
+                    if (row < M && colok) {
                         float *cp = Cb + (long long)row * ldc + col;
                         const float x = stg[rr * 33 + lane];
                         *cp = (beta == 0.0f) ? alpha * x : fmaf(alpha, x, beta * *cp);
@@ -270,13 +274,13 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 // 3-D map over [batch][rows][K] float32 with row stride ld and batch stride sb (elements);
 // box 32 (K) x 128 rows x 1, 128-byte swizzle, zero fill outside.
-bool make_map(CUtensorMap *map, const float *ptr, int K, int rows, int ld, long long sb, int batch) {
+bool make_map(CUtensorMap *map, const float *ptr, int K, int rows, int ld, long long sb, int batch, int box_rows) {
     auto fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)(batch > 0 ? batch : 1)};
     const long long bs = (batch > 1) ? sb * 4 : (long long)ld * rows * 4;
     cuuint64_t strides[2] = {(cuuint64_t)ld * 4, (cuuint64_t)(bs > 0 ? ((bs + 15) / 16) * 16 : 16)};
-    cuuint32_t box[3] = {TBK, TBM, 1};
+    cuuint32_t box[3] = {TBK, (cuuint32_t)box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(ptr), dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -336,34 +340,45 @@ void tc_gemm_nt(cudaStream_t st, int M, int N, int K, float alpha, const float *
                 long long sA, const float *B, const float *Blo, int ldb, long long sB, float beta, float *C, int ldc,
                 long long sC, int batch, bool split) {
     const int nsplit = split ? 3 : 1;
+    const int TN = (N % 112 == 0) ? 112 : 128;
     CUtensorMap ma, mb, malo, mblo;
     const int bA = sA ? batch : 1, bB = sB ? batch : 1;
-    if (!make_map(&ma, A, K, M, lda, sA, bA) || !make_map(&mb, B, K, N, ldb, sB, bB))
+    if (!make_map(&ma, A, K, M, lda, sA, bA, TBM) || !make_map(&mb, B, K, N, ldb, sB, bB, TN))
         throw CudaError{cudaErrorInvalidValue, "cuTensorMapEncodeTiled"};
     const bool asp = split && Alo, bsp = split && Blo;
-    if ((asp && !make_map(&malo, Alo, K, M, lda, sA, bA)) || (bsp && !make_map(&mblo, Blo, K, N, ldb, sB, bB)))
+    if ((asp && !make_map(&malo, Alo, K, M, lda, sA, bA, TBM)) || (bsp && !make_map(&mblo, Blo, K, N, ldb, sB, bB, TN)))
         throw CudaError{cudaErrorInvalidValue, "cuTensorMapEncodeTiled (lo)"};
     if (!asp) malo = ma;
     if (!bsp) mblo = mb;
     const size_t sm = tc_smem(nsplit);
-    static bool attr1 = false, attr3 = false;
-    if (nsplit == 1 && !attr1) {
-        check(cudaFuncSetAttribute(tc_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm), "attr tc1");
-        attr1 = true;
+    static bool attrs = false;
+    if (!attrs) {
+        check(cudaFuncSetAttribute(tc_gemm_kernel<1, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem(1)),
+              "attr tc1");
+        check(cudaFuncSetAttribute(tc_gemm_kernel<1, 112>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem(1)),
+              "attr tc1");
+        check(cudaFuncSetAttribute(tc_gemm_kernel<3, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem(3)),
+              "attr tc3");
+        check(cudaFuncSetAttribute(tc_gemm_kernel<3, 112>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem(3)),
+              "attr tc3");
+        attrs = true;
     }
-    if (nsplit == 3 && !attr3) {
-        check(cudaFuncSetAttribute(tc_gemm_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm), "attr tc3");
-        attr3 = true;
-    }
-    const long long ntiles = (long long)((N + TBN - 1) / TBN) * ((M + TBM - 1) / TBM) * batch;
+    const long long ntiles = (long long)((N + TN - 1) / TN) * ((M + TBM - 1) / TBM) * batch;
     const int grid = (int)std::min<long long>(ntiles, sm_count());
     int *err = error_word();
-    if (nsplit == 3)
-        tc_gemm_kernel<3><<<grid, GEMM_THREADS, sm, st>>>(ma, mb, malo, mblo, asp ? 1 : 0, bsp ? 1 : 0, M, N, K, bA,
-                                                          bB, batch, alpha, beta, C, ldc, sC, err);
+    const int as = asp ? 1 : 0, bs = bsp ? 1 : 0;
+    if (nsplit == 3 && TN == 112)
+        tc_gemm_kernel<3, 112><<<grid, GEMM_THREADS, sm, st>>>(ma, mb, malo, mblo, as, bs, M, N, K, bA, bB, batch,
+                                                               alpha, beta, C, ldc, sC, err);
+    else if (nsplit == 3)
+        tc_gemm_kernel<3, 128><<<grid, GEMM_THREADS, sm, st>>>(ma, mb, malo, mblo, as, bs, M, N, K, bA, bB, batch,
+                                                               alpha, beta, C, ldc, sC, err);
+    else if (TN == 112)
+        tc_gemm_kernel<1, 112><<<grid, GEMM_THREADS, sm, st>>>(ma, mb, malo, mblo, 0, 0, M, N, K, bA, bB, batch, alpha,
+                                                               beta, C, ldc, sC, err);
     else
-        tc_gemm_kernel<1><<<grid, GEMM_THREADS, sm, st>>>(ma, mb, malo, mblo, 0, 0, M, N, K, bA, bB, batch, alpha,
-                                                          beta, C, ldc, sC, err);
+        tc_gemm_kernel<1, 128><<<grid, GEMM_THREADS, sm, st>>>(ma, mb, malo, mblo, 0, 0, M, N, K, bA, bB, batch, alpha,
+                                                               beta, C, ldc, sC, err);
     check_launch("tc_gemm_kernel");
 }
 
