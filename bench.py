@@ -217,8 +217,9 @@ def learned_vs_plain(tddft, sy, torch, stream, k=10, train_atoms=16, eval_atoms=
     s = sy.generate(c1_density_recipe(eval_atoms, 35))
     Y0 = sy.initial_guess(s, k, 35)
     out = {}
-    for pre in ("iter", "learned", "none"):
-        c = tddft.Context(s, precision="fp64", precond=pre, tol=tol, max_iter=1000, stream=stream.cuda_stream)
+    for pre in ("iter", "adaptive", "learned", "none"):
+        c = tddft.Context(s, precision="fp64", precond="iter" if pre == "adaptive" else pre, tol=tol,
+                          max_iter=1000, stream=stream.cuda_stream, precond_adaptive=pre == "adaptive")
         if pre == "learned":
             c.set_mlp(net)
         st = c.state(Y0)
@@ -239,10 +240,12 @@ def learned_vs_plain(tddft, sy, torch, stream, k=10, train_atoms=16, eval_atoms=
             "k": k, "precision": "fp64", "tol_Ha": tol,
             "plain_pcg_s": out["iter"]["s"], "plain_iterations": out["iter"]["iterations"],
             "plain_inner_cg_iterations": out["iter"]["stats"][2],
+            "plain_adaptive_tol_s": out["adaptive"]["s"], "plain_adaptive_tol_iterations": out["adaptive"]["iterations"],
+            "plain_adaptive_tol_inner_cg_iterations": out["adaptive"]["stats"][2],
             "learned_pcg_s": out["learned"]["s"], "learned_iterations": out["learned"]["iterations"],
             "learned_fallbacks": out["learned"]["stats"][1],
             "unpreconditioned_s": out["none"]["s"], "unpreconditioned_iterations": out["none"]["iterations"],
-            "status": [out[p]["status"] for p in ("iter", "learned", "none")],
+            "status": [out[p]["status"] for p in ("iter", "adaptive", "learned", "none")],
             "max_domega_learned_vs_plain_Ha": dw, "train_s": train_s, "train_loss": [l0, l1]}
 
 

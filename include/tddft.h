@@ -99,12 +99,15 @@ typedef struct {
     int32_t max_iter;         /* outer iteration cap of tddft_solve */
     int32_t reapply_every;    /* recompute f = f(P) from scratch every this many steps (10) */
     int32_t restart_every;    /* Polak-Ribiere restart period (10) */
+    int32_t precond_adaptive; /* 0: inner CG to precond_tol every step. 1: loose first, tight at the
+                                 end (Sec. IV A suggests it): the step's inner tolerance is
+                                 min(0.1, max(precond_tol, largest residual of the iterate in Ha)) */
 } tddft_options;
 
 typedef struct tddft_ctx tddft_ctx;
 typedef struct tddft_state tddft_state;
 
-/* Fill *opt with the defaults: FP64, FULL, ITER, 50, 1e-4, tol 1e-6, 500, 10, 10. */
+/* Fill *opt with the defaults: FP64, FULL, ITER, 50, 1e-4, tol 1e-6, 500, 10, 10, not adaptive. */
 void tddft_default_options(tddft_options *opt);
 
 /* Build a context on the current CUDA device: copies the system to the device, builds the

@@ -148,9 +148,11 @@ def gram_schmidt_coefficients(Mg, order):
 
 class PCG:
     def __init__(self, op, Y0, mode=FULL, precond="iter", precond_tol=1e-4,
-                 precond_maxit=50, reapply_every=10, restart_every=10, mlp=None):
+                 precond_maxit=50, reapply_every=10, restart_every=10, mlp=None, precond_adaptive=False):
         """precond: "iter" (inner CG on Eq. precond), "none", or "learned" with mlp =
-        (parameter vector, hidden width) of the atom-block network of ``learned``."""
+        (parameter vector, hidden width) of the atom-block network of ``learned``.
+        precond_adaptive: the inner tolerance of a step is min(0.1, max(precond_tol, largest
+        residual of the iterate)) -- loose first, tight at the end (suggested in Sec. IV A)."""
         self.op = op
         self.mode = mode
         self.precond = precond
@@ -159,6 +161,8 @@ class PCG:
             from .learned import LearnedPreconditioner
             self.learned = LearnedPreconditioner(op.sys, mlp[0], mlp[1], op.mask)
         self.precond_tol = precond_tol
+        self.precond_adaptive = precond_adaptive
+        self.step_tol = precond_tol
         self.precond_maxit = precond_maxit
         self.reapply_every = reapply_every
         self.restart_every = restart_every
@@ -230,6 +234,8 @@ class PCG:
             res = np.array([np.sqrt(max(self.inner(gp[i], gp[i]) + self.inner(gq[i], gq[i]), 0.0))
                             for i in range(k)])
         omega = np.linalg.eigvalsh(0.5 * (Q + Q.T))
+        self.step_tol = (min(0.1, max(self.precond_tol, float(np.max(res)))) if self.precond_adaptive
+                         else self.precond_tol)
         return Q, omega, gp, gq, res
 
     def converged(self, omega, res, tol):
@@ -248,7 +254,7 @@ class PCG:
         rr = self.inner(r, r)
         r0 = np.sqrt(max(rr, 0.0))
         for _ in range(self.precond_maxit):
-            if r0 == 0.0 or np.sqrt(max(rr, 0.0)) <= self.precond_tol * r0:
+            if r0 == 0.0 or np.sqrt(max(rr, 0.0)) <= self.step_tol * r0:
                 break
             Lp = self.Mc @ p - p @ self.Mv
             pLp = self.inner(p, Lp)

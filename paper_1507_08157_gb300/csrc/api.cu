@@ -840,12 +840,18 @@ void precondition(tddft_ctx *c, tddft_state *S, const T *h, T *z) {
     // CG in Loewdin variables X~ = Sc^{1/2} X Sv^{1/2}: the trace metric of Eq. precond's CG becomes
     // the Frobenius product and L becomes M~c X~ - X~ M~v, so an iteration takes two products
     // instead of four; the iterates are those of the CG in the original variables
+    // inner tolerance: fixed, or loose early and tight at the end (adaptive)
+    double ptol = c->opt.precond_tol;
+    if (c->opt.precond_adaptive && !S->resid.empty()) {
+        const double rmax = *std::max_element(S->resid.begin(), S->resid.end());
+        ptol = std::min(0.1, std::max(c->opt.precond_tol, rmax));
+    }
     T *r = B.cLpp, *zt = B.cr, *p = B.cp, *Lp = B.cLp;
     check(cudaMemsetAsync(zt, 0, tot * sizeof(T), st), "memset z");
     sandwich<T>(c, k2, I.Sch, h, I.Svh, r, B.tmp);           // r~ = h~
     check(cudaMemcpyAsync(p, r, tot * sizeof(T), cudaMemcpyDeviceToDevice, st), "copy p");
     dots<T>(st, r, len, r, len, k2, len, B.dvec2, B.gscr);
-    cg_init(st, k2, c->opt.precond_tol, B.dvec2, B.cg_rr, B.cg_r0, B.cg_active, B.cg_nactive);
+    cg_init(st, k2, ptol, B.dvec2, B.cg_rr, B.cg_r0, B.cg_active, B.cg_nactive);
     int *hn = reinterpret_cast<int *>(S->host + 2 * S->k) + 1;
     for (int it = 0; it < c->opt.precond_maxit; ++it) {
         check(cudaMemcpyAsync(hn, B.cg_nactive, sizeof(int), cudaMemcpyDeviceToHost, st), "D2H n_active");
@@ -855,12 +861,12 @@ void precondition(tddft_ctx *c, tddft_state *S, const T *h, T *z) {
         gemm<T>(st, false, false, nc, nv, nc, T(1), I.Mct, nc, 0, p, nv, len, T(0), Lp, nv, len, k2);
         gemm<T>(st, false, false, k2 * nc, nv, nv, T(-1), p, nv, 0, I.Mvt, nv, 0, T(1), Lp, nv, 0, 1);
         dots<T>(st, p, len, Lp, len, k2, len, B.cg_pLp, B.gscr);
-        cg_scalars(st, k2, 0, c->opt.precond_tol, B.cg_pLp, B.cg_rrn, B.cg_rr, B.cg_r0, B.cg_alpha,
+        cg_scalars(st, k2, 0, ptol, B.cg_pLp, B.cg_rrn, B.cg_rr, B.cg_r0, B.cg_alpha,
                    B.cg_beta, B.cg_active, B.cg_nactive);
         axpy_dev<T>(st, B.cg_alpha, 1, 1.0, zt, p, len, k2);
         axpy_dev<T>(st, B.cg_alpha, 1, -1.0, r, Lp, len, k2);
         dots<T>(st, r, len, r, len, k2, len, B.cg_rrn, B.gscr);
-        cg_scalars(st, k2, 1, c->opt.precond_tol, B.cg_pLp, B.cg_rrn, B.cg_rr, B.cg_r0, B.cg_alpha,
+        cg_scalars(st, k2, 1, ptol, B.cg_pLp, B.cg_rrn, B.cg_rr, B.cg_r0, B.cg_alpha,
                    B.cg_beta, B.cg_active, B.cg_nactive);
         cg_dir<T>(st, p, r, B.cg_beta, len, k2);
     }
@@ -1089,6 +1095,7 @@ void tddft_default_options(tddft_options *o) {
     o->max_iter = 500;
     o->reapply_every = 10;
     o->restart_every = 10;
+    o->precond_adaptive = 0;
 }
 
 tddft_status tddft_create(const tddft_system *s, const tddft_options *opt, void *stream,

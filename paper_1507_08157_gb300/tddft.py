@@ -49,7 +49,7 @@ class _Options(ctypes.Structure):
                 ("precond", ctypes.c_int32), ("precond_maxit", ctypes.c_int32),
                 ("precond_tol", ctypes.c_double), ("tol", ctypes.c_double),
                 ("max_iter", ctypes.c_int32), ("reapply_every", ctypes.c_int32),
-                ("restart_every", ctypes.c_int32)]
+                ("restart_every", ctypes.c_int32), ("precond_adaptive", ctypes.c_int32)]
 
 
 class StageStats(ctypes.Structure):
@@ -170,7 +170,7 @@ def _ptr(a):
 
 
 def _options(precision="fp64", mode="full", precond="iter", precond_tol=1e-4, precond_maxit=50,
-             tol=1e-6, max_iter=500, reapply_every=10, restart_every=10):
+             tol=1e-6, max_iter=500, reapply_every=10, restart_every=10, precond_adaptive=False):
     o = _Options()
     load().tddft_default_options(ctypes.byref(o))
     o.precision = FP64 if precision == "fp64" else MIXED
@@ -182,6 +182,7 @@ def _options(precision="fp64", mode="full", precond="iter", precond_tol=1e-4, pr
     o.max_iter = max_iter
     o.reapply_every = reapply_every
     o.restart_every = restart_every
+    o.precond_adaptive = 1 if precond_adaptive else 0
     return o
 
 

@@ -116,3 +116,27 @@ def test_not_converged_reports_last_iterate(tddft, tiny):
     st = ctx.state(sy.initial_guess(tiny, 1, 5))
     om, res, it, rc = st.solve()
     assert rc == tddft.E_NOT_CONVERGED and it == 3 and np.all(np.isfinite(om))
+
+
+def test_adaptive_inner_tolerance_steps_match_oracle(tddft, tiny):
+    """Adaptive inner tolerance: FP64 PCG steps equal the oracle's, and a full solve reaches the
+    dense eigenvalues with fewer inner CG iterations than the fixed tolerance."""
+    k = 2
+    Y0 = sy.initial_guess(tiny, k, 3)
+    ref = osolver.PCG(oop.Operator(tiny), Y0, precond_adaptive=True)
+    ctx = tddft.Context(tiny, precision="fp64", precond_adaptive=True)
+    st = ctx.state(Y0)
+    for _ in range(4):
+        om_r, res_r = ref.step()
+        om_g, res_g = st.step()
+        assert np.max(np.abs(om_g - om_r)) < 1e-10
+        assert np.max(np.abs(res_g - res_r) / res_r) < 1e-6
+    inner = {}
+    for adaptive in (False, True):
+        c = tddft.Context(tiny, precision="fp64", tol=1e-7, max_iter=400, precond_adaptive=adaptive)
+        s_ = c.state(sy.initial_guess(tiny, 3, 1))
+        om, res, it, rc = s_.solve()
+        assert rc == tddft.OK
+        assert np.max(np.abs(om - casida.Casida(tiny).omega_symmetric()[:3])) <= 1e-6
+        inner[adaptive] = s_.stats()[2]
+    assert inner[True] < inner[False]

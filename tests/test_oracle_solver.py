@@ -152,3 +152,19 @@ def test_gram_schmidt_gives_identity():
     for a, i in enumerate(order):
         for j in order[a + 1:]:
             assert C[i, j] == 0.0
+
+
+def test_adaptive_inner_tolerance_reaches_dense_eigenvalues(tiny_system, tiny_operator, tiny_casida):
+    """Loose-then-tight inner tolerance (suggested in Sec. IV A) changes the path, not the fixed
+    point, and spends fewer inner CG iterations than the fixed 1e-4 tolerance."""
+    from oracle import solver as osolver
+    from paper_1507_08157_gb300 import synthetic as sy
+    Y0 = sy.initial_guess(tiny_system, 2, 1)
+    fixed = osolver.PCG(tiny_operator, Y0)
+    om_f, _, _ = fixed.solve(tol=1e-7, max_iter=400)
+    adapt = osolver.PCG(tiny_operator, Y0, precond_adaptive=True)
+    om_a, _, _ = adapt.solve(tol=1e-7, max_iter=400)
+    ref = tiny_casida.omega_symmetric()[:2]
+    assert np.max(np.abs(np.sort(om_a) - ref)) < 1e-6
+    assert np.max(np.abs(np.sort(om_f) - ref)) < 1e-6
+    assert adapt.inner_iters < fixed.inner_iters
