@@ -50,6 +50,14 @@ __global__ void ns_step_kernel(double *T, int n, unsigned long long *dev) {
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) atomicMax(dev, (unsigned long long)__double_as_longlong(m));
 }
+// max |A - B| over n entries into *dev (bit pattern of a non-negative double)
+__global__ void maxdiff_kernel(const double *A, const double *B, long long n, unsigned long long *dev) {
+    double m = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        m = fmax(m, fabs(A[i] - B[i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(dev, (unsigned long long)__double_as_longlong(m));
+}
 __global__ void scale_kernel64(const double *X, double a, double *Y, long long n) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         Y[i] = a * X[i];
@@ -87,6 +95,12 @@ struct Impl {
     // preconditioner in Loewdin variables: S^{1/2}, S^{-1/2} of both overlaps and the transformed
     // M~c = Sc^{1/2} Mc Sc^{-1/2}, M~v = Sv^{-1/2} Mv Sv^{1/2}
     T *Sch = nullptr, *Scmh = nullptr, *Svh = nullptr, *Svmh = nullptr, *Mct = nullptr, *Mvt = nullptr;
+    // the same CG on orthonormal bases U_c, U_v of the ranges of the Loewdin projectors (rc, rv > 0
+    // when P^c and P^v are idempotent): in Wc = U_c^T Sc^{1/2} [rc][nc], Wv = Sv^{1/2} U_v [nv][rv],
+    // out Vc = Sc^{-1/2} U_c [nc][rc], Vv = U_v^T Sv^{-1/2} [rv][nv], operators Mch = U_c^T M~c U_c,
+    // Mvh = U_v^T M~v U_v
+    int rc = 0, rv = 0;
+    T *Wc = nullptr, *Wv = nullptr, *Vc = nullptr, *Vv = nullptr, *Mch = nullptr, *Mvh = nullptr;
     double *fxc64 = nullptr;
     // tensor-core grid path (float32 contexts): point-major f16 chi tables [tile][512][CK]
     unsigned short *chi_pm = nullptr;
@@ -175,8 +189,9 @@ namespace {
 // float32 constants of a context: the tensor-core GEMM caches their split copies
 void register_constants(Impl<float> &I) {
     const float *ps[] = {I.Sc, I.Sv, I.Pc, I.Pv, I.Mc, I.Mv, I.Rc, I.Rv, I.Ac, I.Av, I.Sch, I.Scmh, I.Svh, I.Svmh,
-                         I.Mct, I.Mvt};
-    for (const float *p : ps) tc_register_constant(p);
+                         I.Mct, I.Mvt, I.Wc, I.Wv, I.Vc, I.Vv, I.Mch, I.Mvh};
+    for (const float *p : ps)
+        if (p) tc_register_constant(p);
 }
 void register_constants(Impl<double> &) {}
 }  // namespace
@@ -186,7 +201,7 @@ tddft_ctx::~tddft_ctx() {
     if (d32) {
         Impl<float> &I = *d32;
         const float *ps[] = {I.Sc, I.Sv, I.Pc, I.Pv, I.Mc, I.Mv, I.Rc, I.Rv, I.Ac, I.Av, I.Sch, I.Scmh, I.Svh, I.Svmh,
-                             I.Mct, I.Mvt};
+                             I.Mct, I.Mvt, I.Wc, I.Wv, I.Vc, I.Vv, I.Mch, I.Mvh};
         for (const float *p : ps)
             if (p) tc_unregister_constant(p);
     }
@@ -494,6 +509,63 @@ void overlap_roots(cudaStream_t st, Mem &tmp, const double *S_dev, const double 
     check_launch("scale inverse root");
 }
 
+// Orthonormal basis U [n][r] of the range of the Loewdin projector Pi = Sh P Sh (Sh = S^{1/2}),
+// r = round(trace Pi): U = Y (Y^T Y)^{-1/2} with Y = Pi Omega, Omega a seeded Gaussian n x r
+// matrix. Returns r, or 0 when Pi is not idempotent to 1e-8 (then no reduced space is used).
+int projector_basis(cudaStream_t st, Mem &tmp, const double *Sh, const double *P, int n, unsigned long long seed,
+                    double **U_out) {
+    const long long nn = (long long)n * n;
+    double *W = tmp.alloc<double>(nn), *Pi = tmp.alloc<double>(nn), *Pi2 = tmp.alloc<double>(nn);
+    gemm<double>(st, false, false, n, n, n, 1.0, Sh, n, 0, P, n, 0, 0.0, W, n, 0, 1);
+    gemm<double>(st, false, false, n, n, n, 1.0, W, n, 0, Sh, n, 0, 0.0, Pi, n, 0, 1);
+    gemm<double>(st, false, false, n, n, n, 1.0, Pi, n, 0, Pi, n, 0, 0.0, Pi2, n, 0, 1);
+    unsigned long long *dev = tmp.alloc<unsigned long long>(1);
+    check(cudaMemsetAsync(dev, 0, sizeof(unsigned long long), st), "memset");
+    roots::maxdiff_kernel<<<(int)std::min<long long>((nn + 255) / 256, 1216), 256, 0, st>>>(Pi2, Pi, nn, dev);
+    check_launch("maxdiff");
+    std::vector<double> diag((size_t)n);
+    check(cudaMemcpy2DAsync(diag.data(), sizeof(double), Pi, (size_t)(n + 1) * sizeof(double), sizeof(double), n,
+                            cudaMemcpyDeviceToHost, st),
+          "D2H projector diagonal");
+    unsigned long long hb = 0;
+    check(cudaMemcpyAsync(&hb, dev, sizeof(hb), cudaMemcpyDeviceToHost, st), "D2H idempotency");
+    check(cudaStreamSynchronize(st), "sync projector");
+    double dev_max;
+    std::memcpy(&dev_max, &hb, sizeof(dev_max));
+    double tr = 0.0;
+    for (double d : diag) tr += d;
+    const int r = (int)std::lround(tr);
+    if (!(dev_max < 1e-8) || r < 1 || r >= n || std::fabs(tr - r) > 1e-6) return 0;
+    // seeded Gaussian Omega (splitmix64 + Box-Muller)
+    std::vector<double> om((size_t)n * r);
+    unsigned long long x = seed;
+    auto next = [&]() {
+        unsigned long long z = (x += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return (double)((z ^ (z >> 31)) >> 11) * (1.0 / 9007199254740992.0);
+    };
+    for (size_t i = 0; i < om.size(); i += 2) {
+        const double u1 = std::max(next(), 1e-300), u2 = next();
+        const double rad = std::sqrt(-2.0 * std::log(u1));
+        om[i] = rad * std::cos(6.283185307179586 * u2);
+        if (i + 1 < om.size()) om[i + 1] = rad * std::sin(6.283185307179586 * u2);
+    }
+    double *Om = tmp.alloc<double>((long long)n * r), *Y = tmp.alloc<double>((long long)n * r);
+    double *G = tmp.alloc<double>((long long)r * r), *Gh = tmp.alloc<double>((long long)r * r);
+    double *Gmh = tmp.alloc<double>((long long)r * r), *U = tmp.alloc<double>((long long)n * r);
+    check(cudaMemcpyAsync(Om, om.data(), om.size() * sizeof(double), cudaMemcpyHostToDevice, st), "upload Omega");
+    gemm<double>(st, false, false, n, r, n, 1.0, Pi, n, 0, Om, r, 0, 0.0, Y, r, 0, 1);          // Y = Pi Omega
+    gemm<double>(st, true, false, r, r, n, 1.0, Y, r, 0, Y, r, 0, 0.0, G, r, 0, 1);             // G = Y^T Y
+    std::vector<double> gh((size_t)r * r);
+    check(cudaMemcpyAsync(gh.data(), G, gh.size() * sizeof(double), cudaMemcpyDeviceToHost, st), "D2H gram");
+    check(cudaStreamSynchronize(st), "sync gram");
+    overlap_roots(st, tmp, G, gh.data(), r, Gh, Gmh);
+    gemm<double>(st, false, false, n, r, r, 1.0, Y, r, 0, Gmh, r, 0, 0.0, U, r, 0, 1);          // U = Y G^{-1/2}
+    *U_out = U;
+    return r;
+}
+
 template <typename T>
 void build_impl(tddft_ctx *c, const tddft_system *s) {
     auto I = std::make_unique<Impl<T>>();
@@ -610,6 +682,27 @@ void build_impl(tddft_ctx *c, const tddft_system *s) {
     gemm<double>(st, false, false, nc, nc, nc, 1.0, W, nc, 0, Scmh, nc, 0, 0.0, Mct, nc, 0, 1);  // Sc^1/2 Mc Sc^-1/2
     gemm<double>(st, false, false, nv, nv, nv, 1.0, Svmh, nv, 0, Mv, nv, 0, 0.0, W, nv, 0, 1);
     gemm<double>(st, false, false, nv, nv, nv, 1.0, W, nv, 0, Svh, nv, 0, 0.0, Mvt, nv, 0, 1);   // Sv^-1/2 Mv Sv^1/2
+    // conduction x valence subspace of the preconditioner's solutions (exact when P^c, P^v are
+    // projectors): the CG iterates stay in it, so it runs there on rc x rv matrices
+    double *Uc = nullptr, *Uv = nullptr;
+    int rc = projector_basis(st, tmpm, Sch, Pc, nc, 0x5eed0001ull, &Uc);
+    int rv = rc ? projector_basis(st, tmpm, Svh, Pv, nv, 0x5eed0002ull, &Uv) : 0;
+    if (!rv) rc = 0;
+    double *Wc = nullptr, *Wv = nullptr, *Vc = nullptr, *Vv = nullptr, *Mch = nullptr, *Mvh = nullptr;
+    if (rc) {
+        const long long crc = (long long)nc * rc, vrv = (long long)nv * rv;
+        Wc = tmpm.alloc<double>(crc); Wv = tmpm.alloc<double>(vrv); Vc = tmpm.alloc<double>(crc);
+        Vv = tmpm.alloc<double>(vrv); Mch = tmpm.alloc<double>((long long)rc * rc); Mvh = tmpm.alloc<double>((long long)rv * rv);
+        double *T1 = tmpm.alloc<double>(std::max(crc, vrv));
+        gemm<double>(st, true, false, rc, nc, nc, 1.0, Uc, rc, 0, Sch, nc, 0, 0.0, Wc, nc, 0, 1);   // U_c^T Sc^1/2
+        gemm<double>(st, false, false, nv, rv, nv, 1.0, Svh, nv, 0, Uv, rv, 0, 0.0, Wv, rv, 0, 1);  // Sv^1/2 U_v
+        gemm<double>(st, false, false, nc, rc, nc, 1.0, Scmh, nc, 0, Uc, rc, 0, 0.0, Vc, rc, 0, 1); // Sc^-1/2 U_c
+        gemm<double>(st, true, false, rv, nv, nv, 1.0, Uv, rv, 0, Svmh, nv, 0, 0.0, Vv, nv, 0, 1);  // U_v^T Sv^-1/2
+        gemm<double>(st, false, false, nc, rc, nc, 1.0, Mct, nc, 0, Uc, rc, 0, 0.0, T1, rc, 0, 1);
+        gemm<double>(st, true, false, rc, rc, nc, 1.0, Uc, rc, 0, T1, rc, 0, 0.0, Mch, rc, 0, 1);  // U_c^T M~c U_c
+        gemm<double>(st, false, false, nv, rv, nv, 1.0, Mvt, nv, 0, Uv, rv, 0, 0.0, T1, rv, 0, 1);
+        gemm<double>(st, true, false, rv, rv, nv, 1.0, Uv, rv, 0, T1, rv, 0, 0.0, Mvh, rv, 0, 1);  // U_v^T M~v U_v
+    }
     auto keep = [&](const double *d, long long cnt) {
         T *o = I->mem.template alloc<T>(cnt);
         convert<double, T>(st, d, o, cnt);
@@ -620,6 +713,14 @@ void build_impl(tddft_ctx *c, const tddft_system *s) {
     I->Ac = keep(Ac, cc); I->Av = keep(Av, vv);
     I->Sch = keep(Sch, cc); I->Scmh = keep(Scmh, cc); I->Svh = keep(Svh, vv); I->Svmh = keep(Svmh, vv);
     I->Mct = keep(Mct, cc); I->Mvt = keep(Mvt, vv);
+    const char *nr = std::getenv("TDDFT_NO_REDUCED_PRECOND");
+    if (rc && !(nr && nr[0] == '1')) {
+        I->rc = rc;
+        I->rv = rv;
+        I->Wc = keep(Wc, (long long)rc * nc); I->Wv = keep(Wv, (long long)nv * rv);
+        I->Vc = keep(Vc, (long long)nc * rc); I->Vv = keep(Vv, (long long)rv * nv);
+        I->Mch = keep(Mch, (long long)rc * rc); I->Mvh = keep(Mvh, (long long)rv * rv);
+    }
     register_constants(*I);
     // kernel pattern mask over (chi, phi) function pairs
     std::vector<double> m((size_t)nc * nv);
@@ -657,6 +758,7 @@ struct StateBufs {
     T *Y, *P, *f, *g, *G1, *h, *z, *Z, *dir, *D, *fD, *covP, *covD;
     T *pdir, *pD, *pz, *pZ, *tmp;
     T *cr, *cp, *cLp, *cLpp, *cpv, *cLv;   // inner CG
+    T *qr = nullptr, *qp = nullptr, *qL = nullptr, *qz = nullptr;   // inner CG on the reduced space
     double *A, *BDf, *CDfD, *PP, *PD, *DP, *DD, *Q, *coef, *Cp, *Cq, *lam, *sc, *flip;
     double *dvec, *dvec2, *dvec3, *evout;
     double *cg_pLp, *cg_rr, *cg_rrn, *cg_r0, *cg_alpha, *cg_beta, *gscr;
@@ -710,6 +812,16 @@ void alloc_state(tddft_ctx *c, tddft_state *S) {
                      &B->cg_r0, &B->cg_alpha, &B->cg_beta};
     for (double **m : vv) *m = B->mem.template alloc<double>(k2);
     B->gscr = B->mem.template alloc<double>((size_t)gram_scratch_doubles(64, 32));
+    {
+        Impl<T> &I = impl<T>(c);
+        if (I.rc) {
+            const size_t nq = (size_t)2 * S->k * I.rc * I.rv;
+            B->qr = B->mem.template alloc<T>(nq);
+            B->qp = B->mem.template alloc<T>(nq);
+            B->qL = B->mem.template alloc<T>(nq);
+            B->qz = B->mem.template alloc<T>(nq);
+        }
+    }
     B->status = B->mem.template alloc<int>(1);
     B->cg_active = B->mem.template alloc<int>(k2);
     B->cg_nactive = B->mem.template alloc<int>(1);
@@ -845,6 +957,40 @@ void precondition(tddft_ctx *c, tddft_state *S, const T *h, T *z) {
     if (c->opt.precond_adaptive && !S->resid.empty()) {
         const double rmax = *std::max_element(S->resid.begin(), S->resid.end());
         ptol = std::min(0.1, std::max(c->opt.precond_tol, rmax));
+    }
+    if (I.rc) {
+        // the same CG on the rc x rv coordinates of the conduction x valence subspace:
+        // r^ = U_c^T h~ U_v, z = Sc^{-1/2} U_c z^ U_v^T Sv^{-1/2}
+        const int rc = I.rc, rv = I.rv;
+        const long long lr = (long long)rc * rv;
+        T *r = B.qr, *p = B.qp, *Lp = B.qL, *zh = B.qz;
+        gemm<T>(st, false, false, rc, nv, nc, T(1), I.Wc, nc, 0, h, nv, len, T(0), B.tmp, nv, (long long)rc * nv, k2);
+        gemm<T>(st, false, false, k2 * rc, rv, nv, T(1), B.tmp, nv, 0, I.Wv, rv, 0, T(0), r, rv, 0, 1);
+        check(cudaMemsetAsync(zh, 0, k2 * lr * sizeof(T), st), "memset z");
+        check(cudaMemcpyAsync(p, r, k2 * lr * sizeof(T), cudaMemcpyDeviceToDevice, st), "copy p");
+        dots<T>(st, r, lr, r, lr, k2, lr, B.dvec2, B.gscr);
+        cg_init(st, k2, ptol, B.dvec2, B.cg_rr, B.cg_r0, B.cg_active, B.cg_nactive);
+        int *hn = reinterpret_cast<int *>(S->host + 2 * S->k) + 1;
+        for (int it = 0; it < c->opt.precond_maxit; ++it) {
+            check(cudaMemcpyAsync(hn, B.cg_nactive, sizeof(int), cudaMemcpyDeviceToHost, st), "D2H n_active");
+            check(cudaStreamSynchronize(st), "sync cg");
+            if (*hn == 0) break;
+            S->inner_iters += 1;
+            gemm<T>(st, false, false, rc, rv, rc, T(1), I.Mch, rc, 0, p, rv, lr, T(0), Lp, rv, lr, k2);
+            gemm<T>(st, false, false, k2 * rc, rv, rv, T(-1), p, rv, 0, I.Mvh, rv, 0, T(1), Lp, rv, 0, 1);
+            dots<T>(st, p, lr, Lp, lr, k2, lr, B.cg_pLp, B.gscr);
+            cg_scalars(st, k2, 0, ptol, B.cg_pLp, B.cg_rrn, B.cg_rr, B.cg_r0, B.cg_alpha, B.cg_beta, B.cg_active,
+                       B.cg_nactive);
+            axpy_dev<T>(st, B.cg_alpha, 1, 1.0, zh, p, lr, k2);
+            axpy_dev<T>(st, B.cg_alpha, 1, -1.0, r, Lp, lr, k2);
+            dots<T>(st, r, lr, r, lr, k2, lr, B.cg_rrn, B.gscr);
+            cg_scalars(st, k2, 1, ptol, B.cg_pLp, B.cg_rrn, B.cg_rr, B.cg_r0, B.cg_alpha, B.cg_beta, B.cg_active,
+                       B.cg_nactive);
+            cg_dir<T>(st, p, r, B.cg_beta, lr, k2);
+        }
+        gemm<T>(st, false, false, nc, rv, rc, T(1), I.Vc, rc, 0, zh, rv, lr, T(0), B.tmp, rv, (long long)nc * rv, k2);
+        gemm<T>(st, false, false, k2 * nc, nv, rv, T(1), B.tmp, rv, 0, I.Vv, nv, 0, T(0), z, nv, 0, 1);
+        return;
     }
     T *r = B.cLpp, *zt = B.cr, *p = B.cp, *Lp = B.cLp;
     check(cudaMemsetAsync(zt, 0, tot * sizeof(T), st), "memset z");
