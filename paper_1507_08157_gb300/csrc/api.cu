@@ -108,9 +108,9 @@ struct Impl {
     int CK = 0, NPmax = 0, nslots_chi = 0, maxc = 0;
     bool grid_tc = false, integrals_tc = false;
     bool phi_quads = false;   // every tile's phi list is whole aligned groups of 4 (vector gather)
-    // integrals launches: tiles holding chi and phi, those with <= 256 chi first
+    // integrals launches: tiles holding chi and phi, grouped by 128-row chi blocks (1, 2, 3)
     int *int_tiles = nullptr;
-    int int_small = 0, int_large = 0;
+    int int_count[3] = {0, 0, 0};
     unsigned *tc_bits = nullptr;
     float *tc_scale = nullptr;
     // operator workspace, sized for up to `cap` grid states
@@ -169,7 +169,7 @@ int integrals_tc_group(int NP, int k, int maxc);
 void potential_integrals_tc(cudaStream_t st, const GridShape &g, const TileSet<float> &chi,
                             const TileSet<float> &phi, const unsigned short *chi_fm16, int nslots, int NPmax,
                             int maxc, int nchi, int nphi, const float *V, int k, float *out, unsigned *scratch_bits,
-                            float *scale, const int *tile_list, int tiles_small, int tiles_large, int *err);
+                            float *scale, const int *tile_list, const int *tiles_by_blocks, int *err);
 void response_density_tc(cudaStream_t st, const GridShape &g, const TileSet<float> &chi,
                          const TileSet<float> &phi, const unsigned short *chi_pm, int CK, int NPmax, int nphi,
                          const float *P, long long sP, int k, float *rho, unsigned *scratch_bits,
@@ -426,8 +426,8 @@ void integrals(tddft_ctx *c, Impl<T> &I, int ns) {
     if constexpr (sizeof(T) == 4) {
         if (I.integrals_tc) {
             potential_integrals_tc(c->st, c->grid(), I.chi, I.phi, I.chi_fm16, I.nslots_chi, I.NPmax, I.maxc, c->nc,
-                                   c->nv, I.V, ns, I.Vmat, I.tc_bits, I.tc_scale, I.int_tiles, I.int_small,
-                                   I.int_large, tc_error_word());
+                                   c->nv, I.V, ns, I.Vmat, I.tc_bits, I.tc_scale, I.int_tiles, I.int_count,
+                                   tc_error_word());
             return;
         }
     }
@@ -628,18 +628,20 @@ void build_impl(tddft_ctx *c, const tddft_system *s) {
                                      cudaMemcpyHostToDevice),
                           "upload f16 chi");
                     I->nslots_chi = coff[ntl];
-                    std::vector<int> small, large;
+                    std::vector<int> by[3];
                     for (int t = 0; t < ntl; ++t) {
                         const int nct = coff[t + 1] - coff[t], npt = poff[t + 1] - poff[t];
                         if (nct == 0 || npt == 0) continue;
-                        (nct <= 256 ? small : large).push_back(t);
+                        by[std::min(2, (nct - 1) / 128)].push_back(t);
                     }
-                    I->int_small = (int)small.size();
-                    I->int_large = (int)large.size();
-                    small.insert(small.end(), large.begin(), large.end());
-                    I->int_tiles = I->mem.template alloc<int>(std::max<size_t>(1, small.size()));
-                    if (!small.empty())
-                        check(cudaMemcpy(I->int_tiles, small.data(), small.size() * sizeof(int), cudaMemcpyHostToDevice),
+                    std::vector<int> all;
+                    for (int q = 0; q < 3; ++q) {
+                        I->int_count[q] = (int)by[q].size();
+                        all.insert(all.end(), by[q].begin(), by[q].end());
+                    }
+                    I->int_tiles = I->mem.template alloc<int>(std::max<size_t>(1, all.size()));
+                    if (!all.empty())
+                        check(cudaMemcpy(I->int_tiles, all.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice),
                               "upload integrals tile lists");
                     I->integrals_tc = NP <= 128;
                 }

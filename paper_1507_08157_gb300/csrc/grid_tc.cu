@@ -432,7 +432,7 @@ __device__ __forceinline__ void red_add_v4(float *addr, float a, float b, float 
 
 // CTA = (state group, tile of the launch's list); mbmax: most chi row blocks of a listed tile
 // (sizes the X stages), tmem_cols: TMEM columns allocated (mbmax * acc_stride, a power of two)
-__global__ void __launch_bounds__(192, 2) integrals_tc_kernel(
+__global__ void __launch_bounds__(192, 3) integrals_tc_kernel(
     const __grid_constant__ CUtensorMap mX,   // function-major chi: [slot][512] f16
     int n, int nt, int NP, int G, int k, const int *__restrict__ coff, const int *__restrict__ cids,
     const int *__restrict__ poff, const int *__restrict__ pids, const float *__restrict__ pval, int nchi,
@@ -634,7 +634,7 @@ int integrals_tc_group(int NP, int k, int maxc) {
 void potential_integrals_tc(cudaStream_t st, const GridShape &g, const TileSet<float> &chi,
                             const TileSet<float> &phi, const unsigned short *chi_fm16, int nslots, int NPmax,
                             int maxc, int nchi, int nphi, const float *V, int k, float *out, unsigned *scratch_bits,
-                            float *scale, const int *tile_list, int tiles_small, int tiles_large, int *err) {
+                            float *scale, const int *tile_list, const int *tiles_by_blocks, int *err) {
     if (k <= 0) return;
     ProfScope ps(st, ST_INTEGRALS, 2.0 * k * g.pair_points,
                  2.0 * g.table_values + 4.0 * k * g.n * g.n * g.n + 4.0 * k * nchi * nphi);
@@ -649,8 +649,8 @@ void potential_integrals_tc(cudaStream_t st, const GridShape &g, const TileSet<f
     if (!encode_map_2d(&mx, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, chi_fm16, (unsigned long long)TILE_PTS,
                        (unsigned long long)nslots, (unsigned long long)TILE_PTS * 2, 64, 128))
         throw CudaError{cudaErrorInvalidValue, "cuTensorMapEncodeTiled (integrals)"};
-    // two launches: tiles with <= 256 chi (at most two 128-row blocks) one state per CTA and two
-    // CTAs per SM; tiles with more chi (three blocks) one CTA per SM
+    // one launch per class of tiles by 128-row chi blocks (1, 2, 3), one state per CTA: the
+    // smaller a class's shared memory and TMEM, the more CTAs share an SM (3, 2, 1)
     if (NPmax > 128) throw CudaError{cudaErrorInvalidValue, "integrals_tc: more than 128 phi per tile"};
     static bool attr = false;
     if (!attr) {
@@ -659,18 +659,20 @@ void potential_integrals_tc(cudaStream_t st, const GridShape &g, const TileSet<f
         attr = true;
     }
     const bool vec_ok = (nphi % 4 == 0) && ((reinterpret_cast<unsigned long long>(out) & 15ull) == 0);
-    const int lists[2] = {tiles_small, tiles_large};
-    const int *lp[2] = {tile_list, tile_list + tiles_small};
-    for (int c = 0; c < 2; ++c) {
-        if (lists[c] == 0) continue;
-        const int mbmax = c == 0 ? 2 : 3;
+    const int *lp = tile_list;
+    for (int c = 0; c < 3; ++c) {
+        const int cnt = tiles_by_blocks[c];
+        const int *lst = lp;
+        lp += cnt;
+        if (cnt == 0) continue;
+        const int mbmax = c + 1;
         const int stride = 128;                           // one state: NB = NPmax <= 128 columns
-        const int tmem_cols = c == 0 ? 256 : 512;
+        const int tmem_cols = mbmax == 1 ? 128 : (mbmax == 2 ? 256 : 512);
         const size_t sm = integrals_tc_smem(NPmax, 1, mbmax);
-        dim3 grid(k, lists[c]);
+        dim3 grid(k, cnt);
         integrals_tc_kernel<<<grid, 192, sm, st>>>(mx, g.n, g.nt, NPmax, 1, k, chi.off, chi.ids, phi.off, phi.ids,
                                                    phi.val, nchi, nphi, V, scale, (float)g.dV, out, vec_ok, stride,
-                                                   lp[c], mbmax, tmem_cols, err);
+                                                   lst, mbmax, tmem_cols, err);
         check_launch("integrals_tc_kernel");
     }
 }
