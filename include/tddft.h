@@ -118,6 +118,30 @@ void tddft_default_options(tddft_options *opt);
 tddft_status tddft_create(const tddft_system *sys, const tddft_options *opt, void *cuda_stream,
                           tddft_ctx **out);
 void tddft_destroy(tddft_ctx *ctx);
+
+/* Set-up of nsys independent systems of any sizes (a batch): out[i] receives the context of
+ * sys[i] as tddft_create makes it, except that each context owns a non-blocking CUDA stream of
+ * its own (ordered after the work queued on cuda_stream at the call) and waits on it through a
+ * blocking-sync event, so that the systems overlap on the device and many host threads can
+ * drive them. The set-ups run on up to 16 host threads. Each context is destroyed with
+ * tddft_destroy as usual. On an error every context made so far is destroyed, out[] is all
+ * NULL and the first failing system's status is returned. */
+tddft_status tddft_create_batch(const tddft_system *sys, int32_t nsys, const tddft_options *opt,
+                                void *cuda_stream, tddft_ctx **out);
+
+/* tddft_solve (Sec. III C) for nsys systems at once: st[i] is a state of ctx[i] (contexts
+ * pairwise distinct, best from tddft_create_batch). Host threads (nthreads, <= 0 for up to 16)
+ * take the systems largest first (k x grid work) and iterate each to convergence; the device
+ * interleaves the systems' kernels. omega and resid (either may be NULL) receive system i's k_i
+ * values at offset k_0 + ... + k_{i-1}; iters[i] and status[i] (either may be NULL) its
+ * iteration count and its tddft_solve status. Returns OK if every system returned OK, else the
+ * first non-OK status in system order (INVALID for bad arguments, before any work). The
+ * tensor-core kernels share one error word for expired bounded waits, so such an error is
+ * reported by whichever system reads it first. */
+tddft_status tddft_solve_batch(tddft_ctx *const *ctx, tddft_state *const *st, int32_t nsys,
+                               int32_t nthreads, double *omega, double *resid, int32_t *iters,
+                               int32_t *status);
+
 const char *tddft_last_error(const tddft_ctx *ctx);
 tddft_status tddft_dims(const tddft_ctx *ctx, int32_t *n_chi, int32_t *n_phi, int32_t *n);
 
@@ -193,6 +217,23 @@ tddft_status tddft_solve(tddft_ctx *ctx, tddft_state *st, double *omega, double 
  * NULL) and L (the masked search variables) if Lp/Lq are given. */
 tddft_status tddft_state_get(tddft_ctx *ctx, const tddft_state *st, double *Pp, double *Pq,
                              double *fp, double *fq, double *Lp, double *Lq);
+
+/* Checkpoint and resume of a PCG state (Sec. III C carries, from one iteration to the next, the
+ * trial pairs with their operator images and the previous search direction with its
+ * preconditioned gradient; the checkpoint holds exactly these). tddft_state_export writes into
+ * the caller's host buffer buf of *len bytes: with buf NULL it only stores the size needed in
+ * *len; a buffer smaller than that gives INVALID (with *len set to the size). Layout: a 48-byte
+ * header (magic "TDDFTST1", version 1, precision, k, N_chi, N_phi, iteration count, learned
+ * fallbacks, previous-omega flag as int32, inner CG iterations as int64), the previous omega [k]
+ * and five conjugation scalars as float64, then Y, P, f, cov(P), the previous direction, its
+ * image, the previous preconditioned gradient and its image, each [2k][N_chi][N_phi] in the
+ * context's working type (float64 for FP64, float32 for MIXED), native byte order.
+ * tddft_state_import makes a new state from such a buffer (len exactly the exported size) on a
+ * context of the same precision and sizes (INVALID otherwise); its further steps are those the
+ * exported state would have taken. The caller owns buf; the state belongs to the context it was
+ * imported on and is freed with tddft_state_destroy. */
+tddft_status tddft_state_export(tddft_ctx *ctx, const tddft_state *st, void *buf, size_t *len);
+tddft_status tddft_state_import(tddft_ctx *ctx, const void *buf, size_t len, tddft_state **out);
 
 /* Per Ritz pair of the current subspace: omega [k] ascending and pairing [2k] =
  * |<p, f_p> - omega|, |<q, f_q> - omega| (an eigenpair has both zero; (-p, q) is then the

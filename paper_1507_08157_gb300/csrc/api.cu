@@ -9,6 +9,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -17,6 +19,7 @@
 #include <memory>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 namespace tddft {
@@ -152,6 +155,11 @@ struct tddft_ctx {
     std::string err;
     std::unique_ptr<Impl<double>> d64;
     std::unique_ptr<Impl<float>> d32;
+    // contexts of a batch own their stream and wait on it through a blocking-sync event, so that
+    // many host threads can drive systems at once without spinning
+    bool own_stream = false;
+    cudaEvent_t sync_ev = nullptr;
+    int *hword = nullptr;   // pinned: the tensor-core kernels' error word, read with each status
     GridShape grid() const { return GridShape{n, nt, cell, dV, pair_points, table_values}; }
     ~tddft_ctx();
     long long len() const { return (long long)nc * nv; }
@@ -161,7 +169,8 @@ struct tddft_ctx {
 namespace tddft {
 bool tc_enabled();
 int *tc_error_word();
-int tc_error_read_and_clear(cudaStream_t st);
+void tc_error_fetch(cudaStream_t st, int *host);
+void tc_error_clear(cudaStream_t st);
 void build_point_major_f16(const int *off_h, const float *val_h_or_null, const double *vald_h_or_null,
                            int ntiles, int CK, unsigned short *out_h);
 int density_tc_group(int KBmax, int NP, int k);
@@ -197,6 +206,7 @@ void register_constants(Impl<double> &) {}
 }  // namespace
 
 tddft_ctx::~tddft_ctx() {
+    if (own_stream && st) cudaStreamSynchronize(st);
     if (prof) profiler_delete(prof);
     if (d32) {
         Impl<float> &I = *d32;
@@ -205,6 +215,11 @@ tddft_ctx::~tddft_ctx() {
         for (const float *p : ps)
             if (p) tc_unregister_constant(p);
     }
+    d64.reset();
+    d32.reset();
+    if (sync_ev) cudaEventDestroy(sync_ev);
+    if (hword) cudaFreeHost(hword);
+    if (own_stream && st) cudaStreamDestroy(st);
 }
 
 namespace {
@@ -212,6 +227,15 @@ namespace {
 template <typename T> Impl<T> &impl(tddft_ctx *c);
 template <> Impl<double> &impl<double>(tddft_ctx *c) { return *c->d64; }
 template <> Impl<float> &impl<float>(tddft_ctx *c) { return *c->d32; }
+
+// wait for the context's stream: a blocking-sync event for batch contexts, else a stream sync
+cudaError_t ctx_sync(tddft_ctx *c) {
+    if (c->sync_ev) {
+        cudaError_t e = cudaEventRecord(c->sync_ev, c->st);
+        return e != cudaSuccess ? e : cudaEventSynchronize(c->sync_ev);
+    }
+    return cudaStreamSynchronize(c->st);
+}
 
 struct ProfilerBinding {
     ProfilerBinding(tddft_ctx *c) { active_profiler() = (c->prof_on ? c->prof : nullptr); }
@@ -377,21 +401,21 @@ void download(tddft_ctx *c, Impl<T> &I, const T *src, double *dst, long long cou
     } else {
         convert<T, double>(c->st, src, I.stage, count);
         check(cudaMemcpyAsync(dst, I.stage, count * sizeof(double), cudaMemcpyDeviceToHost, c->st), "D2H");
-        check(cudaStreamSynchronize(c->st), "sync D2H");
+        check(ctx_sync(c), "sync D2H");
     }
 }
 
 template <> void download<double>(tddft_ctx *c, Impl<double> &I, const double *src, double *dst, long long count) {
     if (!dst) return;
     check(cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyDefault, c->st), "copy out");
-    check(cudaStreamSynchronize(c->st), "sync copy out");
+    check(ctx_sync(c), "sync copy out");
 }
 
 // workspace for the operator on up to `states` grid states (2k for a batch of k pairs)
 template <typename T>
 void ensure_workspace(tddft_ctx *c, Impl<T> &I, int states) {
     if (states <= I.cap) return;
-    check(cudaStreamSynchronize(c->st), "sync before workspace");
+    check(ctx_sync(c), "sync before workspace");
     I.wmem.release();
     const long long len = c->len(), n3 = c->n3();
     I.rho = I.wmem.template alloc<T>((size_t)states * n3);
@@ -434,8 +458,14 @@ void integrals(tddft_ctx *c, Impl<T> &I, int ns) {
     potential_integrals<T>(c->st, c->grid(), I.chi, I.phi, c->nc, c->nv, I.V, ns, I.Vmat);
 }
 
+// the error word of the tensor-core kernels (bounded waits that expired), read with one stream wait
 void check_tc_error(tddft_ctx *c) {
-    if (tc_error_read_and_clear(c->st)) throw TimeoutErr{"a bounded wait in a tensor-core kernel expired"};
+    tc_error_fetch(c->st, c->hword);
+    check(ctx_sync(c), "sync tc error");
+    if (*c->hword) {
+        tc_error_clear(c->st);
+        throw TimeoutErr{"a bounded wait in a tensor-core kernel expired"};
+    }
 }
 
 // ---- the operator (Eq. operator_RPA) -------------------------------------------------------------
@@ -742,7 +772,7 @@ void build_impl(tddft_ctx *c, const tddft_system *s) {
         check(cudaMemsetAsync(I->fxc64, 0, n3 * sizeof(double), st), "memset fxc");
         I->fxc = nullptr;
     }
-    check(cudaStreamSynchronize(st), "build sync");
+    check(ctx_sync(c), "build sync");
     if constexpr (sizeof(T) == 8) c->d64 = std::move(I);
     else c->d32 = std::move(I);
 }
@@ -860,8 +890,7 @@ void sync_status(tddft_ctx *c, tddft_state *S, const int *dstatus) {
     check(cudaMemcpyAsync(reinterpret_cast<int *>(S->host + 2 * S->k), dstatus, sizeof(int),
                           cudaMemcpyDeviceToHost, c->st),
           "D2H status");
-    check(cudaStreamSynchronize(c->st), "sync status");
-    check_tc_error(c);
+    check_tc_error(c);   // waits for the status copy too
     const int stv = *reinterpret_cast<int *>(S->host + 2 * S->k);
     if (stv == DEV_BREAKDOWN) throw Breakdown{"non-positive norm in Gram-Schmidt (dependent trial pairs)"};
     if (stv == DEV_NAN) throw Breakdown{"NaN or Inf in the trial pairs"};
@@ -903,7 +932,7 @@ void state_init(tddft_ctx *c, tddft_state *S, const double *Y0) {
     check(cudaMemsetAsync(B.f, 0, 2 * k * len * sizeof(T), c->st), "memset f");
     recombine<T>(c, B, k);
     apply_impl<T>(c, I, k, B.P, B.f);
-    check(cudaStreamSynchronize(c->st), "sync init");
+    check(ctx_sync(c), "sync init");
 }
 
 // Q, omega, gradient and residuals of the current iterate
@@ -975,7 +1004,7 @@ void precondition(tddft_ctx *c, tddft_state *S, const T *h, T *z) {
         int *hn = reinterpret_cast<int *>(S->host + 2 * S->k) + 1;
         for (int it = 0; it < c->opt.precond_maxit; ++it) {
             check(cudaMemcpyAsync(hn, B.cg_nactive, sizeof(int), cudaMemcpyDeviceToHost, st), "D2H n_active");
-            check(cudaStreamSynchronize(st), "sync cg");
+            check(ctx_sync(c), "sync cg");
             if (*hn == 0) break;
             S->inner_iters += 1;
             gemm<T>(st, false, false, rc, rv, rc, T(1), I.Mch, rc, 0, p, rv, lr, T(0), Lp, rv, lr, k2);
@@ -1003,7 +1032,7 @@ void precondition(tddft_ctx *c, tddft_state *S, const T *h, T *z) {
     int *hn = reinterpret_cast<int *>(S->host + 2 * S->k) + 1;
     for (int it = 0; it < c->opt.precond_maxit; ++it) {
         check(cudaMemcpyAsync(hn, B.cg_nactive, sizeof(int), cudaMemcpyDeviceToHost, st), "D2H n_active");
-        check(cudaStreamSynchronize(st), "sync cg");
+        check(ctx_sync(c), "sync cg");
         if (*hn == 0) break;
         S->inner_iters += 1;
         gemm<T>(st, false, false, nc, nv, nc, T(1), I.Mct, nc, 0, p, nv, len, T(0), Lp, nv, len, k2);
@@ -1039,11 +1068,11 @@ void ensure_learned(tddft_ctx *c, Impl<T> &I, int k) {
         learned_fixed_features<T>(c->st, I.Mc, I.Sc, c->nc, c->nca, na, I.lfc);
         learned_fixed_features<T>(c->st, I.Mv, I.Sv, c->nv, c->nva, na, I.lfv);
         learned_feature_rows(c->st, I.lfc, I.lfv, I.ldist, na, c->nca, c->nva, I.lF);
-        check(cudaStreamSynchronize(c->st), "sync learned features");
+        check(ctx_sync(c), "sync learned features");
     }
     const long long rows = (long long)k * na * na;
     if (rows <= I.lrows) return;
-    check(cudaStreamSynchronize(c->st), "sync before learned buffers");
+    check(ctx_sync(c), "sync before learned buffers");
     I.lmemr.release();
     I.ls = I.lmemr.template alloc<float>((size_t)rows);
     I.lrows = rows;
@@ -1110,7 +1139,7 @@ void update(tddft_ctx *c, tddft_state *S) {
     if (learned) {
         // the CG solve stands in when -z is not a descent direction (<g, Z> summed <= 0)
         check(cudaMemcpyAsync(S->host, B.dvec, k2 * sizeof(double), cudaMemcpyDeviceToHost, st), "D2H gz");
-        check(cudaStreamSynchronize(st), "sync gz");
+        check(ctx_sync(c), "sync gz");
         double gz = 0.0;
         for (int i = 0; i < k2; ++i) gz += S->host[i];
         if (!(gz > 0.0)) {
@@ -1177,7 +1206,7 @@ void subspace_pairs(tddft_ctx *c, tddft_state *S, double *omega, double *pairing
     subspace(c->st, k, B.A, B.evout, B.dvec3);
     check(cudaMemcpyAsync(S->host, B.evout, k * sizeof(double), cudaMemcpyDeviceToHost, c->st), "D2H omega");
     check(cudaMemcpyAsync(S->host + k, B.dvec3, 2 * k * sizeof(double), cudaMemcpyDeviceToHost, c->st), "D2H pairing");
-    check(cudaStreamSynchronize(c->st), "sync subspace");
+    check(ctx_sync(c), "sync subspace");
     if (omega) std::memcpy(omega, S->host, k * sizeof(double));
     if (pairing) std::memcpy(pairing, S->host + k, 2 * k * sizeof(double));
 }
@@ -1219,6 +1248,32 @@ tddft_status solve_impl(tddft_ctx *c, tddft_state *S, double *omega, double *res
         }
     }
     return TDDFT_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// checkpoint layout: header, host scalars, omega_prev [k], the conjugation scalars, then the eight
+// device arrays that carry from one PCG step to the next, each [2k][N_chi][N_phi] of T
+constexpr char CKPT_MAGIC[8] = {'T', 'D', 'D', 'F', 'T', 'S', 'T', '1'};
+constexpr int32_t CKPT_VERSION = 1;
+struct CkptHeader {
+    char magic[8];
+    int32_t version, precision, k, n_chi, n_phi, it, fallbacks, have_prev_omega;
+    int64_t inner_iters;
+};
+static_assert(sizeof(CkptHeader) == 48, "checkpoint header layout");
+constexpr int CKPT_SCALARS = 5;   // conjugation scalars (4) and the Gram-Schmidt reorder flag
+
+template <typename T>
+std::array<T *, 8> carried(StateBufs<T> &B) {
+    return {B.Y, B.P, B.f, B.covP, B.pdir, B.pD, B.pz, B.pZ};
+}
+
+size_t ckpt_bytes(const tddft_ctx *c, int k, int prec) {
+    const size_t el = prec == TDDFT_FP64 ? sizeof(double) : sizeof(float);
+    return sizeof(CkptHeader) + (size_t)(k + CKPT_SCALARS) * sizeof(double) + 8 * (size_t)2 * k * c->len() * el;
 }
 
 }  // namespace
@@ -1308,6 +1363,8 @@ tddft_status tddft_create(const tddft_system *s, const tddft_options *opt, void 
                     c->amask[(size_t)a * s->natoms + b] = std::sqrt(d2) <= s->kernel_cutoff ? 1 : 0;
                 }
         }
+        check(cudaMallocHost(reinterpret_cast<void **>(&c->hword), sizeof(int)), "cudaMallocHost");
+        *c->hword = 0;
         if (c->prec == TDDFT_FP64) build_impl<double>(c.get(), s);
         else build_impl<float>(c.get(), s);
         return TDDFT_OK;
@@ -1320,6 +1377,109 @@ tddft_status tddft_create(const tddft_system *s, const tddft_options *opt, void 
     }
     *out = c.release();
     return TDDFT_OK;
+}
+
+tddft_status tddft_create_batch(const tddft_system *sys, int32_t nsys, const tddft_options *opt, void *stream,
+                                tddft_ctx **out) {
+    if (!sys || !out || nsys <= 0) return TDDFT_E_INVALID;
+    for (int i = 0; i < nsys; ++i) out[i] = nullptr;
+    cudaStream_t caller = static_cast<cudaStream_t>(stream);
+    cudaEvent_t ready = nullptr;
+    if (cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(ready, caller) != cudaSuccess) {
+        if (ready) cudaEventDestroy(ready);
+        return TDDFT_E_CUDA;
+    }
+    std::vector<tddft_status> rc(nsys, TDDFT_OK);
+    std::atomic<int> next{0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    auto worker = [&]() {
+        cudaSetDevice(dev);   // the caller's device in every host thread
+        for (int i = next++; i < nsys; i = next++) {
+            cudaStream_t st = nullptr;
+            cudaEvent_t ev = nullptr;
+            if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaStreamWaitEvent(st, ready, 0) != cudaSuccess ||
+                cudaEventCreateWithFlags(&ev, cudaEventBlockingSync | cudaEventDisableTiming) != cudaSuccess) {
+                if (st) cudaStreamDestroy(st);
+                if (ev) cudaEventDestroy(ev);
+                rc[i] = TDDFT_E_CUDA;
+                continue;
+            }
+            tddft_ctx *c = nullptr;
+            rc[i] = tddft_create(&sys[i], opt, st, &c);
+            if (rc[i] != TDDFT_OK) {
+                cudaStreamSynchronize(st);
+                cudaStreamDestroy(st);
+                cudaEventDestroy(ev);
+                continue;
+            }
+            c->own_stream = true;
+            c->sync_ev = ev;
+            out[i] = c;
+        }
+    };
+    const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+    const int nt = std::max(1, std::min({(int)nsys, 16, hw}));
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nt; ++t) pool.emplace_back(worker);
+    worker();
+    for (std::thread &t : pool) t.join();
+    cudaEventDestroy(ready);
+    for (int i = 0; i < nsys; ++i)
+        if (rc[i] != TDDFT_OK) {
+            for (int j = 0; j < nsys; ++j) {
+                tddft_destroy(out[j]);
+                out[j] = nullptr;
+            }
+            return rc[i];
+        }
+    return TDDFT_OK;
+}
+
+tddft_status tddft_solve_batch(tddft_ctx *const *ctx, tddft_state *const *st, int32_t nsys, int32_t nthreads,
+                               double *omega, double *resid, int32_t *iters, int32_t *status) {
+    if (!ctx || !st || nsys <= 0) return TDDFT_E_INVALID;
+    std::vector<long long> off(nsys + 1, 0);
+    for (int i = 0; i < nsys; ++i) {
+        if (!ctx[i] || !st[i] || st[i]->ctx != ctx[i]) return TDDFT_E_INVALID;
+        for (int j = 0; j < i; ++j)
+            if (ctx[j] == ctx[i]) return TDDFT_E_INVALID;   // a context is driven by one thread at a time
+        off[i + 1] = off[i] + st[i]->k;
+    }
+    // largest systems first, so that the long solves start early
+    std::vector<int> order(nsys);
+    for (int i = 0; i < nsys; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return ctx[a]->pair_points * st[a]->k > ctx[b]->pair_points * st[b]->k;
+    });
+    std::vector<tddft_status> rc(nsys, TDDFT_OK);
+    std::vector<int32_t> it(nsys, 0);
+    std::atomic<int> next{0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    auto worker = [&]() {
+        cudaSetDevice(dev);
+        for (int q = next++; q < nsys; q = next++) {
+            const int i = order[q];
+            rc[i] = tddft_solve(ctx[i], st[i], omega ? omega + off[i] : nullptr, resid ? resid + off[i] : nullptr,
+                                &it[i]);
+        }
+    };
+    int nt = nthreads > 0 ? nthreads : 16;
+    nt = std::max(1, std::min(nt, (int)nsys));
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nt; ++t) pool.emplace_back(worker);
+    worker();
+    for (std::thread &t : pool) t.join();
+    tddft_status first = TDDFT_OK;
+    for (int i = 0; i < nsys; ++i) {
+        if (iters) iters[i] = it[i];
+        if (status) status[i] = rc[i];
+        if (first == TDDFT_OK && rc[i] != TDDFT_OK) first = rc[i];
+    }
+    return first;
 }
 
 void tddft_destroy(tddft_ctx *c) {
@@ -1352,7 +1512,6 @@ tddft_status tddft_apply(tddft_ctx *c, int32_t k, const double *Pp, const double
             apply_impl<T>(c, I, k, I.bufP, I.bufF);
             download<T>(c, I, I.bufF, fp, kl);
             download<T>(c, I, I.bufF + kl, fq, kl);
-            check(cudaStreamSynchronize(c->st), "sync apply");
             check_tc_error(c);
             return TDDFT_OK;
         })());
@@ -1369,7 +1528,6 @@ tddft_status tddft_response_density(tddft_ctx *c, int32_t k, const double *P, do
             upload<T>(c, I, P, I.bufP, (long long)k * c->len());
             density(c, I, I.bufP, k);
             download<T>(c, I, I.rho, rho, (long long)k * c->n3());
-            check(cudaStreamSynchronize(c->st), "sync density");
             check_tc_error(c);
             return TDDFT_OK;
         })());
@@ -1386,7 +1544,7 @@ tddft_status tddft_response_potential(tddft_ctx *c, int32_t k, const double *rho
             upload<T>(c, I, rho, I.rho, (long long)k * c->n3());
             hartree_fxc<T>(c->st, c->grid(), I.rho, I.fxc, k, I.V, I.fft);
             download<T>(c, I, I.V, V, (long long)k * c->n3());
-            check(cudaStreamSynchronize(c->st), "sync potential");
+            check(ctx_sync(c), "sync potential");
             return TDDFT_OK;
         })());
     });
@@ -1402,7 +1560,6 @@ tddft_status tddft_potential_integrals(tddft_ctx *c, int32_t k, const double *V,
             upload<T>(c, I, V, I.V, (long long)k * c->n3());
             integrals(c, I, k);
             download<T>(c, I, I.Vmat, out, (long long)k * c->len());
-            check(cudaStreamSynchronize(c->st), "sync integrals");
             check_tc_error(c);
             return TDDFT_OK;
         })());
@@ -1414,7 +1571,7 @@ tddft_status tddft_fxc(tddft_ctx *c, double *fxc) {
     return guarded(c, [&]() -> tddft_status {
         const double *src = c->prec == TDDFT_FP64 ? c->d64->fxc64 : c->d32->fxc64;
         check(cudaMemcpyAsync(fxc, src, c->n3() * sizeof(double), cudaMemcpyDefault, c->st), "copy fxc");
-        check(cudaStreamSynchronize(c->st), "sync fxc");
+        check(ctx_sync(c), "sync fxc");
         return TDDFT_OK;
     });
 }
@@ -1479,10 +1636,107 @@ tddft_status tddft_state_get(tddft_ctx *c, const tddft_state *S, double *Pp, dou
             download<T>(c, I, B.f + kl, fq, kl);
             download<T>(c, I, B.Y, Lp, kl);
             download<T>(c, I, B.Y + kl, Lq, kl);
-            check(cudaStreamSynchronize(c->st), "sync state_get");
+            check(ctx_sync(c), "sync state_get");
             return TDDFT_OK;
         })());
     });
+}
+
+tddft_status tddft_state_export(tddft_ctx *c, const tddft_state *S, void *buf, size_t *len) {
+    if (!c || !S || S->ctx != c || !len) return TDDFT_E_INVALID;
+    return guarded(c, [&]() -> tddft_status {
+        const size_t need = ckpt_bytes(c, S->k, c->prec);
+        if (!buf) {
+            *len = need;
+            return TDDFT_OK;
+        }
+        if (*len < need) {
+            *len = need;
+            throw InvalidArg{"tddft_state_export: buffer too small"};
+        }
+        *len = need;
+        return DISPATCH(c, ([&]() {
+            tddft_state *Sm = const_cast<tddft_state *>(S);
+            StateBufs<T> &B = bufs<T>(Sm);
+            unsigned char *o = static_cast<unsigned char *>(buf);
+            CkptHeader h{};
+            std::memcpy(h.magic, CKPT_MAGIC, 8);
+            h.version = CKPT_VERSION;
+            h.precision = c->prec;
+            h.k = S->k;
+            h.n_chi = c->nc;
+            h.n_phi = c->nv;
+            h.it = S->it;
+            h.fallbacks = S->fallbacks;
+            h.have_prev_omega = S->have_prev_omega ? 1 : 0;
+            h.inner_iters = S->inner_iters;
+            std::memcpy(o, &h, sizeof h);
+            o += sizeof h;
+            std::vector<double> om(S->k, 0.0);
+            if (S->have_prev_omega) std::copy(S->omega_prev.begin(), S->omega_prev.end(), om.begin());
+            std::memcpy(o, om.data(), S->k * sizeof(double));
+            o += S->k * sizeof(double);
+            check(cudaMemcpyAsync(o, B.sc, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->st), "D2H sc");
+            check(cudaMemcpyAsync(o + 4 * sizeof(double), B.flip, sizeof(double), cudaMemcpyDeviceToHost, c->st),
+                  "D2H flip");
+            o += CKPT_SCALARS * sizeof(double);
+            const size_t bytes = (size_t)2 * S->k * c->len() * sizeof(T);
+            for (T *X : carried<T>(B)) {
+                check(cudaMemcpyAsync(o, X, bytes, cudaMemcpyDeviceToHost, c->st), "D2H checkpoint");
+                o += bytes;
+            }
+            check(ctx_sync(c), "sync export");
+            return TDDFT_OK;
+        })());
+    });
+}
+
+tddft_status tddft_state_import(tddft_ctx *c, const void *buf, size_t len, tddft_state **out) {
+    if (!c || !buf || !out) return TDDFT_E_INVALID;
+    *out = nullptr;
+    auto S = std::make_unique<tddft_state>();
+    tddft_status rc = guarded(c, [&]() -> tddft_status {
+        CkptHeader h{};
+        if (len < sizeof h) throw InvalidArg{"tddft_state_import: truncated checkpoint"};
+        std::memcpy(&h, buf, sizeof h);
+        if (std::memcmp(h.magic, CKPT_MAGIC, 8) != 0 || h.version != CKPT_VERSION)
+            throw InvalidArg{"tddft_state_import: not a checkpoint of this format"};
+        if (h.precision != c->prec || h.n_chi != c->nc || h.n_phi != c->nv)
+            throw InvalidArg{"tddft_state_import: checkpoint precision or sizes differ from the context"};
+        if (h.k <= 0 || h.k > KMAX || h.it < 0) throw InvalidArg{"tddft_state_import: bad header"};
+        if (len != ckpt_bytes(c, h.k, c->prec)) throw InvalidArg{"tddft_state_import: length does not match"};
+        S->ctx = c;
+        S->k = h.k;
+        S->it = h.it;
+        S->fallbacks = h.fallbacks;
+        S->inner_iters = h.inner_iters;
+        S->have_prev_omega = h.have_prev_omega != 0;
+        check(cudaMallocHost(reinterpret_cast<void **>(&S->host), (4 * S->k + 16) * sizeof(double)),
+              "cudaMallocHost");
+        return DISPATCH(c, ([&]() {
+            Impl<T> &I = impl<T>(c);
+            alloc_state<T>(c, S.get());
+            ensure_workspace(c, I, 2 * S->k);
+            StateBufs<T> &B = bufs<T>(S.get());
+            const unsigned char *p = static_cast<const unsigned char *>(buf) + sizeof h;
+            const double *om = reinterpret_cast<const double *>(p);
+            if (S->have_prev_omega) S->omega_prev.assign(om, om + S->k);
+            p += S->k * sizeof(double);
+            check(cudaMemcpyAsync(B.sc, p, 4 * sizeof(double), cudaMemcpyHostToDevice, c->st), "H2D sc");
+            check(cudaMemcpyAsync(B.flip, p + 4 * sizeof(double), sizeof(double), cudaMemcpyHostToDevice, c->st),
+                  "H2D flip");
+            p += CKPT_SCALARS * sizeof(double);
+            const size_t bytes = (size_t)2 * S->k * c->len() * sizeof(T);
+            for (T *X : carried<T>(B)) {
+                check(cudaMemcpyAsync(X, p, bytes, cudaMemcpyHostToDevice, c->st), "H2D checkpoint");
+                p += bytes;
+            }
+            check(ctx_sync(c), "sync import");
+            return TDDFT_OK;
+        })());
+    });
+    if (rc == TDDFT_OK) *out = S.release();
+    return rc;
 }
 
 tddft_status tddft_subspace(tddft_ctx *c, tddft_state *S, double *omega, double *pairing) {
@@ -1498,7 +1752,7 @@ tddft_status tddft_subspace(tddft_ctx *c, tddft_state *S, double *omega, double 
 tddft_status tddft_profile(tddft_ctx *c, int32_t enable) {
     if (!c) return TDDFT_E_INVALID;
     return guarded(c, [&]() -> tddft_status {
-        check(cudaStreamSynchronize(c->st), "sync profile");
+        check(ctx_sync(c), "sync profile");
         if (!c->prof) c->prof = profiler_new();
         profiler_reset(c->prof);
         c->prof_on = enable != 0;
@@ -1590,7 +1844,7 @@ tddft_status tddft_samples(tddft_ctx *c, tddft_state *S, int64_t cap, float *X, 
             if (c->trunc) mask_mul<T>(c->st, B.z, I.mask, c->len(), k2);
             learned_features<T>(c->st, h, k, na, c->nca, c->nva, c->nc, c->nv, I.lfc, I.lfv, I.ldist, X, I.ls);
             learned_targets<T>(c->st, B.z, h, I.ls, k, na, c->nca, c->nva, c->nc, c->nv, Tg, Wt);
-            check(cudaStreamSynchronize(c->st), "sync samples");
+            check(ctx_sync(c), "sync samples");
             return TDDFT_OK;
         })());
     });

@@ -16,12 +16,11 @@ void tc_gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, float alpha
 bool tc_gemm_available();
 
 bool tc_enabled() {
-    static int on = -1;
-    if (on < 0) {
+    static const bool on = []() {
         const char *e = std::getenv("TDDFT_NO_TC");
-        on = (e && e[0] == '1') ? 0 : (tc_gemm_available() ? 1 : 0);
-    }
-    return on == 1;
+        return !(e && e[0] == '1') && tc_gemm_available();
+    }();
+    return on;
 }
 
 namespace {

@@ -480,12 +480,12 @@ void response_density(cudaStream_t st, const GridShape &g, const TileSet<T> &chi
     ProfScope ps(st, ST_DENSITY, 2.0 * k * g.pair_points,
                  sizeof(T) * (g.table_values + (double)k * g.n * g.n * g.n));
     const size_t sm = density_smem(sizeof(T));
-    static bool attr = false;
-    if (!attr) {
+    static const bool attr = [&]() {   // once per process, thread-safe
         check(cudaFuncSetAttribute(density_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
               "cudaFuncSetAttribute(density)");
-        attr = true;
-    }
+        return true;
+    }();
+    (void)attr;
     dim3 grid(chi.ntiles, k);
     density_kernel<T><<<grid, 256, sm, st>>>(g.n, g.nt, chi.off, chi.ids, chi.val, phi.off, phi.ids,
                                              phi.val, nphi, P, sP, rho);
@@ -518,16 +518,16 @@ void hartree_fxc(cudaStream_t st, const GridShape &g, const T *rho, const T *fxc
     const double n3d = (double)n * n * n;
     ProfScope ps(st, ST_FFT, pairs * 2.0 * 5.0 * n3d * std::log2(n3d), sizeof(T) * (2.0 * k + 1.0) * n3d);
     const size_t sm = 2 * (size_t)L * n * sizeof(Vc);
-    static bool attr = false;
-    if (!attr) {
+    static const bool attr = [&]() {   // once per process, thread-safe
         const int mx = 2 * L * 256 * (int)sizeof(Vc);
         check(cudaFuncSetAttribute(fft_z_forward_real<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx), "attr fz");
         check(cudaFuncSetAttribute(fft_z_inverse_real<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx), "attr iz");
         check(cudaFuncSetAttribute(fft_strided<T, 1, -1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx), "attr fy");
         check(cudaFuncSetAttribute(fft_strided<T, 1, +1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx), "attr iy");
         check(cudaFuncSetAttribute(fft_strided<T, 0, -1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx), "attr x");
-        attr = true;
-    }
+        return true;
+    }();
+    (void)attr;
     Vc *w = reinterpret_cast<Vc *>(work);
     const long long nlines = (long long)n * n;
     dim3 gz((unsigned)((nlines + L - 1) / L), pairs);

@@ -384,12 +384,12 @@ void response_density_tc(cudaStream_t st, const GridShape &g, const TileSet<floa
     if (G < 1) throw CudaError{cudaErrorInvalidValue, "density_tc: tile too large for shared memory"};
     const int ngroups = (k + G - 1) / G;
     const size_t sm = density_tc_smem(KBmax, G * NP);
-    static bool attr = false;
-    if (!attr) {
+    static const bool attr = [&]() {   // once per process, thread-safe
         check(cudaFuncSetAttribute(density_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),
               "attr density_tc");
-        attr = true;
-    }
+        return true;
+    }();
+    (void)attr;
     dim3 grid(ngroups, chi.ntiles);
     density_tc_kernel<<<grid, DENS_THREADS, sm, st>>>(mx, g.n, g.nt, KBmax, NP, G, k, chi.off, chi.ids, phi.off,
                                                       phi.ids, phi.val, nphi, P, sP, scale, rho, err,
@@ -652,12 +652,12 @@ void potential_integrals_tc(cudaStream_t st, const GridShape &g, const TileSet<f
     // one launch per class of tiles by 128-row chi blocks (1, 2, 3), one state per CTA: the
     // smaller a class's shared memory and TMEM, the more CTAs share an SM (3, 2, 1)
     if (NPmax > 128) throw CudaError{cudaErrorInvalidValue, "integrals_tc: more than 128 phi per tile"};
-    static bool attr = false;
-    if (!attr) {
+    static const bool attr = [&]() {   // once per process, thread-safe
         check(cudaFuncSetAttribute(integrals_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),
               "attr integrals_tc");
-        attr = true;
-    }
+        return true;
+    }();
+    (void)attr;
     const bool vec_ok = (nphi % 4 == 0) && ((reinterpret_cast<unsigned long long>(out) & 15ull) == 0);
     const int *lp = tile_list;
     for (int c = 0; c < 3; ++c) {

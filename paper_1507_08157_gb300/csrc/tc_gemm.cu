@@ -294,21 +294,22 @@ size_t tc_smem(int nsplit) {
 }
 
 int sm_count() {
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
+    static const int n = []() {
+        int dev = 0, v = 0;
         check(cudaGetDevice(&dev), "cudaGetDevice");
-        check(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev), "SM count");
-    }
+        check(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev), "SM count");
+        return v;
+    }();
     return n;
 }
 
 int *error_word() {
-    static int *w = nullptr;
-    if (!w) {
-        check(cudaMalloc(&w, sizeof(int)), "cudaMalloc tc error word");
-        check(cudaMemset(w, 0, sizeof(int)), "memset tc error word");
-    }
+    static int *const w = []() {
+        int *p = nullptr;
+        check(cudaMalloc(&p, sizeof(int)), "cudaMalloc tc error word");
+        check(cudaMemset(p, 0, sizeof(int)), "memset tc error word");
+        return p;
+    }();
     return w;
 }
 
@@ -351,8 +352,7 @@ void tc_gemm_nt(cudaStream_t st, int M, int N, int K, float alpha, const float *
     if (!asp) malo = ma;
     if (!bsp) mblo = mb;
     const size_t sm = tc_smem(nsplit);
-    static bool attrs = false;
-    if (!attrs) {
+    static const bool attrs = [&]() {   // once per process, thread-safe
         check(cudaFuncSetAttribute(tc_gemm_kernel<1, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem(1)),
               "attr tc1");
         check(cudaFuncSetAttribute(tc_gemm_kernel<1, 112>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem(1)),
@@ -361,8 +361,9 @@ void tc_gemm_nt(cudaStream_t st, int M, int N, int K, float alpha, const float *
               "attr tc3");
         check(cudaFuncSetAttribute(tc_gemm_kernel<3, 112>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem(3)),
               "attr tc3");
-        attrs = true;
-    }
+        return true;
+    }();
+    (void)attrs;
     const long long ntiles = (long long)((N + TN - 1) / TN) * ((M + TBM - 1) / TBM) * batch;
     const int grid = (int)std::min<long long>(ntiles, sm_count());
     int *err = error_word();
@@ -600,13 +601,10 @@ void tc_gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, float alpha
 
 int *tc_error_word() { return error_word(); }
 
-int tc_error_read_and_clear(cudaStream_t st) {
-    int h = 0;
-    int *w = error_word();
-    check(cudaMemcpyAsync(&h, w, sizeof(int), cudaMemcpyDeviceToHost, st), "D2H tc error");
-    check(cudaStreamSynchronize(st), "sync tc error");
-    if (h) check(cudaMemsetAsync(w, 0, sizeof(int), st), "clear tc error");
-    return h;
+void tc_error_fetch(cudaStream_t st, int *host) {
+    check(cudaMemcpyAsync(host, error_word(), sizeof(int), cudaMemcpyDeviceToHost, st), "D2H tc error");
 }
+
+void tc_error_clear(cudaStream_t st) { check(cudaMemsetAsync(error_word(), 0, sizeof(int), st), "clear tc error"); }
 
 }  // namespace tddft

@@ -66,7 +66,8 @@ SYMBOLS = sorted(["tddft_default_options", "tddft_create", "tddft_destroy", "tdd
                   "tddft_work", "tddft_mlp_create", "tddft_mlp_destroy", "tddft_mlp_last_error",
                   "tddft_mlp_size", "tddft_mlp_set", "tddft_mlp_get", "tddft_mlp_forward",
                   "tddft_mlp_loss_grad", "tddft_mlp_train", "tddft_learned_dims", "tddft_set_mlp",
-                  "tddft_samples", "tddft_state_stats"])
+                  "tddft_samples", "tddft_state_stats", "tddft_state_export",
+                  "tddft_state_import", "tddft_create_batch", "tddft_solve_batch"])
 
 _lib = None
 _live = weakref.WeakSet()      # open contexts and states, closed before interpreter shutdown
@@ -135,13 +136,20 @@ def load(path: str = LIB_PATH):
     lib.tddft_set_mlp.argtypes = [vp, vp]
     lib.tddft_samples.argtypes = [vp, vp, i64, vp, vp, vp, ctypes.POINTER(i64)]
     lib.tddft_state_stats.argtypes = [vp, c_int32_p, c_int32_p, ctypes.POINTER(i64)]
+    lib.tddft_state_export.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_size_t)]
+    lib.tddft_state_import.argtypes = [vp, vp, ctypes.c_size_t, ctypes.POINTER(vp)]
+    lib.tddft_create_batch.argtypes = [ctypes.POINTER(_System), ctypes.c_int32, ctypes.POINTER(_Options), vp,
+                                       ctypes.POINTER(vp)]
+    lib.tddft_solve_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int32, ctypes.c_int32,
+                                      vp, vp, c_int32_p, c_int32_p]
     for name in ("tddft_create", "tddft_dims", "tddft_apply", "tddft_response_density",
                  "tddft_response_potential", "tddft_potential_integrals", "tddft_fxc",
                  "tddft_state_create", "tddft_pcg_step", "tddft_solve", "tddft_state_get",
                  "tddft_subspace", "tddft_pattern", "tddft_profile", "tddft_profile_read",
                  "tddft_work", "tddft_mlp_create", "tddft_mlp_set", "tddft_mlp_get", "tddft_mlp_forward",
                  "tddft_mlp_loss_grad", "tddft_mlp_train", "tddft_learned_dims", "tddft_set_mlp",
-                 "tddft_samples", "tddft_state_stats"):
+                 "tddft_samples", "tddft_state_stats", "tddft_state_export",
+                 "tddft_state_import", "tddft_create_batch", "tddft_solve_batch"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -186,51 +194,95 @@ def _options(precision="fp64", mode="full", precond="iter", precond_tol=1e-4, pr
     return o
 
 
+def _marshal(sys: System, fxc="lda"):
+    """The tddft_system view of a System; `keep` holds the arrays it points into."""
+    keep = []
+
+    def arr(a, dt):
+        a = np.ascontiguousarray(a, dtype=dt)
+        keep.append(a)
+        return a.ctypes.data_as(ctypes.POINTER(np.ctypeslib.as_ctypes_type(dt)))
+
+    def funcs(fs):
+        f = _Funcs()
+        f.nfun = fs.nfun
+        f.atom = arr(fs.atom, np.int32)
+        f.box = arr(fs.box, np.int32)
+        f.off = arr(fs.off, np.int64)
+        f.val = arr(fs.val, np.float64)
+        return f
+
+    s = _System()
+    s.cell = sys.cell
+    s.n = sys.n
+    s.natoms = sys.natoms
+    s.pos = arr(sys.pos, np.float64)
+    s.phi = funcs(sys.phi)
+    s.chi = funcs(sys.chi)
+    s.S_chi = arr(sys.S_chi, np.float64)
+    s.S_phi = arr(sys.S_phi, np.float64)
+    s.H_chi = arr(sys.H_chi, np.float64)
+    s.H_phi = arr(sys.H_phi, np.float64)
+    s.P_v = arr(sys.P_v, np.float64)
+    s.P_c = arr(sys.P_c, np.float64)
+    s.n0 = arr(sys.n0, np.float64)
+    s.fxc_kind = FXC[fxc]
+    s.kernel_cutoff = sys.kernel_cutoff
+    return s, keep
+
+
+def create_batch(systems, fxc="lda", stream=None, **opts):
+    """Contexts for several systems at once (tddft_create_batch): each owns its own stream."""
+    lib = load()
+    n = len(systems)
+    views = [_marshal(sy_, fxc) for sy_ in systems]
+    arr = (_System * n)(*[v[0] for v in views])
+    out = (ctypes.c_void_p * n)()
+    options = _options(**opts)
+    st = ctypes.c_void_p(stream) if stream is not None else None
+    rc = lib.tddft_create_batch(arr, n, ctypes.byref(options), st, out)
+    if rc != OK:
+        raise TddftError(rc, "tddft_create_batch failed (see stderr)")
+    return [Context(sy_, _handle=ctypes.c_void_p(out[i]), **opts) for i, sy_ in enumerate(systems)]
+
+
+def solve_batch(states, nthreads=0):
+    """tddft_solve_batch over states of distinct contexts. Returns per system (omega, resid),
+    the iteration counts and the statuses."""
+    lib = load()
+    n = len(states)
+    ks = [s_.k for s_ in states]
+    om, res = np.zeros(sum(ks)), np.zeros(sum(ks))
+    it = np.zeros(n, dtype=np.int32)
+    status = np.zeros(n, dtype=np.int32)
+    cs = (ctypes.c_void_p * n)(*[s_.ctx._ctx.value for s_ in states])
+    ss = (ctypes.c_void_p * n)(*[s_._st.value for s_ in states])
+    rc = lib.tddft_solve_batch(cs, ss, n, nthreads, om.ctypes.data, res.ctypes.data,
+                               it.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                               status.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    if rc == E_INVALID:
+        raise TddftError(rc, "tddft_solve_batch: bad arguments")
+    off = np.concatenate([[0], np.cumsum(ks)])
+    return ([(om[off[i]:off[i + 1]], res[off[i]:off[i + 1]]) for i in range(n)], it, status)
+
+
 class Context:
     """One system on the GPU (tddft_create). Keyword options follow tddft_options."""
 
-    def __init__(self, sys: System, fxc="lda", stream=None, **opts):
+    def __init__(self, sys: System, fxc="lda", stream=None, _handle=None, **opts):
         lib = load()
         self._lib = lib
         self.sys = sys
-        keep = []
-
-        def arr(a, dt):
-            a = np.ascontiguousarray(a, dtype=dt)
-            keep.append(a)
-            return a.ctypes.data_as(ctypes.POINTER(np.ctypeslib.as_ctypes_type(dt)))
-
-        def funcs(fs):
-            f = _Funcs()
-            f.nfun = fs.nfun
-            f.atom = arr(fs.atom, np.int32)
-            f.box = arr(fs.box, np.int32)
-            f.off = arr(fs.off, np.int64)
-            f.val = arr(fs.val, np.float64)
-            return f
-
-        s = _System()
-        s.cell = sys.cell
-        s.n = sys.n
-        s.natoms = sys.natoms
-        s.pos = arr(sys.pos, np.float64)
-        s.phi = funcs(sys.phi)
-        s.chi = funcs(sys.chi)
-        s.S_chi = arr(sys.S_chi, np.float64)
-        s.S_phi = arr(sys.S_phi, np.float64)
-        s.H_chi = arr(sys.H_chi, np.float64)
-        s.H_phi = arr(sys.H_phi, np.float64)
-        s.P_v = arr(sys.P_v, np.float64)
-        s.P_c = arr(sys.P_c, np.float64)
-        s.n0 = arr(sys.n0, np.float64)
-        s.fxc_kind = FXC[fxc]
-        s.kernel_cutoff = sys.kernel_cutoff
         self.options = _options(**opts)
-        ctx = ctypes.c_void_p()
-        st = ctypes.c_void_p(stream) if stream is not None else None
-        rc = lib.tddft_create(ctypes.byref(s), ctypes.byref(self.options), st, ctypes.byref(ctx))
-        if rc != OK:
-            raise TddftError(rc, "tddft_create failed (see stderr)")
+        if _handle is None:
+            s, keep = _marshal(sys, fxc)
+            ctx = ctypes.c_void_p()
+            st = ctypes.c_void_p(stream) if stream is not None else None
+            rc = lib.tddft_create(ctypes.byref(s), ctypes.byref(self.options), st, ctypes.byref(ctx))
+            if rc != OK:
+                raise TddftError(rc, "tddft_create failed (see stderr)")
+        else:
+            ctx = _handle
         self._ctx = ctx
         self.nc, self.nv, self.n = sys.chi.nfun, sys.phi.nfun, sys.n
         self._states = weakref.WeakSet()
@@ -309,6 +361,10 @@ class Context:
     def state(self, Y0):
         return State(self, Y0)
 
+    def import_state(self, blob):
+        """A state resumed from the bytes of State.export (tddft_state_import)."""
+        return State(self, None, blob=bytes(blob))
+
     def profile(self, enable=True):
         self._check(self._lib.tddft_profile(self._ctx, 1 if enable else 0))
 
@@ -355,12 +411,17 @@ class Context:
 class State:
     """Trial pairs of the PCG solver (tddft_state_create)."""
 
-    def __init__(self, ctx: Context, Y0):
+    def __init__(self, ctx: Context, Y0, blob=None):
         self.ctx = ctx
-        self.k = Y0.shape[0]
-        Y0 = np.ascontiguousarray(Y0, dtype=np.float64) if isinstance(Y0, np.ndarray) else Y0
         st = ctypes.c_void_p()
-        ctx._check(ctx._lib.tddft_state_create(ctx._ctx, self.k, _ptr(Y0), ctypes.byref(st)))
+        if blob is not None:
+            buf = ctypes.create_string_buffer(blob, len(blob))
+            ctx._check(ctx._lib.tddft_state_import(ctx._ctx, buf, len(blob), ctypes.byref(st)))
+            self.k = int(np.frombuffer(blob, dtype=np.int32, count=1, offset=16)[0])
+        else:
+            self.k = Y0.shape[0]
+            Y0 = np.ascontiguousarray(Y0, dtype=np.float64) if isinstance(Y0, np.ndarray) else Y0
+            ctx._check(ctx._lib.tddft_state_create(ctx._ctx, self.k, _ptr(Y0), ctypes.byref(st)))
         self._st = st
         ctx._states.add(self)
         _live.add(self)
@@ -397,6 +458,14 @@ class State:
         self.ctx._check(self.ctx._lib.tddft_state_get(
             self.ctx._ctx, self._st, *(_ptr(out[n]) for n in ("Pp", "Pq", "fp", "fq", "Lp", "Lq"))))
         return out
+
+    def export(self):
+        """The state as checkpoint bytes (tddft_state_export)."""
+        n = ctypes.c_size_t(0)
+        self.ctx._check(self.ctx._lib.tddft_state_export(self.ctx._ctx, self._st, None, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        self.ctx._check(self.ctx._lib.tddft_state_export(self.ctx._ctx, self._st, buf, ctypes.byref(n)))
+        return buf.raw[:n.value]
 
     def stats(self):
         """(PCG steps, learned-to-CG fallbacks, inner CG iterations)."""
