@@ -218,6 +218,24 @@ tddft_status tddft_solve(tddft_ctx *ctx, tddft_state *st, double *omega, double 
 tddft_status tddft_state_get(tddft_ctx *ctx, const tddft_state *st, double *Pp, double *Pq,
                              double *fp, double *fq, double *Lp, double *Lq);
 
+/* Oscillator strengths of the current Ritz pairs (the paper reports its results as energies
+ * with oscillator strengths, Sec. IV). The pairs are rotated by the eigenvectors of the
+ * symmetrised Q of the subspace diagonalisation (Sec. III C); the transition dipole of pair m is
+ * the dipole of its response density rho^q (Sec. II C) with the position of grid point i along
+ * an axis taken as i h - L/2 (from the cell centre), and f_m = (2/3) omega_m |mu_m|^2 with
+ * <p_m, q_m> = 1. Outputs (host, any may be NULL): omega [k] ascending (Ha), f [k]
+ * (dimensionless), mu [k][3] (e bohr; the sign of each row is arbitrary). Meaningful at
+ * convergence; any iterate gives the values of its subspace. */
+tddft_status tddft_oscillator_strengths(tddft_ctx *ctx, tddft_state *st, double *omega, double *f,
+                                        double *mu);
+
+/* Broadened absorption spectrum S(E_e) = sum_i f_i (gamma / pi) / ((E_e - omega_i)^2 + gamma^2)
+ * for n energies E (Ha), gamma the half width at half maximum (Ha; the paper's figures use
+ * 0.025 eV). omega, f [k], E and S [n] are host or device buffers; runs on the context's stream.
+ * INVALID for k <= 0, n <= 0, gamma <= 0 or NULL buffers. */
+tddft_status tddft_spectrum(tddft_ctx *ctx, int32_t k, const double *omega, const double *f,
+                            double gamma, int32_t n, const double *E, double *S);
+
 /* Checkpoint and resume of a PCG state (Sec. III C carries, from one iteration to the next, the
  * trial pairs with their operator images and the previous search direction with its
  * preconditioned gradient; the checkpoint holds exactly these). tddft_state_export writes into

@@ -1739,6 +1739,54 @@ tddft_status tddft_state_import(tddft_ctx *c, const void *buf, size_t len, tddft
     return rc;
 }
 
+tddft_status tddft_oscillator_strengths(tddft_ctx *c, tddft_state *S, double *omega, double *f, double *mu) {
+    if (!c || !S || S->ctx != c) return TDDFT_E_INVALID;
+    return guarded(c, [&]() -> tddft_status {
+        return DISPATCH(c, ([&]() {
+            Impl<T> &I = impl<T>(c);
+            StateBufs<T> &B = bufs<T>(S);
+            const int k = S->k;
+            const long long len = c->len();
+            if (!S->evaluated) evaluate<T>(c, S);
+            ensure_workspace(c, I, 2 * k);
+            // Ritz values and vectors of the symmetrised Q; eigenvectors in coef (k x k)
+            subspace(c->st, k, B.A, B.evout, B.dvec3, B.coef);
+            density(c, I, B.P + k * len, k);                  // rho^q of the current q_j
+            const int nblk = 152;
+            double *part = B.gscr, *out = B.gscr + (size_t)KMAX * nblk * 3;
+            const double h = c->cell / c->n;
+            dipole_partials<T>(c->st, I.rho, c->n, h, c->cell, k, nblk, part);
+            ritz_strengths(c->st, k, B.evout, B.coef, part, nblk, c->dV, out);
+            std::vector<double> hv(4 * (size_t)k), om(k);
+            check(cudaMemcpyAsync(om.data(), B.evout, k * sizeof(double), cudaMemcpyDeviceToHost, c->st), "D2H omega");
+            check(cudaMemcpyAsync(hv.data(), out, 4 * k * sizeof(double), cudaMemcpyDeviceToHost, c->st), "D2H f");
+            check_tc_error(c);
+            if (omega) std::memcpy(omega, om.data(), k * sizeof(double));
+            if (f) std::memcpy(f, hv.data(), k * sizeof(double));
+            if (mu) std::memcpy(mu, hv.data() + k, 3 * k * sizeof(double));
+            return TDDFT_OK;
+        })());
+    });
+}
+
+tddft_status tddft_spectrum(tddft_ctx *c, int32_t k, const double *omega, const double *f, double gamma, int32_t n,
+                            const double *E, double *S) {
+    if (!c) return TDDFT_E_INVALID;
+    return guarded(c, [&]() -> tddft_status {
+        if (k <= 0 || n <= 0 || !omega || !f || !E || !S || !(gamma > 0.0))
+            throw InvalidArg{"tddft_spectrum: bad arguments"};
+        Mem tmp;
+        double *d = tmp.alloc<double>(2 * (size_t)k + 2 * (size_t)n);
+        check(cudaMemcpyAsync(d, omega, k * sizeof(double), cudaMemcpyDefault, c->st), "copy omega");
+        check(cudaMemcpyAsync(d + k, f, k * sizeof(double), cudaMemcpyDefault, c->st), "copy f");
+        check(cudaMemcpyAsync(d + 2 * k, E, n * sizeof(double), cudaMemcpyDefault, c->st), "copy E");
+        lorentz_spectrum(c->st, k, d, d + k, gamma, n, d + 2 * k, d + 2 * k + n);
+        check(cudaMemcpyAsync(S, d + 2 * k + n, n * sizeof(double), cudaMemcpyDefault, c->st), "copy S");
+        check(ctx_sync(c), "sync spectrum");
+        return TDDFT_OK;
+    });
+}
+
 tddft_status tddft_subspace(tddft_ctx *c, tddft_state *S, double *omega, double *pairing) {
     if (!c || !S || S->ctx != c) return TDDFT_E_INVALID;
     return guarded(c, [&]() -> tddft_status {

@@ -819,7 +819,7 @@ __global__ void cg_dir_kernel(T *__restrict__ p, const T *__restrict__ r, const 
 
 // Ritz pairs of Q and the pairing errors: rotated halves |<p, f_p>_a - omega_a|,
 // |<q, f_q>_a - omega_a| from the p-part and q-part matrices of A.
-__global__ void subspace_kernel(int k, const double *A, double *omega, double *pairing) {
+__global__ void subspace_kernel(int k, const double *A, double *omega, double *pairing, double *vecs) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const int k2 = 2 * k;
     double Q[KMAX * KMAX], Ap[KMAX * KMAX], Aq[KMAX * KMAX], V[KMAX * KMAX];
@@ -886,6 +886,8 @@ __global__ void subspace_kernel(int k, const double *A, double *omega, double *p
         omega[m] = om;
         pairing[2 * m] = fabs(hp - om);
         pairing[2 * m + 1] = fabs(hq - om);
+        if (vecs)
+            for (int i = 0; i < k; ++i) vecs[i * k + m] = V[i * k + c];   // column m: Ritz pair m
     }
 }
 
@@ -1035,9 +1037,9 @@ void cg_scalars(cudaStream_t st, int n, int phase, double tol, const double *pLp
                                                           n_active);
     check_launch("cg_scalars_kernel");
 }
-void subspace(cudaStream_t st, int k, const double *A, double *omega, double *pairing) {
+void subspace(cudaStream_t st, int k, const double *A, double *omega, double *pairing, double *vecs) {
     ProfScope ps(st, ST_SMALL, 0.0, 0.0);
-    subspace_kernel<<<1, 1, 0, st>>>(k, A, omega, pairing);
+    subspace_kernel<<<1, 1, 0, st>>>(k, A, omega, pairing, vecs);
     check_launch("subspace_kernel");
 }
 

@@ -67,7 +67,8 @@ SYMBOLS = sorted(["tddft_default_options", "tddft_create", "tddft_destroy", "tdd
                   "tddft_mlp_size", "tddft_mlp_set", "tddft_mlp_get", "tddft_mlp_forward",
                   "tddft_mlp_loss_grad", "tddft_mlp_train", "tddft_learned_dims", "tddft_set_mlp",
                   "tddft_samples", "tddft_state_stats", "tddft_state_export",
-                  "tddft_state_import", "tddft_create_batch", "tddft_solve_batch"])
+                  "tddft_state_import", "tddft_create_batch", "tddft_solve_batch",
+                  "tddft_oscillator_strengths", "tddft_spectrum"])
 
 _lib = None
 _live = weakref.WeakSet()      # open contexts and states, closed before interpreter shutdown
@@ -138,6 +139,8 @@ def load(path: str = LIB_PATH):
     lib.tddft_state_stats.argtypes = [vp, c_int32_p, c_int32_p, ctypes.POINTER(i64)]
     lib.tddft_state_export.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_size_t)]
     lib.tddft_state_import.argtypes = [vp, vp, ctypes.c_size_t, ctypes.POINTER(vp)]
+    lib.tddft_oscillator_strengths.argtypes = [vp, vp, vp, vp, vp]
+    lib.tddft_spectrum.argtypes = [vp, ctypes.c_int32, vp, vp, ctypes.c_double, ctypes.c_int32, vp, vp]
     lib.tddft_create_batch.argtypes = [ctypes.POINTER(_System), ctypes.c_int32, ctypes.POINTER(_Options), vp,
                                        ctypes.POINTER(vp)]
     lib.tddft_solve_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int32, ctypes.c_int32,
@@ -149,7 +152,8 @@ def load(path: str = LIB_PATH):
                  "tddft_work", "tddft_mlp_create", "tddft_mlp_set", "tddft_mlp_get", "tddft_mlp_forward",
                  "tddft_mlp_loss_grad", "tddft_mlp_train", "tddft_learned_dims", "tddft_set_mlp",
                  "tddft_samples", "tddft_state_stats", "tddft_state_export",
-                 "tddft_state_import", "tddft_create_batch", "tddft_solve_batch"):
+                 "tddft_state_import", "tddft_create_batch", "tddft_solve_batch",
+                 "tddft_oscillator_strengths", "tddft_spectrum"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -361,6 +365,16 @@ class Context:
     def state(self, Y0):
         return State(self, Y0)
 
+    def spectrum(self, omega, f, E, gamma):
+        """S(E) = sum_i f_i (gamma / pi) / ((E - omega_i)^2 + gamma^2) on the device (tddft_spectrum)."""
+        omega = np.ascontiguousarray(omega, dtype=np.float64)
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        S = np.empty_like(E)
+        self._check(self._lib.tddft_spectrum(self._ctx, omega.size, omega.ctypes.data, f.ctypes.data, gamma,
+                                             E.size, E.ctypes.data, S.ctypes.data))
+        return S
+
     def import_state(self, blob):
         """A state resumed from the bytes of State.export (tddft_state_import)."""
         return State(self, None, blob=bytes(blob))
@@ -458,6 +472,13 @@ class State:
         self.ctx._check(self.ctx._lib.tddft_state_get(
             self.ctx._ctx, self._st, *(_ptr(out[n]) for n in ("Pp", "Pq", "fp", "fq", "Lp", "Lq"))))
         return out
+
+    def oscillator_strengths(self):
+        """(omega [k], f [k], mu [k, 3]) of the current Ritz pairs (tddft_oscillator_strengths)."""
+        om, f, mu = np.empty(self.k), np.empty(self.k), np.empty((self.k, 3))
+        self.ctx._check(self.ctx._lib.tddft_oscillator_strengths(self.ctx._ctx, self._st, om.ctypes.data,
+                                                                 f.ctypes.data, mu.ctypes.data))
+        return om, f, mu
 
     def export(self):
         """The state as checkpoint bytes (tddft_state_export)."""
