@@ -248,8 +248,9 @@ tddft_status tddft_spectrum(tddft_ctx *ctx, int32_t k, const double *omega, cons
  * context's working type (float64 for FP64, float32 for MIXED), native byte order.
  * tddft_state_import makes a new state from such a buffer (len exactly the exported size) on a
  * context of the same precision and sizes (INVALID otherwise); its further steps are those the
- * exported state would have taken. The caller owns buf; the state belongs to the context it was
- * imported on and is freed with tddft_state_destroy. */
+ * exported state would have taken, up to the rounding order of the grid integrals' atomic
+ * accumulation, which varies from run to run. The caller owns buf; the state belongs to the
+ * context it was imported on and is freed with tddft_state_destroy. */
 tddft_status tddft_state_export(tddft_ctx *ctx, const tddft_state *st, void *buf, size_t *len);
 tddft_status tddft_state_import(tddft_ctx *ctx, const void *buf, size_t len, tddft_state **out);
 

@@ -522,20 +522,39 @@ __global__ void __launch_bounds__(192, 3) integrals_tc_kernel(
             mma_commit(&ctl->acc_done);
         }
     } else {
-        // workers: build W slices, then the epilogue
+        // workers: build W slices, then the epilogue. The phi values of a slice are loaded into
+        // registers before the wait for the stage (all loads of a thread in flight at once, and
+        // overlapping the MMAs that still read the stage), then scaled by V, rounded and stored.
+        constexpr int WIT = 8;                       // (NB x 8) / 128 items per thread, NB <= 128
         for (int kb = 0; kb < KS; ++kb) {
             const int st = kb & 1, use = kb >> 1;
-            if (use > 0 && !mbar_wait(&ctl->mma_done[st], (use - 1) & 1, abort)) break;
-            unsigned char *W = Ws + (size_t)st * NB * 128;
-            for (int idx = threadIdx.x; idx < NB * 8; idx += 128) {
+            float4 pa[WIT], pb[WIT];
+#pragma unroll
+            for (int u = 0; u < WIT; ++u) {
+                const int idx = threadIdx.x + u * 128;
                 const int row = idx % NB, c8 = idx / NB;
                 const int sl = row / NP, b = row - sl * NP;
-                unsigned short h[8];
-                if (sl < gs && b < np) {
-                    // 8 consecutive points: two 16-byte loads each of phi (global) and V (shared)
+                pa[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                pb[u] = pa[u];
+                if (idx < NB * 8 && sl < gs && b < np) {
                     const float4 *ph = reinterpret_cast<const float4 *>(pval + (long long)(p0 + b) * TILE_PTS + kb * 64 + c8 * 8);
+                    pa[u] = __ldg(ph);
+                    pb[u] = __ldg(ph + 1);
+                }
+            }
+            if (use > 0 && !mbar_wait(&ctl->mma_done[st], (use - 1) & 1, abort)) break;
+            unsigned char *W = Ws + (size_t)st * NB * 128;
+#pragma unroll
+            for (int u = 0; u < WIT; ++u) {
+                const int idx = threadIdx.x + u * 128;
+                if (idx >= NB * 8) break;
+                const int row = idx % NB, c8 = idx / NB;
+                const int sl = row / NP;
+                unsigned short h[8];
+                if (sl < gs) {
+                    // 8 consecutive points: phi from the registers, V from shared memory
                     const float4 *vv = reinterpret_cast<const float4 *>(Vt + sl * TILE_PTS + kb * 64 + c8 * 8);
-                    const float4 p0v = __ldg(ph), p1v = __ldg(ph + 1), v0 = vv[0], v1 = vv[1];
+                    const float4 v0 = vv[0], v1 = vv[1], p0v = pa[u], p1v = pb[u];
                     h[0] = __half_as_ushort(__float2half_rn(p0v.x * v0.x));
                     h[1] = __half_as_ushort(__float2half_rn(p0v.y * v0.y));
                     h[2] = __half_as_ushort(__float2half_rn(p0v.z * v0.z));
@@ -620,15 +639,11 @@ size_t integrals_tc_smem(int NB, int G, int mbmax) {
     return 1024 + (size_t)2 * mbmax * 16384 + (size_t)2 * NB * 128 + (size_t)G * TILE_PTS * 4 + sizeof(IntShared);
 }
 
-// accumulator stride in TMEM columns: 256 when every tile has <= 256 chi (2 M blocks), else 128
-int integrals_tc_stride(int maxc) { return maxc <= 256 ? 256 : 128; }
-
+// one state per CTA: the accumulator of each 128-row chi block takes NP <= 128 TMEM columns, and
+// a tile may hold up to three such blocks
 int integrals_tc_group(int NP, int k, int maxc) {
-    if (maxc > 384) return 0;
-    const int stride = integrals_tc_stride(maxc);
-    for (int G = std::min(16, std::min(k, stride / NP)); G >= 1; --G)
-        if (integrals_tc_smem(G * NP, G, 3) <= 227 * 1024) return G;
-    return 0;
+    if (maxc > 384 || NP > 128 || k < 1) return 0;
+    return integrals_tc_smem(NP, 1, 3) <= 227 * 1024 ? 1 : 0;
 }
 
 void potential_integrals_tc(cudaStream_t st, const GridShape &g, const TileSet<float> &chi,
