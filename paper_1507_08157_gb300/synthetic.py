@@ -54,6 +54,7 @@ class Recipe:
     h_decay_ang: float = 2.0   # entries decay as exp(-d / h_decay)
     kernel_cutoff_ang: float = 0.0   # <= 0: response kernels not truncated
     seed: int = 0
+    cluster_ang: float = 0.0   # > 0: atoms only inside a centred cube of this side (vacuum around)
 
 
 # The smallest workload: 8 atoms, 16 A cell, 48^3 grid, 4 phi + 4 chi (s, p) per atom, 7 A radius,
@@ -123,15 +124,16 @@ def _workers():
     return max(1, min(32, os.cpu_count() or 1))
 
 
-def _rsa_positions(rng, natoms, cell, min_sep):
+def _rsa_positions(rng, natoms, cell, min_sep, cluster=0.0):
     pos = np.zeros((natoms, 3))
     placed = 0
     tries = 0
+    lo, hi = (0.0, cell) if cluster <= 0.0 else (0.5 * (cell - cluster), 0.5 * (cell + cluster))
     while placed < natoms:
         tries += 1
         if tries > 2000000:
             raise RuntimeError("could not place atoms at the requested minimum separation")
-        x = rng.uniform(0.0, cell, size=3)
+        x = rng.uniform(lo, hi, size=3)
         if placed:
             d = pos[:placed] - x
             d -= cell * np.round(d / cell)
@@ -346,7 +348,8 @@ def generate(recipe: Recipe) -> System:
     n = int(recipe.ngrid)
     h = cell / n
     R = recipe.radius_ang * BOHR_PER_ANG
-    pos = _rsa_positions(r_pos, recipe.natoms, cell, recipe.min_sep_ang * BOHR_PER_ANG)
+    pos = _rsa_positions(r_pos, recipe.natoms, cell, recipe.min_sep_ang * BOHR_PER_ANG,
+                         recipe.cluster_ang * BOHR_PER_ANG)
     width = (recipe.width_ang[0] * BOHR_PER_ANG, recipe.width_ang[1] * BOHR_PER_ANG)
     phi = _tabulate(r_wphi, pos, recipe.nphi, cell, n, R, width)
     chi = _tabulate(r_wchi, pos, recipe.nchi, cell, n, R, width)
@@ -370,6 +373,35 @@ def generate(recipe: Recipe) -> System:
                   S_phi=S_phi, S_chi=S_chi, H_phi=H_phi, H_chi=H_chi, P_v=P_v, P_c=P_c,
                   n0=n0, kernel_cutoff=recipe.kernel_cutoff_ang * BOHR_PER_ANG,
                   n_occ=n_occ, n_cond=n_cond)
+
+
+def smooth_grid(n: int) -> int:
+    """The smallest 2/3/5-smooth integer >= n (FFT-friendly grid sizes)."""
+    while True:
+        m = n
+        for p in (2, 3, 5):
+            while m % p == 0:
+                m //= p
+        if m == 1:
+            return n
+        n += 1
+
+
+def batch_recipes(nsys: int, seed: int, n_min=20, n_max=300, density=0.1, radius=7.0, h=0.25, k_max=8):
+    """Uneven systems for a batched launch: atom counts log-uniform in [n_min, n_max], atoms in a
+    cube at `density` atoms / A^3, the cell the cube plus 2R + 1 A of vacuum rounded up to a
+    2/3/5-smooth grid of spacing h, 4 phi + 4 chi (s, p) per atom of radius R, states uniform in
+    1..k_max. Returns [(Recipe, k)]."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(nsys):
+        natoms = int(round(math.exp(rng.uniform(math.log(n_min), math.log(n_max)))))
+        side = (natoms / density) ** (1.0 / 3.0)
+        n = smooth_grid(int(math.ceil((side + 2.0 * radius + 1.0) / h)))
+        k = int(rng.integers(1, k_max + 1))
+        out.append((Recipe(natoms=natoms, cell_ang=n * h, ngrid=n, nphi=4, nchi=4, radius_ang=radius,
+                           cluster_ang=side, seed=1000 * seed + i), k))
+    return out
 
 
 def initial_guess(sys: System, k: int, seed: int):

@@ -26,10 +26,10 @@ def tddft():
     return td
 
 
-RECIPES = [sy.Recipe(natoms=2, cell_ang=9.0, ngrid=27, radius_ang=4.0, seed=31),
+RECIPES = [sy.Recipe(natoms=2, cell_ang=10.0, ngrid=30, radius_ang=4.0, seed=31),
            sy.Recipe(natoms=3, cell_ang=10.0, ngrid=30, radius_ang=4.0, seed=32),
            sy.Recipe(natoms=4, cell_ang=11.0, ngrid=32, radius_ang=4.0, seed=33),
-           sy.Recipe(natoms=3, cell_ang=10.0, ngrid=36, radius_ang=4.5, seed=34)]
+           sy.Recipe(natoms=3, cell_ang=11.0, ngrid=36, radius_ang=4.5, seed=34)]
 KS = [1, 2, 3, 2]
 
 
