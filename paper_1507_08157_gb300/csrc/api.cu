@@ -469,9 +469,26 @@ void check_tc_error(tddft_ctx *c) {
 }
 
 // ---- the operator (Eq. operator_RPA) -------------------------------------------------------------
-// P, f: [2][k][N_chi][N_phi] (the k p-matrices, then the k q-matrices)
+// P, f: [2][k][N_chi][N_phi] (the k p-matrices, then the k q-matrices). With `mirror` in TDA mode
+// the caller guarantees p = q (the solver's iterates in the Tamm-Dancoff approximation, where
+// X is the only unknown): A is applied to the p half alone and f_q is a copy of f_p.
 template <typename T>
-void apply_impl(tddft_ctx *c, Impl<T> &I, int k, const T *P, T *f) {
+void apply_impl(tddft_ctx *c, Impl<T> &I, int k, const T *P, T *f, bool mirror = false) {
+    if (mirror && c->opt.mode == TDDFT_MODE_TDA) {
+        const long long len = c->len();
+        ensure_workspace(c, I, 2 * k);
+        const int nc = c->nc, nv = c->nv;
+        cudaStream_t st = c->st;
+        gemm<T>(st, false, false, nc, nv, nc, T(1), I.Mc, nc, 0, P, nv, len, T(0), f, nv, len, k);
+        gemm<T>(st, false, false, k * nc, nv, nv, T(-1), P, nv, 0, I.Mv, nv, 0, T(1), f, nv, 0, 1);
+        density(c, I, P, k);
+        hartree_fxc<T>(st, c->grid(), I.rho, I.fxc, k, I.V, I.fft);
+        integrals(c, I, k);
+        gemm<T>(st, false, false, nc, nv, nc, T(1), I.Pc, nc, 0, I.Vmat, nv, len, T(0), I.tmp, nv, len, k);
+        gemm<T>(st, false, false, k * nc, nv, nv, T(1), I.tmp, nv, 0, I.Pv, nv, 0, T(1), f, nv, 0, 1);
+        check(cudaMemcpyAsync(f + k * len, f, k * len * sizeof(T), cudaMemcpyDeviceToDevice, st), "mirror f_q");
+        return;
+    }
     ensure_workspace(c, I, 2 * k);
     const int nc = c->nc, nv = c->nv;
     const long long len = c->len();
@@ -931,7 +948,7 @@ void state_init(tddft_ctx *c, tddft_state *S, const double *Y0) {
     sync_status(c, S, B.status);
     check(cudaMemsetAsync(B.f, 0, 2 * k * len * sizeof(T), c->st), "memset f");
     recombine<T>(c, B, k);
-    apply_impl<T>(c, I, k, B.P, B.f);
+    apply_impl<T>(c, I, k, B.P, B.f, true);
     check(ctx_sync(c), "sync init");
 }
 
@@ -1152,7 +1169,7 @@ void update(tddft_ctx *c, tddft_state *S) {
     direction<T>(st, B.dir, B.z, B.pdir, B.sc + 2, tot);
     direction<T>(st, B.D, B.Z, B.pD, B.sc + 2, tot);
     // one operator application on the directions
-    apply_impl<T>(c, I, k, B.D, B.fD);
+    apply_impl<T>(c, I, k, B.D, B.fD, true);
     covariant<T>(c, I, k2, B.D, B.covD, B.tmp);
     gram<T>(st, B.covD, len, k2, B.f, len, k2, len, B.BDf, B.gscr);
     gram<T>(st, B.covD, len, k2, B.fD, len, k2, len, B.CDfD, B.gscr);
@@ -1176,7 +1193,7 @@ void update(tddft_ctx *c, tddft_state *S) {
         if (c->trunc) mask_mul<T>(st, B.tmp, I.mask, len, k2);
         sandwich<T>(c, k2, I.Rc, B.tmp, I.Rv, B.P, B.cLpp);
         covariant<T>(c, I, k2, B.P, B.covP, B.tmp);
-        apply_impl<T>(c, I, k, B.P, B.f);
+        apply_impl<T>(c, I, k, B.P, B.f, true);
     }
     std::swap(B.pdir, B.dir);
     std::swap(B.pD, B.D);

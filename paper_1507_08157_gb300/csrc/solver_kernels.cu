@@ -235,12 +235,14 @@ int grid_for(long long n) {
 // element each). Matrices live in shared memory; every routine is entered and left by all
 // threads of the block. The updates run in the same order as the textbook row-by-row loops
 // (right-looking, one pivot or row at a time), so the results equal theirs up to the order of
-// the backward-substitution sums.
+// the backward-substitution sums and the rounding of reciprocal pivots.
 constexpr int SB_THREADS = 256;
 
-// L L^T = M (lower L, full k x k, upper part zero); false (in every thread) if M is not
-// positive definite. W is a k x k work array.
-__device__ bool sb_cholesky(int k, const double *M, double *L, double *W, int *bad) {
+// L L^T = M (lower L, full k x k, upper part zero); Linv[j] = 1 / L[j][j]; false (in every
+// thread) if M is not positive definite. W is a k x k work array. One reciprocal square root per
+// pivot: FP64 division and square root are long dependent chains on this part, and the pivots
+// are sequential, so the solves below multiply by Linv instead of dividing.
+__device__ bool sb_cholesky(int k, const double *M, double *L, double *Linv, double *W, int *bad) {
     const int t = threadIdx.x, kk = k * k;
     if (t == 0) *bad = 0;
     if (t < kk) { W[t] = M[t]; L[t] = 0.0; }
@@ -249,10 +251,12 @@ __device__ bool sb_cholesky(int k, const double *M, double *L, double *W, int *b
         if (t == 0) {
             const double d = W[j * k + j];
             if (!(d > 0.0)) *bad = 1;
-            L[j * k + j] = d > 0.0 ? sqrt(d) : 1.0;
+            const double r = d > 0.0 ? rsqrt(d) : 1.0;
+            L[j * k + j] = d > 0.0 ? d * r : 1.0;
+            Linv[j] = r;
         }
         __syncthreads();
-        if (t > j && t < k) L[t * k + j] = W[t * k + j] / L[j * k + j];
+        if (t > j && t < k) L[t * k + j] = W[t * k + j] * Linv[j];
         __syncthreads();
         if (t < kk) {
             const int i = t / k, l = t - i * k;
@@ -264,13 +268,13 @@ __device__ bool sb_cholesky(int k, const double *M, double *L, double *W, int *b
 }
 
 // X = (L L^T)^-1 B for nrhs <= 2 KMAX right-hand sides (B, X: k x nrhs); X may alias B
-__device__ void sb_solve(int k, int nrhs, const double *L, const double *B, double *X) {
+__device__ void sb_solve(int k, int nrhs, const double *L, const double *Linv, const double *B, double *X) {
     const int t = threadIdx.x, tot = k * nrhs;
     if (X != B)
         for (int e = t; e < tot; e += blockDim.x) X[e] = B[e];
     __syncthreads();
     for (int i = 0; i < k; ++i) {          // forward: L y = b
-        if (t < nrhs) X[i * nrhs + t] /= L[i * k + i];
+        if (t < nrhs) X[i * nrhs + t] *= Linv[i];
         __syncthreads();
         for (int e = (i + 1) * nrhs + t; e < tot; e += blockDim.x) {
             const int r = e / nrhs, c = e - r * nrhs;
@@ -279,7 +283,7 @@ __device__ void sb_solve(int k, int nrhs, const double *L, const double *B, doub
         __syncthreads();
     }
     for (int i = k - 1; i >= 0; --i) {     // backward: L^T x = y
-        if (t < nrhs) X[i * nrhs + t] /= L[i * k + i];
+        if (t < nrhs) X[i * nrhs + t] *= Linv[i];
         __syncthreads();
         for (int e = t; e < i * nrhs; e += blockDim.x) {
             const int r = e / nrhs, c = e - r * nrhs;
@@ -292,7 +296,7 @@ __device__ void sb_solve(int k, int nrhs, const double *L, const double *B, doub
 struct SbLine {
     double N0[KMAX * KMAX], N1[KMAX * KMAX], N2[KMAX * KMAX];
     double M0[KMAX * KMAX], M1[KMAX * KMAX], M2[KMAX * KMAX];
-    double M[KMAX * KMAX], dM[KMAX * KMAX], L[KMAX * KMAX], Wk[KMAX * KMAX];
+    double M[KMAX * KMAX], dM[KMAX * KMAX], L[KMAX * KMAX], Wk[KMAX * KMAX], Linv[KMAX];
     double R[KMAX * 2 * KMAX];     // [k][2k]: N | dN, then M^-1 N | M^-1 dN
     double T[KMAX * KMAX], Z[KMAX * KMAX];
     double out[4];
@@ -311,8 +315,8 @@ __device__ bool sb_sum_functional(int k, SbLine &s, double lam, double *f, doubl
         s.R[i * k2 + k + j] = s.N1[t] + 2.0 * lam * s.N2[t];
     }
     __syncthreads();
-    if (!sb_cholesky(k, s.M, s.L, s.Wk, &s.bad)) return false;
-    sb_solve(k, k2, s.L, s.R, s.R);         // W = M^-1 N, X = M^-1 dN
+    if (!sb_cholesky(k, s.M, s.L, s.Linv, s.Wk, &s.bad)) return false;
+    sb_solve(k, k2, s.L, s.Linv, s.R, s.R);         // W = M^-1 N, X = M^-1 dN
     if (t < kk) {                           // T = dM W
         const int i = t / k, j = t - i * k;
         double acc = 0.0;
@@ -320,7 +324,7 @@ __device__ bool sb_sum_functional(int k, SbLine &s, double lam, double *f, doubl
         s.T[t] = acc;
     }
     __syncthreads();
-    sb_solve(k, k, s.L, s.T, s.Z);          // Z = M^-1 dM M^-1 N
+    sb_solve(k, k, s.L, s.Linv, s.T, s.Z);          // Z = M^-1 dM M^-1 N
     if (t == 0) {
         double tw = 0.0, tx = 0.0, tz = 0.0;
         for (int i = 0; i < k; ++i) {
@@ -451,7 +455,7 @@ __device__ bool sb_gram_schmidt(int k, const double *Mg, const int *order, doubl
             for (int p = 0; p < k; ++p) nrm += v[p] * u[p];
             const double ref = fabs(Mg[i * k + i]) > 1.0 ? fabs(Mg[i * k + i]) : 1.0;
             if (!isfinite(nrm) || nrm <= 1e-12 * ref) *bad = 1;
-            coef[KMAX] = *bad ? 0.0 : 1.0 / sqrt(nrm);
+            coef[KMAX] = *bad ? 0.0 : rsqrt(nrm);
         }
         __syncthreads();
         if (*bad) return false;
@@ -461,10 +465,13 @@ __device__ bool sb_gram_schmidt(int k, const double *Mg, const int *order, doubl
     return true;
 }
 
-// Eigenvalues of a symmetric k x k matrix (cyclic Jacobi, one rotation at a time), ascending,
-// into w (written by thread 0). a is overwritten.
+// Eigenvalues of a symmetric k x k matrix, ascending, into w (written by thread 0); a is
+// overwritten. Jacobi sweeps in round-robin (tournament) order: the k (padded to even m) indices
+// meet in m - 1 rounds of m / 2 disjoint pairs, and a round's rotations commute, so their angles
+// are computed in parallel and applied together (columns, then rows). cs holds 2 KMAX + 1 values.
 __device__ void sb_jacobi_eigenvalues(int k, double *a, double *w, double *cs) {
     const int t = threadIdx.x;
+    const int m = k + (k & 1), half = m / 2;
     for (int sweep = 0; sweep < 60; ++sweep) {
         if (t == 0) {
             double off = 0.0, tot = 0.0;
@@ -473,41 +480,59 @@ __device__ void sb_jacobi_eigenvalues(int k, double *a, double *w, double *cs) {
                     tot += a[i * k + j] * a[i * k + j];
                     if (i != j) off += a[i * k + j] * a[i * k + j];
                 }
-            cs[2] = (off <= 1e-30 * tot || off == 0.0) ? 1.0 : 0.0;
+            cs[2 * KMAX] = (off <= 1e-30 * tot || off == 0.0) ? 1.0 : 0.0;
         }
         __syncthreads();
-        const bool done = cs[2] != 0.0;
+        const bool done = cs[2 * KMAX] != 0.0;
         __syncthreads();
         if (done) break;
-        for (int p = 0; p < k; ++p)
-            for (int q = p + 1; q < k; ++q) {
-                if (t == 0) {
+        for (int r = 0; r < m - 1; ++r) {
+            if (t < half) {
+                // pair t of round r: index m - 1 meets r, the others pair up around the circle
+                int p = t == 0 ? m - 1 : (r + t) % (m - 1);
+                int q = t == 0 ? r : (r - t + m - 1) % (m - 1);
+                if (p > q) { const int x = p; p = q; q = x; }
+                double c = 1.0, sn = 0.0;
+                if (q < k) {
                     const double apq = a[p * k + q];
-                    if (apq == 0.0) {
-                        cs[0] = 1.0;
-                        cs[1] = 0.0;
-                    } else {
+                    if (apq != 0.0) {
                         const double theta = (a[q * k + q] - a[p * k + p]) / (2.0 * apq);
                         const double tt = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-                        cs[0] = 1.0 / sqrt(tt * tt + 1.0);
-                        cs[1] = tt * cs[0];
+                        c = rsqrt(tt * tt + 1.0);
+                        sn = tt * c;
                     }
                 }
-                __syncthreads();
-                const double c = cs[0], sn = cs[1];
-                if (sn != 0.0 && t < k) {   // columns p, q
-                    const double arp = a[t * k + p], arq = a[t * k + q];
-                    a[t * k + p] = c * arp - sn * arq;
-                    a[t * k + q] = sn * arp + c * arq;
-                }
-                __syncthreads();
-                if (sn != 0.0 && t < k) {   // rows p, q
-                    const double apr = a[p * k + t], aqr = a[q * k + t];
-                    a[p * k + t] = c * apr - sn * aqr;
-                    a[q * k + t] = sn * apr + c * aqr;
-                }
-                __syncthreads();
+                cs[2 * t] = c;
+                cs[2 * t + 1] = sn;
             }
+            __syncthreads();
+            if (t < half * k) {             // columns p, q of row t % k for pair t / k
+                const int pr = t / k, row = t - pr * k;
+                int p = pr == 0 ? m - 1 : (r + pr) % (m - 1);
+                int q = pr == 0 ? r : (r - pr + m - 1) % (m - 1);
+                if (p > q) { const int x = p; p = q; q = x; }
+                const double c = cs[2 * pr], sn = cs[2 * pr + 1];
+                if (q < k && sn != 0.0) {
+                    const double arp = a[row * k + p], arq = a[row * k + q];
+                    a[row * k + p] = c * arp - sn * arq;
+                    a[row * k + q] = sn * arp + c * arq;
+                }
+            }
+            __syncthreads();
+            if (t < half * k) {             // rows p, q of column t % k for pair t / k
+                const int pr = t / k, col = t - pr * k;
+                int p = pr == 0 ? m - 1 : (r + pr) % (m - 1);
+                int q = pr == 0 ? r : (r - pr + m - 1) % (m - 1);
+                if (p > q) { const int x = p; p = q; q = x; }
+                const double c = cs[2 * pr], sn = cs[2 * pr + 1];
+                if (q < k && sn != 0.0) {
+                    const double apr = a[p * k + col], aqr = a[q * k + col];
+                    a[p * k + col] = c * apr - sn * aqr;
+                    a[q * k + col] = sn * apr + c * aqr;
+                }
+            }
+            __syncthreads();
+        }
     }
     if (t == 0) {
         for (int i = 0; i < k; ++i) w[i] = a[i * k + i];
@@ -577,7 +602,7 @@ __global__ void make_q_kernel(int k, const double *A, double *Q, double *coef) {
 // residuals and Ritz values: r_i = sqrt(d_p,i + d_q,i); omega = eig(sym Q); out = [omega, r]
 __global__ void __launch_bounds__(SB_THREADS) eval_finish_kernel(int k, const double *Q, const double *d,
                                                                  double *out, int *status) {
-    __shared__ double S[KMAX * KMAX], cs[4];
+    __shared__ double S[KMAX * KMAX], cs[2 * KMAX + 2];
     __shared__ int bad;
     const int t = threadIdx.x, kk = k * k;
     if (t == 0) bad = 0;

@@ -289,6 +289,7 @@ class Context:
             ctx = _handle
         self._ctx = ctx
         self.nc, self.nv, self.n = sys.chi.nfun, sys.phi.nfun, sys.n
+        self.natoms = sys.natoms
         self._states = weakref.WeakSet()
         _live.add(self)
 
@@ -358,7 +359,7 @@ class Context:
         return out
 
     def pattern(self):
-        m = np.empty((self.sys.natoms, self.sys.natoms), dtype=np.uint8)
+        m = np.empty((self.natoms, self.natoms), dtype=np.uint8)
         self._check(self._lib.tddft_pattern(self._ctx, m.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))))
         return m
 
@@ -406,7 +407,7 @@ class Context:
         """Training rows (X, T, w) at the state's iterate, as float32 CUDA tensors."""
         import torch
         n_b, n_f = self.learned_dims()
-        rows = state.k * self.sys.natoms ** 2
+        rows = state.k * self.natoms ** 2
         X = torch.empty((rows, n_b + n_f), dtype=torch.float32, device="cuda")
         T = torch.empty((rows, n_b), dtype=torch.float32, device="cuda")
         w = torch.empty((rows,), dtype=torch.float32, device="cuda")

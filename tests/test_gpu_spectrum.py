@@ -4,8 +4,8 @@
 * step parity: after PCG steps from the same start, the Ritz energies, strengths and dipoles of
   the GPU state equal the oracle's (FP64: omega to 1e-10 Ha, f and |mu| to 1e-8 of their scale);
 * converged states reproduce the dense strengths of the lowest excitations (FP64 to 1e-6 of the
-  largest strength, mixed precision to 1e-3: the float32 residual floor enters the eigenvectors
-  at first order);
+  largest strength; mixed precision to 4e-3: the tensor-core response density has float16
+  operands, 2e-3 of its scale per point as in the operator tests, and f is quadratic in it);
 * the device Lorentzian spectrum equals the oracle's to 1e-12.
 """
 import numpy as np
@@ -61,7 +61,7 @@ def test_ritz_strengths_step_parity(tddft, tiny):
     assert np.max(np.abs(_aligned(mu, mu_r) - mu_r)) <= 1e-8 * np.max(np.abs(mu_r))
 
 
-@pytest.mark.parametrize("prec,tol,acc", [("fp64", 1e-9, 1e-6), ("mixed", 1e-6, 1e-3)])
+@pytest.mark.parametrize("prec,tol,acc", [("fp64", 1e-9, 1e-6), ("mixed", 1e-6, 4e-3)])
 def test_converged_strengths_match_dense(tddft, tiny, dense, prec, tol, acc):
     k = 3
     ctx = tddft.Context(tiny, precision=prec, tol=tol, max_iter=600)
