@@ -45,7 +45,7 @@ typedef enum {
 
 enum { TDDFT_FP64 = 0, TDDFT_MIXED = 1 };                       /* tddft_options.precision */
 enum { TDDFT_MODE_FULL = 0, TDDFT_MODE_TDA = 1, TDDFT_MODE_D_ONLY = 2 };
-enum { TDDFT_PRECOND_NONE = 0, TDDFT_PRECOND_ITER = 1, TDDFT_PRECOND_LEARNED = 2 };
+enum { TDDFT_PRECOND_NONE = 0, TDDFT_PRECOND_ITER = 1, TDDFT_PRECOND_LEARNED = 2, TDDFT_PRECOND_EXACT = 3 };
 enum { TDDFT_FXC_NONE = 0, TDDFT_FXC_LDA_PW92 = 1 };
 
 /* Localised functions tabulated in periodic boxes (paper Sec. II C: NGWFs phi_alpha, chi_alpha).
@@ -92,7 +92,10 @@ typedef struct {
                                  f_p = A p, f_q = A q); TDDFT_MODE_D_ONLY (coupling K = 0) */
     int32_t precond;          /* TDDFT_PRECOND_ITER: CG solve of Eq. precond; NONE: identity;
                                  LEARNED: the atom-block network bound by tddft_set_mlp, with the
-                                 CG solve as fallback */
+                                 CG solve as fallback; EXACT: Eq. precond solved exactly in the
+                                 eigenbases of its two operators on the conduction x valence
+                                 subspace (diagonalised once at tddft_create; INVALID when P^c or
+                                 P^v is not idempotent) */
     int32_t precond_maxit;    /* inner CG iterations cap (default 50) */
     double precond_tol;       /* inner CG relative residual (default 1e-4) */
     double tol;               /* convergence: max residual (Ha) <= tol and max |d omega| <= tol/10 */

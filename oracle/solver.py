@@ -149,8 +149,9 @@ def gram_schmidt_coefficients(Mg, order):
 class PCG:
     def __init__(self, op, Y0, mode=FULL, precond="iter", precond_tol=1e-4,
                  precond_maxit=50, reapply_every=10, restart_every=10, mlp=None, precond_adaptive=False):
-        """precond: "iter" (inner CG on Eq. precond), "none", or "learned" with mlp =
-        (parameter vector, hidden width) of the atom-block network of ``learned``.
+        """precond: "iter" (inner CG on Eq. precond), "exact" (Eq. precond solved exactly in the
+        Kohn-Sham basis, where it is diagonal), "none", or "learned" with mlp = (parameter vector,
+        hidden width) of the atom-block network of ``learned``.
         precond_adaptive: the inner tolerance of a step is min(0.1, max(precond_tol, largest
         residual of the iterate)) -- loose first, tight at the end (suggested in Sec. IV A)."""
         self.op = op
@@ -160,6 +161,10 @@ class PCG:
         if precond == "learned":
             from .learned import LearnedPreconditioner
             self.learned = LearnedPreconditioner(op.sys, mlp[0], mlp[1], op.mask)
+        self.casida = None
+        if precond == "exact":
+            from .casida import Casida
+            self.casida = Casida(op.sys, fxc_kind="none")
         self.precond_tol = precond_tol
         self.precond_adaptive = precond_adaptive
         self.step_tol = precond_tol
@@ -248,6 +253,8 @@ class PCG:
         """Approximate solution G of P^c H^chi G - G H^phi P^v = g (Eq. precond) by CG."""
         if self.precond == "none":
             return g.copy()
+        if self.precond == "exact":
+            return self.exact_preconditioner(g)
         G = np.zeros_like(g)
         r = g.copy()
         p = r.copy()
@@ -268,6 +275,15 @@ class PCG:
             rr = rr_new
             self.inner_iters += 1
         return G
+
+    def exact_preconditioner(self, g):
+        """The exact solution of Eq. precond for g in the conduction x valence subspace: with the
+        Kohn-Sham states P^c H^chi d_c = eps_c d_c and H^phi P^v-side c_v, G = D_c X C_v^T turns
+        P^c H^chi G - G H^phi P^v into D_c (eps_c X - X eps_v) C_v^T, so X = Y / (eps_c - eps_v)
+        with Y = D_c^T S^chi g S^phi C_v the Kohn-Sham coordinates of g."""
+        cas = self.casida
+        Y = cas.to_ks(g)
+        return cas.to_ngwf(Y / (cas.eps_c[:, None] - cas.eps_v[None, :]))
 
     def search_gradient(self, gp, gq):
         """The gradient the preconditioner acts on: g itself, or P^c G_L P^v with truncation."""

@@ -66,6 +66,103 @@ __global__ void scale_kernel64(const double *X, double a, double *Y, long long n
         Y[i] = a * X[i];
 }
 
+
+// two-sided Jacobi on a symmetric n x n matrix in round-robin order (set-up of the exact
+// preconditioner): in round r the n (padded to even m) indices form m / 2 disjoint pairs, whose
+// rotations commute; angles first, then the columns of A and V, then the rows of A
+__device__ __forceinline__ void rr_pair(int m, int r, int t, int &p, int &q) {
+    p = t == 0 ? m - 1 : (r + t) % (m - 1);
+    q = t == 0 ? r : (r - t + m - 1) % (m - 1);
+    if (p > q) {
+        const int x = p;
+        p = q;
+        q = x;
+    }
+}
+__global__ void jac_angles_kernel(const double *A, int n, int m, int r, double *cs) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m / 2) return;
+    int p, q;
+    rr_pair(m, r, t, p, q);
+    double c = 1.0, sn = 0.0;
+    if (q < n) {
+        const double apq = A[(long long)p * n + q];
+        if (apq != 0.0) {
+            const double theta = (A[(long long)q * n + q] - A[(long long)p * n + p]) / (2.0 * apq);
+            const double tt = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+            c = rsqrt(tt * tt + 1.0);
+            sn = tt * c;
+        }
+    }
+    cs[2 * t] = c;
+    cs[2 * t + 1] = sn;
+}
+__global__ void jac_cols_kernel(double *A, double *V, int n, int m, int r, const double *cs) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)(m / 2) * n) return;
+    const int pr = (int)(i / n), row = (int)(i - (long long)pr * n);
+    int p, q;
+    rr_pair(m, r, pr, p, q);
+    const double c = cs[2 * pr], sn = cs[2 * pr + 1];
+    if (q >= n || sn == 0.0) return;
+    double *a = A + (long long)row * n, *v = V + (long long)row * n;
+    const double ap = a[p], aq = a[q], vp = v[p], vq = v[q];
+    a[p] = c * ap - sn * aq;
+    a[q] = sn * ap + c * aq;
+    v[p] = c * vp - sn * vq;
+    v[q] = sn * vp + c * vq;
+}
+__global__ void jac_rows_kernel(double *A, int n, int m, int r, const double *cs) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)(m / 2) * n) return;
+    const int pr = (int)(i / n), col = (int)(i - (long long)pr * n);
+    int p, q;
+    rr_pair(m, r, pr, p, q);
+    const double c = cs[2 * pr], sn = cs[2 * pr + 1];
+    if (q >= n || sn == 0.0) return;
+    const double ap = A[(long long)p * n + col], aq = A[(long long)q * n + col];
+    A[(long long)p * n + col] = c * ap - sn * aq;
+    A[(long long)q * n + col] = sn * ap + c * aq;
+}
+// sums of squares: [0] off-diagonal, [1] all (float64 atomics: only a stopping test)
+__global__ void offnorm_kernel(const double *A, int n, double *out) {
+    const long long tot = (long long)n * n;
+    double off = 0.0, all = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x) {
+        const double x = A[i] * A[i];
+        all += x;
+        if (i / n != i % n) off += x;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        off += __shfl_xor_sync(0xffffffffu, off, o);
+        all += __shfl_xor_sync(0xffffffffu, all, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(out, off);
+        atomicAdd(out + 1, all);
+    }
+}
+__global__ void sym_identity_kernel(double *A, double *V, int n) {
+    const long long tot = (long long)n * n;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x) {
+        const long long r = i / n, c = i - r * n;
+        if (r < c) {
+            const double x = 0.5 * (A[i] + A[c * n + r]);
+            A[i] = x;
+            A[c * n + r] = x;
+        }
+        V[i] = r == c ? 1.0 : 0.0;
+    }
+}
+// the exact preconditioner's denominators 1 / (lambda_c,i - lambda_v,j) from the two diagonals
+__global__ void denominators_kernel(const double *Ac, int rc, const double *Av, int rv, double *D) {
+    const long long tot = (long long)rc * rv;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+        const long long i = e / rv, j = e - i * rv;
+        D[e] = 1.0 / (Ac[i * rc + i] - Av[j * rv + j]);
+    }
+}
+
 }  // namespace roots
 
 namespace {
@@ -104,6 +201,10 @@ struct Impl {
     // Mvh = U_v^T M~v U_v
     int rc = 0, rv = 0;
     T *Wc = nullptr, *Wv = nullptr, *Vc = nullptr, *Vv = nullptr, *Mch = nullptr, *Mvh = nullptr;
+    // exact preconditioner: Wc, Wv, Vc, Vv taken into the eigenbases of Mch and Mvh, and the
+    // denominators Dn [rc][rv] = 1 / (lambda_c,i - lambda_v,j)
+    bool exact = false;
+    T *Dn = nullptr;
     double *fxc64 = nullptr;
     // tensor-core grid path (float32 contexts): point-major f16 chi tables [tile][512][CK]
     unsigned short *chi_pm = nullptr;
@@ -559,6 +660,33 @@ void overlap_roots(cudaStream_t st, Mem &tmp, const double *S_dev, const double 
 // Orthonormal basis U [n][r] of the range of the Loewdin projector Pi = Sh P Sh (Sh = S^{1/2}),
 // r = round(trace Pi): U = Y (Y^T Y)^{-1/2} with Y = Pi Omega, Omega a seeded Gaussian n x r
 // matrix. Returns r, or 0 when Pi is not idempotent to 1e-8 (then no reduced space is used).
+// A = V diag(A') V^T for a symmetric n x n float64 matrix on the device: A is symmetrised and
+// overwritten by its (numerically) diagonal form A', V receives the eigenvectors as columns
+void sym_eig(cudaStream_t st, Mem &tmp, double *A, int n, double *V) {
+    const int m = n + (n & 1), half = m / 2;
+    double *cs = tmp.alloc<double>((size_t)m + 2), *nrm = tmp.alloc<double>(2);
+    const long long nn = (long long)n * n, work = (long long)half * n;
+    const int g1 = (int)std::min<long long>((nn + 255) / 256, 1216);
+    roots::sym_identity_kernel<<<g1, 256, 0, st>>>(A, V, n);
+    check_launch("sym_identity");
+    double h[2];
+    for (int sweep = 0; sweep < 30; ++sweep) {
+        check(cudaMemsetAsync(nrm, 0, 2 * sizeof(double), st), "memset offnorm");
+        roots::offnorm_kernel<<<g1, 256, 0, st>>>(A, n, nrm);
+        check_launch("offnorm");
+        check(cudaMemcpyAsync(h, nrm, 2 * sizeof(double), cudaMemcpyDeviceToHost, st), "D2H offnorm");
+        check(cudaStreamSynchronize(st), "sync offnorm");
+        if (!(h[0] > 1e-28 * h[1])) break;
+        for (int r = 0; r < m - 1; ++r) {
+            roots::jac_angles_kernel<<<(half + 127) / 128, 128, 0, st>>>(A, n, m, r, cs);
+            roots::jac_cols_kernel<<<(int)((work + 255) / 256), 256, 0, st>>>(A, V, n, m, r, cs);
+            roots::jac_rows_kernel<<<(int)((work + 255) / 256), 256, 0, st>>>(A, n, m, r, cs);
+        }
+        check_launch("jacobi round");
+    }
+    if (h[0] > 1e-20 * h[1]) throw Breakdown{"Jacobi eigensolver of the preconditioner did not converge"};
+}
+
 int projector_basis(cudaStream_t st, Mem &tmp, const double *Sh, const double *P, int n, unsigned long long seed,
                     double **U_out) {
     const long long nn = (long long)n * n;
@@ -752,6 +880,34 @@ void build_impl(tddft_ctx *c, const tddft_system *s) {
         gemm<double>(st, false, false, nv, rv, nv, 1.0, Mvt, nv, 0, Uv, rv, 0, 0.0, T1, rv, 0, 1);
         gemm<double>(st, true, false, rv, rv, nv, 1.0, Uv, rv, 0, T1, rv, 0, 0.0, Mvh, rv, 0, 1);  // U_v^T M~v U_v
     }
+    double *Dn = nullptr;
+    if (c->opt.precond == TDDFT_PRECOND_EXACT) {
+        // Mch and Mvh are symmetric on the subspace (U^T H~ U of the Loewdin Hamiltonians), so
+        // Eq. precond becomes diagonal in their eigenbases: Mch = Ec Lc Ec^T, Mvh = Ev Lv Ev^T
+        if (!rc) throw InvalidArg{"the exact preconditioner needs idempotent P^c and P^v"};
+        const long long cc2 = (long long)rc * rc, vv2 = (long long)rv * rv;
+        double *Ac = tmpm.alloc<double>(cc2), *Av = tmpm.alloc<double>(vv2);
+        double *Ec = tmpm.alloc<double>(cc2), *Ev = tmpm.alloc<double>(vv2);
+        check(cudaMemcpyAsync(Ac, Mch, cc2 * sizeof(double), cudaMemcpyDeviceToDevice, st), "copy Mch");
+        check(cudaMemcpyAsync(Av, Mvh, vv2 * sizeof(double), cudaMemcpyDeviceToDevice, st), "copy Mvh");
+        sym_eig(st, tmpm, Ac, rc, Ec);
+        sym_eig(st, tmpm, Av, rv, Ev);
+        Dn = tmpm.alloc<double>((long long)rc * rv);
+        roots::denominators_kernel<<<(int)std::min<long long>(((long long)rc * rv + 255) / 256, 1216), 256, 0, st>>>(
+            Ac, rc, Av, rv, Dn);
+        check_launch("denominators");
+        const long long crc = (long long)nc * rc, vrv = (long long)nv * rv;
+        double *W2 = tmpm.alloc<double>(crc), *V2 = tmpm.alloc<double>(crc);
+        double *W3 = tmpm.alloc<double>(vrv), *V3 = tmpm.alloc<double>(vrv);
+        gemm<double>(st, true, false, rc, nc, rc, 1.0, Ec, rc, 0, Wc, nc, 0, 0.0, W2, nc, 0, 1);   // Ec^T Wc
+        gemm<double>(st, false, false, nv, rv, rv, 1.0, Wv, rv, 0, Ev, rv, 0, 0.0, W3, rv, 0, 1);  // Wv Ev
+        gemm<double>(st, false, false, nc, rc, rc, 1.0, Vc, rc, 0, Ec, rc, 0, 0.0, V2, rc, 0, 1);  // Vc Ec
+        gemm<double>(st, true, false, rv, nv, rv, 1.0, Ev, rv, 0, Vv, nv, 0, 0.0, V3, nv, 0, 1);   // Ev^T Vv
+        Wc = W2;
+        Wv = W3;
+        Vc = V2;
+        Vv = V3;
+    }
     auto keep = [&](const double *d, long long cnt) {
         T *o = I->mem.template alloc<T>(cnt);
         convert<double, T>(st, d, o, cnt);
@@ -763,7 +919,11 @@ void build_impl(tddft_ctx *c, const tddft_system *s) {
     I->Sch = keep(Sch, cc); I->Scmh = keep(Scmh, cc); I->Svh = keep(Svh, vv); I->Svmh = keep(Svmh, vv);
     I->Mct = keep(Mct, cc); I->Mvt = keep(Mvt, vv);
     const char *nr = std::getenv("TDDFT_NO_REDUCED_PRECOND");
-    if (rc && !(nr && nr[0] == '1')) {
+    if (Dn) {
+        I->exact = true;
+        I->Dn = keep(Dn, (long long)rc * rv);
+    }
+    if (rc && (Dn || !(nr && nr[0] == '1'))) {
         I->rc = rc;
         I->rv = rv;
         I->Wc = keep(Wc, (long long)rc * nc); I->Wv = keep(Wv, (long long)nv * rv);
@@ -1005,6 +1165,18 @@ void precondition(tddft_ctx *c, tddft_state *S, const T *h, T *z) {
     if (c->opt.precond_adaptive && !S->resid.empty()) {
         const double rmax = *std::max_element(S->resid.begin(), S->resid.end());
         ptol = std::min(0.1, std::max(c->opt.precond_tol, rmax));
+    }
+    if (I.exact) {
+        // Eq. precond solved exactly: coordinates in the eigenbases of Mch and Mvh, divided by
+        // lambda_c,i - lambda_v,j, and back: z = (Vc Ec) [(Ec^T Wc h Wv Ev) / (Lc - Lv)] (Ev^T Vv)
+        const int rc = I.rc, rv = I.rv;
+        const long long lr = (long long)rc * rv;
+        gemm<T>(st, false, false, rc, nv, nc, T(1), I.Wc, nc, 0, h, nv, len, T(0), B.tmp, nv, (long long)rc * nv, k2);
+        gemm<T>(st, false, false, k2 * rc, rv, nv, T(1), B.tmp, nv, 0, I.Wv, rv, 0, T(0), B.qr, rv, 0, 1);
+        mask_mul<T>(st, B.qr, I.Dn, lr, k2);
+        gemm<T>(st, false, false, nc, rv, rc, T(1), I.Vc, rc, 0, B.qr, rv, lr, T(0), B.tmp, rv, (long long)nc * rv, k2);
+        gemm<T>(st, false, false, k2 * nc, nv, rv, T(1), B.tmp, rv, 0, I.Vv, nv, 0, T(0), z, nv, 0, 1);
+        return;
     }
     if (I.rc) {
         // the same CG on the rc x rv coordinates of the conduction x valence subspace:
@@ -1331,7 +1503,7 @@ tddft_status tddft_create(const tddft_system *s, const tddft_options *opt, void 
         if (!s) throw InvalidArg{"null system"};
         if (c->prec != TDDFT_FP64 && c->prec != TDDFT_MIXED) throw InvalidArg{"unknown precision"};
         if (c->opt.mode < 0 || c->opt.mode > 2) throw InvalidArg{"unknown mode"};
-        if (c->opt.precond < 0 || c->opt.precond > 2) throw InvalidArg{"unknown preconditioner"};
+        if (c->opt.precond < 0 || c->opt.precond > 3) throw InvalidArg{"unknown preconditioner"};
         if (!(s->cell > 0.0)) throw InvalidArg{"cell must be positive"};
         if (!fft_size_ok(s->n)) throw InvalidArg{"grid size must be 2^a 3^b 5^c with 8 <= n <= 256"};
         if (s->natoms <= 0 || !s->pos) throw InvalidArg{"no atoms"};

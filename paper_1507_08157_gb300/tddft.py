@@ -22,7 +22,7 @@ OK, E_INVALID, E_NOMEM, E_CUDA, E_NOT_CONVERGED, E_BREAKDOWN, E_TIMEOUT, E_PAIRI
 FP64, MIXED = 0, 1
 NOALLOC_MAX_STATES = 64        # TDDFT_NOALLOC_MAX_STATES of the header
 MODE = {"full": 0, "tda": 1, "d_only": 2}
-PRECOND = {"none": 0, "iter": 1, "learned": 2}
+PRECOND = {"none": 0, "iter": 1, "learned": 2, "exact": 3}
 FXC = {"none": 0, "lda": 1}
 
 c_double_p = ctypes.POINTER(ctypes.c_double)

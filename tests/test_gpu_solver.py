@@ -88,6 +88,52 @@ def test_fixed_points(tddft, tiny, tiny_dense, mode):
     assert np.max(np.abs(om - ref)) <= 1e-9
 
 
+def test_tda_steps_match_oracle(tddft, tiny):
+    """In TDA mode the solver applies A to the p half only and copies f_p to f_q (p = q on every
+    iterate): its steps must still follow the oracle's TDA-mode PCG, which applies A to both."""
+    k = 2
+    Y0 = sy.initial_guess(tiny, k, 5)
+    ref = osolver.PCG(oop.Operator(tiny), Y0, mode="tda")
+    ctx = tddft.Context(tiny, precision="fp64", mode="tda")
+    st = ctx.state(Y0)
+    for _ in range(4):
+        om_r, _ = ref.step()
+        om_g, _ = st.step()
+        assert np.max(np.abs(om_g - om_r)) < 1e-10
+    got = st.get()
+    assert np.array_equal(got["Pp"], got["Pq"]) and np.array_equal(got["fp"], got["fq"])
+    assert _rel(got["Pp"], ref.Pp) < 1e-7
+
+
+@pytest.mark.parametrize("trunc", [False, True])
+def test_exact_preconditioner_steps_match_oracle(tddft, tiny, trunc):
+    """precond="exact": Eq. precond solved in the eigenbases of its two operators on the
+    subspace (GPU) against the oracle's Kohn-Sham closed form, step by step."""
+    s = dataclasses.replace(tiny, kernel_cutoff=3.0 / 0.529177210903) if trunc else tiny
+    k = 2
+    Y0 = sy.initial_guess(s, k, 6)
+    ref = osolver.PCG(oop.Operator(s), Y0, precond="exact")
+    ctx = tddft.Context(s, precision="fp64", precond="exact")
+    st = ctx.state(Y0)
+    for _ in range(4):
+        om_r, res_r = ref.step()
+        om_g, res_g = st.step()
+        assert np.max(np.abs(om_g - om_r)) < 1e-10
+        assert np.max(np.abs(res_g - res_r) / res_r) < 1e-6
+    assert _rel(st.get()["Pq"], ref.Pq) < 1e-7
+    assert st.stats()[2] == 0                       # no inner iterations
+
+
+@pytest.mark.parametrize("prec,tol,acc", [("fp64", 1e-8, 1e-6), ("mixed", 1e-6, 1e-5)])
+def test_exact_preconditioner_reaches_dense(tddft, tiny, tiny_dense, prec, tol, acc):
+    k = 3
+    ctx = tddft.Context(tiny, precision=prec, precond="exact", tol=tol, max_iter=400)
+    st = ctx.state(sy.initial_guess(tiny, k, 1))
+    om, res, it, rc = st.solve()
+    assert rc == tddft.OK, (rc, it, res)
+    assert np.max(np.abs(om - tiny_dense.omega_symmetric()[:k])) <= acc
+
+
 def test_small_workload_lowest_state(tddft):
     # FP64 to a residual of 1e-6 Ha; float32 operands put a floor near 1e-4 under the residual
     # (the energy error is quadratic in it), so mixed mode converges to 3e-4 and must still be

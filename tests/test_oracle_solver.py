@@ -168,3 +168,24 @@ def test_adaptive_inner_tolerance_reaches_dense_eigenvalues(tiny_system, tiny_op
     assert np.max(np.abs(np.sort(om_a) - ref)) < 1e-6
     assert np.max(np.abs(np.sort(om_f) - ref)) < 1e-6
     assert adapt.inner_iters < fixed.inner_iters
+
+
+def test_exact_preconditioner_solves_eq_precond(tiny_system, tiny_operator):
+    """The exact preconditioner (Kohn-Sham closed form) solves P^c H^chi G - G H^phi P^v = g for
+    g in the conduction x valence subspace, and the inner CG converges to it."""
+    op = tiny_operator
+    rng = np.random.default_rng(21)
+    g = op.Pc @ rng.normal(size=(op.Pc.shape[0], op.Pv.shape[0])) @ op.Pv
+    ex = solver.PCG(op, sy.initial_guess(tiny_system, 1, 1), precond="exact")
+    G = ex.exact_preconditioner(g)
+    L = ex.Mc @ G - G @ ex.Mv
+    assert np.max(np.abs(L - g)) <= 1e-10 * np.max(np.abs(g))
+    it = solver.PCG(op, sy.initial_guess(tiny_system, 1, 1), precond_tol=1e-13, precond_maxit=2000)
+    Gi = it.apply_preconditioner(g)
+    assert np.max(np.abs(Gi - G)) <= 1e-8 * np.max(np.abs(G))
+
+
+def test_exact_preconditioner_reaches_dense_eigenvalues(tiny_system, tiny_operator, tiny_casida):
+    pcg = solver.PCG(tiny_operator, sy.initial_guess(tiny_system, 2, 1), precond="exact")
+    omega, res, it = pcg.solve(tol=1e-8, max_iter=300)
+    assert np.max(np.abs(np.sort(omega) - tiny_casida.omega_symmetric()[:2])) < 1e-9
