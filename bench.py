@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--k", type=int, default=10)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--config", default="chromophore", choices=["chromophore", "small"])
+    ap.add_argument("--precond", default="iter", choices=["iter", "exact", "none"],
+                    help="preconditioner of the timed PCG steps (iter: the paper's inner CG)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-time-to-k", action="store_true",
                     help="skip the separate time-to-solution report (not part of the timed steps)")
@@ -222,7 +224,7 @@ def learned_vs_plain(tddft, sy, torch, stream, k=10, train_atoms=16, eval_atoms=
     s = sy.generate(c1_density_recipe(eval_atoms, 35))
     Y0 = sy.initial_guess(s, k, 35)
     out = {}
-    for pre in ("iter", "adaptive", "learned", "none"):
+    for pre in ("iter", "adaptive", "exact", "learned", "none"):
         c = tddft.Context(s, precision="fp64", precond="iter" if pre == "adaptive" else pre, tol=tol,
                           max_iter=1000, stream=stream.cuda_stream, precond_adaptive=pre == "adaptive")
         if pre == "learned":
@@ -249,8 +251,11 @@ def learned_vs_plain(tddft, sy, torch, stream, k=10, train_atoms=16, eval_atoms=
             "plain_adaptive_tol_inner_cg_iterations": out["adaptive"]["stats"][2],
             "learned_pcg_s": out["learned"]["s"], "learned_iterations": out["learned"]["iterations"],
             "learned_fallbacks": out["learned"]["stats"][1],
+            "exact_precond_s": out["exact"]["s"], "exact_precond_iterations": out["exact"]["iterations"],
             "unpreconditioned_s": out["none"]["s"], "unpreconditioned_iterations": out["none"]["iterations"],
-            "status": [out[p]["status"] for p in ("iter", "adaptive", "learned", "none")],
+            "status": [out[p]["status"] for p in ("iter", "adaptive", "exact", "learned", "none")],
+            "max_domega_exact_vs_plain_Ha": max(abs(a - b) for a, b in zip(out["exact"]["omega_Ha"],
+                                                                            out["iter"]["omega_Ha"])),
             "max_domega_learned_vs_plain_Ha": dw, "train_s": train_s, "train_loss": [l0, l1]}
 
 
@@ -269,7 +274,7 @@ def run_ours(args):
     tddft.load()
     s = sy.generate(recipe(args.config))
     stream = torch.cuda.current_stream()
-    ctx = tddft.Context(s, precision=args.precision, stream=stream.cuda_stream, tol=1e-5)
+    ctx = tddft.Context(s, precision=args.precision, stream=stream.cuda_stream, tol=1e-5, precond=args.precond)
     k = args.k
     st = ctx.state(sy.initial_guess(s, k, 0))
     for _ in range(args.warmup):
@@ -381,6 +386,7 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
                 "config": {"workload": workload_name(args), "states": k, "precision": args.precision,
+                           "precond": args.precond,
                            "parallelism": f"replicas{world}" if world > 1 else "single",
                            "l2": "inputs larger than L2 (function tables > 1 GB per pass)",
                            "applies_per_step": applies / args.steps},

@@ -271,6 +271,7 @@ namespace tddft {
 bool tc_enabled();
 int *tc_error_word();
 void tc_error_fetch(cudaStream_t st, int *host);
+void tc_release_stream(cudaStream_t st);
 void tc_error_clear(cudaStream_t st);
 void build_point_major_f16(const int *off_h, const float *val_h_or_null, const double *vald_h_or_null,
                            int ntiles, int CK, unsigned short *out_h);
@@ -320,7 +321,10 @@ tddft_ctx::~tddft_ctx() {
     d32.reset();
     if (sync_ev) cudaEventDestroy(sync_ev);
     if (hword) cudaFreeHost(hword);
-    if (own_stream && st) cudaStreamDestroy(st);
+    if (own_stream && st) {
+        tc_release_stream(st);
+        cudaStreamDestroy(st);
+    }
 }
 
 namespace {

@@ -441,13 +441,15 @@ __global__ void transpose_split_kernel(const float *__restrict__ in, int rows, i
     }
 }
 
-// process-wide scratch for the split operands (grown on demand, never shrunk)
+// scratch for the split operands, one buffer per stream (grown on demand, never shrunk): work on
+// one stream runs in order, so its products may share a buffer, while products on different
+// streams (the contexts of a batch) run concurrently and must not
 struct Scratch {
     float *p = nullptr;
     size_t cap = 0;
     float *get(size_t n) {
         if (n > cap) {
-            if (p) cudaFree(p);
+            if (p) cudaFree(p);   // synchronises the device: earlier users of the buffer are done
             p = nullptr;
             check(cudaMalloc(&p, n * sizeof(float)), "cudaMalloc tc scratch");
             cap = n;
@@ -455,9 +457,14 @@ struct Scratch {
         return p;
     }
 };
-Scratch &scratch() {
-    static Scratch s;
-    return s;
+std::mutex g_scratch_mu;
+std::vector<std::pair<cudaStream_t, Scratch *>> g_scratch;
+Scratch &scratch(cudaStream_t st) {
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    for (auto &e : g_scratch)
+        if (e.first == st) return *e.second;
+    g_scratch.push_back({st, new Scratch});
+    return *g_scratch.back().second;
 }
 
 int grid1(long long n) {
@@ -551,7 +558,7 @@ void tc_gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, float alpha
     const int nsp = split ? 2 : 1;                      // copies carry hi and lo when splitting
     auto up64 = [](size_t n) { return (n + 63) / 64 * 64; };
     const size_t na = a_copy ? up64((size_t)M * Kp * bA) : 0, nbt = b_copy ? up64((size_t)N * Kp * bB) : 0;
-    float *base = (na + nbt) ? scratch().get(nsp * (na + nbt)) : nullptr;
+    float *base = (na + nbt) ? scratch(st).get(nsp * (na + nbt)) : nullptr;
     const float *Ak = A, *Alo = nullptr, *Bk = B, *Blo = nullptr;
     int lak = lda, lbk = ldb;
     long long sak = sA, sbk = sB;
@@ -606,5 +613,18 @@ void tc_error_fetch(cudaStream_t st, int *host) {
 }
 
 void tc_error_clear(cudaStream_t st) { check(cudaMemsetAsync(error_word(), 0, sizeof(int), st), "clear tc error"); }
+
+
+// free the split scratch of a stream that is about to be destroyed (its work has completed)
+void tc_release_stream(cudaStream_t st) {
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    for (size_t i = 0; i < g_scratch.size(); ++i)
+        if (g_scratch[i].first == st) {
+            if (g_scratch[i].second->p) cudaFree(g_scratch[i].second->p);
+            delete g_scratch[i].second;
+            g_scratch.erase(g_scratch.begin() + (long)i);
+            return;
+        }
+}
 
 }  // namespace tddft
