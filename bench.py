@@ -458,7 +458,7 @@ def run_batched(args):
             t0 = time.perf_counter()
             systems = pool.map(_generate, [recs[i][0] for i in chunk])
             t1 = time.perf_counter()
-            cs = tddft.create_batch(systems, precision="mixed", tol=tol, max_iter=400)
+            cs = tddft.create_batch(systems, precision="mixed", tol=tol, max_iter=400, precond=args.precond)
             for i, c, sys_ in zip(chunk, cs, systems):
                 k = recs[i][1]
                 states.append(c.state(sy.initial_guess(sys_, k, i)))
@@ -486,7 +486,8 @@ def run_batched(args):
             "config": {"workload": f"batched: {len(states)} systems, {min(m[1] for m in meta)}-"
                                    f"{max(m[1] for m in meta)} atoms (log-uniform, seed {args.batch_seed}), "
                                    "0.1 atoms/A^3 cube + 2R + 1 A vacuum, 0.25 A grid, 4 phi + 4 chi per atom, "
-                                   "7 A radius, 1-8 states, mixed precision, residual 3e-4 Ha",
+                                   f"7 A radius, 1-8 states, mixed precision, {args.precond} preconditioner, "
+                                   "residual 3e-4 Ha",
                        "systems": len(states), "atoms_total": int(sum(m[1] for m in meta)),
                        "states_total": int(sum(m[2] for m in meta)), "host_threads": 16},
             "wall_s": wall, "converged": ok, "iters_total": int(np.sum(iters)),

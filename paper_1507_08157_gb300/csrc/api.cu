@@ -209,7 +209,8 @@ struct Impl {
     // tensor-core grid path (float32 contexts): point-major f16 chi tables [tile][512][CK]
     unsigned short *chi_pm = nullptr;
     unsigned short *chi_fm16 = nullptr;   // function-major f16 chi tables [slot][512]
-    int CK = 0, NPmax = 0, nslots_chi = 0, maxc = 0;
+    unsigned short *phi_fm16 = nullptr;   // function-major f16 phi tables [slot][512]
+    int CK = 0, NPmax = 0, nslots_chi = 0, nslots_phi = 0, maxc = 0;
     bool grid_tc = false, integrals_tc = false;
     bool phi_quads = false;   // every tile's phi list is whole aligned groups of 4 (vector gather)
     // integrals launches: tiles holding chi and phi, grouped by 128-row chi blocks (1, 2, 3)
@@ -278,7 +279,8 @@ void build_point_major_f16(const int *off_h, const float *val_h_or_null, const d
 int density_tc_group(int KBmax, int NP, int k);
 int integrals_tc_group(int NP, int k, int maxc);
 void potential_integrals_tc(cudaStream_t st, const GridShape &g, const TileSet<float> &chi,
-                            const TileSet<float> &phi, const unsigned short *chi_fm16, int nslots, int NPmax,
+                            const TileSet<float> &phi, const unsigned short *chi_fm16, int nslots,
+                            const unsigned short *phi_fm16, int nslots_phi, int NPmax,
                             int maxc, int nchi, int nphi, const float *V, int k, float *out, unsigned *scratch_bits,
                             float *scale, const int *tile_list, const int *tiles_by_blocks, int *err);
 void response_density_tc(cudaStream_t st, const GridShape &g, const TileSet<float> &chi,
@@ -554,7 +556,8 @@ template <typename T>
 void integrals(tddft_ctx *c, Impl<T> &I, int ns) {
     if constexpr (sizeof(T) == 4) {
         if (I.integrals_tc) {
-            potential_integrals_tc(c->st, c->grid(), I.chi, I.phi, I.chi_fm16, I.nslots_chi, I.NPmax, I.maxc, c->nc,
+            potential_integrals_tc(c->st, c->grid(), I.chi, I.phi, I.chi_fm16, I.nslots_chi, I.phi_fm16, I.nslots_phi,
+                                   I.NPmax, I.maxc, c->nc,
                                    c->nv, I.V, ns, I.Vmat, I.tc_bits, I.tc_scale, I.int_tiles, I.int_count,
                                    tc_error_word());
             return;
@@ -807,6 +810,21 @@ void build_impl(tddft_ctx *c, const tddft_system *s) {
                                      cudaMemcpyHostToDevice),
                           "upload f16 chi");
                     I->nslots_chi = coff[ntl];
+                    {
+                        // f16 phi tables for the integrals' B operand (TMA-loaded, scaled by V in place)
+                        std::vector<float> pv((size_t)poff[ntl] * TILE_PTS);
+                        check(cudaMemcpy(pv.data(), I->phi.val, pv.size() * sizeof(float), cudaMemcpyDeviceToHost),
+                              "D2H phi tables");
+                        std::vector<unsigned short> ph(pv.size());
+#pragma omp parallel for schedule(static)
+                        for (long long i = 0; i < (long long)pv.size(); ++i)
+                            ph[i] = __half_as_ushort(__float2half_rn(pv[i]));
+                        I->phi_fm16 = I->mem.template alloc<unsigned short>(std::max<size_t>(1, ph.size()));
+                        check(cudaMemcpy(I->phi_fm16, ph.data(), ph.size() * sizeof(unsigned short),
+                                         cudaMemcpyHostToDevice),
+                              "upload f16 phi");
+                        I->nslots_phi = poff[ntl];
+                    }
                     std::vector<int> by[3];
                     for (int t = 0; t < ntl; ++t) {
                         const int nct = coff[t + 1] - coff[t], npt = poff[t + 1] - poff[t];

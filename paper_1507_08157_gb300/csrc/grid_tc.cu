@@ -421,8 +421,7 @@ struct __align__(8) IntShared {
     unsigned long long acc_done;
     unsigned int tmem_base;
     int abort;
-    int pid[256];      // the tile's phi indices (np <= NP <= 256)
-    float vsc[16];     // scales of the group's states
+    int pid[256];      // the tile's phi indices (np <= NP <= 128)
 };
 
 __device__ __forceinline__ void red_add_v4(float *addr, float a, float b, float c, float d) {
@@ -430,32 +429,35 @@ __device__ __forceinline__ void red_add_v4(float *addr, float a, float b, float 
                  : "memory");
 }
 
-// CTA = (state group, tile of the launch's list); mbmax: most chi row blocks of a listed tile
-// (sizes the X stages), tmem_cols: TMEM columns allocated (mbmax * acc_stride, a power of two)
+// CTA = (state, tile of the launch's list); mbmax: most chi row blocks of a listed tile (sizes the
+// X stages), tmem_cols: TMEM columns allocated (mbmax x acc_stride, a power of two). Per 64-point
+// K slice the TMA warp loads the tile's chi rows (mX) and its phi rows (mP, float16 copies of the
+// phi tables) straight into the B operand's stage; four warps then scale that stage in place by
+// V at its points (shared memory only), and the MMA warp multiplies. Rows of the stage past the
+// tile's np hold other tiles' phi: their accumulator columns are never read.
 __global__ void __launch_bounds__(192, 3) integrals_tc_kernel(
     const __grid_constant__ CUtensorMap mX,   // function-major chi: [slot][512] f16
-    int n, int nt, int NP, int G, int k, const int *__restrict__ coff, const int *__restrict__ cids,
-    const int *__restrict__ poff, const int *__restrict__ pids, const float *__restrict__ pval, int nchi,
-    int nphi, const float *__restrict__ V, const float *__restrict__ vscale, float dV, float *__restrict__ out,
-    bool vec_ok, int acc_stride, const int *__restrict__ tiles, int mbmax, int tmem_cols, int *err) {
+    const __grid_constant__ CUtensorMap mP,   // function-major phi: [slot][512] f16, box NP rows
+    int n, int nt, int NP, int k, const int *__restrict__ coff, const int *__restrict__ cids,
+    const int *__restrict__ poff, const int *__restrict__ pids, int nchi, int nphi, const float *__restrict__ V,
+    const float *__restrict__ vscale, float dV, float *__restrict__ out, bool vec_ok, int acc_stride,
+    const int *__restrict__ tiles, int mbmax, int tmem_cols, int *err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<unsigned long long>(smem_raw) + 1023ull) & ~1023ull);
-    const int t = tiles[blockIdx.y], grp = blockIdx.x;
-    const int s0 = grp * G;
-    const int gs = min(G, k - s0);
+    const int t = tiles[blockIdx.y], s0 = blockIdx.x;
     const int c0 = coff[t], nc = coff[t + 1] - c0;
     const int p0 = poff[t], np = poff[t + 1] - p0;
     if (nc == 0 || np == 0) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int MB = (nc + 127) / 128;                 // <= mbmax (the host lists tiles by M blocks)
-    const int NB = G * NP;                           // <= acc_stride, multiple of 16
-    // layout: X stages [2][mbmax x 16 KB], W stages [2][NB x 128 B], V tile [G][512] f32, control
+    const int NB = NP;                               // <= acc_stride, multiple of 16
+    // layout: X stages [2][mbmax x 16 KB], W stages [2][NB x 128 B], V tile [512] f32, control
     unsigned char *Xs = base;
     const int xstage = mbmax * 16384;
     unsigned char *Ws = base + 2 * xstage;
     float *Vt = reinterpret_cast<float *>(Ws + (size_t)2 * NB * 128);
-    IntShared *ctl = reinterpret_cast<IntShared *>(Vt + (size_t)G * TILE_PTS);
+    IntShared *ctl = reinterpret_cast<IntShared *>(Vt + TILE_PTS);
     volatile int *abort = &ctl->abort;
     const long long n3 = (long long)n * n * n;
     const int tx = t / (nt * nt), ty = (t / nt) % nt, tz = t % nt;
@@ -476,14 +478,13 @@ __global__ void __launch_bounds__(192, 3) integrals_tc_kernel(
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     for (int i = threadIdx.x; i < np; i += blockDim.x) ctl->pid[i] = pids[p0 + i];
-    if (threadIdx.x < gs) ctl->vsc[threadIdx.x] = vscale[s0 + threadIdx.x];
-    // V of the group's states on the tile points, scaled
-    for (int i = threadIdx.x; i < gs * TILE_PTS; i += blockDim.x) {
-        const int sl = i / TILE_PTS, lp = i - sl * TILE_PTS;
+    // V of the state on the tile points, scaled
+    const float vs = vscale[s0];
+    for (int lp = threadIdx.x; lp < TILE_PTS; lp += blockDim.x) {
         const int gx = tx * TILE + (lp >> 6), gy = ty * TILE + ((lp >> 3) & 7), gz = tz * TILE + (lp & 7);
         float v = 0.0f;
-        if (gx < n && gy < n && gz < n) v = V[(long long)(s0 + sl) * n3 + ((long long)gx * n + gy) * n + gz];
-        Vt[i] = v * vscale[s0 + sl];
+        if (gx < n && gy < n && gz < n) v = V[(long long)s0 * n3 + ((long long)gx * n + gy) * n + gz];
+        Vt[lp] = v * vs;
     }
     tc_fence_before();
     __syncthreads();
@@ -497,9 +498,10 @@ __global__ void __launch_bounds__(192, 3) integrals_tc_kernel(
             for (int kb = 0; kb < KS; ++kb) {
                 const int st = kb & 1, use = kb >> 1;
                 if (use > 0 && !mbar_wait(&ctl->mma_done[st], (use - 1) & 1, abort)) break;
-                mbar_expect_tx(&ctl->x_full[st], MB * 16384);
+                mbar_expect_tx(&ctl->x_full[st], MB * 16384 + NB * 128);
                 for (int mb = 0; mb < MB; ++mb)
                     tma_load_2d(Xs + st * xstage + mb * 16384, &mX, &ctl->x_full[st], kb * 64, c0 + mb * 128);
+                tma_load_2d(Ws + (size_t)st * NB * 128, &mP, &ctl->x_full[st], kb * 64, p0);
             }
         }
     } else if (warp == 5) {
@@ -522,94 +524,52 @@ __global__ void __launch_bounds__(192, 3) integrals_tc_kernel(
             mma_commit(&ctl->acc_done);
         }
     } else {
-        // workers: build W slices, then the epilogue. The phi values of a slice are loaded into
-        // registers before the wait for the stage (all loads of a thread in flight at once, and
-        // overlapping the MMAs that still read the stage), then scaled by V, rounded and stored.
-        constexpr int WIT = 8;                       // (NB x 8) / 128 items per thread, NB <= 128
+        // workers: scale the phi rows of each landed stage by V (8 points per 16-byte chunk),
+        // then the epilogue
         for (int kb = 0; kb < KS; ++kb) {
             const int st = kb & 1, use = kb >> 1;
-            float4 pa[WIT], pb[WIT];
-#pragma unroll
-            for (int u = 0; u < WIT; ++u) {
-                const int idx = threadIdx.x + u * 128;
-                const int row = idx % NB, c8 = idx / NB;
-                const int sl = row / NP, b = row - sl * NP;
-                pa[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-                pb[u] = pa[u];
-                if (idx < NB * 8 && sl < gs && b < np) {
-                    const float4 *ph = reinterpret_cast<const float4 *>(pval + (long long)(p0 + b) * TILE_PTS + kb * 64 + c8 * 8);
-                    pa[u] = __ldg(ph);
-                    pb[u] = __ldg(ph + 1);
-                }
-            }
-            if (use > 0 && !mbar_wait(&ctl->mma_done[st], (use - 1) & 1, abort)) break;
+            if (!mbar_wait(&ctl->x_full[st], use & 1, abort)) break;
             unsigned char *W = Ws + (size_t)st * NB * 128;
-#pragma unroll
-            for (int u = 0; u < WIT; ++u) {
-                const int idx = threadIdx.x + u * 128;
-                if (idx >= NB * 8) break;
-                const int row = idx % NB, c8 = idx / NB;
-                const int sl = row / NP;
-                unsigned short h[8];
-                if (sl < gs) {
-                    // 8 consecutive points: phi from the registers, V from shared memory
-                    const float4 *vv = reinterpret_cast<const float4 *>(Vt + sl * TILE_PTS + kb * 64 + c8 * 8);
-                    const float4 v0 = vv[0], v1 = vv[1], p0v = pa[u], p1v = pb[u];
-                    h[0] = __half_as_ushort(__float2half_rn(p0v.x * v0.x));
-                    h[1] = __half_as_ushort(__float2half_rn(p0v.y * v0.y));
-                    h[2] = __half_as_ushort(__float2half_rn(p0v.z * v0.z));
-                    h[3] = __half_as_ushort(__float2half_rn(p0v.w * v0.w));
-                    h[4] = __half_as_ushort(__float2half_rn(p1v.x * v1.x));
-                    h[5] = __half_as_ushort(__float2half_rn(p1v.y * v1.y));
-                    h[6] = __half_as_ushort(__float2half_rn(p1v.z * v1.z));
-                    h[7] = __half_as_ushort(__float2half_rn(p1v.w * v1.w));
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) h[j] = 0;
-                }
-                uint4 q;
-                q.x = h[0] | ((unsigned)h[1] << 16);
-                q.y = h[2] | ((unsigned)h[3] << 16);
-                q.z = h[4] | ((unsigned)h[5] << 16);
-                q.w = h[6] | ((unsigned)h[7] << 16);
-                *reinterpret_cast<uint4 *>(W + sw128_offset(row, c8)) = q;
+            for (int idx = threadIdx.x; idx < np * 8; idx += 128) {
+                const int row = idx >> 3, c8 = idx & 7;
+                uint4 *q = reinterpret_cast<uint4 *>(W + sw128_offset(row, c8));
+                uint4 w = *q;
+                const float4 *vv = reinterpret_cast<const float4 *>(Vt + kb * 64 + c8 * 8);
+                const float4 v0 = vv[0], v1 = vv[1];
+                __half2 *h = reinterpret_cast<__half2 *>(&w);
+                float2 a;
+                a = __half22float2(h[0]); h[0] = __floats2half2_rn(a.x * v0.x, a.y * v0.y);
+                a = __half22float2(h[1]); h[1] = __floats2half2_rn(a.x * v0.z, a.y * v0.w);
+                a = __half22float2(h[2]); h[2] = __floats2half2_rn(a.x * v1.x, a.y * v1.y);
+                a = __half22float2(h[3]); h[3] = __floats2half2_rn(a.x * v1.z, a.y * v1.w);
+                *q = w;
             }
             fence_async_smem();
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ctl->w_ready[st])) : "memory");
         }
         const bool ok = mbar_wait(&ctl->acc_done, 0, abort) && !*abort;
         tc_fence_after();
+        const float f = dV / vs;
         for (int mb = 0; mb < MB; ++mb) {
             const int a = mb * 128 + warp * 32 + lane;
             const bool arow = ok && a < nc;
-            const long long rowoff = arow ? (long long)cids[c0 + a] * nphi : 0;
-            for (int c = 0; c < NB; c += 32) {
-                if (NP % 32 == 0) {
-                    // state-aligned chunk: skip it when it is all padding (warp-uniform)
-                    const int sl = c / NP;
-                    if (sl >= gs || c - sl * NP >= np) continue;
-                }
+            float *o = out + (long long)s0 * nchi * nphi + (arow ? (long long)cids[c0 + a] * nphi : 0);
+            for (int c = 0; c < np; c += 32) {
                 float v[32];
                 tmem_ld32(tmem + mb * acc_stride + ((unsigned)(warp * 32) << 16) + (unsigned)c, v);
                 if (!arow) continue;
 #pragma unroll
                 for (int j = 0; j < 32; j += 4) {
-                    const int col = c + j;
-                    const int sl = col / NP, b = col - sl * NP;
-                    if (sl >= gs || b >= np) continue;
-                    const float f = dV / ctl->vsc[sl];
-                    float *o = out + (long long)(s0 + sl) * nchi * nphi + rowoff;
+                    const int b = c + j;
+                    if (b >= np) break;
                     const int B0 = ctl->pid[b];
                     // four consecutive phi of one atom land on one aligned float4
-                    const bool vec = vec_ok && (b + 3 < np) && (B0 % 4 == 0) && ctl->pid[b + 3] == B0 + 3;
-                    if (vec) {
+                    if (vec_ok && b + 3 < np && (B0 & 3) == 0 && ctl->pid[b + 3] == B0 + 3) {
                         red_add_v4(o + B0, f * v[j], f * v[j + 1], f * v[j + 2], f * v[j + 3]);
                     } else {
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const int bu = b + u;
-                            if (bu < np && (col + u) / NP == sl) atomicAdd(o + ctl->pid[bu], f * v[j + u]);
-                        }
+                        for (int u = 0; u < 4; ++u)
+                            if (b + u < np) atomicAdd(o + ctl->pid[b + u], f * v[j + u]);
                     }
                 }
             }
@@ -647,7 +607,8 @@ int integrals_tc_group(int NP, int k, int maxc) {
 }
 
 void potential_integrals_tc(cudaStream_t st, const GridShape &g, const TileSet<float> &chi,
-                            const TileSet<float> &phi, const unsigned short *chi_fm16, int nslots, int NPmax,
+                            const TileSet<float> &phi, const unsigned short *chi_fm16, int nslots,
+                            const unsigned short *phi_fm16, int nslots_phi, int NPmax,
                             int maxc, int nchi, int nphi, const float *V, int k, float *out, unsigned *scratch_bits,
                             float *scale, const int *tile_list, const int *tiles_by_blocks, int *err) {
     if (k <= 0) return;
@@ -664,6 +625,11 @@ void potential_integrals_tc(cudaStream_t st, const GridShape &g, const TileSet<f
     if (!encode_map_2d(&mx, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, chi_fm16, (unsigned long long)TILE_PTS,
                        (unsigned long long)nslots, (unsigned long long)TILE_PTS * 2, 64, 128))
         throw CudaError{cudaErrorInvalidValue, "cuTensorMapEncodeTiled (integrals)"};
+    if (NPmax > 128 || NPmax % 16) throw CudaError{cudaErrorInvalidValue, "integrals_tc: phi per tile"};
+    CUtensorMap mp;
+    if (!encode_map_2d(&mp, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, phi_fm16, (unsigned long long)TILE_PTS,
+                       (unsigned long long)nslots_phi, (unsigned long long)TILE_PTS * 2, 64, NPmax))
+        throw CudaError{cudaErrorInvalidValue, "cuTensorMapEncodeTiled (integrals phi)"};
     // one launch per class of tiles by 128-row chi blocks (1, 2, 3), one state per CTA: the
     // smaller a class's shared memory and TMEM, the more CTAs share an SM (3, 2, 1)
     if (NPmax > 128) throw CudaError{cudaErrorInvalidValue, "integrals_tc: more than 128 phi per tile"};
@@ -685,9 +651,9 @@ void potential_integrals_tc(cudaStream_t st, const GridShape &g, const TileSet<f
         const int tmem_cols = mbmax == 1 ? 128 : (mbmax == 2 ? 256 : 512);
         const size_t sm = integrals_tc_smem(NPmax, 1, mbmax);
         dim3 grid(k, cnt);
-        integrals_tc_kernel<<<grid, 192, sm, st>>>(mx, g.n, g.nt, NPmax, 1, k, chi.off, chi.ids, phi.off, phi.ids,
-                                                   phi.val, nchi, nphi, V, scale, (float)g.dV, out, vec_ok, stride,
-                                                   lst, mbmax, tmem_cols, err);
+        integrals_tc_kernel<<<grid, 192, sm, st>>>(mx, mp, g.n, g.nt, NPmax, k, chi.off, chi.ids, phi.off, phi.ids,
+                                                   nchi, nphi, V, scale, (float)g.dV, out, vec_ok, stride, lst,
+                                                   mbmax, tmem_cols, err);
         check_launch("integrals_tc_kernel");
     }
 }
