@@ -210,6 +210,7 @@ struct Impl {
     unsigned short *chi_pm = nullptr;
     unsigned short *chi_fm16 = nullptr;   // function-major f16 chi tables [slot][512]
     unsigned short *phi_fm16 = nullptr;   // function-major f16 phi tables [slot][512]
+    unsigned short *phi_pm = nullptr;     // point-major f16 phi tables [tile][512][NPmax], zero padded
     int CK = 0, NPmax = 0, nslots_chi = 0, nslots_phi = 0, maxc = 0;
     bool grid_tc = false, integrals_tc = false;
     bool phi_quads = false;   // every tile's phi list is whole aligned groups of 4 (vector gather)
@@ -286,7 +287,7 @@ void potential_integrals_tc(cudaStream_t st, const GridShape &g, const TileSet<f
 void response_density_tc(cudaStream_t st, const GridShape &g, const TileSet<float> &chi,
                          const TileSet<float> &phi, const unsigned short *chi_pm, int CK, int NPmax, int nphi,
                          const float *P, long long sP, int k, float *rho, unsigned *scratch_bits,
-                         float *scale, int *err, bool phi_quads);
+                         float *scale, int *err, bool phi_quads, const unsigned short *phi_pm);
 int noalloc_max_states();
 void response_density_tc_noalloc(cudaStream_t st, const GridShape &g, const TileSet<float> &chi,
                                  const TileSet<float> &phi, const unsigned short *chi_pm, int CK, int NPmax,
@@ -545,7 +546,7 @@ void density(tddft_ctx *c, Impl<T> &I, const T *P, int ns) {
     if constexpr (sizeof(T) == 4) {
         if (I.grid_tc) {
             response_density_tc(c->st, c->grid(), I.chi, I.phi, I.chi_pm, I.CK, I.NPmax, c->nv, P, c->len(), ns,
-                                I.rho, I.tc_bits, I.tc_scale, tc_error_word(), I.phi_quads);
+                                I.rho, I.tc_bits, I.tc_scale, tc_error_word(), I.phi_quads, I.phi_pm);
             return;
         }
     }
@@ -781,6 +782,19 @@ void build_impl(tddft_ctx *c, const tddft_system *s) {
                 check(cudaMemcpy(I->chi_pm, pm.data(), pm.size() * sizeof(unsigned short), cudaMemcpyHostToDevice),
                       "upload point-major chi");
                 I->CK = CK;
+                // phi tables on the host once: point-major f16 for the density epilogue (and the
+                // function-major f16 copy of the integrals below)
+                std::vector<float> pv((size_t)poff[ntl] * TILE_PTS);
+                check(cudaMemcpy(pv.data(), I->phi.val, pv.size() * sizeof(float), cudaMemcpyDeviceToHost),
+                      "D2H phi tables");
+                if (NP % 32 == 0) {
+                    std::vector<unsigned short> ppm((size_t)ntl * TILE_PTS * NP, 0);
+                    build_point_major_f16(poff.data(), pv.data(), nullptr, ntl, NP, ppm.data());
+                    I->phi_pm = I->mem.template alloc<unsigned short>(ppm.size());
+                    check(cudaMemcpy(I->phi_pm, ppm.data(), ppm.size() * sizeof(unsigned short),
+                                     cudaMemcpyHostToDevice),
+                          "upload point-major phi");
+                }
                 I->NPmax = NP;
                 I->grid_tc = true;
                 {
@@ -812,9 +826,6 @@ void build_impl(tddft_ctx *c, const tddft_system *s) {
                     I->nslots_chi = coff[ntl];
                     {
                         // f16 phi tables for the integrals' B operand (TMA-loaded, scaled by V in place)
-                        std::vector<float> pv((size_t)poff[ntl] * TILE_PTS);
-                        check(cudaMemcpy(pv.data(), I->phi.val, pv.size() * sizeof(float), cudaMemcpyDeviceToHost),
-                              "D2H phi tables");
                         std::vector<unsigned short> ph(pv.size());
 #pragma omp parallel for schedule(static)
                         for (long long i = 0; i < (long long)pv.size(); ++i)

@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(DENS_THREADS, 1) density_tc_kernel(
     int n, int nt, int KBmax, int NP, int G, int k, const int *__restrict__ coff, const int *__restrict__ cids,
     const int *__restrict__ poff, const int *__restrict__ pids, const float *__restrict__ pval, int nphi,
     const float *__restrict__ P, long long sP, const float *__restrict__ pscale, float *__restrict__ rho,
-    int *err, int quad) {
+    int *err, int quad, const unsigned short *__restrict__ phi_pm) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<unsigned long long>(smem_raw) + 1023ull) & ~1023ull);
@@ -246,9 +246,27 @@ __global__ void __launch_bounds__(DENS_THREADS, 1) density_tc_kernel(
                 };
                 auto load_phi = [&](int cc, float *dst) {
                     const int b0 = cc - (cc / NP) * NP;
+                    if (phi_pm) {
+                        // point-major f16 phi [tile][point][NP] (zero past np): 32 values in four
+                        // 16-byte loads
+                        const uint4 *q = reinterpret_cast<const uint4 *>(
+                            phi_pm + ((long long)t * TILE_PTS + lp) * NP + b0);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        dst[j] = (b0 + j < np) ? pval[(long long)(p0 + b0 + j) * TILE_PTS + lp] : 0.0f;
+                        for (int w = 0; w < 4; ++w) {
+                            const uint4 x = __ldg(q + w);
+                            const __half2 *h = reinterpret_cast<const __half2 *>(&x);
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const float2 f2 = __half22float2(h[e]);
+                                dst[8 * w + 2 * e] = f2.x;
+                                dst[8 * w + 2 * e + 1] = f2.y;
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            dst[j] = (b0 + j < np) ? pval[(long long)(p0 + b0 + j) * TILE_PTS + lp] : 0.0f;
+                    }
                 };
                 int c = 0;
                 while (c < NB && !live(c)) c += 32;
@@ -367,7 +385,7 @@ int density_tc_group(int KBmax, int NP, int k) {
 void response_density_tc(cudaStream_t st, const GridShape &g, const TileSet<float> &chi,
                          const TileSet<float> &phi, const unsigned short *chi_pm, int CK, int NPmax, int nphi,
                          const float *P, long long sP, int k, float *rho, unsigned *scratch_bits,
-                         float *scale, int *err, bool phi_quads) {
+                         float *scale, int *err, bool phi_quads, const unsigned short *phi_pm) {
     if (k <= 0) return;
     ProfScope ps(st, ST_DENSITY, 2.0 * k * g.pair_points, 2.0 * g.table_values + 4.0 * k * g.n * g.n * g.n);
     check(cudaMemsetAsync(scratch_bits, 0, sizeof(unsigned) * k, st), "memset maxabs");
@@ -393,7 +411,7 @@ void response_density_tc(cudaStream_t st, const GridShape &g, const TileSet<floa
     dim3 grid(ngroups, chi.ntiles);
     density_tc_kernel<<<grid, DENS_THREADS, sm, st>>>(mx, g.n, g.nt, KBmax, NP, G, k, chi.off, chi.ids, phi.off,
                                                       phi.ids, phi.val, nphi, P, sP, scale, rho, err,
-                                                      phi_quads ? 1 : 0);
+                                                      phi_quads ? 1 : 0, NP % 32 == 0 ? phi_pm : nullptr);
     check_launch("density_tc_kernel");
 }
 
@@ -402,15 +420,17 @@ void response_density_tc(cudaStream_t st, const GridShape &g, const TileSet<floa
 // ================================================================================================
 // Potential integrals on the tensor cores (mixed precision): V_s,ab = dV sum_r chi_a(r) V_s(r) phi_b(r)
 // (the <chi|V_SCF|phi> matrix of Eqs. operator_TDA / operator_RPA) as one tcgen05 kind::f16
-// product per tile and state group,
+// product per tile and state,
 //
-//   D[a][(s,b)] = sum_r X[a][r] W[(s,b)][r],   W[(s,b)][r] = V_s(r) phi_b(r)
+//   D[a][b] = sum_r X[a][r] W[b][r],   W[b][r] = V_s(r) phi_b(r)
 //
-// M = chi functions of the tile (<= 2 blocks of 128), N = states x phi functions, K = the 512
-// tile points in 8 slices of 64. The chi block comes by TMA from the function-major f16 table;
-// four worker warps build W slice by slice (V scaled per state by a power of two) into a
-// double-buffered swizzled stage; one thread issues the MMAs. The epilogue adds dV * D into the
-// output matrices with vector reductions where four phi of one atom are contiguous.
+// M = chi functions of the tile (up to 3 blocks of 128), N = phi functions of the tile, K = the
+// 512 tile points in 8 slices of 64. Per slice the chi rows and the phi rows (float16 copies of
+// both tables, function-major) come by TMA into a double-buffered, 128-byte-swizzled stage; four
+// worker warps scale the phi rows in place by V_s (scaled by a power of two), and one thread
+// issues the MMAs. The epilogue adds dV * D into the output matrix with vector reductions where
+// four phi of one atom are contiguous. Tiles are launched by class of chi blocks (1, 2, 3) so
+// that the smaller ones share an SM three or two at a time.
 namespace tddft {
 namespace {
 
@@ -728,7 +748,8 @@ void response_density_tc_noalloc(cudaStream_t st, const GridShape &g, const Tile
           "attr density_tc");
     dim3 grid((k + G - 1) / G, chi.ntiles);
     density_tc_kernel<<<grid, DENS_THREADS, sm, st>>>(mx, g.n, g.nt, KBmax, NP, G, k, chi.off, chi.ids, phi.off,
-                                                      phi.ids, phi.val, nphi, P, sP, s->scale, rho, &s->err, 0);
+                                                      phi.ids, phi.val, nphi, P, sP, s->scale, rho, &s->err, 0,
+                                                      nullptr);
     check_launch("density_tc_kernel (allocation-free)");
 }
 
