@@ -1089,11 +1089,11 @@ void covariant(tddft_ctx *c, Impl<T> &I, int nb, const T *X, T *out, T *tmp) {
 
 // out = L X R (left nc x nc, right nv x nv) for nb matrices
 template <typename T>
-void sandwich(tddft_ctx *c, int nb, const T *Lm, const T *X, const T *Rm, T *out, T *tmp) {
+void sandwich(tddft_ctx *c, int nb, const T *Lm, const T *X, const T *Rm, T *out, T *tmp, bool approx = false) {
     const int nc = c->nc, nv = c->nv;
     const long long len = c->len();
-    gemm<T>(c->st, false, false, nc, nv, nc, T(1), Lm, nc, 0, X, nv, len, T(0), tmp, nv, len, nb);
-    gemm<T>(c->st, false, false, nb * nc, nv, nv, T(1), tmp, nv, 0, Rm, nv, 0, T(0), out, nv, 0, 1);
+    gemm<T>(c->st, false, false, nc, nv, nc, T(1), Lm, nc, 0, X, nv, len, T(0), tmp, nv, len, nb, approx);
+    gemm<T>(c->st, false, false, nb * nc, nv, nv, T(1), tmp, nv, 0, Rm, nv, 0, T(0), out, nv, 0, 1, approx);
 }
 
 void sync_status(tddft_ctx *c, tddft_state *S, const int *dstatus) {
@@ -1204,11 +1204,15 @@ void precondition(tddft_ctx *c, tddft_state *S, const T *h, T *z) {
         // lambda_c,i - lambda_v,j, and back: z = (Vc Ec) [(Ec^T Wc h Wv Ev) / (Lc - Lv)] (Ev^T Vv)
         const int rc = I.rc, rv = I.rv;
         const long long lr = (long long)rc * rv;
-        gemm<T>(st, false, false, rc, nv, nc, T(1), I.Wc, nc, 0, h, nv, len, T(0), B.tmp, nv, (long long)rc * nv, k2);
-        gemm<T>(st, false, false, k2 * rc, rv, nv, T(1), B.tmp, nv, 0, I.Wv, rv, 0, T(0), B.qr, rv, 0, 1);
+        // (a preconditioner's errors change the search direction, not the fixed point: one TF32
+        // MMA per product)
+        gemm<T>(st, false, false, rc, nv, nc, T(1), I.Wc, nc, 0, h, nv, len, T(0), B.tmp, nv, (long long)rc * nv, k2,
+                true);
+        gemm<T>(st, false, false, k2 * rc, rv, nv, T(1), B.tmp, nv, 0, I.Wv, rv, 0, T(0), B.qr, rv, 0, 1, true);
         mask_mul<T>(st, B.qr, I.Dn, lr, k2);
-        gemm<T>(st, false, false, nc, rv, rc, T(1), I.Vc, rc, 0, B.qr, rv, lr, T(0), B.tmp, rv, (long long)nc * rv, k2);
-        gemm<T>(st, false, false, k2 * nc, nv, rv, T(1), B.tmp, rv, 0, I.Vv, nv, 0, T(0), z, nv, 0, 1);
+        gemm<T>(st, false, false, nc, rv, rc, T(1), I.Vc, rc, 0, B.qr, rv, lr, T(0), B.tmp, rv, (long long)nc * rv, k2,
+                true);
+        gemm<T>(st, false, false, k2 * nc, nv, rv, T(1), B.tmp, rv, 0, I.Vv, nv, 0, T(0), z, nv, 0, 1, true);
         return;
     }
     if (I.rc) {
@@ -1324,7 +1328,9 @@ const T *search_gradient(tddft_ctx *c, tddft_state *S) {
     Impl<T> &I = impl<T>(c);
     StateBufs<T> &B = bufs<T>(S);
     if (c->trunc) {
-        sandwich<T>(c, 2 * S->k, I.Pc, B.G1, I.Pv, B.h, B.tmp);   // P^c G_L P^v
+        // P^c G_L P^v; with the exact preconditioner it only feeds that preconditioner, whose
+        // errors change the search direction and not the fixed point: one TF32 MMA per product
+        sandwich<T>(c, 2 * S->k, I.Pc, B.G1, I.Pv, B.h, B.tmp, I.exact);
         return B.h;
     }
     return B.g;

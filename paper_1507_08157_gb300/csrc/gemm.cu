@@ -114,7 +114,7 @@ void launch(cudaStream_t st, int M, int N, int K, T alpha, const T *A, int lda, 
 template <typename T>
 void gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, T alpha, const T *A, int lda,
           long long sA, const T *B, int ldb, long long sB, T beta, T *C, int ldc, long long sC,
-          int batch) {
+          int batch, bool approx) {
     if (M <= 0 || N <= 0 || batch <= 0) return;
     const double bytes = sizeof(T) * ((double)M * K * (sA ? batch : 1) + (double)K * N * (sB ? batch : 1) +
                                       (double)M * N * batch * (beta == T(0) ? 1 : 2));
@@ -123,7 +123,7 @@ void gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, T alpha, const
     // accuracy); float64 and tiny products stay on the CUDA cores
     if (sizeof(T) == 4 && tc_enabled() && (double)M * N * K * batch >= 2.0e6) {
         tc_gemm(st, ta, tb, M, N, K, (float)alpha, (const float *)A, lda, sA, (const float *)B, ldb, sB,
-                (float)beta, (float *)C, ldc, sC, batch, true);
+                (float)beta, (float *)C, ldc, sC, batch, !approx);
         return;
     }
     if (!ta && !tb) launch<T, false, false>(st, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch);
@@ -134,9 +134,9 @@ void gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, T alpha, const
 
 template void gemm<float>(cudaStream_t, bool, bool, int, int, int, float, const float *, int,
                           long long, const float *, int, long long, float, float *, int,
-                          long long, int);
+                          long long, int, bool);
 template void gemm<double>(cudaStream_t, bool, bool, int, int, int, double, const double *, int,
                            long long, const double *, int, long long, double, double *, int,
-                           long long, int);
+                           long long, int, bool);
 
 }  // namespace tddft

@@ -90,11 +90,13 @@ struct GridShape {
 void tc_register_constant(const float *p);
 void tc_unregister_constant(const float *p);
 
-// dense GEMM, row-major: C[b] = alpha * op(A[b]) op(B[b]) + beta * C[b]
+// dense GEMM, row-major: C[b] = alpha * op(A[b]) op(B[b]) + beta * C[b]. approx: a float32
+// product on the tensor cores may take one TF32 MMA instead of the three-term split (about 1e-3
+// relative error; for operands whose errors the method tolerates, such as a preconditioner's)
 template <typename T>
 void gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, T alpha, const T *A, int lda,
           long long sA, const T *B, int ldb, long long sB, T beta, T *C, int ldc, long long sC,
-          int batch);
+          int batch, bool approx = false);
 
 // ---------------------------------------------------------------------------------------------
 // grid work
