@@ -30,7 +30,7 @@ struct __align__(8) DensShared {
     unsigned long long a_empty[4];
     unsigned long long acc_full[2];
     unsigned long long acc_empty[2];
-    unsigned long long b_ready;
+    unsigned long long b_ready[16];   // per 64-wide K block of the gathered P block
     unsigned int tmem_base;
     int abort;
 };
@@ -38,6 +38,7 @@ struct __align__(8) DensShared {
 constexpr int DENS_THREADS = 256;      // warps 0-3 gather + epilogue, 4 TMA, 5 MMA, 6-7 gather
 constexpr int DENS_GATHER = 192;       // gathering threads: warps 0-3 and 6-7
 constexpr int DENS_STAGES = 4;         // chi-block ring (16 KB each)
+constexpr int DENS_KBMAX = 16;         // K blocks of the gathered P block (CK <= 1024)
 
 __device__ __forceinline__ int gather_rank(int warp, int lane) { return (warp < 4 ? warp : warp - 2) * 32 + lane; }
 
@@ -82,7 +83,7 @@ __global__ void __launch_bounds__(DENS_THREADS, 1) density_tc_kernel(
             mbar_init(&ctl->acc_full[i], 1);
             mbar_init(&ctl->acc_empty[i], 128);
         }
-        mbar_init(&ctl->b_ready, DENS_GATHER);
+        for (int i = 0; i < DENS_KBMAX; ++i) mbar_init(&ctl->b_ready[i], DENS_GATHER);
         ctl->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -112,7 +113,7 @@ __global__ void __launch_bounds__(DENS_THREADS, 1) density_tc_kernel(
         // MMA issuer: accumulator pb % 2, one commit per chi block (frees the ring slot)
         if (lane == 0) {
             const unsigned idesc = idesc_f16(128, NB);
-            bool ok = mbar_wait(&ctl->b_ready, 0, abort);
+            bool ok = true;
             int i = 0;
             for (int pb = 0; pb < TILE_PTS / 128 && ok; ++pb) {
                 const int acc = pb & 1, use = pb >> 1;
@@ -120,7 +121,8 @@ __global__ void __launch_bounds__(DENS_THREADS, 1) density_tc_kernel(
                 tc_fence_after();
                 for (int kb = 0; kb < KB; ++kb, ++i) {
                     const int st = i % DENS_STAGES, u = i / DENS_STAGES;
-                    if (!mbar_wait(&ctl->a_full[st], u & 1, abort)) {
+                    // the P block's K block kb is gathered (the first M block waits, the rest pass)
+                    if (!mbar_wait(&ctl->b_ready[kb], 0, abort) || !mbar_wait(&ctl->a_full[st], u & 1, abort)) {
                         ok = false;
                         break;
                     }
@@ -142,6 +144,15 @@ __global__ void __launch_bounds__(DENS_THREADS, 1) density_tc_kernel(
         // chunk), quads fastest so a warp reads 512 contiguous bytes of one P row per load
         const int rank = gather_rank(warp, lane);
         const int nq = NB / 4, chunks = KB * 8, total = nq * chunks;
+        // a thread's items come in increasing K order: once its next item lies in K block q, its
+        // share of every block before q is stored and it arrives on those blocks' barriers
+        int sig = 0;
+        auto signal_upto = [&](int q) {
+            if (sig >= q) return;
+            fence_async_smem();
+            for (; sig < q; ++sig)
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ctl->b_ready[sig])) : "memory");
+        };
         for (int i0 = rank; i0 < total; i0 += 2 * DENS_GATHER) {
             float4 v[2][8];
 #pragma unroll
@@ -181,15 +192,22 @@ __global__ void __launch_bounds__(DENS_THREADS, 1) density_tc_kernel(
                     *reinterpret_cast<uint4 *>(B + (size_t)(ch >> 3) * NB * 128 + sw128_offset(qd * 4 + r, ch & 7)) = q;
                 }
             }
+            signal_upto(min(KB, ((i0 + 2 * DENS_GATHER) / nq) >> 3));
         }
-        fence_async_smem();
-        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ctl->b_ready)) : "memory");
+        signal_upto(KB);
     } else if (warp < 4 || warp >= 6) {
         // gather the P block: row (s, b), K = a, 8 consecutive a per 16-byte chunk; four items in
         // flight per thread (32 independent loads)
         const int rank = gather_rank(warp, lane);
         const int chunks = KB * 8;
         const int total = NB * chunks;
+        int sig = 0;   // as above: arrive on each K block once this thread's share of it is stored
+        auto signal_upto = [&](int q) {
+            if (sig >= q) return;
+            fence_async_smem();
+            for (; sig < q; ++sig)
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ctl->b_ready[sig])) : "memory");
+        };
         for (int i0 = rank; i0 < total; i0 += 4 * DENS_GATHER) {
             float v[4][8];
 #pragma unroll
@@ -222,9 +240,9 @@ __global__ void __launch_bounds__(DENS_THREADS, 1) density_tc_kernel(
                 q.w = h[6] | ((unsigned)h[7] << 16);
                 *reinterpret_cast<uint4 *>(B + (size_t)(ch >> 3) * NB * 128 + sw128_offset(row, ch & 7)) = q;
             }
+            signal_upto(min(KB, ((i0 + 4 * DENS_GATHER) / NB) >> 3));
         }
-        fence_async_smem();
-        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ctl->b_ready)) : "memory");
+        signal_upto(KB);
     }
     if (warp < 4) {
         // epilogue: rho_s(r) = sum_b T[r][(s,b)] phi_b(r) for the 128 points of block pb
@@ -377,6 +395,7 @@ size_t density_tc_smem(int KBmax, int NB) {
 
 // largest state group G (<= 16, G * NP <= 256) whose shared memory fits; 0 if none does
 int density_tc_group(int KBmax, int NP, int k) {
+    if (KBmax > DENS_KBMAX) return 0;
     for (int G = std::min(16, std::min(k, 256 / NP)); G >= 1; --G)
         if (density_tc_smem(KBmax, G * NP) <= 227 * 1024) return G;
     return 0;
