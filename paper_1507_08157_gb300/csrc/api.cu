@@ -291,7 +291,8 @@ void response_density_tc(cudaStream_t st, const GridShape &g, const TileSet<floa
 int noalloc_max_states();
 void response_density_tc_noalloc(cudaStream_t st, const GridShape &g, const TileSet<float> &chi,
                                  const TileSet<float> &phi, const unsigned short *chi_pm, int CK, int NPmax,
-                                 int nphi, const float *P, long long sP, int k, float *rho);
+                                 int nphi, const float *P, long long sP, int k, float *rho,
+                                 const unsigned short *phi_pm);
 int response_density_tc_noalloc_error(cudaStream_t st);
 Profiler *profiler_new();
 void profiler_delete(Profiler *p);
@@ -2075,7 +2076,7 @@ tddft_status tddft_response_density_noalloc(tddft_ctx *c, int32_t k, const float
             throw InvalidArg{"tddft_response_density_noalloc: P and rho must be device pointers"};
         Impl<float> &I = *c->d32;
         response_density_tc_noalloc(c->st, c->grid(), I.chi, I.phi, I.chi_pm, I.CK, I.NPmax, c->nv, P, c->len(), k,
-                                    rho);
+                                    rho, I.phi_pm);
         if (response_density_tc_noalloc_error(c->st))
             throw TimeoutErr{"a bounded wait in the density kernel expired"};
         return TDDFT_OK;

@@ -746,7 +746,8 @@ int noalloc_max_states() { return NOALLOC_MAX_STATES; }
 // rho[k][n^3] from P[k][N_chi][N_phi] (float32, device); no allocation, no context workspace.
 void response_density_tc_noalloc(cudaStream_t st, const GridShape &g, const TileSet<float> &chi,
                                  const TileSet<float> &phi, const unsigned short *chi_pm, int CK, int NPmax,
-                                 int nphi, const float *P, long long sP, int k, float *rho) {
+                                 int nphi, const float *P, long long sP, int k, float *rho,
+                                 const unsigned short *phi_pm) {
     if (k < 1 || k > NOALLOC_MAX_STATES) throw CudaError{cudaErrorInvalidValue, "k beyond the scratch maximum"};
     NoallocScratch *s = noalloc_scratch_address();
     // the scale words must start at zero for the max reduction; the flag is cleared per call
@@ -768,7 +769,7 @@ void response_density_tc_noalloc(cudaStream_t st, const GridShape &g, const Tile
     dim3 grid((k + G - 1) / G, chi.ntiles);
     density_tc_kernel<<<grid, DENS_THREADS, sm, st>>>(mx, g.n, g.nt, KBmax, NP, G, k, chi.off, chi.ids, phi.off,
                                                       phi.ids, phi.val, nphi, P, sP, s->scale, rho, &s->err, 0,
-                                                      nullptr);
+                                                      NP % 32 == 0 ? phi_pm : nullptr);
     check_launch("density_tc_kernel (allocation-free)");
 }
 
