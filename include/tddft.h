@@ -239,6 +239,19 @@ tddft_status tddft_oscillator_strengths(tddft_ctx *ctx, tddft_state *st, double 
 tddft_status tddft_spectrum(tddft_ctx *ctx, int32_t k, const double *omega, const double *f,
                             double gamma, int32_t n, const double *E, double *S);
 
+/* Conduction projector of the joint unoccupied representation {varphi} = {phi} (+) {chi}
+ * (Sec. II C, Eq. proj): P^c = S^-1 - S^-1 S^{varphi phi} P^v S^{phi varphi} S^-1, with S the
+ * overlap of the joint functions [n_joint][n_joint], S_joint_phi = S^{varphi phi}
+ * [n_joint][n_phi] and P_v [n_phi][n_phi]; P_c [n_joint][n_joint] out. The result projects onto
+ * the whole unoccupied space the joint functions represent; a context made with chi := the
+ * joint functions, S_chi := S, H_chi := the joint Hamiltonian and this P_c solves in that
+ * representation (the paper's production setting). Float64 on the device (S^-1 from the
+ * coupled Newton-Schulz square roots); buffers host or device, work on cuda_stream, synchronous.
+ * INVALID for non-positive sizes or NULL buffers, or when S is not positive definite. */
+tddft_status tddft_joint_projector(void *cuda_stream, int32_t n_joint, int32_t n_phi,
+                                   const double *S_joint, const double *S_joint_phi,
+                                   const double *P_v, double *P_c);
+
 /* Checkpoint and resume of a PCG state (Sec. III C carries, from one iteration to the next, the
  * trial pairs with their operator images and the previous search direction with its
  * preconditioned gradient; the checkpoint holds exactly these). tddft_state_export writes into

@@ -20,16 +20,30 @@ from . import grid, hartree, xc
 
 
 class Casida:
-    def __init__(self, sys, fxc_kind="lda"):
+    def __init__(self, sys, fxc_kind="lda", conduction="spectral"):
+        """conduction: "spectral" takes the lowest n_cond states of H^chi d = eps S^chi d;
+        "projector" diagonalises H^chi on the range of the given P^c (the joint representation of
+        Eq. proj, where the unoccupied space is the range of P^c, not a set of lowest states)."""
         self.sys = sys
         eps_v, C = scipy.linalg.eigh(sys.H_phi, sys.S_phi)
-        eps_c, Dm = scipy.linalg.eigh(sys.H_chi, sys.S_chi)
         self.eps_v = eps_v[:sys.n_occ]
-        self.eps_c = eps_c[:sys.n_cond]
         self.Cv = C[:, :sys.n_occ]
-        self.Dc = Dm[:, :sys.n_cond]
+        if conduction == "spectral":
+            eps_c, Dm = scipy.linalg.eigh(sys.H_chi, sys.S_chi)
+            self.eps_c = eps_c[:sys.n_cond]
+            self.Dc = Dm[:, :sys.n_cond]
+        else:
+            # S-orthonormal basis of range(P^c): eigenvectors of S^1/2 P^c S^1/2 with eigenvalue 1
+            w, U = scipy.linalg.eigh(sys.S_chi)
+            Sh = U @ np.diag(np.sqrt(w)) @ U.T
+            Smh = U @ np.diag(1.0 / np.sqrt(w)) @ U.T
+            pw, PU = scipy.linalg.eigh(Sh @ sys.P_c @ Sh)
+            B = PU[:, pw > 0.5]
+            eps_c, Y = scipy.linalg.eigh(B.T @ Smh @ sys.H_chi @ Smh @ B)
+            self.eps_c = eps_c
+            self.Dc = Smh @ B @ Y
         self.fxc = xc.fxc_lda(sys.n0) if fxc_kind == "lda" else np.zeros_like(sys.n0)
-        self.nc, self.nv = sys.n_cond, sys.n_occ
+        self.nc, self.nv = self.Dc.shape[1], sys.n_occ
 
     def ks_orbitals(self):
         n = self.sys.n

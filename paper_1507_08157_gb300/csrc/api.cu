@@ -1711,6 +1711,41 @@ tddft_status tddft_solve_batch(tddft_ctx *const *ctx, tddft_state *const *st, in
     return first;
 }
 
+tddft_status tddft_joint_projector(void *cuda_stream, int32_t n_joint, int32_t n_phi, const double *S_joint,
+                                   const double *S_joint_phi, const double *P_v, double *P_c) {
+    if (n_joint <= 0 || n_phi <= 0 || !S_joint || !S_joint_phi || !P_v || !P_c) return TDDFT_E_INVALID;
+    tddft_ctx tmp;   // carries the error text only
+    tmp.st = static_cast<cudaStream_t>(cuda_stream);
+    const tddft_status rc = guarded(&tmp, [&]() -> tddft_status {
+        cudaStream_t st = tmp.st;
+        const int nj = n_joint, nv = n_phi;
+        const long long jj = (long long)nj * nj, jv = (long long)nj * nv, vv = (long long)nv * nv;
+        Mem m;
+        double *S = m.alloc<double>(jj), *Sjp = m.alloc<double>(jv), *Pv = m.alloc<double>(vv);
+        check(cudaMemcpyAsync(S, S_joint, jj * sizeof(double), cudaMemcpyDefault, st), "copy S_joint");
+        check(cudaMemcpyAsync(Sjp, S_joint_phi, jv * sizeof(double), cudaMemcpyDefault, st), "copy S_joint_phi");
+        check(cudaMemcpyAsync(Pv, P_v, vv * sizeof(double), cudaMemcpyDefault, st), "copy P_v");
+        std::vector<double> Sh_host((size_t)jj);
+        check(cudaMemcpyAsync(Sh_host.data(), S, jj * sizeof(double), cudaMemcpyDeviceToHost, st), "D2H S_joint");
+        check(cudaStreamSynchronize(st), "sync joint projector");
+        double *Sh = m.alloc<double>(jj), *Smh = m.alloc<double>(jj), *X = m.alloc<double>(jj);
+        overlap_roots(st, m, S, Sh_host.data(), nj, Sh, Smh);
+        gemm<double>(st, false, false, nj, nj, nj, 1.0, Smh, nj, 0, Smh, nj, 0, 0.0, X, nj, 0, 1);        // S^-1
+        double *T1 = m.alloc<double>(jv), *T = m.alloc<double>(jj), *Y = m.alloc<double>(jj);
+        gemm<double>(st, false, false, nj, nv, nv, 1.0, Sjp, nv, 0, Pv, nv, 0, 0.0, T1, nv, 0, 1);         // S^{vp} P^v
+        gemm<double>(st, false, true, nj, nj, nv, 1.0, T1, nv, 0, Sjp, nv, 0, 0.0, T, nj, 0, 1);          // .. S^{pv}
+        gemm<double>(st, false, false, nj, nj, nj, 1.0, X, nj, 0, T, nj, 0, 0.0, Y, nj, 0, 1);            // S^-1 T
+        double *Pc = m.alloc<double>(jj);
+        check(cudaMemcpyAsync(Pc, X, jj * sizeof(double), cudaMemcpyDeviceToDevice, st), "copy S^-1");
+        gemm<double>(st, false, false, nj, nj, nj, -1.0, Y, nj, 0, X, nj, 0, 1.0, Pc, nj, 0, 1);          // X - Y X
+        check(cudaMemcpyAsync(P_c, Pc, jj * sizeof(double), cudaMemcpyDefault, st), "copy P_c");
+        check(cudaStreamSynchronize(st), "sync joint projector");
+        return TDDFT_OK;
+    });
+    if (rc != TDDFT_OK) std::fprintf(stderr, "tddft_joint_projector: %s\n", tmp.err.c_str());
+    return rc;
+}
+
 void tddft_destroy(tddft_ctx *c) {
     if (!c) return;
     cudaStreamSynchronize(c->st);

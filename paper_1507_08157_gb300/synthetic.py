@@ -375,6 +375,75 @@ def generate(recipe: Recipe) -> System:
                   n_occ=n_occ, n_cond=n_cond)
 
 
+@dataclasses.dataclass
+class JointInputs:
+    """Raw inputs of the joint unoccupied representation {varphi} = {phi} (+) {chi}: the joint
+    function set (per atom its phi, then its chi), its overlap and Hamiltonian, the columns
+    S^{varphi phi} of the overlap that belong to phi, and the valence side (H^phi shifted so that
+    its unoccupied part lies `gap` above the valence states, P^v unchanged). The conduction
+    projector of that representation is not made here: it is the method's own step."""
+    funcs: FunctionSet
+    S_joint: np.ndarray
+    H_joint: np.ndarray
+    S_joint_phi: np.ndarray
+    H_phi: np.ndarray
+    phi_cols: np.ndarray   # int64 [N_phi]: joint index of each phi function
+
+
+def joint_inputs(sys: System, seed: int, cross_sigma=0.02, chi_shift_ev=4.0) -> JointInputs:
+    """Joint-representation inputs from a generated system: per atom its nphi phi and nchi chi
+    functions; the joint overlap from the tables; the joint Hamiltonian with the phi block the
+    valence Hamiltonian (unoccupied part lifted by the system's gap), the chi block the
+    conduction Hamiltonian lifted by chi_shift_ev * S^chi, and random cross blocks of std
+    cross_sigma Ha decaying with distance like the other blocks."""
+    r = sys.recipe
+    nphi, nchi = r.nphi, r.nchi
+    nper = nphi + nchi
+    na = sys.natoms
+    e3 = int(sys.phi.off[1] - sys.phi.off[0])
+    if int(sys.chi.off[1] - sys.chi.off[0]) != e3:
+        raise ValueError("phi and chi boxes differ in size")
+    nfun = na * nper
+    atom = np.repeat(np.arange(na, dtype=np.int32), nper)
+    box = np.zeros((nfun, 6), dtype=np.int32)
+    off = np.arange(nfun + 1, dtype=np.int64) * e3
+    val = np.empty(int(off[-1]))
+    phi_cols = np.zeros(na * nphi, dtype=np.int64)
+    chi_cols = np.zeros(na * nchi, dtype=np.int64)
+    for a in range(na):
+        for q in range(nphi):
+            f, g = a * nper + q, a * nphi + q
+            box[f] = sys.phi.box[g]
+            val[off[f]:off[f + 1]] = sys.phi.val[sys.phi.off[g]:sys.phi.off[g + 1]]
+            phi_cols[g] = f
+        for q in range(nchi):
+            f, g = a * nper + nphi + q, a * nchi + q
+            box[f] = sys.chi.box[g]
+            val[off[f]:off[f + 1]] = sys.chi.val[sys.chi.off[g]:sys.chi.off[g + 1]]
+            chi_cols[g] = f
+    funcs = FunctionSet(atom=atom, box=box, off=off, val=val)
+    R = r.radius_ang * BOHR_PER_ANG
+    S = _overlap_matrix(funcs, nper, sys.pos, sys.cell, sys.n, sys.dV, 2.0 * R)
+    # valence Hamiltonian with its unoccupied part lifted: P^v stays its spectral projector
+    gap = r.gap_ev * HA_PER_EV
+    Sv = sys.S_phi
+    Hv = sys.H_phi + gap * (Sv - Sv @ sys.P_v @ Sv)
+    rng = np.random.default_rng(seed)
+    H = _random_hamiltonian(rng, sys.pos, sys.cell, nper, 2.0 * R, cross_sigma, r.h_decay_ang * BOHR_PER_ANG)
+    H[np.ix_(phi_cols, phi_cols)] = Hv
+    H[np.ix_(chi_cols, chi_cols)] = sys.H_chi + chi_shift_ev * HA_PER_EV * sys.S_chi
+    H = 0.5 * (H + H.T)
+    return JointInputs(funcs=funcs, S_joint=S, H_joint=H, S_joint_phi=S[:, phi_cols], H_phi=Hv, phi_cols=phi_cols)
+
+
+def with_joint(sys: System, ji: JointInputs, P_c: np.ndarray) -> System:
+    """The system in the joint representation: chi := {varphi}, with the conduction projector
+    P_c of that representation (from the method, Eq. proj) supplied by the caller."""
+    n_cond = int(round(np.trace(P_c @ ji.S_joint)))
+    return dataclasses.replace(sys, chi=ji.funcs, S_chi=ji.S_joint, H_chi=ji.H_joint, H_phi=ji.H_phi, P_c=P_c,
+                               n_cond=n_cond)
+
+
 def smooth_grid(n: int) -> int:
     """The smallest 2/3/5-smooth integer >= n (FFT-friendly grid sizes)."""
     while True:

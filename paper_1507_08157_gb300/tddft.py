@@ -68,7 +68,7 @@ SYMBOLS = sorted(["tddft_default_options", "tddft_create", "tddft_destroy", "tdd
                   "tddft_mlp_loss_grad", "tddft_mlp_train", "tddft_learned_dims", "tddft_set_mlp",
                   "tddft_samples", "tddft_state_stats", "tddft_state_export",
                   "tddft_state_import", "tddft_create_batch", "tddft_solve_batch",
-                  "tddft_oscillator_strengths", "tddft_spectrum"])
+                  "tddft_oscillator_strengths", "tddft_spectrum", "tddft_joint_projector"])
 
 _lib = None
 _live = weakref.WeakSet()      # open contexts and states, closed before interpreter shutdown
@@ -140,6 +140,7 @@ def load(path: str = LIB_PATH):
     lib.tddft_state_export.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_size_t)]
     lib.tddft_state_import.argtypes = [vp, vp, ctypes.c_size_t, ctypes.POINTER(vp)]
     lib.tddft_oscillator_strengths.argtypes = [vp, vp, vp, vp, vp]
+    lib.tddft_joint_projector.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, vp, vp, vp, vp]
     lib.tddft_spectrum.argtypes = [vp, ctypes.c_int32, vp, vp, ctypes.c_double, ctypes.c_int32, vp, vp]
     lib.tddft_create_batch.argtypes = [ctypes.POINTER(_System), ctypes.c_int32, ctypes.POINTER(_Options), vp,
                                        ctypes.POINTER(vp)]
@@ -153,7 +154,7 @@ def load(path: str = LIB_PATH):
                  "tddft_mlp_loss_grad", "tddft_mlp_train", "tddft_learned_dims", "tddft_set_mlp",
                  "tddft_samples", "tddft_state_stats", "tddft_state_export",
                  "tddft_state_import", "tddft_create_batch", "tddft_solve_batch",
-                 "tddft_oscillator_strengths", "tddft_spectrum"):
+                 "tddft_oscillator_strengths", "tddft_spectrum", "tddft_joint_projector"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -233,6 +234,20 @@ def _marshal(sys: System, fxc="lda"):
     s.fxc_kind = FXC[fxc]
     s.kernel_cutoff = sys.kernel_cutoff
     return s, keep
+
+
+def joint_projector(S_joint, S_joint_phi, P_v, stream=None):
+    """P^c of the joint representation (Eq. proj) on the device (tddft_joint_projector)."""
+    lib = load()
+    S = np.ascontiguousarray(S_joint, dtype=np.float64)
+    Sjp = np.ascontiguousarray(S_joint_phi, dtype=np.float64)
+    Pv = np.ascontiguousarray(P_v, dtype=np.float64)
+    out = np.empty_like(S)
+    rc = lib.tddft_joint_projector(ctypes.c_void_p(stream) if stream is not None else None, S.shape[0], Pv.shape[0],
+                                   S.ctypes.data, Sjp.ctypes.data, Pv.ctypes.data, out.ctypes.data)
+    if rc != OK:
+        raise TddftError(rc, "tddft_joint_projector failed (see stderr)")
+    return out
 
 
 def create_batch(systems, fxc="lda", stream=None, **opts):
