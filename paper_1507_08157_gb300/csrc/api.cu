@@ -1383,12 +1383,15 @@ void update(tddft_ctx *c, tddft_state *S) {
     // one operator application on the directions
     apply_impl<T>(c, I, k, B.D, B.fD, true);
     covariant<T>(c, I, k2, B.D, B.covD, B.tmp);
-    gram<T>(st, B.covD, len, k2, B.f, len, k2, len, B.BDf, B.gscr);
-    gram<T>(st, B.covD, len, k2, B.fD, len, k2, len, B.CDfD, B.gscr);
-    gram<T>(st, B.covP, len, k2, B.P, len, k2, len, B.PP, B.gscr);
-    gram<T>(st, B.covP, len, k2, B.D, len, k2, len, B.PD, B.gscr);
-    gram<T>(st, B.covD, len, k2, B.P, len, k2, len, B.DP, B.gscr);
-    gram<T>(st, B.covD, len, k2, B.D, len, k2, len, B.DD, B.gscr);
+    {
+        // the six traces of the line step in two passes (cov(D) and cov(P) read once each)
+        const T *yd[4] = {B.f, B.fD, B.P, B.D};
+        double *gd[4] = {B.BDf, B.CDfD, B.DP, B.DD};
+        gram_multi<T>(st, B.covD, len, k2, 4, yd, len, k2, len, gd, B.gscr);
+        const T *yp[2] = {B.P, B.D};
+        double *gp[2] = {B.PP, B.PD};
+        gram_multi<T>(st, B.covP, len, k2, 2, yp, len, k2, len, gp, B.gscr);
+    }
     line_gs(st, k, B.A, B.BDf, B.CDfD, B.PP, B.PD, B.DP, B.DD, B.Q, B.lam, B.Cp, B.Cq, B.flip,
             B.status);
     axpy_dev<T>(st, B.lam, 0, 1.0, B.Y, B.dir, tot, 1);

@@ -28,6 +28,31 @@ __global__ void gram_final(const double *__restrict__ partial, int nblocks, int 
     if (lane == 0) G[p] = s;
 }
 
+// up to four Gram matrices of one X against several Y sets, [nx][per] each
+struct GOut {
+    double *g[4];
+};
+__global__ void gram_final_multi(const double *__restrict__ partial, int nblocks, int pairs, int ny, int per,
+                                 GOut out) {
+    const int lane = threadIdx.x & 31;
+    const int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (p >= pairs) return;
+    double s = 0.0;
+    for (int b = lane; b < nblocks; b += 32) s += partial[(long long)b * pairs + p];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+        const int i = p / ny, j = p - i * ny, q = j / per;
+        out.g[q][i * per + (j - q * per)] = s;
+    }
+}
+
+// the Y rows of a trace product: row j is row (j % per) of set j / per
+template <typename T>
+struct YSet {
+    const T *p[4];
+    int per;
+};
+
 // ------------------------------------------------------------------------------------------------
 // Register-tiled trace products. Block (x, y): pair tile x of TI x TJ (i, j), element slice y
 // (consecutive blocks share a slice, so the rows a tile re-reads come from L2). Each thread sums
@@ -41,12 +66,18 @@ constexpr int TI = 4, TJ = 8;
 
 template <typename T>
 __global__ void __launch_bounds__(256, 2) gram_tiled(const T *__restrict__ X, long long sx, int nx,
-                                                     const T *__restrict__ Y, long long sy, int ny,
+                                                     const YSet<T> ys, long long sy, int ny,
                                                      long long len, int tiles_j, double *__restrict__ partial,
                                                      int pairs) {
     __shared__ double red[TI][TJ][8];
     const int ti = blockIdx.x / tiles_j, tj = blockIdx.x - ti * tiles_j;
     const int i0 = ti * TI, j0 = tj * TJ;
+    const T *yr[TJ];
+#pragma unroll
+    for (int b = 0; b < TJ; ++b) {
+        const int j = j0 + b < ny ? j0 + b : 0, q = j / ys.per;
+        yr[b] = ys.p[q] + (long long)(j - q * ys.per) * sy;
+    }
     T tot[TI][TJ], run[TI][TJ];
 #pragma unroll
     for (int a = 0; a < TI; ++a)
@@ -59,7 +90,7 @@ __global__ void __launch_bounds__(256, 2) gram_tiled(const T *__restrict__ X, lo
 #pragma unroll
         for (int a = 0; a < TI; ++a) xv[a] = (i0 + a < nx) ? X[(i0 + a) * sx + e] : T(0);
 #pragma unroll
-        for (int b = 0; b < TJ; ++b) yv[b] = (j0 + b < ny) ? Y[(j0 + b) * sy + e] : T(0);
+        for (int b = 0; b < TJ; ++b) yv[b] = (j0 + b < ny) ? yr[b][e] : T(0);
 #pragma unroll
         for (int a = 0; a < TI; ++a)
 #pragma unroll
@@ -938,15 +969,35 @@ int trace_slices(long long len, int want, int cap) {
 template <typename T>
 void gram(cudaStream_t st, const T *X, long long sx, int nx, const T *Y, long long sy, int ny,
           long long len, double *G, double *scratch) {
-    const int pairs = nx * ny;
-    if (pairs <= 0) return;
-    if (nx > 64 || ny > 64) throw CudaError{cudaErrorInvalidValue, "gram: too many matrices"};
+    gram_multi<T>(st, X, sx, nx, 1, &Y, sy, ny, len, &G, scratch);
+}
+
+template <typename T>
+void gram_multi(cudaStream_t st, const T *X, long long sx, int nx, int nset, const T *const *Y, long long sy,
+                int per, long long len, double *const *G, double *scratch) {
+    if (nx <= 0 || per <= 0 || nset < 1) return;
+    if (nset > 4 || nx * per > 64 * 32) throw CudaError{cudaErrorInvalidValue, "gram: too many matrices"};
+    if (nx * per * nset > 64 * 32) {
+        // the partial sums of all pairs must fit the scratch: split the sets
+        const int h = nset / 2;
+        gram_multi<T>(st, X, sx, nx, h, Y, sy, per, len, G, scratch);
+        gram_multi<T>(st, X, sx, nx, nset - h, Y + h, sy, per, len, G + h, scratch);
+        return;
+    }
+    const int ny = nset * per, pairs = nx * ny;
     ProfScope ps(st, ST_TRACE, 2.0 * pairs * (double)len, sizeof(T) * (double)(nx + ny) * len);
+    YSet<T> ys{};
+    GOut go{};
+    for (int q = 0; q < 4; ++q) {
+        ys.p[q] = q < nset ? Y[q] : Y[0];
+        go.g[q] = q < nset ? G[q] : G[0];
+    }
+    ys.per = per;
     const int ti = (nx + TI - 1) / TI, tj = (ny + TJ - 1) / TJ;
     const int slices = trace_slices(len, TRACE_SLICES, 2 * TRACE_SLICES);
-    gram_tiled<T><<<dim3(ti * tj, slices), 256, 0, st>>>(X, sx, nx, Y, sy, ny, len, tj, scratch, pairs);
+    gram_tiled<T><<<dim3(ti * tj, slices), 256, 0, st>>>(X, sx, nx, ys, sy, ny, len, tj, scratch, pairs);
     check_launch("gram_tiled");
-    gram_final<<<(pairs + 7) / 8, 256, 0, st>>>(scratch, slices, pairs, G);
+    gram_final_multi<<<(pairs + 7) / 8, 256, 0, st>>>(scratch, slices, pairs, ny, per, go);
     check_launch("gram_final");
 }
 
@@ -1071,6 +1122,8 @@ void subspace(cudaStream_t st, int k, const double *A, double *omega, double *pa
 #define INST(T)                                                                                   \
     template void gram<T>(cudaStream_t, const T *, long long, int, const T *, long long, int,      \
                           long long, double *, double *);                                         \
+    template void gram_multi<T>(cudaStream_t, const T *, long long, int, int, const T *const *,     \
+                                long long, int, long long, double *const *, double *);            \
     template void dots<T>(cudaStream_t, const T *, long long, const T *, long long, int, long long, \
                           double *, double *);                                                    \
     template void combine<T>(cudaStream_t, const double *, int, int, int, const T *, long long,    \

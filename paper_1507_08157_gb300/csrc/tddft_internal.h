@@ -125,6 +125,11 @@ long long gram_scratch_doubles(int nx, int ny);
 template <typename T>
 void gram(cudaStream_t st, const T *X, long long sx, int nx, const T *Y, long long sy, int ny,
           long long len, double *G, double *scratch);
+// several Gram matrices of one X at once: Y[q] (q < nset <= 4) holds `per` rows of stride sy and
+// G[q] receives [nx][per]; X is read once for all of them
+template <typename T>
+void gram_multi(cudaStream_t st, const T *X, long long sx, int nx, int nset, const T *const *Y, long long sy,
+                int per, long long len, double *const *G, double *scratch);
 
 // out_i = beta * out_i + sum_j C[i*ldc + j] * in_j (C float64 on the device), out != in.
 template <typename T>
