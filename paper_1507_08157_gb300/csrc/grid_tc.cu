@@ -35,8 +35,8 @@ struct __align__(8) DensShared {
     int abort;
 };
 
-constexpr int DENS_THREADS = 256;      // warps 0-3 gather + epilogue, 4 TMA, 5 MMA, 6-7 gather
-constexpr int DENS_GATHER = 192;       // gathering threads: warps 0-3 and 6-7
+constexpr int DENS_THREADS = 384;      // warps 0-3 and 8-11 gather + epilogue, 4 TMA, 5 MMA, 6-7 gather
+constexpr int DENS_GATHER = 320;       // gathering threads: warps 0-3 and 6-11
 constexpr int DENS_STAGES = 4;         // chi-block ring (16 KB each)
 constexpr int DENS_KBMAX = 16;         // K blocks of the gathered P block (CK <= 1024)
 
@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(DENS_THREADS, 1) density_tc_kernel(
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(&ctl->acc_full[i], 1);
-            mbar_init(&ctl->acc_empty[i], 128);
+            mbar_init(&ctl->acc_empty[i], 256);
         }
         for (int i = 0; i < DENS_KBMAX; ++i) mbar_init(&ctl->b_ready[i], DENS_GATHER);
         ctl->abort = 0;
@@ -244,17 +244,25 @@ __global__ void __launch_bounds__(DENS_THREADS, 1) density_tc_kernel(
         }
         signal_upto(KB);
     }
-    if (warp < 4) {
-        // epilogue: rho_s(r) = sum_b T[r][(s,b)] phi_b(r) for the 128 points of block pb
+    if (warp < 4 || warp >= 8) {
+        // epilogue: rho_s(r) = sum_b T[r][(s,b)] phi_b(r) for the 128 points of block pb. Two
+        // groups of four warps (0-3 and 8-11) read the same TMEM lanes (warp % 4 selects the
+        // quarter) and split the states: the first half of the group's states to one, the rest
+        // to the other
+        const int eg = warp < 4 ? 0 : 1, quarter = warp & 3;
+        const int gsplit = (gs + 1) / 2;
+        const bool aligned = NP % 32 == 0 && phi_pm != nullptr;
+        const int sbeg = aligned ? (eg ? gsplit : 0) : 0;
+        const int send = aligned ? (eg ? gs : gsplit) : (eg ? 0 : gs);
         for (int pb = 0; pb < TILE_PTS / 128; ++pb) {
             const int acc = pb & 1;
             const bool ok = mbar_wait(&ctl->acc_full[acc], (pb >> 1) & 1, abort) && !*abort;
             tc_fence_after();
-            const int lp = pb * 128 + warp * 32 + lane;
+            const int lp = pb * 128 + quarter * 32 + lane;
             float r[16];
 #pragma unroll
             for (int q = 0; q < 16; ++q) r[q] = 0.0f;
-            if (NP % 32 == 0) {
+            if (aligned) {
                 // every 32-column chunk belongs to one state: skip the chunks that are all padding
                 // (warp-uniform), prefetch the next chunk's phi while this chunk's columns come
                 // out of TMEM, and add one dot product per chunk
@@ -262,58 +270,50 @@ __global__ void __launch_bounds__(DENS_THREADS, 1) density_tc_kernel(
                     const int sl = cc / NP;
                     return sl < gs && cc - sl * NP < np;
                 };
-                auto load_phi = [&](int cc, float *dst) {
-                    const int b0 = cc - (cc / NP) * NP;
-                    if (phi_pm) {
-                        // point-major f16 phi [tile][point][NP] (zero past np): 32 values in four
-                        // 16-byte loads
-                        const uint4 *q = reinterpret_cast<const uint4 *>(
-                            phi_pm + ((long long)t * TILE_PTS + lp) * NP + b0);
+                const int cend = send * NP;
+                int c = sbeg * NP;
+                while (c < cend && !live(c)) c += 32;
+                // phi kept as float16 pairs in registers (16 per chunk) and widened at the dot
+                auto load_q = [&](int cc, uint4 *dst) {
+                    const uint4 *q = reinterpret_cast<const uint4 *>(
+                        phi_pm + ((long long)t * TILE_PTS + lp) * NP + (cc - (cc / NP) * NP));
 #pragma unroll
-                        for (int w = 0; w < 4; ++w) {
-                            const uint4 x = __ldg(q + w);
-                            const __half2 *h = reinterpret_cast<const __half2 *>(&x);
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                const float2 f2 = __half22float2(h[e]);
-                                dst[8 * w + 2 * e] = f2.x;
-                                dst[8 * w + 2 * e + 1] = f2.y;
-                            }
-                        }
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < 32; ++j)
-                            dst[j] = (b0 + j < np) ? pval[(long long)(p0 + b0 + j) * TILE_PTS + lp] : 0.0f;
-                    }
+                    for (int w = 0; w < 4; ++w) dst[w] = __ldg(q + w);
                 };
-                int c = 0;
-                while (c < NB && !live(c)) c += 32;
-                float ph[32];
-                if (c < NB) load_phi(c, ph);
-                while (c < NB) {
+                uint4 ph[4];
+                if (c < cend) load_q(c, ph);
+                while (c < cend) {
                     int cn = c + 32;
-                    while (cn < NB && !live(cn)) cn += 32;
-                    float phn[32];
-                    if (cn < NB) load_phi(cn, phn);
+                    while (cn < cend && !live(cn)) cn += 32;
+                    uint4 phn[4];
+                    if (cn < cend) load_q(cn, phn);
                     float v[32];
-                    tmem_ld32(tmem + acc * 256 + ((unsigned)(warp * 32) << 16) + (unsigned)c, v);
+                    tmem_ld32(tmem + acc * 256 + ((unsigned)(quarter * 32) << 16) + (unsigned)c, v);
                     float d = 0.0f;
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) d = fmaf(v[j], ph[j], d);
+                    for (int w = 0; w < 4; ++w) {
+                        const __half2 *h = reinterpret_cast<const __half2 *>(&ph[w]);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const float2 f2 = __half22float2(h[e]);
+                            d = fmaf(v[8 * w + 2 * e], f2.x, d);
+                            d = fmaf(v[8 * w + 2 * e + 1], f2.y, d);
+                        }
+                    }
                     const int sl = c / NP;
 #pragma unroll
                     for (int q = 0; q < 16; ++q)
                         if (q == sl) r[q] += d;
-                    if (cn < NB) {
+                    if (cn < cend) {
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) ph[j] = phn[j];
+                        for (int w = 0; w < 4; ++w) ph[w] = phn[w];
                     }
                     c = cn;
                 }
-            } else {
+            } else if (eg == 0) {
                 for (int c = 0; c < NB; c += 32) {
                     float v[32];
-                    tmem_ld32(tmem + acc * 256 + ((unsigned)(warp * 32) << 16) + (unsigned)c, v);
+                    tmem_ld32(tmem + acc * 256 + ((unsigned)(quarter * 32) << 16) + (unsigned)c, v);
                     float ph[32];
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(DENS_THREADS, 1) density_tc_kernel(
                 const long long gi = ((long long)gx * n + gy) * n + gz;
 #pragma unroll
                 for (int q = 0; q < 16; ++q)
-                    if (q < gs) rho[(long long)(s0 + q) * n3 + gi] = r[q] / pscale[s0 + q];
+                    if (q >= sbeg && q < send) rho[(long long)(s0 + q) * n3 + gi] = r[q] / pscale[s0 + q];
             }
         }
     }
