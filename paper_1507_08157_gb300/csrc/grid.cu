@@ -267,39 +267,67 @@ __device__ __forceinline__ void small_dft(int R, V *v) {
     }
 }
 
+// Per-CTA tables of a plan, built once before the transforms: the stage twiddles
+// tw[off_s + kk (R - 1) + r - 1] = exp(-2 pi i kk r / (Ns R)) (forward sign; the inverse takes the
+// conjugate) and kk = j mod Ns for every butterfly index j of every stage. The transforms then
+// look these up instead of evaluating sines and dividing per element.
+constexpr int FFT_KK_BYTES = 2048;      // sum over stages of n / R (n <= 256)
+
+template <typename T>
+__device__ void fft_tables(const Plan &pl, typename C2<T>::t *tw, unsigned char *kkt) {
+    const int n = pl.n;
+    int Ns = 1, toff = 0, koff = 0;
+    for (int st = 0; st < pl.nst; ++st) {
+        const int R = pl.radix[st], nb = n / R;
+        for (int i = threadIdx.x; i < Ns * (R - 1); i += blockDim.x) {
+            const int kk = i / (R - 1), r = i - kk * (R - 1) + 1;
+            T sn, cs;
+            sincospi_t<T>(T(-2) * T(kk * r) / T(Ns * R), &sn, &cs);
+            tw[toff + i] = {cs, sn};
+        }
+        for (int jj = threadIdx.x; jj < nb; jj += blockDim.x) kkt[koff + jj] = (unsigned char)(jj % Ns);
+        toff += Ns * (R - 1);
+        koff += nb;
+        Ns *= R;
+    }
+}
+
 // FFT of `lines` lines of length n held at buf0 (line-major); returns the buffer with the result.
+// blockDim.x / lines threads work on each line (lines divides blockDim.x).
 template <typename T, int SG>
 __device__ typename C2<T>::t *fft_lines(typename C2<T>::t *buf0, typename C2<T>::t *buf1, int lines,
-                                        const Plan &pl) {
+                                        const Plan &pl, const typename C2<T>::t *tw, const unsigned char *kkt) {
     using V = typename C2<T>::t;
     V *in = buf0, *out = buf1;
     const int n = pl.n;
-    int Ns = 1;
+    const int tpl = blockDim.x / lines;
+    const int line = threadIdx.x / tpl, t0 = threadIdx.x - line * tpl;
+    int Ns = 1, toff = 0, koff = 0;
     for (int st = 0; st < pl.nst; ++st) {
         const int R = pl.radix[st];
         const int nb = n / R;
-        for (int idx = threadIdx.x; idx < lines * nb; idx += blockDim.x) {
-            const int line = idx / nb, j = idx - line * nb;
+        if (line < lines) {
             const V *src = in + line * n;
             V *dst = out + line * n;
-            V v[5];
-            for (int r = 0; r < R; ++r) v[r] = src[j + r * nb];
-            const int kk = j % Ns;
-            if (Ns > 1) {
-                for (int r = 1; r < R; ++r) {
-                    T sn, cs;
-                    sincospi_t<T>(T(2 * SG) * T(kk * r) / T(Ns * R), &sn, &cs);
-                    v[r] = cmul(v[r], cs, sn);
+            for (int j = t0; j < nb; j += tpl) {
+                V v[5];
+                for (int r = 0; r < R; ++r) v[r] = src[j + r * nb];
+                const int kk = kkt[koff + j];
+                if (Ns > 1) {
+                    const V *w = tw + toff + kk * (R - 1) - 1;
+                    for (int r = 1; r < R; ++r) v[r] = cmul(v[r], w[r].x, SG < 0 ? w[r].y : -w[r].y);
                 }
+                small_dft<T, SG>(R, v);
+                const int base = (j - kk) * R + kk;
+                for (int r = 0; r < R; ++r) dst[base + r * Ns] = v[r];
             }
-            small_dft<T, SG>(R, v);
-            const int base = (j / Ns) * Ns * R + kk;
-            for (int r = 0; r < R; ++r) dst[base + r * Ns] = v[r];
         }
         __syncthreads();
         V *tmp = in;
         in = out;
         out = tmp;
+        toff += Ns * (R - 1);
+        koff += nb;
         Ns *= R;
     }
     return in;
@@ -314,7 +342,9 @@ __global__ void __launch_bounds__(256) fft_z_forward_real(Plan pl, const T *__re
     using V = typename C2<T>::t;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = pl.n, L = lines_per_cta<T>();
-    V *b0 = reinterpret_cast<V *>(smem_raw), *b1 = b0 + L * n;
+    V *b0 = reinterpret_cast<V *>(smem_raw), *b1 = b0 + L * n, *tw = b1 + L * n;
+    unsigned char *kkt = reinterpret_cast<unsigned char *>(tw + n);
+    fft_tables<T>(pl, tw, kkt);
     const long long n3 = (long long)n * n * n;
     const int pair = blockIdx.y;
     const long long line0 = (long long)blockIdx.x * L;
@@ -333,7 +363,7 @@ __global__ void __launch_bounds__(256) fft_z_forward_real(Plan pl, const T *__re
         b0[i] = v;
     }
     __syncthreads();
-    V *res = fft_lines<T, -1>(b0, b1, L, pl);
+    V *res = fft_lines<T, -1>(b0, b1, L, pl, tw, kkt);
     V *w = work + (long long)pair * n3;
     for (int i = threadIdx.x; i < L * n; i += blockDim.x) {
         const int l = i / n, j = i - l * n;
@@ -350,7 +380,9 @@ __global__ void __launch_bounds__(256) fft_z_inverse_real(Plan pl, const typenam
     using Vc = typename C2<T>::t;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = pl.n, L = lines_per_cta<T>();
-    Vc *b0 = reinterpret_cast<Vc *>(smem_raw), *b1 = b0 + L * n;
+    Vc *b0 = reinterpret_cast<Vc *>(smem_raw), *b1 = b0 + L * n, *tw = b1 + L * n;
+    unsigned char *kkt = reinterpret_cast<unsigned char *>(tw + n);
+    fft_tables<T>(pl, tw, kkt);
     const long long n3 = (long long)n * n * n;
     const int pair = blockIdx.y;
     const long long line0 = (long long)blockIdx.x * L;
@@ -361,7 +393,7 @@ __global__ void __launch_bounds__(256) fft_z_inverse_real(Plan pl, const typenam
         b0[i] = (line0 + l < nlines) ? w[(line0 + l) * n + j] : Vc{T(0), T(0)};
     }
     __syncthreads();
-    Vc *res = fft_lines<T, +1>(b0, b1, L, pl);
+    Vc *res = fft_lines<T, +1>(b0, b1, L, pl, tw, kkt);
     const bool has_b = 2 * pair + 1 < k;
     for (int i = threadIdx.x; i < L * n; i += blockDim.x) {
         const int l = i / n, j = i - l * n;
@@ -386,7 +418,9 @@ __global__ void __launch_bounds__(256) fft_strided(Plan pl, typename C2<T>::t *_
     using V = typename C2<T>::t;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = pl.n, W = lines_per_cta<T>();
-    V *b0 = reinterpret_cast<V *>(smem_raw), *b1 = b0 + W * n;
+    V *b0 = reinterpret_cast<V *>(smem_raw), *b1 = b0 + W * n, *tw = b1 + W * n;
+    unsigned char *kkt = reinterpret_cast<unsigned char *>(tw + n);
+    fft_tables<T>(pl, tw, kkt);
     const long long n3 = (long long)n * n * n;
     const int pair = blockIdx.z;
     const int o = blockIdx.y;            // x index (AXIS 1) or y index (AXIS 0)
@@ -403,9 +437,9 @@ __global__ void __launch_bounds__(256) fft_strided(Plan pl, typename C2<T>::t *_
     __syncthreads();
     V *res;
     if (!POISSON) {
-        res = fft_lines<T, SG>(b0, b1, W, pl);
+        res = fft_lines<T, SG>(b0, b1, W, pl, tw, kkt);
     } else {
-        res = fft_lines<T, -1>(b0, b1, W, pl);
+        res = fft_lines<T, -1>(b0, b1, W, pl, tw, kkt);
         const T inv_n3 = T(1) / T(n3);
         for (int i = threadIdx.x; i < W * n; i += blockDim.x) {
             const int w = i / n, j = i - w * n;
@@ -420,7 +454,7 @@ __global__ void __launch_bounds__(256) fft_strided(Plan pl, typename C2<T>::t *_
         }
         __syncthreads();
         V *other = (res == b0) ? b1 : b0;
-        res = fft_lines<T, +1>(res, other, W, pl);
+        res = fft_lines<T, +1>(res, other, W, pl, tw, kkt);
     }
     for (int i = threadIdx.x; i < W * n; i += blockDim.x) {
         const int j = i / W, w = i - j * W;
@@ -517,9 +551,9 @@ void hartree_fxc(cudaStream_t st, const GridShape &g, const T *rho, const T *fxc
     const int pairs = (k + 1) / 2;
     const double n3d = (double)n * n * n;
     ProfScope ps(st, ST_FFT, pairs * 2.0 * 5.0 * n3d * std::log2(n3d), sizeof(T) * (2.0 * k + 1.0) * n3d);
-    const size_t sm = 2 * (size_t)L * n * sizeof(Vc);
+    const size_t sm = (2 * (size_t)L * n + n) * sizeof(Vc) + FFT_KK_BYTES;
     static const bool attr = [&]() {   // once per process, thread-safe
-        const int mx = 2 * L * 256 * (int)sizeof(Vc);
+        const int mx = (2 * L * 256 + 256) * (int)sizeof(Vc) + FFT_KK_BYTES;
         check(cudaFuncSetAttribute(fft_z_forward_real<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx), "attr fz");
         check(cudaFuncSetAttribute(fft_z_inverse_real<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx), "attr iz");
         check(cudaFuncSetAttribute(fft_strided<T, 1, -1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx), "attr fy");
