@@ -292,10 +292,10 @@ __device__ void fft_tables(const Plan &pl, typename C2<T>::t *tw, unsigned char 
     }
 }
 
-// FFT of `lines` lines of length n held at buf0 (line-major); returns the buffer with the result.
-// blockDim.x / lines threads work on each line (lines divides blockDim.x).
+// FFT of `lines` lines of length n held at buf0 (line-major, lines ld >= n apart); returns the
+// buffer with the result. blockDim.x / lines threads work on each line (lines divides blockDim.x).
 template <typename T, int SG>
-__device__ typename C2<T>::t *fft_lines(typename C2<T>::t *buf0, typename C2<T>::t *buf1, int lines,
+__device__ typename C2<T>::t *fft_lines(typename C2<T>::t *buf0, typename C2<T>::t *buf1, int lines, int ld,
                                         const Plan &pl, const typename C2<T>::t *tw, const unsigned char *kkt) {
     using V = typename C2<T>::t;
     V *in = buf0, *out = buf1;
@@ -307,8 +307,8 @@ __device__ typename C2<T>::t *fft_lines(typename C2<T>::t *buf0, typename C2<T>:
         const int R = pl.radix[st];
         const int nb = n / R;
         if (line < lines) {
-            const V *src = in + line * n;
-            V *dst = out + line * n;
+            const V *src = in + line * ld;
+            V *dst = out + line * ld;
             for (int j = t0; j < nb; j += tpl) {
                 V v[5];
                 for (int r = 0; r < R; ++r) v[r] = src[j + r * nb];
@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(256) fft_z_forward_real(Plan pl, const T *__re
         b0[i] = v;
     }
     __syncthreads();
-    V *res = fft_lines<T, -1>(b0, b1, L, pl, tw, kkt);
+    V *res = fft_lines<T, -1>(b0, b1, L, n, pl, tw, kkt);
     V *w = work + (long long)pair * n3;
     for (int i = threadIdx.x; i < L * n; i += blockDim.x) {
         const int l = i / n, j = i - l * n;
@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(256) fft_z_inverse_real(Plan pl, const typenam
         b0[i] = (line0 + l < nlines) ? w[(line0 + l) * n + j] : Vc{T(0), T(0)};
     }
     __syncthreads();
-    Vc *res = fft_lines<T, +1>(b0, b1, L, pl, tw, kkt);
+    Vc *res = fft_lines<T, +1>(b0, b1, L, n, pl, tw, kkt);
     const bool has_b = 2 * pair + 1 < k;
     for (int i = threadIdx.x; i < L * n; i += blockDim.x) {
         const int l = i / n, j = i - l * n;
@@ -418,7 +418,10 @@ __global__ void __launch_bounds__(256) fft_strided(Plan pl, typename C2<T>::t *_
     using V = typename C2<T>::t;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = pl.n, W = lines_per_cta<T>();
-    V *b0 = reinterpret_cast<V *>(smem_raw), *b1 = b0 + W * n, *tw = b1 + W * n;
+    // lines n + 1 apart: the transposing loads and stores (consecutive threads, consecutive
+    // lines) then hit distinct banks
+    const int ld = n + 1;
+    V *b0 = reinterpret_cast<V *>(smem_raw), *b1 = b0 + W * ld, *tw = b1 + W * ld;
     unsigned char *kkt = reinterpret_cast<unsigned char *>(tw + n);
     fft_tables<T>(pl, tw, kkt);
     const long long n3 = (long long)n * n * n;
@@ -432,14 +435,14 @@ __global__ void __launch_bounds__(256) fft_strided(Plan pl, typename C2<T>::t *_
         const int j = i / W, w = i - j * W;    // consecutive threads -> consecutive z
         V v = {T(0), T(0)};
         if (w0 + w < n) v = data[(long long)j * s + w0 + w];
-        b0[w * n + j] = v;
+        b0[w * ld + j] = v;
     }
     __syncthreads();
     V *res;
     if (!POISSON) {
-        res = fft_lines<T, SG>(b0, b1, W, pl, tw, kkt);
+        res = fft_lines<T, SG>(b0, b1, W, ld, pl, tw, kkt);
     } else {
-        res = fft_lines<T, -1>(b0, b1, W, pl, tw, kkt);
+        res = fft_lines<T, -1>(b0, b1, W, ld, pl, tw, kkt);
         const T inv_n3 = T(1) / T(n3);
         for (int i = threadIdx.x; i < W * n; i += blockDim.x) {
             const int w = i / n, j = i - w * n;
@@ -449,16 +452,16 @@ __global__ void __launch_bounds__(256) fft_strided(Plan pl, typename C2<T>::t *_
             const int mz = zz <= n / 2 ? zz : zz - n;
             const T g2 = two_pi_over_L * two_pi_over_L * T(mx * mx + my * my + mz * mz);
             const T kern = (mx == 0 && my == 0 && mz == 0) ? T(0) : T(4.0 * 3.14159265358979323846) / g2 * inv_n3;
-            res[i].x *= kern;
-            res[i].y *= kern;
+            res[w * ld + j].x *= kern;
+            res[w * ld + j].y *= kern;
         }
         __syncthreads();
         V *other = (res == b0) ? b1 : b0;
-        res = fft_lines<T, +1>(res, other, W, pl, tw, kkt);
+        res = fft_lines<T, +1>(res, other, W, ld, pl, tw, kkt);
     }
     for (int i = threadIdx.x; i < W * n; i += blockDim.x) {
         const int j = i / W, w = i - j * W;
-        if (w0 + w < n) data[(long long)j * s + w0 + w] = res[w * n + j];
+        if (w0 + w < n) data[(long long)j * s + w0 + w] = res[w * ld + j];
     }
 }
 
@@ -551,9 +554,9 @@ void hartree_fxc(cudaStream_t st, const GridShape &g, const T *rho, const T *fxc
     const int pairs = (k + 1) / 2;
     const double n3d = (double)n * n * n;
     ProfScope ps(st, ST_FFT, pairs * 2.0 * 5.0 * n3d * std::log2(n3d), sizeof(T) * (2.0 * k + 1.0) * n3d);
-    const size_t sm = (2 * (size_t)L * n + n) * sizeof(Vc) + FFT_KK_BYTES;
+    const size_t sm = (2 * (size_t)L * (n + 1) + n) * sizeof(Vc) + FFT_KK_BYTES;
     static const bool attr = [&]() {   // once per process, thread-safe
-        const int mx = (2 * L * 256 + 256) * (int)sizeof(Vc) + FFT_KK_BYTES;
+        const int mx = (2 * L * 257 + 256) * (int)sizeof(Vc) + FFT_KK_BYTES;
         check(cudaFuncSetAttribute(fft_z_forward_real<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx), "attr fz");
         check(cudaFuncSetAttribute(fft_z_inverse_real<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx), "attr iz");
         check(cudaFuncSetAttribute(fft_strided<T, 1, -1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx), "attr fy");
