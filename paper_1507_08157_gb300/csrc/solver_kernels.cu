@@ -62,10 +62,10 @@ struct YSet {
 // sums the partials over slices in float64. float64 arithmetic is scarce on this part, so it is
 // kept off the per-element path.
 constexpr int RUN = 32;
-constexpr int TI = 4, TJ = 4;
+constexpr int TI = 4, TJ = 8;
 
 template <typename T>
-__global__ void __launch_bounds__(256, 3) gram_tiled(const T *__restrict__ X, long long sx, int nx,
+__global__ void __launch_bounds__(256, 2) gram_tiled(const T *__restrict__ X, long long sx, int nx,
                                                      const YSet<T> ys, long long sy, int ny,
                                                      long long len, int tiles_j, double *__restrict__ partial,
                                                      int pairs) {
