@@ -1161,8 +1161,10 @@ void evaluate(tddft_ctx *c, tddft_state *S) {
     check(cudaMemcpyAsync(B.g, B.f, 2 * k * len * sizeof(T), cudaMemcpyDeviceToDevice, st), "copy g");
     combine<T>(st, B.coef, 2 * k, 2 * k, 2 * k, B.P, len, B.g, len, len, true);
     if (c->trunc) {
-        // G_L = mask * (S P^c S) g (S P^v S); residual = Frobenius norm
-        sandwich<T>(c, 2 * k, I.Ac, B.g, I.Av, B.G1, B.tmp);
+        // G_L = mask * (S P^c S) g (S P^v S); residual = Frobenius norm. With the exact
+        // preconditioner G_L only steers the search (its error changes the direction and the
+        // residual's last digits, not the fixed point, where g = 0): one TF32 MMA per product
+        sandwich<T>(c, 2 * k, I.Ac, B.g, I.Av, B.G1, B.tmp, I.exact);
         mask_mul<T>(st, B.G1, I.mask, len, 2 * k);
         dots<T>(st, B.G1, len, B.G1, len, 2 * k, len, B.dvec, B.gscr);
     } else {
