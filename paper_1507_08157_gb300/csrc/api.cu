@@ -211,6 +211,8 @@ struct Impl {
     unsigned short *chi_fm16 = nullptr;   // function-major f16 chi tables [slot][512]
     unsigned short *phi_fm16 = nullptr;   // function-major f16 phi tables [slot][512]
     unsigned short *phi_pm = nullptr;     // point-major f16 phi tables [tile][512][NPmax], zero padded
+    int *live_tiles = nullptr;            // tiles with both chi and phi (the persistent density's items)
+    int nlive = 0;
     int CK = 0, NPmax = 0, nslots_chi = 0, nslots_phi = 0, maxc = 0;
     bool grid_tc = false, integrals_tc = false;
     bool phi_quads = false;   // every tile's phi list is whole aligned groups of 4 (vector gather)
@@ -287,7 +289,8 @@ void potential_integrals_tc(cudaStream_t st, const GridShape &g, const TileSet<f
 void response_density_tc(cudaStream_t st, const GridShape &g, const TileSet<float> &chi,
                          const TileSet<float> &phi, const unsigned short *chi_pm, int CK, int NPmax, int nphi,
                          const float *P, long long sP, int k, float *rho, unsigned *scratch_bits,
-                         float *scale, int *err, bool phi_quads, const unsigned short *phi_pm);
+                         float *scale, int *err, bool phi_quads, const unsigned short *phi_pm,
+                         const int *live_tiles, int nlive);
 int noalloc_max_states();
 void response_density_tc_noalloc(cudaStream_t st, const GridShape &g, const TileSet<float> &chi,
                                  const TileSet<float> &phi, const unsigned short *chi_pm, int CK, int NPmax,
@@ -547,7 +550,8 @@ void density(tddft_ctx *c, Impl<T> &I, const T *P, int ns) {
     if constexpr (sizeof(T) == 4) {
         if (I.grid_tc) {
             response_density_tc(c->st, c->grid(), I.chi, I.phi, I.chi_pm, I.CK, I.NPmax, c->nv, P, c->len(), ns,
-                                I.rho, I.tc_bits, I.tc_scale, tc_error_word(), I.phi_quads, I.phi_pm);
+                                I.rho, I.tc_bits, I.tc_scale, tc_error_word(), I.phi_quads, I.phi_pm,
+                                I.live_tiles, I.nlive);
             return;
         }
     }
@@ -783,6 +787,16 @@ void build_impl(tddft_ctx *c, const tddft_system *s) {
                 check(cudaMemcpy(I->chi_pm, pm.data(), pm.size() * sizeof(unsigned short), cudaMemcpyHostToDevice),
                       "upload point-major chi");
                 I->CK = CK;
+                {
+                    std::vector<int> live;
+                    for (int t = 0; t < ntl; ++t)
+                        if (coff[t + 1] > coff[t] && poff[t + 1] > poff[t]) live.push_back(t);
+                    I->nlive = (int)live.size();
+                    I->live_tiles = I->mem.template alloc<int>(std::max<size_t>(1, live.size()));
+                    if (!live.empty())
+                        check(cudaMemcpy(I->live_tiles, live.data(), live.size() * sizeof(int), cudaMemcpyHostToDevice),
+                              "upload live tiles");
+                }
                 // phi tables on the host once: point-major f16 for the density epilogue (and the
                 // function-major f16 copy of the integrals below)
                 std::vector<float> pv((size_t)poff[ntl] * TILE_PTS);

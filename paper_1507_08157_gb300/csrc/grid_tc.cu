@@ -17,6 +17,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <mutex>
 
 namespace tddft {
@@ -350,6 +351,247 @@ __global__ void __launch_bounds__(DENS_THREADS, 1) density_tc_kernel(
     if (threadIdx.x == 0 && ctl->abort) atomicExch(err, 1);
 }
 
+// ------------------------------------------------------------------------------------------------
+// Persistent variant: one CTA per SM walks a list of work items (tile, state) and overlaps the
+// P-block gather of its next item with the MMAs and epilogue of the current one (two B buffers).
+// 512 threads: warps 0-3 and 8-11 are the epilogue groups (accumulator 0 / 1, i.e. even / odd
+// 128-point blocks, on the TMEM lanes warp % 4), warp 4 the TMA producer, warp 5 the MMA issuer,
+// warps 6-7 and 12-15 gather. For systems whose tile phi lists are whole aligned atom quads, one
+// state per item (NB = NP <= 128) and at most PDENS_KB K blocks of 64 chi per tile.
+constexpr int PDENS_THREADS = 512;
+constexpr int PDENS_GATHER = 192;      // warps 6-7 and 12-15
+constexpr int PDENS_STAGES = 4;        // chi-block ring (16 KB each)
+constexpr int PDENS_KB = 5;            // K blocks per B buffer (2 x 5 x 16 KB + ring = 224 KB)
+
+struct __align__(8) PDensShared {
+    unsigned long long a_full[PDENS_STAGES];
+    unsigned long long a_empty[PDENS_STAGES];
+    unsigned long long acc_full[2];
+    unsigned long long acc_empty[2];
+    unsigned long long b_full[2];
+    unsigned long long b_free[2];
+    unsigned int tmem_base;
+    int abort;
+};
+
+__device__ __forceinline__ int pgather_rank(int warp, int lane) {
+    return (warp < 8 ? warp - 6 : warp - 10) * 32 + lane;   // warps 6, 7, 12-15 -> 0 .. 191
+}
+
+__global__ void __launch_bounds__(PDENS_THREADS, 1) density_tc_persistent_kernel(
+    const __grid_constant__ CUtensorMap mX,   // point-major chi: [tile*512 + point][CK] f16
+    int n, int nt, int NP, int k, const int *__restrict__ items_tiles, int nitems,
+    const int *__restrict__ coff, const int *__restrict__ cids, const int *__restrict__ poff,
+    const int *__restrict__ pids, int nphi, const unsigned short *__restrict__ phi_pm,
+    const float *__restrict__ P, long long sP, const float *__restrict__ pscale, float *__restrict__ rho,
+    int *err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *base = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<unsigned long long>(smem_raw) + 1023ull) & ~1023ull);
+    const int NB = NP;
+    unsigned char *A = base;                                      // ring [STAGES][128 x 128 B]
+    unsigned char *Bb = base + PDENS_STAGES * 16384;              // [2][PDENS_KB][NB x 128 B]
+    const size_t bsize = (size_t)PDENS_KB * NB * 128;
+    PDensShared *ctl = reinterpret_cast<PDensShared *>(Bb + 2 * bsize);
+    volatile int *abort = &ctl->abort;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long n3 = (long long)n * n * n;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < PDENS_STAGES; ++i) {
+            mbar_init(&ctl->a_full[i], 1);
+            mbar_init(&ctl->a_empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&ctl->acc_full[i], 1);
+            mbar_init(&ctl->acc_empty[i], 128);
+            mbar_init(&ctl->b_full[i], PDENS_GATHER);
+            mbar_init(&ctl->b_free[i], 1);
+        }
+        ctl->abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 5) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&ctl->tmem_base)),
+                     "r"(256));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = ctl->tmem_base;
+    // items of this CTA: it = blockIdx.x + j * gridDim.x; item -> (tile list entry it / k, state it % k)
+
+    if (warp == 4) {
+        // TMA producer: for every item, the chi blocks (pb, kb) through the ring
+        if (lane == 0) {
+            long long q = 0;
+            for (int it = blockIdx.x; it < nitems && !*abort; it += gridDim.x) {
+                const int t = items_tiles[it / k];
+                const int KB = (coff[t + 1] - coff[t] + 63) / 64;
+                for (int pb = 0; pb < TILE_PTS / 128; ++pb)
+                    for (int kb = 0; kb < KB; ++kb, ++q) {
+                        const int st = (int)(q % PDENS_STAGES);
+                        const long long use = q / PDENS_STAGES;
+                        if (use > 0 && !mbar_wait(&ctl->a_empty[st], (unsigned)((use - 1) & 1), abort)) break;
+                        mbar_expect_tx(&ctl->a_full[st], 16384);
+                        tma_load_2d(A + st * 16384, &mX, &ctl->a_full[st], kb * 64, t * TILE_PTS + pb * 128);
+                    }
+            }
+        }
+    } else if (warp == 5) {
+        // MMA issuer
+        if (lane == 0) {
+            const unsigned idesc = idesc_f16(128, NB);
+            long long q = 0, pbg = 0;
+            int j = 0;
+            bool ok = true;
+            for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x, ++j) {
+                const int t = items_tiles[it / k];
+                const int KB = (coff[t + 1] - coff[t] + 63) / 64;
+                const int buf = j & 1;
+                if (!mbar_wait(&ctl->b_full[buf], (unsigned)((j >> 1) & 1), abort)) break;
+                tc_fence_after();
+                const unsigned char *B = Bb + buf * bsize;
+                for (int pb = 0; pb < TILE_PTS / 128 && ok; ++pb, ++pbg) {
+                    const int acc = (int)(pbg & 1);
+                    const long long ause = pbg >> 1;
+                    if (ause > 0 && !mbar_wait(&ctl->acc_empty[acc], (unsigned)((ause - 1) & 1), abort)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    for (int kb = 0; kb < KB; ++kb, ++q) {
+                        const int st = (int)(q % PDENS_STAGES);
+                        if (!mbar_wait(&ctl->a_full[st], (unsigned)((q / PDENS_STAGES) & 1), abort)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const unsigned a = smem_u32(A + st * 16384), bb = smem_u32(B + (size_t)kb * NB * 128);
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk)
+                            mma_f16(tmem + acc * 128, smem_desc(a + kk * 32), smem_desc(bb + kk * 32), idesc,
+                                    (kb > 0 || kk > 0) ? 1u : 0u);
+                        mma_commit(&ctl->a_empty[st]);
+                    }
+                    if (!ok) break;
+                    mma_commit(&ctl->acc_full[acc]);
+                }
+                if (!ok) break;
+                mma_commit(&ctl->b_free[buf]);   // this item's B buffer is free once its MMAs finish
+            }
+        }
+    } else if ((warp >= 6 && warp < 8) || warp >= 12) {
+        // gather the P block of each item into B[j % 2] by phi quads (aligned groups of four)
+        const int rank = pgather_rank(warp, lane);
+        int j = 0;
+        for (int it = blockIdx.x; it < nitems; it += gridDim.x, ++j) {
+            const int t = items_tiles[it / k], s = it % k;
+            const int c0 = coff[t], nc = coff[t + 1] - c0;
+            const int p0 = poff[t], np = poff[t + 1] - p0;
+            const int KB = (nc + 63) / 64;
+            const int buf = j & 1;
+            if (j >= 2 && !mbar_wait(&ctl->b_free[buf], (unsigned)(((j >> 1) - 1) & 1), abort)) break;
+            unsigned char *B = Bb + buf * bsize;
+            const float sc = pscale[s];
+            const float *Ps = P + (long long)s * sP;
+            const int nq = NB / 4, total = nq * KB * 8;
+            for (int i0 = rank; i0 < total; i0 += 2 * PDENS_GATHER) {
+                float4 v[2][8];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int idx = i0 + u * PDENS_GATHER;
+                    const int qd = idx % nq, ch = idx / nq;
+                    const bool live = idx < total && qd * 4 < np;
+                    const float *Pq = Ps + (live ? pids[p0 + qd * 4] : 0);
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const int a = (ch >> 3) * 64 + (ch & 7) * 8 + e;
+                        v[u][e] = (live && a < nc) ? __ldg(reinterpret_cast<const float4 *>(Pq + (long long)cids[c0 + a] * nphi))
+                                                   : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int idx = i0 + u * PDENS_GATHER;
+                    if (idx >= total) continue;
+                    const int qd = idx % nq, ch = idx / nq;
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        unsigned short h[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            const float x = r == 0 ? v[u][e].x : r == 1 ? v[u][e].y : r == 2 ? v[u][e].z : v[u][e].w;
+                            h[e] = __half_as_ushort(__float2half_rn(x * sc));
+                        }
+                        uint4 qv;
+                        qv.x = h[0] | ((unsigned)h[1] << 16);
+                        qv.y = h[2] | ((unsigned)h[3] << 16);
+                        qv.z = h[4] | ((unsigned)h[5] << 16);
+                        qv.w = h[6] | ((unsigned)h[7] << 16);
+                        *reinterpret_cast<uint4 *>(B + (size_t)(ch >> 3) * NB * 128 + sw128_offset(qd * 4 + r, ch & 7)) = qv;
+                    }
+                }
+            }
+            fence_async_smem();
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ctl->b_full[buf])) : "memory");
+        }
+    } else {
+        // epilogue groups: warps 0-3 take accumulator 0 (even point blocks), warps 8-11 accumulator 1
+        const int eg = warp < 4 ? 0 : 1, quarter = warp & 3;
+        long long ause = 0;
+        for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+            const int t = items_tiles[it / k], s = it % k;
+            const int p0 = poff[t], np = poff[t + 1] - p0;
+            const int tx = t / (nt * nt), ty = (t / nt) % nt, tz = t % nt;
+            const float inv = 1.0f / pscale[s];
+            bool stop = false;
+            for (int pb = eg; pb < TILE_PTS / 128; pb += 2, ++ause) {
+                const bool ok = mbar_wait(&ctl->acc_full[eg], (unsigned)(ause & 1), abort) && !*abort;
+                tc_fence_after();
+                const int lp = pb * 128 + quarter * 32 + lane;
+                float r = 0.0f;
+                if (ok) {
+                    const uint4 *q = reinterpret_cast<const uint4 *>(phi_pm + ((long long)t * TILE_PTS + lp) * NP);
+                    for (int c = 0; c < np; c += 32) {
+                        uint4 ph[4];
+#pragma unroll
+                        for (int w = 0; w < 4; ++w) ph[w] = __ldg(q + c / 8 + w);
+                        float v[32];
+                        tmem_ld32(tmem + eg * 128 + ((unsigned)(quarter * 32) << 16) + (unsigned)c, v);
+#pragma unroll
+                        for (int w = 0; w < 4; ++w) {
+                            const __half2 *h = reinterpret_cast<const __half2 *>(&ph[w]);
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const float2 f2 = __half22float2(h[e]);
+                                r = fmaf(v[8 * w + 2 * e], f2.x, r);
+                                r = fmaf(v[8 * w + 2 * e + 1], f2.y, r);
+                            }
+                        }
+                    }
+                }
+                tc_fence_before();
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ctl->acc_empty[eg])) : "memory");
+                if (!ok) {
+                    stop = true;
+                    break;
+                }
+                const int gx = tx * TILE + (lp >> 6), gy = ty * TILE + ((lp >> 3) & 7), gz = tz * TILE + (lp & 7);
+                if (gx < n && gy < n && gz < n) rho[(long long)s * n3 + ((long long)gx * n + gy) * n + gz] = r * inv;
+            }
+            if (stop) break;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 5) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+    }
+    if (threadIdx.x == 0 && ctl->abort) atomicExch(err, 1);
+}
+
 // per-state power-of-two scale: 2^-e with 2^(e-1) < max|P_s| <= 2^e (1 for an all-zero state)
 __global__ void maxabs_kernel(const float *__restrict__ P, long long len, int k, unsigned *__restrict__ bits) {
     const int s = blockIdx.y;
@@ -404,7 +646,8 @@ int density_tc_group(int KBmax, int NP, int k) {
 void response_density_tc(cudaStream_t st, const GridShape &g, const TileSet<float> &chi,
                          const TileSet<float> &phi, const unsigned short *chi_pm, int CK, int NPmax, int nphi,
                          const float *P, long long sP, int k, float *rho, unsigned *scratch_bits,
-                         float *scale, int *err, bool phi_quads, const unsigned short *phi_pm) {
+                         float *scale, int *err, bool phi_quads, const unsigned short *phi_pm,
+                         const int *live_tiles, int nlive) {
     if (k <= 0) return;
     ProfScope ps(st, ST_DENSITY, 2.0 * k * g.pair_points, 2.0 * g.table_values + 4.0 * k * g.n * g.n * g.n);
     check(cudaMemsetAsync(scratch_bits, 0, sizeof(unsigned) * k, st), "memset maxabs");
@@ -417,6 +660,34 @@ void response_density_tc(cudaStream_t st, const GridShape &g, const TileSet<floa
                        (unsigned long long)chi.ntiles * TILE_PTS, (unsigned long long)CK * 2, 64, 128))
         throw CudaError{cudaErrorInvalidValue, "cuTensorMapEncodeTiled (density)"};
     const int NP = NPmax, KBmax = CK / 64;
+    static const bool no_persistent = [] {
+        const char *e = std::getenv("TDDFT_NO_PERSISTENT_DENSITY");
+        return e && e[0] == '1';
+    }();
+    if (!no_persistent && phi_quads && phi_pm && live_tiles && NP % 32 == 0 && NP <= 128 && KBmax <= PDENS_KB) {
+        // persistent kernel over (tile, state) items; tiles without chi or phi only need zeros
+        const size_t psm = 1024 + (size_t)PDENS_STAGES * 16384 + 2 * (size_t)PDENS_KB * NP * 128 + sizeof(PDensShared);
+        static const bool pattr = [&]() {
+            check(cudaFuncSetAttribute(density_tc_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       227 * 1024),
+                  "attr density_tc_persistent");
+            return true;
+        }();
+        (void)pattr;
+        check(cudaMemsetAsync(rho, 0, sizeof(float) * (size_t)k * g.n * g.n * g.n, st), "memset rho");
+        const int nitems = nlive * k;
+        if (nitems > 0) {
+            int dev = 0, sms = 0;
+            check(cudaGetDevice(&dev), "cudaGetDevice");
+            check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+            const int grid = std::min(sms, nitems);
+            density_tc_persistent_kernel<<<grid, PDENS_THREADS, psm, st>>>(mx, g.n, g.nt, NP, k, live_tiles, nitems,
+                                                                           chi.off, chi.ids, phi.off, phi.ids, nphi,
+                                                                           phi_pm, P, sP, scale, rho, err);
+            check_launch("density_tc_persistent_kernel");
+        }
+        return;
+    }
     const int G = density_tc_group(KBmax, NP, k);
     if (G < 1) throw CudaError{cudaErrorInvalidValue, "density_tc: tile too large for shared memory"};
     const int ngroups = (k + G - 1) / G;
