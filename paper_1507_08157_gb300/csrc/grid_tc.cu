@@ -898,9 +898,10 @@ __global__ void __launch_bounds__(192, 3) integrals_tc_kernel(
 // The chi and phi slices of an item stream through the same double-buffered stages as above,
 // continuing from the previous item, and the accumulators are double-buffered in TMEM
 // (2 x 2 blocks of 128 columns), so an item's epilogue runs while the next item's slices are
-// scaled and multiplied. 320 threads: warps 0-3 scale, warp 4 loads (TMA), warp 5 issues the
-// MMAs, warps 6-9 read the accumulators out (TMEM lanes warp % 4).
-constexpr int PINT_THREADS = 320;
+// scaled and multiplied. 448 threads: warps 0-7 scale, warp 8 loads (TMA), warp 9 issues the
+// MMAs, warps 10-13 read the accumulators out (TMEM lanes warp % 4).
+constexpr int PINT_THREADS = 448;
+constexpr int PINT_BUILD = 256;      // scaling threads: warps 0-7
 
 struct __align__(8) PIntShared {
     unsigned long long x_full[2];
@@ -933,17 +934,17 @@ __global__ void __launch_bounds__(PINT_THREADS, 1) integrals_tc_persistent_kerne
     if (threadIdx.x == 0) {
         for (int i = 0; i < 2; ++i) {
             mbar_init(&ctl->x_full[i], 1);
-            mbar_init(&ctl->w_ready[i], 128);
+            mbar_init(&ctl->w_ready[i], PINT_BUILD);
             mbar_init(&ctl->mma_done[i], 1);
             mbar_init(&ctl->acc_full[i], 1);
             mbar_init(&ctl->acc_empty[i], 128);
         }
-        mbar_init(&ctl->v_done, 128);
-        mbar_init(&ctl->v_set, 128);
+        mbar_init(&ctl->v_done, PINT_BUILD);
+        mbar_init(&ctl->v_set, PINT_BUILD);
         ctl->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 5) {
+    if (warp == 9) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&ctl->tmem_base)),
                      "r"(512));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -954,7 +955,7 @@ __global__ void __launch_bounds__(PINT_THREADS, 1) integrals_tc_persistent_kerne
     const unsigned tmem = ctl->tmem_base;
     constexpr int KS = TILE_PTS / 64;
 
-    if (warp == 4) {
+    if (warp == 8) {
         if (lane == 0) {
             long long q = 0;
             bool ok = true;
@@ -975,7 +976,7 @@ __global__ void __launch_bounds__(PINT_THREADS, 1) integrals_tc_persistent_kerne
                 }
             }
         }
-    } else if (warp == 5) {
+    } else if (warp == 9) {
         if (lane == 0) {
             const unsigned idesc = idesc_f16(128, NB);
             long long q = 0;
@@ -1009,7 +1010,7 @@ __global__ void __launch_bounds__(PINT_THREADS, 1) integrals_tc_persistent_kerne
                 mma_commit(&ctl->acc_full[a]);
             }
         }
-    } else if (warp < 4) {
+    } else if (warp < 8) {
         // scale each landed phi slice by V_s at its points
         long long q = 0;
         int j = 0;
@@ -1021,7 +1022,7 @@ __global__ void __launch_bounds__(PINT_THREADS, 1) integrals_tc_persistent_kerne
             // every scaling thread is done with the previous item's V (bounded waits, no named
             // barrier: a thread that gives up cannot strand the others)
             if (j > 0 && !mbar_wait(&ctl->v_done, (unsigned)((j - 1) & 1), abort)) break;
-            for (int lp = threadIdx.x; lp < TILE_PTS; lp += 128) {
+            for (int lp = threadIdx.x; lp < TILE_PTS; lp += PINT_BUILD) {
                 const int gx = tx * TILE + (lp >> 6), gy = ty * TILE + ((lp >> 3) & 7), gz = tz * TILE + (lp & 7);
                 float v = 0.0f;
                 if (gx < n && gy < n && gz < n) v = V[(long long)s * n3 + ((long long)gx * n + gy) * n + gz];
@@ -1037,7 +1038,7 @@ __global__ void __launch_bounds__(PINT_THREADS, 1) integrals_tc_persistent_kerne
                     break;
                 }
                 unsigned char *W = Ws + (size_t)st * NB * 128;
-                for (int idx = threadIdx.x; idx < np * 8; idx += 128) {
+                for (int idx = threadIdx.x; idx < np * 8; idx += PINT_BUILD) {
                     const int row = idx >> 3, c8 = idx & 7;
                     uint4 *qp = reinterpret_cast<uint4 *>(W + sw128_offset(row, c8));
                     uint4 w = *qp;
@@ -1058,7 +1059,7 @@ __global__ void __launch_bounds__(PINT_THREADS, 1) integrals_tc_persistent_kerne
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ctl->v_done)) : "memory");
         }
     } else {
-        // epilogue warps 6-9: TMEM lanes (warp % 4) * 32
+        // epilogue warps 10-13: TMEM lanes (warp % 4) * 32
         const int quarter = warp & 3;
         int j = 0;
         for (int it = blockIdx.x; it < nitems; it += gridDim.x, ++j) {
@@ -1100,7 +1101,7 @@ __global__ void __launch_bounds__(PINT_THREADS, 1) integrals_tc_persistent_kerne
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 5) {
+    if (warp == 9) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
     }
