@@ -894,220 +894,6 @@ __global__ void __launch_bounds__(192, 3) integrals_tc_kernel(
     if (threadIdx.x == 0 && ctl->abort) atomicExch(err, 1);
 }
 
-// Persistent variant for tiles with at most 256 chi: one CTA per SM walks (tile, state) items.
-// The chi and phi slices of an item stream through the same double-buffered stages as above,
-// continuing from the previous item, and the accumulators are double-buffered in TMEM
-// (2 x 2 blocks of 128 columns), so an item's epilogue runs while the next item's slices are
-// scaled and multiplied. 448 threads: warps 0-7 scale, warp 8 loads (TMA), warp 9 issues the
-// MMAs, warps 10-13 read the accumulators out (TMEM lanes warp % 4).
-constexpr int PINT_THREADS = 448;
-constexpr int PINT_BUILD = 256;      // scaling threads: warps 0-7
-
-struct __align__(8) PIntShared {
-    unsigned long long x_full[2];
-    unsigned long long w_ready[2];
-    unsigned long long mma_done[2];
-    unsigned long long acc_full[2];
-    unsigned long long acc_empty[2];
-    unsigned long long v_done;   // all scaling threads finished their item (V may be replaced)
-    unsigned long long v_set;    // all scaling threads wrote their part of the item's V
-    unsigned int tmem_base;
-    int abort;
-};
-
-__global__ void __launch_bounds__(PINT_THREADS, 1) integrals_tc_persistent_kernel(
-    const __grid_constant__ CUtensorMap mX, const __grid_constant__ CUtensorMap mP, int n, int nt, int NP, int k,
-    const int *__restrict__ tiles, int nitems, const int *__restrict__ coff, const int *__restrict__ cids,
-    const int *__restrict__ poff, const int *__restrict__ pids, int nchi, int nphi, const float *__restrict__ V,
-    const float *__restrict__ vscale, float dV, float *__restrict__ out, bool vec_ok, int *err) {
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char *base = reinterpret_cast<unsigned char *>(
-        (reinterpret_cast<unsigned long long>(smem_raw) + 1023ull) & ~1023ull);
-    const int NB = NP;
-    unsigned char *Xs = base;                                   // [2][2 x 16 KB]
-    unsigned char *Ws = base + 2 * 32768;                       // [2][NB x 128 B]
-    float *Vt = reinterpret_cast<float *>(Ws + (size_t)2 * NB * 128);
-    PIntShared *ctl = reinterpret_cast<PIntShared *>(Vt + TILE_PTS);
-    volatile int *abort = &ctl->abort;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long n3 = (long long)n * n * n;
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < 2; ++i) {
-            mbar_init(&ctl->x_full[i], 1);
-            mbar_init(&ctl->w_ready[i], PINT_BUILD);
-            mbar_init(&ctl->mma_done[i], 1);
-            mbar_init(&ctl->acc_full[i], 1);
-            mbar_init(&ctl->acc_empty[i], 128);
-        }
-        mbar_init(&ctl->v_done, PINT_BUILD);
-        mbar_init(&ctl->v_set, PINT_BUILD);
-        ctl->abort = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 9) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&ctl->tmem_base)),
-                     "r"(512));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const unsigned tmem = ctl->tmem_base;
-    constexpr int KS = TILE_PTS / 64;
-
-    if (warp == 8) {
-        if (lane == 0) {
-            long long q = 0;
-            bool ok = true;
-            for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
-                const int t = tiles[it / k];
-                const int c0 = coff[t], MB = (coff[t + 1] - c0 + 127) / 128, p0 = poff[t];
-                for (int kb = 0; kb < KS; ++kb, ++q) {
-                    const int st = (int)(q & 1);
-                    const long long use = q >> 1;
-                    if (use > 0 && !mbar_wait(&ctl->mma_done[st], (unsigned)((use - 1) & 1), abort)) {
-                        ok = false;
-                        break;
-                    }
-                    mbar_expect_tx(&ctl->x_full[st], MB * 16384 + NB * 128);
-                    for (int mb = 0; mb < MB; ++mb)
-                        tma_load_2d(Xs + st * 32768 + mb * 16384, &mX, &ctl->x_full[st], kb * 64, c0 + mb * 128);
-                    tma_load_2d(Ws + (size_t)st * NB * 128, &mP, &ctl->x_full[st], kb * 64, p0);
-                }
-            }
-        }
-    } else if (warp == 9) {
-        if (lane == 0) {
-            const unsigned idesc = idesc_f16(128, NB);
-            long long q = 0;
-            int j = 0;
-            bool ok = true;
-            for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x, ++j) {
-                const int t = tiles[it / k];
-                const int MB = (coff[t + 1] - coff[t] + 127) / 128;
-                const int a = j & 1, ause = j >> 1;
-                if (ause > 0 && !mbar_wait(&ctl->acc_empty[a], (unsigned)((ause - 1) & 1), abort)) break;
-                tc_fence_after();
-                for (int kb = 0; kb < KS; ++kb, ++q) {
-                    const int st = (int)(q & 1);
-                    const unsigned ph = (unsigned)((q >> 1) & 1);
-                    if (!mbar_wait(&ctl->x_full[st], ph, abort) || !mbar_wait(&ctl->w_ready[st], ph, abort)) {
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-                    const unsigned wb = smem_u32(Ws + (size_t)st * NB * 128);
-                    for (int mb = 0; mb < MB; ++mb) {
-                        const unsigned xa = smem_u32(Xs + st * 32768 + mb * 16384);
-#pragma unroll
-                        for (int kk = 0; kk < 4; ++kk)
-                            mma_f16(tmem + a * 256 + mb * 128, smem_desc(xa + kk * 32), smem_desc(wb + kk * 32), idesc,
-                                    (kb > 0 || kk > 0) ? 1u : 0u);
-                    }
-                    mma_commit(&ctl->mma_done[st]);
-                }
-                if (!ok) break;
-                mma_commit(&ctl->acc_full[a]);
-            }
-        }
-    } else if (warp < 8) {
-        // scale each landed phi slice by V_s at its points
-        long long q = 0;
-        int j = 0;
-        for (int it = blockIdx.x; it < nitems; it += gridDim.x, ++j) {
-            const int t = tiles[it / k], s = it % k;
-            const int np = poff[t + 1] - poff[t];
-            const int tx = t / (nt * nt), ty = (t / nt) % nt, tz = t % nt;
-            const float vs = vscale[s];
-            // every scaling thread is done with the previous item's V (bounded waits, no named
-            // barrier: a thread that gives up cannot strand the others)
-            if (j > 0 && !mbar_wait(&ctl->v_done, (unsigned)((j - 1) & 1), abort)) break;
-            for (int lp = threadIdx.x; lp < TILE_PTS; lp += PINT_BUILD) {
-                const int gx = tx * TILE + (lp >> 6), gy = ty * TILE + ((lp >> 3) & 7), gz = tz * TILE + (lp & 7);
-                float v = 0.0f;
-                if (gx < n && gy < n && gz < n) v = V[(long long)s * n3 + ((long long)gx * n + gy) * n + gz];
-                Vt[lp] = v * vs;
-            }
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ctl->v_set)) : "memory");
-            if (!mbar_wait(&ctl->v_set, (unsigned)(j & 1), abort)) break;   // the new V is in place
-            bool ok = true;
-            for (int kb = 0; kb < KS; ++kb, ++q) {
-                const int st = (int)(q & 1);
-                if (!mbar_wait(&ctl->x_full[st], (unsigned)((q >> 1) & 1), abort)) {
-                    ok = false;
-                    break;
-                }
-                unsigned char *W = Ws + (size_t)st * NB * 128;
-                for (int idx = threadIdx.x; idx < np * 8; idx += PINT_BUILD) {
-                    const int row = idx >> 3, c8 = idx & 7;
-                    uint4 *qp = reinterpret_cast<uint4 *>(W + sw128_offset(row, c8));
-                    uint4 w = *qp;
-                    const float4 *vv = reinterpret_cast<const float4 *>(Vt + kb * 64 + c8 * 8);
-                    const float4 v0 = vv[0], v1 = vv[1];
-                    __half2 *h = reinterpret_cast<__half2 *>(&w);
-                    float2 f2;
-                    f2 = __half22float2(h[0]); h[0] = __floats2half2_rn(f2.x * v0.x, f2.y * v0.y);
-                    f2 = __half22float2(h[1]); h[1] = __floats2half2_rn(f2.x * v0.z, f2.y * v0.w);
-                    f2 = __half22float2(h[2]); h[2] = __floats2half2_rn(f2.x * v1.x, f2.y * v1.y);
-                    f2 = __half22float2(h[3]); h[3] = __floats2half2_rn(f2.x * v1.z, f2.y * v1.w);
-                    *qp = w;
-                }
-                fence_async_smem();
-                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ctl->w_ready[st])) : "memory");
-            }
-            if (!ok) break;
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ctl->v_done)) : "memory");
-        }
-    } else {
-        // epilogue warps 10-13: TMEM lanes (warp % 4) * 32
-        const int quarter = warp & 3;
-        int j = 0;
-        for (int it = blockIdx.x; it < nitems; it += gridDim.x, ++j) {
-            const int t = tiles[it / k], s = it % k;
-            const int c0 = coff[t], nc = coff[t + 1] - c0;
-            const int p0 = poff[t], np = poff[t + 1] - p0;
-            const int MB = (nc + 127) / 128;
-            const int a = j & 1;
-            const bool ok = mbar_wait(&ctl->acc_full[a], (unsigned)((j >> 1) & 1), abort) && !*abort;
-            tc_fence_after();
-            const float f = dV / vscale[s];
-            for (int mb = 0; mb < MB && ok; ++mb) {
-                const int row = mb * 128 + quarter * 32 + lane;
-                const bool arow = row < nc;
-                float *o = out + (long long)s * nchi * nphi + (arow ? (long long)cids[c0 + row] * nphi : 0);
-                for (int c = 0; c < np; c += 32) {
-                    float v[32];
-                    tmem_ld32(tmem + a * 256 + mb * 128 + ((unsigned)(quarter * 32) << 16) + (unsigned)c, v);
-                    if (!arow) continue;
-#pragma unroll
-                    for (int jj = 0; jj < 32; jj += 4) {
-                        const int b = c + jj;
-                        if (b >= np) break;
-                        const int B0 = pids[p0 + b];
-                        if (vec_ok && b + 3 < np && (B0 & 3) == 0 && pids[p0 + b + 3] == B0 + 3) {
-                            red_add_v4(o + B0, f * v[jj], f * v[jj + 1], f * v[jj + 2], f * v[jj + 3]);
-                        } else {
-#pragma unroll
-                            for (int u = 0; u < 4; ++u)
-                                if (b + u < np) atomicAdd(o + pids[p0 + b + u], f * v[jj + u]);
-                        }
-                    }
-                }
-            }
-            tc_fence_before();
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ctl->acc_empty[a])) : "memory");
-            if (!ok) break;
-        }
-    }
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 9) {
-        tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
-    }
-    if (threadIdx.x == 0 && ctl->abort) atomicExch(err, 1);
-}
-
 __global__ void vmaxabs_kernel(const float *__restrict__ V, long long n3, unsigned *__restrict__ bits) {
     const int s = blockIdx.y;
     float m = 0.0f;
@@ -1164,44 +950,12 @@ void potential_integrals_tc(cudaStream_t st, const GridShape &g, const TileSet<f
     }();
     (void)attr;
     const bool vec_ok = (nphi % 4 == 0) && ((reinterpret_cast<unsigned long long>(out) & 15ull) == 0);
-    static const bool no_persistent = [] {
-        const char *e = std::getenv("TDDFT_NO_PERSISTENT_INTEGRALS");
-        return e && e[0] == '1';
-    }();
-    int first_class = 0;
-    if (!no_persistent) {
-        // tiles with at most 256 chi (the first two classes, contiguous in the list) in one
-        // persistent launch; tiles with more keep the one-CTA-per-item kernel below
-        const int nsmall = tiles_by_blocks[0] + tiles_by_blocks[1];
-        const int nitems = nsmall * k;
-        if (nitems > 0) {
-            // at least 116 KB of shared memory so that no SM holds two of these CTAs: each
-            // allocates all 512 TMEM columns, and a second one would sit in its allocation
-            const size_t psm = std::max<size_t>(116 * 1024, 1024 + (size_t)2 * 32768 + (size_t)2 * NPmax * 128 +
-                                                                (size_t)TILE_PTS * 4 + sizeof(PIntShared));
-            static const bool pattr = [&]() {
-                check(cudaFuncSetAttribute(integrals_tc_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           227 * 1024),
-                      "attr integrals_tc_persistent");
-                return true;
-            }();
-            (void)pattr;
-            int dev = 0, sms = 0;
-            check(cudaGetDevice(&dev), "cudaGetDevice");
-            check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
-            integrals_tc_persistent_kernel<<<std::min(sms, nitems), PINT_THREADS, psm, st>>>(
-                mx, mp, g.n, g.nt, NPmax, k, tile_list, nitems, chi.off, chi.ids, phi.off, phi.ids, nchi, nphi, V,
-                scale, (float)g.dV, out, vec_ok, err);
-            check_launch("integrals_tc_persistent_kernel");
-        }
-        first_class = 2;
-    }
     const int *lp = tile_list;
     for (int c = 0; c < 3; ++c) {
         const int cnt = tiles_by_blocks[c];
         const int *lst = lp;
         lp += cnt;
-        if (cnt == 0 || c < first_class) continue;
+        if (cnt == 0) continue;
         const int mbmax = c + 1;
         const int stride = 128;                           // one state: NB = NPmax <= 128 columns
         const int tmem_cols = mbmax == 1 ? 128 : (mbmax == 2 ? 256 : 512);
