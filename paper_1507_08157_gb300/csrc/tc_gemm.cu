@@ -552,14 +552,7 @@ void tc_gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, float alpha
     SplitCopy cav{}, cbv{};
     const SplitCopy *ca = (split && bA == 1 && const_split(st, A, ta, M, K, lda, &cav)) ? &cav : nullptr;
     const SplitCopy *cb = (split && bB == 1 && const_split(st, B, !tb, N, K, ldb, &cbv)) ? &cbv : nullptr;
-    // a direct operand is split inside the kernel once per output tile that reads it: that pays
-    // when few tiles share it (one tile column for A, one tile row for B); otherwise one split
-    // copy up front is cheaper (measured: the right products, 5 tile columns, ran at a quarter
-    // of the left products' rate with the in-kernel split)
-    const int tn_cols = (N + ((N % 112 == 0) ? 112 : TBN) - 1) / ((N % 112 == 0) ? 112 : TBN);
-    const int tm_rows = (M + TBM - 1) / TBM;
-    const bool a_direct = !ca && !ta && direct(A, lda, sA) && (!split || tn_cols <= 1);
-    const bool b_direct = !cb && tb && direct(B, ldb, sB) && (!split || tm_rows <= 1);
+    const bool a_direct = !ca && !ta && direct(A, lda, sA), b_direct = !cb && tb && direct(B, ldb, sB);
     const bool a_copy = !ca && !a_direct, b_copy = !cb && !b_direct;
     const int Kp = (K + 3) / 4 * 4;                     // 16-byte rows for the tensor maps
     const int nsp = split ? 2 : 1;                      // copies carry hi and lo when splitting
