@@ -359,9 +359,10 @@ def run_ours(args):
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained x 1.1/2.25 (tf32/bf16 nominal)",
                 "note": "achieved counts 2MNK per product; the three-term split issues 3 MMAs per product",
                 "frac_of_fp32_accurate_peak": achieved / (peak / 3.0),
-                "traffic_note": "the stage mixes product shapes; ncu DRAM bytes of the left product "
-                                "(1260 x 1260 by 20 x 1260 x 560): 1.6e8 per launch against ~1.8e8 "
-                                "algorithmic (profiles/launches_tc_chromophore140.md)"}
+                "traffic_note": "the stage mixes product shapes; ncu DRAM bytes per launch of the operator's "
+                                "left product (1260 x 1260 by 20 x 1260 x 560): 1.26e8 read + 0.32e8 written "
+                                "against 1.82e8 algorithmic; right product 1.15e8 + 0.09e8 against 1.70e8 "
+                                "(profiles/launches_tc_chromophore140.md)"}
     elif (name in ("potential_integrals", "response_density") and args.precision == "mixed"
           and os.environ.get("TDDFT_NO_TC") != "1" and os.environ.get("TDDFT_NO_GRID_TC") != "1"):
         # tcgen05 kind::f16 grid contractions: the roof is the larger of the algorithmic bytes at
