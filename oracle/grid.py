@@ -132,3 +132,63 @@ def full_grid(fs, n):
         gz = (oz + np.arange(ez)) % n
         out[f][np.ix_(gx, gy, gz)] += vals
     return out
+
+
+def _inside(g, p, n):
+    """Box offsets of grid point p in group g, or None when p is outside its nonzero support."""
+    _, _, org, _, lo, hi = g
+    off = (np.asarray(p, dtype=np.int64) - org) % n
+    if np.all(off >= lo) and np.all(off < hi):
+        return off
+    return None
+
+
+def values_at(bs: BoxedSet, p):
+    """All function values of a set at one grid point p = (ix, iy, iz): a dense vector [nfun]."""
+    out = np.zeros(bs.nfun)
+    for g in bs.groups:
+        off = _inside(g, p, bs.n)
+        if off is not None:
+            f0, f1, _, vals, _, _ = g
+            out[f0:f1] = vals[:, off[0], off[1], off[2]]
+    return out
+
+
+def density_at(chi: BoxedSet, phi: BoxedSet, P, points):
+    """rho_s(r) = sum_ab chi_a(r) P_s[a, b] phi_b(r) at the given grid points only: [s, npoints].
+    The same definition as response_density, evaluated point by point (for workloads whose full
+    grid is too large for the oracle)."""
+    P = np.asarray(P)
+    out = np.zeros((P.shape[0], len(points)))
+    for i, p in enumerate(points):
+        xc = values_at(chi, p)
+        xp = values_at(phi, p)
+        a = np.nonzero(xc)[0]
+        b = np.nonzero(xp)[0]
+        if a.size and b.size:
+            out[:, i] = np.einsum("a,sab,b->s", xc[a], P[:, a][:, :, b], xp[b])
+    return out
+
+
+def integrals_at(chi: BoxedSet, phi: BoxedSet, V, dV, pairs):
+    """V_s[a, b] = dV sum_r chi_a(r) V_s(r) phi_b(r) for the listed (a, b) pairs only: [s, npairs].
+    The same sums as potential_integrals, over the common support of the two functions."""
+    n = chi.n
+    V = np.asarray(V)
+    k = V.shape[0]
+
+    def group_of(bs, f):
+        for g in bs.groups:
+            if g[0] <= f < g[1]:
+                return g
+        raise IndexError(f)
+
+    out = np.zeros((k, len(pairs)))
+    for i, (a, b) in enumerate(pairs):
+        ga, gb = group_of(chi, a), group_of(phi, b)
+        for sa, sb, gx, gy, gz in _common(ga, gb, n):
+            xa = ga[3][a - ga[0]][sa[1:]].reshape(-1)
+            xb = gb[3][b - gb[0]][sb[1:]].reshape(-1)
+            vsub = V[np.ix_(np.arange(k), gx, gy, gz)].reshape(k, -1)
+            out[:, i] += dV * (vsub @ (xa * xb))
+    return out
