@@ -53,6 +53,10 @@ def parse():
     ap.add_argument("--batch-max-atoms", type=int, default=300)
     ap.add_argument("--batch-seed", type=int, default=3)
     ap.add_argument("--batch-workers", type=int, default=8, help="processes generating the systems")
+    ap.add_argument("--scaling", default="",
+                    help="comma-separated atom counts of the core + shell series: time operator applies "
+                         "on each (one JSON line with the series)")
+    ap.add_argument("--scaling-k", type=int, default=4)
     return ap.parse_args()
 
 
@@ -496,8 +500,76 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def run_scaling(args):
+    """Operator applies on the linear-scaling series (synthetic.scaling_recipe: a 140-atom core
+    and a solvent-like shell at 0.1 atoms / A^3, 4 phi + 9 chi per atom, R = 8 A, 0.25 A grid,
+    15 A kernel cutoff), k states, mixed precision. Per size: device-resident applies timed with
+    CUDA events after warm-up, the per-stage times of the library's profiler, and the time per
+    unit of algorithmic work W (flops: 2 k pair_points for each grid contraction, 2MNK for every
+    dense product; the stage counters add them up), so that time / W stays flat when the time
+    grows with the work."""
+    import torch
+    from paper_1507_08157_gb300 import synthetic as sy
+    from paper_1507_08157_gb300 import tddft
+    torch.cuda.set_device(0)
+    tddft.load()
+    stream = torch.cuda.current_stream()
+    k = args.scaling_k
+    series = []
+    for natoms in [int(x) for x in args.scaling.split(",") if x.strip()]:
+        rec = sy.scaling_recipe(natoms)
+        t0 = time.perf_counter()
+        s = sy.generate(rec)
+        t1 = time.perf_counter()
+        ctx = tddft.Context(s, precision="mixed", stream=stream.cuda_stream, precond="none")
+        t2 = time.perf_counter()
+        ctx.sys = None                                  # the device holds the system now
+        pair_points, table_values = ctx.work()
+        Pp, Pq = sy.random_kernels(s, k, 3)
+        dPp, dPq = torch.from_numpy(Pp).cuda(), torch.from_numpy(Pq).cuda()
+        del s, Pp, Pq
+        for _ in range(args.warmup):
+            ctx.apply(dPp, dPq)
+        ctx.profile(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(0) as clk:
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(args.steps):
+                ctx.apply(dPp, dPq)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        prof = ctx.profile_read()
+        ctx.profile(False)
+        flops = sum(v[2] for v in prof.values()) / args.steps
+        series.append({
+            "atoms": natoms, "cell_ang": rec.cell_ang, "grid": rec.ngrid,
+            "n_chi": ctx.nc, "n_phi": ctx.nv, "pair_points": pair_points, "table_values": table_values,
+            "ms_per_apply": ms, "applies_per_s": k / (ms / 1000.0),
+            "work_tflop_per_apply": flops / 1e12, "ns_per_mflop": 1e6 * ms / max(flops / 1e6, 1e-30),
+            "stages_ms": {n: round(v[1] / args.steps, 3) for n, v in prof.items() if v[0]},
+            "generate_s": t1 - t0, "create_s": t2 - t1,
+            "clocks": {k_: clk.summary()[k_] for k_ in ("sm_mhz", "sm_max_mhz", "reasons")}})
+        ctx.close()
+        del dPp, dPq
+        torch.cuda.empty_cache()
+    line = {"metric": "operator applies/s and time per unit of work vs atom count", "unit": UNIT,
+            "n_gpus": 1, "higher_is_better": True, "impl": "ours", "dtype": "f32", "data": "synthetic",
+            "steps": args.steps, "warmup": args.warmup,
+            "config": {"workload": "linear-scaling series: 140-atom core + shell at 0.1 atoms/A^3, 4 phi + 9 chi "
+                                   "per atom, 8 A radius, 0.25 A grid, 15 A kernel cutoff, "
+                                   f"k={k}, mixed precision",
+                       "l2": "inputs larger than L2 (function tables of several GB)"},
+            "series": series}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.scaling:
+        run_scaling(args)
+        return
     if args.batched > 0:
         run_batched(args)
         return

@@ -55,6 +55,8 @@ class Recipe:
     kernel_cutoff_ang: float = 0.0   # <= 0: response kernels not truncated
     seed: int = 0
     cluster_ang: float = 0.0   # > 0: atoms only inside a centred cube of this side (vacuum around)
+    sphere_density: float = 0.0   # > 0: atoms fill a centred sphere at this density (A^-3) ...
+    core_atoms: int = 0           # ... the first core_atoms its inner sphere, the rest the shell
 
 
 # The smallest workload: 8 atoms, 16 A cell, 48^3 grid, 4 phi + 4 chi (s, p) per atom, 7 A radius,
@@ -65,6 +67,19 @@ CONFIG_SMALL = Recipe(natoms=8, cell_ang=16.0, ngrid=48, nphi=4, nchi=4, radius_
 # atom, 8 A radius, response kernels truncated at 12 A.
 CONFIG_CHROMOPHORE = Recipe(natoms=140, cell_ang=30.0, ngrid=120, nphi=4, nchi=9, radius_ang=8.0,
                             kernel_cutoff_ang=12.0, seed=2)
+
+
+def scaling_recipe(natoms: int, seed: int = 5) -> Recipe:
+    """The linear-scaling series: a 140-atom core sphere and a shell grown to natoms, both at
+    0.1 atoms per A^3 (RSA, 1.4 A minimum separation); cell = cluster diameter + 2R + 10 A of
+    vacuum, rounded up to a 2/3/5-smooth grid at 0.25 A (500 atoms: 48 A, 192^3; 1000: 54 A,
+    216^3; 2000: 60 A, 240^3); 4 phi + 9 chi per atom, R = 8 A, kernels truncated at 15 A."""
+    density, R, h = 0.1, 8.0, 0.25
+    r_cluster = (3.0 * natoms / (4.0 * math.pi * density)) ** (1.0 / 3.0)
+    n = smooth_grid(int(math.ceil((2.0 * r_cluster + 2.0 * R + 10.0) / h)))
+    return Recipe(natoms=natoms, cell_ang=n * h, ngrid=n, nphi=4, nchi=9, radius_ang=R,
+                  kernel_cutoff_ang=15.0, seed=seed, sphere_density=density,
+                  core_atoms=min(140, natoms))
 
 
 @dataclasses.dataclass
@@ -134,6 +149,36 @@ def _rsa_positions(rng, natoms, cell, min_sep, cluster=0.0):
         if tries > 2000000:
             raise RuntimeError("could not place atoms at the requested minimum separation")
         x = rng.uniform(lo, hi, size=3)
+        if placed:
+            d = pos[:placed] - x
+            d -= cell * np.round(d / cell)
+            if np.min(np.einsum("ij,ij->i", d, d)) < min_sep * min_sep:
+                continue
+        pos[placed] = x
+        placed += 1
+    return pos
+
+
+def _rsa_sphere_positions(rng, natoms, cell, min_sep, density, core):
+    """RSA inside a centred sphere holding natoms at the given density (bohr^-3): atoms
+    0..core-1 in the inner sphere that holds core atoms at that density, the rest between the two
+    spheres."""
+    r_out = (3.0 * natoms / (4.0 * math.pi * density)) ** (1.0 / 3.0)
+    r_in = (3.0 * core / (4.0 * math.pi * density)) ** (1.0 / 3.0) if core > 0 else 0.0
+    centre = np.full(3, 0.5 * cell)
+    pos = np.zeros((natoms, 3))
+    placed = 0
+    tries = 0
+    while placed < natoms:
+        tries += 1
+        if tries > 20000000:
+            raise RuntimeError("could not place atoms at the requested minimum separation")
+        lo, hi = (0.0, r_in) if placed < core else (r_in, r_out)
+        v = rng.standard_normal(3)
+        r = hi * rng.uniform() ** (1.0 / 3.0)
+        if r < lo:
+            continue
+        x = centre + r * v / np.linalg.norm(v)
         if placed:
             d = pos[:placed] - x
             d -= cell * np.round(d / cell)
@@ -265,8 +310,12 @@ def _overlap_matrix(fs, nper, pos, cell, n, dV, rmax):
     N = natoms * nper
     S = np.zeros((N, N))
     pairs = _atom_pairs_within(pos, cell, rmax)
-    with concurrent.futures.ThreadPoolExecutor(_workers()) as ex:
-        blocks = list(ex.map(lambda p: dV * _pair_overlap(fs, fs, nper, nper, p[0], p[1], n), pairs))
+    blocks = _pooled(fs, nper, n, None, _w_overlap, pairs)
+    if blocks is not None:
+        blocks = [dV * b for part in blocks for b in part]
+    else:
+        with concurrent.futures.ThreadPoolExecutor(_workers()) as ex:
+            blocks = list(ex.map(lambda p: dV * _pair_overlap(fs, fs, nper, nper, p[0], p[1], n), pairs))
     for (i, j, _), blk in zip(pairs, blocks):
         S[i * nper:(i + 1) * nper, j * nper:(j + 1) * nper] = blk
         if i != j:
@@ -316,22 +365,99 @@ def _split(start, length, n):
     return [(start, 0, first), (0, first, length - first)]
 
 
+def _add_parts(out, parts, n):
+    for x0, y0, z0, contrib in parts:
+        lx, ly, lz = contrib.shape
+        for (dx, sx, nx) in _split(x0, lx, n):
+            for (dy, sy, ny) in _split(y0, ly, n):
+                for (dz, sz, nz) in _split(z0, lz, n):
+                    out[dx:dx + nx, dy:dy + ny, dz:dz + nz] += contrib[sx:sx + nx, sy:sy + ny, sz:sz + nz]
+
+
 def _density_on_grid(fs, nper, K, pos, cell, n, rmax):
     """sum_ab f_a(r) K_ab f_b(r) on the full grid, over atom pairs within rmax."""
-    out = np.zeros((n, n, n))
     jobs = []
     for (i, j, _) in _atom_pairs_within(pos, cell, rmax):
         jobs += [(i, j), (j, i)] if i != j else [(i, i)]
+    partial = _pooled(fs, nper, n, K, _w_density, jobs)
+    if partial is not None:
+        out = partial[0]
+        for g in partial[1:]:
+            out += g
+        return out
+    out = np.zeros((n, n, n))
     with concurrent.futures.ThreadPoolExecutor(_workers()) as ex:
         for parts in ex.map(lambda p: _density_contrib(fs, nper, K, n, p[0], p[1]), jobs):
-            for x0, y0, z0, contrib in parts:
-                lx, ly, lz = contrib.shape
-                for (dx, sx, nx) in _split(x0, lx, n):
-                    for (dy, sy, ny) in _split(y0, ly, n):
-                        for (dz, sz, nz) in _split(z0, lz, n):
-                            out[dx:dx + nx, dy:dy + ny, dz:dz + nz] += \
-                                contrib[sx:sx + nx, sy:sy + ny, sz:sz + nz]
+            _add_parts(out, parts, n)
     return out
+
+
+# Large systems (tens of thousands of atom pairs): the per-pair table sums are copy-bound numpy
+# work that threads do not speed up, so they run in a pool of spawned processes that map the
+# tables from POSIX shared memory. The work is cut into a fixed number of chunks, whatever the
+# core count, so the partial sums are added in the same order on every machine.
+_POOL_MIN_JOBS = 20000
+_POOL_CHUNKS = 64
+_W = {}   # worker-side state (set by _w_init in each spawned process)
+
+
+def _w_init(shm_name, shape, atom, box, off, nper, n, K):
+    from multiprocessing import shared_memory
+    shm = shared_memory.SharedMemory(name=shm_name)   # the creating process unlinks it
+    _W.update(shm=shm, nper=nper, n=n, K=K,
+              fs=FunctionSet(atom=atom, box=box, off=off,
+                             val=np.ndarray(shape, dtype=np.float64, buffer=shm.buf)))
+
+
+def _w_overlap(pairs):
+    fs, nper, n = _W["fs"], _W["nper"], _W["n"]
+    return [_pair_overlap(fs, fs, nper, nper, i, j, n) for (i, j, _) in pairs]
+
+
+def _w_density(jobs):
+    fs, nper, n, K = _W["fs"], _W["nper"], _W["n"], _W["K"]
+    out = np.zeros((n, n, n))
+    for (i, j) in jobs:
+        _add_parts(out, _density_contrib(fs, nper, K, n, i, j), n)
+    return out
+
+
+def _pooled(fs, nper, n, K, fn, jobs):
+    """fn over fixed chunks of jobs in spawned workers, results in chunk order; None (the caller
+    uses threads) for small job lists or when shared memory cannot hold the tables."""
+    if len(jobs) < _POOL_MIN_JOBS:
+        return None
+    try:
+        st = os.statvfs("/dev/shm")
+        if st.f_bavail * st.f_frsize < 1.2 * fs.val.nbytes:
+            return None
+    except OSError:
+        return None
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+    shm = shared_memory.SharedMemory(create=True, size=max(8, fs.val.nbytes))
+    try:
+        np.ndarray(fs.val.shape, dtype=np.float64, buffer=shm.buf)[:] = fs.val
+        step = -(-len(jobs) // _POOL_CHUNKS)
+        chunks = [jobs[c:c + step] for c in range(0, len(jobs), step)]
+        keys = ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")
+        saved = {k: os.environ.get(k) for k in keys}
+        os.environ.update({k: "1" for k in keys})   # one BLAS thread per worker process
+        try:
+            pool = mp.get_context("spawn").Pool(
+                max(1, min(64, os.cpu_count() or 1)), initializer=_w_init,
+                initargs=(shm.name, fs.val.shape, fs.atom, fs.box, fs.off, nper, n, K))
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        with pool:
+            return pool.map(fn, chunks, chunksize=1)
+    finally:
+        shm.close()
+        shm.unlink()
 
 
 def _spectral_projector(H, S, nkeep):
@@ -348,8 +474,12 @@ def generate(recipe: Recipe) -> System:
     n = int(recipe.ngrid)
     h = cell / n
     R = recipe.radius_ang * BOHR_PER_ANG
-    pos = _rsa_positions(r_pos, recipe.natoms, cell, recipe.min_sep_ang * BOHR_PER_ANG,
-                         recipe.cluster_ang * BOHR_PER_ANG)
+    if recipe.sphere_density > 0.0:
+        pos = _rsa_sphere_positions(r_pos, recipe.natoms, cell, recipe.min_sep_ang * BOHR_PER_ANG,
+                                    recipe.sphere_density / BOHR_PER_ANG ** 3, recipe.core_atoms)
+    else:
+        pos = _rsa_positions(r_pos, recipe.natoms, cell, recipe.min_sep_ang * BOHR_PER_ANG,
+                             recipe.cluster_ang * BOHR_PER_ANG)
     width = (recipe.width_ang[0] * BOHR_PER_ANG, recipe.width_ang[1] * BOHR_PER_ANG)
     phi = _tabulate(r_wphi, pos, recipe.nphi, cell, n, R, width)
     chi = _tabulate(r_wchi, pos, recipe.nchi, cell, n, R, width)

@@ -1,0 +1,97 @@
+"""The first size of the linear-scaling series, in the launch configuration `bench.py --scaling`
+times: 500 atoms (a 140-atom core and a shell at 0.1 atoms per A^3, 48 A cell, 192^3 grid, 4 phi +
+9 chi per atom, 8 A radius, 15 A kernel cutoff), k = 4 states, mixed precision. At this atom
+density a grid tile holds more functions than the tensor-core grid kernels take (256 phi), so the
+contractions run on the float32 CUDA-core kernels. Checked against the FP64 oracle:
+
+* response density at 160 sampled grid points (oracle/grid.py: density_at);
+* potential integrals at 160 uniformly drawn (chi, phi) pairs over a smooth potential
+  (integrals_at);
+* the Kohn-Sham difference part of the operator (mode d_only) on every entry.
+
+Float32 sums over thousands of functions per point and N_chi = 4500-long dense products: 1e-4 of
+the largest entry of each state.
+
+Generating the system takes minutes of host time (tens of GB of tables); the module runs only
+with TDDFT_SCALING_TESTS=1.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import grid as ogrid
+from paper_1507_08157_gb300 import synthetic as sy
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(os.environ.get("TDDFT_SCALING_TESTS") != "1",
+                                 reason="set TDDFT_SCALING_TESTS=1 (minutes of host time)")]
+
+K = 4
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def tddft():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1507_08157_gb300 import build, tddft as td
+    build.build()
+    td.load()
+    return td
+
+
+@pytest.fixture(scope="module")
+def shell500():
+    s = sy.generate(sy.scaling_recipe(500))
+    return s, ogrid.BoxedSet(s.chi, s.n), ogrid.BoxedSet(s.phi, s.n)
+
+
+@pytest.fixture(scope="module")
+def ctx(tddft, shell500):
+    return tddft.Context(shell500[0], precision="mixed", precond="none")
+
+
+def test_density_sampled(ctx, shell500):
+    s, chi, phi = shell500
+    _, P = sy.random_kernels(s, K, 51)
+    rho = ctx.response_density(P)
+    rng = np.random.default_rng(52)
+    centre = s.n // 2
+    for q in range(K):
+        # half the points inside the cluster, half anywhere
+        pts = [tuple(int(v) for v in centre + rng.integers(-s.n // 5, s.n // 5, size=3)) for _ in range(20)]
+        pts += [tuple(int(v) for v in rng.integers(0, s.n, size=3)) for _ in range(20)]
+        ref = ogrid.density_at(chi, phi, P[q:q + 1], pts)[0]
+        got = np.array([rho[q][p] for p in pts])
+        assert np.max(np.abs(got - ref)) <= TOL * np.max(np.abs(rho[q])), q
+
+
+def test_integrals_sampled(ctx, shell500):
+    s, chi, phi = shell500
+    x = np.arange(s.n) * (2.0 * np.pi / s.n)
+    X, Y, Z = np.meshgrid(x, x, x, indexing="ij")
+    V = np.stack([np.cos(X + 0.3 * q) + 0.5 * np.sin(2.0 * Y - 0.1 * q) + 0.25 * np.cos(3.0 * Z + X)
+                  for q in range(K)])
+    out = ctx.potential_integrals(V)
+    rng = np.random.default_rng(53)
+    for q in range(K):
+        pairs = [(int(rng.integers(s.chi.nfun)), int(rng.integers(s.phi.nfun))) for _ in range(40)]
+        ref = ogrid.integrals_at(chi, phi, V[q:q + 1], s.dV, pairs)[0]
+        got = np.array([out[q][a, b] for a, b in pairs])
+        assert np.max(np.abs(got - ref)) <= TOL * np.max(np.abs(out[q])), q
+
+
+def test_ks_difference_every_entry(tddft, shell500):
+    s = shell500[0]
+    ctx_d = tddft.Context(s, precision="mixed", mode="d_only", precond="none")
+    Pp, Pq = sy.random_kernels(s, 2, 54)
+    fp, fq = ctx_d.apply(Pp, Pq)
+    Mc = s.P_c @ s.H_chi
+    Mv = s.H_phi @ s.P_v
+    for X, f in ((Pp, fp), (Pq, fq)):
+        ref = np.einsum("ij,sjk->sik", Mc, X) - np.einsum("sij,jk->sik", X, Mv)
+        for q in range(X.shape[0]):
+            assert np.max(np.abs(f[q] - ref[q])) <= TOL * np.max(np.abs(ref[q])), q
+    ctx_d.close()
