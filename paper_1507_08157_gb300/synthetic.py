@@ -424,8 +424,10 @@ def _w_density(jobs):
 
 def _pooled(fs, nper, n, K, fn, jobs):
     """fn over fixed chunks of jobs in spawned workers, results in chunk order; None (the caller
-    uses threads) for small job lists or when shared memory cannot hold the tables."""
-    if len(jobs) < _POOL_MIN_JOBS:
+    uses threads) for small job lists, inside a daemonic pool worker, or when shared memory cannot
+    hold the tables."""
+    import multiprocessing as mp
+    if len(jobs) < _POOL_MIN_JOBS or mp.current_process().daemon:   # pool workers cannot fork
         return None
     try:
         st = os.statvfs("/dev/shm")
@@ -433,7 +435,6 @@ def _pooled(fs, nper, n, K, fn, jobs):
             return None
     except OSError:
         return None
-    import multiprocessing as mp
     from multiprocessing import shared_memory
     shm = shared_memory.SharedMemory(create=True, size=max(8, fs.val.nbytes))
     try:

@@ -91,7 +91,7 @@ def test_ks_difference_every_entry(tddft, shell500):
     Mc = s.P_c @ s.H_chi
     Mv = s.H_phi @ s.P_v
     for X, f in ((Pp, fp), (Pq, fq)):
-        ref = np.einsum("ij,sjk->sik", Mc, X) - np.einsum("sij,jk->sik", X, Mv)
+        ref = np.matmul(Mc, X) - np.matmul(X, Mv)
         for q in range(X.shape[0]):
             assert np.max(np.abs(f[q] - ref[q])) <= TOL * np.max(np.abs(ref[q])), q
     ctx_d.close()
