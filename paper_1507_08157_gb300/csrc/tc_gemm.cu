@@ -226,21 +226,31 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(
             const int n0 = (t % tn) * TN, m0 = ((t / tn) % tm) * TBM, b = t / (tn * tm);
             float *Cb = C + (long long)b * sC;
             for (int c0 = 0; c0 < TN; c0 += 32) {
+                const int col = n0 + c0 + lane;
+                const bool colok = c0 + lane < TN && col < N;
+                const int nrow = min(32, M - (m0 + warp * 32));   // rows of this warp inside C
+                float *cw = Cb + (long long)(m0 + warp * 32) * ldc + col;
+                // with beta, read the 32 old values of this column strip first: independent loads
+                // in flight together, instead of one round trip per row behind each store
+                float old[32];
+                if (beta != 0.0f) {
+#pragma unroll
+                    for (int rr = 0; rr < 32; ++rr)
+                        old[rr] = (rr < nrow && colok) ? cw[(long long)rr * ldc] : 0.0f;
+                }
                 float v[32];
                 tmem_ld32(tmem + (unsigned)(buf * TBN) + ((unsigned)(warp * 32) << 16) + (unsigned)c0, v);
 #pragma unroll
                 for (int j = 0; j < 32; ++j) stg[lane * 33 + j] = v[j];
                 __syncwarp();
-                const int col = n0 + c0 + lane;
-                const bool colok = c0 + lane < TN && col < N;
+                if (beta == 0.0f) {
 #pragma unroll 8
-                for (int rr = 0; rr < 32; ++rr) {
-                    const int row = m0 + warp * 32 + rr;
-                    if (row < M && colok) {
-                        float *cp = Cb + (long long)row * ldc + col;
-                        const float x = stg[rr * 33 + lane];
-                        *cp = (beta == 0.0f) ? alpha * x : fmaf(alpha, x, beta * *cp);
-                    }
+                    for (int rr = 0; rr < 32; ++rr)
+                        if (rr < nrow && colok) cw[(long long)rr * ldc] = alpha * stg[rr * 33 + lane];
+                } else {
+#pragma unroll
+                    for (int rr = 0; rr < 32; ++rr)
+                        if (rr < nrow && colok) cw[(long long)rr * ldc] = fmaf(alpha, stg[rr * 33 + lane], beta * old[rr]);
                 }
                 __syncwarp();
             }
