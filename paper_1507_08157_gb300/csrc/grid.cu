@@ -292,6 +292,30 @@ __device__ void fft_tables(const Plan &pl, typename C2<T>::t *tw, unsigned char 
     }
 }
 
+// One Stockham stage of radix R (a compile-time constant, so that the R values of a butterfly
+// stay in registers) on one line: butterflies j = t0, t0 + tpl, ... < nb = n / R.
+template <typename T, int SG, int R>
+__device__ __forceinline__ void fft_stage(const typename C2<T>::t *src, typename C2<T>::t *dst, int nb, int Ns,
+                                          int t0, int tpl, const typename C2<T>::t *tws,
+                                          const unsigned char *kks) {
+    using V = typename C2<T>::t;
+    for (int j = t0; j < nb; j += tpl) {
+        V v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = src[j + r * nb];
+        const int kk = kks[j];
+        if (Ns > 1) {
+            const V *w = tws + kk * (R - 1) - 1;
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], w[r].x, SG < 0 ? w[r].y : -w[r].y);
+        }
+        small_dft<T, SG>(R, v);
+        const int base = (j - kk) * R + kk;
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst[base + r * Ns] = v[r];
+    }
+}
+
 // FFT of `lines` lines of length n held at buf0 (line-major, lines ld >= n apart); returns the
 // buffer with the result. blockDim.x / lines threads work on each line (lines divides blockDim.x).
 template <typename T, int SG>
@@ -309,17 +333,11 @@ __device__ typename C2<T>::t *fft_lines(typename C2<T>::t *buf0, typename C2<T>:
         if (line < lines) {
             const V *src = in + line * ld;
             V *dst = out + line * ld;
-            for (int j = t0; j < nb; j += tpl) {
-                V v[5];
-                for (int r = 0; r < R; ++r) v[r] = src[j + r * nb];
-                const int kk = kkt[koff + j];
-                if (Ns > 1) {
-                    const V *w = tw + toff + kk * (R - 1) - 1;
-                    for (int r = 1; r < R; ++r) v[r] = cmul(v[r], w[r].x, SG < 0 ? w[r].y : -w[r].y);
-                }
-                small_dft<T, SG>(R, v);
-                const int base = (j - kk) * R + kk;
-                for (int r = 0; r < R; ++r) dst[base + r * Ns] = v[r];
+            switch (R) {
+                case 2: fft_stage<T, SG, 2>(src, dst, nb, Ns, t0, tpl, tw + toff, kkt + koff); break;
+                case 3: fft_stage<T, SG, 3>(src, dst, nb, Ns, t0, tpl, tw + toff, kkt + koff); break;
+                case 4: fft_stage<T, SG, 4>(src, dst, nb, Ns, t0, tpl, tw + toff, kkt + koff); break;
+                default: fft_stage<T, SG, 5>(src, dst, nb, Ns, t0, tpl, tw + toff, kkt + koff); break;
             }
         }
         __syncthreads();

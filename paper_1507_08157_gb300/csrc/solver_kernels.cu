@@ -62,9 +62,34 @@ struct YSet {
 // sums the partials over slices in float64. float64 arithmetic is scarce on this part, so it is
 // kept off the per-element path.
 constexpr int RUN = 32;
-constexpr int TI = 4, TJ = 8;
+constexpr int TI = 4;   // pair tile: TI x TJ (TJ = 8 for scalar loads, 4 for pairs of elements)
 
-template <typename T>
+// VEC consecutive elements per load (float4 / double2 when every row start is aligned and len
+// a multiple of VEC), so that more bytes are in flight per load instruction
+template <typename T, int VEC> struct VecLd;
+template <typename T> struct VecLd<T, 1> {
+    static __device__ __forceinline__ void ld(const T *p, long long e, T *o) { o[0] = p[e]; }
+};
+template <> struct VecLd<float, 2> {
+    static __device__ __forceinline__ void ld(const float *p, long long e, float *o) {
+        const float2 v = reinterpret_cast<const float2 *>(p)[e];
+        o[0] = v.x, o[1] = v.y;
+    }
+};
+template <> struct VecLd<float, 4> {
+    static __device__ __forceinline__ void ld(const float *p, long long e, float *o) {
+        const float4 v = reinterpret_cast<const float4 *>(p)[e];
+        o[0] = v.x, o[1] = v.y, o[2] = v.z, o[3] = v.w;
+    }
+};
+template <> struct VecLd<double, 2> {
+    static __device__ __forceinline__ void ld(const double *p, long long e, double *o) {
+        const double2 v = reinterpret_cast<const double2 *>(p)[e];
+        o[0] = v.x, o[1] = v.y;
+    }
+};
+
+template <typename T, int VEC, int TJ>
 __global__ void __launch_bounds__(256, 2) gram_tiled(const T *__restrict__ X, long long sx, int nx,
                                                      const YSet<T> ys, long long sy, int ny,
                                                      long long len, int tiles_j, double *__restrict__ partial,
@@ -84,18 +109,31 @@ __global__ void __launch_bounds__(256, 2) gram_tiled(const T *__restrict__ X, lo
 #pragma unroll
         for (int b = 0; b < TJ; ++b) tot[a][b] = T(0), run[a][b] = T(0);
     const long long stride = (long long)gridDim.y * blockDim.x;
+    const long long nvec = len / VEC;
     int cnt = 0;
-    for (long long e = blockIdx.y * (long long)blockDim.x + threadIdx.x; e < len; e += stride) {
-        T xv[TI], yv[TJ];
+    for (long long e = blockIdx.y * (long long)blockDim.x + threadIdx.x; e < nvec; e += stride) {
+        T xv[TI][VEC], yv[TJ][VEC];
 #pragma unroll
-        for (int a = 0; a < TI; ++a) xv[a] = (i0 + a < nx) ? X[(i0 + a) * sx + e] : T(0);
+        for (int a = 0; a < TI; ++a) {
+            if (i0 + a < nx) VecLd<T, VEC>::ld(X + (i0 + a) * sx, e, xv[a]);
+            else
 #pragma unroll
-        for (int b = 0; b < TJ; ++b) yv[b] = (j0 + b < ny) ? yr[b][e] : T(0);
+                for (int u = 0; u < VEC; ++u) xv[a][u] = T(0);
+        }
 #pragma unroll
-        for (int a = 0; a < TI; ++a)
+        for (int b = 0; b < TJ; ++b) {
+            if (j0 + b < ny) VecLd<T, VEC>::ld(yr[b], e, yv[b]);
+            else
 #pragma unroll
-            for (int b = 0; b < TJ; ++b) run[a][b] = fma(xv[a], yv[b], run[a][b]);
-        if (++cnt == RUN) {
+                for (int u = 0; u < VEC; ++u) yv[b][u] = T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < VEC; ++u)
+#pragma unroll
+            for (int a = 0; a < TI; ++a)
+#pragma unroll
+                for (int b = 0; b < TJ; ++b) run[a][b] = fma(xv[a][u], yv[b][u], run[a][b]);
+        if (++cnt == RUN / VEC) {
 #pragma unroll
             for (int a = 0; a < TI; ++a)
 #pragma unroll
@@ -993,9 +1031,18 @@ void gram_multi(cudaStream_t st, const T *X, long long sx, int nx, int nset, con
         go.g[q] = q < nset ? G[q] : G[0];
     }
     ys.per = per;
-    const int ti = (nx + TI - 1) / TI, tj = (ny + TJ - 1) / TJ;
     const int slices = trace_slices(len, TRACE_SLICES, 2 * TRACE_SLICES);
-    gram_tiled<T><<<dim3(ti * tj, slices), 256, 0, st>>>(X, sx, nx, ys, sy, ny, len, tj, scratch, pairs);
+    constexpr int VW = sizeof(T) == 4 ? 4 : 2;   // 16-byte loads
+    bool vec = len % VW == 0 && sx % VW == 0 && sy % VW == 0 && reinterpret_cast<uintptr_t>(X) % 16 == 0;
+    for (int q = 0; q < nset; ++q) vec = vec && reinterpret_cast<uintptr_t>(Y[q]) % 16 == 0;
+    const int ti = (nx + TI - 1) / TI;
+    if (vec) {
+        const int tj = (ny + 3) / 4;
+        gram_tiled<T, VW, 4><<<dim3(ti * tj, slices), 256, 0, st>>>(X, sx, nx, ys, sy, ny, len, tj, scratch, pairs);
+    } else {
+        const int tj = (ny + 7) / 8;
+        gram_tiled<T, 1, 8><<<dim3(ti * tj, slices), 256, 0, st>>>(X, sx, nx, ys, sy, ny, len, tj, scratch, pairs);
+    }
     check_launch("gram_tiled");
     gram_final_multi<<<(pairs + 7) / 8, 256, 0, st>>>(scratch, slices, pairs, ny, per, go);
     check_launch("gram_final");
