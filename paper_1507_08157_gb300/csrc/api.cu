@@ -214,10 +214,11 @@ struct Impl {
     int *live_tiles = nullptr;            // tiles with both chi and phi (the persistent density's items)
     int nlive = 0;
     int CK = 0, NPmax = 0, nslots_chi = 0, nslots_phi = 0, maxc = 0;
+    int NPint = 0;            // phi rows of the integrals' B stage (the largest unit's phi, to 16)
     bool grid_tc = false, integrals_tc = false;
     bool phi_quads = false;   // every tile's phi list is whole aligned groups of 4 (vector gather)
-    // integrals launches: tiles holding chi and phi, grouped by 128-row chi blocks (1, 2, 3)
-    int *int_tiles = nullptr;
+    // integrals launches: units (tiles, or chunks of dense tiles) grouped by 128-row chi blocks
+    VTile *int_units = nullptr;
     int int_count[3] = {0, 0, 0};
     unsigned *tc_bits = nullptr;
     float *tc_scale = nullptr;
@@ -285,7 +286,7 @@ void potential_integrals_tc(cudaStream_t st, const GridShape &g, const TileSet<f
                             const TileSet<float> &phi, const unsigned short *chi_fm16, int nslots,
                             const unsigned short *phi_fm16, int nslots_phi, int NPmax,
                             int maxc, int nchi, int nphi, const float *V, int k, float *out, unsigned *scratch_bits,
-                            float *scale, const int *tile_list, const int *tiles_by_blocks, int *err);
+                            float *scale, const VTile *unit_list, const int *units_by_blocks, int *err);
 void response_density_tc(cudaStream_t st, const GridShape &g, const TileSet<float> &chi,
                          const TileSet<float> &phi, const unsigned short *chi_pm, int CK, int NPmax, int nphi,
                          const float *P, long long sP, int k, float *rho, unsigned *scratch_bits,
@@ -563,8 +564,8 @@ void integrals(tddft_ctx *c, Impl<T> &I, int ns) {
     if constexpr (sizeof(T) == 4) {
         if (I.integrals_tc) {
             potential_integrals_tc(c->st, c->grid(), I.chi, I.phi, I.chi_fm16, I.nslots_chi, I.phi_fm16, I.nslots_phi,
-                                   I.NPmax, I.maxc, c->nc,
-                                   c->nv, I.V, ns, I.Vmat, I.tc_bits, I.tc_scale, I.int_tiles, I.int_count,
+                                   I.NPint, I.maxc, c->nc,
+                                   c->nv, I.V, ns, I.Vmat, I.tc_bits, I.tc_scale, I.int_units, I.int_count,
                                    tc_error_word());
             return;
         }
@@ -777,10 +778,22 @@ void build_impl(tddft_ctx *c, const tddft_system *s) {
             }
             const int CK = std::max(64, (maxc + 63) / 64 * 64);
             const int NP = std::max(16, (maxp + 15) / 16 * 16);
+            // float32 tables on the host, fetched once for whichever tensor-core path needs them
+            std::vector<float> cval, pv;
+            auto fetch_tables = [&]() {
+                if (cval.empty()) {
+                    cval.resize((size_t)coff[ntl] * TILE_PTS);
+                    check(cudaMemcpy(cval.data(), I->chi.val, cval.size() * sizeof(float), cudaMemcpyDeviceToHost),
+                          "D2H chi tables");
+                }
+                if (pv.empty()) {
+                    pv.resize((size_t)poff[ntl] * TILE_PTS);
+                    check(cudaMemcpy(pv.data(), I->phi.val, pv.size() * sizeof(float), cudaMemcpyDeviceToHost),
+                          "D2H phi tables");
+                }
+            };
             if (NP <= 256 && density_tc_group(CK / 64, NP, 1) >= 1) {
-                std::vector<float> cval((size_t)coff[ntl] * TILE_PTS);
-                check(cudaMemcpy(cval.data(), I->chi.val, cval.size() * sizeof(float), cudaMemcpyDeviceToHost),
-                      "D2H chi tables");
+                fetch_tables();
                 std::vector<unsigned short> pm((size_t)ntl * TILE_PTS * CK, 0);
                 build_point_major_f16(coff.data(), cval.data(), nullptr, ntl, CK, pm.data());
                 I->chi_pm = I->mem.template alloc<unsigned short>(pm.size());
@@ -797,11 +810,7 @@ void build_impl(tddft_ctx *c, const tddft_system *s) {
                         check(cudaMemcpy(I->live_tiles, live.data(), live.size() * sizeof(int), cudaMemcpyHostToDevice),
                               "upload live tiles");
                 }
-                // phi tables on the host once: point-major f16 for the density epilogue (and the
-                // function-major f16 copy of the integrals below)
-                std::vector<float> pv((size_t)poff[ntl] * TILE_PTS);
-                check(cudaMemcpy(pv.data(), I->phi.val, pv.size() * sizeof(float), cudaMemcpyDeviceToHost),
-                      "D2H phi tables");
+                // point-major f16 phi tables for the density epilogue
                 if (NP % 32 == 0) {
                     std::vector<unsigned short> ppm((size_t)ntl * TILE_PTS * NP, 0);
                     build_point_major_f16(poff.data(), pv.data(), nullptr, ntl, NP, ppm.data());
@@ -828,13 +837,41 @@ void build_impl(tddft_ctx *c, const tddft_system *s) {
                     const char *nq = std::getenv("TDDFT_NO_QUAD_GATHER");
                     I->phi_quads = ok && !(nq && nq[0] == '1');
                 }
-                I->maxc = maxc;
-                if (integrals_tc_group(NP, 1, maxc) >= 1) {
+            }
+            // integrals: units of at most 384 chi and 128 phi slots of one tile (a denser tile is
+            // cut into several). TDDFT_INTEGRALS_CHUNK="nc,np" cuts smaller units (multiples of
+            // 128 and 16), for tests of the cut on small systems.
+            {
+                int cch = 384, pch = 128;
+                if (const char *e = std::getenv("TDDFT_INTEGRALS_CHUNK")) {
+                    int a = 0, b = 0;
+                    if (std::sscanf(e, "%d,%d", &a, &b) == 2 && a >= 128 && a <= 384 && a % 128 == 0 && b >= 16 &&
+                        b <= 128 && b % 16 == 0) {
+                        cch = a;
+                        pch = b;
+                    }
+                }
+                std::vector<VTile> by[3];
+                int maxnc = 0, maxnp = 0;
+                for (int t = 0; t < ntl; ++t) {
+                    const int nct = coff[t + 1] - coff[t], npt = poff[t + 1] - poff[t];
+                    if (nct == 0 || npt == 0) continue;
+                    for (int cc = 0; cc < nct; cc += cch)
+                        for (int pc = 0; pc < npt; pc += pch) {
+                            const VTile u{t, coff[t] + cc, std::min(cch, nct - cc), poff[t] + pc, std::min(pch, npt - pc), 0};
+                            maxnc = std::max(maxnc, u.nc);
+                            maxnp = std::max(maxnp, u.np);
+                            by[(u.nc - 1) / 128].push_back(u);
+                        }
+                }
+                const int NPi = std::max(16, (maxnp + 15) / 16 * 16);
+                if (integrals_tc_group(NPi, 1, maxnc) >= 1) {
+                    fetch_tables();
                     std::vector<unsigned short> fm(cval.size());
 #pragma omp parallel for schedule(static)
                     for (long long i = 0; i < (long long)cval.size(); ++i)
                         fm[i] = __half_as_ushort(__float2half_rn(cval[i]));
-                    I->chi_fm16 = I->mem.template alloc<unsigned short>(fm.size());
+                    I->chi_fm16 = I->mem.template alloc<unsigned short>(std::max<size_t>(1, fm.size()));
                     check(cudaMemcpy(I->chi_fm16, fm.data(), fm.size() * sizeof(unsigned short),
                                      cudaMemcpyHostToDevice),
                           "upload f16 chi");
@@ -851,22 +888,18 @@ void build_impl(tddft_ctx *c, const tddft_system *s) {
                               "upload f16 phi");
                         I->nslots_phi = poff[ntl];
                     }
-                    std::vector<int> by[3];
-                    for (int t = 0; t < ntl; ++t) {
-                        const int nct = coff[t + 1] - coff[t], npt = poff[t + 1] - poff[t];
-                        if (nct == 0 || npt == 0) continue;
-                        by[std::min(2, (nct - 1) / 128)].push_back(t);
-                    }
-                    std::vector<int> all;
+                    std::vector<VTile> all;
                     for (int q = 0; q < 3; ++q) {
                         I->int_count[q] = (int)by[q].size();
                         all.insert(all.end(), by[q].begin(), by[q].end());
                     }
-                    I->int_tiles = I->mem.template alloc<int>(std::max<size_t>(1, all.size()));
+                    I->int_units = I->mem.template alloc<VTile>(std::max<size_t>(1, all.size()));
                     if (!all.empty())
-                        check(cudaMemcpy(I->int_tiles, all.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice),
-                              "upload integrals tile lists");
-                    I->integrals_tc = NP <= 128;
+                        check(cudaMemcpy(I->int_units, all.data(), all.size() * sizeof(VTile), cudaMemcpyHostToDevice),
+                              "upload integrals units");
+                    I->maxc = maxnc;
+                    I->NPint = NPi;
+                    I->integrals_tc = true;
                 }
             }
         }

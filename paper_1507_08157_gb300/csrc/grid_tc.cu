@@ -739,8 +739,9 @@ __device__ __forceinline__ void red_add_v4(float *addr, float a, float b, float 
                  : "memory");
 }
 
-// CTA = (state, tile of the launch's list); mbmax: most chi row blocks of a listed tile (sizes the
-// X stages), tmem_cols: TMEM columns allocated (mbmax x acc_stride, a power of two). Per 64-point
+// CTA = (state, unit of the launch's list: a tile, or a chunk of a dense tile's chi and phi
+// slots); mbmax: most chi row blocks of a listed unit (sizes the X stages), tmem_cols: TMEM
+// columns allocated (mbmax x acc_stride, a power of two). Per 64-point
 // K slice the TMA warp loads the tile's chi rows (mX) and its phi rows (mP, float16 copies of the
 // phi tables) straight into the B operand's stage; four warps then scale that stage in place by
 // V at its points (shared memory only), and the MMA warp multiplies. Rows of the stage past the
@@ -748,16 +749,16 @@ __device__ __forceinline__ void red_add_v4(float *addr, float a, float b, float 
 __global__ void __launch_bounds__(192, 3) integrals_tc_kernel(
     const __grid_constant__ CUtensorMap mX,   // function-major chi: [slot][512] f16
     const __grid_constant__ CUtensorMap mP,   // function-major phi: [slot][512] f16, box NP rows
-    int n, int nt, int NP, int k, const int *__restrict__ coff, const int *__restrict__ cids,
-    const int *__restrict__ poff, const int *__restrict__ pids, int nchi, int nphi, const float *__restrict__ V,
-    const float *__restrict__ vscale, float dV, float *__restrict__ out, bool vec_ok, int acc_stride,
-    const int *__restrict__ tiles, int mbmax, int tmem_cols, int *err) {
+    int n, int nt, int NP, int k, const int *__restrict__ cids, const int *__restrict__ pids, int nchi,
+    int nphi, const float *__restrict__ V, const float *__restrict__ vscale, float dV, float *__restrict__ out,
+    bool vec_ok, int acc_stride, const VTile *__restrict__ units, int mbmax, int tmem_cols, int *err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<unsigned long long>(smem_raw) + 1023ull) & ~1023ull);
-    const int t = tiles[blockIdx.y], s0 = blockIdx.x;
-    const int c0 = coff[t], nc = coff[t + 1] - c0;
-    const int p0 = poff[t], np = poff[t + 1] - p0;
+    const VTile u = units[blockIdx.y];
+    const int t = u.t, s0 = blockIdx.x;
+    const int c0 = u.c0, nc = u.nc;
+    const int p0 = u.p0, np = u.np;
     if (nc == 0 || np == 0) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int MB = (nc + 127) / 128;                 // <= mbmax (the host lists tiles by M blocks)
@@ -920,7 +921,7 @@ void potential_integrals_tc(cudaStream_t st, const GridShape &g, const TileSet<f
                             const TileSet<float> &phi, const unsigned short *chi_fm16, int nslots,
                             const unsigned short *phi_fm16, int nslots_phi, int NPmax,
                             int maxc, int nchi, int nphi, const float *V, int k, float *out, unsigned *scratch_bits,
-                            float *scale, const int *tile_list, const int *tiles_by_blocks, int *err) {
+                            float *scale, const VTile *unit_list, const int *units_by_blocks, int *err) {
     if (k <= 0) return;
     ProfScope ps(st, ST_INTEGRALS, 2.0 * k * g.pair_points,
                  2.0 * g.table_values + 4.0 * k * g.n * g.n * g.n + 4.0 * k * nchi * nphi);
@@ -940,7 +941,7 @@ void potential_integrals_tc(cudaStream_t st, const GridShape &g, const TileSet<f
     if (!encode_map_2d(&mp, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, phi_fm16, (unsigned long long)TILE_PTS,
                        (unsigned long long)nslots_phi, (unsigned long long)TILE_PTS * 2, 64, NPmax))
         throw CudaError{cudaErrorInvalidValue, "cuTensorMapEncodeTiled (integrals phi)"};
-    // one launch per class of tiles by 128-row chi blocks (1, 2, 3), one state per CTA: the
+    // one launch per class of units by 128-row chi blocks (1, 2, 3), one state per CTA: the
     // smaller a class's shared memory and TMEM, the more CTAs share an SM (3, 2, 1)
     if (NPmax > 128) throw CudaError{cudaErrorInvalidValue, "integrals_tc: more than 128 phi per tile"};
     static const bool attr = [&]() {   // once per process, thread-safe
@@ -950,10 +951,10 @@ void potential_integrals_tc(cudaStream_t st, const GridShape &g, const TileSet<f
     }();
     (void)attr;
     const bool vec_ok = (nphi % 4 == 0) && ((reinterpret_cast<unsigned long long>(out) & 15ull) == 0);
-    const int *lp = tile_list;
+    const VTile *lp = unit_list;
     for (int c = 0; c < 3; ++c) {
-        const int cnt = tiles_by_blocks[c];
-        const int *lst = lp;
+        const int cnt = units_by_blocks[c];
+        const VTile *lst = lp;
         lp += cnt;
         if (cnt == 0) continue;
         const int mbmax = c + 1;
@@ -961,9 +962,9 @@ void potential_integrals_tc(cudaStream_t st, const GridShape &g, const TileSet<f
         const int tmem_cols = mbmax == 1 ? 128 : (mbmax == 2 ? 256 : 512);
         const size_t sm = integrals_tc_smem(NPmax, 1, mbmax);
         dim3 grid(k, cnt);
-        integrals_tc_kernel<<<grid, 192, sm, st>>>(mx, mp, g.n, g.nt, NPmax, k, chi.off, chi.ids, phi.off, phi.ids,
-                                                   nchi, nphi, V, scale, (float)g.dV, out, vec_ok, stride, lst,
-                                                   mbmax, tmem_cols, err);
+        integrals_tc_kernel<<<grid, 192, sm, st>>>(mx, mp, g.n, g.nt, NPmax, k, chi.ids, phi.ids, nchi, nphi, V,
+                                                   scale, (float)g.dV, out, vec_ok, stride, lst, mbmax, tmem_cols,
+                                                   err);
         check_launch("integrals_tc_kernel");
     }
 }

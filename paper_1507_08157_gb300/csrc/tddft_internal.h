@@ -75,6 +75,16 @@ struct TileSet {
     const T *val = nullptr;       // [slots][512]
 };
 
+// One unit of the tensor-core integrals launches: a grid tile with a chunk of its chi slots (at
+// most three 128-row blocks) and a chunk of its phi slots (at most 128). A tile whose lists fit is
+// one unit; a denser tile is cut into several units, each adding its part into the output.
+struct VTile {
+    int t;        // grid tile (whose 512 points the unit sums over)
+    int c0, nc;   // first chi slot, count
+    int p0, np;   // first phi slot, count
+    int pad;
+};
+
 struct GridShape {
     int n;          // points per side
     int nt;         // tiles per side = ceil(n / 8)

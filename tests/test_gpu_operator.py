@@ -1,8 +1,9 @@
 """Parity of the CUDA operator path with the FP64 oracle, element by element, through the C ABI.
 
 Cases: a 3-atom system on a 30^3 grid (tiles of 8 leave a ragged tail of 6), a 2-atom system whose
-boxes wrap the periodic cell on every axis (20^3), a 9-chi (s, p, d) system, and the 8-atom /
-48^3 workload. Tolerances, relative to the largest reference entry:
+boxes wrap the periodic cell on every axis (20^3), a 9-chi (s, p, d) system, the 8-atom /
+48^3 workload, and a dense 24-atom system whose tiles are cut into several tensor-core
+integrals units. Tolerances, relative to the largest reference entry:
   * FP64 mode: 1e-10;
   * mixed mode, float32 stages (FFT Poisson + f_xc, potential integrals, matrix products on
     three-term-split TF32 tensor cores): 3e-5 (float32 roundoff 6e-8 times ~500-term tile sums and
@@ -44,6 +45,8 @@ def _systems():
         "tiny30": sy.Recipe(natoms=3, cell_ang=10.0, ngrid=30, radius_ang=4.0, seed=11),
         "wrap20": sy.Recipe(natoms=2, cell_ang=7.0, ngrid=20, radius_ang=2.8, seed=5),
         "d9": sy.Recipe(natoms=3, cell_ang=10.0, ngrid=30, nchi=9, radius_ang=4.0, seed=12),
+        # dense: up to 162 chi and 72 phi per tile, 36^3 grid (ragged tail of 4)
+        "dense24": sy.Recipe(natoms=24, cell_ang=12.0, ngrid=36, nchi=9, radius_ang=4.5, seed=31),
     }
 
 
@@ -148,3 +151,22 @@ def test_invalid_sizes_are_rejected(tddft):
     with pytest.raises(tddft.TddftError) as e:
         tddft.Context(bad, precision="fp64")
     assert e.value.status == tddft.E_INVALID
+
+
+@pytest.mark.parametrize("chunk", ["128,16", "384,128"])
+def test_integrals_units_of_dense_tiles(tddft, monkeypatch, chunk):
+    # "128,16" cuts every tile of the dense system into units of at most 128 chi and 16 phi
+    # (up to 2 x 5 units per tile, each adding its part into the output); "384,128" is the
+    # default, under which these tiles are whole units
+    s = system("dense24")
+    monkeypatch.setenv("TDDFT_INTEGRALS_CHUNK", chunk)
+    ctx = tddft.Context(s, precision="mixed")
+    V = np.random.default_rng(9).standard_normal((3, s.n, s.n, s.n))
+    got = ctx.potential_integrals(V)
+    ref = ogrid.potential_integrals(ogrid.BoxedSet(s.chi, s.n), ogrid.BoxedSet(s.phi, s.n), V, s.dV)
+    assert _err(got, ref) < TOL_DENSITY["mixed"]
+    Pp, Pq = sy.random_kernels(s, 2, 8)
+    fp, fq = ctx.apply(Pp, Pq)
+    rp, rq = oop.Operator(s).apply(Pp, Pq)
+    assert _err(fp, rp) < TOL["mixed"] and _err(fq, rq) < TOL_DENSITY["mixed"]
+    ctx.close()
