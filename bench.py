@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--batch-max-atoms", type=int, default=300)
     ap.add_argument("--batch-seed", type=int, default=3)
     ap.add_argument("--batch-workers", type=int, default=8, help="processes generating the systems")
+    ap.add_argument("--batch-pool-atoms", type=int, default=150,
+                    help="systems from this size up are generated in the main process (pooled table sums)")
     ap.add_argument("--scaling", default="",
                     help="comma-separated atom counts of the core + shell series: time operator applies "
                          "on each (one JSON line with the series)")
@@ -457,11 +459,19 @@ def run_batched(args):
     tol = 3e-4
     ctxs, states, meta = [], [], []
     t_gen = t_create = 0.0
+    # large systems are generated one at a time in this process, whose generator spreads their
+    # table sums over a process pool of its own (a pool worker cannot start one); the rest go to
+    # the worker pool a chunk at a time
+    big = [i for i in order if recs[i][0].natoms >= args.batch_pool_atoms]
+    rest = [i for i in order if recs[i][0].natoms < args.batch_pool_atoms]
+    chunks = [[i] for i in big] + [rest[c:c + workers] for c in range(0, len(rest), workers)]
     try:
-        for c0 in range(0, len(order), workers):
-            chunk = order[c0:c0 + workers]
+        for chunk in chunks:
             t0 = time.perf_counter()
-            systems = pool.map(_generate, [recs[i][0] for i in chunk])
+            if len(chunk) == 1 and recs[chunk[0]][0].natoms >= args.batch_pool_atoms:
+                systems = [sy.generate(recs[chunk[0]][0])]
+            else:
+                systems = pool.map(_generate, [recs[i][0] for i in chunk])
             t1 = time.perf_counter()
             cs = tddft.create_batch(systems, precision="mixed", tol=tol, max_iter=400, precond=args.precond)
             for i, c, sys_ in zip(chunk, cs, systems):
