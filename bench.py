@@ -74,6 +74,24 @@ def workload_name(args):
 
 
 # ------------------------------------------------------------------------------------------------
+# N replicas (one per GPU): the job's time is the slowest rank's, its rate all ranks' units over it
+def max_over_ranks(ms, world, device):
+    """The largest of the ranks' timed-region lengths (every rank takes part)."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, ms_max):
+    """Units processed by all ranks per second of the slowest rank's timed region."""
+    return units_per_rank * world / (ms_max / 1000.0)
+
+
+# ------------------------------------------------------------------------------------------------
 # GPU clocks during the timed region
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
@@ -309,11 +327,8 @@ def run_ours(args):
     ms = ev0.elapsed_time(ev1)
     prof = ctx.profile_read()
     ctx.profile(False)
-    t = torch.tensor([ms], device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = applies * world / (ms_max / 1000.0)
+    ms_max = max_over_ranks(ms, world, "cuda")
+    value = whole_job_rate(applies, world, ms_max)
 
     # end to end: tddft_apply from pinned host buffers, copies inside the timed region
     Pp, Pq = sy.random_kernels(s, k, 3)
