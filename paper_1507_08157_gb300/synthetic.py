@@ -288,6 +288,12 @@ def _atom_block(fs, ia, nper):
     return fs.val[fs.off[f0]:fs.off[f0 + nper]].reshape(nper, e, e, e), fs.box[f0, :3], e
 
 
+# The per-pair sums below run over the common points XB planes (of x) at a time: the slices of
+# a few planes stay in cache while they are copied and multiplied, where one slice of the whole
+# common box (megabytes) would not.
+XB = 2
+
+
 def _pair_overlap(fa, fb, nper_a, nper_b, ia, ib, n):
     """sum_r f_a(r) f_b(r) for all functions of atoms ia (set fa) and ib (set fb)."""
     A, oa, e = _atom_block(fa, ia, nper_a)
@@ -299,9 +305,11 @@ def _pair_overlap(fa, fb, nper_a, nper_b, ia, ib, n):
     for (ax, bx, lx) in rx:
         for (ay, by, ly) in ry:
             for (az, bz, lz) in rz:
-                a = A[:, ax:ax + lx, ay:ay + ly, az:az + lz].reshape(nper_a, -1)
-                b = B[:, bx:bx + lx, by:by + ly, bz:bz + lz].reshape(nper_b, -1)
-                out += a @ b.T
+                for x in range(0, lx, XB):
+                    px = min(XB, lx - x)
+                    a = A[:, ax + x:ax + x + px, ay:ay + ly, az:az + lz].reshape(nper_a, -1)
+                    b = B[:, bx + x:bx + x + px, by:by + ly, bz:bz + lz].reshape(nper_b, -1)
+                    out += a @ b.T
     return out
 
 
@@ -337,8 +345,8 @@ def _random_hamiltonian(rng, pos, cell, nper, rmax, sigma, decay):
     return H
 
 
-def _density_contrib(fs, nper, K, n, ia, ib):
-    """(index arrays, values) of sum_ab f_a K_ab f_b over the common points of atoms ia, ib."""
+def _density_contrib(fs, nper, K, n, ia, ib, w=1.0):
+    """(index arrays, values) of w sum_ab f_a K_ab f_b over the common points of atoms ia, ib."""
     A, oa, e = _atom_block(fs, ia, nper)
     B, ob, _ = _atom_block(fs, ib, nper)
     Kab = K[ia * nper:(ia + 1) * nper, ib * nper:(ib + 1) * nper]
@@ -349,9 +357,13 @@ def _density_contrib(fs, nper, K, n, ia, ib):
     for (ax, bx, lx) in rx:
         for (ay, by, ly) in ry:
             for (az, bz, lz) in rz:
-                a = A[:, ax:ax + lx, ay:ay + ly, az:az + lz].reshape(nper, -1)
-                b = B[:, bx:bx + lx, by:by + ly, bz:bz + lz].reshape(nper, -1)
-                contrib = np.einsum("ar,ar->r", Kab @ b, a).reshape(lx, ly, lz)
+                planes = []
+                for x in range(0, lx, XB):
+                    px = min(XB, lx - x)
+                    a = A[:, ax + x:ax + x + px, ay:ay + ly, az:az + lz].reshape(nper, -1)
+                    b = B[:, bx + x:bx + x + px, by:by + ly, bz:bz + lz].reshape(nper, -1)
+                    planes.append(w * np.einsum("ar,ar->r", Kab @ b, a))
+                contrib = np.concatenate(planes).reshape(lx, ly, lz)
                 out.append(((int(oa[0]) + ax) % n, (int(oa[1]) + ay) % n, (int(oa[2]) + az) % n,
                             contrib))
     return out
@@ -375,10 +387,11 @@ def _add_parts(out, parts, n):
 
 
 def _density_on_grid(fs, nper, K, pos, cell, n, rmax):
-    """sum_ab f_a(r) K_ab f_b(r) on the full grid, over atom pairs within rmax."""
-    jobs = []
-    for (i, j, _) in _atom_pairs_within(pos, cell, rmax):
-        jobs += [(i, j), (j, i)] if i != j else [(i, i)]
+    """sum_ab f_a(r) K_ab f_b(r) on the full grid, over atom pairs within rmax, for a symmetric K:
+    the (i, j) and (j, i) blocks of a pair of atoms give the same values, so each pair i < j is
+    summed once with weight 2."""
+    K = 0.5 * (K + K.T)
+    jobs = [(i, j, 1.0 if i == j else 2.0) for (i, j, _) in _atom_pairs_within(pos, cell, rmax)]
     partial = _pooled(fs, nper, n, K, _w_density, jobs)
     if partial is not None:
         out = partial[0]
@@ -387,7 +400,7 @@ def _density_on_grid(fs, nper, K, pos, cell, n, rmax):
         return out
     out = np.zeros((n, n, n))
     with concurrent.futures.ThreadPoolExecutor(_workers()) as ex:
-        for parts in ex.map(lambda p: _density_contrib(fs, nper, K, n, p[0], p[1]), jobs):
+        for parts in ex.map(lambda p: _density_contrib(fs, nper, K, n, p[0], p[1], p[2]), jobs):
             _add_parts(out, parts, n)
     return out
 
@@ -417,8 +430,8 @@ def _w_overlap(pairs):
 def _w_density(jobs):
     fs, nper, n, K = _W["fs"], _W["nper"], _W["n"], _W["K"]
     out = np.zeros((n, n, n))
-    for (i, j) in jobs:
-        _add_parts(out, _density_contrib(fs, nper, K, n, i, j), n)
+    for (i, j, w) in jobs:
+        _add_parts(out, _density_contrib(fs, nper, K, n, i, j, w), n)
     return out
 
 
