@@ -370,6 +370,24 @@ tddft_status tddft_profile_read(tddft_ctx *ctx, tddft_stage_stats *out, int32_t 
  * |supp chi_a  intersect  supp phi_b|; table_values = nonzero tabulated values of both sets. */
 tddft_status tddft_work(const tddft_ctx *ctx, double *pair_points, double *table_values);
 
+/* Environment variables. Each selects an alternative code path of the same operation, for
+ * comparisons and tests; none skips work. TDDFT_NO_TC is read once per process, the others at
+ * every tddft_create (or, for TDDFT_NO_PERSISTENT_DENSITY, at the first density launch).
+ *   TDDFT_NO_TC=1                  matrix products on CUDA cores instead of tcgen05 (and with
+ *                                  them the tensor-core grid kernels)
+ *   TDDFT_NO_GRID_TC=1             response density and potential integrals on CUDA cores
+ *   TDDFT_NO_PERSISTENT_DENSITY=1  the per-tile tensor-core density kernel instead of the
+ *                                  persistent one
+ *   TDDFT_NO_QUAD_GATHER=1         gather the density's P block element by element instead of
+ *                                  by aligned groups of four phi
+ *   TDDFT_NO_REDUCED_PRECOND=1     the inner CG of the iterative preconditioner on the full
+ *                                  N_chi x N_phi space instead of the conduction x valence
+ *                                  subspace
+ *   TDDFT_INTEGRALS_CHUNK=nc,np    largest chi / phi slot counts of one tensor-core integrals
+ *                                  unit (multiples of 128 up to 384, and of 16 up to 128;
+ *                                  default 384,128); smaller values cut tiles that would fit,
+ *                                  which tests the cut on small systems */
+
 #ifdef __cplusplus
 }
 #endif
