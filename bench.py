@@ -552,6 +552,7 @@ def run_scaling(args):
         pair_points, table_values = ctx.work()
         Pp, Pq = sy.random_kernels(s, k, 3)
         dPp, dPq = torch.from_numpy(Pp).cuda(), torch.from_numpy(Pq).cuda()
+        cpu = None if args.no_cpu_baseline else cpu_oracle_sample(s)
         del s, Pp, Pq
         for _ in range(args.warmup):
             ctx.apply(dPp, dPq)
@@ -574,7 +575,7 @@ def run_scaling(args):
             "ms_per_apply": ms, "applies_per_s": k / (ms / 1000.0),
             "work_tflop_per_apply": flops / 1e12, "ns_per_mflop": 1e6 * ms / max(flops / 1e6, 1e-30),
             "stages_ms": {n: round(v[1] / args.steps, 3) for n, v in prof.items() if v[0]},
-            "generate_s": t1 - t0, "create_s": t2 - t1,
+            "generate_s": t1 - t0, "create_s": t2 - t1, "cpu_baseline": cpu,
             "clocks": {k_: clk.summary()[k_] for k_ in ("sm_mhz", "sm_max_mhz", "reasons")}})
         ctx.close()
         del dPp, dPq
