@@ -35,3 +35,25 @@ def test_integrals_at_equals_full_sums():
     got = grid.integrals_at(chi, phi, V, s.dV, pairs)
     ref = np.array([[full[q][a, b] for (a, b) in pairs] for q in range(2)])
     assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(full))
+
+
+def test_density_at_wrapping_boxes_against_brute_force():
+    s, chi, phi = _case(sy.Recipe(natoms=2, cell_ang=7.0, ngrid=20, radius_ang=2.8, nchi=9, seed=5))
+    _, Pq = sy.random_kernels(s, 2, 8)
+    X = grid.full_grid(s.chi, s.n).reshape(s.chi.nfun, -1)
+    F = grid.full_grid(s.phi, s.n).reshape(s.phi.nfun, -1)
+    rng = np.random.default_rng(9)
+    pts = [tuple(int(v) for v in rng.integers(0, s.n, size=3)) for _ in range(40)]
+    idx = [(p[0] * s.n + p[1]) * s.n + p[2] for p in pts]
+    ref = np.einsum("ar,sab,br->sr", X[:, idx], Pq, F[:, idx])
+    got = grid.density_at(chi, phi, Pq, pts)
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def test_points_outside_every_support_are_zero():
+    # two atoms in a 4 A cube at the centre of a 16 A cell, 3 A radius: the corners are empty
+    s, chi, phi = _case(sy.Recipe(natoms=2, cell_ang=16.0, ngrid=48, radius_ang=3.0, cluster_ang=4.0, seed=7))
+    _, Pq = sy.random_kernels(s, 1, 10)
+    pts = [(0, 0, 0), (s.n - 1, 0, s.n - 1), (2, s.n - 3, 1)]
+    assert np.all(grid.density_at(chi, phi, Pq, pts) == 0.0)
+    assert np.any(grid.density_at(chi, phi, Pq, [(s.n // 2,) * 3]) != 0.0)
