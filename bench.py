@@ -13,6 +13,11 @@ region). `--impl reference` times the FP64 CPU oracle on a bounded sample of one
 
 Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under torch.distributed.run,
 one independent replica per GPU (the single-system path has no data-parallel split).
+
+Other lines (one JSON line each, not the default):
+  --batched S     S uneven systems solved at once (tddft_create_batch / tddft_solve_batch);
+  --scaling N,..  operator applies on the core + shell series (synthetic.scaling_recipe) at the
+                  given atom counts, with time per unit of algorithmic work.
 """
 import argparse
 import json
