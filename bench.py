@@ -51,6 +51,10 @@ def parse():
                     help="preconditioner of the timed PCG steps (exact: Eq. precond solved in its "
                          "eigenbases; iter: the paper's inner CG to 1e-4)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--learned-train-atoms", type=int, default=16,
+                    help="atoms of the two training systems of the time-to-k comparison")
+    ap.add_argument("--learned-eval-atoms", type=int, default=24,
+                    help="atoms of the unseen system the time-to-k comparison solves")
     ap.add_argument("--no-time-to-k", action="store_true",
                     help="skip the separate time-to-solution report (not part of the timed steps)")
     ap.add_argument("--batched", type=int, default=0,
@@ -428,7 +432,8 @@ def run_ours(args):
     # start from the same vectors on an unseen, larger system
     time_to_k = None
     if rank == 0 and not args.no_time_to_k:
-        time_to_k = learned_vs_plain(tddft, sy, torch, stream)
+        time_to_k = learned_vs_plain(tddft, sy, torch, stream, train_atoms=args.learned_train_atoms,
+                                     eval_atoms=args.learned_eval_atoms)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
