@@ -154,6 +154,54 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------------------------
+def host_cpu():
+    """(logical cores, CPU model) of this host."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if model is None:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    return os.cpu_count(), model or "unknown"
+
+
+def blas_threads(n):
+    """Set the thread count of the BLAS numpy loaded (OpenBLAS or MKL) through its own call;
+    returns False when no such call is found."""
+    import ctypes
+    ok = False
+    try:
+        with open("/proc/self/maps") as f:
+            libs = {l.split()[-1] for l in f if ".so" in l and ("blas" in l.lower() or "mkl" in l.lower())}
+    except OSError:
+        libs = set()
+    for path in libs:
+        try:
+            lib = ctypes.CDLL(path)
+        except OSError:
+            continue
+        for sym in ("openblas_set_num_threads", "openblas_set_num_threads64_", "scipy_openblas_set_num_threads",
+                    "scipy_openblas_set_num_threads64_", "MKL_Set_Num_Threads"):
+            fn = getattr(lib, sym, None)
+            if fn is not None:
+                fn(ctypes.c_int(n))
+                ok = True
+    return ok
+
+
 def cpu_oracle_sample(sys_, target_s=15.0):
     """Time the FP64 oracle's operator application on a bounded sample and scale it to one
     state-pair application: all matrix products and one FFT Poisson solve in full, the response
@@ -183,10 +231,24 @@ def cpu_oracle_sample(sys_, target_s=15.0):
         spent += time.perf_counter() - t1
         m += 1
     per_apply = t_fixed + spent * len(groups) / max(m, 1)
-    return {"value": 1.0 / per_apply, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+    cores, model = host_cpu()
+    return {"value": 1.0 / per_apply, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": model,
+            "estimate": True, "timed_s": t_fixed + spent,
             "sample": (f"one state-pair application: matrix products and FFT Poisson solve in full, "
                        f"grid contractions on the chi functions of {m} of {len(groups)} atoms "
                        f"({spent:.1f} s), scaled linearly; numpy/scipy float64, BLAS threads = all cores")}
+
+
+def cpu_oracle_one_thread(sys_, target_s=6.0):
+    """The same bounded sample with the BLAS on one thread (the grid contractions of the oracle
+    are single-threaded numpy either way)."""
+    if not blas_threads(1):
+        return None
+    try:
+        r = cpu_oracle_sample(sys_, target_s=target_s)
+    finally:
+        blas_threads(os.cpu_count() or 1)
+    return {"value": r["value"], "unit": UNIT, "cores": 1, "sample": r["sample"].replace("all cores", "1")}
 
 
 # ------------------------------------------------------------------------------------------------
@@ -196,19 +258,24 @@ def run_reference(args):
         return
     from paper_1507_08157_gb300 import synthetic as sy
     s = sy.generate(recipe(args.config))
-    vals = []
+    vals, timed = [], []
     for i in range(args.warmup + args.steps):
         r = cpu_oracle_sample(s, target_s=3.0)
         if i >= args.warmup:
             vals.append(r["value"])
+            timed.append(r["timed_s"])
     v = float(np.mean(vals))
+    cores, model = host_cpu()
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * args.k / v,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": workload_name(args), "states": args.k, "precision": "fp64"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": model,
                              "sample": r["sample"]},
+            "estimate": "each step times a bounded sample of one application and scales its grid "
+                        "contractions to the whole system: value and ms_per_step are extrapolated",
+            "timed_s_per_step": float(np.mean(timed)),
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -388,11 +455,7 @@ def run_ours(args):
                 "frac": achieved / peak, "traffic": None, "kernel": name,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained x 1.1/2.25 (tf32/bf16 nominal)",
                 "note": "achieved counts 2MNK per product; the three-term split issues 3 MMAs per product",
-                "frac_of_fp32_accurate_peak": achieved / (peak / 3.0),
-                "traffic_note": "the stage mixes product shapes; ncu DRAM bytes per launch of the operator's "
-                                "left product (1260 x 1260 by 20 x 1260 x 560): 1.26e8 read + 0.32e8 written "
-                                "against 1.82e8 algorithmic; right product 1.15e8 + 0.09e8 against 1.70e8 "
-                                "(profiles/launches_tc_chromophore140.md)"}
+                "frac_of_fp32_accurate_peak": achieved / (peak / 3.0)}
     elif (name in ("potential_integrals", "response_density") and args.precision == "mixed"
           and os.environ.get("TDDFT_NO_TC") != "1" and os.environ.get("TDDFT_NO_GRID_TC") != "1"):
         # tcgen05 kind::f16 grid contractions: the roof is the larger of the algorithmic bytes at
@@ -412,9 +475,7 @@ def run_ours(args):
                      "roof_ms": {"bytes_at_hbm": 1e3 * t_byte, "flops_at_tensor": 1e3 * t_flop,
                                  "measured_per_call": dms / max(launches, 1)},
                      "note": "algorithmic work: 2 k pair_points flops (pairs of nonzero chi and phi values "
-                             "at each grid point) and the tables, grids and outputs read or written once",
-                     "traffic_note": "ncu DRAM bytes per launch: profiles/integrals_tc_chromophore140.md, "
-                                     "profiles/density_tc_chromophore140.md"})
+                             "at each grid point) and the tables, grids and outputs read or written once"})
     else:
         # CUDA-core float32 (mixed) or float64 contraction: ALU bound.
         lanes = 128 if args.precision == "mixed" else 2
@@ -452,6 +513,7 @@ def run_ours(args):
                 "omega_last": [float(x) for x in om], "resid_last": [float(x) for x in res]}
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_oracle_sample(s)
+            line["cpu_baseline"]["one_thread"] = cpu_oracle_one_thread(s)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -39,7 +39,14 @@ typedef enum {
     TDDFT_E_CUDA = 3,           /* CUDA runtime error (message names the call) */
     TDDFT_E_NOT_CONVERGED = 4,  /* tddft_solve hit max_iter; outputs hold the last iterate */
     TDDFT_E_BREAKDOWN = 5,      /* NaN/Inf, or a non-positive norm in Gram-Schmidt */
-    TDDFT_E_TIMEOUT = 6,        /* reserved: a bounded device wait expired */
+    TDDFT_E_TIMEOUT = 6,        /* a bounded wait inside a tensor-core kernel expired (limit:
+                                   tddft_options.spin_limit_cycles). Any call that runs the
+                                   tensor-core products or grid kernels of a TDDFT_MIXED context
+                                   (apply, the component entry points, state_create, pcg_step,
+                                   solve, oscillator_strengths, the allocation-free density) and
+                                   tddft_wait_check can return it; the kernel gives up, lets its
+                                   copies in flight land, frees its tensor memory and returns, and
+                                   the context stays usable */
     TDDFT_E_PAIRING = 7         /* converged pairs fail the +-omega pairing check */
 } tddft_status;
 
@@ -105,12 +112,16 @@ typedef struct {
     int32_t precond_adaptive; /* 0: inner CG to precond_tol every step. 1: loose first, tight at the
                                  end (Sec. IV A suggests it): the step's inner tolerance is
                                  min(0.1, max(precond_tol, largest residual of the iterate in Ha)) */
+    int64_t spin_limit_cycles; /* limit of every bounded wait in the context's tensor-core kernels,
+                                 in SM clock cycles (clock64); <= 0: the default 4e9 (about 2 s).
+                                 An expired wait makes the call return TDDFT_E_TIMEOUT */
 } tddft_options;
 
 typedef struct tddft_ctx tddft_ctx;
 typedef struct tddft_state tddft_state;
 
-/* Fill *opt with the defaults: FP64, FULL, ITER, 50, 1e-4, tol 1e-6, 500, 10, 10, not adaptive. */
+/* Fill *opt with the defaults: FP64, FULL, ITER, 50, 1e-4, tol 1e-6, 500, 10, 10, not adaptive,
+ * spin limit 0 (the default 4e9 cycles). */
 void tddft_default_options(tddft_options *opt);
 
 /* Build a context on the current CUDA device: copies the system to the device, builds the
@@ -169,6 +180,13 @@ tddft_status tddft_response_density(tddft_ctx *ctx, int32_t k, const double *P, 
 tddft_status tddft_response_potential(tddft_ctx *ctx, int32_t k, const double *rho, double *V);
 tddft_status tddft_potential_integrals(tddft_ctx *ctx, int32_t k, const double *V, double *out);
 tddft_status tddft_fxc(tddft_ctx *ctx, double *fxc);
+
+/* Check of the bounded-wait path (no counterpart in the paper; it tests the library's failure
+ * detection without faulting or hanging the GPU): launches one small kernel on the context's
+ * stream that waits, with the context's spin_limit_cycles, on a shared-memory barrier that
+ * nothing completes, so the wait must expire. Returns TDDFT_E_TIMEOUT when it did and the
+ * context is usable afterwards (the expected result); TDDFT_E_CUDA if the launch failed. */
+tddft_status tddft_wait_check(tddft_ctx *ctx);
 
 /* Allocation-free response density. The paper has no counterpart: this is a library-level
  * variant of tddft_response_density for callers that cannot allocate device memory when they

@@ -177,6 +177,16 @@ struct TimeoutErr {
     std::string msg;
 };
 
+// device ordinal of a device (or managed) pointer, -1 for anything else
+int device_of(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) ? a.device : -1;
+}
+
 bool is_device_ptr(const void *p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -266,6 +276,7 @@ struct tddft_ctx {
     bool own_stream = false;
     cudaEvent_t sync_ev = nullptr;
     int *hword = nullptr;   // pinned: the tensor-core kernels' error word, read with each status
+    int device = 0;         // the CUDA device the context was made on
     GridShape grid() const { return GridShape{n, nt, cell, dV, pair_points, table_values}; }
     ~tddft_ctx();
     long long len() const { return (long long)nc * nv; }
@@ -278,6 +289,7 @@ int *tc_error_word();
 void tc_error_fetch(cudaStream_t st, int *host);
 void tc_release_stream(cudaStream_t st);
 void tc_error_clear(cudaStream_t st);
+void tc_wait_probe(cudaStream_t st);
 void build_point_major_f16(const int *off_h, const float *val_h_or_null, const double *vald_h_or_null,
                            int ntiles, int CK, unsigned short *out_h);
 int density_tc_group(int KBmax, int NP, int k);
@@ -355,10 +367,19 @@ struct ProfilerBinding {
     ~ProfilerBinding() { active_profiler() = nullptr; }
 };
 
+// the context's bounded-wait limit for the kernels launched during one call
+struct WaitLimitBinding {
+    WaitLimitBinding(tddft_ctx *c) {
+        active_wait_limit() = c->opt.spin_limit_cycles > 0 ? (long long)c->opt.spin_limit_cycles : DEFAULT_WAIT_LIMIT;
+    }
+    ~WaitLimitBinding() { active_wait_limit() = DEFAULT_WAIT_LIMIT; }
+};
+
 template <typename F>
 tddft_status guarded(tddft_ctx *c, F &&f) {
     try {
         ProfilerBinding pb(c);
+        WaitLimitBinding wb(c);
         return f();
     } catch (const CudaError &e) {
         c->err = std::string(e.where) + ": " + cudaGetErrorString(e.code);
@@ -1580,6 +1601,7 @@ void tddft_default_options(tddft_options *o) {
     o->reapply_every = 10;
     o->restart_every = 10;
     o->precond_adaptive = 0;
+    o->spin_limit_cycles = 0;
 }
 
 tddft_status tddft_create(const tddft_system *s, const tddft_options *opt, void *stream,
@@ -1644,6 +1666,7 @@ tddft_status tddft_create(const tddft_system *s, const tddft_options *opt, void 
                     c->amask[(size_t)a * s->natoms + b] = std::sqrt(d2) <= s->kernel_cutoff ? 1 : 0;
                 }
         }
+        check(cudaGetDevice(&c->device), "cudaGetDevice");
         check(cudaMallocHost(reinterpret_cast<void **>(&c->hword), sizeof(int)), "cudaMallocHost");
         *c->hword = 0;
         if (c->prec == TDDFT_FP64) build_impl<double>(c.get(), s);
@@ -2161,12 +2184,29 @@ tddft_status tddft_response_density_noalloc(tddft_ctx *c, int32_t k, const float
                              std::to_string(noalloc_max_states())};
         if (!P || !rho || !is_device_ptr(P) || !is_device_ptr(rho))
             throw InvalidArg{"tddft_response_density_noalloc: P and rho must be device pointers"};
+        // the scratch array's address and the kernel are those of the current device: it must be
+        // the context's, and so must the buffers
+        int cur = -1;
+        check(cudaGetDevice(&cur), "cudaGetDevice");
+        if (cur != c->device || device_of(P) != c->device || device_of(rho) != c->device)
+            throw InvalidArg{"tddft_response_density_noalloc: the current device and the devices of P and rho must "
+                             "be the context's device"};
         Impl<float> &I = *c->d32;
         response_density_tc_noalloc(c->st, c->grid(), I.chi, I.phi, I.chi_pm, I.CK, I.NPmax, c->nv, P, c->len(), k,
                                     rho, I.phi_pm);
         if (response_density_tc_noalloc_error(c->st))
             throw TimeoutErr{"a bounded wait in the density kernel expired"};
         return TDDFT_OK;
+    });
+}
+
+tddft_status tddft_wait_check(tddft_ctx *c) {
+    if (!c) return TDDFT_E_INVALID;
+    return guarded(c, [&]() -> tddft_status {
+        tc_wait_probe(c->st);
+        check_tc_error(c);   // throws TimeoutErr when the probe's wait expired, as it must
+        c->err = "the bounded wait of the probe did not expire";
+        return TDDFT_E_CUDA;
     });
 }
 

@@ -32,6 +32,7 @@ struct __align__(8) DensShared {
     unsigned long long acc_full[2];
     unsigned long long acc_empty[2];
     unsigned long long b_ready[16];   // per 64-wide K block of the gathered P block
+    unsigned long long drain;         // MMA completion after an abort (teardown only)
     unsigned int tmem_base;
     int abort;
 };
@@ -48,7 +49,7 @@ __global__ void __launch_bounds__(DENS_THREADS, 1) density_tc_kernel(
     int n, int nt, int KBmax, int NP, int G, int k, const int *__restrict__ coff, const int *__restrict__ cids,
     const int *__restrict__ poff, const int *__restrict__ pids, const float *__restrict__ pval, int nphi,
     const float *__restrict__ P, long long sP, const float *__restrict__ pscale, float *__restrict__ rho,
-    int *err, int quad, const unsigned short *__restrict__ phi_pm) {
+    int *err, int quad, const unsigned short *__restrict__ phi_pm, long long wlim) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<unsigned long long>(smem_raw) + 1023ull) & ~1023ull);
@@ -85,6 +86,7 @@ __global__ void __launch_bounds__(DENS_THREADS, 1) density_tc_kernel(
             mbar_init(&ctl->acc_empty[i], 256);
         }
         for (int i = 0; i < DENS_KBMAX; ++i) mbar_init(&ctl->b_ready[i], DENS_GATHER);
+        mbar_init(&ctl->drain, 1);
         ctl->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -105,10 +107,14 @@ __global__ void __launch_bounds__(DENS_THREADS, 1) density_tc_kernel(
             for (int pb = 0; pb < TILE_PTS / 128 && !*abort; ++pb)
                 for (int kb = 0; kb < KB; ++kb, ++i) {
                     const int st = i % DENS_STAGES, use = i / DENS_STAGES;
-                    if (use > 0 && !mbar_wait(&ctl->a_empty[st], (use - 1) & 1, abort)) break;
+                    if (use > 0 && !mbar_wait(&ctl->a_empty[st], (use - 1) & 1, abort, wlim)) break;
                     mbar_expect_tx(&ctl->a_full[st], 16384);
                     tma_load_2d(A + st * 16384, &mX, &ctl->a_full[st], kb * 64, t * TILE_PTS + pb * 128);
                 }
+            // after an abort, the loads already issued land before the block exits
+            if (*abort)
+                for (int j = i > DENS_STAGES ? i - DENS_STAGES : 0; j < i; ++j)
+                    mbar_drain(&ctl->a_full[j % DENS_STAGES], (unsigned)((j / DENS_STAGES) & 1), wlim);
         }
     } else if (warp == 5) {
         // MMA issuer: accumulator pb % 2, one commit per chi block (frees the ring slot)
@@ -118,12 +124,12 @@ __global__ void __launch_bounds__(DENS_THREADS, 1) density_tc_kernel(
             int i = 0;
             for (int pb = 0; pb < TILE_PTS / 128 && ok; ++pb) {
                 const int acc = pb & 1, use = pb >> 1;
-                if (use > 0 && !mbar_wait(&ctl->acc_empty[acc], (use - 1) & 1, abort)) break;
+                if (use > 0 && !mbar_wait(&ctl->acc_empty[acc], (use - 1) & 1, abort, wlim)) break;
                 tc_fence_after();
                 for (int kb = 0; kb < KB; ++kb, ++i) {
                     const int st = i % DENS_STAGES, u = i / DENS_STAGES;
                     // the P block's K block kb is gathered (the first M block waits, the rest pass)
-                    if (!mbar_wait(&ctl->b_ready[kb], 0, abort) || !mbar_wait(&ctl->a_full[st], u & 1, abort)) {
+                    if (!mbar_wait(&ctl->b_ready[kb], 0, abort, wlim) || !mbar_wait(&ctl->a_full[st], u & 1, abort, wlim)) {
                         ok = false;
                         break;
                     }
@@ -136,6 +142,11 @@ __global__ void __launch_bounds__(DENS_THREADS, 1) density_tc_kernel(
                     mma_commit(&ctl->a_empty[st]);
                 }
                 mma_commit(&ctl->acc_full[acc]);
+            }
+            // after an abort, the MMAs already issued finish before TMEM is freed
+            if (*abort) {
+                mma_commit(&ctl->drain);
+                mbar_drain(&ctl->drain, 0, wlim);
             }
         }
     }
@@ -257,7 +268,7 @@ __global__ void __launch_bounds__(DENS_THREADS, 1) density_tc_kernel(
         const int send = aligned ? (eg ? gs : gsplit) : (eg ? 0 : gs);
         for (int pb = 0; pb < TILE_PTS / 128; ++pb) {
             const int acc = pb & 1;
-            const bool ok = mbar_wait(&ctl->acc_full[acc], (pb >> 1) & 1, abort) && !*abort;
+            const bool ok = mbar_wait(&ctl->acc_full[acc], (pb >> 1) & 1, abort, wlim) && !*abort;
             tc_fence_after();
             const int lp = pb * 128 + quarter * 32 + lane;
             float r[16];
@@ -370,6 +381,7 @@ struct __align__(8) PDensShared {
     unsigned long long acc_empty[2];
     unsigned long long b_full[2];
     unsigned long long b_free[2];
+    unsigned long long drain;
     unsigned int tmem_base;
     int abort;
 };
@@ -384,7 +396,7 @@ __global__ void __launch_bounds__(PDENS_THREADS, 1) density_tc_persistent_kernel
     const int *__restrict__ coff, const int *__restrict__ cids, const int *__restrict__ poff,
     const int *__restrict__ pids, int nphi, const unsigned short *__restrict__ phi_pm,
     const float *__restrict__ P, long long sP, const float *__restrict__ pscale, float *__restrict__ rho,
-    int *err) {
+    int *err, long long wlim) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<unsigned long long>(smem_raw) + 1023ull) & ~1023ull);
@@ -407,6 +419,7 @@ __global__ void __launch_bounds__(PDENS_THREADS, 1) density_tc_persistent_kernel
             mbar_init(&ctl->b_full[i], PDENS_GATHER);
             mbar_init(&ctl->b_free[i], 1);
         }
+        mbar_init(&ctl->drain, 1);
         ctl->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -432,11 +445,15 @@ __global__ void __launch_bounds__(PDENS_THREADS, 1) density_tc_persistent_kernel
                     for (int kb = 0; kb < KB; ++kb, ++q) {
                         const int st = (int)(q % PDENS_STAGES);
                         const long long use = q / PDENS_STAGES;
-                        if (use > 0 && !mbar_wait(&ctl->a_empty[st], (unsigned)((use - 1) & 1), abort)) break;
+                        if (use > 0 && !mbar_wait(&ctl->a_empty[st], (unsigned)((use - 1) & 1), abort, wlim)) break;
                         mbar_expect_tx(&ctl->a_full[st], 16384);
                         tma_load_2d(A + st * 16384, &mX, &ctl->a_full[st], kb * 64, t * TILE_PTS + pb * 128);
                     }
             }
+            // after an abort, the loads already issued land before the block exits
+            if (*abort)
+                for (long long j = q > PDENS_STAGES ? q - PDENS_STAGES : 0; j < q; ++j)
+                    mbar_drain(&ctl->a_full[j % PDENS_STAGES], (unsigned)((j / PDENS_STAGES) & 1), wlim);
         }
     } else if (warp == 5) {
         // MMA issuer
@@ -449,20 +466,20 @@ __global__ void __launch_bounds__(PDENS_THREADS, 1) density_tc_persistent_kernel
                 const int t = items_tiles[it / k];
                 const int KB = (coff[t + 1] - coff[t] + 63) / 64;
                 const int buf = j & 1;
-                if (!mbar_wait(&ctl->b_full[buf], (unsigned)((j >> 1) & 1), abort)) break;
+                if (!mbar_wait(&ctl->b_full[buf], (unsigned)((j >> 1) & 1), abort, wlim)) break;
                 tc_fence_after();
                 const unsigned char *B = Bb + buf * bsize;
                 for (int pb = 0; pb < TILE_PTS / 128 && ok; ++pb, ++pbg) {
                     const int acc = (int)(pbg & 1);
                     const long long ause = pbg >> 1;
-                    if (ause > 0 && !mbar_wait(&ctl->acc_empty[acc], (unsigned)((ause - 1) & 1), abort)) {
+                    if (ause > 0 && !mbar_wait(&ctl->acc_empty[acc], (unsigned)((ause - 1) & 1), abort, wlim)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
                     for (int kb = 0; kb < KB; ++kb, ++q) {
                         const int st = (int)(q % PDENS_STAGES);
-                        if (!mbar_wait(&ctl->a_full[st], (unsigned)((q / PDENS_STAGES) & 1), abort)) {
+                        if (!mbar_wait(&ctl->a_full[st], (unsigned)((q / PDENS_STAGES) & 1), abort, wlim)) {
                             ok = false;
                             break;
                         }
@@ -480,6 +497,10 @@ __global__ void __launch_bounds__(PDENS_THREADS, 1) density_tc_persistent_kernel
                 if (!ok) break;
                 mma_commit(&ctl->b_free[buf]);   // this item's B buffer is free once its MMAs finish
             }
+            if (*abort) {
+                mma_commit(&ctl->drain);
+                mbar_drain(&ctl->drain, 0, wlim);
+            }
         }
     } else if ((warp >= 6 && warp < 8) || warp >= 12) {
         // gather the P block of each item into B[j % 2] by phi quads (aligned groups of four)
@@ -491,7 +512,7 @@ __global__ void __launch_bounds__(PDENS_THREADS, 1) density_tc_persistent_kernel
             const int p0 = poff[t], np = poff[t + 1] - p0;
             const int KB = (nc + 63) / 64;
             const int buf = j & 1;
-            if (j >= 2 && !mbar_wait(&ctl->b_free[buf], (unsigned)(((j >> 1) - 1) & 1), abort)) break;
+            if (j >= 2 && !mbar_wait(&ctl->b_free[buf], (unsigned)(((j >> 1) - 1) & 1), abort, wlim)) break;
             unsigned char *B = Bb + buf * bsize;
             const float sc = pscale[s];
             const float *Ps = P + (long long)s * sP;
@@ -547,7 +568,7 @@ __global__ void __launch_bounds__(PDENS_THREADS, 1) density_tc_persistent_kernel
             const float inv = 1.0f / pscale[s];
             bool stop = false;
             for (int pb = eg; pb < TILE_PTS / 128; pb += 2, ++ause) {
-                const bool ok = mbar_wait(&ctl->acc_full[eg], (unsigned)(ause & 1), abort) && !*abort;
+                const bool ok = mbar_wait(&ctl->acc_full[eg], (unsigned)(ause & 1), abort, wlim) && !*abort;
                 tc_fence_after();
                 const int lp = pb * 128 + quarter * 32 + lane;
                 float r = 0.0f;
@@ -683,7 +704,8 @@ void response_density_tc(cudaStream_t st, const GridShape &g, const TileSet<floa
             const int grid = std::min(sms, nitems);
             density_tc_persistent_kernel<<<grid, PDENS_THREADS, psm, st>>>(mx, g.n, g.nt, NP, k, live_tiles, nitems,
                                                                            chi.off, chi.ids, phi.off, phi.ids, nphi,
-                                                                           phi_pm, P, sP, scale, rho, err);
+                                                                           phi_pm, P, sP, scale, rho, err,
+                                                                           active_wait_limit());
             check_launch("density_tc_persistent_kernel");
         }
         return;
@@ -701,7 +723,8 @@ void response_density_tc(cudaStream_t st, const GridShape &g, const TileSet<floa
     dim3 grid(ngroups, chi.ntiles);
     density_tc_kernel<<<grid, DENS_THREADS, sm, st>>>(mx, g.n, g.nt, KBmax, NP, G, k, chi.off, chi.ids, phi.off,
                                                       phi.ids, phi.val, nphi, P, sP, scale, rho, err,
-                                                      phi_quads ? 1 : 0, NP % 32 == 0 ? phi_pm : nullptr);
+                                                      phi_quads ? 1 : 0, NP % 32 == 0 ? phi_pm : nullptr,
+                                                      active_wait_limit());
     check_launch("density_tc_kernel");
 }
 
@@ -729,6 +752,7 @@ struct __align__(8) IntShared {
     unsigned long long w_ready[2];
     unsigned long long mma_done[2];
     unsigned long long acc_done;
+    unsigned long long drain;
     unsigned int tmem_base;
     int abort;
     int pid[256];      // the tile's phi indices (np <= NP <= 128)
@@ -751,7 +775,8 @@ __global__ void __launch_bounds__(192, 3) integrals_tc_kernel(
     const __grid_constant__ CUtensorMap mP,   // function-major phi: [slot][512] f16, box NP rows
     int n, int nt, int NP, int k, const int *__restrict__ cids, const int *__restrict__ pids, int nchi,
     int nphi, const float *__restrict__ V, const float *__restrict__ vscale, float dV, float *__restrict__ out,
-    bool vec_ok, int acc_stride, const VTile *__restrict__ units, int mbmax, int tmem_cols, int *err) {
+    bool vec_ok, int acc_stride, const VTile *__restrict__ units, int mbmax, int tmem_cols, int *err,
+    long long wlim) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<unsigned long long>(smem_raw) + 1023ull) & ~1023ull);
@@ -780,6 +805,7 @@ __global__ void __launch_bounds__(192, 3) integrals_tc_kernel(
             mbar_init(&ctl->mma_done[i], 1);
         }
         mbar_init(&ctl->acc_done, 1);
+        mbar_init(&ctl->drain, 1);
         ctl->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -806,21 +832,25 @@ __global__ void __launch_bounds__(192, 3) integrals_tc_kernel(
 
     if (warp == 4) {
         if (lane == 0) {
-            for (int kb = 0; kb < KS; ++kb) {
+            int kb = 0;
+            for (; kb < KS; ++kb) {
                 const int st = kb & 1, use = kb >> 1;
-                if (use > 0 && !mbar_wait(&ctl->mma_done[st], (use - 1) & 1, abort)) break;
+                if (use > 0 && !mbar_wait(&ctl->mma_done[st], (use - 1) & 1, abort, wlim)) break;
                 mbar_expect_tx(&ctl->x_full[st], MB * 16384 + NB * 128);
                 for (int mb = 0; mb < MB; ++mb)
                     tma_load_2d(Xs + st * xstage + mb * 16384, &mX, &ctl->x_full[st], kb * 64, c0 + mb * 128);
                 tma_load_2d(Ws + (size_t)st * NB * 128, &mP, &ctl->x_full[st], kb * 64, p0);
             }
+            // after an abort, the loads already issued land before the block exits
+            if (*abort)
+                for (int j = kb > 2 ? kb - 2 : 0; j < kb; ++j) mbar_drain(&ctl->x_full[j & 1], (unsigned)((j >> 1) & 1), wlim);
         }
     } else if (warp == 5) {
         if (lane == 0) {
             for (int kb = 0; kb < KS; ++kb) {
                 const int st = kb & 1, use = kb >> 1;
-                if (!mbar_wait(&ctl->x_full[st], use & 1, abort)) break;
-                if (!mbar_wait(&ctl->w_ready[st], use & 1, abort)) break;
+                if (!mbar_wait(&ctl->x_full[st], use & 1, abort, wlim)) break;
+                if (!mbar_wait(&ctl->w_ready[st], use & 1, abort, wlim)) break;
                 tc_fence_after();
                 const unsigned wb = smem_u32(Ws + (size_t)st * NB * 128);
                 for (int mb = 0; mb < MB; ++mb) {
@@ -833,13 +863,17 @@ __global__ void __launch_bounds__(192, 3) integrals_tc_kernel(
                 mma_commit(&ctl->mma_done[st]);
             }
             mma_commit(&ctl->acc_done);
+            if (*abort) {
+                mma_commit(&ctl->drain);
+                mbar_drain(&ctl->drain, 0, wlim);
+            }
         }
     } else {
         // workers: scale the phi rows of each landed stage by V (8 points per 16-byte chunk),
         // then the epilogue
         for (int kb = 0; kb < KS; ++kb) {
             const int st = kb & 1, use = kb >> 1;
-            if (!mbar_wait(&ctl->x_full[st], use & 1, abort)) break;
+            if (!mbar_wait(&ctl->x_full[st], use & 1, abort, wlim)) break;
             unsigned char *W = Ws + (size_t)st * NB * 128;
             for (int idx = threadIdx.x; idx < np * 8; idx += 128) {
                 const int row = idx >> 3, c8 = idx & 7;
@@ -858,7 +892,7 @@ __global__ void __launch_bounds__(192, 3) integrals_tc_kernel(
             fence_async_smem();
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ctl->w_ready[st])) : "memory");
         }
-        const bool ok = mbar_wait(&ctl->acc_done, 0, abort) && !*abort;
+        const bool ok = mbar_wait(&ctl->acc_done, 0, abort, wlim) && !*abort;
         tc_fence_after();
         const float f = dV / vs;
         for (int mb = 0; mb < MB; ++mb) {
@@ -964,7 +998,7 @@ void potential_integrals_tc(cudaStream_t st, const GridShape &g, const TileSet<f
         dim3 grid(k, cnt);
         integrals_tc_kernel<<<grid, 192, sm, st>>>(mx, mp, g.n, g.nt, NPmax, k, chi.ids, phi.ids, nchi, nphi, V,
                                                    scale, (float)g.dV, out, vec_ok, stride, lst, mbmax, tmem_cols,
-                                                   err);
+                                                   err, active_wait_limit());
         check_launch("integrals_tc_kernel");
     }
 }
@@ -1041,7 +1075,7 @@ void response_density_tc_noalloc(cudaStream_t st, const GridShape &g, const Tile
     dim3 grid((k + G - 1) / G, chi.ntiles);
     density_tc_kernel<<<grid, DENS_THREADS, sm, st>>>(mx, g.n, g.nt, KBmax, NP, G, k, chi.off, chi.ids, phi.off,
                                                       phi.ids, phi.val, nphi, P, sP, s->scale, rho, &s->err, 0,
-                                                      NP % 32 == 0 ? phi_pm : nullptr);
+                                                      NP % 32 == 0 ? phi_pm : nullptr, active_wait_limit());
     check_launch("density_tc_kernel (allocation-free)");
 }
 

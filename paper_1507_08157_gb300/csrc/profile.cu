@@ -59,6 +59,11 @@ Profiler *&active_profiler() {
     return p;
 }
 
+long long &active_wait_limit() {
+    static thread_local long long w = DEFAULT_WAIT_LIMIT;
+    return w;
+}
+
 const char *stage_name(int s) {
     static const char *names[ST_COUNT] = {"gemm", "response_density", "potential_integrals",
                                           "fft_poisson_fxc", "trace", "vector", "small_fp64"};

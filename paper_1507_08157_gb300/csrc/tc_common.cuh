@@ -6,7 +6,9 @@
 namespace tddft {
 namespace tc {
 
-constexpr long long TC_WAIT_LIMIT = 4000000000LL;   // clock64 ticks (~2 s) for any bounded wait
+// default limit of every bounded wait, in clock64 ticks (about 2 s at 2 GHz); a context may set
+// its own (tddft_options.spin_limit_cycles), which the launchers pass to the kernels
+constexpr long long TC_WAIT_LIMIT = 4000000000LL;
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) {
     return static_cast<unsigned>(__cvta_generic_to_shared(p));
@@ -31,17 +33,27 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *b, unsigned pa
     return ok != 0;
 }
 
-// bounded wait; returns false on expiry or when another role already gave up
-__device__ __forceinline__ bool mbar_wait(unsigned long long *b, unsigned parity, volatile int *abort) {
+// bounded wait; returns false on expiry (and raises the block's abort flag) or when another role
+// already gave up
+__device__ __forceinline__ bool mbar_wait(unsigned long long *b, unsigned parity, volatile int *abort,
+                                          long long limit) {
     const long long t0 = clock64();
     while (!mbar_try_wait(b, parity)) {
         if (*abort) return false;
-        if (clock64() - t0 > TC_WAIT_LIMIT) {
+        if (clock64() - t0 > limit) {
             *abort = 1;
             return false;
         }
     }
     return true;
+}
+
+// teardown after an abort: wait, again bounded, for the phase `parity` of b to complete whatever
+// the abort flag says, so that a copy or an MMA this thread started lands before the block exits
+__device__ __forceinline__ void mbar_drain(unsigned long long *b, unsigned parity, long long limit) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(b, parity))
+        if (clock64() - t0 > limit) return;
 }
 
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, unsigned long long *bar,

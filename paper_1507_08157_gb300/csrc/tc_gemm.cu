@@ -45,6 +45,7 @@ struct __align__(8) TcShared {
     unsigned long long empty[TSTAGES];
     unsigned long long acc_full[2];
     unsigned long long acc_empty[2];
+    unsigned long long drain;      // MMA completion after an abort (teardown only)
     unsigned int tmem_base;
     int abort;
 };
@@ -69,7 +70,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(
     const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
     const __grid_constant__ CUtensorMap mAlo, const __grid_constant__ CUtensorMap mBlo, int a_split, int b_split,
     int M, int N, int K, int batchA, int batchB, int batch, float alpha, float beta, float *__restrict__ C, int ldc,
-    long long sC, int *err) {
+    long long sC, int *err, long long wlim) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<unsigned long long>(smem_raw) + 1023ull) & ~1023ull);
@@ -94,6 +95,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(
             mbar_init(&ctl->acc_full[i], 1);
             mbar_init(&ctl->acc_empty[i], 128);
         }
+        mbar_init(&ctl->drain, 1);
         ctl->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -118,7 +120,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(
                 for (int kb = 0; kb < nk; ++kb, ++it) {
                     const int s = (int)(it % S);
                     const unsigned par = (unsigned)(((it / S) & 1) ^ 1);
-                    if (!mbar_wait(&ctl->empty[s], par, abort)) {
+                    if (!mbar_wait(&ctl->empty[s], par, abort, wlim)) {
                         go = false;
                         break;
                     }
@@ -132,6 +134,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(
                     if (NSPLIT == 3 && b_split) tma_load_3d(st + 3 * TILE_BYTES, &mBlo, &ctl->full[s], kb * TBK, n0, bb);
                 }
             }
+            // after an abort, the loads already issued land before the block exits
+            if (*abort)
+                for (long long j = it > S ? it - S : 0; j < it; ++j)
+                    mbar_drain(&ctl->full[j % S], (unsigned)((j / S) & 1), wlim);
         }
     } else if (warp == 9) {
         if (lane == 0) {
@@ -142,13 +148,13 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(
             bool ok = true;
             for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tcount) {
                 const int buf = tcount & 1, use = tcount >> 1;
-                if (!mbar_wait(&ctl->acc_empty[buf], (unsigned)((use & 1) ^ 1), abort)) break;
+                if (!mbar_wait(&ctl->acc_empty[buf], (unsigned)((use & 1) ^ 1), abort, wlim)) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const unsigned acc_t = tmem + (unsigned)(buf * TBN);
                 for (int kb = 0; kb < nk; ++kb, ++it) {
                     const int s = (int)(it % S);
                     const unsigned par = (unsigned)((it / S) & 1);
-                    if (!mbar_wait(NSPLIT == 3 ? &ctl->split[s] : &ctl->full[s], par, abort)) {
+                    if (!mbar_wait(NSPLIT == 3 ? &ctl->split[s] : &ctl->full[s], par, abort, wlim)) {
                         ok = false;
                         break;
                     }
@@ -171,6 +177,11 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(
                 if (!ok) break;
                 mma_commit(&ctl->acc_full[buf]);
             }
+            // after an abort, the MMAs already issued finish before TMEM is freed
+            if (*abort) {
+                mma_commit(&ctl->drain);
+                mbar_drain(&ctl->drain, 0, wlim);
+            }
         }
     } else if (warp >= 4) {
         if (NSPLIT == 3) {
@@ -183,7 +194,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(
                 for (int kb = 0; kb < nk; ++kb, ++it) {
                     const int s = (int)(it % S);
                     const unsigned par = (unsigned)((it / S) & 1);
-                    if (!mbar_wait(&ctl->full[s], par, abort)) {
+                    if (!mbar_wait(&ctl->full[s], par, abort, wlim)) {
                         go = false;
                         break;
                     }
@@ -221,7 +232,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(
         int tcount = 0;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tcount) {
             const int buf = tcount & 1, use = tcount >> 1;
-            if (!mbar_wait(&ctl->acc_full[buf], (unsigned)(use & 1), abort)) break;
+            if (!mbar_wait(&ctl->acc_full[buf], (unsigned)(use & 1), abort, wlim)) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int n0 = (t % tn) * TN, m0 = ((t / tn) % tm) * TBM, b = t / (tn * tm);
             float *Cb = C + (long long)b * sC;
@@ -377,19 +388,20 @@ void tc_gemm_nt(cudaStream_t st, int M, int N, int K, float alpha, const float *
     const long long ntiles = (long long)((N + TN - 1) / TN) * ((M + TBM - 1) / TBM) * batch;
     const int grid = (int)std::min<long long>(ntiles, sm_count());
     int *err = error_word();
+    const long long wlim = active_wait_limit();
     const int as = asp ? 1 : 0, bs = bsp ? 1 : 0;
     if (nsplit == 3 && TN == 112)
         tc_gemm_kernel<3, 112><<<grid, GEMM_THREADS, sm, st>>>(ma, mb, malo, mblo, as, bs, M, N, K, bA, bB, batch,
-                                                               alpha, beta, C, ldc, sC, err);
+                                                               alpha, beta, C, ldc, sC, err, wlim);
     else if (nsplit == 3)
         tc_gemm_kernel<3, 128><<<grid, GEMM_THREADS, sm, st>>>(ma, mb, malo, mblo, as, bs, M, N, K, bA, bB, batch,
-                                                               alpha, beta, C, ldc, sC, err);
+                                                               alpha, beta, C, ldc, sC, err, wlim);
     else if (TN == 112)
         tc_gemm_kernel<1, 112><<<grid, GEMM_THREADS, sm, st>>>(ma, mb, malo, mblo, 0, 0, M, N, K, bA, bB, batch, alpha,
-                                                               beta, C, ldc, sC, err);
+                                                               beta, C, ldc, sC, err, wlim);
     else
         tc_gemm_kernel<1, 128><<<grid, GEMM_THREADS, sm, st>>>(ma, mb, malo, mblo, 0, 0, M, N, K, bA, bB, batch, alpha,
-                                                               beta, C, ldc, sC, err);
+                                                               beta, C, ldc, sC, err, wlim);
     check_launch("tc_gemm_kernel");
 }
 
@@ -617,6 +629,30 @@ void tc_gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, float alpha
 }
 
 int *tc_error_word() { return error_word(); }
+
+namespace {
+// waits, with the caller's limit, on a barrier that nothing completes: the wait must expire and
+// set the error word (a check of the bounded-wait path that faults nothing)
+__global__ void wait_probe_kernel(int *err, long long wlim) {
+    __shared__ unsigned long long bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile int *ab = &abort_flag;
+        if (!mbar_wait(&bar, 0, ab, wlim)) atomicExch(err, 1);
+    }
+}
+}  // namespace
+
+void tc_wait_probe(cudaStream_t st) {
+    wait_probe_kernel<<<1, 32, 0, st>>>(error_word(), active_wait_limit());
+    check_launch("wait_probe_kernel");
+}
 
 void tc_error_fetch(cudaStream_t st, int *host) {
     check(cudaMemcpyAsync(host, error_word(), sizeof(int), cudaMemcpyDeviceToHost, st), "D2H tc error");

@@ -52,6 +52,12 @@ const char *stage_name(int s);
 struct Profiler;                        // defined in profile.cu
 Profiler *&active_profiler();           // thread-local; null when profiling is off
 
+// Limit of every bounded wait inside the tensor-core kernels, in clock64 ticks: thread-local, set
+// for the duration of a call from the context's options (tddft_options.spin_limit_cycles) and read
+// by the launchers, which pass it to the kernels.
+constexpr long long DEFAULT_WAIT_LIMIT = 4000000000LL;   // about 2 s at 2 GHz
+long long &active_wait_limit();
+
 // Records an event pair around one launch when a profiler is active; `flops` and `bytes` are the
 // algorithmic counts of the launch.
 struct ProfScope {

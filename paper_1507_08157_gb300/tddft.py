@@ -49,7 +49,8 @@ class _Options(ctypes.Structure):
                 ("precond", ctypes.c_int32), ("precond_maxit", ctypes.c_int32),
                 ("precond_tol", ctypes.c_double), ("tol", ctypes.c_double),
                 ("max_iter", ctypes.c_int32), ("reapply_every", ctypes.c_int32),
-                ("restart_every", ctypes.c_int32), ("precond_adaptive", ctypes.c_int32)]
+                ("restart_every", ctypes.c_int32), ("precond_adaptive", ctypes.c_int32),
+                ("spin_limit_cycles", ctypes.c_int64)]
 
 
 class StageStats(ctypes.Structure):
@@ -68,7 +69,8 @@ SYMBOLS = sorted(["tddft_default_options", "tddft_create", "tddft_destroy", "tdd
                   "tddft_mlp_loss_grad", "tddft_mlp_train", "tddft_learned_dims", "tddft_set_mlp",
                   "tddft_samples", "tddft_state_stats", "tddft_state_export",
                   "tddft_state_import", "tddft_create_batch", "tddft_solve_batch",
-                  "tddft_oscillator_strengths", "tddft_spectrum", "tddft_joint_projector"])
+                  "tddft_oscillator_strengths", "tddft_spectrum", "tddft_joint_projector",
+                  "tddft_wait_check"])
 
 _lib = None
 _live = weakref.WeakSet()      # open contexts and states, closed before interpreter shutdown
@@ -106,6 +108,8 @@ def load(path: str = LIB_PATH):
     for name in ("tddft_response_density", "tddft_response_potential", "tddft_potential_integrals"):
         getattr(lib, name).argtypes = [vp, ctypes.c_int32, vp, vp]
     lib.tddft_fxc.argtypes = [vp, vp]
+    lib.tddft_wait_check.argtypes = [vp]
+    lib.tddft_wait_check.restype = ctypes.c_int
     lib.tddft_response_density_noalloc.argtypes = [vp, ctypes.c_int32, vp, vp]
     lib.tddft_response_density_noalloc.restype = ctypes.c_int
     lib.tddft_state_create.argtypes = [vp, ctypes.c_int32, vp, ctypes.POINTER(vp)]
@@ -183,7 +187,8 @@ def _ptr(a):
 
 
 def _options(precision="fp64", mode="full", precond="iter", precond_tol=1e-4, precond_maxit=50,
-             tol=1e-6, max_iter=500, reapply_every=10, restart_every=10, precond_adaptive=False):
+             tol=1e-6, max_iter=500, reapply_every=10, restart_every=10, precond_adaptive=False,
+             spin_limit_cycles=0):
     o = _Options()
     load().tddft_default_options(ctypes.byref(o))
     o.precision = FP64 if precision == "fp64" else MIXED
@@ -196,6 +201,7 @@ def _options(precision="fp64", mode="full", precond="iter", precond_tol=1e-4, pr
     o.reapply_every = reapply_every
     o.restart_every = restart_every
     o.precond_adaptive = 1 if precond_adaptive else 0
+    o.spin_limit_cycles = int(spin_limit_cycles)
     return o
 
 
@@ -367,6 +373,10 @@ class Context:
         out = self._out(V, (V.shape[0], self.nc, self.nv))
         self._check(self._lib.tddft_potential_integrals(self._ctx, V.shape[0], _ptr(V), _ptr(out)))
         return out
+
+    def wait_check(self):
+        """Status of tddft_wait_check: a kernel whose bounded wait must expire (E_TIMEOUT expected)."""
+        return int(self._lib.tddft_wait_check(self._ctx))
 
     def fxc(self):
         out = np.empty((self.n, self.n, self.n))

@@ -49,6 +49,23 @@ def test_default_options_without_gpu(lib_path):
     o = tddft._options()
     assert o.precision == tddft.FP64 and o.precond_maxit == 50 and abs(o.precond_tol - 1e-4) < 1e-18
     assert o.reapply_every == 10 and o.restart_every == 10
+    assert o.spin_limit_cycles == 0
+
+
+def test_options_struct_layout_matches_the_header(lib_path, tmp_path):
+    # the binding's mirror of tddft_options must have the layout the C compiler gives the header
+    import ctypes
+    from paper_1507_08157_gb300 import tddft
+    src = tmp_path / "layout.c"
+    fields = [f for f, _ in tddft._Options._fields_]
+    body = "".join(f'printf("%zu ", offsetof(tddft_options, {f}));' for f in fields)
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "tddft.h"\n'
+                   'int main(void) { ' + body + 'printf("%zu", sizeof(tddft_options)); return 0; }\n')
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert got[:-1] == [getattr(tddft._Options, f).offset for f in fields]
+    assert got[-1] == ctypes.sizeof(tddft._Options)
 
 
 def test_product_code_does_not_import_the_oracle():

@@ -1,11 +1,19 @@
 """The allocation-free response density (tddft_response_density_noalloc) against the regular
 entry point, through the C ABI.
 
-The two calls run the same tensor-core kernel on the same float32 values of P (the regular entry
-rounds the float64 input to float32 on the device, torch rounds it the same way here), so their
-densities agree to float32 roundoff of the epilogue; the bound is 1e-6 of max|rho|. Two calls in
-a row on different inputs check that the call clears its fixed scratch (the per-state maxima)
-before use. This file is collected last so that it also runs after the other GPU tests.
+Some callers cannot allocate device memory when they need a density (a pool allocator that
+already holds the device memory, or a loop where cudaMalloc / cudaFree would synchronise the
+device); the allocation-free entry serves them from a fixed static scratch array.
+
+The two entries run two different tensor-core kernels on the same float32 values of P (the
+regular entry rounds the float64 input to float32 on the device, torch rounds it the same way
+here): on this workload the regular entry takes the persistent kernel over (tile, state) items
+with the vector P gather (density_tc_persistent_kernel), the allocation-free entry the per-tile
+kernel with the element-wise gather (density_tc_kernel). Both round the scaled P block to float16
+the same way and accumulate in float32 on the tensor cores; they differ only in the order of the
+float32 epilogue sums, so the densities agree to 1e-6 of max|rho|. Two calls in a row on
+different inputs check that the call clears its fixed scratch (the per-state maxima) before use.
+This file is collected last so that it also runs after the other GPU tests.
 """
 import numpy as np
 import pytest
