@@ -33,6 +33,8 @@ class Operator:
         self.Hc, self.Hv = sys.H_chi, sys.H_phi
         self.Pc, self.Pv = sys.P_c, sys.P_v
         self.mask = kernel_mask(sys)
+        self.Mc = self.Pc @ self.Hc
+        self.Mv = self.Hv @ self.Pv
 
     # -- V_SCF (Secs. II A, II C) --------------------------------------------------------------
     def response_density(self, P):
@@ -74,6 +76,14 @@ class Operator:
     def project(self, L):
         """Eq. auxiliary: P = P^c S^chi L S^phi P^v (L masked to the kernel pattern)."""
         return self.Pc @ self.Sc @ (self.mask * L) @ self.Sv @ self.Pv
+
+    def ks_difference(self, X):
+        """The left-hand side of Eq. precond for one matrix: P^c H^chi X - X H^phi P^v."""
+        return self.Mc @ X - X @ self.Mv
+
+    def pc_x_pv(self, G):
+        """P^c G P^v (the projection of an L-space gradient back to a response kernel)."""
+        return self.Pc @ G @ self.Pv
 
     def l_gradient(self, g):
         """Gradient with respect to L of a functional whose contravariant P-gradient is g:

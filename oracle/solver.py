@@ -172,8 +172,6 @@ class PCG:
         self.reapply_every = reapply_every
         self.restart_every = restart_every
         self.trunc = op.sys.kernel_cutoff > 0.0
-        self.Mc = op.Pc @ op.Hc
-        self.Mv = op.Hv @ op.Pv
         m = op.mask
         self.Yp = np.array([m * Y for Y in Y0])
         self.Yq = self.Yp.copy()
@@ -263,7 +261,7 @@ class PCG:
         for _ in range(self.precond_maxit):
             if r0 == 0.0 or np.sqrt(max(rr, 0.0)) <= self.step_tol * r0:
                 break
-            Lp = self.Mc @ p - p @ self.Mv
+            Lp = self.op.ks_difference(p)
             pLp = self.inner(p, Lp)
             if pLp <= 0.0:
                 break
@@ -290,8 +288,8 @@ class PCG:
         op = self.op
         if self.trunc:
             # precondition the L-gradient: z = mask * Pinv(P^c G_L P^v), positive in Frobenius
-            return (np.array([op.Pc @ G @ op.Pv for G in self.GLp]),
-                    np.array([op.Pc @ G @ op.Pv for G in self.GLq]))
+            return (np.array([op.pc_x_pv(G) for G in self.GLp]),
+                    np.array([op.pc_x_pv(G) for G in self.GLq]))
         return gp, gq
 
     def iterative_z(self, hp, hq):
@@ -311,6 +309,11 @@ class PCG:
         X, s = feat.rows(hp, hq)
         return X, feat.targets(zp, zq, s, hp, hq), feat.weights(s, self.k)
 
+    def gdot(self, gp, gq, zp, zq, Zp, Zq):
+        """sum_i <g_i, Z_i>: the slope of the sum functional along Z (z its L-space preimage, not
+        needed here)."""
+        return sum(self.inner(gp[i], Zp[i]) + self.inner(gq[i], Zq[i]) for i in range(self.k))
+
     def update(self, Q, omega, gp, gq):
         k = self.k
         op = self.op
@@ -322,19 +325,19 @@ class PCG:
             zp, zq = self.learned.apply(hp, hq)
             Zp = np.array([op.project(X) for X in zp])
             Zq = np.array([op.project(X) for X in zq])
-            gz = sum(self.inner(gp[i], Zp[i]) + self.inner(gq[i], Zq[i]) for i in range(k))
+            gz = self.gdot(gp, gq, zp, zq, Zp, Zq)
             if not gz > 0.0:
                 self.fallbacks += 1
         if self.learned is None or not gz > 0.0:
             zp, zq = self.iterative_z(hp, hq)
             Zp = np.array([op.project(X) for X in zp])
             Zq = np.array([op.project(X) for X in zq])
-            gz = sum(self.inner(gp[i], Zp[i]) + self.inner(gq[i], Zq[i]) for i in range(k))
+            gz = self.gdot(gp, gq, zp, zq, Zp, Zq)
         restart = self.prev is None or self.it % self.restart_every == 0 or self.flipped
         beta = 0.0
         if not restart:
-            pdir_p, pdir_q, pDp, pDq, pZp, pZq, pgz = self.prev
-            gzp = sum(self.inner(gp[i], pZp[i]) + self.inner(gq[i], pZq[i]) for i in range(k))
+            pdir_p, pdir_q, pDp, pDq, pzp, pzq, pZp, pZq, pgz = self.prev
+            gzp = self.gdot(gp, gq, pzp, pzq, pZp, pZq)
             beta = max(0.0, (gz - gzp) / pgz) if pgz != 0.0 else 0.0
         # descent directions: d = -z + beta d_prev (L space), Delta = its image in P space
         dir_p, dir_q, Dp, Dq = -zp, -zq, -Zp, -Zq
@@ -343,7 +346,7 @@ class PCG:
             dir_q = dir_q + beta * pdir_q
             Dp = Dp + beta * pDp
             Dq = Dq + beta * pDq
-            slope = sum(self.inner(gp[i], Dp[i]) + self.inner(gq[i], Dq[i]) for i in range(k))
+            slope = self.gdot(gp, gq, dir_p, dir_q, Dp, Dq)
             if slope >= 0.0:
                 beta = 0.0
                 dir_p, dir_q, Dp, Dq = -zp, -zq, -Zp, -Zq
@@ -379,7 +382,7 @@ class PCG:
             self.Pp = np.array([op.project(Y) for Y in self.Yp])
             self.Pq = np.array([op.project(Y) for Y in self.Yq])
             self.reapply()
-        self.prev = (dir_p, dir_q, Dp, Dq, Zp, Zq, gz)
+        self.prev = (dir_p, dir_q, Dp, Dq, zp, zq, Zp, Zq, gz)
         self.omega_prev = omega
         return lam
 

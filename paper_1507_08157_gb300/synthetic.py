@@ -53,6 +53,7 @@ class Recipe:
     h_sigma: float = 0.1       # Ha, std of the random Hamiltonian entries
     h_decay_ang: float = 2.0   # entries decay as exp(-d / h_decay)
     kernel_cutoff_ang: float = 0.0   # <= 0: response kernels not truncated
+    density_kernel_cutoff_ang: float = 0.0   # > 0: P^v, P^c truncated at this radius (sparse form)
     seed: int = 0
     cluster_ang: float = 0.0   # > 0: atoms only inside a centred cube of this side (vacuum around)
     sphere_density: float = 0.0   # > 0: atoms fill a centred sphere at this density (A^-3) ...
@@ -118,6 +119,7 @@ class System:
     kernel_cutoff: float   # bohr; <= 0 means no truncation
     n_occ: int
     n_cond: int
+    density_kernel_cutoff: float = 0.0   # bohr; > 0: P^v, P^c truncated there (sparse form)
 
     @property
     def natoms(self) -> int:
@@ -516,7 +518,8 @@ def generate(recipe: Recipe) -> System:
     return System(recipe=recipe, cell=cell, n=n, pos=pos, phi=phi, chi=chi,
                   S_phi=S_phi, S_chi=S_chi, H_phi=H_phi, H_chi=H_chi, P_v=P_v, P_c=P_c,
                   n0=n0, kernel_cutoff=recipe.kernel_cutoff_ang * BOHR_PER_ANG,
-                  n_occ=n_occ, n_cond=n_cond)
+                  n_occ=n_occ, n_cond=n_cond,
+                  density_kernel_cutoff=recipe.density_kernel_cutoff_ang * BOHR_PER_ANG)
 
 
 @dataclasses.dataclass

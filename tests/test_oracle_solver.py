@@ -178,7 +178,7 @@ def test_exact_preconditioner_solves_eq_precond(tiny_system, tiny_operator):
     g = op.Pc @ rng.normal(size=(op.Pc.shape[0], op.Pv.shape[0])) @ op.Pv
     ex = solver.PCG(op, sy.initial_guess(tiny_system, 1, 1), precond="exact")
     G = ex.exact_preconditioner(g)
-    L = ex.Mc @ G - G @ ex.Mv
+    L = op.Pc @ op.Hc @ G - G @ op.Hv @ op.Pv
     assert np.max(np.abs(L - g)) <= 1e-10 * np.max(np.abs(g))
     it = solver.PCG(op, sy.initial_guess(tiny_system, 1, 1), precond_tol=1e-13, precond_maxit=2000)
     Gi = it.apply_preconditioner(g)
