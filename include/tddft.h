@@ -91,6 +91,42 @@ typedef struct {
                                  <= kernel_cutoff */
 } tddft_system;
 
+/* An atom-blocked sparse matrix (block sparse row). Block rows and block columns are atoms; block
+ * (I, J) is dim(I) x dim(J) with dim(I) the number of functions of atom I in the row set (chi or
+ * phi, as the field's name says) and dim(J) likewise in the column set; a function set lists its
+ * functions grouped by atom (atom[] nondecreasing), and the rows of a block follow that order.
+ *   row_ptr [natoms + 1]: blocks of row I are row_ptr[I] .. row_ptr[I+1]-1
+ *   col_idx [nnzb]: column atom of each block, strictly ascending within a row
+ *   blk_off [nnzb + 1]: values of block b are val[blk_off[b] .. blk_off[b+1]), row-major,
+ *                       blk_off[b+1] - blk_off[b] = dim(I) dim(J)
+ * Absent blocks are zero. All host pointers, owned by the caller. */
+typedef struct {
+    const int64_t *row_ptr;
+    const int32_t *col_idx;
+    const int64_t *blk_off;
+    const double *val;
+} tddft_bsr;
+
+/* One system in the truncated (linear-scaling) form of Sec. IV: every density matrix truncated by
+ * atom-pair distance so that every matrix product scales linearly with the number of atoms.
+ * Ground-state matrices come atom-blocked; see tddft_create_sparse for the semantics. */
+typedef struct {
+    double cell;              /* cubic cell side (bohr) */
+    int32_t n;                /* grid points per side: 2^a 3^b 5^c, 8 <= n <= 256 */
+    int32_t natoms;
+    const double *pos;        /* [natoms][3] (bohr) */
+    tddft_funcs phi;          /* valence functions, grouped by atom, <= 64 per atom */
+    tddft_funcs chi;          /* conduction functions, grouped by atom, <= 128 per atom */
+    tddft_bsr S_chi, H_chi, P_c;   /* chi x chi */
+    tddft_bsr S_phi, H_phi, P_v;   /* phi x phi */
+    const double *n0;         /* [n^3] ground-state density (bohr^-3), for f_xc */
+    int32_t fxc_kind;         /* TDDFT_FXC_LDA_PW92 or TDDFT_FXC_NONE */
+    double kernel_cutoff;     /* bohr, > 0: the pattern of every chi x phi matrix (atom pairs
+                                 within this minimum-image distance) */
+    double density_kernel_cutoff;  /* bohr; > 0: P^c and P^v are truncated to atom pairs within
+                                 it; <= 0: they are used as given */
+} tddft_sparse_system;
+
 typedef struct {
     int32_t precision;        /* TDDFT_FP64: all arithmetic in float64.
                                  TDDFT_MIXED: matrices, grids and FFTs in float32; traces,
@@ -132,6 +168,36 @@ void tddft_default_options(tddft_options *opt);
 tddft_status tddft_create(const tddft_system *sys, const tddft_options *opt, void *cuda_stream,
                           tddft_ctx **out);
 void tddft_destroy(tddft_ctx *ctx);
+
+/* A context in the truncated (linear-scaling) form (Sec. IV, "Linear-scaling capabilities"; the
+ * auxiliary matrices of Sec. III A, Eq. auxiliary). Semantics:
+ *  - P^c_t, P^v_t: P^c and P^v with the atom blocks beyond density_kernel_cutoff removed;
+ *  - products of ground-state matrices are exact: M_c = P^c_t H^chi, M_v = H^phi P^v_t,
+ *    R_c = P^c_t S^chi, R_v = S^phi P^v_t, A_c = S^chi R_c, A_v = R_v S^phi;
+ *  - every product whose result is a chi x phi matrix is truncated to the kernel pattern (atom
+ *    pairs within kernel_cutoff), a chain of two products after each one; so Eq. operator_RPA
+ *    reads f_p = T(M_c P^p) - T(P^p M_v), f_q = T(M_c P^q) - T(P^q M_v) + 2 T(T(P^c_t V) P^v_t)
+ *    with V = T(V_SCF[P^q]), the trace metric is <X, Y> = sum cov(X) * Y with
+ *    cov(X) = T(T(S^chi X) S^phi), Eq. auxiliary is P = T(T(R_c L) R_v), the L-gradient
+ *    T(T(A_c g) A_v), Eq. precond's operator T(M_c G) - T(G M_v).
+ * Every chi x phi array at the boundary of a sparse context (tddft_apply, tddft_state_create,
+ * tddft_state_get, tddft_response_density's P, tddft_potential_integrals' out) is [k][nnz]: the
+ * values of the kernel pattern in the atom-blocked order tddft_kernel_pattern describes. Inside,
+ * atoms are grouped into spatial clusters and every matrix is a list of dense cluster blocks
+ * (128 chi x 64 phi for the kernels) multiplied block by block, only over pairs of nonzero blocks
+ * (tensor cores for TDDFT_MIXED). Preconditioners: TDDFT_PRECOND_ITER (CG on Eq. precond in the
+ * trace metric) or NONE; others give INVALID. Errors: INVALID (sizes, patterns, functions not
+ * grouped by atom, more than 128 chi or 64 phi functions on an atom, kernel_cutoff <= 0), NOMEM,
+ * CUDA. */
+tddft_status tddft_create_sparse(const tddft_sparse_system *sys, const tddft_options *opt, void *cuda_stream,
+                                 tddft_ctx **out);
+
+/* The atom-blocked pattern of the response kernels of a sparse context (the order of its
+ * boundary arrays): nnzb blocks and nnz values; row_ptr [natoms + 1], col_idx [nnzb] and
+ * blk_off [nnzb + 1] as in tddft_bsr (rows chi atoms, columns phi atoms). Any pointer may be
+ * NULL (call once for the sizes). INVALID for a dense context. */
+tddft_status tddft_kernel_pattern(const tddft_ctx *ctx, int64_t *nnzb, int64_t *nnz, int64_t *row_ptr,
+                                  int32_t *col_idx, int64_t *blk_off);
 
 /* Set-up of nsys independent systems of any sizes (a batch): out[i] receives the context of
  * sys[i] as tddft_create makes it, except that each context owns a non-blocking CUDA stream of

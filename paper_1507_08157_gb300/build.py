@@ -11,8 +11,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libtddft.so")
-SOURCES = ["api.cu", "gemm.cu", "grid.cu", "grid_tc.cu", "learned.cu", "solver_kernels.cu", "spectrum.cu", "profile.cu",
-           "tc_gemm.cu"]
+SOURCES = ["api.cu", "bsr_tc.cu", "gemm.cu", "grid.cu", "grid_tc.cu", "learned.cu", "solver_kernels.cu", "sparse.cu",
+           "spectrum.cu", "profile.cu", "tc_gemm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -3,6 +3,7 @@
 #include "tddft.h"
 #include "learned.h"
 #include "solver_kernels.h"
+#include "sparse.h"
 #include "tddft_internal.h"
 
 #include <cuda_fp16.h>
@@ -18,6 +19,7 @@
 #include <initializer_list>
 #include <memory>
 #include <new>
+#include <stdexcept>
 #include <string>
 #include <thread>
 #include <vector>
@@ -245,6 +247,11 @@ struct Impl {
     float *lfc = nullptr, *lfv = nullptr, *ldist = nullptr, *lF = nullptr, *lA = nullptr, *ls = nullptr;
     const tddft_mlp *lA_model = nullptr;
     long long lA_version = -1;
+    // truncated (sparse) form: constants as cluster blocks in T (chi x chi, phi x phi, and the phi
+    // ones transposed for the tensor-core products), a dense scratch for the grid kernels and the
+    // transposed right operands of the tensor-core left products (workspace)
+    T *cc[SP_NCONST] = {}, *vv[SP_NCONST] = {}, *vvT[SP_NCONST] = {};
+    T *dense = nullptr, *opT = nullptr;
 };
 
 }  // namespace
@@ -277,9 +284,12 @@ struct tddft_ctx {
     cudaEvent_t sync_ev = nullptr;
     int *hword = nullptr;   // pinned: the tensor-core kernels' error word, read with each status
     int device = 0;         // the CUDA device the context was made on
+    bool sparse = false;    // truncated (linear-scaling) form: cluster-blocked matrices
+    std::unique_ptr<SparseLayout> sp;
     GridShape grid() const { return GridShape{n, nt, cell, dV, pair_points, table_values}; }
     ~tddft_ctx();
-    long long len() const { return (long long)nc * nv; }
+    long long len() const { return sparse ? sp->len() : (long long)nc * nv; }
+    long long nnz_abi() const { return sparse ? sp->nnz_abi : (long long)nc * nv; }   // values per state at the ABI
     long long n3() const { return (long long)n * n * n; }
 };
 
@@ -545,6 +555,40 @@ template <> void download<double>(tddft_ctx *c, Impl<double> &I, const double *s
     check(ctx_sync(c), "sync copy out");
 }
 
+// k chi x phi matrices across the ABI: dense [k][N_chi][N_phi], or in a sparse context [k][nnz]
+// in the atom-blocked order of the kernel pattern (converted to and from the cluster blocks)
+template <typename T>
+void abi_in(tddft_ctx *c, Impl<T> &I, const double *src, T *dst, int k) {
+    if (!c->sparse) {
+        upload<T>(c, I, src, dst, (long long)k * c->len());
+        return;
+    }
+    const long long n = (long long)k * c->nnz_abi();
+    const double *d = src;
+    if (!is_device_ptr(src)) {
+        check(cudaMemcpyAsync(I.stage, src, n * sizeof(double), cudaMemcpyHostToDevice, c->st), "H2D");
+        d = I.stage;
+    }
+    cb_from_abi<T>(c->st, *c->sp, d, dst, k);
+}
+
+template <typename T>
+void abi_out(tddft_ctx *c, Impl<T> &I, const T *src, double *dst, int k) {
+    if (!dst) return;
+    if (!c->sparse) {
+        download<T>(c, I, src, dst, (long long)k * c->len());
+        return;
+    }
+    const long long n = (long long)k * c->nnz_abi();
+    if (is_device_ptr(dst)) {
+        cb_to_abi<T>(c->st, *c->sp, src, dst, k);
+    } else {
+        cb_to_abi<T>(c->st, *c->sp, src, I.stage, k);
+        check(cudaMemcpyAsync(dst, I.stage, n * sizeof(double), cudaMemcpyDeviceToHost, c->st), "D2H");
+        check(ctx_sync(c), "sync D2H");
+    }
+}
+
 // workspace for the operator on up to `states` grid states (2k for a batch of k pairs)
 template <typename T>
 void ensure_workspace(tddft_ctx *c, Impl<T> &I, int states) {
@@ -559,9 +603,16 @@ void ensure_workspace(tddft_ctx *c, Impl<T> &I, int states) {
     I.tmp = I.wmem.template alloc<T>((size_t)states * len);
     I.bufP = I.wmem.template alloc<T>((size_t)states * len);
     I.bufF = I.wmem.template alloc<T>((size_t)states * len);
-    I.stage = I.wmem.template alloc<double>((size_t)std::max<long long>(states * len, states * n3));
+    I.stage = I.wmem.template alloc<double>(
+        (size_t)std::max({states * len, states * n3, states * c->nnz_abi()}));
     I.tc_bits = I.wmem.template alloc<unsigned>((size_t)states);
     I.tc_scale = I.wmem.template alloc<float>((size_t)states);
+    if (c->sparse) {
+        // the grid kernels address P and V densely; the tensor-core left products take their
+        // right operand block-transposed
+        I.dense = I.wmem.template alloc<T>((size_t)states * c->nc * c->nv);
+        I.opT = I.wmem.template alloc<T>((size_t)states * len);
+    }
     I.cap = states;
 }
 
@@ -569,29 +620,102 @@ void ensure_workspace(tddft_ctx *c, Impl<T> &I, int states) {
 // whose tiles fit, CUDA cores otherwise
 template <typename T>
 void density(tddft_ctx *c, Impl<T> &I, const T *P, int ns) {
+    if (c->sparse) {
+        cb_to_dense<T>(c->st, *c->sp, P, I.dense, ns);
+        P = I.dense;
+    }
     if constexpr (sizeof(T) == 4) {
         if (I.grid_tc) {
-            response_density_tc(c->st, c->grid(), I.chi, I.phi, I.chi_pm, I.CK, I.NPmax, c->nv, P, c->len(), ns,
+            response_density_tc(c->st, c->grid(), I.chi, I.phi, I.chi_pm, I.CK, I.NPmax, c->nv, P,
+                                (long long)c->nc * c->nv, ns,
                                 I.rho, I.tc_bits, I.tc_scale, tc_error_word(), I.phi_quads, I.phi_pm,
                                 I.live_tiles, I.nlive);
             return;
         }
     }
-    response_density<T>(c->st, c->grid(), I.chi, I.phi, c->nv, P, c->len(), ns, I.rho);
+    response_density<T>(c->st, c->grid(), I.chi, I.phi, c->nv, P, (long long)c->nc * c->nv, ns, I.rho);
 }
 
 template <typename T>
 void integrals(tddft_ctx *c, Impl<T> &I, int ns) {
+    // sparse form: the dense integrals into the scratch, then T(V) into the cluster blocks
+    T *out = c->sparse ? I.dense : I.Vmat;
+    bool done = false;
     if constexpr (sizeof(T) == 4) {
         if (I.integrals_tc) {
             potential_integrals_tc(c->st, c->grid(), I.chi, I.phi, I.chi_fm16, I.nslots_chi, I.phi_fm16, I.nslots_phi,
                                    I.NPint, I.maxc, c->nc,
-                                   c->nv, I.V, ns, I.Vmat, I.tc_bits, I.tc_scale, I.int_units, I.int_count,
+                                   c->nv, I.V, ns, out, I.tc_bits, I.tc_scale, I.int_units, I.int_count,
                                    tc_error_word());
+            done = true;
+        }
+    }
+    if (!done) potential_integrals<T>(c->st, c->grid(), I.chi, I.phi, c->nc, c->nv, I.V, ns, out);
+    if (c->sparse) cb_from_dense<T>(c->st, *c->sp, I.dense, I.Vmat, I.mask, ns);
+}
+
+// ---- products with the constants -------------------------------------------------------------------
+// chi x chi constant by role (SP_M: P^c H^chi, SP_P: P^c, SP_R: P^c S^chi, SP_A: S^chi P^c S^chi,
+// SP_S: S^chi) and the phi x phi ones (H^phi P^v, P^v, S^phi P^v, S^phi P^v S^phi, S^phi)
+template <typename T>
+const T *cconst(Impl<T> &I, int x) {
+    const T *m[SP_NCONST] = {I.Mc, I.Pc, I.Rc, I.Ac, I.Sc};
+    return m[x];
+}
+template <typename T>
+const T *vconst(Impl<T> &I, int x) {
+    const T *m[SP_NCONST] = {I.Mv, I.Pv, I.Rv, I.Av, I.Sv};
+    return m[x];
+}
+
+bool sparse_tc(tddft_ctx *c) { return c->prec == TDDFT_MIXED && tc_enabled() && bsr_tc_available(); }
+
+// out_b = alpha C_x X_b + beta out_b for nb chi x phi matrices; in the sparse form a block-sparse
+// product cut to the kernel pattern (Sec. IV truncation)
+template <typename T>
+void lprod(tddft_ctx *c, Impl<T> &I, int x, const T *X, T *out, int nb, T alpha, T beta, bool approx = false) {
+    const long long len = c->len();
+    if (!c->sparse) {
+        const int nc = c->nc, nv = c->nv;
+        gemm<T>(c->st, false, false, nc, nv, nc, alpha, cconst(I, x), nc, 0, X, nv, len, beta, out, nv, len, nb, approx);
+        return;
+    }
+    const SparseLayout &L = *c->sp;
+    const PairList &pl = L.left[x];
+    ProfScope ps(c->st, ST_GEMM, (double)pl.nnz_flops * nb,
+                 sizeof(T) * ((double)L.cc_len(x) + (double)len * nb * (beta == T(0) ? 2 : 3)));
+    if constexpr (sizeof(T) == 4) {
+        if (sparse_tc(c)) {
+            bsr_transpose<T>(c->st, X, I.opT, CB_R, CB_C, L.pk.nnzb(), nb);
+            bsr_tc(c->st, CB_R, pl, L.pcc[x].nnzb(), (const float *)I.cc[x], 0, L.pk.nnzb(), (const float *)I.opT, len,
+                   (float *)out, len, nb, (float)alpha, (float)beta, (const float *)I.mask, approx);
             return;
         }
     }
-    potential_integrals<T>(c->st, c->grid(), I.chi, I.phi, c->nc, c->nv, I.V, ns, I.Vmat);
+    bsr_simt<T>(c->st, CB_R, CB_R, CB_C, pl, L.pk.nnzb(), I.cc[x], 0, X, len, out, len, nb, alpha, beta, I.mask);
+}
+
+// out_b = alpha X_b D_x + beta out_b
+template <typename T>
+void rprod(tddft_ctx *c, Impl<T> &I, const T *X, int x, T *out, int nb, T alpha, T beta, bool approx = false) {
+    const long long len = c->len();
+    if (!c->sparse) {
+        const int nc = c->nc, nv = c->nv;
+        gemm<T>(c->st, false, false, nb * nc, nv, nv, alpha, X, nv, 0, vconst(I, x), nv, 0, beta, out, nv, 0, 1, approx);
+        return;
+    }
+    const SparseLayout &L = *c->sp;
+    const PairList &pl = L.right[x];
+    ProfScope ps(c->st, ST_GEMM, (double)pl.nnz_flops * nb,
+                 sizeof(T) * ((double)L.vv_len(x) + (double)len * nb * (beta == T(0) ? 2 : 3)));
+    if constexpr (sizeof(T) == 4) {
+        if (sparse_tc(c)) {
+            bsr_tc(c->st, CB_C, pl, L.pk.nnzb(), (const float *)X, len, L.pvv[x].nnzb(), (const float *)I.vvT[x], 0,
+                   (float *)out, len, nb, (float)alpha, (float)beta, (const float *)I.mask, approx);
+            return;
+        }
+    }
+    bsr_simt<T>(c->st, CB_R, CB_C, CB_C, pl, L.pk.nnzb(), X, len, I.vv[x], 0, out, len, nb, alpha, beta, I.mask);
 }
 
 // the error word of the tensor-core kernels (bounded waits that expired), read with one stream wait
@@ -613,25 +737,23 @@ void apply_impl(tddft_ctx *c, Impl<T> &I, int k, const T *P, T *f, bool mirror =
     if (mirror && c->opt.mode == TDDFT_MODE_TDA) {
         const long long len = c->len();
         ensure_workspace(c, I, 2 * k);
-        const int nc = c->nc, nv = c->nv;
         cudaStream_t st = c->st;
-        gemm<T>(st, false, false, nc, nv, nc, T(1), I.Mc, nc, 0, P, nv, len, T(0), f, nv, len, k);
-        gemm<T>(st, false, false, k * nc, nv, nv, T(-1), P, nv, 0, I.Mv, nv, 0, T(1), f, nv, 0, 1);
+        lprod<T>(c, I, SP_M, P, f, k, T(1), T(0));
+        rprod<T>(c, I, P, SP_M, f, k, T(-1), T(1));
         density(c, I, P, k);
         hartree_fxc<T>(st, c->grid(), I.rho, I.fxc, k, I.V, I.fft);
         integrals(c, I, k);
-        gemm<T>(st, false, false, nc, nv, nc, T(1), I.Pc, nc, 0, I.Vmat, nv, len, T(0), I.tmp, nv, len, k);
-        gemm<T>(st, false, false, k * nc, nv, nv, T(1), I.tmp, nv, 0, I.Pv, nv, 0, T(1), f, nv, 0, 1);
+        lprod<T>(c, I, SP_P, I.Vmat, I.tmp, k, T(1), T(0));
+        rprod<T>(c, I, I.tmp, SP_P, f, k, T(1), T(1));
         check(cudaMemcpyAsync(f + k * len, f, k * len * sizeof(T), cudaMemcpyDeviceToDevice, st), "mirror f_q");
         return;
     }
     ensure_workspace(c, I, 2 * k);
-    const int nc = c->nc, nv = c->nv;
     const long long len = c->len();
     cudaStream_t st = c->st;
     // Kohn-Sham difference part: f = (P^c H^chi) P - P (H^phi P^v) on all 2k matrices
-    gemm<T>(st, false, false, nc, nv, nc, T(1), I.Mc, nc, 0, P, nv, len, T(0), f, nv, len, 2 * k);
-    gemm<T>(st, false, false, 2 * k * nc, nv, nv, T(-1), P, nv, 0, I.Mv, nv, 0, T(1), f, nv, 0, 1);
+    lprod<T>(c, I, SP_M, P, f, 2 * k, T(1), T(0));
+    rprod<T>(c, I, P, SP_M, f, 2 * k, T(-1), T(1));
     if (c->opt.mode == TDDFT_MODE_D_ONLY) return;
     const bool tda = c->opt.mode == TDDFT_MODE_TDA;
     const int ns = tda ? 2 * k : k;
@@ -643,8 +765,8 @@ void apply_impl(tddft_ctx *c, Impl<T> &I, int k, const T *P, T *f, bool mirror =
     hartree_fxc<T>(st, g, I.rho, I.fxc, ns, I.V, I.fft);
     integrals(c, I, ns);
     // coupling: f_q += 2 P^c V_SCF P^v
-    gemm<T>(st, false, false, nc, nv, nc, T(1), I.Pc, nc, 0, I.Vmat, nv, len, T(0), I.tmp, nv, len, ns);
-    gemm<T>(st, false, false, ns * nc, nv, nv, alpha, I.tmp, nv, 0, I.Pv, nv, 0, T(1), fs, nv, 0, 1);
+    lprod<T>(c, I, SP_P, I.Vmat, I.tmp, ns, T(1), T(0));
+    rprod<T>(c, I, I.tmp, SP_P, fs, ns, alpha, T(1));
 }
 
 // ---- context construction ----------------------------------------------------------------------
@@ -777,13 +899,22 @@ int projector_basis(cudaStream_t st, Mem &tmp, const double *Sh, const double *P
 }
 
 template <typename T>
-void build_impl(tddft_ctx *c, const tddft_system *s) {
+void build_dense_matrices(tddft_ctx *c, Impl<T> *I, const tddft_system *s, Mem &tmpm);
+template <typename T>
+void build_sparse_matrices(tddft_ctx *c, Impl<T> *I);
+
+// s: a dense system, or null with ss: a system of the truncated form
+template <typename T>
+void build_impl(tddft_ctx *c, const tddft_system *s, const tddft_sparse_system *ss = nullptr) {
     auto I = std::make_unique<Impl<T>>();
-    const int nc = c->nc, nv = c->nv, n = c->n;
+    const int n = c->n;
     cudaStream_t st = c->st;
+    const tddft_funcs &chi_f = s ? s->chi : ss->chi, &phi_f = s ? s->phi : ss->phi;
+    const double *n0_in = s ? s->n0 : ss->n0;
+    const int fxc_kind = s ? s->fxc_kind : ss->fxc_kind;
     std::vector<int> cc_cnt, cv_cnt;
-    build_tiles<T>(s->chi, n, c->nt, I->mem, I->chi, cc_cnt);
-    build_tiles<T>(s->phi, n, c->nt, I->mem, I->phi, cv_cnt);
+    build_tiles<T>(chi_f, n, c->nt, I->mem, I->chi, cc_cnt);
+    build_tiles<T>(phi_f, n, c->nt, I->mem, I->phi, cv_cnt);
     if constexpr (sizeof(T) == 4) {
         // tensor-core grid path: point-major f16 chi copy, state-group shape
         const char *ng = std::getenv("TDDFT_NO_GRID_TC");
@@ -932,8 +1063,63 @@ void build_impl(tddft_ctx *c, const tddft_system *s) {
     }
     c->pair_points = pp;
     c->table_values = tv;
-    // float64 products on the device, then stored in T
     Mem tmpm;
+    auto up64 = [&](const double *h, long long cnt) {
+        double *d = tmpm.alloc<double>(cnt);
+        check(cudaMemcpyAsync(d, h, cnt * sizeof(double), cudaMemcpyHostToDevice, st), "upload matrix");
+        return d;
+    };
+    auto keep = [&](const double *d, long long cnt) {
+        T *o = I->mem.template alloc<T>(cnt);
+        convert<double, T>(st, d, o, cnt);
+        return o;
+    };
+    if (s) build_dense_matrices<T>(c, I.get(), s, tmpm);
+    else build_sparse_matrices<T>(c, I.get());
+    // f_xc[n0], float64, once per system
+    const long long n3 = c->n3();
+    I->fxc64 = I->mem.template alloc<double>(n3);
+    if (fxc_kind == TDDFT_FXC_LDA_PW92) {
+        double *n0 = up64(n0_in, n3);
+        fxc_lda(st, n0, I->fxc64, n3);
+        I->fxc = keep(I->fxc64, n3);
+    } else {
+        check(cudaMemsetAsync(I->fxc64, 0, n3 * sizeof(double), st), "memset fxc");
+        I->fxc = nullptr;
+    }
+    check(ctx_sync(c), "build sync");
+    if constexpr (sizeof(T) == 8) c->d64 = std::move(I);
+    else c->d32 = std::move(I);
+}
+
+// the cluster-block constants of the truncated form in T (and the phi ones transposed for the
+// tensor-core right products), and the kernel-pattern mask
+template <typename T>
+void build_sparse_matrices(tddft_ctx *c, Impl<T> *I) {
+    const SparseLayout &L = *c->sp;
+    cudaStream_t st = c->st;
+    const bool tc = sparse_tc(c);
+    for (int x = 0; x < SP_NCONST; ++x) {
+        const long long nc_ = L.cc_len(x), nv_ = L.vv_len(x);
+        I->cc[x] = I->mem.template alloc<T>(std::max<long long>(1, nc_));
+        convert<double, T>(st, L.cc64[x], I->cc[x], nc_);
+        I->vv[x] = I->mem.template alloc<T>(std::max<long long>(1, nv_));
+        convert<double, T>(st, L.vv64[x], I->vv[x], nv_);
+        if (tc) {
+            I->vvT[x] = I->mem.template alloc<T>(std::max<long long>(1, nv_));
+            bsr_transpose<T>(st, I->vv[x], I->vvT[x], CB_C, CB_C, L.pvv[x].nnzb(), 1);
+        }
+    }
+    I->mask = I->mem.template alloc<T>(std::max<long long>(1, L.len()));
+    cb_mask<T>(st, L, I->mask);
+}
+
+// the dense constants: products, overlap roots and the preconditioner's bases (float64 on the
+// device, kept in T), and the kernel-pattern mask
+template <typename T>
+void build_dense_matrices(tddft_ctx *c, Impl<T> *I, const tddft_system *s, Mem &tmpm) {
+    const int nc = c->nc, nv = c->nv;
+    cudaStream_t st = c->st;
     auto up64 = [&](const double *h, long long cnt) {
         double *d = tmpm.alloc<double>(cnt);
         check(cudaMemcpyAsync(d, h, cnt * sizeof(double), cudaMemcpyHostToDevice, st), "upload matrix");
@@ -1040,20 +1226,7 @@ void build_impl(tddft_ctx *c, const tddft_system *s) {
             m[(size_t)a * nv + b] = c->amask[(size_t)s->chi.atom[a] * c->natoms + s->phi.atom[b]] ? 1.0 : 0.0;
     double *dm = up64(m.data(), (long long)nc * nv);
     I->mask = keep(dm, (long long)nc * nv);
-    // f_xc[n0], float64, once per system
-    const long long n3 = c->n3();
-    I->fxc64 = I->mem.template alloc<double>(n3);
-    if (s->fxc_kind == TDDFT_FXC_LDA_PW92) {
-        double *n0 = up64(s->n0, n3);
-        fxc_lda(st, n0, I->fxc64, n3);
-        I->fxc = keep(I->fxc64, n3);
-    } else {
-        check(cudaMemsetAsync(I->fxc64, 0, n3 * sizeof(double), st), "memset fxc");
-        I->fxc = nullptr;
-    }
     check(ctx_sync(c), "build sync");
-    if constexpr (sizeof(T) == 8) c->d64 = std::move(I);
-    else c->d32 = std::move(I);
 }
 
 }  // namespace
@@ -1150,13 +1323,18 @@ void alloc_state(tddft_ctx *c, tddft_state *S) {
 // cov(X) = S^chi X S^phi for 2k matrices
 template <typename T>
 void covariant(tddft_ctx *c, Impl<T> &I, int nb, const T *X, T *out, T *tmp) {
-    const int nc = c->nc, nv = c->nv;
-    const long long len = c->len();
-    gemm<T>(c->st, false, false, nc, nv, nc, T(1), I.Sc, nc, 0, X, nv, len, T(0), tmp, nv, len, nb);
-    gemm<T>(c->st, false, false, nb * nc, nv, nv, T(1), tmp, nv, 0, I.Sv, nv, 0, T(0), out, nv, 0, 1);
+    lprod<T>(c, I, SP_S, X, tmp, nb, T(1), T(0));
+    rprod<T>(c, I, tmp, SP_S, out, nb, T(1), T(0));
 }
 
-// out = L X R (left nc x nc, right nv x nv) for nb matrices
+// out = C_x X D_x for nb matrices (x = SP_R: Eq. auxiliary; SP_A: the L-gradient; SP_P: P^c G P^v)
+template <typename T>
+void sandwich_x(tddft_ctx *c, Impl<T> &I, int nb, int x, const T *X, T *out, T *tmp, bool approx = false) {
+    lprod<T>(c, I, x, X, tmp, nb, T(1), T(0), approx);
+    rprod<T>(c, I, tmp, x, out, nb, T(1), T(0), approx);
+}
+
+// out = L X R (left nc x nc, right nv x nv dense matrices) for nb matrices
 template <typename T>
 void sandwich(tddft_ctx *c, int nb, const T *Lm, const T *X, const T *Rm, T *out, T *tmp, bool approx = false) {
     const int nc = c->nc, nv = c->nv;
@@ -1199,11 +1377,11 @@ void state_init(tddft_ctx *c, tddft_state *S, const double *Y0) {
     const long long len = c->len();
     ensure_workspace(c, I, 2 * k);
     // Y = mask * Y0 for both p and q (X random, Y = 0 => p = q)
-    upload<T>(c, I, Y0, B.Y, k * len);
+    abi_in<T>(c, I, Y0, B.Y, k);
     if (c->trunc) mask_mul<T>(c->st, B.Y, I.mask, len, k);
     check(cudaMemcpyAsync(B.Y + k * len, B.Y, k * len * sizeof(T), cudaMemcpyDeviceToDevice, c->st), "copy Y");
     // P = P^c S^chi L S^phi P^v (Eq. auxiliary)
-    sandwich<T>(c, 2 * k, I.Rc, B.Y, I.Rv, B.P, B.tmp);
+    sandwich_x<T>(c, I, 2 * k, SP_R, B.Y, B.P, B.tmp);
     covariant<T>(c, I, 2 * k, B.P, B.covP, B.tmp);
     gram<T>(c->st, B.covP, len, 2 * k, B.P, len, 2 * k, len, B.PP, B.gscr);
     init_gs(c->st, k, B.PP, B.Cp, B.Cq, B.status);
@@ -1232,7 +1410,7 @@ void evaluate(tddft_ctx *c, tddft_state *S) {
         // G_L = mask * (S P^c S) g (S P^v S); residual = Frobenius norm. With the exact
         // preconditioner G_L only steers the search (its error changes the direction and the
         // residual's last digits, not the fixed point, where g = 0): one TF32 MMA per product
-        sandwich<T>(c, 2 * k, I.Ac, B.g, I.Av, B.G1, B.tmp, I.exact);
+        sandwich_x<T>(c, I, 2 * k, SP_A, B.g, B.G1, B.tmp, I.exact);
         mask_mul<T>(st, B.G1, I.mask, len, 2 * k);
         dots<T>(st, B.G1, len, B.G1, len, 2 * k, len, B.dvec, B.gscr);
     } else {
@@ -1269,6 +1447,38 @@ void precondition(tddft_ctx *c, tddft_state *S, const T *h, T *z) {
     if (c->opt.precond_adaptive && !S->resid.empty()) {
         const double rmax = *std::max_element(S->resid.begin(), S->resid.end());
         ptol = std::min(0.1, std::max(c->opt.precond_tol, rmax));
+    }
+    if (c->sparse) {
+        // truncated form: CG in the original variables on T(M_c G) - T(G M_v) = h with the metric
+        // <X, Y> = sum cov(X) * Y, from G = 0 (every product block-sparse, cut to the pattern)
+        T *r = B.cr, *p = B.cp, *Lp = B.cLp, *cv = B.cLpp;
+        check(cudaMemsetAsync(z, 0, tot * sizeof(T), st), "memset z");
+        check(cudaMemcpyAsync(r, h, tot * sizeof(T), cudaMemcpyDeviceToDevice, st), "copy r");
+        check(cudaMemcpyAsync(p, h, tot * sizeof(T), cudaMemcpyDeviceToDevice, st), "copy p");
+        covariant<T>(c, I, k2, r, cv, B.tmp);
+        dots<T>(st, cv, len, r, len, k2, len, B.dvec2, B.gscr);
+        cg_init(st, k2, ptol, B.dvec2, B.cg_rr, B.cg_r0, B.cg_active, B.cg_nactive);
+        int *hn = reinterpret_cast<int *>(S->host + 2 * S->k) + 1;
+        for (int it = 0; it < c->opt.precond_maxit; ++it) {
+            check(cudaMemcpyAsync(hn, B.cg_nactive, sizeof(int), cudaMemcpyDeviceToHost, st), "D2H n_active");
+            check(ctx_sync(c), "sync cg");
+            if (*hn == 0) break;
+            S->inner_iters += 1;
+            lprod<T>(c, I, SP_M, p, Lp, k2, T(1), T(0));
+            rprod<T>(c, I, p, SP_M, Lp, k2, T(-1), T(1));
+            covariant<T>(c, I, k2, p, cv, B.tmp);
+            dots<T>(st, cv, len, Lp, len, k2, len, B.cg_pLp, B.gscr);
+            cg_scalars(st, k2, 0, ptol, B.cg_pLp, B.cg_rrn, B.cg_rr, B.cg_r0, B.cg_alpha, B.cg_beta, B.cg_active,
+                       B.cg_nactive);
+            axpy_dev<T>(st, B.cg_alpha, 1, 1.0, z, p, len, k2);
+            axpy_dev<T>(st, B.cg_alpha, 1, -1.0, r, Lp, len, k2);
+            covariant<T>(c, I, k2, r, cv, B.tmp);
+            dots<T>(st, cv, len, r, len, k2, len, B.cg_rrn, B.gscr);
+            cg_scalars(st, k2, 1, ptol, B.cg_pLp, B.cg_rrn, B.cg_rr, B.cg_r0, B.cg_alpha, B.cg_beta, B.cg_active,
+                       B.cg_nactive);
+            cg_dir<T>(st, p, r, B.cg_beta, len, k2);
+        }
+        return;
     }
     if (I.exact) {
         // Eq. precond solved exactly: coordinates in the eigenbases of Mch and Mvh, divided by
@@ -1401,7 +1611,7 @@ const T *search_gradient(tddft_ctx *c, tddft_state *S) {
     if (c->trunc) {
         // P^c G_L P^v; with the exact preconditioner it only feeds that preconditioner, whose
         // errors change the search direction and not the fixed point: one TF32 MMA per product
-        sandwich<T>(c, 2 * S->k, I.Pc, B.G1, I.Pv, B.h, B.tmp, I.exact);
+        sandwich_x<T>(c, I, 2 * S->k, SP_P, B.G1, B.h, B.tmp, I.exact);
         return B.h;
     }
     return B.g;
@@ -1421,7 +1631,7 @@ void update(tddft_ctx *c, tddft_state *S) {
         if (learned) learned_precondition<T>(c, S, h, B.z);
         else precondition<T>(c, S, h, B.z);
         if (c->trunc) mask_mul<T>(st, B.z, I.mask, len, k2);
-        sandwich<T>(c, k2, I.Rc, B.z, I.Rv, B.Z, B.tmp);     // Z = P^c S z S P^v (Eq. auxiliary)
+        sandwich_x<T>(c, I, k2, SP_R, B.z, B.Z, B.tmp);     // Z = P^c S z S P^v (Eq. auxiliary)
         // Polak-Ribiere over the set
         if (c->trunc) {
             dots<T>(st, B.G1, len, B.z, len, k2, len, B.dvec, B.gscr);
@@ -1476,7 +1686,7 @@ void update(tddft_ctx *c, tddft_state *S) {
         // P = P^c S L S P^v afresh from the search variables (Eq. auxiliary), then f = f(P)
         check(cudaMemcpyAsync(B.tmp, B.Y, tot * sizeof(T), cudaMemcpyDeviceToDevice, st), "copy Y");
         if (c->trunc) mask_mul<T>(st, B.tmp, I.mask, len, k2);
-        sandwich<T>(c, k2, I.Rc, B.tmp, I.Rv, B.P, B.cLpp);
+        sandwich_x<T>(c, I, k2, SP_R, B.tmp, B.P, B.cLpp);
         covariant<T>(c, I, k2, B.P, B.covP, B.tmp);
         apply_impl<T>(c, I, k, B.P, B.f, true);
     }
@@ -1683,6 +1893,73 @@ tddft_status tddft_create(const tddft_system *s, const tddft_options *opt, void 
     return TDDFT_OK;
 }
 
+tddft_status tddft_create_sparse(const tddft_sparse_system *s, const tddft_options *opt, void *stream,
+                                 tddft_ctx **out) {
+    if (!out) return TDDFT_E_INVALID;
+    *out = nullptr;
+    auto c = std::make_unique<tddft_ctx>();
+    if (opt) c->opt = *opt;
+    else tddft_default_options(&c->opt);
+    c->st = static_cast<cudaStream_t>(stream);
+    c->prec = c->opt.precision;
+    tddft_status rc = guarded(c.get(), [&]() -> tddft_status {
+        if (!s) throw InvalidArg{"null system"};
+        if (c->prec != TDDFT_FP64 && c->prec != TDDFT_MIXED) throw InvalidArg{"unknown precision"};
+        if (c->opt.mode < 0 || c->opt.mode > 2) throw InvalidArg{"unknown mode"};
+        if (c->opt.precond != TDDFT_PRECOND_ITER && c->opt.precond != TDDFT_PRECOND_NONE)
+            throw InvalidArg{"the truncated form takes the iterative preconditioner or none"};
+        if (!(s->cell > 0.0)) throw InvalidArg{"cell must be positive"};
+        if (!fft_size_ok(s->n)) throw InvalidArg{"grid size must be 2^a 3^b 5^c with 8 <= n <= 256"};
+        if (s->natoms <= 0 || !s->pos) throw InvalidArg{"no atoms"};
+        if (!(s->kernel_cutoff > 0.0)) throw InvalidArg{"the truncated form needs kernel_cutoff > 0"};
+        if (s->fxc_kind == TDDFT_FXC_LDA_PW92 && !s->n0) throw InvalidArg{"LDA kernel needs n0"};
+        validate_funcs(s->phi, s->n, s->natoms, "phi");
+        validate_funcs(s->chi, s->n, s->natoms, "chi");
+        c->n = s->n;
+        c->nt = (s->n + TILE - 1) / TILE;
+        c->natoms = s->natoms;
+        c->nc = s->chi.nfun;
+        c->nv = s->phi.nfun;
+        c->cell = s->cell;
+        const double h = s->cell / s->n;
+        c->dV = h * h * h;
+        c->trunc = true;
+        c->sparse = true;
+        c->uniform = false;   // the learned preconditioner is not offered in this form
+        check(cudaGetDevice(&c->device), "cudaGetDevice");
+        check(cudaMallocHost(reinterpret_cast<void **>(&c->hword), sizeof(int)), "cudaMallocHost");
+        *c->hword = 0;
+        try {
+            c->sp = sparse_build(c->st, s);
+        } catch (const std::invalid_argument &e) {
+            throw InvalidArg{e.what()};
+        }
+        c->amask = c->sp->amask;
+        c->adist.assign((size_t)s->natoms * s->natoms, 0.0f);
+        if (c->prec == TDDFT_FP64) build_impl<double>(c.get(), nullptr, s);
+        else build_impl<float>(c.get(), nullptr, s);
+        return TDDFT_OK;
+    });
+    if (rc != TDDFT_OK) {
+        std::fprintf(stderr, "tddft_create_sparse: %s\n", c->err.c_str());
+        return rc;
+    }
+    *out = c.release();
+    return TDDFT_OK;
+}
+
+tddft_status tddft_kernel_pattern(const tddft_ctx *c, int64_t *nnzb, int64_t *nnz, int64_t *row_ptr, int32_t *col_idx,
+                                  int64_t *blk_off) {
+    if (!c || !c->sparse) return TDDFT_E_INVALID;
+    const SparseLayout &L = *c->sp;
+    if (nnzb) *nnzb = (int64_t)L.abi_col.size();
+    if (nnz) *nnz = L.nnz_abi;
+    if (row_ptr) std::copy(L.abi_row_ptr.begin(), L.abi_row_ptr.end(), row_ptr);
+    if (col_idx) std::copy(L.abi_col.begin(), L.abi_col.end(), col_idx);
+    if (blk_off) std::copy(L.abi_blk_off.begin(), L.abi_blk_off.end(), blk_off);
+    return TDDFT_OK;
+}
+
 tddft_status tddft_create_batch(const tddft_system *sys, int32_t nsys, const tddft_options *opt, void *stream,
                                 tddft_ctx **out) {
     if (!sys || !out || nsys <= 0) return TDDFT_E_INVALID;
@@ -1846,11 +2123,11 @@ tddft_status tddft_apply(tddft_ctx *c, int32_t k, const double *Pp, const double
         return DISPATCH(c, ([&]() {
             Impl<T> &I = impl<T>(c);
             ensure_workspace(c, I, 2 * k);
-            upload<T>(c, I, Pp, I.bufP, kl);
-            upload<T>(c, I, Pq, I.bufP + kl, kl);
+            abi_in<T>(c, I, Pp, I.bufP, k);
+            abi_in<T>(c, I, Pq, I.bufP + kl, k);
             apply_impl<T>(c, I, k, I.bufP, I.bufF);
-            download<T>(c, I, I.bufF, fp, kl);
-            download<T>(c, I, I.bufF + kl, fq, kl);
+            abi_out<T>(c, I, I.bufF, fp, k);
+            abi_out<T>(c, I, I.bufF + kl, fq, k);
             check_tc_error(c);
             return TDDFT_OK;
         })());
@@ -1864,7 +2141,7 @@ tddft_status tddft_response_density(tddft_ctx *c, int32_t k, const double *P, do
         return DISPATCH(c, ([&]() {
             Impl<T> &I = impl<T>(c);
             ensure_workspace(c, I, k);
-            upload<T>(c, I, P, I.bufP, (long long)k * c->len());
+            abi_in<T>(c, I, P, I.bufP, k);
             density(c, I, I.bufP, k);
             download<T>(c, I, I.rho, rho, (long long)k * c->n3());
             check_tc_error(c);
@@ -1898,7 +2175,7 @@ tddft_status tddft_potential_integrals(tddft_ctx *c, int32_t k, const double *V,
             ensure_workspace(c, I, k);
             upload<T>(c, I, V, I.V, (long long)k * c->n3());
             integrals(c, I, k);
-            download<T>(c, I, I.Vmat, out, (long long)k * c->len());
+            abi_out<T>(c, I, I.Vmat, out, k);
             check_tc_error(c);
             return TDDFT_OK;
         })());
@@ -1969,12 +2246,12 @@ tddft_status tddft_state_get(tddft_ctx *c, const tddft_state *S, double *Pp, dou
             StateBufs<T> &B = bufs<T>(const_cast<tddft_state *>(S));
             const long long kl = (long long)S->k * c->len();
             ensure_workspace(c, I, 2 * S->k);
-            download<T>(c, I, B.P, Pp, kl);
-            download<T>(c, I, B.P + kl, Pq, kl);
-            download<T>(c, I, B.f, fp, kl);
-            download<T>(c, I, B.f + kl, fq, kl);
-            download<T>(c, I, B.Y, Lp, kl);
-            download<T>(c, I, B.Y + kl, Lq, kl);
+            abi_out<T>(c, I, B.P, Pp, S->k);
+            abi_out<T>(c, I, B.P + kl, Pq, S->k);
+            abi_out<T>(c, I, B.f, fp, S->k);
+            abi_out<T>(c, I, B.f + kl, fq, S->k);
+            abi_out<T>(c, I, B.Y, Lp, S->k);
+            abi_out<T>(c, I, B.Y + kl, Lq, S->k);
             check(ctx_sync(c), "sync state_get");
             return TDDFT_OK;
         })());
@@ -2192,7 +2469,8 @@ tddft_status tddft_response_density_noalloc(tddft_ctx *c, int32_t k, const float
             throw InvalidArg{"tddft_response_density_noalloc: the current device and the devices of P and rho must "
                              "be the context's device"};
         Impl<float> &I = *c->d32;
-        response_density_tc_noalloc(c->st, c->grid(), I.chi, I.phi, I.chi_pm, I.CK, I.NPmax, c->nv, P, c->len(), k,
+        response_density_tc_noalloc(c->st, c->grid(), I.chi, I.phi, I.chi_pm, I.CK, I.NPmax, c->nv, P,
+                                    (long long)c->nc * c->nv, k,
                                     rho, I.phi_pm);
         if (response_density_tc_noalloc_error(c->st))
             throw TimeoutErr{"a bounded wait in the density kernel expired"};

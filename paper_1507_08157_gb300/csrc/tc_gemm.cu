@@ -338,6 +338,22 @@ int *error_word() {
 
 bool tc_gemm_available() { return encode_fn() != nullptr; }
 
+// 3-D tiled float32 map, 128-byte swizzle, zero fill outside: dims d0 (contiguous) x d1 x d2,
+// strides of dims 1 and 2 in bytes, box b0 x b1 x 1
+bool encode_map_3d_f32(CUtensorMap *map, const float *ptr, unsigned long long d0, unsigned long long d1,
+                       unsigned long long d2, unsigned long long s1_bytes, unsigned long long s2_bytes, unsigned b0,
+                       unsigned b1) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[3] = {d0, d1, d2};
+    cuuint64_t strides[2] = {s1_bytes, s2_bytes};
+    cuuint32_t box[3] = {b0, b1, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(ptr), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // 2-D tiled map, 128-byte swizzle, zero fill outside: `inner` elements per row (contiguous),
 // `rows` rows `row_bytes` apart; box box_inner x box_rows
 bool encode_map_2d(CUtensorMap *map, CUtensorMapDataType dt, const void *ptr, unsigned long long inner,

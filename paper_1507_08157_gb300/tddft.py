@@ -44,6 +44,19 @@ class _System(ctypes.Structure):
                 ("kernel_cutoff", ctypes.c_double)]
 
 
+class _Bsr(ctypes.Structure):
+    _fields_ = [("row_ptr", c_int64_p), ("col_idx", c_int32_p), ("blk_off", c_int64_p), ("val", c_double_p)]
+
+
+class _SparseSystem(ctypes.Structure):
+    _fields_ = [("cell", ctypes.c_double), ("n", ctypes.c_int32), ("natoms", ctypes.c_int32),
+                ("pos", c_double_p), ("phi", _Funcs), ("chi", _Funcs),
+                ("S_chi", _Bsr), ("H_chi", _Bsr), ("P_c", _Bsr),
+                ("S_phi", _Bsr), ("H_phi", _Bsr), ("P_v", _Bsr),
+                ("n0", c_double_p), ("fxc_kind", ctypes.c_int32),
+                ("kernel_cutoff", ctypes.c_double), ("density_kernel_cutoff", ctypes.c_double)]
+
+
 class _Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("mode", ctypes.c_int32),
                 ("precond", ctypes.c_int32), ("precond_maxit", ctypes.c_int32),
@@ -70,7 +83,7 @@ SYMBOLS = sorted(["tddft_default_options", "tddft_create", "tddft_destroy", "tdd
                   "tddft_samples", "tddft_state_stats", "tddft_state_export",
                   "tddft_state_import", "tddft_create_batch", "tddft_solve_batch",
                   "tddft_oscillator_strengths", "tddft_spectrum", "tddft_joint_projector",
-                  "tddft_wait_check"])
+                  "tddft_wait_check", "tddft_create_sparse", "tddft_kernel_pattern"])
 
 _lib = None
 _live = weakref.WeakSet()      # open contexts and states, closed before interpreter shutdown
@@ -99,6 +112,9 @@ def load(path: str = LIB_PATH):
     lib.tddft_default_options.argtypes = [ctypes.POINTER(_Options)]
     lib.tddft_default_options.restype = None
     lib.tddft_create.argtypes = [ctypes.POINTER(_System), ctypes.POINTER(_Options), vp, ctypes.POINTER(vp)]
+    lib.tddft_create_sparse.argtypes = [ctypes.POINTER(_SparseSystem), ctypes.POINTER(_Options), vp,
+                                        ctypes.POINTER(vp)]
+    lib.tddft_kernel_pattern.argtypes = [vp, c_int64_p, c_int64_p, c_int64_p, c_int32_p, c_int64_p]
     lib.tddft_destroy.argtypes = [vp]
     lib.tddft_destroy.restype = None
     lib.tddft_last_error.argtypes = [vp]
@@ -150,7 +166,8 @@ def load(path: str = LIB_PATH):
                                        ctypes.POINTER(vp)]
     lib.tddft_solve_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int32, ctypes.c_int32,
                                       vp, vp, c_int32_p, c_int32_p]
-    for name in ("tddft_create", "tddft_dims", "tddft_apply", "tddft_response_density",
+    for name in ("tddft_create", "tddft_create_sparse", "tddft_kernel_pattern", "tddft_dims", "tddft_apply",
+                 "tddft_response_density",
                  "tddft_response_potential", "tddft_potential_integrals", "tddft_fxc",
                  "tddft_state_create", "tddft_pcg_step", "tddft_solve", "tddft_state_get",
                  "tddft_subspace", "tddft_pattern", "tddft_profile", "tddft_profile_read",
@@ -205,8 +222,9 @@ def _options(precision="fp64", mode="full", precond="iter", precond_tol=1e-4, pr
     return o
 
 
-def _marshal(sys: System, fxc="lda"):
-    """The tddft_system view of a System; `keep` holds the arrays it points into."""
+def _marshal(sys: System, fxc="lda", matrices=True):
+    """The tddft_system view of a System; `keep` holds the arrays it points into (matrices=False:
+    only the geometry, functions and n0)."""
     keep = []
 
     def arr(a, dt):
@@ -230,15 +248,79 @@ def _marshal(sys: System, fxc="lda"):
     s.pos = arr(sys.pos, np.float64)
     s.phi = funcs(sys.phi)
     s.chi = funcs(sys.chi)
-    s.S_chi = arr(sys.S_chi, np.float64)
-    s.S_phi = arr(sys.S_phi, np.float64)
-    s.H_chi = arr(sys.H_chi, np.float64)
-    s.H_phi = arr(sys.H_phi, np.float64)
-    s.P_v = arr(sys.P_v, np.float64)
-    s.P_c = arr(sys.P_c, np.float64)
+    if matrices:
+        s.S_chi = arr(sys.S_chi, np.float64)
+        s.S_phi = arr(sys.S_phi, np.float64)
+        s.H_chi = arr(sys.H_chi, np.float64)
+        s.H_phi = arr(sys.H_phi, np.float64)
+        s.P_v = arr(sys.P_v, np.float64)
+        s.P_c = arr(sys.P_c, np.float64)
     s.n0 = arr(sys.n0, np.float64)
     s.fxc_kind = FXC[fxc]
     s.kernel_cutoff = sys.kernel_cutoff
+    return s, keep
+
+
+def atom_counts(atom, natoms):
+    """Functions per atom of a set grouped by atom."""
+    return np.bincount(np.asarray(atom, dtype=np.int64), minlength=natoms)
+
+
+def atom_bsr(M, row_atom, col_atom, natoms):
+    """The atom-blocked form (tddft_bsr) of a dense matrix whose rows and columns are functions
+    grouped by atom: blocks with a nonzero entry, in row-major order of (row atom, column atom).
+    Returns (row_ptr int64 [natoms+1], col_idx int32 [nnzb], blk_off int64 [nnzb+1], val float64)."""
+    M = np.asarray(M, dtype=np.float64)
+    rc, cc = atom_counts(row_atom, natoms), atom_counts(col_atom, natoms)
+    r0 = np.concatenate([[0], np.cumsum(rc)])
+    c0 = np.concatenate([[0], np.cumsum(cc)])
+    if np.all(rc == rc[0]) and np.all(cc == cc[0]) and rc[0] > 0 and cc[0] > 0:
+        nr, nc = int(rc[0]), int(cc[0])
+        blocks = M.reshape(natoms, nr, natoms, nc).transpose(0, 2, 1, 3)
+        keep = np.any(blocks != 0.0, axis=(2, 3))
+        I, J = np.nonzero(keep)
+        val = np.ascontiguousarray(blocks[I, J]).ravel()
+        sizes = np.full(I.size, nr * nc, dtype=np.int64)
+    else:
+        I, J, parts = [], [], []
+        for a in range(natoms):
+            for b in range(natoms):
+                blk = M[r0[a]:r0[a + 1], c0[b]:c0[b + 1]]
+                if blk.size and np.any(blk != 0.0):
+                    I.append(a)
+                    J.append(b)
+                    parts.append(blk.ravel())
+        I, J = np.array(I, dtype=np.int64), np.array(J, dtype=np.int64)
+        val = np.concatenate(parts) if parts else np.zeros(0)
+        sizes = rc[I] * cc[J]
+    row_ptr = np.concatenate([[0], np.cumsum(np.bincount(I, minlength=natoms))]).astype(np.int64)
+    blk_off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    return row_ptr, J.astype(np.int32), blk_off, val
+
+
+def _marshal_sparse(sys: System, fxc="lda"):
+    """The tddft_sparse_system view of a System (matrices in atom-blocked form)."""
+    base, keep = _marshal(sys, fxc, matrices=False)
+
+    def arr(a, dt):
+        a = np.ascontiguousarray(a, dtype=dt)
+        keep.append(a)
+        return a.ctypes.data_as(ctypes.POINTER(np.ctypeslib.as_ctypes_type(dt)))
+
+    def bsr(M, ra, ca):
+        rp, ci, bo, v = atom_bsr(M, ra, ca, sys.natoms)
+        b = _Bsr()
+        b.row_ptr, b.col_idx, b.blk_off, b.val = arr(rp, np.int64), arr(ci, np.int32), arr(bo, np.int64), arr(v, np.float64)
+        return b
+
+    s = _SparseSystem()
+    s.cell, s.n, s.natoms, s.pos, s.phi, s.chi = base.cell, base.n, base.natoms, base.pos, base.phi, base.chi
+    ca, pa = sys.chi.atom, sys.phi.atom
+    s.S_chi, s.H_chi, s.P_c = bsr(sys.S_chi, ca, ca), bsr(sys.H_chi, ca, ca), bsr(sys.P_c, ca, ca)
+    s.S_phi, s.H_phi, s.P_v = bsr(sys.S_phi, pa, pa), bsr(sys.H_phi, pa, pa), bsr(sys.P_v, pa, pa)
+    s.n0, s.fxc_kind = base.n0, base.fxc_kind
+    s.kernel_cutoff = sys.kernel_cutoff
+    s.density_kernel_cutoff = getattr(sys, "density_kernel_cutoff", 0.0)
     return s, keep
 
 
@@ -294,16 +376,23 @@ def solve_batch(states, nthreads=0):
 class Context:
     """One system on the GPU (tddft_create). Keyword options follow tddft_options."""
 
-    def __init__(self, sys: System, fxc="lda", stream=None, _handle=None, **opts):
+    def __init__(self, sys: System, fxc="lda", stream=None, _handle=None, sparse=False, **opts):
+        """sparse=True: the truncated (linear-scaling) form (tddft_create_sparse); every chi x phi
+        array then has the shape [k][nnz] of the kernel pattern (see to_pattern / from_pattern)."""
         lib = load()
         self._lib = lib
         self.sys = sys
+        self.sparse = bool(sparse)
         self.options = _options(**opts)
         if _handle is None:
-            s, keep = _marshal(sys, fxc)
             ctx = ctypes.c_void_p()
             st = ctypes.c_void_p(stream) if stream is not None else None
-            rc = lib.tddft_create(ctypes.byref(s), ctypes.byref(self.options), st, ctypes.byref(ctx))
+            if self.sparse:
+                s, keep = _marshal_sparse(sys, fxc)
+                rc = lib.tddft_create_sparse(ctypes.byref(s), ctypes.byref(self.options), st, ctypes.byref(ctx))
+            else:
+                s, keep = _marshal(sys, fxc)
+                rc = lib.tddft_create(ctypes.byref(s), ctypes.byref(self.options), st, ctypes.byref(ctx))
             if rc != OK:
                 raise TddftError(rc, "tddft_create failed (see stderr)")
         else:
@@ -313,6 +402,48 @@ class Context:
         self.natoms = sys.natoms
         self._states = weakref.WeakSet()
         _live.add(self)
+        if self.sparse:
+            self._pattern_arrays()
+
+    def _pattern_arrays(self):
+        nnzb, nnz = ctypes.c_int64(), ctypes.c_int64()
+        self._check(self._lib.tddft_kernel_pattern(self._ctx, ctypes.byref(nnzb), ctypes.byref(nnz), None, None, None))
+        self.nnz = int(nnz.value)
+        self.kp_row_ptr = np.zeros(self.natoms + 1, dtype=np.int64)
+        self.kp_col = np.zeros(int(nnzb.value), dtype=np.int32)
+        self.kp_blk_off = np.zeros(int(nnzb.value) + 1, dtype=np.int64)
+        self._check(self._lib.tddft_kernel_pattern(
+            self._ctx, None, None, self.kp_row_ptr.ctypes.data_as(c_int64_p),
+            self.kp_col.ctypes.data_as(c_int32_p), self.kp_blk_off.ctypes.data_as(c_int64_p)))
+        # (row, column) of every pattern value in the dense chi x phi matrix
+        rc = atom_counts(self.sys.chi.atom, self.natoms)
+        cc = atom_counts(self.sys.phi.atom, self.natoms)
+        r0 = np.concatenate([[0], np.cumsum(rc)])
+        c0 = np.concatenate([[0], np.cumsum(cc)])
+        rows, cols = [], []
+        for I in range(self.natoms):
+            for b in range(self.kp_row_ptr[I], self.kp_row_ptr[I + 1]):
+                J = int(self.kp_col[b])
+                rr, cc_ = np.meshgrid(np.arange(r0[I], r0[I + 1]), np.arange(c0[J], c0[J + 1]), indexing="ij")
+                rows.append(rr.ravel())
+                cols.append(cc_.ravel())
+        self.kp_rows = np.concatenate(rows) if rows else np.zeros(0, dtype=np.int64)
+        self.kp_cols = np.concatenate(cols) if cols else np.zeros(0, dtype=np.int64)
+
+    def to_pattern(self, X):
+        """Dense [k][N_chi][N_phi] -> [k][nnz]: the kernel pattern's entries in the boundary order."""
+        X = np.asarray(X, dtype=np.float64)
+        return np.ascontiguousarray(X[:, self.kp_rows, self.kp_cols])
+
+    def from_pattern(self, x):
+        """[k][nnz] -> dense [k][N_chi][N_phi] (zero off the pattern)."""
+        x = np.asarray(x, dtype=np.float64)
+        out = np.zeros((x.shape[0], self.nc, self.nv))
+        out[:, self.kp_rows, self.kp_cols] = x
+        return out
+
+    def _kshape(self, k):
+        return (k, self.nnz) if self.sparse else (k, self.nc, self.nv)
 
     def close(self):
         if getattr(self, "_ctx", None):
@@ -340,7 +471,7 @@ class Context:
     # -- Eq. operator_RPA --------------------------------------------------------------------------
     def apply(self, Pp, Pq, fp=None, fq=None):
         k = Pp.shape[0]
-        shape = (k, self.nc, self.nv)
+        shape = self._kshape(k)
         fp = self._out(Pp, shape) if fp is None else fp
         fq = self._out(Pp, shape) if fq is None else fq
         self._check(self._lib.tddft_apply(self._ctx, k, _ptr(Pp), _ptr(Pq), _ptr(fp), _ptr(fq)))
@@ -370,7 +501,7 @@ class Context:
         return out
 
     def potential_integrals(self, V):
-        out = self._out(V, (V.shape[0], self.nc, self.nv))
+        out = self._out(V, self._kshape(V.shape[0]))
         self._check(self._lib.tddft_potential_integrals(self._ctx, V.shape[0], _ptr(V), _ptr(out)))
         return out
 
@@ -493,7 +624,7 @@ class State:
         return om, res, int(it.value), rc
 
     def get(self):
-        shape = (self.k, self.ctx.nc, self.ctx.nv)
+        shape = self.ctx._kshape(self.k)
         out = {name: np.empty(shape) for name in ("Pp", "Pq", "fp", "fq", "Lp", "Lq")}
         self.ctx._check(self.ctx._lib.tddft_state_get(
             self.ctx._ctx, self._st, *(_ptr(out[n]) for n in ("Pp", "Pq", "fp", "fq", "Lp", "Lq"))))
