@@ -4,7 +4,7 @@ against the truncated FP64 oracle (oracle/sparse.py), element by element, throug
 
 Systems:
 * sparse48: 48 atoms (4 phi + 9 chi per atom, so clusters of at most 14 atoms and 128-row
-  blocks) in a 22 A cell on a 66^3 grid, 3.5 A functions, kernel and density-kernel cutoffs of 6 A
+  blocks) in a 22 A cell on a 64^3 grid, 3.5 A functions, kernel and density-kernel cutoffs of 6 A
   (about a tenth of the atom pairs kept): several clusters, block pairs that are skipped, output
   blocks without any pair, atom pairs cut inside present blocks;
 * tiny: 3 atoms with cutoffs covering the cell, where the truncated form is the plain one and
@@ -42,7 +42,7 @@ def tddft():
 
 @pytest.fixture(scope="module")
 def sparse48():
-    rec = sy.Recipe(natoms=48, cell_ang=22.0, ngrid=66, nchi=9, radius_ang=3.5, kernel_cutoff_ang=6.0,
+    rec = sy.Recipe(natoms=48, cell_ang=22.0, ngrid=64, nchi=9, radius_ang=3.5, kernel_cutoff_ang=6.0,
                     density_kernel_cutoff_ang=6.0, seed=41)
     s = sy.generate(rec)
     return s, osp.TruncatedOperator(s)
