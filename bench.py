@@ -68,6 +68,10 @@ def parse():
                     help="comma-separated atom counts of the core + shell series: time operator applies "
                          "on each (one JSON line with the series)")
     ap.add_argument("--scaling-k", type=int, default=4)
+    ap.add_argument("--scaling-dense", action="store_true",
+                    help="the series with dense products instead of the truncated form")
+    ap.add_argument("--scaling-cpu-max-atoms", type=int, default=500,
+                    help="largest member whose oracle sample runs (dense products grow as N^3)")
     return ap.parse_args()
 
 
@@ -597,14 +601,22 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def _loglog_slope(x, y):
+    """Least-squares slope of log y against log x."""
+    lx, ly = np.log(np.asarray(x, dtype=float)), np.log(np.asarray(y, dtype=float))
+    return float(np.polyfit(lx, ly, 1)[0]) if len(lx) > 1 else None
+
+
 def run_scaling(args):
     """Operator applies on the linear-scaling series (synthetic.scaling_recipe: a 140-atom core
     and a solvent-like shell at 0.1 atoms / A^3, 4 phi + 9 chi per atom, R = 8 A, 0.25 A grid,
-    15 A kernel cutoff), k states, mixed precision. Per size: device-resident applies timed with
-    CUDA events after warm-up, the per-stage times of the library's profiler, and the time per
-    unit of algorithmic work W (flops: 2 k pair_points for each grid contraction, 2MNK for every
-    dense product; the stage counters add them up), so that time / W stays flat when the time
-    grows with the work."""
+    every density matrix truncated at 15 A), k states, mixed precision, in the truncated form of
+    Sec. IV (tddft_create_sparse: cluster-blocked matrices, block-sparse tensor-core products).
+    Per size: device-resident applies timed with CUDA events after warm-up, the per-stage times of
+    the library's profiler, and the time per unit of algorithmic work W (flops: 2 k pair_points
+    for each grid contraction, the block products' padded 2MNK), so that time / W stays flat when
+    the time grows with the work; the line ends with the fitted exponents of time against N and
+    of W against N."""
     import torch
     from paper_1507_08157_gb300 import synthetic as sy
     from paper_1507_08157_gb300 import tddft
@@ -618,14 +630,20 @@ def run_scaling(args):
         t0 = time.perf_counter()
         s = sy.generate(rec)
         t1 = time.perf_counter()
-        ctx = tddft.Context(s, precision="mixed", stream=stream.cuda_stream, precond="none")
+        ctx = tddft.Context(s, precision="mixed", stream=stream.cuda_stream, precond="none",
+                            sparse=not args.scaling_dense)
         t2 = time.perf_counter()
         ctx.sys = None                                  # the device holds the system now
         pair_points, table_values = ctx.work()
-        Pp, Pq = sy.random_kernels(s, k, 3)
-        dPp, dPq = torch.from_numpy(Pp).cuda(), torch.from_numpy(Pq).cuda()
-        cpu = None if args.no_cpu_baseline else cpu_oracle_sample(s)
-        del s, Pp, Pq
+        rng = np.random.default_rng(3)
+        shape = (k, ctx.nnz) if ctx.sparse else (k, ctx.nc, ctx.nv)
+        dPp = torch.from_numpy(rng.standard_normal(shape)).cuda()
+        dPq = torch.from_numpy(rng.standard_normal(shape)).cuda()
+        cpu = None
+        if not args.no_cpu_baseline and natoms <= args.scaling_cpu_max_atoms:
+            cpu = cpu_oracle_sample(s)
+        nnz = ctx.nnz if ctx.sparse else ctx.nc * ctx.nv
+        del s
         for _ in range(args.warmup):
             ctx.apply(dPp, dPq)
         ctx.profile(True)
@@ -643,23 +661,31 @@ def run_scaling(args):
         flops = sum(v[2] for v in prof.values()) / args.steps
         series.append({
             "atoms": natoms, "cell_ang": rec.cell_ang, "grid": rec.ngrid,
-            "n_chi": ctx.nc, "n_phi": ctx.nv, "pair_points": pair_points, "table_values": table_values,
+            "n_chi": ctx.nc, "n_phi": ctx.nv, "kernel_values": nnz,
+            "kernel_fill": nnz / float(ctx.nc * ctx.nv),
+            "pair_points": pair_points, "table_values": table_values,
             "ms_per_apply": ms, "applies_per_s": k / (ms / 1000.0),
             "work_tflop_per_apply": flops / 1e12, "ns_per_mflop": 1e6 * ms / max(flops / 1e6, 1e-30),
             "stages_ms": {n: round(v[1] / args.steps, 3) for n, v in prof.items() if v[0]},
             "generate_s": t1 - t0, "create_s": t2 - t1, "cpu_baseline": cpu,
             "clocks": {k_: clk.summary()[k_] for k_ in ("sm_mhz", "sm_max_mhz", "reasons")}})
+        print(json.dumps({"partial": series[-1]}), flush=True)
         ctx.close()
         del dPp, dPq
         torch.cuda.empty_cache()
+    atoms = [r["atoms"] for r in series]
     line = {"metric": "operator applies/s and time per unit of work vs atom count", "unit": UNIT,
             "n_gpus": 1, "higher_is_better": True, "impl": "ours", "dtype": "f32", "data": "synthetic",
             "steps": args.steps, "warmup": args.warmup,
             "config": {"workload": "linear-scaling series: 140-atom core + shell at 0.1 atoms/A^3, 4 phi + 9 chi "
-                                   "per atom, 8 A radius, 0.25 A grid, 15 A kernel cutoff, "
+                                   "per atom, 8 A radius, 0.25 A grid, every density matrix truncated at 15 A "
+                                   f"({'dense products' if args.scaling_dense else 'truncated form, block-sparse products'}), "
                                    f"k={k}, mixed precision",
                        "l2": "inputs larger than L2 (function tables of several GB)"},
-            "series": series}
+            "series": series,
+            "exponent_time_vs_atoms": _loglog_slope(atoms, [r["ms_per_apply"] for r in series]),
+            "exponent_work_vs_atoms": _loglog_slope(atoms, [r["work_tflop_per_apply"] for r in series]),
+            "exponent_time_per_work_vs_atoms": _loglog_slope(atoms, [r["ns_per_mflop"] for r in series])}
     print(json.dumps(line), flush=True)
 
 

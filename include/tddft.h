@@ -59,13 +59,15 @@ enum { TDDFT_FXC_NONE = 0, TDDFT_FXC_LDA_PW92 = 1 };
  * Function f covers the grid points ((ox+i) mod n, (oy+j) mod n, (oz+l) mod n) for
  * 0 <= i < ex, 0 <= j < ey, 0 <= l < ez, with box[6f..6f+5] = (ox, oy, oz, ex, ey, ez),
  * 0 <= o < n, 1 <= e <= n. Its values are val[off[f] .. off[f+1]), C order (l fastest), and
- * off[f+1] - off[f] = ex*ey*ez. atom[f] is the owning atom (used for the kernel cutoff). */
+ * off[f+1] - off[f] = ex*ey*ez; with val NULL they are val32 (float32) instead, which halves the
+ * host memory of large systems. atom[f] is the owning atom (used for the kernel cutoff). */
 typedef struct {
     int32_t nfun;
     const int32_t *atom;
     const int32_t *box;
     const int64_t *off;
     const double *val;
+    const float *val32;
 } tddft_funcs;
 
 /* One system: the ground-state inputs the linear-response calculation takes as given

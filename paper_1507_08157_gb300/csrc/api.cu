@@ -165,7 +165,21 @@ __global__ void denominators_kernel(const double *Ac, int rc, const double *Av, 
     }
 }
 
+// float32 -> float16 (round to nearest even), bit patterns out
+__global__ void f16_kernel(const float *__restrict__ in, unsigned short *__restrict__ out, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = __half_as_ushort(__float2half_rn(in[i]));
+}
+
 }  // namespace roots
+
+namespace {
+void to_f16(cudaStream_t st, const float *in, unsigned short *out, long long n) {
+    if (n <= 0) return;
+    roots::f16_kernel<<<(int)std::min<long long>((n + 255) / 256, 8 * 1216), 256, 0, st>>>(in, out, n);
+    check_launch("f16_kernel");
+}
+}  // namespace
 
 namespace {
 
@@ -411,11 +425,19 @@ tddft_status guarded(tddft_ctx *c, F &&f) {
 }
 
 // ---- grid tables -------------------------------------------------------------------------------
+// value i of a function set's tables (float64, or float32 when val is null)
+struct FuncVals {
+    const double *v64;
+    const float *v32;
+    double operator[](long long i) const { return v64 ? v64[i] : (double)v32[i]; }
+};
+
 template <typename T>
 void build_tiles(const tddft_funcs &fs, int n, int nt, Mem &mem, TileSet<T> &out,
                  std::vector<int> &cnt) {
     const int ntiles = nt * nt * nt;
     const int nf = fs.nfun;
+    const FuncVals fv{fs.val, fs.val32};
     std::vector<std::vector<int>> ftiles(nf);
 #pragma omp parallel
     {
@@ -425,14 +447,14 @@ void build_tiles(const tddft_funcs &fs, int n, int nt, Mem &mem, TileSet<T> &out
         for (int f = 0; f < nf; ++f) {
             ++stamp;
             const int *b = fs.box + 6 * f;
-            const double *v = fs.val + fs.off[f];
+            const long long v = fs.off[f];
             for (int i = 0; i < b[3]; ++i) {
                 const int gx = (b[0] + i) % n;
                 for (int j = 0; j < b[4]; ++j) {
                     const int gy = (b[1] + j) % n;
-                    const double *row = v + ((long long)i * b[4] + j) * b[5];
+                    const long long row = v + ((long long)i * b[4] + j) * b[5];
                     for (int l = 0; l < b[5]; ++l) {
-                        if (row[l] == 0.0) continue;
+                        if (fv[row + l] == 0.0) continue;
                         const int gz = (b[2] + l) % n;
                         const int t = ((gx / TILE) * nt + gy / TILE) * nt + gz / TILE;
                         if (mark[t] != stamp) {
@@ -473,18 +495,19 @@ void build_tiles(const tddft_funcs &fs, int n, int nt, Mem &mem, TileSet<T> &out
         for (int f = 0; f < nf; ++f) {
             for (size_t a = 0; a < ftiles[f].size(); ++a) slot_of[ftiles[f][a]] = fslot[f][a];
             const int *b = fs.box + 6 * f;
-            const double *v = fs.val + fs.off[f];
+            const long long v = fs.off[f];
             for (int i = 0; i < b[3]; ++i) {
                 const int gx = (b[0] + i) % n;
                 for (int j = 0; j < b[4]; ++j) {
                     const int gy = (b[1] + j) % n;
-                    const double *row = v + ((long long)i * b[4] + j) * b[5];
+                    const long long row = v + ((long long)i * b[4] + j) * b[5];
                     for (int l = 0; l < b[5]; ++l) {
-                        if (row[l] == 0.0) continue;
+                        const double x = fv[row + l];
+                        if (x == 0.0) continue;
                         const int gz = (b[2] + l) % n;
                         const int t = ((gx / TILE) * nt + gy / TILE) * nt + gz / TILE;
                         const int lp = ((gx % TILE) * TILE + gy % TILE) * TILE + gz % TILE;
-                        val[(size_t)slot_of[t] * TILE_PTS + lp] = T(row[l]);
+                        val[(size_t)slot_of[t] * TILE_PTS + lp] = T(x);
                     }
                 }
             }
@@ -512,7 +535,7 @@ void build_tiles(const tddft_funcs &fs, int n, int nt, Mem &mem, TileSet<T> &out
 }
 
 void validate_funcs(const tddft_funcs &fs, int n, int natoms, const char *name) {
-    if (fs.nfun <= 0 || !fs.atom || !fs.box || !fs.off || !fs.val)
+    if (fs.nfun <= 0 || !fs.atom || !fs.box || !fs.off || (!fs.val && !fs.val32))
         throw InvalidArg{std::string(name) + ": empty or null function set"};
     if (fs.off[0] != 0) throw InvalidArg{std::string(name) + ": off[0] must be 0"};
     for (int f = 0; f < fs.nfun; ++f) {
@@ -1018,28 +1041,15 @@ void build_impl(tddft_ctx *c, const tddft_system *s, const tddft_sparse_system *
                 }
                 const int NPi = std::max(16, (maxnp + 15) / 16 * 16);
                 if (integrals_tc_group(NPi, 1, maxnc) >= 1) {
-                    fetch_tables();
-                    std::vector<unsigned short> fm(cval.size());
-#pragma omp parallel for schedule(static)
-                    for (long long i = 0; i < (long long)cval.size(); ++i)
-                        fm[i] = __half_as_ushort(__float2half_rn(cval[i]));
-                    I->chi_fm16 = I->mem.template alloc<unsigned short>(std::max<size_t>(1, fm.size()));
-                    check(cudaMemcpy(I->chi_fm16, fm.data(), fm.size() * sizeof(unsigned short),
-                                     cudaMemcpyHostToDevice),
-                          "upload f16 chi");
+                    // function-major f16 copies of both tables, rounded on the device (the f16 phi
+                    // rows are the integrals' B operand, TMA-loaded and scaled by V in place)
+                    const long long nch = (long long)coff[ntl] * TILE_PTS, nph = (long long)poff[ntl] * TILE_PTS;
+                    I->chi_fm16 = I->mem.template alloc<unsigned short>(std::max<long long>(1, nch));
+                    to_f16(st, reinterpret_cast<const float *>(I->chi.val), I->chi_fm16, nch);
                     I->nslots_chi = coff[ntl];
-                    {
-                        // f16 phi tables for the integrals' B operand (TMA-loaded, scaled by V in place)
-                        std::vector<unsigned short> ph(pv.size());
-#pragma omp parallel for schedule(static)
-                        for (long long i = 0; i < (long long)pv.size(); ++i)
-                            ph[i] = __half_as_ushort(__float2half_rn(pv[i]));
-                        I->phi_fm16 = I->mem.template alloc<unsigned short>(std::max<size_t>(1, ph.size()));
-                        check(cudaMemcpy(I->phi_fm16, ph.data(), ph.size() * sizeof(unsigned short),
-                                         cudaMemcpyHostToDevice),
-                              "upload f16 phi");
-                        I->nslots_phi = poff[ntl];
-                    }
+                    I->phi_fm16 = I->mem.template alloc<unsigned short>(std::max<long long>(1, nph));
+                    to_f16(st, reinterpret_cast<const float *>(I->phi.val), I->phi_fm16, nph);
+                    I->nslots_phi = poff[ntl];
                     std::vector<VTile> all;
                     for (int q = 0; q < 3; ++q) {
                         I->int_count[q] = (int)by[q].size();

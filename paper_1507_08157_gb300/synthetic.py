@@ -58,6 +58,8 @@ class Recipe:
     cluster_ang: float = 0.0   # > 0: atoms only inside a centred cube of this side (vacuum around)
     sphere_density: float = 0.0   # > 0: atoms fill a centred sphere at this density (A^-3) ...
     core_atoms: int = 0           # ... the first core_atoms its inner sphere, the rest the shell
+    fast: bool = False            # large systems: float32 tables, separable overlap sums, one
+                                  # eigendecomposition per Hamiltonian, atomic n0 (see generate)
 
 
 # The smallest workload: 8 atoms, 16 A cell, 48^3 grid, 4 phi + 4 chi (s, p) per atom, 7 A radius,
@@ -79,8 +81,8 @@ def scaling_recipe(natoms: int, seed: int = 5) -> Recipe:
     r_cluster = (3.0 * natoms / (4.0 * math.pi * density)) ** (1.0 / 3.0)
     n = smooth_grid(int(math.ceil((2.0 * r_cluster + 2.0 * R + 10.0) / h)))
     return Recipe(natoms=natoms, cell_ang=n * h, ngrid=n, nphi=4, nchi=9, radius_ang=R,
-                  kernel_cutoff_ang=15.0, seed=seed, sphere_density=density,
-                  core_atoms=min(140, natoms))
+                  kernel_cutoff_ang=15.0, density_kernel_cutoff_ang=15.0, seed=seed, sphere_density=density,
+                  core_atoms=min(140, natoms), fast=True)
 
 
 @dataclasses.dataclass
@@ -220,7 +222,9 @@ def box_half_width(radius, h):
     return int(math.ceil(radius / h)) + 1
 
 
-def _tabulate(rng_w, pos, nper, cell, n, radius, width):
+def _tabulate(rng_w, pos, nper, cell, n, radius, width, dtype=np.float64, params=None):
+    """Tables of the functions of every atom; `params` (a dict), when given, receives the widths,
+    the normalisation factors, the box centres (grid index of each atom) and the half width m."""
     h = cell / n
     m = box_half_width(radius, h)
     e = 2 * m + 1
@@ -231,8 +235,9 @@ def _tabulate(rng_w, pos, nper, cell, n, radius, width):
     atom = np.repeat(np.arange(natoms, dtype=np.int32), nper)
     box = np.zeros((nfun, 6), dtype=np.int32)
     off = np.arange(nfun + 1, dtype=np.int64) * (e ** 3)
-    val = np.empty(int(off[-1]), dtype=np.float64)
+    val = np.empty(int(off[-1]), dtype=dtype)
     widths = rng_w.uniform(width[0], width[1], size=nfun)   # one draw per function, in order
+    norms = np.zeros(nfun)
     dV = h ** 3
     t = np.arange(-m, m + 1, dtype=np.float64)
 
@@ -247,14 +252,120 @@ def _tabulate(rng_w, pos, nper, cell, n, radius, width):
             w = widths[f]
             g = np.exp(-r2 / (w * w)) * _angular(kf, dx, dy, dz, w)
             g[~inside] = 0.0
-            g /= math.sqrt(dV * np.sum(g * g))
+            norms[f] = 1.0 / math.sqrt(dV * np.sum(g * g))
+            g *= norms[f]
             val[off[f]:off[f + 1]] = g.ravel()
             box[f, :3] = np.mod(c - m, n)
             box[f, 3:] = e
 
     with concurrent.futures.ThreadPoolExecutor(_workers()) as ex:
         list(ex.map(one_atom, range(natoms)))
+    if params is not None:
+        params.update(widths=widths, norms=norms, centre=np.rint(pos / h).astype(np.int64), m=m, h=h, n=n)
     return FunctionSet(atom=atom, box=box, off=off, val=val)
+
+
+# ---- sums that factor along the axes (large systems) ------------------------------------------
+# A tabulated function is N_f exp(-|r - R_a|^2 / w_f^2) A_f(r - R_a) inside the radius R and zero
+# beyond, with A_f a polynomial of degree <= 2 (_angular). Beyond R the Gaussian is below
+# exp(-R^2 / w^2) <= exp(-44) of its peak for the widths used, so the sum over the grid of a
+# product of two tables equals, to double rounding, the sum of the uncut functions over the
+# common points of their boxes, and that factors into one-dimensional sums along x, y and z.
+
+_SQ3 = math.sqrt(3.0)
+_MONO = {   # kind -> [(coefficient times w^degree, (px, py, pz))], the monomials of _angular
+    0: [(1.0, (0, 0, 0))],
+    1: [(1.0, (1, 0, 0))], 2: [(1.0, (0, 1, 0))], 3: [(1.0, (0, 0, 1))],
+    4: [(1.0, (1, 1, 0))], 5: [(1.0, (0, 1, 1))], 6: [(1.0, (1, 0, 1))],
+    7: [(0.5, (2, 0, 0)), (-0.5, (0, 2, 0))],
+    8: [(1.0 / _SQ3, (0, 0, 2)), (-0.5 / _SQ3, (2, 0, 0)), (-0.5 / _SQ3, (0, 2, 0))],
+}
+
+
+def _axis_factors(pos, nper, params):
+    """U[atom, axis, t, f * 3 + p] = exp(-d^2 / w_f^2) d^p along one axis of the atom's box
+    (d the displacement of box point t from the atom), and the monomial tables of the set."""
+    natoms = pos.shape[0]
+    m, h = params["m"], params["h"]
+    T = 2 * m + 1
+    t = np.arange(-m, m + 1, dtype=np.float64)
+    w = params["widths"].reshape(natoms, nper)
+    U = np.empty((natoms, 3, T, nper * 3))
+    for ax in range(3):
+        d = (params["centre"][:, ax][:, None] + t[None, :]) * h - pos[:, ax][:, None]      # [atoms, T]
+        e = np.exp(-(d[:, :, None] ** 2) / (w[:, None, :] ** 2))                            # [atoms, T, f]
+        for p in range(3):
+            U[:, ax, :, p::3] = e * (d[:, :, None] ** p)
+    coef = np.zeros((nper, 3))
+    expo = np.zeros((nper, 3, 3), dtype=np.int64)
+    for kf in range(nper):
+        for q, (c, ex) in enumerate(_MONO[kf]):
+            coef[kf, q] = c
+            expo[kf, q] = ex
+    return U, coef, expo
+
+
+def _separable_overlaps(fs, nper, pos, cell, n, dV, rmax, params, chunk=2048):
+    """S_ab = dV sum_r f_a(r) f_b(r) for atom pairs within rmax, from the factored axis sums
+    (needs boxes no wider than half the cell, so that two boxes meet in one run per axis)."""
+    natoms = pos.shape[0]
+    m = params["m"]
+    T = 2 * m + 1
+    if 2 * T > n:
+        raise ValueError("separable overlaps need boxes no wider than half the cell")
+    U, coef, expo = _axis_factors(pos, nper, params)
+    w = params["widths"].reshape(natoms, nper)
+    nrm = params["norms"].reshape(natoms, nper)
+    deg = expo[:, 0, :].sum(axis=1)     # degree of each kind (every monomial of a kind has it)
+    N = natoms * nper
+    S = np.zeros((N, N))
+    pairs = np.array([(i, j) for (i, j, _) in _atom_pairs_within(pos, cell, rmax)], dtype=np.int64)
+    cen = params["centre"]
+    fi = np.arange(nper)
+    for c0 in range(0, len(pairs), chunk):
+        pr = pairs[c0:c0 + chunk]
+        a, b = pr[:, 0], pr[:, 1]
+        P = len(pr)
+        G = []
+        for ax in range(3):
+            s_ = (cen[a, ax] - cen[b, ax]) % n
+            s_ = np.where(s_ > n // 2, s_ - n, s_)                     # b index = a index + s
+            idx = np.arange(T)[None, :] + s_[:, None]                  # [P, T]
+            ok = (idx >= 0) & (idx < T)
+            Ub = U[b[:, None], ax, np.clip(idx, 0, T - 1)] * ok[:, :, None]   # [P, T, nper*3]
+            Ua = U[a, ax]                                               # [P, T, nper*3]
+            G.append(np.matmul(Ua.transpose(0, 2, 1), Ub).reshape(P, nper, 3, nper, 3))
+        blk = np.zeros((P, nper, nper))
+        for q in range(3):
+            for r in range(3):
+                cq = coef[:, q][None, :, None] * coef[:, r][None, None, :]
+                if not np.any(cq):
+                    continue
+                term = cq * np.ones((P, 1, 1))
+                for ax in range(3):
+                    term = term * G[ax][:, fi[:, None], expo[:, q, ax][:, None], fi[None, :], expo[:, r, ax][None, :]]
+                blk += term
+        scale = (dV * nrm[a][:, :, None] * nrm[b][:, None, :] /
+                 (w[a][:, :, None] ** deg[None, :, None] * w[b][:, None, :] ** deg[None, None, :]))
+        blk *= scale
+        for (i, j), B in zip(pr, blk):
+            S[i * nper:(i + 1) * nper, j * nper:(j + 1) * nper] = B
+            if i != j:
+                S[j * nper:(j + 1) * nper, i * nper:(i + 1) * nper] = B.T
+    return 0.5 * (S + S.T)
+
+
+def _atomic_density(fs, nper, K, n):
+    """sum over atoms I of sum_{a, b on I} f_a(r) K_ab f_b(r) on the full grid (the on-site
+    blocks of K only: a superposition of atomic densities)."""
+    out = np.zeros((n, n, n))
+    for ia in range(fs.nfun // nper):
+        A, o, e = _atom_block(fs, ia, nper)
+        Kaa = K[ia * nper:(ia + 1) * nper, ia * nper:(ia + 1) * nper]
+        Af = A.reshape(nper, -1).astype(np.float64)
+        contrib = np.einsum("ar,ar->r", Kaa @ Af, Af).reshape(e, e, e)
+        _add_parts(out, [(int(o[0]), int(o[1]), int(o[2]), contrib)], n)
+    return out
 
 
 def _axis_overlaps(oa, ob, e, n):
@@ -497,11 +608,19 @@ def generate(recipe: Recipe) -> System:
         pos = _rsa_positions(r_pos, recipe.natoms, cell, recipe.min_sep_ang * BOHR_PER_ANG,
                              recipe.cluster_ang * BOHR_PER_ANG)
     width = (recipe.width_ang[0] * BOHR_PER_ANG, recipe.width_ang[1] * BOHR_PER_ANG)
-    phi = _tabulate(r_wphi, pos, recipe.nphi, cell, n, R, width)
-    chi = _tabulate(r_wchi, pos, recipe.nchi, cell, n, R, width)
+    dtype = np.float32 if recipe.fast else np.float64
+    par_phi, par_chi = {}, {}
+    phi = _tabulate(r_wphi, pos, recipe.nphi, cell, n, R, width, dtype, par_phi)
+    chi = _tabulate(r_wchi, pos, recipe.nchi, cell, n, R, width, dtype, par_chi)
     dV = h ** 3
-    S_phi = _overlap_matrix(phi, recipe.nphi, pos, cell, n, dV, 2.0 * R)
-    S_chi = _overlap_matrix(chi, recipe.nchi, pos, cell, n, dV, 2.0 * R)
+    if recipe.fast:
+        # large systems: the overlap sums factor along the axes (exact to double rounding, see
+        # _separable_overlaps); the tables are kept in float32
+        S_phi = _separable_overlaps(phi, recipe.nphi, pos, cell, n, dV, 2.0 * R, par_phi)
+        S_chi = _separable_overlaps(chi, recipe.nchi, pos, cell, n, dV, 2.0 * R, par_chi)
+    else:
+        S_phi = _overlap_matrix(phi, recipe.nphi, pos, cell, n, dV, 2.0 * R)
+        S_chi = _overlap_matrix(chi, recipe.nchi, pos, cell, n, dV, 2.0 * R)
     decay = recipe.h_decay_ang * BOHR_PER_ANG
     H_phi = _random_hamiltonian(r_hphi, pos, cell, recipe.nphi, 2.0 * R, recipe.h_sigma, decay)
     H_chi = _random_hamiltonian(r_hchi, pos, cell, recipe.nchi, 2.0 * R, recipe.h_sigma, decay)
@@ -510,11 +629,22 @@ def generate(recipe: Recipe) -> System:
     n_occ = n_phi // 2
     n_cond = n_chi // 2
     eps_v, P_v = _spectral_projector(H_phi, S_phi, n_occ)
-    eps_c = scipy.linalg.eigh(H_chi, S_chi, eigvals_only=True)
-    shift = recipe.gap_ev * HA_PER_EV - (eps_c[0] - eps_v[n_occ - 1])
-    H_chi = H_chi + shift * S_chi
-    _, P_c = _spectral_projector(H_chi, S_chi, n_cond)
-    n0 = 2.0 * _density_on_grid(phi, recipe.nphi, P_v, pos, cell, n, 2.0 * R)
+    if recipe.fast:
+        # one decomposition: shifting H^chi by s S^chi shifts every eigenvalue by s and keeps the
+        # eigenvectors, so the projector onto the lowest n_cond states is that of H^chi itself
+        eps_c, C = scipy.linalg.eigh(H_chi, S_chi)
+        shift = recipe.gap_ev * HA_PER_EV - (eps_c[0] - eps_v[n_occ - 1])
+        H_chi = H_chi + shift * S_chi
+        P_c = C[:, :n_cond] @ C[:, :n_cond].T
+        del C
+        # ground-state density: superposition of the atoms' on-site valence densities
+        n0 = 2.0 * _atomic_density(phi, recipe.nphi, P_v, n)
+    else:
+        eps_c = scipy.linalg.eigh(H_chi, S_chi, eigvals_only=True)
+        shift = recipe.gap_ev * HA_PER_EV - (eps_c[0] - eps_v[n_occ - 1])
+        H_chi = H_chi + shift * S_chi
+        _, P_c = _spectral_projector(H_chi, S_chi, n_cond)
+        n0 = 2.0 * _density_on_grid(phi, recipe.nphi, P_v, pos, cell, n, 2.0 * R)
     return System(recipe=recipe, cell=cell, n=n, pos=pos, phi=phi, chi=chi,
                   S_phi=S_phi, S_chi=S_chi, H_phi=H_phi, H_chi=H_chi, P_v=P_v, P_c=P_c,
                   n0=n0, kernel_cutoff=recipe.kernel_cutoff_ang * BOHR_PER_ANG,

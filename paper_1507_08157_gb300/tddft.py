@@ -32,7 +32,7 @@ c_int64_p = ctypes.POINTER(ctypes.c_int64)
 
 class _Funcs(ctypes.Structure):
     _fields_ = [("nfun", ctypes.c_int32), ("atom", c_int32_p), ("box", c_int32_p),
-                ("off", c_int64_p), ("val", c_double_p)]
+                ("off", c_int64_p), ("val", c_double_p), ("val32", ctypes.POINTER(ctypes.c_float))]
 
 
 class _System(ctypes.Structure):
@@ -238,7 +238,10 @@ def _marshal(sys: System, fxc="lda", matrices=True):
         f.atom = arr(fs.atom, np.int32)
         f.box = arr(fs.box, np.int32)
         f.off = arr(fs.off, np.int64)
-        f.val = arr(fs.val, np.float64)
+        if fs.val.dtype == np.float32:
+            f.val32 = arr(fs.val, np.float32)     # float32 tables pass as they are
+        else:
+            f.val = arr(fs.val, np.float64)
         return f
 
     s = _System()

@@ -1,35 +1,31 @@
-"""The first size of the linear-scaling series, in the launch configuration `bench.py --scaling`
+"""The first member of the linear-scaling series in the launch configuration `bench.py --scaling`
 times: 500 atoms (a 140-atom core and a shell at 0.1 atoms per A^3, 48 A cell, 192^3 grid, 4 phi +
-9 chi per atom, 8 A radius, 15 A kernel cutoff), k = 4 states, mixed precision. At this atom
-density a grid tile holds more functions than the tensor-core density kernel takes (256 phi), so
-the density runs on the float32 CUDA-core kernel; the integrals cut such tiles into tensor-core
-units (float16 operands). Checked against the FP64 oracle:
+9 chi per atom, 8 A radius, every density matrix truncated at 15 A), k = 4 states, mixed precision,
+the truncated form of Sec. IV (tddft_create_sparse: cluster-blocked matrices, block-sparse
+products on the tensor cores). At this atom density a grid tile holds more functions than the
+tensor-core density kernel takes (256 phi), so the density runs on the float32 CUDA-core kernel;
+the integrals cut such tiles into tensor-core units (float16 operands). Checked against the FP64
+oracle (oracle/sparse.py for the truncated products, oracle/grid.py point by point):
 
-* response density at 160 sampled grid points (oracle/grid.py: density_at);
-* potential integrals at 160 uniformly drawn (chi, phi) pairs over a smooth potential
-  (integrals_at);
-* the Kohn-Sham difference part of the operator (mode d_only) on every entry.
+* the Kohn-Sham difference part (mode d_only: T(M_c P) - T(P M_v)) on every entry of the
+  kernel pattern;
+* the response density at 160 sampled grid points (density_at);
+* the potential integrals at 160 (chi, phi) pairs of the pattern over a smooth potential
+  (integrals_at), cut to the pattern.
 
-Tolerances, relative to the largest entry of each state: 1e-4 for the float32 density (sums
-over thousands of functions per point) and the N_chi = 4500-long split-TF32 products; 2e-3 for
-the integrals on float16 tensor-core operands (unit roundoff 4.9e-4, as in the small-system
-operator tests).
-
-Generating the system takes minutes of host time (tens of GB of tables); the module runs only
-with TDDFT_SCALING_TESTS=1.
+Tolerances, relative to the largest entry of each state: 1e-4 for the float32 density (sums over
+thousands of functions per point) and the split-TF32 block products with K up to N_chi = 4500;
+2e-3 for the integrals on float16 tensor-core operands (as in the small-system tests).
 """
-import os
-
 import numpy as np
 import pytest
 
 from oracle import grid as ogrid
 from oracle import operator as ooperator
+from oracle import sparse as osp
 from paper_1507_08157_gb300 import synthetic as sy
 
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.skipif(os.environ.get("TDDFT_SCALING_TESTS") != "1",
-                                 reason="set TDDFT_SCALING_TESTS=1 (minutes of host time)")]
+pytestmark = pytest.mark.gpu
 
 K = 4
 TOL = 1e-4
@@ -55,13 +51,19 @@ def shell500():
 
 @pytest.fixture(scope="module")
 def ctx(tddft, shell500):
-    return tddft.Context(shell500[0], precision="mixed", precond="none")
+    return tddft.Context(shell500[0], precision="mixed", precond="none", sparse=True)
+
+
+def _kernels(ctx, seed):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((K, ctx.nnz))
 
 
 def test_density_sampled(ctx, shell500):
     s, chi, phi = shell500
-    _, P = sy.random_kernels(s, K, 51)
-    rho = ctx.response_density(P)
+    x = _kernels(ctx, 51)
+    rho = ctx.response_density(x)
+    P = ctx.from_pattern(x)
     rng = np.random.default_rng(52)
     centre = s.n // 2
     for q in range(K):
@@ -79,10 +81,12 @@ def test_integrals_sampled(ctx, shell500):
     X, Y, Z = np.meshgrid(x, x, x, indexing="ij")
     V = np.stack([np.cos(X + 0.3 * q) + 0.5 * np.sin(2.0 * Y - 0.1 * q) + 0.25 * np.cos(3.0 * Z + X)
                   for q in range(K)])
-    out = ctx.potential_integrals(V)
+    out = ctx.from_pattern(ctx.potential_integrals(V))
     rng = np.random.default_rng(53)
+    rows, cols = ctx.kp_rows, ctx.kp_cols
     for q in range(K):
-        pairs = [(int(rng.integers(s.chi.nfun)), int(rng.integers(s.phi.nfun))) for _ in range(40)]
+        pick = rng.integers(0, rows.size, size=40)
+        pairs = [(int(rows[i]), int(cols[i])) for i in pick]
         ref = ogrid.integrals_at(chi, phi, V[q:q + 1], s.dV, pairs)[0]
         got = np.array([out[q][a, b] for a, b in pairs])
         assert np.max(np.abs(got - ref)) <= TOL_F16 * np.max(np.abs(out[q])), q
@@ -90,11 +94,13 @@ def test_integrals_sampled(ctx, shell500):
 
 def test_ks_difference_every_entry(tddft, shell500):
     s = shell500[0]
-    ctx_d = tddft.Context(s, precision="mixed", mode="d_only", precond="none")
-    Pp, Pq = sy.random_kernels(s, 2, 54)
-    fp, fq = ctx_d.apply(Pp, Pq)
-    rp, rq = ooperator.Operator(s).apply(Pp, Pq, mode=ooperator.D_ONLY)
+    ctx_d = tddft.Context(s, precision="mixed", mode="d_only", precond="none", sparse=True)
+    op = osp.TruncatedOperator(s)
+    xp, xq = _kernels(ctx_d, 54)[:2], _kernels(ctx_d, 55)[:2]
+    fp, fq = ctx_d.apply(xp, xq)
+    rp, rq = op.apply(ctx_d.from_pattern(xp), ctx_d.from_pattern(xq), mode=ooperator.D_ONLY)
     for f, ref in ((fp, rp), (fq, rq)):
         for q in range(f.shape[0]):
-            assert np.max(np.abs(f[q] - ref[q])) <= TOL * np.max(np.abs(ref[q])), q
+            got = ctx_d.from_pattern(f[q:q + 1])[0]
+            assert np.max(np.abs(got - ref[q])) <= TOL * np.max(np.abs(ref[q])), q
     ctx_d.close()
