@@ -51,6 +51,9 @@ def parse():
                     help="preconditioner of the timed PCG steps (exact: Eq. precond solved in its "
                          "eigenbases; iter: the paper's inner CG to 1e-4)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default tile shapes of the grid kernels")
+    ap.add_argument("--no-iter-line", action="store_true",
+                    help="skip the extra timing of PCG steps with the paper's inner-CG preconditioner")
     ap.add_argument("--learned-train-atoms", type=int, default=16,
                     help="atoms of the two training systems of the time-to-k comparison")
     ap.add_argument("--learned-eval-atoms", type=int, default=24,
@@ -381,6 +384,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     ctx = tddft.Context(s, precision=args.precision, stream=stream.cuda_stream, tol=1e-5, precond=args.precond)
     k = args.k
+    # tile shapes of the grid kernels picked by the library's autotuner (outside the timed region)
+    tuning = ctx.autotune(k) if args.precision == "mixed" and not args.no_autotune else None
     st = ctx.state(sy.initial_guess(s, k, 0))
     for _ in range(args.warmup):
         st.step()
@@ -492,6 +497,35 @@ def run_ours(args):
     stages = {n: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / max(ms, 1e-9), 4)}
               for n, v in prof.items() if v[0]}
 
+    # the same PCG steps with the paper's preconditioner (inner CG on Eq. precond to 1e-4), when
+    # the timed steps used another one: both are reported
+    iter_line = None
+    if rank == 0 and not args.no_iter_line and args.precond != "iter":
+        ctx_i = tddft.Context(s, precision=args.precision, stream=stream.cuda_stream, tol=1e-5, precond="iter")
+        if tuning is not None:
+            ctx_i.autotune(k)
+        st_i = ctx_i.state(sy.initial_guess(s, k, 0))
+        for _ in range(args.warmup):
+            st_i.step()
+        n_i = max(3, args.steps // 2)
+        extra_i = sum(1 for i in range(args.warmup, args.warmup + n_i) if reapply > 0 and (i + 1) % reapply == 0)
+        ctx_i.profile(True)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(n_i):
+            st_i.step()
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms_i = f0.elapsed_time(f1)
+        prof_i = ctx_i.profile_read()
+        iter_line = {"precond": "iter (inner CG on Eq. precond to 1e-4, the paper's)", "steps": n_i,
+                     "ms_per_step": ms_i / n_i, "applies_per_s": k * (n_i + extra_i) / (ms_i / 1000.0),
+                     "inner_cg_iterations": st_i.stats()[2],
+                     "stages_ms_per_step": {n_: round(v[1] / n_i, 3) for n_, v in prof_i.items() if v[0]}}
+        st_i.close()
+        ctx_i.close()
+
     # time to k states at 1e-5 Ha, learned vs plain PCG (FP64): the model is trained on rows from
     # plain-PCG runs on two systems of the small workload's recipe and density, then both solvers
     # start from the same vectors on an unseen, larger system
@@ -513,7 +547,7 @@ def run_ours(args):
                 "e2e": e2e, "apply_only": {"value": apply_only, "unit": UNIT},
                 "roofline": roof, "stages": stages, "gpu_launches": int(gpu_launches),
                 "clocks": {k_: clock[k_] for k_ in ("sm_mhz", "sm_max_mhz", "reasons")},
-                "time_to_k": time_to_k,
+                "time_to_k": time_to_k, "precond_iter": iter_line, "autotune": tuning,
                 "omega_last": [float(x) for x in om], "resid_last": [float(x) for x in res]}
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_oracle_sample(s)
@@ -635,6 +669,7 @@ def run_scaling(args):
         t2 = time.perf_counter()
         ctx.sys = None                                  # the device holds the system now
         pair_points, table_values = ctx.work()
+        tuning = None if args.no_autotune else ctx.autotune(k)
         rng = np.random.default_rng(3)
         shape = (k, ctx.nnz) if ctx.sparse else (k, ctx.nc, ctx.nv)
         dPp = torch.from_numpy(rng.standard_normal(shape)).cuda()
@@ -668,6 +703,8 @@ def run_scaling(args):
             "work_tflop_per_apply": flops / 1e12, "ns_per_mflop": 1e6 * ms / max(flops / 1e6, 1e-30),
             "stages_ms": {n: round(v[1] / args.steps, 3) for n, v in prof.items() if v[0]},
             "generate_s": t1 - t0, "create_s": t2 - t1, "cpu_baseline": cpu,
+            "autotune": [{k_: r[k_] for k_ in ("stage", "kind", "chi_chunk", "phi_chunk", "ms", "chosen")}
+                         for r in tuning] if tuning else None,
             "clocks": {k_: clk.summary()[k_] for k_ in ("sm_mhz", "sm_max_mhz", "reasons")}})
         print(json.dumps({"partial": series[-1]}), flush=True)
         ctx.close()

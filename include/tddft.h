@@ -249,6 +249,28 @@ tddft_status tddft_response_potential(tddft_ctx *ctx, int32_t k, const double *r
 tddft_status tddft_potential_integrals(tddft_ctx *ctx, int32_t k, const double *V, double *out);
 tddft_status tddft_fxc(tddft_ctx *ctx, double *fxc);
 
+/* Autotuner of the tensor-core grid kernels' tile shapes (no counterpart in the paper). For a
+ * TDDFT_MIXED context it times, on k trial states of the context's own system (deterministic
+ * pseudo-random P and V), every candidate cut of the grid work into tensor-core units:
+ *   response_density: the per-tile kernels (kind 0, when every tile fits them) and units of at
+ *     most chi_chunk x phi_chunk functions of a tile (kind 1; chi 128..320 in steps of 64, phi 64
+ *     or 128);
+ *   potential_integrals: units of at most chi_chunk (128, 256, 384) x phi_chunk (32, 64, 128).
+ * Each candidate runs once to warm up and three times timed with CUDA events on the context's
+ * stream (ms = the mean). The fastest of each stage is installed and kept by the context for all
+ * later calls (chosen = 1). out receives up to cap entries, count the number of candidates.
+ * INVALID for k outside 1..32 or a context without the tensor-core grid kernels. */
+typedef struct {
+    char stage[32];
+    int32_t kind;        /* 0: per-tile kernels, 1: units */
+    int32_t chi_chunk;   /* largest chi count of a unit (0 for kind 0) */
+    int32_t phi_chunk;   /* largest phi count of a unit */
+    int32_t chosen;      /* 1 for the candidate installed */
+    double ms;           /* mean time of one call for k states */
+} tddft_tuning_entry;
+
+tddft_status tddft_autotune(tddft_ctx *ctx, int32_t k, tddft_tuning_entry *out, int32_t cap, int32_t *count);
+
 /* Check of the bounded-wait path (no counterpart in the paper; it tests the library's failure
  * detection without faulting or hanging the GPU): launches one small kernel on the context's
  * stream that waits, with the context's spin_limit_cycles, on a shared-memory barrier that
@@ -469,6 +491,9 @@ tddft_status tddft_work(const tddft_ctx *ctx, double *pair_points, double *table
  *   TDDFT_NO_REDUCED_PRECOND=1     the inner CG of the iterative preconditioner on the full
  *                                  N_chi x N_phi space instead of the conduction x valence
  *                                  subspace
+ *   TDDFT_NO_DENSITY_UNITS=1       the CUDA-core density on systems whose tiles exceed the
+ *                                  per-tile tensor-core kernels, instead of the density units
+ *   TDDFT_DENSITY_UNITS=1          the density units even where the per-tile kernels fit
  *   TDDFT_INTEGRALS_CHUNK=nc,np    largest chi / phi slot counts of one tensor-core integrals
  *                                  unit (multiples of 128 up to 384, and of 16 up to 128;
  *                                  default 384,128); smaller values cut tiles that would fit,

@@ -171,6 +171,18 @@ __global__ void f16_kernel(const float *__restrict__ in, unsigned short *__restr
         out[i] = __half_as_ushort(__float2half_rn(in[i]));
 }
 
+// deterministic pseudo-random values in [-1, 1) (splitmix64 of the index and a seed), for the
+// autotuner's trial inputs
+__global__ void fill_random_kernel(float *__restrict__ x, long long n, unsigned long long seed) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        unsigned long long z = seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(i + 1);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        x[i] = (float)((double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0);
+    }
+}
+
 }  // namespace roots
 
 namespace {
@@ -237,6 +249,17 @@ struct Impl {
     unsigned short *chi_fm16 = nullptr;   // function-major f16 chi tables [slot][512]
     unsigned short *phi_fm16 = nullptr;   // function-major f16 phi tables [slot][512]
     unsigned short *phi_pm = nullptr;     // point-major f16 phi tables [tile][512][NPmax], zero padded
+    // dense tiles: density units with chunked point-major f16 tables ([chunk][512][64] chi,
+    // [chunk][512][32] phi)
+    bool dens_units = false;              // the density runs on units (selected)
+    bool units_ok = false;                // chunked tables built (every tile's phi in whole quads)
+    unsigned short *chi_pmc = nullptr, *phi_pmc = nullptr;
+    long long nchunks_chi = 0;
+    DUnit *dunits = nullptr;
+    int ndunits = 0;
+    int dens_cut[2] = {320, 128}, int_cut[2] = {384, 128};   // unit cuts in use (chi, phi)
+    std::vector<int> coff_h, poff_h, cfirst_h, pfirst_h;    // host tile offsets, first chunks
+    Mem umem_dens, umem_int;              // unit lists (replaced when the autotuner recuts)
     int *live_tiles = nullptr;            // tiles with both chi and phi (the persistent density's items)
     int nlive = 0;
     int CK = 0, NPmax = 0, nslots_chi = 0, nslots_phi = 0, maxc = 0;
@@ -328,6 +351,12 @@ void response_density_tc(cudaStream_t st, const GridShape &g, const TileSet<floa
                          const float *P, long long sP, int k, float *rho, unsigned *scratch_bits,
                          float *scale, int *err, bool phi_quads, const unsigned short *phi_pm,
                          const int *live_tiles, int nlive);
+long long build_chunked_pm(cudaStream_t st, Mem &mem, const TileSet<float> &ts, const std::vector<int> &off_h, int W,
+                           unsigned short **out, std::vector<int> &first);
+void response_density_units(cudaStream_t st, const GridShape &g, const TileSet<float> &chi, const TileSet<float> &phi,
+                            const unsigned short *chi_pmc, long long nchunks_chi, const unsigned short *phi_pmc,
+                            const DUnit *units, int nunits, int nphi, const float *P, long long sP, int k, float *rho,
+                            unsigned *scratch_bits, float *scale, int *err);
 int noalloc_max_states();
 void response_density_tc_noalloc(cudaStream_t st, const GridShape &g, const TileSet<float> &chi,
                                  const TileSet<float> &phi, const unsigned short *chi_pm, int CK, int NPmax,
@@ -465,6 +494,22 @@ void build_tiles(const tddft_funcs &fs, int n, int nt, Mem &mem, TileSet<T> &out
                 }
             }
         }
+    }
+    // functions of one atom that share a box are listed together on every tile any of them
+    // touches (a narrow function's table may hold exact zeros where its neighbours do not), so
+    // that an atom's functions stay consecutive in every tile's list
+    for (int f0 = 0; f0 < nf;) {
+        int f1 = f0 + 1;
+        while (f1 < nf && fs.atom[f1] == fs.atom[f0] && std::equal(fs.box + 6 * f1, fs.box + 6 * f1 + 6, fs.box + 6 * f0))
+            ++f1;
+        if (f1 - f0 > 1) {
+            std::vector<int> u;
+            for (int f = f0; f < f1; ++f) u.insert(u.end(), ftiles[f].begin(), ftiles[f].end());
+            std::sort(u.begin(), u.end());
+            u.erase(std::unique(u.begin(), u.end()), u.end());
+            for (int f = f0; f < f1; ++f) ftiles[f] = u;
+        }
+        f0 = f1;
     }
     std::vector<int> off(ntiles + 1, 0);
     for (int f = 0; f < nf; ++f)
@@ -648,6 +693,12 @@ void density(tddft_ctx *c, Impl<T> &I, const T *P, int ns) {
         P = I.dense;
     }
     if constexpr (sizeof(T) == 4) {
+        if (I.dens_units) {
+            response_density_units(c->st, c->grid(), I.chi, I.phi, I.chi_pmc, I.nchunks_chi, I.phi_pmc, I.dunits,
+                                   I.ndunits, c->nv, P, (long long)c->nc * c->nv, ns, I.rho, I.tc_bits, I.tc_scale,
+                                   tc_error_word());
+            return;
+        }
         if (I.grid_tc) {
             response_density_tc(c->st, c->grid(), I.chi, I.phi, I.chi_pm, I.CK, I.NPmax, c->nv, P,
                                 (long long)c->nc * c->nv, ns,
@@ -921,6 +972,90 @@ int projector_basis(cudaStream_t st, Mem &tmp, const double *Sh, const double *P
     return r;
 }
 
+// ---- tensor-core units of the grid kernels (the cuts are what the autotuner varies) -------------
+// chunked point-major f16 tables of both sets for the density units; false unless every tile's
+// phi list is whole aligned atom quads
+bool build_density_chunks(tddft_ctx *c, Impl<float> &I) {
+    if (I.units_ok) return true;
+    const int ntl = I.chi.ntiles;
+    const std::vector<int> &coff = I.coff_h, &poff = I.poff_h;
+    std::vector<int> pids(poff[ntl]);
+    if (!pids.empty())
+        check(cudaMemcpy(pids.data(), I.phi.ids, pids.size() * sizeof(int), cudaMemcpyDeviceToHost), "D2H phi ids");
+    for (int t = 0; t < ntl; ++t) {
+        const int p0 = poff[t], np = poff[t + 1] - p0;
+        if (np % 4) return false;
+        for (int q = 0; q + 3 < np; q += 4)
+            if (!(pids[p0 + q] % 4 == 0 && pids[p0 + q + 1] == pids[p0 + q] + 1 && pids[p0 + q + 2] == pids[p0 + q] + 2 &&
+                  pids[p0 + q + 3] == pids[p0 + q] + 3))
+                return false;
+    }
+    I.nchunks_chi = build_chunked_pm(c->st, I.mem, I.chi, coff, 64, &I.chi_pmc, I.cfirst_h);
+    build_chunked_pm(c->st, I.mem, I.phi, poff, 32, &I.phi_pmc, I.pfirst_h);
+    I.units_ok = true;
+    return true;
+}
+
+// the density's units: chunks of at most cch chi (a multiple of 64, <= 320) and pch phi (a
+// multiple of 32, <= 128) of each tile
+void set_density_units(Impl<float> &I, int cch, int pch) {
+    const int ntl = I.chi.ntiles;
+    const std::vector<int> &coff = I.coff_h, &poff = I.poff_h;
+    std::vector<DUnit> us;
+    for (int t = 0; t < ntl; ++t) {
+        const int nct = coff[t + 1] - coff[t], npt = poff[t + 1] - poff[t];
+        if (nct == 0 || npt == 0) continue;
+        for (int cc = 0; cc < nct; cc += cch)
+            for (int pc = 0; pc < npt; pc += pch)
+                us.push_back(DUnit{t, coff[t] + cc, std::min(cch, nct - cc), poff[t] + pc, std::min(pch, npt - pc),
+                                   I.cfirst_h[t] + cc / 64, I.pfirst_h[t] + pc / 32, 0});
+    }
+    I.umem_dens.release();
+    I.ndunits = (int)us.size();
+    I.dunits = I.umem_dens.alloc<DUnit>(std::max<size_t>(1, us.size()));
+    if (!us.empty())
+        check(cudaMemcpy(I.dunits, us.data(), us.size() * sizeof(DUnit), cudaMemcpyHostToDevice), "upload density units");
+    I.dens_cut[0] = cch;
+    I.dens_cut[1] = pch;
+}
+
+// the integrals' units: chunks of at most cch chi (a multiple of 128, <= 384) and pch phi (a
+// multiple of 16, <= 128), listed by class of 128-row chi blocks; false if they do not fit
+bool set_integrals_units(Impl<float> &I, int cch, int pch) {
+    const int ntl = I.chi.ntiles;
+    const std::vector<int> &coff = I.coff_h, &poff = I.poff_h;
+    std::vector<VTile> by[3];
+    int maxnc = 0, maxnp = 0;
+    for (int t = 0; t < ntl; ++t) {
+        const int nct = coff[t + 1] - coff[t], npt = poff[t + 1] - poff[t];
+        if (nct == 0 || npt == 0) continue;
+        for (int cc = 0; cc < nct; cc += cch)
+            for (int pc = 0; pc < npt; pc += pch) {
+                const VTile u{t, coff[t] + cc, std::min(cch, nct - cc), poff[t] + pc, std::min(pch, npt - pc), 0};
+                maxnc = std::max(maxnc, u.nc);
+                maxnp = std::max(maxnp, u.np);
+                by[(u.nc - 1) / 128].push_back(u);
+            }
+    }
+    const int NPi = std::max(16, (maxnp + 15) / 16 * 16);
+    if (integrals_tc_group(NPi, 1, maxnc) < 1) return false;
+    std::vector<VTile> all;
+    for (int q = 0; q < 3; ++q) {
+        I.int_count[q] = (int)by[q].size();
+        all.insert(all.end(), by[q].begin(), by[q].end());
+    }
+    I.umem_int.release();
+    I.int_units = I.umem_int.alloc<VTile>(std::max<size_t>(1, all.size()));
+    if (!all.empty())
+        check(cudaMemcpy(I.int_units, all.data(), all.size() * sizeof(VTile), cudaMemcpyHostToDevice),
+              "upload integrals units");
+    I.maxc = maxnc;
+    I.NPint = NPi;
+    I.int_cut[0] = cch;
+    I.int_cut[1] = pch;
+    return true;
+}
+
 template <typename T>
 void build_dense_matrices(tddft_ctx *c, Impl<T> *I, const tddft_system *s, Mem &tmpm);
 template <typename T>
@@ -1013,6 +1148,20 @@ void build_impl(tddft_ctx *c, const tddft_system *s, const tddft_sparse_system *
                     I->phi_quads = ok && !(nq && nq[0] == '1');
                 }
             }
+            I->coff_h = coff;
+            I->poff_h = poff;
+            // dense tiles: the density in units of <= 320 chi and <= 128 phi of a tile, when every
+            // tile's phi list is whole aligned atom quads (the P gather loads four phi at once);
+            // TDDFT_DENSITY_UNITS=1 takes them even where the per-tile kernels fit
+            {
+                const char *nu = std::getenv("TDDFT_NO_DENSITY_UNITS");
+                const char *fu = std::getenv("TDDFT_DENSITY_UNITS");
+                const bool want = !I->grid_tc || (fu && fu[0] == '1');
+                if (want && !(nu && nu[0] == '1') && c->nv % 4 == 0 && build_density_chunks(c, *I)) {
+                    set_density_units(*I, 320, 128);
+                    I->dens_units = true;
+                }
+            }
             // integrals: units of at most 384 chi and 128 phi slots of one tile (a denser tile is
             // cut into several). TDDFT_INTEGRALS_CHUNK="nc,np" cuts smaller units (multiples of
             // 128 and 16), for tests of the cut on small systems.
@@ -1026,21 +1175,7 @@ void build_impl(tddft_ctx *c, const tddft_system *s, const tddft_sparse_system *
                         pch = b;
                     }
                 }
-                std::vector<VTile> by[3];
-                int maxnc = 0, maxnp = 0;
-                for (int t = 0; t < ntl; ++t) {
-                    const int nct = coff[t + 1] - coff[t], npt = poff[t + 1] - poff[t];
-                    if (nct == 0 || npt == 0) continue;
-                    for (int cc = 0; cc < nct; cc += cch)
-                        for (int pc = 0; pc < npt; pc += pch) {
-                            const VTile u{t, coff[t] + cc, std::min(cch, nct - cc), poff[t] + pc, std::min(pch, npt - pc), 0};
-                            maxnc = std::max(maxnc, u.nc);
-                            maxnp = std::max(maxnp, u.np);
-                            by[(u.nc - 1) / 128].push_back(u);
-                        }
-                }
-                const int NPi = std::max(16, (maxnp + 15) / 16 * 16);
-                if (integrals_tc_group(NPi, 1, maxnc) >= 1) {
+                if (set_integrals_units(*I, cch, pch)) {
                     // function-major f16 copies of both tables, rounded on the device (the f16 phi
                     // rows are the integrals' B operand, TMA-loaded and scaled by V in place)
                     const long long nch = (long long)coff[ntl] * TILE_PTS, nph = (long long)poff[ntl] * TILE_PTS;
@@ -1050,17 +1185,6 @@ void build_impl(tddft_ctx *c, const tddft_system *s, const tddft_sparse_system *
                     I->phi_fm16 = I->mem.template alloc<unsigned short>(std::max<long long>(1, nph));
                     to_f16(st, reinterpret_cast<const float *>(I->phi.val), I->phi_fm16, nph);
                     I->nslots_phi = poff[ntl];
-                    std::vector<VTile> all;
-                    for (int q = 0; q < 3; ++q) {
-                        I->int_count[q] = (int)by[q].size();
-                        all.insert(all.end(), by[q].begin(), by[q].end());
-                    }
-                    I->int_units = I->mem.template alloc<VTile>(std::max<size_t>(1, all.size()));
-                    if (!all.empty())
-                        check(cudaMemcpy(I->int_units, all.data(), all.size() * sizeof(VTile), cudaMemcpyHostToDevice),
-                              "upload integrals units");
-                    I->maxc = maxnc;
-                    I->NPint = NPi;
                     I->integrals_tc = true;
                 }
             }
@@ -2484,6 +2608,105 @@ tddft_status tddft_response_density_noalloc(tddft_ctx *c, int32_t k, const float
                                     rho, I.phi_pm);
         if (response_density_tc_noalloc_error(c->st))
             throw TimeoutErr{"a bounded wait in the density kernel expired"};
+        return TDDFT_OK;
+    });
+}
+
+tddft_status tddft_autotune(tddft_ctx *c, int32_t k, tddft_tuning_entry *out, int32_t cap, int32_t *count) {
+    if (!c) return TDDFT_E_INVALID;
+    return guarded(c, [&]() -> tddft_status {
+        if (k < 1 || k > 2 * KMAX) throw InvalidArg{"tddft_autotune: need 1 <= k <= 32"};
+        if (c->prec != TDDFT_MIXED || !c->d32 || !tc_enabled())
+            throw InvalidArg{"tddft_autotune: the tensor-core grid kernels belong to mixed-precision contexts"};
+        Impl<float> &I = *c->d32;
+        ensure_workspace(c, I, k);
+        cudaStream_t st = c->st;
+        const long long nP = (long long)k * c->len(), nV = (long long)k * c->n3();
+        roots::fill_random_kernel<<<1216, 256, 0, st>>>(I.bufP, nP, 0x7a11ull);
+        roots::fill_random_kernel<<<1216, 256, 0, st>>>(I.V, nV, 0x7a12ull);
+        check_launch("fill_random_kernel");
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        check(cudaEventCreate(&e0), "cudaEventCreate");
+        check(cudaEventCreate(&e1), "cudaEventCreate");
+        struct Ev {
+            cudaEvent_t a, b;
+            ~Ev() { cudaEventDestroy(a); cudaEventDestroy(b); }
+        } evs{e0, e1};
+        auto time_it = [&](auto &&fn) {
+            fn();   // warm-up
+            check(cudaEventRecord(e0, st), "cudaEventRecord");
+            for (int r = 0; r < 3; ++r) fn();
+            check(cudaEventRecord(e1, st), "cudaEventRecord");
+            check(cudaEventSynchronize(e1), "cudaEventSynchronize");
+            float ms = 0.0f;
+            check(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+            return ms / 3.0;
+        };
+        std::vector<tddft_tuning_entry> rows;
+        auto add = [&](const char *stage, int kind, int a, int b, double ms) {
+            tddft_tuning_entry e{};
+            std::strncpy(e.stage, stage, sizeof(e.stage) - 1);
+            e.kind = kind;
+            e.chi_chunk = a;
+            e.phi_chunk = b;
+            e.ms = ms;
+            rows.push_back(e);
+        };
+        // response density: the per-tile kernels (when every tile fits them) and units of each cut
+        {
+            const bool units_possible = c->nv % 4 == 0 && build_density_chunks(c, I);
+            int best = -1;
+            double best_ms = 1e300;
+            if (I.grid_tc) {
+                I.dens_units = false;
+                add("response_density", 0, 0, 0, time_it([&]() { density(c, I, I.bufP, k); }));
+                best = (int)rows.size() - 1;
+                best_ms = rows.back().ms;
+            }
+            if (units_possible) {
+                const int cuts[][2] = {{320, 128}, {256, 128}, {192, 128}, {128, 128}, {320, 64}, {192, 64}, {128, 64}};
+                for (const auto &cut : cuts) {
+                    set_density_units(I, cut[0], cut[1]);
+                    I.dens_units = true;
+                    add("response_density", 1, cut[0], cut[1], time_it([&]() { density(c, I, I.bufP, k); }));
+                    if (rows.back().ms < best_ms) {
+                        best_ms = rows.back().ms;
+                        best = (int)rows.size() - 1;
+                    }
+                }
+            }
+            if (best >= 0) {
+                rows[best].chosen = 1;
+                if (rows[best].kind == 1) {
+                    set_density_units(I, rows[best].chi_chunk, rows[best].phi_chunk);
+                    I.dens_units = true;
+                } else {
+                    I.dens_units = false;
+                }
+            }
+        }
+        // potential integrals: unit cuts (chi a multiple of 128, phi of 16)
+        if (I.integrals_tc) {
+            const int cuts[][2] = {{384, 128}, {256, 128}, {128, 128}, {384, 64}, {256, 64}, {128, 64}, {384, 32}};
+            int best = -1;
+            double best_ms = 1e300;
+            for (const auto &cut : cuts) {
+                if (!set_integrals_units(I, cut[0], cut[1])) continue;
+                add("potential_integrals", 1, cut[0], cut[1], time_it([&]() { integrals(c, I, k); }));
+                if (rows.back().ms < best_ms) {
+                    best_ms = rows.back().ms;
+                    best = (int)rows.size() - 1;
+                }
+            }
+            if (best >= 0) {
+                rows[best].chosen = 1;
+                set_integrals_units(I, rows[best].chi_chunk, rows[best].phi_chunk);
+            }
+        }
+        check_tc_error(c);
+        const int n = std::min<int>(cap, (int)rows.size());
+        for (int i = 0; i < n && out; ++i) out[i] = rows[i];
+        if (count) *count = (int)rows.size();
         return TDDFT_OK;
     });
 }

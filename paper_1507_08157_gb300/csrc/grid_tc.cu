@@ -613,6 +613,259 @@ __global__ void __launch_bounds__(PDENS_THREADS, 1) density_tc_persistent_kernel
     if (threadIdx.x == 0 && ctl->abort) atomicExch(err, 1);
 }
 
+// ------------------------------------------------------------------------------------------------
+// Dense tiles (more chi or phi on a tile than the per-tile kernels hold, as in the solvated
+// systems of Sec. IV): each tile's lists are cut into units of at most 5 x 64 chi and 4 x 32 phi,
+// and each unit adds
+//   rho_s(r) += sum_{b in unit} [ sum_{a in unit} chi_a(r) P_s,ab ] phi_b(r)
+// for the tile's 512 points into rho with float32 reductions. Persistent, one CTA per SM over
+// (unit, state) items, with the roles of the persistent per-tile kernel: warp 4 brings the chi
+// chunks of the unit by TMA from a chunked point-major table [chunk][512][64] (chunk = 64
+// consecutive chi slots of one tile, zero padded), warp 5 issues the MMAs (M = 128 points,
+// N = 128 phi rows, K = the unit's chi), warps 6-7 and 12-15 gather the next item's P block
+// (float16, scaled per state) into the other B buffer, and the two epilogue groups (warps 0-3,
+// 8-11) read their accumulator and multiply by phi from a chunked point-major table
+// [chunk][512][32]. Every wait is bounded.
+constexpr int UD_KB = 5;              // chi blocks of 64 per unit
+constexpr int UD_NB = 128;            // phi rows of the B operand
+
+__global__ void __launch_bounds__(PDENS_THREADS, 1) density_units_kernel(
+    const __grid_constant__ CUtensorMap mX,   // [chi chunk * 512 + point][64] f16, box 64 x 128
+    int n, int nt, int k, const DUnit *__restrict__ units, int nitems, const int *__restrict__ cids,
+    const int *__restrict__ pids, int nphi, const unsigned short *__restrict__ phi_pmc,
+    const float *__restrict__ P, long long sP, const float *__restrict__ pscale, float *__restrict__ rho,
+    int *err, long long wlim) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *base = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<unsigned long long>(smem_raw) + 1023ull) & ~1023ull);
+    constexpr int NB = UD_NB;
+    unsigned char *A = base;                                      // ring [STAGES][128 x 128 B]
+    unsigned char *Bb = base + PDENS_STAGES * 16384;              // [2][UD_KB][NB x 128 B]
+    constexpr size_t bsize = (size_t)UD_KB * NB * 128;
+    PDensShared *ctl = reinterpret_cast<PDensShared *>(Bb + 2 * bsize);
+    volatile int *abort = &ctl->abort;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long n3 = (long long)n * n * n;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < PDENS_STAGES; ++i) {
+            mbar_init(&ctl->a_full[i], 1);
+            mbar_init(&ctl->a_empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&ctl->acc_full[i], 1);
+            mbar_init(&ctl->acc_empty[i], 128);
+            mbar_init(&ctl->b_full[i], PDENS_GATHER);
+            mbar_init(&ctl->b_free[i], 1);
+        }
+        mbar_init(&ctl->drain, 1);
+        ctl->abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 5) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&ctl->tmem_base)),
+                     "r"(256));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = ctl->tmem_base;
+
+    if (warp == 4) {
+        if (lane == 0) {
+            long long q = 0;
+            for (int it = blockIdx.x; it < nitems && !*abort; it += gridDim.x) {
+                const DUnit u = units[it / k];
+                const int KB = (u.nc + 63) / 64;
+                for (int pb = 0; pb < TILE_PTS / 128; ++pb)
+                    for (int kb = 0; kb < KB; ++kb, ++q) {
+                        const int st = (int)(q % PDENS_STAGES);
+                        const long long use = q / PDENS_STAGES;
+                        if (use > 0 && !mbar_wait(&ctl->a_empty[st], (unsigned)((use - 1) & 1), abort, wlim)) break;
+                        mbar_expect_tx(&ctl->a_full[st], 16384);
+                        tma_load_2d(A + st * 16384, &mX, &ctl->a_full[st], 0, (u.cch + kb) * TILE_PTS + pb * 128);
+                    }
+            }
+            if (*abort)
+                for (long long j = q > PDENS_STAGES ? q - PDENS_STAGES : 0; j < q; ++j)
+                    mbar_drain(&ctl->a_full[j % PDENS_STAGES], (unsigned)((j / PDENS_STAGES) & 1), wlim);
+        }
+    } else if (warp == 5) {
+        if (lane == 0) {
+            const unsigned idesc = idesc_f16(128, NB);
+            long long q = 0, pbg = 0;
+            int j = 0;
+            bool ok = true;
+            for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x, ++j) {
+                const DUnit u = units[it / k];
+                const int KB = (u.nc + 63) / 64;
+                const int buf = j & 1;
+                if (!mbar_wait(&ctl->b_full[buf], (unsigned)((j >> 1) & 1), abort, wlim)) break;
+                tc_fence_after();
+                const unsigned char *B = Bb + buf * bsize;
+                for (int pb = 0; pb < TILE_PTS / 128 && ok; ++pb, ++pbg) {
+                    const int acc = (int)(pbg & 1);
+                    const long long ause = pbg >> 1;
+                    if (ause > 0 && !mbar_wait(&ctl->acc_empty[acc], (unsigned)((ause - 1) & 1), abort, wlim)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    for (int kb = 0; kb < KB; ++kb, ++q) {
+                        const int st = (int)(q % PDENS_STAGES);
+                        if (!mbar_wait(&ctl->a_full[st], (unsigned)((q / PDENS_STAGES) & 1), abort, wlim)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const unsigned a = smem_u32(A + st * 16384), bb = smem_u32(B + (size_t)kb * NB * 128);
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk)
+                            mma_f16(tmem + acc * 128, smem_desc(a + kk * 32), smem_desc(bb + kk * 32), idesc,
+                                    (kb > 0 || kk > 0) ? 1u : 0u);
+                        mma_commit(&ctl->a_empty[st]);
+                    }
+                    if (!ok) break;
+                    mma_commit(&ctl->acc_full[acc]);
+                }
+                if (!ok) break;
+                mma_commit(&ctl->b_free[buf]);
+            }
+            if (*abort) {
+                mma_commit(&ctl->drain);
+                mbar_drain(&ctl->drain, 0, wlim);
+            }
+        }
+    } else if ((warp >= 6 && warp < 8) || warp >= 12) {
+        // the P block of each item (rows = the unit's phi, K = its chi) by phi quads, zeros past
+        // the unit's counts (every row and K column of the buffer is written)
+        const int rank = pgather_rank(warp, lane);
+        int j = 0;
+        for (int it = blockIdx.x; it < nitems; it += gridDim.x, ++j) {
+            const DUnit u = units[it / k];
+            const int s = it % k;
+            const int KB = (u.nc + 63) / 64;
+            const int buf = j & 1;
+            if (j >= 2 && !mbar_wait(&ctl->b_free[buf], (unsigned)(((j >> 1) - 1) & 1), abort, wlim)) break;
+            unsigned char *B = Bb + buf * bsize;
+            const float sc = pscale[s];
+            const float *Ps = P + (long long)s * sP;
+            constexpr int nq = NB / 4;
+            const int total = nq * KB * 8;
+            for (int i0 = rank; i0 < total; i0 += 2 * PDENS_GATHER) {
+                float4 v[2][8];
+#pragma unroll
+                for (int uu = 0; uu < 2; ++uu) {
+                    const int idx = i0 + uu * PDENS_GATHER;
+                    const int qd = idx % nq, ch = idx / nq;
+                    const bool live = idx < total && qd * 4 < u.np;
+                    const float *Pq = Ps + (live ? pids[u.p0 + qd * 4] : 0);
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const int a = (ch >> 3) * 64 + (ch & 7) * 8 + e;
+                        v[uu][e] = (live && a < u.nc)
+                                       ? __ldg(reinterpret_cast<const float4 *>(Pq + (long long)cids[u.c0 + a] * nphi))
+                                       : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    }
+                }
+#pragma unroll
+                for (int uu = 0; uu < 2; ++uu) {
+                    const int idx = i0 + uu * PDENS_GATHER;
+                    if (idx >= total) continue;
+                    const int qd = idx % nq, ch = idx / nq;
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        unsigned short h[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            const float x = r == 0 ? v[uu][e].x : r == 1 ? v[uu][e].y : r == 2 ? v[uu][e].z : v[uu][e].w;
+                            h[e] = __half_as_ushort(__float2half_rn(x * sc));
+                        }
+                        uint4 qv;
+                        qv.x = h[0] | ((unsigned)h[1] << 16);
+                        qv.y = h[2] | ((unsigned)h[3] << 16);
+                        qv.z = h[4] | ((unsigned)h[5] << 16);
+                        qv.w = h[6] | ((unsigned)h[7] << 16);
+                        *reinterpret_cast<uint4 *>(B + (size_t)(ch >> 3) * NB * 128 + sw128_offset(qd * 4 + r, ch & 7)) = qv;
+                    }
+                }
+            }
+            fence_async_smem();
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ctl->b_full[buf])) : "memory");
+        }
+    } else {
+        // epilogue groups: warps 0-3 accumulator 0 (even point blocks), warps 8-11 accumulator 1
+        const int eg = warp < 4 ? 0 : 1, quarter = warp & 3;
+        long long ause = 0;
+        for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+            const DUnit u = units[it / k];
+            const int s = it % k;
+            const int tx = u.t / (nt * nt), ty = (u.t / nt) % nt, tz = u.t % nt;
+            const float inv = 1.0f / pscale[s];
+            bool stop = false;
+            for (int pb = eg; pb < TILE_PTS / 128; pb += 2, ++ause) {
+                const bool ok = mbar_wait(&ctl->acc_full[eg], (unsigned)(ause & 1), abort, wlim) && !*abort;
+                tc_fence_after();
+                const int lp = pb * 128 + quarter * 32 + lane;
+                float r = 0.0f;
+                if (ok) {
+                    for (int c = 0; c < u.np; c += 32) {
+                        const uint4 *q = reinterpret_cast<const uint4 *>(
+                            phi_pmc + ((long long)(u.pch + c / 32) * TILE_PTS + lp) * 32);
+                        uint4 ph[4];
+#pragma unroll
+                        for (int w = 0; w < 4; ++w) ph[w] = __ldg(q + w);
+                        float v[32];
+                        tmem_ld32(tmem + eg * 128 + ((unsigned)(quarter * 32) << 16) + (unsigned)c, v);
+#pragma unroll
+                        for (int w = 0; w < 4; ++w) {
+                            const __half2 *hh = reinterpret_cast<const __half2 *>(&ph[w]);
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const float2 f2 = __half22float2(hh[e]);
+                                r = fmaf(v[8 * w + 2 * e], f2.x, r);
+                                r = fmaf(v[8 * w + 2 * e + 1], f2.y, r);
+                            }
+                        }
+                    }
+                }
+                tc_fence_before();
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ctl->acc_empty[eg])) : "memory");
+                if (!ok) {
+                    stop = true;
+                    break;
+                }
+                const int gx = tx * TILE + (lp >> 6), gy = ty * TILE + ((lp >> 3) & 7), gz = tz * TILE + (lp & 7);
+                if (gx < n && gy < n && gz < n)
+                    atomicAdd(rho + (long long)s * n3 + ((long long)gx * n + gy) * n + gz, r * inv);
+            }
+            if (stop) break;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 5) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+    }
+    if (threadIdx.x == 0 && ctl->abort) atomicExch(err, 1);
+}
+
+// chunked point-major f16 copy of a tile set's tables: chunk c of tile t holds the slots
+// off[t] + j*W .. + W - 1 (j = c - first[t]) as [512 points][W], zeros past the tile's count
+__global__ void chunked_pm_kernel(const float *__restrict__ val, const int *__restrict__ off,
+                                  const int *__restrict__ chunk_tile, const int *__restrict__ chunk_j, int W,
+                                  long long nchunks, unsigned short *__restrict__ out) {
+    const long long tot = nchunks * TILE_PTS * W;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+        const long long ch = e / ((long long)TILE_PTS * W);
+        const int rem = (int)(e - ch * TILE_PTS * W), p = rem / W, a = rem - p * W;
+        const int t = chunk_tile[ch], sl = chunk_j[ch] * W + a;
+        const int cnt = off[t + 1] - off[t];
+        out[e] = sl < cnt ? __half_as_ushort(__float2half_rn(val[(long long)(off[t] + sl) * TILE_PTS + p])) : 0;
+    }
+}
+
 // per-state power-of-two scale: 2^-e with 2^(e-1) < max|P_s| <= 2^e (1 for an all-zero state)
 __global__ void maxabs_kernel(const float *__restrict__ P, long long len, int k, unsigned *__restrict__ bits) {
     const int s = blockIdx.y;
@@ -726,6 +979,75 @@ void response_density_tc(cudaStream_t st, const GridShape &g, const TileSet<floa
                                                       phi_quads ? 1 : 0, NP % 32 == 0 ? phi_pm : nullptr,
                                                       active_wait_limit());
     check_launch("density_tc_kernel");
+}
+
+// chunked point-major f16 tables of a tile set (device built); returns the number of chunks
+long long build_chunked_pm(cudaStream_t st, Mem &mem, const TileSet<float> &ts, const std::vector<int> &off_h, int W,
+                           unsigned short **out, std::vector<int> &first) {
+    const int ntl = ts.ntiles;
+    first.assign(ntl + 1, 0);
+    std::vector<int> ct, cj;
+    for (int t = 0; t < ntl; ++t) {
+        const int nch = (off_h[t + 1] - off_h[t] + W - 1) / W;
+        first[t + 1] = first[t] + nch;
+        for (int j = 0; j < nch; ++j) {
+            ct.push_back(t);
+            cj.push_back(j);
+        }
+    }
+    const long long nchunks = first[ntl];
+    *out = mem.alloc<unsigned short>(std::max<long long>(1, nchunks * TILE_PTS * W));
+    if (nchunks == 0) return 0;
+    int *dct = mem.alloc<int>(ct.size()), *dcj = mem.alloc<int>(cj.size());
+    check(cudaMemcpy(dct, ct.data(), ct.size() * sizeof(int), cudaMemcpyHostToDevice), "upload chunk tiles");
+    check(cudaMemcpy(dcj, cj.data(), cj.size() * sizeof(int), cudaMemcpyHostToDevice), "upload chunk index");
+    const long long tot = nchunks * TILE_PTS * W;
+    chunked_pm_kernel<<<(int)std::min<long long>((tot + 255) / 256, 8 * 1216), 256, 0, st>>>(
+        ts.val, ts.off, dct, dcj, W, nchunks, *out);
+    check_launch("chunked_pm_kernel");
+    check(cudaStreamSynchronize(st), "sync chunked tables");
+    return nchunks;
+}
+
+size_t density_units_smem() {
+    return 1024 + (size_t)PDENS_STAGES * 16384 + 2 * (size_t)UD_KB * UD_NB * 128 + sizeof(PDensShared);
+}
+
+// response density of dense tiles: units of <= 320 chi and <= 128 phi of a tile, rho accumulated
+void response_density_units(cudaStream_t st, const GridShape &g, const TileSet<float> &chi, const TileSet<float> &phi,
+                            const unsigned short *chi_pmc, long long nchunks_chi, const unsigned short *phi_pmc,
+                            const DUnit *units, int nunits, int nphi, const float *P, long long sP, int k, float *rho,
+                            unsigned *scratch_bits, float *scale, int *err) {
+    if (k <= 0) return;
+    ProfScope ps(st, ST_DENSITY, 2.0 * k * g.pair_points, 2.0 * g.table_values + 4.0 * k * g.n * g.n * g.n);
+    check(cudaMemsetAsync(scratch_bits, 0, sizeof(unsigned) * k, st), "memset maxabs");
+    maxabs_kernel<<<dim3(64, k), 256, 0, st>>>(P, sP, k, scratch_bits);
+    check_launch("maxabs_kernel");
+    scale_kernel<<<(k + 127) / 128, 128, 0, st>>>(scratch_bits, k, scale);
+    check_launch("scale_kernel");
+    check(cudaMemsetAsync(rho, 0, sizeof(float) * (size_t)k * g.n * g.n * g.n, st), "memset rho");
+    const long long nitems = (long long)nunits * k;
+    if (nitems == 0) return;
+    if (nitems > (1LL << 31) - 1) throw CudaError{cudaErrorInvalidValue, "density units: too many items"};
+    CUtensorMap mx;
+    if (!encode_map_2d(&mx, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, chi_pmc, 64ull, (unsigned long long)nchunks_chi * TILE_PTS,
+                       128ull, 64, 128))
+        throw CudaError{cudaErrorInvalidValue, "cuTensorMapEncodeTiled (density units)"};
+    static const bool attr = [&]() {
+        check(cudaFuncSetAttribute(density_units_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)density_units_smem()),
+              "attr density_units");
+        return true;
+    }();
+    (void)attr;
+    int dev = 0, sms = 0;
+    check(cudaGetDevice(&dev), "cudaGetDevice");
+    check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    const int grid = (int)std::min<long long>(sms, nitems);
+    density_units_kernel<<<grid, PDENS_THREADS, density_units_smem(), st>>>(
+        mx, g.n, g.nt, k, units, (int)nitems, chi.ids, phi.ids, nphi, phi_pmc, P, sP, scale, rho, err,
+        active_wait_limit());
+    check_launch("density_units_kernel");
 }
 
 }  // namespace tddft
@@ -995,11 +1317,14 @@ void potential_integrals_tc(cudaStream_t st, const GridShape &g, const TileSet<f
         const int stride = 128;                           // one state: NB = NPmax <= 128 columns
         const int tmem_cols = mbmax == 1 ? 128 : (mbmax == 2 ? 256 : 512);
         const size_t sm = integrals_tc_smem(NPmax, 1, mbmax);
-        dim3 grid(k, cnt);
-        integrals_tc_kernel<<<grid, 192, sm, st>>>(mx, mp, g.n, g.nt, NPmax, k, chi.ids, phi.ids, nchi, nphi, V,
-                                                   scale, (float)g.dV, out, vec_ok, stride, lst, mbmax, tmem_cols,
-                                                   err, active_wait_limit());
-        check_launch("integrals_tc_kernel");
+        // grid.y holds at most 65535 units: launch the class in slices
+        for (int u0 = 0; u0 < cnt; u0 += 65535) {
+            dim3 grid(k, std::min(65535, cnt - u0));
+            integrals_tc_kernel<<<grid, 192, sm, st>>>(mx, mp, g.n, g.nt, NPmax, k, chi.ids, phi.ids, nchi, nphi, V,
+                                                       scale, (float)g.dV, out, vec_ok, stride, lst + u0, mbmax,
+                                                       tmem_cols, err, active_wait_limit());
+            check_launch("integrals_tc_kernel");
+        }
     }
 }
 

@@ -91,6 +91,18 @@ struct VTile {
     int pad;
 };
 
+// One unit of the tensor-core density on dense tiles: a chunk of a tile's chi slots (at most five
+// blocks of 64) and of its phi slots (at most 128, in chunks of 32), with the indices of their first
+// 64-wide chi chunk and 32-wide phi chunk in the chunked point-major tables.
+struct DUnit {
+    int t;        // grid tile
+    int c0, nc;   // first chi slot, count
+    int p0, np;   // first phi slot, count
+    int cch;      // first chi chunk
+    int pch;      // first phi chunk
+    int pad;
+};
+
 struct GridShape {
     int n;          // points per side
     int nt;         // tiles per side = ceil(n / 8)

@@ -57,6 +57,11 @@ class _SparseSystem(ctypes.Structure):
                 ("kernel_cutoff", ctypes.c_double), ("density_kernel_cutoff", ctypes.c_double)]
 
 
+class TuningEntry(ctypes.Structure):
+    _fields_ = [("stage", ctypes.c_char * 32), ("kind", ctypes.c_int32), ("chi_chunk", ctypes.c_int32),
+                ("phi_chunk", ctypes.c_int32), ("chosen", ctypes.c_int32), ("ms", ctypes.c_double)]
+
+
 class _Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("mode", ctypes.c_int32),
                 ("precond", ctypes.c_int32), ("precond_maxit", ctypes.c_int32),
@@ -83,7 +88,8 @@ SYMBOLS = sorted(["tddft_default_options", "tddft_create", "tddft_destroy", "tdd
                   "tddft_samples", "tddft_state_stats", "tddft_state_export",
                   "tddft_state_import", "tddft_create_batch", "tddft_solve_batch",
                   "tddft_oscillator_strengths", "tddft_spectrum", "tddft_joint_projector",
-                  "tddft_wait_check", "tddft_create_sparse", "tddft_kernel_pattern"])
+                  "tddft_wait_check", "tddft_create_sparse", "tddft_kernel_pattern",
+                  "tddft_autotune"])
 
 _lib = None
 _live = weakref.WeakSet()      # open contexts and states, closed before interpreter shutdown
@@ -124,6 +130,8 @@ def load(path: str = LIB_PATH):
     for name in ("tddft_response_density", "tddft_response_potential", "tddft_potential_integrals"):
         getattr(lib, name).argtypes = [vp, ctypes.c_int32, vp, vp]
     lib.tddft_fxc.argtypes = [vp, vp]
+    lib.tddft_autotune.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(TuningEntry), ctypes.c_int32, c_int32_p]
+    lib.tddft_autotune.restype = ctypes.c_int
     lib.tddft_wait_check.argtypes = [vp]
     lib.tddft_wait_check.restype = ctypes.c_int
     lib.tddft_response_density_noalloc.argtypes = [vp, ctypes.c_int32, vp, vp]
@@ -507,6 +515,16 @@ class Context:
         out = self._out(V, self._kshape(V.shape[0]))
         self._check(self._lib.tddft_potential_integrals(self._ctx, V.shape[0], _ptr(V), _ptr(out)))
         return out
+
+    def autotune(self, k):
+        """tddft_autotune: time the candidate unit cuts of the grid kernels for k states and keep the
+        fastest; returns one dict per candidate."""
+        buf = (TuningEntry * 64)()
+        n = ctypes.c_int32(0)
+        self._check(self._lib.tddft_autotune(self._ctx, k, buf, 64, ctypes.byref(n)))
+        return [{"stage": buf[i].stage.decode(), "kind": "units" if buf[i].kind else "per-tile",
+                 "chi_chunk": buf[i].chi_chunk, "phi_chunk": buf[i].phi_chunk, "ms": buf[i].ms,
+                 "chosen": bool(buf[i].chosen)} for i in range(min(n.value, 64))]
 
     def wait_check(self):
         """Status of tddft_wait_check: a kernel whose bounded wait must expire (E_TIMEOUT expected)."""
