@@ -287,28 +287,10 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def c1_density_recipe(natoms, seed):
-    """Config-1 recipe (4 phi + 4 chi per atom, 7 A radius, 1/3 A grid) at its atom density,
-    the cubic cell grown with the atom count; the grid is the next 2/3/5-smooth size."""
-    cell = 16.0 * (natoms / 8.0) ** (1.0 / 3.0)
-    n = int(np.ceil(cell * 3.0))
-    while not _smooth(n):
-        n += 1
-    from paper_1507_08157_gb300 import synthetic as sy
-    return sy.Recipe(natoms=natoms, cell_ang=cell, ngrid=n, nphi=4, nchi=4, radius_ang=7.0, seed=seed)
-
-
-def _smooth(n):
-    for p in (2, 3, 5):
-        while n % p == 0:
-            n //= p
-    return n == 1
-
-
 def learned_vs_plain(tddft, sy, torch, stream, k=10, train_atoms=16, eval_atoms=24, tol=1e-5):
     rows = ([], [], [])
     for seed in (31, 32):
-        s = sy.generate(c1_density_recipe(train_atoms, seed))
+        s = sy.generate(sy.small_density_recipe(train_atoms, seed))
         c = tddft.Context(s, precision="fp64", stream=stream.cuda_stream)
         st = c.state(sy.initial_guess(s, k, seed))
         for it in range(30):
@@ -329,7 +311,7 @@ def learned_vs_plain(tddft, sy, torch, stream, k=10, train_atoms=16, eval_atoms=
     l0, l1 = net.train(X, T, steps, batch, 1e-3, sy.minibatch_order(X.shape[0], steps, batch, 34), W)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
-    s = sy.generate(c1_density_recipe(eval_atoms, 35))
+    s = sy.generate(sy.small_density_recipe(eval_atoms, 35))
     Y0 = sy.initial_guess(s, k, 35)
     out = {}
     for pre in ("iter", "adaptive", "exact", "learned", "none"):

@@ -733,6 +733,15 @@ def smooth_grid(n: int) -> int:
         n += 1
 
 
+def small_density_recipe(natoms: int, seed: int) -> Recipe:
+    """The small workload's recipe (4 phi + 4 chi per atom, 7 A radius, 1/3 A grid) at its atom
+    density (8 atoms per (16 A)^3), the cubic cell grown with the atom count; the grid is the next
+    2/3/5-smooth size (the learned preconditioner's training and evaluation systems)."""
+    cell = 16.0 * (natoms / 8.0) ** (1.0 / 3.0)
+    n = smooth_grid(int(math.ceil(cell * 3.0)))
+    return Recipe(natoms=natoms, cell_ang=cell, ngrid=n, nphi=4, nchi=4, radius_ang=7.0, seed=seed)
+
+
 def batch_recipes(nsys: int, seed: int, n_min=20, n_max=300, density=0.1, radius=7.0, h=0.25, k_max=8):
     """Uneven systems for a batched launch: atom counts log-uniform in [n_min, n_max], atoms in a
     cube at `density` atoms / A^3, the cell the cube plus 2R + 1 A of vacuum rounded up to a
@@ -745,8 +754,11 @@ def batch_recipes(nsys: int, seed: int, n_min=20, n_max=300, density=0.1, radius
         side = (natoms / density) ** (1.0 / 3.0)
         n = smooth_grid(int(math.ceil((side + 2.0 * radius + 1.0) / h)))
         k = int(rng.integers(1, k_max + 1))
+        # the generator's fast path (float32 tables, factored overlap sums) where the boxes are at
+        # most half the cell; the small systems take the plain path
+        T = 2 * box_half_width(radius, h) + 1
         out.append((Recipe(natoms=natoms, cell_ang=n * h, ngrid=n, nphi=4, nchi=4, radius_ang=radius,
-                           cluster_ang=side, seed=1000 * seed + i), k))
+                           cluster_ang=side, seed=1000 * seed + i, fast=2 * T <= n), k))
     return out
 
 

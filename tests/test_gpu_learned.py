@@ -167,28 +167,25 @@ def test_learned_pcg_reaches_dense_eigenvalues(tddft, tiny, prec, tol, acc):
     assert np.max(np.abs(om - ref)) <= acc
 
 
-def _system(seed, natoms=6):
-    return sy.generate(sy.Recipe(natoms=natoms, cell_ang=12.0, ngrid=36, radius_ang=5.0, seed=seed))
-
-
-def test_trained_model_against_plain_pcg(tddft):
-    """Train on rows from plain-PCG runs on two systems, then solve an unseen third one with the
-    learned map, the plain (inner-CG) preconditioner and none. The learned PCG must reach the plain
-    PCG's eigenvalues (plain PCG is the judge); iterations and wall times of the three runs are
-    printed, the measure of what the model gains or loses against the method without it. (On
-    these 6-atom cells every atom overlaps every other and the block map has so far not beaten
-    the unpreconditioned method; no gain is asserted.)"""
+def test_trained_model_gains_over_the_method_without_it(tddft):
+    """Train on rows from plain-PCG runs on two systems of the small workload's recipe and atom
+    density (16 atoms, 20 A cell), then solve an unseen 24-atom system (k = 10, 1e-5 Ha, FP64) with
+    the learned map, with no preconditioner (the method without the network) and with the plain
+    inner-CG preconditioner. The learned PCG must reach the plain PCG's eigenvalues (plain PCG is
+    the judge) in fewer iterations than the unpreconditioned method. (Against plain PCG it loses:
+    the block-local map carries only part of Eq. precond's inverse; the benchmark's time_to_k
+    block reports the three at the learned model's evaluation size.)"""
     import time
     import torch
-    k, w = 3, 128
+    k, w = 10, 256
     rows_X, rows_T, rows_w = [], [], []
-    for seed in (21, 22):
-        s = _system(seed)
+    for seed in (31, 32):
+        s = sy.generate(sy.small_density_recipe(16, seed))
         ctx = tddft.Context(s, precision="fp64")
         st = ctx.state(sy.initial_guess(s, k, seed))
-        for it in range(40):
+        for it in range(30):
             st.step()
-            if it % 2 == 1:
+            if it % 3 == 2:
                 X, T, w_ = ctx.samples(st)
                 rows_X.append(X)
                 rows_T.append(T)
@@ -201,18 +198,18 @@ def test_trained_model_against_plain_pcg(tddft):
     n_b = T.shape[1]
     n_f = X.shape[1] - n_b
     net = tddft.Mlp(n_b, n_f, w)
-    net.set(sy.mlp_init(n_f, w, n_b * n_b, 23))
+    net.set(sy.mlp_init(n_f, w, n_b * n_b, 33))
     l0, _ = net.loss_grad(X, T, Wt)
-    steps, batch = 1500, 256
-    net.train(X, T, steps, batch, 1e-3, sy.minibatch_order(X.shape[0], steps, batch, 24), Wt)
+    steps, batch = 2000, 512
+    net.train(X, T, steps, batch, 1e-3, sy.minibatch_order(X.shape[0], steps, batch, 34), Wt)
     l1, _ = net.loss_grad(X, T, Wt)
     assert l1 < 0.2 * l0
 
-    s = _system(25)
-    Y0 = sy.initial_guess(s, k, 25)
+    s = sy.generate(sy.small_density_recipe(24, 35))
+    Y0 = sy.initial_guess(s, k, 35)
     out = {}
     for pre in ("none", "learned", "iter"):
-        ctx = tddft.Context(s, precision="fp64", precond=pre, tol=1e-5, max_iter=500)
+        ctx = tddft.Context(s, precision="fp64", precond=pre, tol=1e-5, max_iter=600)
         if pre == "learned":
             ctx.set_mlp(net)
         st = ctx.state(Y0)
@@ -226,3 +223,4 @@ def test_trained_model_against_plain_pcg(tddft):
           (l0, l1, out["none"][0], out["none"][1], out["learned"][0], out["learned"][1], out["learned"][3][1],
            out["iter"][0], out["iter"][1]))
     assert np.max(np.abs(out["learned"][2] - out["iter"][2])) <= 1e-5
+    assert out["learned"][0] < out["none"][0]
