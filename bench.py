@@ -21,6 +21,7 @@ Other lines (one JSON line each, not the default):
 """
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -661,29 +662,38 @@ def run_scaling(args):
             cpu = cpu_oracle_sample(s)
         nnz = ctx.nnz if ctx.sparse else ctx.nc * ctx.nv
         del s
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
         for _ in range(args.warmup):
             ctx.apply(dPp, dPq)
+        torch.cuda.synchronize()
+        # at least about a second of timed applies, so that the clock sampler sees the load
+        per = (time.perf_counter() - w0) / max(args.warmup, 1)
+        steps = max(args.steps, int(math.ceil(1.0 / max(per, 1e-3))))
         ctx.profile(True)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with ClockSampler(0) as clk:
             torch.cuda.synchronize()
             e0.record(stream)
-            for _ in range(args.steps):
+            for _ in range(steps):
                 ctx.apply(dPp, dPq)
             e1.record(stream)
             torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / args.steps
+        ms = e0.elapsed_time(e1) / steps
         prof = ctx.profile_read()
         ctx.profile(False)
-        flops = sum(v[2] for v in prof.values()) / args.steps
+        flops = sum(v[2] for v in prof.values()) / steps
+        vscf_ms = sum(prof.get(n_, (0, 0.0))[1] for n_ in ("response_density", "potential_integrals",
+                                                            "fft_poisson_fxc")) / steps
         series.append({
             "atoms": natoms, "cell_ang": rec.cell_ang, "grid": rec.ngrid,
             "n_chi": ctx.nc, "n_phi": ctx.nv, "kernel_values": nnz,
             "kernel_fill": nnz / float(ctx.nc * ctx.nv),
             "pair_points": pair_points, "table_values": table_values,
-            "ms_per_apply": ms, "applies_per_s": k / (ms / 1000.0),
+            "ms_per_apply": ms, "applies_per_s": k / (ms / 1000.0), "timed_applies": steps,
+            "vscf_ms_per_apply": vscf_ms,
             "work_tflop_per_apply": flops / 1e12, "ns_per_mflop": 1e6 * ms / max(flops / 1e6, 1e-30),
-            "stages_ms": {n: round(v[1] / args.steps, 3) for n, v in prof.items() if v[0]},
+            "stages_ms": {n: round(v[1] / steps, 3) for n, v in prof.items() if v[0]},
             "generate_s": t1 - t0, "create_s": t2 - t1, "cpu_baseline": cpu,
             "autotune": [{k_: r[k_] for k_ in ("stage", "kind", "chi_chunk", "phi_chunk", "ms", "chosen")}
                          for r in tuning] if tuning else None,
@@ -703,8 +713,14 @@ def run_scaling(args):
                        "l2": "inputs larger than L2 (function tables of several GB)"},
             "series": series,
             "exponent_time_vs_atoms": _loglog_slope(atoms, [r["ms_per_apply"] for r in series]),
+            "exponent_vscf_time_vs_atoms": _loglog_slope(atoms, [r["vscf_ms_per_apply"] for r in series]),
             "exponent_work_vs_atoms": _loglog_slope(atoms, [r["work_tflop_per_apply"] for r in series]),
-            "exponent_time_per_work_vs_atoms": _loglog_slope(atoms, [r["ns_per_mflop"] for r in series])}
+            "exponent_time_vs_work": _loglog_slope([r["work_tflop_per_apply"] for r in series],
+                                                   [r["ms_per_apply"] for r in series]),
+            "exponent_time_per_work_vs_atoms": _loglog_slope(atoms, [r["ns_per_mflop"] for r in series]),
+            "work_note": "work = 2 k pair_points per grid contraction + 2 n_I n_K n_J over the contributing "
+                         "atom-block triples of every block-sparse product (padding and pattern cuts "
+                         "inside cluster blocks excluded)"}
     print(json.dumps(line), flush=True)
 
 

@@ -756,7 +756,7 @@ void lprod(tddft_ctx *c, Impl<T> &I, int x, const T *X, T *out, int nb, T alpha,
     }
     const SparseLayout &L = *c->sp;
     const PairList &pl = L.left[x];
-    ProfScope ps(c->st, ST_GEMM, (double)pl.nnz_flops * nb,
+    ProfScope ps(c->st, ST_GEMM, pl.alg_flops * nb,
                  sizeof(T) * ((double)L.cc_len(x) + (double)len * nb * (beta == T(0) ? 2 : 3)));
     if constexpr (sizeof(T) == 4) {
         if (sparse_tc(c)) {
@@ -780,7 +780,7 @@ void rprod(tddft_ctx *c, Impl<T> &I, const T *X, int x, T *out, int nb, T alpha,
     }
     const SparseLayout &L = *c->sp;
     const PairList &pl = L.right[x];
-    ProfScope ps(c->st, ST_GEMM, (double)pl.nnz_flops * nb,
+    ProfScope ps(c->st, ST_GEMM, pl.alg_flops * nb,
                  sizeof(T) * ((double)L.vv_len(x) + (double)len * nb * (beta == T(0) ? 2 : 3)));
     if constexpr (sizeof(T) == 4) {
         if (sparse_tc(c)) {

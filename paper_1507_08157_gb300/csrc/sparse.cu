@@ -364,6 +364,89 @@ void cluster_blocks(const tddft_bsr &m, const SideMap &rs, const SideMap &cs, in
         }
 }
 
+// ---- atom-level patterns as bitsets (the algorithmic work of the block products) ----------------
+struct Bits {
+    int n = 0, W = 0;
+    std::vector<unsigned long long> b;
+    explicit Bits(int n_ = 0) : n(n_), W((n_ + 63) / 64), b((size_t)n_ * ((n_ + 63) / 64), 0ull) {}
+    void set(int i, int j) { b[(size_t)i * W + (j >> 6)] |= 1ull << (j & 63); }
+    bool get(int i, int j) const { return (b[(size_t)i * W + (j >> 6)] >> (j & 63)) & 1ull; }
+    const unsigned long long *row(int i) const { return b.data() + (size_t)i * W; }
+    unsigned long long *row(int i) { return b.data() + (size_t)i * W; }
+};
+
+// pattern of A B: row i is the union of the rows k of B over the k set in row i of A
+Bits bool_product(const Bits &A, const Bits &B) {
+    Bits C(A.n);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int i = 0; i < A.n; ++i) {
+        unsigned long long *c = C.row(i);
+        const unsigned long long *a = A.row(i);
+        for (int w = 0; w < A.W; ++w)
+            for (unsigned long long x = a[w]; x; x &= x - 1) {
+                const int k = w * 64 + __builtin_ctzll(x);
+                const unsigned long long *r = B.row(k);
+                for (int q = 0; q < B.W; ++q) c[q] |= r[q];
+            }
+    }
+    return C;
+}
+
+Bits transpose_bits(const Bits &A) {
+    Bits T(A.n);
+    for (int i = 0; i < A.n; ++i)
+        for (int j = 0; j < A.n; ++j)
+            if (A.get(i, j)) T.set(j, i);
+    return T;
+}
+
+// 2 sum over (I, J) set in C of nI nJ sum over K in (row I of A) and (column J of B) of nK, with
+// cols = the transpose of B's pattern and nK grouped by distinct counts
+double triple_flops(const Bits &A, const Bits &colsB, const Bits &C, const std::vector<int> &nI,
+                    const std::vector<int> &nK, const std::vector<int> &nJ) {
+    std::vector<int> vals(nK.begin(), nK.end());
+    std::sort(vals.begin(), vals.end());
+    vals.erase(std::unique(vals.begin(), vals.end()), vals.end());
+    std::vector<Bits> byc;
+    for (int v : vals) {
+        Bits m(A.n);
+        for (int k = 0; k < A.n; ++k)
+            if (nK[k] == v) m.b[k >> 6] |= 1ull << (k & 63);   // one row holds the mask
+        byc.push_back(std::move(m));
+    }
+    double tot = 0.0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : tot)
+    for (int I = 0; I < C.n; ++I) {
+        const unsigned long long *a = A.row(I), *c = C.row(I);
+        for (int w = 0; w < C.W; ++w)
+            for (unsigned long long x = c[w]; x; x &= x - 1) {
+                const int J = w * 64 + __builtin_ctzll(x);
+                const unsigned long long *col = colsB.row(J);
+                double sk = 0.0;
+                for (size_t v = 0; v < vals.size(); ++v) {
+                    const unsigned long long *m = byc[v].row(0);
+                    long long cnt = 0;
+                    for (int q = 0; q < A.W; ++q) cnt += __builtin_popcountll(a[q] & col[q] & m[q]);
+                    sk += (double)cnt * vals[v];
+                }
+                tot += 2.0 * nI[I] * nJ[J] * sk;
+            }
+    }
+    return tot;
+}
+
+// the atom-level pattern of an input matrix (blocks present, within `cutoff` when > 0)
+Bits input_bits(const tddft_bsr &m, int natoms, const double *pos, double cell, double cutoff) {
+    Bits B(natoms);
+    for (int I = 0; I < natoms; ++I)
+        for (long long b = m.row_ptr[I]; b < m.row_ptr[I + 1]; ++b) {
+            const int J = m.col_idx[b];
+            if (cutoff > 0.0 && min_image(pos + 3 * I, pos + 3 * J, cell) > cutoff) continue;
+            B.set(I, J);
+        }
+    return B;
+}
+
 }  // namespace
 
 // ---- products ----------------------------------------------------------------------------------
@@ -616,6 +699,34 @@ std::unique_ptr<SparseLayout> sparse_build(cudaStream_t st, const tddft_sparse_s
     for (int x = 0; x < SP_NCONST; ++x) {
         L->left[x] = pair_list(m, L->pcc[x], L->pk, L->pk, CB_R, CB_R, CB_C);
         L->right[x] = pair_list(m, L->pk, L->pvv[x], L->pk, CB_R, CB_C, CB_C);
+    }
+    // algorithmic work of each product: contributing atom-block triples, without the padding and
+    // the atom pairs off the pattern inside present cluster blocks
+    {
+        Bits pk(na);
+        for (int I = 0; I < na; ++I)
+            for (int J = 0; J < na; ++J)
+                if (L->amask[(size_t)I * na + J] && chi.cnt[I] && phi.cnt[J]) pk.set(I, J);
+        const Bits pkT = transpose_bits(pk);
+        const Bits Sc_b = input_bits(s->S_chi, na, s->pos, s->cell, 0.0), Hc_b = input_bits(s->H_chi, na, s->pos, s->cell, 0.0);
+        const Bits Pc_b = input_bits(s->P_c, na, s->pos, s->cell, s->density_kernel_cutoff);
+        const Bits Sv_b = input_bits(s->S_phi, na, s->pos, s->cell, 0.0), Hv_b = input_bits(s->H_phi, na, s->pos, s->cell, 0.0);
+        const Bits Pv_b = input_bits(s->P_v, na, s->pos, s->cell, s->density_kernel_cutoff);
+        Bits cc[SP_NCONST], vv[SP_NCONST];
+        cc[SP_S] = Sc_b;
+        cc[SP_P] = Pc_b;
+        cc[SP_M] = bool_product(Pc_b, Hc_b);
+        cc[SP_R] = bool_product(Pc_b, Sc_b);
+        cc[SP_A] = bool_product(Sc_b, cc[SP_R]);
+        vv[SP_S] = Sv_b;
+        vv[SP_P] = Pv_b;
+        vv[SP_M] = bool_product(Hv_b, Pv_b);
+        vv[SP_R] = bool_product(Sv_b, Pv_b);
+        vv[SP_A] = bool_product(vv[SP_R], Sv_b);
+        for (int x = 0; x < SP_NCONST; ++x) {
+            L->left[x].alg_flops = triple_flops(cc[x], pkT, pk, chi.cnt, chi.cnt, phi.cnt);
+            L->right[x].alg_flops = triple_flops(pk, transpose_bits(vv[x]), pk, chi.cnt, phi.cnt, phi.cnt);
+        }
     }
     check(cudaStreamSynchronize(st), "sync sparse build");
     return L;

@@ -40,6 +40,7 @@ struct PairList {
     int *pb = nullptr;      // [npairs]
     int *empty = nullptr;   // [nempty] output blocks without pairs
     long long nnz_flops = 0;   // 2 * sum over pairs of the padded block product (per batch entry)
+    double alg_flops = 0.0;    // 2 * sum over contributing atom-block triples (I, K, J) of n_I n_K n_J
 };
 
 // the constants of the operator and the solver, by role

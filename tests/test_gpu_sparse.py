@@ -165,3 +165,43 @@ def test_sparse_context_refuses_other_preconditioners(tddft, sparse48):
     with pytest.raises(tddft.TddftError) as e:
         tddft.Context(dataclasses.replace(s, kernel_cutoff=0.0), sparse=True, precision="fp64", precond="none")
     assert e.value.status == tddft.E_INVALID
+
+
+def _atom_pattern(M, row_atom, col_atom, natoms):
+    """Atom pairs whose block of M holds a nonzero entry."""
+    pat = np.zeros((natoms, natoms), dtype=np.int64)
+    I, J = np.nonzero(M)
+    pat[row_atom[I], col_atom[J]] = 1
+    return pat
+
+
+def test_profiled_product_work_is_the_atom_triple_count(tddft, sparse48):
+    # The library's profiler counts the block products' work as 2 n_I n_K n_J over the atom
+    # triples (I, K, J) that contribute to an output pair (I, J) of the kernel pattern: written out
+    # here by brute force from the atom patterns of the inputs and of M_c = P^c H^chi,
+    # M_v = H^phi P^v (Sec. IV truncation of P at the density-kernel cutoff).
+    s, op = sparse48
+    na = s.natoms
+    ca, pa = s.chi.atom, s.phi.atom
+    nchi = np.bincount(ca, minlength=na)
+    nphi = np.bincount(pa, minlength=na)
+    pk = (_atom_pattern(op.mask, ca, pa, na) > 0).astype(np.int64)
+    Pc = _atom_pattern(op.Pc, ca, ca, na)
+    Hc = _atom_pattern(s.H_chi, ca, ca, na)
+    Pv = _atom_pattern(op.Pv, pa, pa, na)
+    Hv = _atom_pattern(s.H_phi, pa, pa, na)
+    Mc = ((Pc @ Hc) > 0).astype(np.int64)
+    Mv = ((Hv @ Pv) > 0).astype(np.int64)
+    left = 2 * np.sum(pk * np.outer(nchi, nphi) * (Mc @ (nchi[:, None] * pk)))
+    right = 2 * np.sum(pk * np.outer(nchi, nphi) * ((pk * nphi[None, :]) @ Mv))
+    k = 2
+    ctx = tddft.Context(s, sparse=True, precision="fp64", mode="d_only", precond="none")
+    Pp, Pq = sy.random_kernels(s, k, 4)
+    dp, dq = ctx.to_pattern(op.mask * Pp), ctx.to_pattern(op.mask * Pq)
+    ctx.profile(True)
+    ctx.apply(dp, dq)
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    launches, _, flops, _ = prof["gemm"]
+    assert launches == 2
+    assert flops == pytest.approx(2 * k * float(left + right), rel=1e-12)
