@@ -242,6 +242,153 @@ template <> struct Vec16<double> {
     __device__ static double2 mul(double2 x, double2 m) { return make_double2(x.x * m.x, x.y * m.y); }
 };
 
+// ------------------------------------------------------------------------------------------------
+// Trace products with every row read once: block s takes one contiguous range of elements and
+// all nx x ny pairs. Chunks of 256 bytes of each of the nx + ny rows stream through a ring of
+// GST shared-memory stages by cp.async (16-byte copies, zero fill past the range), so that
+// several chunks per block are in flight. A staged row takes 272 bytes (17 16-byte units, an
+// odd number), and thread (a, b) of the pair grid owns the rows a, a + gx, a + 2 gx, a + 3 gx of
+// X and b, b + gy, ... of Y, so the 16-byte reads of the lanes of a warp (consecutive b) fall on
+// distinct bank groups. The pair grid (at most 128 threads) is held twice: the two halves of
+// the block take the two halves of every chunk. Products are summed in T over a half chunk,
+// those sums in a compensated (Kahan) sum in T; the halves meet in shared memory at the end and
+// partial[s][pair] is written in float64, summed over the slices by gram_final_multi.
+template <typename T> __host__ __device__ constexpr int gram_chunk() { return 256 / (int)sizeof(T); }
+template <typename T> __host__ __device__ constexpr int gram_row() { return 272 / (int)sizeof(T); }
+constexpr int GQ = 4;           // pair tile edge
+constexpr int GST = 4;          // ring stages
+constexpr int GMAXT = 10;       // 16-byte copies per thread and chunk: nx + ny <= 160
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, bool full) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(full ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <typename T>
+__global__ void __launch_bounds__(256) gram_rows_kernel(const T *__restrict__ X, long long sx, int nx,
+                                                        const YSet<T> ys, long long sy, int ny, long long len,
+                                                        long long per_slice, int RX, int RY,
+                                                        double *__restrict__ partial, int pairs) {
+    extern __shared__ __align__(16) unsigned char gram_smem[];
+    constexpr int VW = Vec16<T>::n;
+    constexpr int GC = gram_chunk<T>();      // elements per staged chunk of a row
+    constexpr int RS = gram_row<T>();        // staged row stride (elements)
+    constexpr int TPR = GC / VW;             // 16-byte copies per row and chunk (16)
+    T *ring = reinterpret_cast<T *>(gram_smem);
+    const int stage_elems = (RX + RY) * RS;
+    const int gy = (ny + GQ - 1) / GQ, gx = (nx + GQ - 1) / GQ;
+    const int t = threadIdx.x, half = t >> 7, tl = t & 127;
+    const bool owner = tl < gx * gy;
+    const int ta = owner ? tl / gy : 0, tb = owner ? tl - (tl / gy) * gy : 0;
+    const long long e0 = (long long)blockIdx.x * per_slice;
+    const long long e1 = e0 + per_slice < len ? e0 + per_slice : len;
+    const int nch = e1 > e0 ? (int)((e1 - e0 + GC - 1) / GC) : 0;
+    const int tasks = (nx + ny) * TPR;
+
+    auto issue = [&](int ch) {
+        if (ch < nch) {
+            T *stg = ring + (ch % GST) * stage_elems;
+#pragma unroll
+            for (int m = 0; m < GMAXT; ++m) {
+                const int q = t + 256 * m;
+                if (q < tasks) {
+                    const int row = q / TPR, g = q - row * TPR;
+                    const long long e = e0 + (long long)ch * GC + (long long)g * VW;
+                    const T *src;
+                    int srow;
+                    if (row < nx) {
+                        src = X + row * sx;
+                        srow = row;
+                    } else {
+                        const int j = row - nx, s = j / ys.per;
+                        const T *set = s == 0 ? ys.p[0] : s == 1 ? ys.p[1] : s == 2 ? ys.p[2] : ys.p[3];
+                        src = set + (long long)(j - s * ys.per) * sy;
+                        srow = RX + j;
+                    }
+                    const bool in = e < e1;
+                    cp_async16(stg + srow * RS + g * VW, in ? src + e : src, in);
+                }
+            }
+        }
+        cp_async_commit();
+    };
+
+    T tot[GQ][GQ], cmp[GQ][GQ];
+#pragma unroll
+    for (int a = 0; a < GQ; ++a)
+#pragma unroll
+        for (int b = 0; b < GQ; ++b) tot[a][b] = T(0), cmp[a][b] = T(0);
+#pragma unroll
+    for (int c = 0; c < GST - 1; ++c) issue(c);
+    for (int ch = 0; ch < nch; ++ch) {
+        cp_async_wait<GST - 2>();
+        __syncthreads();             // chunk ch has landed for every thread; stage (ch - 1) is free
+        issue(ch + GST - 1);
+        if (owner) {
+            const T *stg = ring + (ch % GST) * stage_elems;
+            T run[GQ][GQ];
+#pragma unroll
+            for (int a = 0; a < GQ; ++a)
+#pragma unroll
+                for (int b = 0; b < GQ; ++b) run[a][b] = T(0);
+#pragma unroll 2
+            for (int c = half * (GC / 2); c < (half + 1) * (GC / 2); c += VW) {
+                T xa[GQ][VW], yb[GQ][VW];
+#pragma unroll
+                for (int a = 0; a < GQ; ++a) {
+                    const auto v = *reinterpret_cast<const typename Vec16<T>::type *>(stg + (ta + a * gx) * RS + c);
+                    const T *pv = reinterpret_cast<const T *>(&v);
+#pragma unroll
+                    for (int u = 0; u < VW; ++u) xa[a][u] = pv[u];
+                }
+#pragma unroll
+                for (int b = 0; b < GQ; ++b) {
+                    const auto v = *reinterpret_cast<const typename Vec16<T>::type *>(stg + (RX + tb + b * gy) * RS + c);
+                    const T *pv = reinterpret_cast<const T *>(&v);
+#pragma unroll
+                    for (int u = 0; u < VW; ++u) yb[b][u] = pv[u];
+                }
+#pragma unroll
+                for (int u = 0; u < VW; ++u)
+#pragma unroll
+                    for (int a = 0; a < GQ; ++a)
+#pragma unroll
+                        for (int b = 0; b < GQ; ++b) run[a][b] = fma(xa[a][u], yb[b][u], run[a][b]);
+            }
+#pragma unroll
+            for (int a = 0; a < GQ; ++a)
+#pragma unroll
+                for (int b = 0; b < GQ; ++b) {
+                    const T y = run[a][b] - cmp[a][b];
+                    const T s = tot[a][b] + y;
+                    cmp[a][b] = (s - tot[a][b]) - y;
+                    tot[a][b] = s;
+                }
+        }
+    }
+    cp_async_wait<0>();
+    __syncthreads();                 // the ring is free: the second half hands over its sums
+    double *hand = reinterpret_cast<double *>(gram_smem);   // [GQ * GQ][128]
+    if (owner && half == 1)
+#pragma unroll
+        for (int a = 0; a < GQ; ++a)
+#pragma unroll
+            for (int b = 0; b < GQ; ++b) hand[(a * GQ + b) * 128 + tl] = (double)tot[a][b] - (double)cmp[a][b];
+    __syncthreads();
+    if (!owner || half == 1) return;
+#pragma unroll
+    for (int a = 0; a < GQ; ++a)
+#pragma unroll
+        for (int b = 0; b < GQ; ++b) {
+            const int i = ta + a * gx, j = tb + b * gy;
+            if (i < nx && j < ny)
+                partial[(long long)blockIdx.x * pairs + i * ny + j] =
+                    ((double)tot[a][b] - (double)cmp[a][b]) + hand[(a * GQ + b) * 128 + tl];
+        }
+}
+
 // Batched element-wise kernels: blockIdx.y = matrix b of nb, blockIdx.x strides over the len
 // entries of one matrix (in 16-byte vectors when len allows), so the per-matrix coefficient is
 // read once per thread and no index division runs per element.
@@ -302,104 +449,92 @@ int grid_for(long long n) {
 // ------------------------------------------------------------------------------------------------
 // Small float64 algebra for one thread block (k <= KMAX, so k * k <= 256 threads hold one matrix
 // element each). Matrices live in shared memory; every routine is entered and left by all
-// threads of the block. The updates run in the same order as the textbook row-by-row loops
-// (right-looking, one pivot or row at a time), so the results equal theirs up to the order of
-// the backward-substitution sums and the rounding of reciprocal pivots.
+// threads of the block, and the steps that must follow one another (pivots, Gram-Schmidt
+// vectors) are the only sequential parts: float64 latency and block barriers are what this
+// code costs on this part, not arithmetic.
 constexpr int SB_THREADS = 256;
-
-// L L^T = M (lower L, full k x k, upper part zero); Linv[j] = 1 / L[j][j]; false (in every
-// thread) if M is not positive definite. W is a k x k work array. One reciprocal square root per
-// pivot: FP64 division and square root are long dependent chains on this part, and the pivots
-// are sequential, so the solves below multiply by Linv instead of dividing.
-__device__ bool sb_cholesky(int k, const double *M, double *L, double *Linv, double *W, int *bad) {
-    const int t = threadIdx.x, kk = k * k;
-    if (t == 0) *bad = 0;
-    if (t < kk) { W[t] = M[t]; L[t] = 0.0; }
-    __syncthreads();
-    for (int j = 0; j < k; ++j) {
-        if (t == 0) {
-            const double d = W[j * k + j];
-            if (!(d > 0.0)) *bad = 1;
-            const double r = d > 0.0 ? rsqrt(d) : 1.0;
-            L[j * k + j] = d > 0.0 ? d * r : 1.0;
-            Linv[j] = r;
-        }
-        __syncthreads();
-        if (t > j && t < k) L[t * k + j] = W[t * k + j] * Linv[j];
-        __syncthreads();
-        if (t < kk) {
-            const int i = t / k, l = t - i * k;
-            if (i > j && l > j && l <= i) W[i * k + l] -= L[i * k + j] * L[l * k + j];
-        }
-        __syncthreads();
-    }
-    return *bad == 0;
-}
-
-// X = (L L^T)^-1 B for nrhs <= 2 KMAX right-hand sides (B, X: k x nrhs); X may alias B
-__device__ void sb_solve(int k, int nrhs, const double *L, const double *Linv, const double *B, double *X) {
-    const int t = threadIdx.x, tot = k * nrhs;
-    if (X != B)
-        for (int e = t; e < tot; e += blockDim.x) X[e] = B[e];
-    __syncthreads();
-    for (int i = 0; i < k; ++i) {          // forward: L y = b
-        if (t < nrhs) X[i * nrhs + t] *= Linv[i];
-        __syncthreads();
-        for (int e = (i + 1) * nrhs + t; e < tot; e += blockDim.x) {
-            const int r = e / nrhs, c = e - r * nrhs;
-            X[e] -= L[r * k + i] * X[i * nrhs + c];
-        }
-        __syncthreads();
-    }
-    for (int i = k - 1; i >= 0; --i) {     // backward: L^T x = y
-        if (t < nrhs) X[i * nrhs + t] *= Linv[i];
-        __syncthreads();
-        for (int e = t; e < i * nrhs; e += blockDim.x) {
-            const int r = e / nrhs, c = e - r * nrhs;
-            X[e] -= L[i * k + r] * X[i * nrhs + c];
-        }
-        __syncthreads();
-    }
-}
 
 struct SbLine {
     double N0[KMAX * KMAX], N1[KMAX * KMAX], N2[KMAX * KMAX];
     double M0[KMAX * KMAX], M1[KMAX * KMAX], M2[KMAX * KMAX];
-    double M[KMAX * KMAX], dM[KMAX * KMAX], L[KMAX * KMAX], Wk[KMAX * KMAX], Linv[KMAX];
-    double R[KMAX * 2 * KMAX];     // [k][2k]: N | dN, then M^-1 N | M^-1 dN
+    double A[2][KMAX * KMAX];              // M, reduced in place to M^-1 (two buffers)
+    double dM[KMAX * KMAX], N[KMAX * KMAX], dN[KMAX * KMAX];
     double T[KMAX * KMAX], Z[KMAX * KMAX];
+    double red[SB_THREADS / 32][3];
     double out[4];
     int bad;
 };
 
 // Omega(lam) = Tr[M^-1 N]/2 and dOmega/dlam = Tr[M^-1 dN - M^-1 dM M^-1 N]/2 with
-// M = M0 + lam M1 + lam^2 M2, N likewise; false (in every thread) if M is not positive definite
+// M = M0 + lam M1 + lam^2 M2, N likewise; false (in every thread) if M is not positive definite.
+// M^-1 by Gauss-Jordan elimination without pivoting, one pivot per step with every element
+// updated at once: for a symmetric M the pivots are those of its L D L^T factorisation, so all
+// are positive exactly when M is positive definite. The traces are element-wise sums
+// (Tr[A B] = sum_ij A_ij B_ji), so only W = M^-1 N and U = M^-1 dM are formed:
+// Omega = Tr[W]/2, dOmega = (sum_ij Minv_ij dN_ji - sum_ij U_ij W_ji)/2.
 __device__ bool sb_sum_functional(int k, SbLine &s, double lam, double *f, double *d) {
-    const int t = threadIdx.x, kk = k * k, k2 = 2 * k;
+    const int t = threadIdx.x, kk = k * k;
+    const int i = t < kk ? t / k : 0, j = t < kk ? t - i * k : 0;
     if (t < kk) {
-        const int i = t / k, j = t - i * k;
-        s.M[t] = s.M0[t] + lam * s.M1[t] + lam * lam * s.M2[t];
+        s.A[0][t] = s.M0[t] + lam * s.M1[t] + lam * lam * s.M2[t];
         s.dM[t] = s.M1[t] + 2.0 * lam * s.M2[t];
-        s.R[i * k2 + j] = s.N0[t] + lam * s.N1[t] + lam * lam * s.N2[t];
-        s.R[i * k2 + k + j] = s.N1[t] + 2.0 * lam * s.N2[t];
+        s.N[t] = s.N0[t] + lam * s.N1[t] + lam * lam * s.N2[t];
+        s.dN[t] = s.N1[t] + 2.0 * lam * s.N2[t];
     }
     __syncthreads();
-    if (!sb_cholesky(k, s.M, s.L, s.Linv, s.Wk, &s.bad)) return false;
-    sb_solve(k, k2, s.L, s.Linv, s.R, s.R);         // W = M^-1 N, X = M^-1 dN
-    if (t < kk) {                           // T = dM W
-        const int i = t / k, j = t - i * k;
-        double acc = 0.0;
-        for (int p = 0; p < k; ++p) acc += s.dM[i * k + p] * s.R[p * k2 + j];
-        s.T[t] = acc;
+    int cur = 0;
+    for (int p = 0; p < k; ++p) {
+        const double *a = s.A[cur];
+        const double piv = a[p * k + p];
+        if (!(piv > 0.0)) {                 // the same value in every thread
+            __syncthreads();
+            return false;
+        }
+        if (t < kk) {
+            const double r = 1.0 / piv;
+            double v;
+            if (i == p) v = (j == p) ? r : a[t] * r;
+            else if (j == p) v = -a[t] * r;
+            else v = a[t] - a[i * k + p] * a[p * k + j] * r;
+            s.A[cur ^ 1][t] = v;
+        }
+        cur ^= 1;
+        __syncthreads();
+    }
+    const double *mi = s.A[cur];
+    if (t < kk) {
+        double w = 0.0, u = 0.0;
+        for (int q = 0; q < k; ++q) {
+            w += mi[i * k + q] * s.N[q * k + j];
+            u += mi[i * k + q] * s.dM[q * k + j];
+        }
+        s.T[t] = w;
+        s.Z[t] = u;
     }
     __syncthreads();
-    sb_solve(k, k, s.L, s.Linv, s.T, s.Z);          // Z = M^-1 dM M^-1 N
+    double v0 = 0.0, v1 = 0.0, v2 = 0.0;
+    if (t < kk) {
+        v0 = i == j ? s.T[t] : 0.0;
+        v1 = mi[t] * s.dN[j * k + i];
+        v2 = s.Z[t] * s.T[j * k + i];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+        v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+        v2 += __shfl_xor_sync(0xffffffffu, v2, o);
+    }
+    if ((t & 31) == 0) {
+        s.red[t >> 5][0] = v0;
+        s.red[t >> 5][1] = v1;
+        s.red[t >> 5][2] = v2;
+    }
+    __syncthreads();
     if (t == 0) {
         double tw = 0.0, tx = 0.0, tz = 0.0;
-        for (int i = 0; i < k; ++i) {
-            tw += s.R[i * k2 + i];
-            tx += s.R[i * k2 + k + i];
-            tz += s.Z[i * k + i];
+        for (int w = 0; w < (kk + 31) / 32; ++w) {
+            tw += s.red[w][0];
+            tx += s.red[w][1];
+            tz += s.red[w][2];
         }
         s.out[0] = 0.5 * tw;
         s.out[1] = 0.5 * (tx - tz);
@@ -1031,10 +1166,30 @@ void gram_multi(cudaStream_t st, const T *X, long long sx, int nx, int nset, con
         go.g[q] = q < nset ? G[q] : G[0];
     }
     ys.per = per;
-    const int slices = trace_slices(len, TRACE_SLICES, 2 * TRACE_SLICES);
     constexpr int VW = sizeof(T) == 4 ? 4 : 2;   // 16-byte loads
     bool vec = len % VW == 0 && sx % VW == 0 && sy % VW == 0 && reinterpret_cast<uintptr_t>(X) % 16 == 0;
     for (int q = 0; q < nset; ++q) vec = vec && reinterpret_cast<uintptr_t>(Y[q]) % 16 == 0;
+    const int gx = (nx + GQ - 1) / GQ, gy = (ny + GQ - 1) / GQ;
+    if (vec && nx + ny <= 256 * GMAXT / 16 && gx * gy <= 128) {
+        // every row read once (all pairs of a slice in one block)
+        constexpr int GC = gram_chunk<T>();
+        const long long chunks = (len + GC - 1) / GC;
+        const long long want = std::max<long long>(1, std::min<long long>(2 * TRACE_SLICES, (chunks + 15) / 16));
+        const long long per_slice = (chunks + want - 1) / want * GC;
+        const int slices = (int)((len + per_slice - 1) / per_slice);
+        const int RX = GQ * gx, RY = GQ * gy;
+        const size_t smem = std::max((size_t)GST * (RX + RY) * gram_row<T>() * sizeof(T),
+                                     (size_t)GQ * GQ * 128 * sizeof(double));
+        if (smem > 48 * 1024)
+            check(cudaFuncSetAttribute(gram_rows_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                  "gram_rows smem");
+        gram_rows_kernel<T><<<slices, 256, smem, st>>>(X, sx, nx, ys, sy, ny, len, per_slice, RX, RY, scratch, pairs);
+        check_launch("gram_rows_kernel");
+        gram_final_multi<<<(pairs + 7) / 8, 256, 0, st>>>(scratch, slices, pairs, ny, per, go);
+        check_launch("gram_final");
+        return;
+    }
+    const int slices = trace_slices(len, TRACE_SLICES, 2 * TRACE_SLICES);
     const int ti = (nx + TI - 1) / TI;
     if (vec) {
         const int tj = (ny + 3) / 4;
