@@ -461,7 +461,8 @@ tddft_status tddft_state_stats(const tddft_state *st, int32_t *iters, int32_t *f
  * gemm, response_density, potential_integrals, fft_poisson_fxc, trace, vector, small_fp64.
  * tddft_profile_read synchronises and fills up to cap entries (count = entries written). flops
  * and bytes are algorithmic counts (for response_density and potential_integrals:
- * 2 * pair_points per state and the nonzero table values plus the grids; for gemm 2MNK). */
+ * 2 * pair_points per state and the nonzero table values plus the grids; for gemm 2MNK, and in
+ * the truncated form 2 n_I n_K n_J summed over the atom-block triples that contribute). */
 typedef struct {
     char name[32];
     int64_t launches;

@@ -68,6 +68,25 @@ def test_options_struct_layout_matches_the_header(lib_path, tmp_path):
     assert got[-1] == ctypes.sizeof(tddft._Options)
 
 
+
+@pytest.mark.parametrize("struct", ["tddft_options", "tddft_tuning_entry", "tddft_stage_stats"])
+def test_struct_layouts_match_the_header(lib_path, tmp_path, struct):
+    # every ctypes mirror of a boundary struct has the layout the C compiler gives the header
+    import ctypes
+    from paper_1507_08157_gb300 import tddft
+    mirror = {"tddft_options": tddft._Options, "tddft_tuning_entry": tddft.TuningEntry,
+              "tddft_stage_stats": tddft.StageStats}[struct]
+    src = tmp_path / "layout.c"
+    fields = [f for f, _ in mirror._fields_]
+    body = "".join(f'printf("%zu ", offsetof({struct}, {f}));' for f in fields)
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "tddft.h"\n'
+                   'int main(void) { ' + body + f'printf("%zu", sizeof({struct})); return 0; }}\n')
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert got[:-1] == [getattr(mirror, f).offset for f in fields]
+    assert got[-1] == ctypes.sizeof(mirror)
+
 def test_product_code_does_not_import_the_oracle():
     pkg = os.path.join(ROOT, "paper_1507_08157_gb300")
     for dirpath, _, files in os.walk(pkg):
