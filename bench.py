@@ -350,6 +350,45 @@ def learned_vs_plain(tddft, sy, torch, stream, k=10, train_atoms=16, eval_atoms=
             "max_domega_learned_vs_plain_Ha": dw, "train_s": train_s, "train_loss": [l0, l1]}
 
 
+# DRAM bytes (read + write) per tc_gemm_kernel launch in a timed PCG step of the default workload,
+# mean over the step's 16 launches, from one capture of this build:
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none
+#       -k regex:tc_gemm_kernel --csv python bench.py --steps 1 --warmup 1 --no-cpu-baseline
+#       --no-time-to-k --no-iter-line --no-autotune
+GEMM_TRAFFIC_PER_LAUNCH = 82.0e6
+
+
+def stage_rooflines(prof, peaks, args):
+    """Per stage of the timed steps: the time its algorithmic work takes at the measured peaks
+    (roof_ms = the larger of flops at the stage's compute peak and bytes at the HBM copy rate),
+    against the measured time; and the same summed over the stages that have a roof (the small
+    float64 algebra has none: it is latency, not throughput)."""
+    bf16 = peaks.get("bf16_tflops_sustained", 1700.0)
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    mixed = args.precision == "mixed"
+    compute_peak = {"gemm": bf16 * 1.1 / 2.25 if mixed else 1.25,
+                    "response_density": bf16 if mixed else 1.25,
+                    "potential_integrals": bf16 if mixed else 1.25}
+    out, roof_sum, ms_sum = {}, 0.0, 0.0
+    for name, (launches, ms_, flops, bytes_) in prof.items():
+        if not launches or name == "small_fp64":
+            continue
+        t_flop = flops / (compute_peak[name] * 1e12) * 1e3 if name in compute_peak else 0.0
+        t_byte = bytes_ / (hbm * 1e9) * 1e3
+        roof_ms = max(t_flop, t_byte)
+        out[name] = {"ms": round(ms_, 4), "roof_ms": round(roof_ms, 4), "frac": round(roof_ms / max(ms_, 1e-12), 4),
+                     "bound": "tensor" if t_flop >= t_byte and name in compute_peak else "hbm"}
+        roof_sum += roof_ms
+        ms_sum += ms_
+    small = prof.get("small_fp64", (0, 0.0))[1]
+    summed = {"roof_ms": round(roof_sum, 4), "measured_ms": round(ms_sum, 4),
+              "frac": round(roof_sum / max(ms_sum, 1e-12), 4), "small_fp64_ms_excluded": round(small, 4),
+              "peaks": {"tf32_tflops": round(bf16 * 1.1 / 2.25, 1), "f16_tflops": bf16, "hbm_gbs": hbm},
+              "note": "gemm flops are 2MNK of each product (the float32-accurate split issues three MMAs); "
+                      "float64 stages against the nominal 1.25 TFLOP/s"}
+    return out, summed
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -479,6 +518,11 @@ def run_ours(args):
     gpu_launches = sum(v[0] for v in prof.values()) + 4 * prof.get("fft_poisson_fxc", (0,))[0]
     stages = {n: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / max(ms, 1e-9), 4)}
               for n, v in prof.items() if v[0]}
+    stage_roofs, summed = stage_rooflines(prof, peaks, args)
+    if roof.get("kernel") == "gemm" and roof.get("bound") == "tensor":
+        roof["traffic"] = GEMM_TRAFFIC_PER_LAUNCH
+        roof["traffic_note"] = ("dram__bytes_read.sum + dram__bytes_write.sum per tc_gemm_kernel launch, mean "
+                                "over the 16 launches of one timed PCG step (one ncu capture of this build)")
 
     # the same PCG steps with the paper's preconditioner (inner CG on Eq. precond to 1e-4), when
     # the timed steps used another one: both are reported
@@ -528,7 +572,8 @@ def run_ours(args):
                            "l2": "inputs larger than L2 (function tables > 1 GB per pass)",
                            "applies_per_step": applies / args.steps},
                 "e2e": e2e, "apply_only": {"value": apply_only, "unit": UNIT},
-                "roofline": roof, "stages": stages, "gpu_launches": int(gpu_launches),
+                "roofline": roof, "stages": stages, "stage_rooflines": stage_roofs,
+                "summed_roofline": summed, "gpu_launches": int(gpu_launches),
                 "clocks": {k_: clock[k_] for k_ in ("sm_mhz", "sm_max_mhz", "reasons")},
                 "time_to_k": time_to_k, "precond_iter": iter_line, "autotune": tuning,
                 "omega_last": [float(x) for x in om], "resid_last": [float(x) for x in res]}
@@ -603,6 +648,9 @@ def run_batched(args):
     per = [{"atoms": a, "k": k, "iters": int(iters[j]), "status": int(status[j]),
             "omega_min": float(res[j][0][0]), "resid_max": float(np.max(res[j][1]))}
            for j, (i, a, k) in enumerate(meta)]
+    for j, p_ in enumerate(per):
+        if p_["status"] != tddft.OK:
+            p_["error"] = states[j].ctx.last_error()
     line = {"metric": "systems solved per second (batched, uneven sizes)", "value": len(states) / wall,
             "unit": "systems/s", "n_gpus": 1, "higher_is_better": True, "impl": "ours",
             "dtype": "f32", "data": "synthetic",
@@ -631,9 +679,10 @@ def run_scaling(args):
     Sec. IV (tddft_create_sparse: cluster-blocked matrices, block-sparse tensor-core products).
     Per size: device-resident applies timed with CUDA events after warm-up, the per-stage times of
     the library's profiler, and the time per unit of algorithmic work W (flops: 2 k pair_points
-    for each grid contraction, the block products' padded 2MNK), so that time / W stays flat when
-    the time grows with the work; the line ends with the fitted exponents of time against N and
-    of W against N."""
+    for each grid contraction, 2 n_I n_K n_J over the atom-block triples that contribute to each
+    block-sparse product), so that time / W stays flat when the time grows with the work; the line
+    ends with the fitted exponents of time, of the grid stages' time and of W against N, and of
+    time against W."""
     import torch
     from paper_1507_08157_gb300 import synthetic as sy
     from paper_1507_08157_gb300 import tddft

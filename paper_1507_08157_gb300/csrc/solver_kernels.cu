@@ -1180,9 +1180,14 @@ void gram_multi(cudaStream_t st, const T *X, long long sx, int nx, int nset, con
         const int RX = GQ * gx, RY = GQ * gy;
         const size_t smem = std::max((size_t)GST * (RX + RY) * gram_row<T>() * sizeof(T),
                                      (size_t)GQ * GQ * 128 * sizeof(double));
-        if (smem > 48 * 1024)
-            check(cudaFuncSetAttribute(gram_rows_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+        // the attribute is set once, to the most any launch asks for: contexts on other host
+        // threads launch this kernel concurrently, and a per-launch value would race with them
+        static const bool attr = []() {
+            check(cudaFuncSetAttribute(gram_rows_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),
                   "gram_rows smem");
+            return true;
+        }();
+        (void)attr;
         gram_rows_kernel<T><<<slices, 256, smem, st>>>(X, sx, nx, ys, sy, ny, len, per_slice, RX, RY, scratch, pairs);
         check_launch("gram_rows_kernel");
         gram_final_multi<<<(pairs + 7) / 8, 256, 0, st>>>(scratch, slices, pairs, ny, per, go);

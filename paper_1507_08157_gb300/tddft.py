@@ -473,6 +473,10 @@ class Context:
         if rc != OK:
             raise TddftError(rc, self._lib.tddft_last_error(self._ctx).decode())
 
+    def last_error(self):
+        """The message of the context's last failed call (tddft_last_error)."""
+        return self._lib.tddft_last_error(self._ctx).decode()
+
     def _out(self, like, shape):
         if like is not None and hasattr(like, "data_ptr"):
             import torch

@@ -70,3 +70,26 @@ def test_batch_refuses_bad_arguments(tddft, systems):
         tddft.solve_batch([st, st2])         # one context twice
     res, _, status = tddft.solve_batch([st])
     assert status[0] in (tddft.OK, tddft.E_NOT_CONVERGED)
+
+
+RECIPES_K = [sy.Recipe(natoms=4, cell_ang=11.0, ngrid=32, radius_ang=4.0, seed=41),
+             sy.Recipe(natoms=5, cell_ang=11.0, ngrid=32, radius_ang=4.0, seed=42),
+             sy.Recipe(natoms=4, cell_ang=12.0, ngrid=36, radius_ang=4.0, seed=43),
+             sy.Recipe(natoms=6, cell_ang=12.0, ngrid=36, radius_ang=4.0, seed=44),
+             sy.Recipe(natoms=5, cell_ang=12.0, ngrid=36, radius_ang=4.0, seed=45),
+             sy.Recipe(natoms=4, cell_ang=11.0, ngrid=32, radius_ang=4.0, seed=46)]
+KS_K = [6, 5, 8, 7, 5, 6]   # each k ends at a gap of the spectrum (>= 6 % to the next state)
+
+
+def test_batch_of_many_states_runs_concurrently(tddft):
+    # 5 to 8 states per system: the trace kernels then take more than 48 KB of shared memory, a
+    # launch attribute that must not race between the host threads of the batch (FP64, so that
+    # the eigenvalues are checked at the FP64 accuracy)
+    systems = [sy.generate(r) for r in RECIPES_K]
+    ctxs = tddft.create_batch(systems, precision="fp64", tol=1e-8, max_iter=400)
+    states = [c.state(sy.initial_guess(s, k, 20 + i)) for i, (c, s, k) in enumerate(zip(ctxs, systems, KS_K))]
+    res, iters, status = tddft.solve_batch(states, nthreads=6)
+    assert list(status) == [tddft.OK] * len(systems), [(st, c.last_error()) for st, c in zip(status, ctxs)]
+    for (om, r), s, k in zip(res, systems, KS_K):
+        ref = casida.Casida(s).omega_symmetric()
+        assert np.max(np.abs(om - ref[:k])) <= 1e-6
