@@ -485,10 +485,16 @@ __global__ void __launch_bounds__(256) fft_strided(Plan pl, typename C2<T>::t *_
 
 // ------------------------------------------------------------------------------------------------
 // LDA kernel
+// f_xc(n) = d^2(n eps_xc)/dn^2 (Slater exchange, PW92 correlation at zeta = 0), derived here in
+// the variable x = rs^(1/2) = (3 / (4 pi n))^(1/6), in which PW92's denominator is the quartic
+// Q(x) = 2A (b1 x + b2 x^2 + b3 x^3 + b4 x^4) and eps_c = -2A (1 + a1 x^2) ln(1 + 1/Q). With
+// dx/dn = -x / (6n), d^2(n eps)/dn^2 = x (x eps'' - 5 eps') / (36 n) (primes: d/dx); exchange,
+// n eps_x = -(3/4)(3/pi)^(1/3) n^(4/3), gives -(4/9)(3/4)(3/pi)^(1/3) n^(-2/3).
 __global__ void fxc_kernel(const double *__restrict__ n0, double *__restrict__ out, long long npts) {
     const double A = 0.031091, a1 = 0.21370;
     const double b1 = 7.5957, b2 = 3.5876, b3 = 1.6382, b4 = 0.49294;
     const double pi = 3.14159265358979323846;
+    const double cx = 0.75 * cbrt(3.0 / pi);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npts;
          i += (long long)gridDim.x * blockDim.x) {
         const double n = n0[i];
@@ -496,25 +502,17 @@ __global__ void fxc_kernel(const double *__restrict__ n0, double *__restrict__ o
             out[i] = 0.0;
             continue;
         }
-        // exchange: d^2/dn^2 of -(3/4)(3/pi)^(1/3) n^(4/3)
-        const double c13 = cbrt(3.0 / pi);
-        const double fx = -c13 / (3.0 * cbrt(n * n));
-        // correlation (PW92, zeta = 0, p = 1)
-        const double rs = cbrt(3.0 / (4.0 * pi * n));
-        const double sq = sqrt(rs);
-        const double q0 = -2.0 * A * (1.0 + a1 * rs);
-        const double dq0 = -2.0 * A * a1;
-        const double q1 = 2.0 * A * (b1 * sq + b2 * rs + b3 * rs * sq + b4 * rs * rs);
-        const double dq1 = 2.0 * A * (0.5 * b1 / sq + b2 + 1.5 * b3 * sq + 2.0 * b4 * rs);
-        const double d2q1 = 2.0 * A * (-0.25 * b1 / (rs * sq) + 0.75 * b3 / sq + 2.0 * b4);
-        const double lg = log1p(1.0 / q1);
-        const double den = q1 * q1 + q1;
-        const double dlg = -dq1 / den;
-        const double d2lg = -d2q1 / den + dq1 * dq1 * (2.0 * q1 + 1.0) / (den * den);
-        const double de = dq0 * lg + q0 * dlg;
-        const double d2e = 2.0 * dq0 * dlg + q0 * d2lg;
-        const double fc = -(rs / (3.0 * n)) * ((2.0 / 3.0) * de - (rs / 3.0) * d2e);
-        out[i] = fx + fc;
+        const double fx = -(4.0 / 9.0) * cx / cbrt(n * n);
+        const double x = sqrt(cbrt(3.0 / (4.0 * pi * n)));
+        const double Q = 2.0 * A * x * (b1 + x * (b2 + x * (b3 + x * b4)));
+        const double Q1 = 2.0 * A * (b1 + x * (2.0 * b2 + x * (3.0 * b3 + x * 4.0 * b4)));
+        const double Q2 = 2.0 * A * (2.0 * b2 + x * (6.0 * b3 + x * 12.0 * b4));
+        const double P0 = -2.0 * A * (1.0 + a1 * x * x), P1 = -4.0 * A * a1 * x, P2 = -4.0 * A * a1;
+        const double qq = Q * (Q + 1.0);
+        const double L0 = log1p(1.0 / Q), L1 = -Q1 / qq, L2 = -Q2 / qq + Q1 * Q1 * (2.0 * Q + 1.0) / (qq * qq);
+        const double e1 = P1 * L0 + P0 * L1;
+        const double e2 = P2 * L0 + 2.0 * P1 * L1 + P0 * L2;
+        out[i] = fx + x * (x * e2 - 5.0 * e1) / (36.0 * n);
     }
 }
 
