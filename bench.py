@@ -65,6 +65,7 @@ def parse():
                     help="instead of the default line: solve this many uneven systems at once (systems/s)")
     ap.add_argument("--batch-max-atoms", type=int, default=300)
     ap.add_argument("--batch-seed", type=int, default=3)
+    ap.add_argument("--batch-tol", type=float, default=1e-5, help="residual (Ha) each batched system converges to")
     ap.add_argument("--batch-workers", type=int, default=8, help="processes generating the systems")
     ap.add_argument("--batch-pool-atoms", type=int, default=150,
                     help="systems from this size up are generated in the main process (pooled table sums)")
@@ -286,6 +287,32 @@ def run_reference(args):
             "timed_s_per_step": float(np.mean(timed)),
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def mixed_time_to_k(tddft, sy, torch, stream, s, k, autotune, tol=1e-5):
+    """Time to the lowest k states at a 1e-5 Ha residual in mixed precision on the benchmark's
+    system, from the seeded random start, with the exact preconditioner and with the paper's
+    inner CG (Eq. precond to 1e-4). The response kernels are not truncated here: at the
+    throughput workload's 12 A cutoff the synthetic system's PCG stalls near 1e-2 Ha (its density
+    kernels decay slowly), so there is no converged answer to time."""
+    import dataclasses
+    su = dataclasses.replace(s, kernel_cutoff=0.0)
+    out = {"workload": "the benchmark's chromophore-140 system, response kernels untruncated", "k": k,
+           "precision": "mixed", "tol_Ha": tol}
+    for pre in ("exact", "iter"):
+        c = tddft.Context(su, precision="mixed", stream=stream.cuda_stream, tol=tol, max_iter=600, precond=pre)
+        if autotune:
+            c.autotune(k)
+        st = c.state(sy.initial_guess(su, k, 0))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        om, res, it, rc = st.solve()
+        torch.cuda.synchronize()
+        out[pre] = {"s": time.perf_counter() - t0, "iterations": int(it), "status": int(rc),
+                    "resid_max": float(np.max(res)), "omega": [float(x) for x in om]}
+        st.close()
+        c.close()
+    return out
 
 
 def learned_vs_plain(tddft, sy, torch, stream, k=10, train_atoms=16, eval_atoms=24, tol=1e-5):
@@ -556,8 +583,10 @@ def run_ours(args):
     # time to k states at 1e-5 Ha, learned vs plain PCG (FP64): the model is trained on rows from
     # plain-PCG runs on two systems of the small workload's recipe and density, then both solvers
     # start from the same vectors on an unseen, larger system
-    time_to_k = None
+    time_to_k = time_to_k_mixed = None
     if rank == 0 and not args.no_time_to_k:
+        if args.config == "chromophore" and args.precision == "mixed":
+            time_to_k_mixed = mixed_time_to_k(tddft, sy, torch, stream, s, k, tuning is not None)
         time_to_k = learned_vs_plain(tddft, sy, torch, stream, train_atoms=args.learned_train_atoms,
                                      eval_atoms=args.learned_eval_atoms)
 
@@ -575,7 +604,8 @@ def run_ours(args):
                 "roofline": roof, "stages": stages, "stage_rooflines": stage_roofs,
                 "summed_roofline": summed, "gpu_launches": int(gpu_launches),
                 "clocks": {k_: clock[k_] for k_ in ("sm_mhz", "sm_max_mhz", "reasons")},
-                "time_to_k": time_to_k, "precond_iter": iter_line, "autotune": tuning,
+                "time_to_k": time_to_k, "time_to_k_mixed": time_to_k_mixed, "precond_iter": iter_line,
+                "autotune": tuning,
                 "omega_last": [float(x) for x in om], "resid_last": [float(x) for x in res]}
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_oracle_sample(s)
@@ -594,8 +624,8 @@ def run_batched(args):
     """Many independent systems of uneven size solved at once (tddft_create_batch /
     tddft_solve_batch): atom counts log-uniform in [20, max], atoms in a cube at 0.1 atoms / A^3
     with 2R + 1 A of vacuum, 0.25 A grids, 4 phi + 4 chi (s, p) per atom of 7 A radius, 1 to 8
-    states each. Mixed precision, converged to a residual of 3e-4 Ha (float32 operands floor the
-    residual near 1e-4 Ha; the energy error is quadratic in it). The systems are generated on the
+    states each. Mixed precision, converged to the method's 1e-5 Ha residual (--batch-tol) within
+    600 iterations. The systems are generated on the
     host in a spawn process pool, a chunk at a time, before any of them is solved; the timed
     region is the concurrent solve of all systems (wall clock, device synchronised on both
     sides), from states already created."""
@@ -609,7 +639,7 @@ def run_batched(args):
     torch.cuda.set_device(0)
     from paper_1507_08157_gb300 import tddft
     tddft.load()
-    tol = 3e-4
+    tol = args.batch_tol
     ctxs, states, meta = [], [], []
     t_gen = t_create = 0.0
     # large systems are generated one at a time in this process, whose generator spreads their
@@ -626,7 +656,7 @@ def run_batched(args):
             else:
                 systems = pool.map(_generate, [recs[i][0] for i in chunk])
             t1 = time.perf_counter()
-            cs = tddft.create_batch(systems, precision="mixed", tol=tol, max_iter=400, precond=args.precond)
+            cs = tddft.create_batch(systems, precision="mixed", tol=tol, max_iter=600, precond=args.precond)
             for i, c, sys_ in zip(chunk, cs, systems):
                 k = recs[i][1]
                 states.append(c.state(sy.initial_guess(sys_, k, i)))
@@ -658,7 +688,7 @@ def run_batched(args):
                                    f"{max(m[1] for m in meta)} atoms (log-uniform, seed {args.batch_seed}), "
                                    "0.1 atoms/A^3 cube + 2R + 1 A vacuum, 0.25 A grid, 4 phi + 4 chi per atom, "
                                    f"7 A radius, 1-8 states, mixed precision, {args.precond} preconditioner, "
-                                   "residual 3e-4 Ha",
+                                   f"residual {tol:g} Ha, at most 600 iterations",
                        "systems": len(states), "atoms_total": int(sum(m[1] for m in meta)),
                        "states_total": int(sum(m[2] for m in meta)), "host_threads": 16},
             "wall_s": wall, "converged": ok, "iters_total": int(np.sum(iters)),

@@ -1,10 +1,8 @@
 """Config 2's accuracy statement: the lowest 10 excitations of chromophore-140 (140 atoms, 30 A
-cell, 120^3 grid, 4 phi + 9 chi per atom, 8 A radius) converged on the GPU in mixed precision
-(float32 / float16 grid work on the tensor cores, float64 traces and small algebra) and in FP64
-mode, from the same random start, agree to 1e-5 Ha. The response kernels are not truncated here:
-with the 12 A cutoff of the benchmark the truncated PCG of the dense form stalls near a 3e-3 Ha
-residual on this system (the synthetic density kernels decay slowly), so no converged energies
-exist to compare there.
+cell, 120^3 grid, 4 phi + 9 chi per atom, 8 A radius) converged on the GPU to a 1e-5 Ha residual
+in mixed precision (float32 / float16 grid work on the tensor cores, float64 traces and small
+algebra) and in FP64 mode agree to 1e-5 Ha. The response kernels are not truncated here (the
+benchmark's 12 A cutoff changes the eigenproblem; its own convergence is reported by the bench).
 
 How the oracle pins this size: the FP64 oracle cannot iterate a 140-atom system (minutes per
 operator application), so the pins are (1) the operator in the launch configuration of the
@@ -13,8 +11,7 @@ benchmark against the oracle, element by element and at sampled points (test_gpu
 (test_gpu_solver.py), and (3) here, the FP64 GPU mode as the reference of the mixed mode and the
 pairing check of the converged Ritz pairs (each half of the Tsiper numerator equals omega).
 
-The mixed solve runs to its residual floor (3e-4 Ha); the energy error is second order in the
-residual. The FP64 solve starts from the mixed solution's q vectors, which shortens it.
+The FP64 solve starts from the mixed solution's q vectors, which shortens it.
 """
 import dataclasses
 
@@ -48,10 +45,11 @@ def chromo():
 def test_lowest_ten_mixed_against_fp64(tddft, chromo):
     s = chromo
     Y0 = sy.initial_guess(s, K, 0)
-    cm = tddft.Context(s, precision="mixed", precond="exact", tol=3e-4, max_iter=400)
+    cm = tddft.Context(s, precision="mixed", precond="exact", tol=1e-5, max_iter=400)
     sm = cm.state(Y0)
     om_m, res_m, it_m, rc_m = sm.solve()
     assert rc_m == tddft.OK, (rc_m, it_m, res_m)
+    assert np.max(res_m) <= 1e-5
     q = sm.get()["Pq"]
     sm.close()
     cm.close()
