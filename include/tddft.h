@@ -451,8 +451,10 @@ tddft_status tddft_set_mlp(tddft_ctx *ctx, tddft_mlp *m);
  * count returns INVALID. */
 tddft_status tddft_samples(tddft_ctx *ctx, tddft_state *st, int64_t cap, float *X, float *T, float *w,
                            int64_t *count);
-/* Counters of a state: PCG steps taken, steps where the learned direction fell back to the CG
- * solve, and inner CG iterations summed over steps (any pointer may be NULL). */
+/* Counters of a state: PCG steps taken, steps whose preconditioned direction was not a descent
+ * direction and fell back (the learned map to the CG solve; in the truncated form, the inner CG
+ * to the search gradient itself), and inner CG iterations summed over steps (any pointer may be
+ * NULL). */
 tddft_status tddft_state_stats(const tddft_state *st, int32_t *iters, int32_t *fallbacks,
                                int64_t *inner_iters);
 

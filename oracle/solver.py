@@ -309,6 +309,12 @@ class PCG:
         X, s = feat.rows(hp, hq)
         return X, feat.targets(zp, zq, s, hp, hq), feat.weights(s, self.k)
 
+    def gradient_when_not_descent(self):
+        """Whether a non-descent preconditioned direction is replaced by the search gradient
+        (no: the dense form's preconditioner is positive definite on the conduction x valence
+        space, where its CG stays)."""
+        return False
+
     def gdot(self, gp, gq, zp, zq, Zp, Zq):
         """sum_i <g_i, Z_i>: the slope of the sum functional along Z (z its L-space preimage, not
         needed here)."""
@@ -333,6 +339,15 @@ class PCG:
             Zp = np.array([op.project(X) for X in zp])
             Zq = np.array([op.project(X) for X in zq])
             gz = self.gdot(gp, gq, zp, zq, Zp, Zq)
+            if self.learned is None and not gz > 0.0 and self.gradient_when_not_descent():
+                # the preconditioned direction does not descend: the step takes the search
+                # gradient itself (the form's reading of Eq. precond, see TruncatedPCG)
+                self.fallbacks += 1
+                m = op.mask if self.trunc else 1.0
+                zp, zq = m * hp, m * hq
+                Zp = np.array([op.project(X) for X in zp])
+                Zq = np.array([op.project(X) for X in zq])
+                gz = self.gdot(gp, gq, zp, zq, Zp, Zq)
         restart = self.prev is None or self.it % self.restart_every == 0 or self.flipped
         beta = 0.0
         if not restart:

@@ -121,6 +121,15 @@ class TruncatedPCG(PCG):
             raise ValueError("the truncated form has the inner-CG preconditioner or none")
         super().__init__(op, Y0, **kw)
 
+    def gradient_when_not_descent(self):
+        """With every product cut to the pattern and P^c, P^v truncated, the inner CG's operator
+        T(M_c G) - T(G M_v) need not be positive definite on the pattern (the truncated P^c is no
+        longer a projector, and H^chi's large eigenvalues magnify the difference), so the CG can
+        stop on non-positive curvature with a result that does not descend. The paper's
+        preconditioner is only meant to speed up the descent (Sec. III B), so such a step takes
+        the search gradient itself (counted in fallbacks)."""
+        return self.precond == "iter"
+
     def gdot(self, gp, gq, zp, zq, Zp, Zq):
         """sum_i <G_L,i, z_i>_F, the slope in L space."""
         return float(sum(np.sum(self.GLp[i] * zp[i]) + np.sum(self.GLq[i] * zq[i]) for i in range(self.k)))

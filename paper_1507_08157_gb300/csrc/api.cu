@@ -1761,9 +1761,12 @@ void update(tddft_ctx *c, tddft_state *S) {
     cudaStream_t st = c->st;
     // preconditioned gradient in the search variables
     const T *h = search_gradient<T>(c, S);
-    auto precondition_and_dots = [&](bool learned) {
-        if (learned) learned_precondition<T>(c, S, h, B.z);
-        else precondition<T>(c, S, h, B.z);
+    // z from the learned map (mode 1), the preconditioner of the options (0), or the search
+    // gradient itself (2)
+    auto precondition_and_dots = [&](int mode) {
+        if (mode == 1) learned_precondition<T>(c, S, h, B.z);
+        else if (mode == 0) precondition<T>(c, S, h, B.z);
+        else check(cudaMemcpyAsync(B.z, h, tot * sizeof(T), cudaMemcpyDeviceToDevice, st), "copy z");
         if (c->trunc) mask_mul<T>(st, B.z, I.mask, len, k2);
         sandwich_x<T>(c, I, k2, SP_R, B.z, B.Z, B.tmp);     // Z = P^c S z S P^v (Eq. auxiliary)
         // Polak-Ribiere over the set
@@ -1778,16 +1781,28 @@ void update(tddft_ctx *c, tddft_state *S) {
         }
     };
     const bool learned = c->opt.precond == TDDFT_PRECOND_LEARNED;
-    precondition_and_dots(learned);
-    if (learned) {
-        // the CG solve stands in when -z is not a descent direction (<g, Z> summed <= 0)
+    auto slope_sum = [&]() {
         check(cudaMemcpyAsync(S->host, B.dvec, k2 * sizeof(double), cudaMemcpyDeviceToHost, st), "D2H gz");
         check(ctx_sync(c), "sync gz");
         double gz = 0.0;
         for (int i = 0; i < k2; ++i) gz += S->host[i];
-        if (!(gz > 0.0)) {
+        return gz;
+    };
+    precondition_and_dots(learned ? 1 : 0);
+    if (learned) {
+        // the CG solve stands in when -z is not a descent direction (<g, Z> summed <= 0)
+        if (!(slope_sum() > 0.0)) {
             S->fallbacks += 1;
-            precondition_and_dots(false);
+            precondition_and_dots(0);
+        }
+    } else if (c->sparse && c->opt.precond == TDDFT_PRECOND_ITER) {
+        // truncated form: with every product cut to the pattern, and P^c, P^v truncated, the
+        // inner CG's operator need not be positive definite, and its result need not be a
+        // descent direction (<G_L, z> summed <= 0, the CG stopped on non-positive curvature);
+        // that step then takes the search gradient itself
+        if (!(slope_sum() > 0.0)) {
+            S->fallbacks += 1;
+            precondition_and_dots(2);
         }
     }
     const int restart = (S->it == 0 || S->it % std::max(1, c->opt.restart_every) == 0) ? 1 : 0;

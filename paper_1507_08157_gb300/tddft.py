@@ -671,7 +671,8 @@ class State:
         return buf.raw[:n.value]
 
     def stats(self):
-        """(PCG steps, learned-to-CG fallbacks, inner CG iterations)."""
+        """(PCG steps, preconditioner fallbacks (learned to CG, truncated-form CG to the gradient),
+        inner CG iterations)."""
         a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
         self.ctx._check(self.ctx._lib.tddft_state_stats(self._st, ctypes.byref(a), ctypes.byref(b),
                                                         ctypes.byref(c)))

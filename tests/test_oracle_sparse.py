@@ -139,3 +139,27 @@ def test_truncation_error_shrinks_with_cutoff(four):
         errs.append(np.max(np.abs(fq - fq_ref)))
     assert max(errs[2:]) <= 1e-12 * np.max(np.abs(fq_ref))
     assert errs[0] > errs[1] > 1e3 * errs[2]
+
+
+def test_non_descent_preconditioner_falls_back_to_the_gradient(four, monkeypatch):
+    # plant a preconditioner that points uphill (G = -g): every step must detect <G_L, z> <= 0
+    # and take the search gradient itself, i.e. follow the unpreconditioned PCG step for step
+    s = _cut(four, 6.0, 6.0)
+    Y0 = sy.initial_guess(s, 2, 6)
+    planted = osp.TruncatedPCG(osp.TruncatedOperator(s), Y0, precond="iter")
+    monkeypatch.setattr(planted, "apply_preconditioner", lambda g: -g)
+    plain = osp.TruncatedPCG(osp.TruncatedOperator(s), Y0, precond="none")
+    for _ in range(4):
+        (oa, ra), (ob, rb) = planted.step(), plain.step()
+        assert np.max(np.abs(oa - ob)) < 1e-12
+        assert np.max(np.abs(ra - rb)) < 1e-10 * max(1.0, np.max(rb))
+    assert planted.fallbacks == 4 and plain.fallbacks == 0
+
+
+def test_descending_preconditioner_is_kept(four):
+    # the inner CG of a well-posed truncated system descends: no fallback
+    s = _cut(four, 6.0, 6.0)
+    pcg = osp.TruncatedPCG(osp.TruncatedOperator(s), sy.initial_guess(s, 2, 6), precond="iter")
+    for _ in range(4):
+        pcg.step()
+    assert pcg.fallbacks == 0
