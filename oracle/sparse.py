@@ -71,6 +71,8 @@ class TruncatedOperator(Operator):
         self.Rv = self.Sv @ self.Pv
         self.Ac = self.Sc @ self.Pc @ self.Sc
         self.Av = self.Sv @ self.Pv @ self.Sv
+        self.RcT = self.Sc @ self.Pc        # R_c^T = (P^c S^chi)^T
+        self.RvT = self.Pv @ self.Sv        # R_v^T = (S^phi P^v)^T
 
     def T(self, X):
         return self.mask * X
@@ -108,7 +110,11 @@ class TruncatedOperator(Operator):
         return self.T(self.T(self.Rc @ (self.mask * L)) @ self.Rv)
 
     def l_gradient(self, g):
-        return self.T(self.T(self.Ac @ g) @ self.Av)
+        """The gradient of the sum functional with respect to L through the truncated map
+        P = T(T(R_c L) R_v): with the slope along D in P taken as <g, D> = sum cov(g) * D, it is
+        the map's adjoint applied to cov(g), T(R_c^T T(cov(g) R_v^T)) (the truncations of the map
+        in reverse order; without truncation this is S P^c S g S P^v S)."""
+        return self.T(self.RcT @ self.T(self.cov(g) @ self.RvT))
 
 
 class TruncatedPCG(PCG):

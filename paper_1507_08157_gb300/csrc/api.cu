@@ -1540,10 +1540,19 @@ void evaluate(tddft_ctx *c, tddft_state *S) {
     // g = f - swap(P) Q^T
     check(cudaMemcpyAsync(B.g, B.f, 2 * k * len * sizeof(T), cudaMemcpyDeviceToDevice, st), "copy g");
     combine<T>(st, B.coef, 2 * k, 2 * k, 2 * k, B.P, len, B.g, len, len, true);
-    if (c->trunc) {
-        // G_L = mask * (S P^c S) g (S P^v S); residual = Frobenius norm. With the exact
-        // preconditioner G_L only steers the search (its error changes the direction and the
-        // residual's last digits, not the fixed point, where g = 0): one TF32 MMA per product
+    if (c->sparse) {
+        // truncated form: G_L is the exact gradient of the sum functional with respect to L
+        // through the truncated map P = T(T(R_c L) R_v): its adjoint applied to the Frobenius
+        // gradient cov(g), G_L = T(R_c^T T(cov(g) R_v^T)); residual = Frobenius norm
+        covariant<T>(c, I, 2 * k, B.g, B.G1, B.tmp);
+        rprod<T>(c, I, B.G1, SP_T, B.tmp, 2 * k, T(1), T(0));
+        lprod<T>(c, I, SP_T, B.tmp, B.G1, 2 * k, T(1), T(0));
+        dots<T>(st, B.G1, len, B.G1, len, 2 * k, len, B.dvec, B.gscr);
+    } else if (c->trunc) {
+        // G_L = mask * (S P^c S) g (S P^v S) (the exact L-gradient when only L is truncated);
+        // residual = Frobenius norm. With the exact preconditioner G_L only steers the search
+        // (its error changes the direction and the residual's last digits, not the fixed point,
+        // where g = 0): one TF32 MMA per product
         sandwich_x<T>(c, I, 2 * k, SP_A, B.g, B.G1, B.tmp, I.exact);
         mask_mul<T>(st, B.G1, I.mask, len, 2 * k);
         dots<T>(st, B.G1, len, B.G1, len, 2 * k, len, B.dvec, B.gscr);

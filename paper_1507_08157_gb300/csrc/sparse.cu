@@ -688,6 +688,7 @@ std::unique_ptr<SparseLayout> sparse_build(cudaStream_t st, const tddft_sparse_s
     L->cc64[SP_M] = product(pP, Pc, pH, Hc, CB_R, L->pcc[SP_M]);
     L->cc64[SP_R] = product(pP, Pc, pS, Sc, CB_R, L->pcc[SP_R]);
     L->cc64[SP_A] = product(pS, Sc, L->pcc[SP_R], L->cc64[SP_R], CB_R, L->pcc[SP_A]);
+    L->cc64[SP_T] = product(pS, Sc, pP, Pc, CB_R, L->pcc[SP_T]);
     L->pvv[SP_S] = qS;
     L->vv64[SP_S] = Sv;
     L->pvv[SP_P] = qP;
@@ -695,6 +696,7 @@ std::unique_ptr<SparseLayout> sparse_build(cudaStream_t st, const tddft_sparse_s
     L->vv64[SP_M] = product(qH, Hv, qP, Pv, CB_C, L->pvv[SP_M]);
     L->vv64[SP_R] = product(qS, Sv, qP, Pv, CB_C, L->pvv[SP_R]);
     L->vv64[SP_A] = product(L->pvv[SP_R], L->vv64[SP_R], qS, Sv, CB_C, L->pvv[SP_A]);
+    L->vv64[SP_T] = product(qP, Pv, qS, Sv, CB_C, L->pvv[SP_T]);
     // pair lists of the products into the kernel pattern
     for (int x = 0; x < SP_NCONST; ++x) {
         L->left[x] = pair_list(m, L->pcc[x], L->pk, L->pk, CB_R, CB_R, CB_C);
@@ -718,11 +720,13 @@ std::unique_ptr<SparseLayout> sparse_build(cudaStream_t st, const tddft_sparse_s
         cc[SP_M] = bool_product(Pc_b, Hc_b);
         cc[SP_R] = bool_product(Pc_b, Sc_b);
         cc[SP_A] = bool_product(Sc_b, cc[SP_R]);
+        cc[SP_T] = bool_product(Sc_b, Pc_b);
         vv[SP_S] = Sv_b;
         vv[SP_P] = Pv_b;
         vv[SP_M] = bool_product(Hv_b, Pv_b);
         vv[SP_R] = bool_product(Sv_b, Pv_b);
         vv[SP_A] = bool_product(vv[SP_R], Sv_b);
+        vv[SP_T] = bool_product(Pv_b, Sv_b);
         for (int x = 0; x < SP_NCONST; ++x) {
             L->left[x].alg_flops = triple_flops(cc[x], pkT, pk, chi.cnt, chi.cnt, phi.cnt);
             L->right[x].alg_flops = triple_flops(pk, transpose_bits(vv[x]), pk, chi.cnt, phi.cnt, phi.cnt);

@@ -44,9 +44,11 @@ struct PairList {
 };
 
 // the constants of the operator and the solver, by role
-enum { SP_M = 0, SP_P = 1, SP_R = 2, SP_A = 3, SP_S = 4, SP_NCONST = 5 };
-// chi side: M_c = P^c_t H^chi, P^c_t, R_c = P^c_t S^chi, A_c = S^chi P^c_t S^chi, S^chi
-// phi side: M_v = H^phi P^v_t, P^v_t, R_v = S^phi P^v_t, A_v = S^phi P^v_t S^phi, S^phi
+enum { SP_M = 0, SP_P = 1, SP_R = 2, SP_A = 3, SP_S = 4, SP_T = 5, SP_NCONST = 6 };
+// chi side: M_c = P^c_t H^chi, P^c_t, R_c = P^c_t S^chi, A_c = S^chi P^c_t S^chi, S^chi,
+//           R_c^T = S^chi P^c_t
+// phi side: M_v = H^phi P^v_t, P^v_t, R_v = S^phi P^v_t, A_v = S^phi P^v_t S^phi, S^phi,
+//           R_v^T = P^v_t S^phi
 
 struct SparseLayout {
     Mem mem;

@@ -163,3 +163,23 @@ def test_descending_preconditioner_is_kept(four):
     for _ in range(4):
         pcg.step()
     assert pcg.fallbacks == 0
+
+
+def test_l_gradient_is_the_adjoint_of_the_truncated_map(four):
+    # <G_L(g), z>_F must equal the slope <g, P(z)> = sum cov(g) * P(z) for every g and every z on
+    # the pattern, with P(z) = T(T(R_c z) R_v): the L-gradient is exact for the truncated map
+    s = _cut(four, 5.0, 5.0)
+    op = osp.TruncatedOperator(s)
+    assert 0.0 < op.mask.mean() < 1.0 and op.Pc.astype(bool).sum() < s.P_c.astype(bool).sum()
+    rng = np.random.default_rng(3)
+    for _ in range(3):
+        g = rng.standard_normal(op.mask.shape)
+        z = op.mask * rng.standard_normal(op.mask.shape)
+        lhs = float(np.sum(op.l_gradient(g) * z))
+        rhs = op.inner(g, op.project(z))
+        assert abs(lhs - rhs) <= 1e-12 * max(1.0, abs(rhs))
+    # the untruncated-style expression T(T(A_c g) A_v) is not that gradient once products are cut
+    g = rng.standard_normal(op.mask.shape)
+    z = op.mask * rng.standard_normal(op.mask.shape)
+    naive = float(np.sum(op.T(op.T(op.Ac @ g) @ op.Av) * z))
+    assert abs(naive - op.inner(g, op.project(z))) > 1e-6 * abs(op.inner(g, op.project(z)))
