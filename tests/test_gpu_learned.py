@@ -7,7 +7,7 @@
 * the training rows the context extracts from a PCG iterate (features of the search gradient,
   targets from the inner-CG solve of Eq. precond);
 * PCG steps with the learned map (FP64 context) against the oracle's learned PCG;
-* the fixed point: learned PCG reaches the dense eigenvalues (plain PCG is the judge);
+* the fixed point: learned PCG reaches the dense eigenvalues (plain PCG is the reference);
 * a trained model against plain PCG on an unseen system: same eigenvalues (iterations and wall
   times of the learned, plain and unpreconditioned runs are printed).
 
@@ -171,7 +171,7 @@ def test_trained_model_gains_over_the_method_without_it(tddft):
     density (16 atoms, 20 A cell), then solve an unseen 24-atom system (k = 10, 1e-5 Ha, FP64) with
     the learned map, with no preconditioner (the method without the network) and with the plain
     inner-CG preconditioner. The learned PCG must reach the plain PCG's eigenvalues (plain PCG is
-    the judge) in fewer iterations than the unpreconditioned method. (Against plain PCG it loses:
+    the reference) in fewer iterations than the unpreconditioned method. (Against plain PCG it loses:
     the block-local map carries only part of Eq. precond's inverse; the benchmark's time_to_k
     block reports the three at the learned model's evaluation size.)"""
     import time
