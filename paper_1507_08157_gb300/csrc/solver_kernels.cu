@@ -1170,7 +1170,7 @@ void gram_multi(cudaStream_t st, const T *X, long long sx, int nx, int nset, con
     bool vec = len % VW == 0 && sx % VW == 0 && sy % VW == 0 && reinterpret_cast<uintptr_t>(X) % 16 == 0;
     for (int q = 0; q < nset; ++q) vec = vec && reinterpret_cast<uintptr_t>(Y[q]) % 16 == 0;
     const int gx = (nx + GQ - 1) / GQ, gy = (ny + GQ - 1) / GQ;
-    if (vec && nx + ny <= 256 * GMAXT / 16 && gx * gy <= 128) {
+    if (vec && len > 0 && nx + ny <= 256 * GMAXT / 16 && gx * gy <= 128) {
         // every row read once (all pairs of a slice in one block)
         constexpr int GC = gram_chunk<T>();
         const long long chunks = (len + GC - 1) / GC;
