@@ -26,10 +26,12 @@ Then (Eq. operator_RPA)
     f_q = T(M_c P^q) - T(P^q M_v) + 2 T(T(P^c_t V) P^v_t),   V = T(V_SCF[P^q]),
 the metric of the traces (Eqs. functional_RPA, ortho) is <X, Y> = sum_ab cov(X)_ab Y_ab with
 cov(X) = T(T(S^chi X) S^phi) (for untruncated matrices: Tr[X^T S^chi Y S^phi]),
-Eq. auxiliary is P = T(T(R_c L) R_v) with L on Pi, the L-gradient is T(T(A_c g) A_v), the
-preconditioner's operator (Eq. precond) T(M_c G) - T(G M_v), and the search gradient
-T(T(P^c_t G_L) P^v_t). The slope of the sum functional along a direction is taken in L space,
-<G_L, z>_F (equal to <g, Z> in exact untruncated arithmetic).
+Eq. auxiliary is P = T(T(R_c L) R_v) with L on Pi, the L-gradient is that map's adjoint applied
+to cov(g), G_L = T(R_c^T T(cov(g) R_v^T)), the preconditioner's operator (Eq. precond)
+T(M_c G) - T(G M_v), and the search gradient T(T(P^c_t G_L) P^v_t). The slope of the sum
+functional along a direction is taken in L space, <G_L, z>_F, which equals <g, Z> with
+Z = T(T(R_c z) R_v) exactly. When the inner CG's result does not descend (<G_L, z> <= 0: the
+truncated operator need not be positive definite) the step takes the search gradient itself.
 
 With both cutoffs covering the cell every mask is all ones and this is the plain O2 oracle.
 """
