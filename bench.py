@@ -244,7 +244,7 @@ def cpu_oracle_sample(sys_, target_s=15.0):
     per_apply = t_fixed + spent * len(groups) / max(m, 1)
     cores, model = host_cpu()
     return {"value": 1.0 / per_apply, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": model,
-            "estimate": True, "timed_s": t_fixed + spent,
+            "estimate": m < len(groups), "timed_s": t_fixed + spent,
             "sample": (f"one state-pair application: matrix products and FFT Poisson solve in full, "
                        f"grid contractions on the chi functions of {m} of {len(groups)} atoms "
                        f"({spent:.1f} s), scaled linearly; numpy/scipy float64, BLAS threads = all cores")}
