@@ -180,8 +180,10 @@ void tddft_destroy(tddft_ctx *ctx);
  *    pairs within kernel_cutoff), a chain of two products after each one; so Eq. operator_RPA
  *    reads f_p = T(M_c P^p) - T(P^p M_v), f_q = T(M_c P^q) - T(P^q M_v) + 2 T(T(P^c_t V) P^v_t)
  *    with V = T(V_SCF[P^q]), the trace metric is <X, Y> = sum cov(X) * Y with
- *    cov(X) = T(T(S^chi X) S^phi), Eq. auxiliary is P = T(T(R_c L) R_v), the L-gradient
- *    T(T(A_c g) A_v), Eq. precond's operator T(M_c G) - T(G M_v).
+ *    cov(X) = T(T(S^chi X) S^phi), Eq. auxiliary is P = T(T(R_c L) R_v), the L-gradient is
+ *    that map's adjoint applied to cov(g), T(R_c^T T(cov(g) R_v^T)) (the exact gradient of the
+ *    sum functional in L), Eq. precond's operator T(M_c G) - T(G M_v); a step whose inner-CG
+ *    result does not descend takes the search gradient instead (counted in tddft_state_stats).
  * Every chi x phi array at the boundary of a sparse context (tddft_apply, tddft_state_create,
  * tddft_state_get, tddft_response_density's P, tddft_potential_integrals' out) is [k][nnz]: the
  * values of the kernel pattern in the atom-blocked order tddft_kernel_pattern describes. Inside,
