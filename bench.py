@@ -284,8 +284,9 @@ def run_reference(args):
             "config": {"workload": workload_name(args), "states": args.k, "precision": "fp64"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": model,
                              "sample": r["sample"]},
-            "estimate": "each step times a bounded sample of one application and scales its grid "
-                        "contractions to the whole system: value and ms_per_step are extrapolated",
+            "estimate": ("each step times a bounded sample of one application and scales its grid "
+                         "contractions to the whole system: value and ms_per_step are extrapolated")
+                        if r["estimate"] else None,
             "timed_s_per_step": float(np.mean(timed)),
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
